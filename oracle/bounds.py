@@ -1,0 +1,107 @@
+"""Error estimators: bin widths and error norms (oracle; test infrastructure).
+
+The paper ("Software design") says compression quantizes every multilevel
+coefficient to a multiple of a bin width, that the widths come from error
+estimators taking the quantization errors as inputs, and that the bound is
+guaranteed in several norms selected by the smoothness parameter ``s``.  It
+gives no constants.  The widths below are derived here from the P1
+definitions (readings, listed in full in the design notes):
+
+L-infinity (``s = inf``)
+    Recomposition of quantization errors ``delta_l`` (|delta_l| <= w/2) adds at
+    level l the correction ``C_l delta_l`` to the coarse nodes and
+    ``delta_l`` plus interpolated values (a convex combination) to the new
+    nodes, so ``||e||_inf <= ||delta_0|| + sum_{l>=1} (1 + K_l) ||delta_l||``
+    with ``K_l = prod_d ||(M^d_{l-1})^{-1} (P^d)^T M^d_l||_inf`` (exact 1D
+    row-sum norms).  One width for every level:
+    ``w = 2 tau / (1 + sum_l (1 + K_l))``.
+
+s-norm (finite ``s >= 0``)
+    ``||e||_s^2 = sum_{l=0..L} 4^{s l} ||(Q_l - Q_{l-1}) e||^2`` (``Q_{-1} = 0``;
+    ``s = 0`` is the L2 norm by orthogonality).  The level-l term is at most
+    ``delta_l^T M_l delta_l <= mu_l ||delta_l||_2^2`` with the Gershgorin bound
+    ``mu_l = prod_d max_i (h_{i-1} + h_i) / 2``, so
+    ``w_l = 2 tau / sqrt((L + 1) 4^{s l} mu_l n_l)`` with ``n_l`` the number
+    of new nodes on level l.
+
+Every width is then multiplied by ``1 - 2^-8``.  That margin absorbs the
+rounding of a single-precision quantizer (``x = c * (1/w)`` and ``q * w``
+each rounded to float32 for ``|q| < 2048``), so ``|c - q w| <= w_bound / 2``
+holds for it too.
+
+Relative tolerances scale by ``max|u|`` (L-infinity) or ``||u||_s``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import fem
+from .grid import Hierarchy, hierarchy
+from .multilevel import mass_norm2, projections
+
+WIDTH_MARGIN = 1.0 - 2.0 ** -8
+
+
+def correction_norm_1d(h: Hierarchy, l: int, d: int) -> float:
+    """``||(M_{l-1})^{-1} P^T M_l||_inf`` on axis d (dense, exact in FP64)."""
+    xf, xc = h.coords(l, d), h.coords(l - 1, d)
+    P = fem.prolongation(xf, xc).toarray()
+    Mf = fem.mass_matrix(xf).toarray()
+    Mc = fem.mass_matrix(xc).toarray()
+    A = np.linalg.solve(Mc, P.T @ Mf)
+    return float(np.abs(A).sum(axis=1).max())
+
+
+def K(h: Hierarchy, l: int) -> float:
+    k = 1.0
+    for d in range(h.D):
+        k *= correction_norm_1d(h, l, d)
+    return k
+
+
+def mu(h: Hierarchy, l: int) -> float:
+    m = 1.0
+    for d in range(h.D):
+        x = h.coords(l, d)
+        hh = np.diff(x)
+        left = np.concatenate([[0.0], hh])
+        right = np.concatenate([hh, [0.0]])
+        m *= float(np.max((left + right) / 2.0))
+    return m
+
+
+def bin_widths(shape, tol_abs: float, s: float, max_levels=None) -> np.ndarray:
+    """Quantization bin width of every level 0..L (FP64)."""
+    h = hierarchy(shape, max_levels)
+    L = h.L
+    if math.isinf(s):
+        denom = 1.0 + sum(1.0 + K(h, l) for l in range(1, L + 1))
+        w = np.full(L + 1, 2.0 * tol_abs / denom)
+    else:
+        w = np.empty(L + 1)
+        for l in range(L + 1):
+            m = mu(h, l) if h.D else 1.0
+            n = h.new_count(l) if h.D else 1
+            w[l] = 2.0 * tol_abs / math.sqrt((L + 1) * 4.0 ** (s * l) * m * n)
+    return w * WIDTH_MARGIN
+
+
+def s_norm(u: np.ndarray, s: float, max_levels=None) -> float:
+    """``||u||_s`` from the projections ``Q_l u`` (FP64)."""
+    h = hierarchy(u.shape, max_levels)
+    if h.D == 0:
+        return float(abs(np.asarray(u, dtype=np.float64).reshape(-1)[0]))
+    Q = projections(u, max_levels)
+    E = [mass_norm2(h, l, Q[l]) for l in range(h.L + 1)]
+    total = E[0]
+    for l in range(1, h.L + 1):
+        total += 4.0 ** (s * l) * max(E[l] - E[l - 1], 0.0)
+    return math.sqrt(max(total, 0.0))
+
+
+def norm(u: np.ndarray, s: float, max_levels=None) -> float:
+    if math.isinf(s):
+        return float(np.max(np.abs(np.asarray(u, dtype=np.float64))))
+    return s_norm(u, s, max_levels)

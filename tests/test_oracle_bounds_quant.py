@@ -1,0 +1,130 @@
+"""Pins for the oracle's error estimators and quantizer: operator norms
+against brute-force operators, the bound on adversarial and random
+quantization errors, rounding rules and the symbol layout."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bounds, grid, multilevel, pipeline, quantize
+
+
+def _correction_matrix_1d(n, l):
+    """Dense matrix of the oracle's coarse correction on a 1D level, built by
+    applying it to unit vectors (brute force)."""
+    h = grid.hierarchy((n,))
+    m = len(h.idx[l][0])
+    cols = []
+    for j in range(m):
+        z = np.zeros(m)
+        z[j] = 1.0
+        cols.append(multilevel.correction(h, l, z))
+    return np.array(cols).T, h
+
+
+@pytest.mark.parametrize("n", [5, 6, 9, 17, 30])
+def test_K_is_the_row_sum_norm_of_the_applied_correction(n):
+    A, h = _correction_matrix_1d(n, grid.hierarchy((n,)).L)
+    assert abs(np.abs(A).sum(axis=1).max() - bounds.K(h, h.L)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(9,), (9, 9), (9, 5, 6), (5, 5, 5, 5), (65, 65, 65)])
+def test_K_below_classical_bound(shape):
+    h = grid.hierarchy(shape)
+    for l in range(1, h.L + 1):
+        assert 0 < bounds.K(h, l) <= 3.0 ** h.D
+
+
+def _levels_and_masks(shape):
+    h = grid.hierarchy(shape)
+    lev = grid.node_level(h)
+    return h, lev
+
+
+@pytest.mark.parametrize("shape", [(17,), (9, 9), (9, 6, 5)])
+def test_linf_bound_holds_for_adversarial_errors(shape):
+    """Quantization errors of +-w/2 with the signs that maximise the error at
+    one node: the error reaches a fair part of tau but never exceeds it."""
+    h, lev = _levels_and_masks(shape)
+    tau = 1.0
+    w = bounds.bin_widths(shape, tau, math.inf)[0] / bounds.WIDTH_MARGIN
+    n = int(np.prod(shape))
+    # influence of each coefficient on every output node (recompose is linear)
+    Rm = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Rm[:, j] = multilevel.recompose(e.reshape(shape)).reshape(-1)
+    worst = np.abs(Rm).sum(axis=1).max() * w / 2
+    assert worst <= tau * (1 + 1e-12)
+    assert worst >= 0.1 * tau       # the bound is not vacuous
+    i = int(np.argmax(np.abs(Rm).sum(axis=1)))
+    delta = np.sign(Rm[i]) * w / 2
+    err = np.abs(Rm @ delta).max()
+    assert err <= tau * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("s", [math.inf, 0.0, 1.0])
+@pytest.mark.parametrize("shape", [(33,), (17, 17), (9, 9, 9)])
+def test_bound_holds_for_random_errors(shape, s):
+    rng = np.random.default_rng(7)
+    h, lev = _levels_and_masks(shape)
+    tau = 0.3
+    widths = bounds.bin_widths(shape, tau, s) / bounds.WIDTH_MARGIN
+    for _ in range(5):
+        delta = rng.uniform(-0.5, 0.5, size=shape) * widths[lev]
+        e = multilevel.recompose(delta)
+        assert bounds.norm(e, s) <= tau * (1 + 1e-12)
+
+
+def test_s0_norm_is_l2_norm_of_p1_function():
+    """For s = 0 the s-norm is the L2 norm of the interpolant; for a linear
+    function on [0, 8] its square is the closed form integral."""
+    x = np.arange(9, dtype=float)
+    u = 2.0 * x - 3.0
+    exact = ((2 * 8 - 3) ** 3 - (-3) ** 3) / (3 * 2.0)   # int_0^8 (2x-3)^2 dx
+    assert abs(bounds.s_norm(u, 0.0) ** 2 - exact) < 1e-10
+
+
+def test_rounding_ties_to_even_and_escapes():
+    w = 0.5
+    c = np.array([1.25, 0.75, -1.25, 2047.4 * w, 2047.6 * w, -3000 * w, 0.0])
+    sym, out, hist = quantize.quantize_levels([c], [w])
+    assert sym.tolist() == [2 + 2048, 2 + 2048, -2 + 2048, 2047 + 2048, 0, 0, 2048]
+    assert out.tolist() == [2048, -3000]
+    assert hist.sum() == len(c) and hist[0] == 2
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_dequantized_error_within_half_bound_width(precision):
+    rng = np.random.default_rng(8)
+    w = 3.7e-3
+    c = rng.uniform(-2100 * w, 2100 * w, 20000)
+    if precision == "f32":
+        c = c.astype(np.float32)
+    # points near half-integers are the hard cases
+    c[:2000] = ((rng.integers(-2047, 2047, 2000) + 0.5) * w).astype(c.dtype)
+    sym, out, _ = quantize.quantize_levels([c], [w], precision)
+    back = quantize.dequantize_levels(sym, out, [len(c)], [w], precision)[0]
+    err = np.abs(back.astype(np.float64) - c.astype(np.float64))
+    assert err.max() <= 0.5 * w / bounds.WIDTH_MARGIN
+
+
+@pytest.mark.parametrize("shape", [(9, 6, 7), (17, 17), (5, 5, 5, 5)])
+def test_symbol_layout_round_trip(shape):
+    u = np.random.default_rng(9).standard_normal(shape)
+    levels = multilevel.level_coefficients(u)
+    assert [len(a) for a in levels] == quantize.level_counts(shape)
+    assert sum(quantize.level_counts(shape)) == u.size
+    back = quantize.scatter_levels(levels, shape)
+    assert np.array_equal(back, u)
+
+
+@pytest.mark.parametrize("s", [math.inf, 0.0, 1.0])
+def test_pipeline_meets_tolerance(s):
+    from paper_2401_05994_b300 import synth
+    u = synth.sinusoids_2d(65, 65, seed=3)
+    for tol in (1e-2, 1e-4):
+        c = pipeline.compress(u, tol, s=s)
+        ud = pipeline.decompress(c, symbols=c["symbols"])
+        assert pipeline.error(u, ud, s) <= c["tol_abs"]
