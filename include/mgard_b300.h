@@ -1,0 +1,211 @@
+/*
+ * mgard_b300.h -- C ABI of a B300 (sm_103a) implementation of MGARD's
+ * multilevel decomposition, level-wise quantization and Huffman coding.
+ *
+ * The operations follow the MGARD paper (Gong et al., "MGARD: A multigrid
+ * framework for high-performance, error-controlled data compression and
+ * refactoring"): "Software design" (decomposition of u into multilevel
+ * coefficients u_mc, linear quantization to multiples of a bin width chosen
+ * by error estimators from tau and s, lossless encoding into a
+ * self-describing buffer; decompression is the inverse procedure), "APIs"
+ * (high-level compress/decompress with buffer-location detection; low-level
+ * per-step functions with device asynchrony) and Listing 1 (the argument
+ * list of compress/decompress).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays are row-major (last axis contiguous), 1 <= ndim <= 4, every
+ *    extent >= 1.  Axes of extent 1 are ignored.  Level L is the input grid;
+ *    along an axis the next coarser level keeps the even positions plus the
+ *    last one; L = min over axes of the number of such coarsenings before an
+ *    axis has two nodes (capped by max_levels when max_levels >= 0).
+ *  - dtype selects float (MGARD_F32) or double (MGARD_F64) data.  F32 data is
+ *    decomposed in float with float accumulation; the restriction and
+ *    tridiagonal solves of coarse grids (fewer than 2^21 nodes) run in double.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered.  Functions documented as taking device pointers require
+ *    pointers to device (or managed) memory of the current device.
+ *  - Every function returns a status; nothing is thrown and no function
+ *    aborts the process.  A failing CUDA call is reported as MGARD_ECUDA
+ *    (MGARD_ENOMEM for allocations) with its text in mgard_last_error().
+ *  - The library keeps per-shape tables (the "plan") in device memory for
+ *    the life of the process; mgard_release_plans() drops them.  Workspace is
+ *    taken from the stream-ordered allocator (cudaMallocAsync) on `stream`.
+ */
+#ifndef MGARD_B300_H
+#define MGARD_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MGARD_OK = 0,
+    MGARD_EINVAL = 1,     /* bad argument (tolerance <= 0 or NaN, s < 0, null pointer, ...) */
+    MGARD_ESHAPE = 2,     /* ndim outside 1..4 or an extent < 1 */
+    MGARD_EDTYPE = 3,     /* unknown dtype */
+    MGARD_ENONFINITE = 4, /* input holds NaN or Inf */
+    MGARD_ENOMEM = 5,     /* device or host allocation failed */
+    MGARD_ECUDA = 6,      /* a CUDA runtime call failed */
+    MGARD_ECORRUPT = 7,   /* compressed buffer fails validation */
+    MGARD_EBOUND = 8,     /* verification found the error above the tolerance */
+    MGARD_ETIMEOUT = 9,   /* a bounded device wait gave up */
+    MGARD_ECAPACITY = 10, /* preallocated output too small; required size returned */
+    MGARD_ERANGE = 11     /* tolerance so small that a quantized value exceeds 32 bits */
+} mgard_status;
+
+typedef enum { MGARD_F32 = 0, MGARD_F64 = 1 } mgard_dtype;
+typedef enum { MGARD_ABS = 0, MGARD_REL = 1 } mgard_tolmode;
+
+/* Size of the quantization dictionary and the escape symbol.  Symbol
+ * q + MGARD_DICT/2 codes |q| < MGARD_DICT/2; symbol 0 marks an outlier whose
+ * value q is carried separately as a 32-bit integer. */
+#define MGARD_DICT 4096
+#define MGARD_ESC 0
+/* Huffman stream: chunks of MGARD_CHUNK symbols, each starting on a 32-bit
+ * word, bits MSB-first within a word; codes are at most MGARD_LMAX bits. */
+#define MGARD_CHUNK 1024
+#define MGARD_LMAX 32
+
+const char* mgard_strerror(mgard_status status);
+/* Text of the most recent failure in the calling thread ("" if none). */
+const char* mgard_last_error(void);
+/* Library version as 0xMMmmpp. */
+uint32_t mgard_version(void);
+
+/* Number of levels L for a shape (after squeezing extent-1 axes). */
+mgard_status mgard_levels(int ndim, const int64_t* shape, int max_levels, int* nlevels);
+
+/* ---- Low-level API: decomposition ("Software design", first paragraph) ---
+ * In-place multilevel decomposition of `data` (device pointer, `dtype`).
+ * On return (stream-ordered) every node holds the coefficient of the level
+ * on which it first appears: c = u_l - (multilinear interpolation of the
+ * level-(l-1) values), where u_l are the nodal values of the L2 projection
+ * of the piecewise-multilinear u onto level l; level-0 nodes hold the
+ * values of the projection onto level 0.  Workspace: about 1/7 of the
+ * array for the coarser levels plus two restriction buffers of at most
+ * half of it.  May return before the device work completes. */
+mgard_status mgard_decompose(void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                             int max_levels, void* stream);
+/* Inverse of mgard_decompose, in place (device pointer). */
+mgard_status mgard_recompose(void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                             int max_levels, void* stream);
+
+/* ---- Low-level API: error estimators ("Software design", second paragraph)
+ * Bin widths w_0..w_L (host array of L+1 doubles) for an absolute
+ * tolerance.  s = INFINITY selects the L-infinity bound
+ *   w = 2 tau / (1 + sum_{l=1..L} (1 + K_l)),
+ *   K_l = prod_d ||(M^d_{l-1})^{-1} (P^d)^T M^d_l||_inf,
+ * finite s >= 0 the s-norm bound
+ *   w_l = 2 tau / sqrt((L+1) 4^{s l} mu_l n_l),
+ *   mu_l = prod_d max_i (h_{i-1}+h_i)/2, n_l = nodes new on level l;
+ * every width is multiplied by (1 - 2^-8) so float32 quantization rounding
+ * stays inside the bound.  Host-only (builds the plan on first use). */
+mgard_status mgard_bin_widths(int ndim, const int64_t* shape, int max_levels, double tol_abs,
+                              double s, double* widths, int* nlevels);
+
+/* Norm of a field (device pointer): s = INFINITY gives max|u|; finite s
+ * gives ||u||_s with ||u||_s^2 = sum_l 4^{s l} ||(Q_l - Q_{l-1}) u||_{L2}^2
+ * (s = 0: the L2 norm of the piecewise-multilinear interpolant).  FP64
+ * accumulation; the projections are computed in the data's precision.
+ * Synchronizes the stream; result in *out (host). */
+mgard_status mgard_norm(const void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                        int max_levels, double s, double* out, void* stream);
+/* The same norm of the difference b - a (device pointers), evaluated with
+ * the difference and its projections in FP64 (verification of the error
+ * bound).  MGARD_ENONFINITE if either array holds NaN or Inf. */
+mgard_status mgard_error_norm(const void* a, const void* b, int ndim, const int64_t* shape,
+                              mgard_dtype dtype, int max_levels, double s, double* out,
+                              void* stream);
+
+/* ---- Low-level API: quantization ("Software design", second paragraph) --
+ * Quantize an in-place decomposed array (device pointer) with bin widths
+ * `widths` (host, L+1 entries).  Symbols are written in level order (level
+ * 0 nodes, then the nodes new on levels 1..L, each in row-major order of
+ * that level's grid): n = product of the extents symbols in total.  F32 data
+ * decides q = rint(float(c) * float(1/w)) in float; F64 data
+ * q = rint(c / w) in double.  |q| < MGARD_DICT/2 -> symbol q + MGARD_DICT/2,
+ * else MGARD_ESC and escapes[position] = rint(c / w) (double, as int32).
+ * hist (device, MGARD_DICT uint64) is overwritten with symbol counts.
+ * symbols, escapes: device arrays of n entries.  Synchronizes the stream;
+ * MGARD_ERANGE if some |rint(c/w)| > 2^31-1, MGARD_ENONFINITE for NaN/Inf. */
+mgard_status mgard_quantize(const void* coeffs, int ndim, const int64_t* shape, mgard_dtype dtype,
+                            int max_levels, const double* widths, uint16_t* symbols,
+                            int32_t* escapes, uint64_t* hist, void* stream);
+/* Inverse: writes the in-place coefficient array (device pointer) from
+ * symbols and escapes (device, n entries each): c = q * w (float32 product
+ * for F32 symbols; double product rounded to the dtype for escapes). */
+mgard_status mgard_dequantize(const uint16_t* symbols, const int32_t* escapes, int ndim,
+                              const int64_t* shape, mgard_dtype dtype, int max_levels,
+                              const double* widths, void* coeffs, void* stream);
+
+/* ---- Low-level API: Huffman coding ("Software design", third paragraph) --
+ * Code lengths (device uint8[MGARD_DICT]) and canonical codes (device
+ * uint32[MGARD_DICT]) from a histogram (device uint64[MGARD_DICT]).  Leaves
+ * (symbols with nonzero count) sorted by (count, symbol) are merged with two
+ * FIFO queues, leaf queue first on equal weight; lengths over MGARD_LMAX
+ * repeat the construction on max(1, count >> k) for the smallest k >= 1 that
+ * fits; a single used symbol gets length 1.  Canonical codes are consecutive
+ * in (length, symbol) order. */
+mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint32_t* codes,
+                                    void* stream);
+/* Encode n symbols (device) with code lengths `lengths` (device).  Outputs
+ * (device): words (capacity `words_cap` uint32), word_off / esc_off
+ * (ceil(n / MGARD_CHUNK) uint64 each: exclusive prefix of per-chunk word
+ * counts and escape counts), outliers (escapes gathered in symbol order from
+ * `escapes`, which is indexed by symbol position; capacity `outliers_cap`).
+ * *nwords and *noutliers (host) receive the totals; synchronizes the
+ * stream.  MGARD_ECAPACITY (totals still returned, nothing packed) if a
+ * capacity is short; MGARD_EINVAL if a symbol has no code. */
+mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uint8_t* lengths,
+                                  const int32_t* escapes, uint32_t* words, uint64_t words_cap,
+                                  uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
+                                  uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers,
+                                  void* stream);
+/* Decode n symbols (device output) from a stream produced by
+ * mgard_huffman_encode; escapes[position] receives each outlier value.
+ * Reads never leave the stream: a chunk that runs past its end or holds an
+ * invalid code gives MGARD_ECORRUPT (synchronizes the stream). */
+mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                  const uint8_t* lengths, uint64_t n, const int32_t* outliers,
+                                  uint64_t noutliers, const uint64_t* esc_off, uint16_t* symbols,
+                                  int32_t* escapes, void* stream);
+
+/* ---- High-level API (Listing 1: compress / decompress) -----------------
+ * Upper bound on the compressed size in bytes for a shape. */
+size_t mgard_compress_bound(int ndim, const int64_t* shape, mgard_dtype dtype);
+
+/* Compress `field` (host or device pointer; the location is detected).
+ * tol > 0; s = INFINITY for L-infinity, else s >= 0 for the s-norm; mode
+ * MGARD_REL scales tol by max|u| (L-infinity) or ||u||_s.
+ * out_preallocated = 0: *out receives a new buffer (device memory if field
+ * is on the device, host memory otherwise) to be released with mgard_free;
+ * out_preallocated = 1: *out is the caller's buffer (host or device) of
+ * *out_bytes capacity.  In both cases *out_bytes receives the size.
+ * Synchronizes the stream before returning. */
+mgard_status mgard_compress(const void* field, int ndim, const int64_t* shape, mgard_dtype dtype,
+                            double tol, double s, mgard_tolmode mode, void** out,
+                            size_t* out_bytes, int out_preallocated, void* stream);
+/* Decompress a buffer made by mgard_compress (host or device pointer).
+ * out_preallocated = 0: *field receives a new buffer (device memory if the
+ * compressed buffer is on the device) to be released with mgard_free;
+ * = 1: *field is the caller's buffer (host or device), large enough for the
+ * shape.  Header and section bounds are validated (MGARD_ECORRUPT).
+ * Synchronizes the stream before returning. */
+mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
+                              int out_preallocated, void* stream);
+/* Read the header of a compressed buffer (host or device pointer). */
+mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
+                        mgard_dtype* dtype, double* tol_abs, int* nlevels);
+/* Release a buffer allocated by this library (host or device). */
+void mgard_free(void* p);
+/* Drop cached per-shape tables. */
+void mgard_release_plans(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGARD_B300_H */

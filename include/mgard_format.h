@@ -1,0 +1,55 @@
+/*
+ * mgard_format.h -- layout of the self-describing compressed buffer.
+ *
+ * The paper ("APIs", high-level features) asks for output that carries
+ * everything a decompressor needs: version, error bounds, data topology and
+ * encoder.  This build stores, little-endian:
+ *
+ *   mgard_header                      (fixed size, below)
+ *   widths    [nlevels + 1] double    bin width of each level
+ *   lengths   [dict] uint8            Huffman code length per symbol
+ *   word_off  [nchunks] uint64        exclusive prefix of words per chunk
+ *   esc_off   [nchunks] uint64        exclusive prefix of escapes per chunk
+ *   outliers  [noutliers] int32       escaped quantized values, symbol order
+ *   words     [nwords] uint32         Huffman payload
+ *
+ * Every section starts at the byte offset recorded in the header, a
+ * multiple of 16.  Decompression rejects a buffer whose magic, version,
+ * sizes or offsets are inconsistent (MGARD_ECORRUPT).
+ */
+#ifndef MGARD_FORMAT_H
+#define MGARD_FORMAT_H
+
+#include <stdint.h>
+
+#define MGARD_MAGIC "MGARDB3"
+#define MGARD_FORMAT_VERSION 1u
+
+typedef struct {
+    char magic[8];        /* "MGARDB3\0" */
+    uint32_t version;     /* MGARD_FORMAT_VERSION */
+    uint32_t dtype;       /* mgard_dtype */
+    uint32_t ndim;        /* as passed to compress */
+    uint32_t nlevels;     /* L */
+    int64_t shape[4];     /* as passed to compress; unused entries 1 */
+    double s;             /* smoothness; +infinity for L-infinity */
+    double tol;           /* requested tolerance */
+    double tol_abs;       /* absolute tolerance the widths were derived from */
+    uint32_t mode;        /* mgard_tolmode */
+    uint32_t dict;        /* dictionary size (MGARD_DICT) */
+    uint32_t chunk;       /* symbols per chunk (MGARD_CHUNK) */
+    uint32_t reserved;
+    uint64_t nsymbols;    /* product of the extents */
+    uint64_t nchunks;
+    uint64_t nwords;
+    uint64_t noutliers;
+    uint64_t off_widths;
+    uint64_t off_lengths;
+    uint64_t off_word_off;
+    uint64_t off_esc_off;
+    uint64_t off_outliers;
+    uint64_t off_words;
+    uint64_t total_bytes;
+} mgard_header;
+
+#endif /* MGARD_FORMAT_H */

@@ -1,0 +1,723 @@
+// C ABI (include/mgard_b300.h): argument checks, workspace, buffer-location
+// detection and the self-describing format (include/mgard_format.h).
+//
+// Paper, "APIs": the high-level calls take the data, shape, dtype, tau, s
+// and the bound type (Listing 1), detect where the buffers live and move
+// data as needed; the low-level calls expose each step with device
+// asynchrony.  Pipelines here:
+//   compress:   [norm] -> decompose -> widths -> quantize+histogram ->
+//               codebook -> count/scan -> pack -> header
+//   decompress: header checks -> tables -> decode -> dequantize -> recompose
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mgard_format.h"
+#include "huffman.cuh"
+#include "multilevel.cuh"
+#include "quantize.cuh"
+
+namespace mgb {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+mgard_status check_dtype(mgard_dtype d) {
+    if (d != MGARD_F32 && d != MGARD_F64) {
+        set_error("dtype must be MGARD_F32 or MGARD_F64");
+        return MGARD_EDTYPE;
+    }
+    return MGARD_OK;
+}
+
+mgard_status status_to_error(unsigned st) {
+    if (st & ST_NONFINITE) {
+        set_error("input holds NaN or Inf");
+        return MGARD_ENONFINITE;
+    }
+    if (st & ST_RANGE) {
+        set_error("tolerance too small: a quantized value exceeds the 32-bit range");
+        return MGARD_ERANGE;
+    }
+    if (st & ST_CORRUPT) {
+        set_error("compressed stream is corrupt");
+        return MGARD_ECORRUPT;
+    }
+    if (st & ST_NOCODE) {
+        set_error("a symbol has no Huffman code");
+        return MGARD_EINVAL;
+    }
+    return MGARD_OK;
+}
+
+// Layout of the sections after the header.
+struct Sections {
+    size_t widths, lengths, word_off, esc_off, outliers, words, total;
+};
+
+Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords) {
+    Sections s;
+    size_t o = align16(sizeof(mgard_header));
+    s.widths = o;
+    o = align16(o + 8 * (size_t)(L + 1));
+    s.lengths = o;
+    o = align16(o + DICT);
+    s.word_off = o;
+    o = align16(o + 8 * nchunks);
+    s.esc_off = o;
+    o = align16(o + 8 * nchunks);
+    s.outliers = o;
+    o = align16(o + 4 * nout);
+    s.words = o;
+    o = align16(o + 4 * nwords);
+    s.total = o;
+    return s;
+}
+
+double s_norm_from_levels(const std::vector<double>& E, double s) {
+    double total = E[0];
+    for (size_t l = 1; l < E.size(); ++l) total += std::pow(4.0, s * (double)l) * std::max(E[l] - E[l - 1], 0.0);
+    return std::sqrt(std::max(total, 0.0));
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+mgard_status norm_impl(const Plan& p, const T* data, double s, double* out, cudaStream_t st) {
+    const int64_t N = p.total();
+    if (std::isinf(s)) {
+        unsigned status = 0;
+        MGB_TRY(max_abs<T>(data, nullptr, N, out, &status, st));
+        return status_to_error(status);
+    }
+    unsigned status = 0;
+    double dummy;
+    MGB_TRY(max_abs<T>(data, nullptr, N, &dummy, &status, st));
+    MGB_TRY(status_to_error(status));
+    Pyramid<T> py;
+    MGB_TRY(py.alloc(p, st));
+    DevBuf top;
+    MGB_TRY(top.alloc(N * sizeof(T), st));
+    std::vector<double> E(p.L + 1, 0.0);
+    MGB_TRY(decompose_pyramid<T>(p, data, top.as<T>(), py, st, E.data()));
+    *out = s_norm_from_levels(E, s);
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mgard_dtype dtype,
+                           int ndim, const int64_t* shape, double tol, double s,
+                           mgard_tolmode mode, void** out, size_t* out_bytes, int prealloc,
+                           cudaStream_t st) {
+    const int64_t N = p.total();
+    const int L = p.L;
+    DevBuf inbuf;
+    const T* din = (const T*)field;
+    if (!field_dev) {
+        MGB_TRY(inbuf.alloc(N * sizeof(T), st));
+        MGB_CUDA(cudaMemcpyAsync(inbuf.p, field, N * sizeof(T), cudaMemcpyHostToDevice, st));
+        din = inbuf.as<T>();
+    }
+    Pyramid<T> py;
+    MGB_TRY(py.alloc(p, st));
+    DevBuf top;
+    MGB_TRY(top.alloc(N * sizeof(T), st));
+    double tol_abs = tol;
+    bool decomposed = false;
+    {
+        unsigned status = 0;
+        double m = 0.0;
+        MGB_TRY(max_abs<T>(din, nullptr, N, &m, &status, st));
+        MGB_TRY(status_to_error(status));
+        if (mode == MGARD_REL) {
+            double nrm = m;
+            if (!std::isinf(s)) {
+                std::vector<double> E(L + 1, 0.0);
+                MGB_TRY(decompose_pyramid<T>(p, din, top.as<T>(), py, st, E.data()));
+                decomposed = true;
+                nrm = s_norm_from_levels(E, s);
+            }
+            tol_abs = nrm > 0.0 ? tol * nrm : tol;   // an all-zero field keeps tol as absolute
+        }
+    }
+    if (!decomposed) MGB_TRY(decompose_pyramid<T>(p, din, top.as<T>(), py, st, nullptr));
+    std::vector<double> w(L + 1);
+    bin_widths(p, tol_abs, s, w.data());
+
+    DevBuf sym, esc, hist, stat, lengths, codes, dt, offs, totals;
+    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
+    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    MGB_TRY(hist.alloc(DICT * sizeof(unsigned long long), st));
+    MGB_TRY(stat.alloc(sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(hist.p, 0, DICT * sizeof(unsigned long long), st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
+    for (int l = 0; l <= L; ++l) {
+        const T* lvl = l == L ? (L ? top.as<T>() : din) : py.lv[l];
+        MGB_TRY(quantize_level<T>(p, l, lvl, false, w[l], sym.as<uint16_t>(), esc.as<int32_t>(),
+                                  hist.as<unsigned long long>(), stat.as<unsigned>(), st));
+    }
+    MGB_TRY(lengths.alloc(DICT, st));
+    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(huffman_codebook(hist.as<unsigned long long>(), lengths.as<uint8_t>(), nullptr, st));
+    MGB_TRY(huffman_tables(lengths.as<uint8_t>(), codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    MGB_TRY(offs.alloc(16 * nchunks + 16, st));
+    MGB_TRY(totals.alloc(2 * sizeof(unsigned long long), st));
+    uint64_t* word_off = offs.as<uint64_t>();
+    uint64_t* esc_off = word_off + nchunks;
+    MGB_TRY(huffman_count(sym.as<uint16_t>(), N, lengths.as<uint8_t>(), word_off, esc_off,
+                          totals.as<unsigned long long>(), stat.as<unsigned>(), st));
+    unsigned long long tot[2];
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(tot, totals.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    MGB_TRY(status_to_error(status));
+    const uint64_t nwords = tot[0], nout = tot[1];
+    const Sections sec = layout(L, nchunks, nout, nwords);
+
+    // header
+    mgard_header h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, MGARD_MAGIC, 8);
+    h.version = MGARD_FORMAT_VERSION;
+    h.dtype = (uint32_t)dtype;
+    h.ndim = (uint32_t)ndim;
+    h.nlevels = (uint32_t)L;
+    for (int i = 0; i < 4; ++i) h.shape[i] = i < ndim ? shape[i] : 1;
+    h.s = s;
+    h.tol = tol;
+    h.tol_abs = tol_abs;
+    h.mode = (uint32_t)mode;
+    h.dict = DICT;
+    h.chunk = CHUNK;
+    h.nsymbols = (uint64_t)N;
+    h.nchunks = nchunks;
+    h.nwords = nwords;
+    h.noutliers = nout;
+    h.off_widths = sec.widths;
+    h.off_lengths = sec.lengths;
+    h.off_word_off = sec.word_off;
+    h.off_esc_off = sec.esc_off;
+    h.off_outliers = sec.outliers;
+    h.off_words = sec.words;
+    h.total_bytes = sec.total;
+
+    bool out_dev;
+    char* dst;
+    if (prealloc) {
+        if (!out || !*out || !out_bytes) {
+            set_error("preallocated output missing");
+            return MGARD_EINVAL;
+        }
+        if (*out_bytes < sec.total) {
+            *out_bytes = sec.total;
+            set_error("preallocated output too small");
+            return MGARD_ECAPACITY;
+        }
+        dst = (char*)*out;
+        out_dev = is_device_ptr(dst);
+    } else {
+        out_dev = field_dev;
+        if (out_dev) {
+            void* q = nullptr;
+            cudaError_t e = cudaMalloc(&q, sec.total);
+            if (e != cudaSuccess) {
+                set_error(std::string("output allocation: ") + cudaGetErrorString(e));
+                return MGARD_ENOMEM;
+            }
+            dst = (char*)q;
+        } else {
+            dst = (char*)std::malloc(sec.total);
+            if (!dst) {
+                set_error("host output allocation failed");
+                return MGARD_ENOMEM;
+            }
+        }
+    }
+    DevBuf stage;
+    char* dd = dst;   // device image of the output
+    if (!out_dev) {
+        MGB_TRY(stage.alloc(sec.total, st));
+        dd = stage.as<char>();
+    }
+    std::vector<char> head(sec.lengths, 0);
+    std::memcpy(head.data(), &h, sizeof(h));
+    std::memcpy(head.data() + sec.widths, w.data(), 8 * (L + 1));
+    MGB_CUDA(cudaMemcpyAsync(dd, head.data(), head.size(), cudaMemcpyHostToDevice, st));
+    MGB_CUDA(cudaMemcpyAsync(dd + sec.lengths, lengths.p, DICT, cudaMemcpyDeviceToDevice, st));
+    if (nchunks) {
+        MGB_CUDA(cudaMemcpyAsync(dd + sec.word_off, word_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
+        MGB_CUDA(cudaMemcpyAsync(dd + sec.esc_off, esc_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
+    }
+    MGB_TRY(huffman_pack(sym.as<uint16_t>(), N, lengths.as<uint8_t>(), codes.as<uint32_t>(),
+                         word_off, esc_off, esc.as<int32_t>(), (uint32_t*)(dd + sec.words),
+                         (int32_t*)(dd + sec.outliers), st));
+    if (!out_dev) MGB_CUDA(cudaMemcpyAsync(dst, dd, sec.total, cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    *out = dst;
+    *out_bytes = sec.total;
+    return MGARD_OK;
+}
+
+mgard_status read_header(const void* in, size_t in_bytes, bool in_dev, mgard_header* h,
+                         std::vector<double>* widths, cudaStream_t st) {
+    if (!in || in_bytes < sizeof(mgard_header)) {
+        set_error("compressed buffer too small");
+        return MGARD_ECORRUPT;
+    }
+    if (in_dev) {
+        MGB_CUDA(cudaMemcpyAsync(h, in, sizeof(*h), cudaMemcpyDeviceToHost, st));
+        MGB_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(h, in, sizeof(*h));
+    }
+    auto bad = [](const char* why) {
+        set_error(std::string("corrupt header: ") + why);
+        return MGARD_ECORRUPT;
+    };
+    if (std::memcmp(h->magic, MGARD_MAGIC, 8) != 0) return bad("magic");
+    if (h->version != MGARD_FORMAT_VERSION) return bad("version");
+    if (h->dtype > 1) return bad("dtype");
+    if (h->ndim < 1 || h->ndim > 4) return bad("ndim");
+    if (h->dict != DICT || h->chunk != CHUNK) return bad("dictionary or chunk size");
+    uint64_t n = 1;
+    for (uint32_t i = 0; i < h->ndim; ++i) {
+        if (h->shape[i] < 1 || h->shape[i] > (int64_t(1) << 40)) return bad("shape");
+        n *= (uint64_t)h->shape[i];
+        if (n > (uint64_t(1) << 40)) return bad("shape");
+    }
+    if (n != h->nsymbols) return bad("symbol count");
+    if (h->nchunks != (n + CHUNK - 1) / CHUNK) return bad("chunk count");
+    if (h->nlevels > 64) return bad("levels");
+    if (h->noutliers > n || h->nwords > n + h->nchunks) return bad("section sizes");
+    Sections s = layout((int)h->nlevels, h->nchunks, h->noutliers, h->nwords);
+    if (h->off_widths != s.widths || h->off_lengths != s.lengths || h->off_word_off != s.word_off ||
+        h->off_esc_off != s.esc_off || h->off_outliers != s.outliers || h->off_words != s.words ||
+        h->total_bytes != s.total)
+        return bad("section offsets");
+    if (s.total > in_bytes) return bad("truncated buffer");
+    if (!(h->tol_abs > 0.0) || !std::isfinite(h->tol_abs)) return bad("tolerance");
+    widths->resize(h->nlevels + 1);
+    if (in_dev)
+        MGB_CUDA(cudaMemcpy(widths->data(), (const char*)in + s.widths, 8 * (h->nlevels + 1),
+                            cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(widths->data(), (const char*)in + s.widths, 8 * (h->nlevels + 1));
+    for (double v : *widths)
+        if (!(v > 0.0) || !std::isfinite(v)) return bad("bin width");
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::vector<double>& w,
+                             const char* din, void** field, bool out_dev, void* dst,
+                             cudaStream_t st) {
+    const int64_t N = p.total();
+    const int L = p.L;
+    DevBuf stage;
+    T* dout = (T*)dst;
+    if (!out_dev) {
+        MGB_TRY(stage.alloc(N * sizeof(T), st));
+        dout = stage.as<T>();
+    }
+    DevBuf codes, dt, sym, esc, stat;
+    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
+    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    MGB_TRY(stat.alloc(sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
+    const uint8_t* lengths = (const uint8_t*)(din + h.off_lengths);
+    MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
+    MGB_TRY(huffman_decode((const uint32_t*)(din + h.off_words), h.nwords,
+                           (const uint64_t*)(din + h.off_word_off), dt.as<DecodeTables>(), N,
+                           (const int32_t*)(din + h.off_outliers), h.noutliers,
+                           (const uint64_t*)(din + h.off_esc_off), sym.as<uint16_t>(),
+                           esc.as<int32_t>(), stat.as<unsigned>(), st));
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    MGB_TRY(status_to_error(status));
+    Pyramid<T> py;
+    MGB_TRY(py.alloc(p, st));
+    for (int l = 0; l <= L; ++l) {
+        T* lvl = l == L ? dout : py.lv[l];
+        MGB_TRY(dequantize_level<T>(p, l, sym.as<uint16_t>(), esc.as<int32_t>(), false, w[l], lvl, st));
+    }
+    MGB_TRY(recompose_pyramid<T>(p, dout, dout, py, st));
+    if (!out_dev) MGB_CUDA(cudaMemcpyAsync(dst, dout, N * sizeof(T), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    *field = dst;
+    return MGARD_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace mgb
+
+using namespace mgb;
+
+extern "C" {
+
+const char* mgard_strerror(mgard_status s) {
+    switch (s) {
+        case MGARD_OK: return "ok";
+        case MGARD_EINVAL: return "invalid argument";
+        case MGARD_ESHAPE: return "invalid shape";
+        case MGARD_EDTYPE: return "invalid dtype";
+        case MGARD_ENONFINITE: return "non-finite input";
+        case MGARD_ENOMEM: return "out of memory";
+        case MGARD_ECUDA: return "CUDA error";
+        case MGARD_ECORRUPT: return "corrupt compressed buffer";
+        case MGARD_EBOUND: return "error bound violated";
+        case MGARD_ETIMEOUT: return "device wait timed out";
+        case MGARD_ECAPACITY: return "output capacity too small";
+        case MGARD_ERANGE: return "tolerance too small for 32-bit quantization";
+    }
+    return "unknown status";
+}
+
+const char* mgard_last_error(void) { return g_last_error.c_str(); }
+
+uint32_t mgard_version(void) { return 0x010000u; }
+
+mgard_status mgard_levels(int ndim, const int64_t* shape, int max_levels, int* nlevels) {
+    int64_t n4[4];
+    int D;
+    MGB_TRY(squeeze_shape(ndim, shape, n4, &D));
+    if (!nlevels) return MGARD_EINVAL;
+    *nlevels = level_count(n4, D, max_levels);
+    return MGARD_OK;
+}
+
+mgard_status mgard_decompose(void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                             int max_levels, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!data) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == MGARD_F32) {
+        Pyramid<float> py;
+        MGB_TRY(py.alloc(*p, st));
+        MGB_TRY(decompose_pyramid<float>(*p, (float*)data, (float*)data, py, st, nullptr));
+        MGB_TRY(scatter_levels<float>(*p, py, (float*)data, st));
+    } else {
+        Pyramid<double> py;
+        MGB_TRY(py.alloc(*p, st));
+        MGB_TRY(decompose_pyramid<double>(*p, (double*)data, (double*)data, py, st, nullptr));
+        MGB_TRY(scatter_levels<double>(*p, py, (double*)data, st));
+    }
+    return MGARD_OK;
+}
+
+mgard_status mgard_recompose(void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                             int max_levels, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!data) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == MGARD_F32) {
+        Pyramid<float> py;
+        MGB_TRY(py.alloc(*p, st));
+        MGB_TRY(gather_levels<float>(*p, (float*)data, py, st));
+        MGB_TRY(recompose_pyramid<float>(*p, (float*)data, (float*)data, py, st));
+    } else {
+        Pyramid<double> py;
+        MGB_TRY(py.alloc(*p, st));
+        MGB_TRY(gather_levels<double>(*p, (double*)data, py, st));
+        MGB_TRY(recompose_pyramid<double>(*p, (double*)data, (double*)data, py, st));
+    }
+    return MGARD_OK;
+}
+
+mgard_status mgard_bin_widths(int ndim, const int64_t* shape, int max_levels, double tol_abs,
+                              double s, double* widths, int* nlevels) {
+    if (!widths || !(tol_abs > 0.0) || !std::isfinite(tol_abs) || std::isnan(s) || s < 0.0) {
+        set_error("tol_abs must be positive and finite, s >= 0 or INFINITY");
+        return MGARD_EINVAL;
+    }
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    bin_widths(*p, tol_abs, s, widths);
+    if (nlevels) *nlevels = p->L;
+    return MGARD_OK;
+}
+
+mgard_status mgard_norm(const void* data, int ndim, const int64_t* shape, mgard_dtype dtype,
+                        int max_levels, double s, double* out, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!data || !out || std::isnan(s) || s < 0.0) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == MGARD_F32) return norm_impl<float>(*p, (const float*)data, s, out, st);
+    return norm_impl<double>(*p, (const double*)data, s, out, st);
+}
+
+mgard_status mgard_error_norm(const void* a, const void* b, int ndim, const int64_t* shape,
+                              mgard_dtype dtype, int max_levels, double s, double* out,
+                              void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!a || !b || !out || std::isnan(s) || s < 0.0) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = p->total();
+    unsigned status = 0;
+    if (std::isinf(s)) {
+        if (dtype == MGARD_F32) MGB_TRY(max_abs<float>((const float*)a, (const float*)b, N, out, &status, st));
+        else MGB_TRY(max_abs<double>((const double*)a, (const double*)b, N, out, &status, st));
+        return status_to_error(status);
+    }
+    DevBuf y;
+    MGB_TRY(y.alloc(N * sizeof(double), st));
+    if (dtype == MGARD_F32) MGB_TRY(difference<float>((const float*)a, (const float*)b, y.as<double>(), N, st));
+    else MGB_TRY(difference<double>((const double*)a, (const double*)b, y.as<double>(), N, st));
+    return norm_impl<double>(*p, y.as<double>(), s, out, st);
+}
+
+mgard_status mgard_quantize(const void* coeffs, int ndim, const int64_t* shape, mgard_dtype dtype,
+                            int max_levels, const double* widths, uint16_t* symbols,
+                            int32_t* escapes, uint64_t* hist, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!coeffs || !widths || !symbols || !escapes || !hist) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    for (int l = 0; l <= p->L; ++l)
+        if (!(widths[l] > 0.0) || !std::isfinite(widths[l])) {
+            set_error("bin widths must be positive and finite");
+            return MGARD_EINVAL;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf stat;
+    MGB_TRY(stat.alloc(sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(hist, 0, DICT * sizeof(uint64_t), st));
+    for (int l = 0; l <= p->L; ++l) {
+        if (dtype == MGARD_F32)
+            MGB_TRY(quantize_level<float>(*p, l, (const float*)coeffs, true, widths[l], symbols,
+                                          escapes, (unsigned long long*)hist, stat.as<unsigned>(), st));
+        else
+            MGB_TRY(quantize_level<double>(*p, l, (const double*)coeffs, true, widths[l], symbols,
+                                           escapes, (unsigned long long*)hist, stat.as<unsigned>(), st));
+    }
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    return status_to_error(status);
+}
+
+mgard_status mgard_dequantize(const uint16_t* symbols, const int32_t* escapes, int ndim,
+                              const int64_t* shape, mgard_dtype dtype, int max_levels,
+                              const double* widths, void* coeffs, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!coeffs || !widths || !symbols || !escapes) return MGARD_EINVAL;
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int l = 0; l <= p->L; ++l) {
+        if (dtype == MGARD_F32)
+            MGB_TRY(dequantize_level<float>(*p, l, symbols, escapes, true, widths[l], (float*)coeffs, st));
+        else
+            MGB_TRY(dequantize_level<double>(*p, l, symbols, escapes, true, widths[l], (double*)coeffs, st));
+    }
+    return MGARD_OK;
+}
+
+mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint32_t* codes,
+                                    void* stream) {
+    if (!hist || !lengths || !codes) return MGARD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    MGB_TRY(huffman_codebook((const unsigned long long*)hist, lengths, codes, st));
+    DevBuf dt;
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(huffman_tables(lengths, codes, dt.as<DecodeTables>(), st));
+    return MGARD_OK;
+}
+
+mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uint8_t* lengths,
+                                  const int32_t* escapes, uint32_t* words, uint64_t words_cap,
+                                  uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
+                                  uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers,
+                                  void* stream) {
+    if ((!symbols && n) || !lengths || !nwords || !noutliers || (n && (!word_off || !esc_off)))
+        return MGARD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf totals, stat, codes, dt;
+    MGB_TRY(totals.alloc(16, st));
+    MGB_TRY(stat.alloc(4, st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, 4, st));
+    MGB_TRY(huffman_count(symbols, n, lengths, word_off, esc_off, totals.as<unsigned long long>(),
+                          stat.as<unsigned>(), st));
+    unsigned long long tot[2];
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(tot, totals.p, 16, cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, 4, cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    *nwords = tot[0];
+    *noutliers = tot[1];
+    MGB_TRY(status_to_error(status));
+    if (tot[0] > words_cap || tot[1] > outliers_cap) {
+        set_error("encode capacity too small");
+        return MGARD_ECAPACITY;
+    }
+    MGB_TRY(codes.alloc(DICT * 4, st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
+    MGB_TRY(huffman_pack(symbols, n, lengths, codes.as<uint32_t>(), word_off, esc_off, escapes,
+                         words, outliers, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    return MGARD_OK;
+}
+
+mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                  const uint8_t* lengths, uint64_t n, const int32_t* outliers,
+                                  uint64_t noutliers, const uint64_t* esc_off, uint16_t* symbols,
+                                  int32_t* escapes, void* stream) {
+    if (!lengths || (n && (!words || !word_off || !esc_off || !symbols || !escapes)))
+        return MGARD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf codes, dt, stat;
+    MGB_TRY(codes.alloc(DICT * 4, st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(stat.alloc(4, st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, 4, st));
+    MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
+    MGB_TRY(huffman_decode(words, nwords, word_off, dt.as<DecodeTables>(), n, outliers, noutliers,
+                           esc_off, symbols, escapes, stat.as<unsigned>(), st));
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, 4, cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    return status_to_error(status);
+}
+
+size_t mgard_compress_bound(int ndim, const int64_t* shape, mgard_dtype dtype) {
+    int64_t n4[4];
+    int D;
+    if (squeeze_shape(ndim, shape, n4, &D) != MGARD_OK) return 0;
+    (void)dtype;
+    const uint64_t n = (uint64_t)(n4[0] * n4[1] * n4[2] * n4[3]);
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    return layout(64, nchunks, n, n + nchunks).total;
+}
+
+mgard_status mgard_compress(const void* field, int ndim, const int64_t* shape, mgard_dtype dtype,
+                            double tol, double s, mgard_tolmode mode, void** out,
+                            size_t* out_bytes, int out_preallocated, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!field || !out || !out_bytes) {
+        set_error("null argument");
+        return MGARD_EINVAL;
+    }
+    if (!(tol > 0.0) || !std::isfinite(tol) || std::isnan(s) || s < 0.0 ||
+        (mode != MGARD_ABS && mode != MGARD_REL)) {
+        set_error("tol must be positive and finite, s >= 0 or INFINITY, mode ABS or REL");
+        return MGARD_EINVAL;
+    }
+    const Plan* p;
+    MGB_TRY(get_plan(ndim, shape, -1, &p));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(field);
+    if (dtype == MGARD_F32)
+        return compress_impl<float>(*p, field, dev, dtype, ndim, shape, tol, s, mode, out, out_bytes,
+                                    out_preallocated, st);
+    return compress_impl<double>(*p, field, dev, dtype, ndim, shape, tol, s, mode, out, out_bytes,
+                                 out_preallocated, st);
+}
+
+mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field, int out_preallocated,
+                              void* stream) {
+    if (!in || !field) {
+        set_error("null argument");
+        return MGARD_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool in_dev = is_device_ptr(in);
+    mgard_header h;
+    std::vector<double> w;
+    MGB_TRY(read_header(in, in_bytes, in_dev, &h, &w, st));
+    const Plan* p;
+    MGB_TRY(get_plan((int)h.ndim, h.shape, -1, &p));
+    if (p->L != (int)h.nlevels) {
+        set_error("corrupt header: level count");
+        return MGARD_ECORRUPT;
+    }
+    const size_t nbytes = (size_t)p->total() * ((h.dtype == MGARD_F64) ? 8 : 4);
+    // device image of the compressed buffer
+    DevBuf inbuf;
+    const char* din = (const char*)in;
+    if (!in_dev) {
+        MGB_TRY(inbuf.alloc(h.total_bytes, st));
+        MGB_CUDA(cudaMemcpyAsync(inbuf.p, in, h.total_bytes, cudaMemcpyHostToDevice, st));
+        din = inbuf.as<char>();
+    }
+    void* dst;
+    bool out_dev;
+    if (out_preallocated) {
+        if (!*field) {
+            set_error("preallocated output missing");
+            return MGARD_EINVAL;
+        }
+        dst = *field;
+        out_dev = is_device_ptr(dst);
+    } else {
+        out_dev = in_dev;
+        if (out_dev) {
+            cudaError_t e = cudaMalloc(&dst, nbytes);
+            if (e != cudaSuccess) {
+                set_error(std::string("output allocation: ") + cudaGetErrorString(e));
+                return MGARD_ENOMEM;
+            }
+        } else {
+            dst = std::malloc(nbytes);
+            if (!dst) return MGARD_ENOMEM;
+        }
+    }
+    mgard_status r;
+    if (h.dtype == MGARD_F32) r = decompress_impl<float>(*p, h, w, din, field, out_dev, dst, st);
+    else r = decompress_impl<double>(*p, h, w, din, field, out_dev, dst, st);
+    if (r != MGARD_OK && !out_preallocated) mgard_free(dst);
+    return r;
+}
+
+mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
+                        mgard_dtype* dtype, double* tol_abs, int* nlevels) {
+    mgard_header h;
+    std::vector<double> w;
+    MGB_TRY(read_header(in, in_bytes, is_device_ptr(in), &h, &w, nullptr));
+    if (ndim) *ndim = (int)h.ndim;
+    if (shape)
+        for (int i = 0; i < 4; ++i) shape[i] = h.shape[i];
+    if (dtype) *dtype = (mgard_dtype)h.dtype;
+    if (tol_abs) *tol_abs = h.tol_abs;
+    if (nlevels) *nlevels = (int)h.nlevels;
+    return MGARD_OK;
+}
+
+void mgard_free(void* p) {
+    if (!p) return;
+    if (is_device_ptr(p)) cudaFree(p);
+    else std::free(p);
+}
+
+void mgard_release_plans(void) { release_plans(); }
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Shared definitions of the CUDA library (host and device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mgard_b300.h"
+
+namespace mgb {
+
+// Last-error text, per host thread.
+void set_error(const std::string& msg);
+
+#define MGB_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::mgb::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+            return e_ == cudaErrorMemoryAllocation ? MGARD_ENOMEM : MGARD_ECUDA;    \
+        }                                                                           \
+    } while (0)
+
+#define MGB_TRY(expr)                      \
+    do {                                   \
+        mgard_status s_ = (expr);          \
+        if (s_ != MGARD_OK) return s_;     \
+    } while (0)
+
+constexpr int DICT = MGARD_DICT;
+constexpr int RADIUS = MGARD_DICT / 2;
+constexpr int CHUNK = MGARD_CHUNK;
+constexpr int LMAX = MGARD_LMAX;
+
+// Device status bits set by kernels and read back by the host.
+enum : unsigned {
+    ST_NONFINITE = 1u,
+    ST_RANGE = 2u,
+    ST_NOCODE = 4u,
+    ST_CORRUPT = 8u,
+};
+
+// Per-axis tables of one level transition (fine grid of level l, coarse
+// grid of level l-1).  Pointers are device addresses; for an inactive axis
+// (extent 1) they are null and the axis is treated as "always coarse".
+template <typename T>
+struct AxisT {
+    const int* fcls;     // [m]  coarse index J >= 0, or -(J+1) for a new node between J and J+1
+    const T* wl;         // [m]  interpolation weight of coarse J (new nodes)
+    const T* wr;         // [m]  interpolation weight of coarse J+1 (new nodes)
+    const int* cbefore;  // [m]  number of coarse positions < i
+    const int* rf;       // [mc] fine position of coarse node J
+    const T* rw;         // [mc*5] restriction weights on fine positions rf[J]-2 .. rf[J]+2
+    const T* tsub;       // [mc] Thomas: sub-diagonal a_J
+    const T* tinv;       // [mc] Thomas: 1 / (b_J - a_J c'_{J-1})
+    const T* tcp;        // [mc] Thomas: c'_J
+    const double* mdiag; // [m]  mass matrix of the level-l grid: diagonal
+    const double* moff;  // [m]  mass matrix: M[i][i+1] (last entry 0)
+};
+
+template <typename T>
+struct Level {
+    int64_t n[4];    // fine shape (4D view, leading 1s)
+    int64_t nc[4];   // coarse shape
+    AxisT<T> ax[4];
+};
+
+// Finest-grid position of every level-l node, per axis (in-place layout).
+struct LevelIndex {
+    int64_t n[4];
+    const int64_t* pos[4];
+};
+
+__host__ __device__ inline int64_t prod4(const int64_t* n) { return n[0] * n[1] * n[2] * n[3]; }
+
+__device__ inline void unravel4(int64_t lin, const int64_t* n, int64_t* i) {
+    i[3] = lin % n[3]; lin /= n[3];
+    i[2] = lin % n[2]; lin /= n[2];
+    i[1] = lin % n[1]; lin /= n[1];
+    i[0] = lin;
+}
+
+__host__ __device__ inline int64_t ravel4(const int64_t* i, const int64_t* n) {
+    return ((i[0] * n[1] + i[1]) * n[2] + i[2]) * n[3] + i[3];
+}
+
+inline int grid_for(int64_t work, int block, int64_t cap = 148LL * 64) {
+    int64_t g = (work + block - 1) / block;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace mgb

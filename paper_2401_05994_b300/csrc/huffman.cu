@@ -1,0 +1,540 @@
+// Huffman coding of quantization symbols.
+//
+// Paper, "Software design": the quantized coefficients are losslessly
+// encoded into the self-describing buffer.  This build's coder:
+//  * code lengths: leaves (used symbols) sorted by (count, symbol), merged
+//    with two FIFO queues (leaf queue first on equal weight); depth = length;
+//    lengths over LMAX repeat on max(1, count >> k); one used symbol -> 1 bit;
+//  * canonical codes, consecutive in (length, symbol) order;
+//  * chunks of CHUNK symbols, each starting on a 32-bit word, MSB-first.
+// The codebook is built by one CTA (bitonic sorts and pointer jumping are
+// parallel, the queue merge itself is a short serial loop).  Encoding is a
+// count pass, an exclusive scan over chunks and a pack pass with one warp
+// per chunk.  Decoding runs one thread per chunk with a 12-bit prefix table
+// in shared memory and canonical first-code search for longer codes.
+#include "huffman.cuh"
+
+namespace mgb {
+
+namespace {
+
+constexpr int CB_THREADS = 1024;
+constexpr unsigned long long KEY_NONE = ~0ull;
+
+__device__ void bitonic_sort(unsigned long long* keys, int n) {
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+struct CodebookSmem {
+    unsigned long long keys[DICT];    // sorted leaves: (weight << 12) | symbol
+    unsigned long long iw[DICT];      // internal node weights
+    short parent[2 * DICT];
+    short anc[2 * DICT];
+    unsigned short dep[2 * DICT];
+    int n;
+    int maxlen;
+};
+
+__global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long long* __restrict__ hist,
+                                                         uint8_t* __restrict__ lengths) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CodebookSmem& S = *reinterpret_cast<CodebookSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int s = tid; s < DICT; s += blockDim.x) lengths[s] = 0;
+    for (int shift = 0; shift < 64; ++shift) {
+        for (int s = tid; s < DICT; s += blockDim.x) {
+            unsigned long long f = hist[s];
+            if (f) {
+                f >>= shift;
+                if (f == 0) f = 1;
+                S.keys[s] = (f << 12) | (unsigned long long)s;
+            } else {
+                S.keys[s] = KEY_NONE;
+            }
+        }
+        if (tid == 0) S.maxlen = 0;
+        __syncthreads();
+        bitonic_sort(S.keys, DICT);   // ends with a barrier
+        if (tid == 0) {
+            int n = 0;
+            while (n < DICT && S.keys[n] != KEY_NONE) ++n;
+            S.n = n;
+        }
+        __syncthreads();
+        const int n = S.n;
+        if (n == 0) return;
+        if (n == 1) {
+            if (tid == 0) lengths[S.keys[0] & 0xFFF] = 1;
+            return;
+        }
+        // two-queue merge (serial): leaves 0..n-1, internal nodes n..2n-2
+        if (tid == 0) {
+            int li = 0, ii = 0, nint = 0;
+            const unsigned long long INF = ~0ull;
+            for (int k = 0; k < n - 1; ++k) {
+                int ids[2];
+                unsigned long long ws[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const unsigned long long wl = li < n ? (S.keys[li] >> 12) : INF;
+                    const unsigned long long wi = ii < nint ? S.iw[ii] : INF;
+                    if (wl <= wi) {
+                        ids[t] = li++;
+                        ws[t] = wl;
+                    } else {
+                        ids[t] = n + ii++;
+                        ws[t] = wi;
+                    }
+                }
+                S.iw[nint] = ws[0] + ws[1];
+                S.parent[ids[0]] = (short)(n + nint);
+                S.parent[ids[1]] = (short)(n + nint);
+                ++nint;
+            }
+        }
+        __syncthreads();
+        // depths by pointer jumping: dep[i] = distance to anc[i]
+        const int root = 2 * n - 2;
+        for (int i = tid; i <= root; i += blockDim.x) {
+            S.anc[i] = i == root ? (short)root : S.parent[i];
+            S.dep[i] = i == root ? 0 : 1;
+        }
+        __syncthreads();
+        for (int round = 0; round < 13; ++round) {
+            short na[8];
+            unsigned short nd[8];
+            int c = 0;
+            for (int i = tid; i <= root; i += blockDim.x, ++c) {
+                const int a = S.anc[i];
+                nd[c] = S.dep[i] + S.dep[a];
+                na[c] = S.anc[a];
+            }
+            __syncthreads();
+            c = 0;
+            for (int i = tid; i <= root; i += blockDim.x, ++c) {
+                S.dep[i] = nd[c];
+                S.anc[i] = na[c];
+            }
+            __syncthreads();
+        }
+        int mx = 0;
+        for (int i = tid; i < n; i += blockDim.x) mx = max(mx, (int)S.dep[i]);
+        atomicMax(&S.maxlen, mx);
+        __syncthreads();
+        if (S.maxlen <= LMAX) {
+            for (int i = tid; i < n; i += blockDim.x) lengths[S.keys[i] & 0xFFF] = (uint8_t)S.dep[i];
+            return;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict__ lengths,
+                                                       uint32_t* __restrict__ codes,
+                                                       DecodeTables* __restrict__ dt) {
+    __shared__ unsigned long long keys[DICT];
+    __shared__ unsigned cnt[LMAX + 2];
+    __shared__ unsigned long long fc[LMAX + 2];
+    __shared__ unsigned fi[LMAX + 2];
+    __shared__ unsigned long long kraft;
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid < LMAX + 2) cnt[tid] = 0;
+    if (tid == 0) {
+        kraft = 0;
+        bad = 0;
+    }
+    __syncthreads();
+    for (int s = tid; s < DICT; s += blockDim.x) {
+        const unsigned len = lengths[s];
+        if (len > LMAX) bad = 1;
+        if (len && len <= LMAX) {
+            atomicAdd(&cnt[len], 1u);
+            atomicAdd(&kraft, 1ull << (LMAX - len));
+            keys[s] = ((unsigned long long)len << 12) | (unsigned)s;
+        } else {
+            keys[s] = KEY_NONE;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long code = 0;
+        unsigned idx = 0, maxlen = 0;
+        for (int l = 1; l <= LMAX; ++l) {
+            fc[l] = code;
+            fi[l] = idx;
+            code = (code + cnt[l]) << 1;
+            idx += cnt[l];
+            if (cnt[l]) maxlen = l;
+        }
+        const bool valid = !bad && kraft <= (1ull << LMAX);
+        for (int l = 0; l < LMAX + 2; ++l) {
+            dt->first_code[l] = (l >= 1 && l <= LMAX) ? (uint32_t)fc[l] : 0;
+            dt->count[l] = (l >= 1 && l <= LMAX) ? cnt[l] : 0;
+            dt->first_index[l] = (l >= 1 && l <= LMAX) ? fi[l] : 0;
+        }
+        dt->maxlen = maxlen;
+        dt->valid = valid ? 1 : 0;
+    }
+    for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) dt->lut[k] = 0;
+    bitonic_sort(keys, DICT);   // ends with a barrier
+    for (int p = tid; p < DICT; p += blockDim.x) {
+        const unsigned long long key = keys[p];
+        if (key == KEY_NONE) continue;
+        const unsigned s = key & 0xFFF, len = (unsigned)(key >> 12);
+        const uint32_t c = (uint32_t)(fc[len] + (p - fi[len]));
+        dt->sorted[p] = (uint16_t)s;
+        codes[s] = c;
+        if (len <= LUT_BITS) {
+            const unsigned lo = c << (LUT_BITS - len), hi = (c + 1) << (LUT_BITS - len);
+            for (unsigned e = lo; e < hi && e < (1u << LUT_BITS); ++e) dt->lut[e] = (len << 16) | s;
+        }
+    }
+    for (int s = tid; s < DICT; s += blockDim.x)
+        if (!lengths[s]) codes[s] = 0;
+}
+
+// -- encoding ------------------------------------------------------------------
+constexpr int ENC_WARPS = 8;
+
+__global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
+    const uint16_t* __restrict__ sym, uint64_t n, const uint8_t* __restrict__ lengths,
+    uint64_t* __restrict__ wcnt, uint64_t* __restrict__ ecnt, uint64_t nchunks, unsigned* status) {
+    __shared__ uint8_t len_s[DICT];
+    for (int s = threadIdx.x; s < DICT; s += blockDim.x) len_s[s] = lengths[s];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool nocode = false;
+    for (uint64_t c = blockIdx.x * (uint64_t)ENC_WARPS + warp; c < nchunks;
+         c += (uint64_t)gridDim.x * ENC_WARPS) {
+        const uint64_t base = c * CHUNK + lane * 32;
+        unsigned bits = 0, esc = 0;
+        if (base + 32 <= n) {
+            const uint4* v = reinterpret_cast<const uint4*>(sym + base);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 w = v[q];
+                const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const unsigned s0 = ww[h] & 0xFFFF, s1 = ww[h] >> 16;
+                    const unsigned l0 = len_s[s0], l1 = len_s[s1];
+                    nocode |= (l0 == 0) | (l1 == 0);
+                    bits += l0 + l1;
+                    esc += (s0 == MGARD_ESC) + (s1 == MGARD_ESC);
+                }
+            }
+        } else {
+            for (uint64_t k = base; k < n && k < base + 32; ++k) {
+                const unsigned s = sym[k], l = len_s[s];
+                nocode |= l == 0;
+                bits += l;
+                esc += s == MGARD_ESC;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bits += __shfl_xor_sync(0xffffffffu, bits, o);
+            esc += __shfl_xor_sync(0xffffffffu, esc, o);
+        }
+        if (lane == 0) {
+            wcnt[c] = (bits + 31) / 32;
+            ecnt[c] = esc;
+        }
+    }
+    if (nocode) atomicOr(status, ST_NOCODE);
+}
+
+// Exclusive scan of two arrays in place (one CTA); totals[0..1] = sums.
+__global__ void __launch_bounds__(1024) k_scan2(uint64_t* a, uint64_t* b, uint64_t n,
+                                                unsigned long long* totals) {
+    __shared__ unsigned long long sa[1024], sb[1024];
+    const int t = threadIdx.x;
+    const uint64_t seg = (n + 1023) / 1024;
+    const uint64_t lo = min(n, (uint64_t)t * seg), hi = min(n, lo + seg);
+    unsigned long long xa = 0, xb = 0;
+    for (uint64_t i = lo; i < hi; ++i) {
+        xa += a[i];
+        xb += b[i];
+    }
+    sa[t] = xa;
+    sb[t] = xb;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned long long va = t >= o ? sa[t - o] : 0, vb = t >= o ? sb[t - o] : 0;
+        __syncthreads();
+        sa[t] += va;
+        sb[t] += vb;
+        __syncthreads();
+    }
+    unsigned long long ra = sa[t] - xa, rb = sb[t] - xb;   // exclusive prefix of segment
+    for (uint64_t i = lo; i < hi; ++i) {
+        const unsigned long long va = a[i], vb = b[i];
+        a[i] = ra;
+        b[i] = rb;
+        ra += va;
+        rb += vb;
+    }
+    if (t == 1023) {
+        totals[0] = sa[1023];
+        totals[1] = sb[1023];
+    }
+}
+
+constexpr int PACK_WARPS = 4;
+
+__global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
+    const uint16_t* __restrict__ sym, uint64_t n, const uint8_t* __restrict__ lengths,
+    const uint32_t* __restrict__ codes, const uint64_t* __restrict__ word_off,
+    const uint64_t* __restrict__ esc_off, const int32_t* __restrict__ escapes,
+    uint32_t* __restrict__ words, int32_t* __restrict__ outliers, uint64_t nchunks) {
+    __shared__ uint8_t len_s[DICT];
+    __shared__ uint32_t code_s[DICT];
+    __shared__ uint32_t buf[PACK_WARPS][CHUNK + 1];
+    for (int s = threadIdx.x; s < DICT; s += blockDim.x) {
+        len_s[s] = lengths[s];
+        code_s[s] = codes[s];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* wb = buf[warp];
+    for (uint64_t c = blockIdx.x * (uint64_t)PACK_WARPS + warp; c < nchunks;
+         c += (uint64_t)gridDim.x * PACK_WARPS) {
+        const uint64_t base = c * CHUNK + lane * 32;
+        const int cnt = base >= n ? 0 : (int)min((uint64_t)32, n - base);
+        unsigned s_loc[32];
+        unsigned bits = 0, esc = 0;
+        if (cnt == 32) {
+            const uint4* v = reinterpret_cast<const uint4*>(sym + base);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 w = v[q];
+                s_loc[8 * q + 0] = w.x & 0xFFFF; s_loc[8 * q + 1] = w.x >> 16;
+                s_loc[8 * q + 2] = w.y & 0xFFFF; s_loc[8 * q + 3] = w.y >> 16;
+                s_loc[8 * q + 4] = w.z & 0xFFFF; s_loc[8 * q + 5] = w.z >> 16;
+                s_loc[8 * q + 6] = w.w & 0xFFFF; s_loc[8 * q + 7] = w.w >> 16;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) s_loc[k] = k < cnt ? sym[base + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < cnt) {
+                bits += len_s[s_loc[k]];
+                esc += s_loc[k] == MGARD_ESC;
+            }
+        // warp exclusive scans of bits and escapes
+        unsigned ib = bits, ie = esc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned vb = __shfl_up_sync(0xffffffffu, ib, o);
+            const unsigned ve = __shfl_up_sync(0xffffffffu, ie, o);
+            if (lane >= o) {
+                ib += vb;
+                ie += ve;
+            }
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, ib, 31);
+        unsigned bpos = ib - bits, epos = ie - esc;
+        const unsigned nw = (total + 31) / 32;
+        for (unsigned k = lane; k <= nw && k <= CHUNK; k += 32) wb[k] = 0;
+        __syncwarp();
+        const uint64_t eo = esc_off[c];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < cnt) {
+                const unsigned s = s_loc[k], len = len_s[s];
+                const unsigned w = bpos >> 5, b = bpos & 31;
+                const unsigned long long v = (unsigned long long)code_s[s] << (64 - len - b);
+                atomicOr(&wb[w], (uint32_t)(v >> 32));
+                const uint32_t lo = (uint32_t)v;
+                if (lo) atomicOr(&wb[w + 1], lo);
+                bpos += len;
+                if (s == MGARD_ESC) outliers[eo + epos++] = escapes[base + k];
+            }
+        __syncwarp();
+        const uint64_t wo = word_off[c];
+        for (unsigned k = lane; k < nw; k += 32) words[wo + k] = wb[k];
+        __syncwarp();
+    }
+}
+
+// -- decoding ------------------------------------------------------------------
+constexpr int DEC_THREADS = 128;
+
+__global__ void __launch_bounds__(DEC_THREADS) k_decode(
+    const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
+    const DecodeTables* __restrict__ gdt, uint64_t n, const int32_t* __restrict__ outliers,
+    uint64_t noutliers, const uint64_t* __restrict__ esc_off, uint16_t* __restrict__ sym,
+    int32_t* __restrict__ escapes, unsigned* status, uint64_t nchunks) {
+    __shared__ DecodeTables T;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(gdt);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
+        for (int k = threadIdx.x; k < (int)(sizeof(DecodeTables) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    if (!T.valid) {
+        atomicOr(status, ST_CORRUPT);
+        return;
+    }
+    const uint64_t start = word_off[c];
+    const uint64_t end = c + 1 < nchunks ? word_off[c + 1] : nwords;
+    uint64_t e = esc_off[c];
+    const uint64_t e_end = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
+    if (start > end || end > nwords || e > e_end || e_end > noutliers) {
+        atomicOr(status, ST_CORRUPT);
+        return;
+    }
+    const uint64_t first = c * CHUNK;
+    const int cnt = (int)min((uint64_t)CHUNK, n - first);
+    auto load = [&](uint64_t k) -> uint64_t { return k < end ? (uint64_t)words[k] : 0ull; };
+    uint64_t wi = start;
+    uint64_t win = (load(wi) << 32) | load(wi + 1);
+    unsigned off = 0;
+    uint64_t bit = start * 32;
+    const uint64_t endbit = end * 32;
+    uint32_t pk[4] = {0, 0, 0, 0};
+    bool ok = true;
+    int k = 0;
+    for (; k < cnt; ++k) {
+        const uint32_t top = (uint32_t)((win << off) >> 32);
+        uint32_t ent = T.lut[top >> (32 - LUT_BITS)];
+        unsigned len, s;
+        if (ent) {
+            len = ent >> 16;
+            s = ent & 0xFFFF;
+        } else {
+            len = 0;
+            s = 0;
+            for (unsigned l = LUT_BITS + 1; l <= T.maxlen; ++l) {
+                const uint32_t code = top >> (32 - l);
+                const uint32_t d = code - T.first_code[l];
+                if (d < T.count[l]) {
+                    len = l;
+                    s = T.sorted[T.first_index[l] + d];
+                    break;
+                }
+            }
+            if (!len) {
+                ok = false;
+                break;
+            }
+        }
+        bit += len;
+        if (bit > endbit) {
+            ok = false;
+            break;
+        }
+        off += len;
+        if (off >= 32) {
+            ++wi;
+            win = (win << 32) | load(wi + 1);
+            off -= 32;
+        }
+        if (s == MGARD_ESC) {
+            if (e >= e_end) {
+                ok = false;
+                break;
+            }
+            escapes[first + k] = outliers[e++];
+        }
+        const int slot = k & 7;
+        if (slot & 1) pk[slot >> 1] |= s << 16;
+        else pk[slot >> 1] = s;
+        if (slot == 7) {
+            *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+    if (ok) {
+        const int rem = cnt & 7;   // symbols decoded after the last full group
+        for (int r = 0; r < rem; ++r) {
+            const uint32_t w = pk[r >> 1];
+            sym[first + (cnt - rem) + r] = (uint16_t)((r & 1) ? (w >> 16) : (w & 0xFFFF));
+        }
+        if (e != e_end) ok = false;
+    }
+    if (!ok) atomicOr(status, ST_CORRUPT);
+}
+
+}  // namespace
+
+mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
+                              cudaStream_t st) {
+    const size_t smem = sizeof(CodebookSmem);
+    static bool attr = false;
+    if (!attr) {
+        MGB_CUDA(cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr = true;
+    }
+    k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths);
+    MGB_CUDA(cudaGetLastError());
+    (void)codes;
+    return MGARD_OK;
+}
+
+mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
+                            cudaStream_t st) {
+    k_tables<<<1, CB_THREADS, 0, st>>>(lengths, codes, dt);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
+                           uint64_t* word_off, uint64_t* esc_off, unsigned long long* totals,
+                           unsigned* status, cudaStream_t st) {
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    if (nchunks) {
+        k_chunk_count<<<grid_for((int64_t)nchunks, ENC_WARPS, 148LL * 16), ENC_WARPS * 32, 0, st>>>(
+            sym, n, lengths, word_off, esc_off, nchunks, status);
+        MGB_CUDA(cudaGetLastError());
+    }
+    k_scan2<<<1, 1024, 0, st>>>(word_off, esc_off, nchunks, totals);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
+                          const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
+                          const int32_t* escapes, uint32_t* words, int32_t* outliers,
+                          cudaStream_t st) {
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    if (!nchunks) return MGARD_OK;
+    k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
+        sym, n, lengths, codes, word_off, esc_off, escapes, words, outliers, nchunks);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                            const DecodeTables* dt, uint64_t n, const int32_t* outliers,
+                            uint64_t noutliers, const uint64_t* esc_off, uint16_t* sym,
+                            int32_t* escapes, unsigned* status, cudaStream_t st) {
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    if (!nchunks) return MGARD_OK;
+    const int grid = (int)((nchunks + DEC_THREADS - 1) / DEC_THREADS);
+    k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, dt, n, outliers, noutliers,
+                                          esc_off, sym, escapes, status, nchunks);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+}  // namespace mgb

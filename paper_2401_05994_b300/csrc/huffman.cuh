@@ -1,0 +1,42 @@
+// Huffman codebook, encoder and decoder (declarations).
+#pragma once
+
+#include "common.cuh"
+
+namespace mgb {
+
+constexpr int LUT_BITS = 12;
+
+struct DecodeTables {
+    uint32_t lut[1 << LUT_BITS];   // prefix -> (length << 16) | symbol, 0 if the code is longer
+    uint32_t first_code[LMAX + 2];
+    uint32_t count[LMAX + 2];
+    uint32_t first_index[LMAX + 2];
+    uint16_t sorted[DICT];         // used symbols in (length, symbol) order
+    uint32_t maxlen;
+    uint32_t valid;                // 0 if the lengths violate the Kraft inequality
+};
+
+// Code lengths and canonical codes from a histogram (single CTA).
+mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
+                              cudaStream_t st);
+// Canonical codes and decode tables from code lengths (single CTA).
+mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
+                            cudaStream_t st);
+// Pass 1 of encoding: per-chunk word and escape counts and their exclusive
+// prefixes; totals (device, 2 x uint64) receive total words / escapes.
+mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
+                           uint64_t* word_off, uint64_t* esc_off, unsigned long long* totals,
+                           unsigned* status, cudaStream_t st);
+// Pass 2: pack codes and gather escapes.
+mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
+                          const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
+                          const int32_t* escapes, uint32_t* words, int32_t* outliers,
+                          cudaStream_t st);
+// Decoding with bounds checks (ST_CORRUPT on failure).
+mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                            const DecodeTables* dt, uint64_t n, const int32_t* outliers,
+                            uint64_t noutliers, const uint64_t* esc_off, uint16_t* sym,
+                            int32_t* escapes, unsigned* status, cudaStream_t st);
+
+}  // namespace mgb

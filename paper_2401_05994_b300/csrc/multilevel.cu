@@ -1,0 +1,608 @@
+// Multilevel decomposition and recomposition kernels.
+//
+// Paper, "Software design": u is decomposed recursively into multilevel
+// coefficients over the grid hierarchy; recomposition is the inverse.
+// One step from level l to l-1, on the P1 (piecewise multilinear) spaces:
+//   1. coefficients  z = u_l - Pi_{l-1} u_l   (k_coeff_gather; also copies
+//      the coarse nodal values into the compact level-(l-1) array)
+//   2. load vector   b = P^T M_l z            (k_restrict, one axis at a time,
+//      each pass shrinking that axis to the coarse extent)
+//   3. coarse solve  M_{l-1} c = b             (k_solve_*, tridiagonal along
+//      every axis; batched Thomas with precomputed factors)
+//   4. correction    u_{l-1} = u_l|coarse + c (fused into the last solve)
+// Recomposition runs 2-3 on the stored coefficients, subtracts the
+// correction and refills the fine grid (k_fill).
+#include <algorithm>
+
+#include "multilevel.cuh"
+
+namespace mgb {
+
+namespace {
+
+struct Shape4 {
+    int64_t n[4];
+};
+
+struct Mask {
+    const int* fcls[4];
+    int on;
+};
+
+__host__ __device__ inline int64_t shape_prod(const Shape4& s) {
+    return s.n[0] * s.n[1] * s.n[2] * s.n[3];
+}
+
+// -- step 1 -----------------------------------------------------------------
+template <typename T>
+__global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Level<T> lv) {
+    const int64_t N = prod4(lv.n);
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i[4];
+        unravel4(lin, lv.n, i);
+        int64_t p0[4], p1[4], J[4];
+        T w0[4], w1[4];
+        int nc[4];
+        bool allc = true;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int* fc = lv.ax[a].fcls;
+            nc[a] = 1;
+            p0[a] = p1[a] = i[a];
+            w0[a] = T(1);
+            w1[a] = T(0);
+            J[a] = i[a];
+            if (!fc) continue;
+            int c = fc[i[a]];
+            if (c >= 0) {
+                J[a] = c;
+            } else {
+                allc = false;
+                int left = -c - 1;
+                p0[a] = lv.ax[a].rf[left];
+                p1[a] = lv.ax[a].rf[left + 1];
+                w0[a] = lv.ax[a].wl[i[a]];
+                w1[a] = lv.ax[a].wr[i[a]];
+                nc[a] = 2;
+            }
+        }
+        const T u = in[lin];
+        if (allc) {
+            coarse[ravel4(J, lv.nc)] = u;
+            continue;
+        }
+        T acc = T(0);
+        for (int c0 = 0; c0 < nc[0]; ++c0)
+            for (int c1 = 0; c1 < nc[1]; ++c1)
+                for (int c2 = 0; c2 < nc[2]; ++c2)
+                    for (int c3 = 0; c3 < nc[3]; ++c3) {
+                        int64_t q[4] = {c0 ? p1[0] : p0[0], c1 ? p1[1] : p0[1],
+                                        c2 ? p1[2] : p0[2], c3 ? p1[3] : p0[3]};
+                        T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
+                              (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
+                        acc += w * in[ravel4(q, lv.n)];
+                    }
+        out[lin] = u - acc;
+    }
+}
+
+// -- step 2 -----------------------------------------------------------------
+// Restriction along axis a; with mask.on the input is the fine grid and
+// nodes of the coarse grid count as zero (z vanishes there) -- they are not
+// even read, so stale values at those positions never matter.
+template <typename Tin, typename Tout>
+__global__ void k_restrict(const Tin* __restrict__ in, Tout* __restrict__ out, Shape4 sin, int a,
+                           const int* __restrict__ rf, const Tout* __restrict__ rw, int64_t nca,
+                           Mask mask) {
+    Shape4 so = sin;
+    so.n[a] = nca;
+    const int64_t N = shape_prod(so);
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o[4];
+        unravel4(lin, so.n, o);
+        bool others_coarse = true;
+        if (mask.on) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (b != a && mask.fcls[b] && mask.fcls[b][o[b]] < 0) others_coarse = false;
+        }
+        const int64_t J = o[a];
+        const int64_t f = rf[J];
+        Tout acc = Tout(0);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const int64_t ip = f - 2 + t;
+            if (ip < 0 || ip >= sin.n[a]) continue;
+            const Tout w = rw[J * 5 + t];
+            if (w == Tout(0)) continue;
+            if (mask.on && others_coarse && mask.fcls[a][ip] >= 0) continue;
+            int64_t q[4] = {o[0], o[1], o[2], o[3]};
+            q[a] = ip;
+            acc += w * (Tout)in[ravel4(q, sin.n)];
+        }
+        out[lin] = acc;
+    }
+}
+
+// -- step 3 (+4) --------------------------------------------------------------
+// One thread per line along axis a (coalesced across the following axes).
+template <typename Tw, typename Tdst>
+__global__ void k_solve_lines(Tw* x, Shape4 s, int a, const Tw* __restrict__ sub,
+                              const Tw* __restrict__ inv, const Tw* __restrict__ cp, Tdst* dst,
+                              Tw sign) {
+    const int64_t m = s.n[a];
+    int64_t stride = 1;
+    for (int b = a + 1; b < 4; ++b) stride *= s.n[b];
+    const int64_t lines = shape_prod(s) / m;
+    for (int64_t ln = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ln < lines;
+         ln += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t inner = ln % stride;
+        const int64_t outer = ln / stride;
+        Tw* base = x + outer * m * stride + inner;
+        Tw y = base[0] * inv[0];
+        base[0] = y;
+        for (int64_t k = 1; k < m; ++k) {
+            y = (base[k * stride] - sub[k] * y) * inv[k];
+            base[k * stride] = y;
+        }
+        Tw v = y;
+        Tdst* d = dst ? dst + outer * m * stride + inner : nullptr;
+        if (d) d[(m - 1) * stride] = (Tdst)((Tw)d[(m - 1) * stride] + sign * v);
+        else base[(m - 1) * stride] = v;
+        for (int64_t k = m - 2; k >= 0; --k) {
+            v = base[k * stride] - cp[k] * v;
+            if (d) d[k * stride] = (Tdst)((Tw)d[k * stride] + sign * v);
+            else base[k * stride] = v;
+        }
+    }
+}
+
+// Lines along the contiguous axis: a warp stages 32 lines in shared memory
+// (row stride m+1 keeps the per-thread column walks bank-conflict free).
+template <typename Tw, typename Tdst>
+__global__ void k_solve_rows(Tw* x, int64_t lines, int64_t m, const Tw* __restrict__ sub,
+                             const Tw* __restrict__ inv, const Tw* __restrict__ cp, Tdst* dst,
+                             Tw sign) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tw* tile = (Tw*)smem_raw;
+    const int64_t ld = m + 1;
+    const int tid = threadIdx.x;
+    for (int64_t l0 = blockIdx.x * 32LL; l0 < lines; l0 += (int64_t)gridDim.x * 32) {
+        const int64_t nl = min((int64_t)32, lines - l0);
+        const Tw* src = x + l0 * m;
+        for (int64_t e = tid; e < nl * m; e += 32) tile[(e / m) * ld + e % m] = src[e];
+        __syncwarp();
+        if (tid < nl) {
+            Tw* r = tile + tid * ld;
+            Tw y = r[0] * inv[0];
+            r[0] = y;
+            for (int64_t k = 1; k < m; ++k) {
+                y = (r[k] - sub[k] * y) * inv[k];
+                r[k] = y;
+            }
+            Tw v = y;
+            for (int64_t k = m - 2; k >= 0; --k) {
+                v = r[k] - cp[k] * v;
+                r[k] = v;
+            }
+        }
+        __syncwarp();
+        if (dst) {
+            Tdst* d = dst + l0 * m;
+            for (int64_t e = tid; e < nl * m; e += 32)
+                d[e] = (Tdst)((Tw)d[e] + sign * tile[(e / m) * ld + e % m]);
+        } else {
+            Tw* d = x + l0 * m;
+            for (int64_t e = tid; e < nl * m; e += 32) d[e] = tile[(e / m) * ld + e % m];
+        }
+        __syncwarp();
+    }
+}
+
+// -- recomposition fill ------------------------------------------------------
+template <typename T>
+__global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level<T> lv) {
+    const int64_t N = prod4(lv.n);
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i[4];
+        unravel4(lin, lv.n, i);
+        int64_t j0[4], j1[4];
+        T w0[4], w1[4];
+        int nc[4];
+        bool allc = true;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int* fc = lv.ax[a].fcls;
+            nc[a] = 1;
+            j0[a] = j1[a] = i[a];
+            w0[a] = T(1);
+            w1[a] = T(0);
+            if (!fc) continue;
+            int c = fc[i[a]];
+            if (c >= 0) {
+                j0[a] = c;
+            } else {
+                allc = false;
+                j0[a] = -c - 1;
+                j1[a] = -c;
+                w0[a] = lv.ax[a].wl[i[a]];
+                w1[a] = lv.ax[a].wr[i[a]];
+                nc[a] = 2;
+            }
+        }
+        if (allc) {
+            out[lin] = coarse[ravel4(j0, lv.nc)];
+            continue;
+        }
+        T acc = T(0);
+        for (int c0 = 0; c0 < nc[0]; ++c0)
+            for (int c1 = 0; c1 < nc[1]; ++c1)
+                for (int c2 = 0; c2 < nc[2]; ++c2)
+                    for (int c3 = 0; c3 < nc[3]; ++c3) {
+                        int64_t q[4] = {c0 ? j1[0] : j0[0], c1 ? j1[1] : j0[1],
+                                        c2 ? j1[2] : j0[2], c3 ? j1[3] : j0[3]};
+                        T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
+                              (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
+                        acc += w * coarse[ravel4(q, lv.nc)];
+                    }
+        out[lin] = zin[lin] + acc;
+    }
+}
+
+// -- layout conversion -------------------------------------------------------
+template <typename T, bool kScatter>
+__global__ void k_layout(T* compact, T* data, LevelIndex li, Level<T> lv, int has_tables,
+                         Shape4 fine) {
+    const int64_t N = prod4(li.n);
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i[4];
+        unravel4(lin, li.n, i);
+        if (has_tables) {
+            bool allc = true;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (lv.ax[a].fcls && lv.ax[a].fcls[i[a]] < 0) allc = false;
+            if (allc) continue;
+        }
+        int64_t q[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) q[a] = li.pos[a][i[a]];
+        const int64_t g = ravel4(q, fine.n);
+        if (kScatter) data[g] = compact[lin];
+        else compact[lin] = data[g];
+    }
+}
+
+template <typename T>
+__global__ void k_difference(const T* __restrict__ a, const T* __restrict__ b,
+                             double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)b[i] - (double)a[i];
+}
+
+// -- reductions --------------------------------------------------------------
+constexpr int RED_BLOCKS = 592;
+constexpr int RED_THREADS = 256;
+
+template <typename T>
+__global__ void k_maxabs(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
+                         double* partial, unsigned* status) {
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = b ? (double)b[i] - (double)a[i] : (double)a[i];
+        if (!isfinite(v)) bad = true;
+        m = fmax(m, fabs(v));
+    }
+    __shared__ double sh[RED_THREADS];
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+// sum_i u_i (M u)_i with the tensor mass matrix of a level (3^D stencil).
+template <typename T>
+__global__ void k_mass_norm(const T* __restrict__ u, Level<T> lv, double* partial) {
+    const int64_t N = prod4(lv.n);
+    double s = 0.0;
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i[4];
+        unravel4(lin, lv.n, i);
+        double f[4][3];
+        int lo[4], hi[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double* md = lv.ax[a].mdiag;
+            f[a][0] = f[a][2] = 0.0;
+            if (!md) {
+                lo[a] = hi[a] = 0;
+                f[a][1] = 1.0;
+                continue;
+            }
+            const double* mo = lv.ax[a].moff;
+            lo[a] = i[a] > 0 ? -1 : 0;
+            hi[a] = i[a] + 1 < lv.n[a] ? 1 : 0;
+            f[a][0] = i[a] > 0 ? mo[i[a] - 1] : 0.0;
+            f[a][1] = md[i[a]];
+            f[a][2] = mo[i[a]];
+        }
+        double mu = 0.0;
+        for (int o0 = lo[0]; o0 <= hi[0]; ++o0)
+            for (int o1 = lo[1]; o1 <= hi[1]; ++o1)
+                for (int o2 = lo[2]; o2 <= hi[2]; ++o2)
+                    for (int o3 = lo[3]; o3 <= hi[3]; ++o3) {
+                        int64_t q[4] = {i[0] + o0, i[1] + o1, i[2] + o2, i[3] + o3};
+                        mu += f[0][o0 + 1] * f[1][o1 + 1] * f[2][o2 + 1] * f[3][o3 + 1] *
+                              (double)u[ravel4(q, lv.n)];
+                    }
+        s += (double)u[lin] * mu;
+    }
+    __shared__ double sh[RED_THREADS];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+int max_dyn_smem() {
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0, x = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        v = x > 0 ? x : 48 * 1024;
+    }
+    return v;
+}
+
+template <typename Tw, typename Tdst>
+mgard_status solve_axis(Tw* x, Shape4 s, int a, const Tw* sub, const Tw* inv, const Tw* cp,
+                        Tdst* dst, Tw sign, cudaStream_t st) {
+    const int64_t m = s.n[a];
+    const int64_t lines = shape_prod(s) / m;
+    if (a == 3) {
+        const size_t smem = 32 * (size_t)(m + 1) * sizeof(Tw);
+        const size_t cap = std::min<size_t>((size_t)max_dyn_smem(), 200 * 1024);
+        if (smem <= cap) {
+            static bool attr_set = false;
+            if (!attr_set) {
+                MGB_CUDA(cudaFuncSetAttribute(k_solve_rows<Tw, Tdst>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)cap));
+                attr_set = true;
+            }
+            int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
+            k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, m, sub, inv, cp, dst, sign);
+            MGB_CUDA(cudaGetLastError());
+            return MGARD_OK;
+        }
+    }
+    k_solve_lines<Tw, Tdst><<<grid_for(lines, 128), 128, 0, st>>>(x, s, a, sub, inv, cp, dst, sign);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+// Steps 2-4 for one level: coarse += sign * M_{l-1}^{-1} P^T M_l z, with z
+// read from the level-l array `z` (its coarse positions are ignored).
+template <typename T, typename Tw>
+mgard_status correct_level(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
+                           T sign, cudaStream_t st) {
+    const Level<Tw>& lw = p.level<Tw>(l);
+    const Level<T>& lt = p.level<T>(l);
+    Shape4 s;
+    for (int a = 0; a < 4; ++a) s.n[a] = lt.n[a];
+    Mask mask;
+    for (int a = 0; a < 4; ++a) mask.fcls[a] = lt.ax[a].fcls;
+    mask.on = 1;
+    Mask nomask{};
+    const void* cur = z;
+    bool first = true;
+    Tw* bufs[2] = {(Tw*)t0, (Tw*)t1};
+    int which = 0;
+    int last_axis = -1;
+    for (int a = 0; a < 4; ++a) {
+        if (!lt.ax[a].fcls) continue;
+        Shape4 so = s;
+        so.n[a] = lt.nc[a];
+        const int64_t nout = shape_prod(so);
+        Tw* out = bufs[which];
+        if (first)
+            k_restrict<T, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
+                (const T*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], mask);
+        else
+            k_restrict<Tw, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
+                (const Tw*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], nomask);
+        MGB_CUDA(cudaGetLastError());
+        first = false;
+        s = so;
+        cur = out;
+        which ^= 1;
+        last_axis = a;
+    }
+    if (last_axis < 0) return MGARD_OK;
+    Tw* b = (Tw*)cur;
+    for (int a = 0; a < 4; ++a) {
+        if (!lt.ax[a].fcls) continue;
+        T* dst = a == last_axis ? coarse : nullptr;
+        MGB_TRY((solve_axis<Tw, T>(b, s, a, lw.ax[a].tsub, lw.ax[a].tinv, lw.ax[a].tcp, dst,
+                                   (Tw)sign, st)));
+    }
+    return MGARD_OK;
+}
+
+template <typename T>
+bool level_uses_fp64(const Plan& p, int l) {
+    return sizeof(T) == 8 || p.level_size(l - 1) < FP64_SOLVE_NODES;
+}
+
+template <typename T>
+mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1, T sign,
+                     cudaStream_t st) {
+    if (level_uses_fp64<T>(p, l)) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
+    return correct_level<T, T>(p, l, z, coarse, t0, t1, sign, st);
+}
+
+}  // namespace
+
+template <typename T>
+mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
+    lv.assign(p.L + 1, nullptr);
+    size_t total = 0;
+    std::vector<size_t> off(p.L + 1, 0);
+    for (int l = 0; l < p.L; ++l) {
+        off[l] = total;
+        total += ((size_t)p.level_size(l) * sizeof(T) + 255) & ~size_t(255);
+    }
+    size_t tmax = 16;
+    for (int l = 1; l <= p.L; ++l) {
+        int64_t s[4];
+        for (int a = 0; a < 4; ++a) s[a] = p.shape[l][a];
+        const size_t el = level_uses_fp64<T>(p, l) ? 8 : sizeof(T);
+        for (int a = 0; a < 4; ++a) {
+            if (p.n4[a] == 1) continue;
+            s[a] = p.shape[l - 1][a];
+            tmax = std::max(tmax, (size_t)(s[0] * s[1] * s[2] * s[3]) * el);
+        }
+    }
+    MGB_TRY(store.alloc(total, st));
+    MGB_TRY(temp0.alloc(tmax, st));
+    MGB_TRY(temp1.alloc(tmax, st));
+    for (int l = 0; l < p.L; ++l) lv[l] = (T*)((char*)store.p + off[l]);
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st) {
+    DevBuf part;
+    MGB_TRY(part.alloc(RED_BLOCKS * sizeof(double), st));
+    const Level<T>& lv = p.level<T>(l);   // holds the mass tables of level l
+    k_mass_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(u, lv, part.as<double>());
+    MGB_CUDA(cudaGetLastError());
+    double h[RED_BLOCKS];
+    MGB_CUDA(cudaMemcpyAsync(h, part.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < RED_BLOCKS; ++i) s += h[i];
+    *out = s;
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status max_abs(const T* a, const T* b, int64_t n, double* out, unsigned* status,
+                     cudaStream_t st) {
+    DevBuf part, stat;
+    MGB_TRY(part.alloc(RED_BLOCKS * sizeof(double), st));
+    MGB_TRY(stat.alloc(sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
+    k_maxabs<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, part.as<double>(), stat.as<unsigned>());
+    MGB_CUDA(cudaGetLastError());
+    double h[RED_BLOCKS];
+    unsigned hs = 0;
+    MGB_CUDA(cudaMemcpyAsync(h, part.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaMemcpyAsync(&hs, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    double m = 0.0;
+    for (int i = 0; i < RED_BLOCKS; ++i) m = std::max(m, h[i]);
+    *out = m;
+    if (status) *status = hs;
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status difference(const T* a, const T* b, double* y, int64_t n, cudaStream_t st) {
+    k_difference<T><<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
+                               cudaStream_t st, double* E) {
+    for (int l = p.L; l >= 1; --l) {
+        const T* src = l == p.L ? in : py.lv[l];
+        T* dst = l == p.L ? top : py.lv[l];
+        if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
+        k_coeff_gather<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(src, dst, py.lv[l - 1],
+                                                                          p.level<T>(l));
+        MGB_CUDA(cudaGetLastError());
+        MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
+    }
+    if (E) MGB_TRY(mass_norm2<T>(p, 0, p.L ? py.lv[0] : in, &E[0], st));
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& py,
+                               cudaStream_t st) {
+    if (p.L == 0) {
+        if (out != top)
+            MGB_CUDA(cudaMemcpyAsync(out, top, p.total() * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        return MGARD_OK;
+    }
+    for (int l = 1; l <= p.L; ++l) {
+        const T* z = l == p.L ? top : py.lv[l];
+        T* dst = l == p.L ? out : py.lv[l];
+        MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st));
+        k_fill<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(z, py.lv[l - 1], dst,
+                                                                  p.level<T>(l));
+        MGB_CUDA(cudaGetLastError());
+    }
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status scatter_levels(const Plan& p, const Pyramid<T>& py, T* data, cudaStream_t st) {
+    Shape4 fine;
+    for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
+    for (int l = 0; l < p.L; ++l) {
+        k_layout<T, true><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+            py.lv[l], data, p.lidx[l], p.level<T>(l), l > 0 ? 1 : 0, fine);
+        MGB_CUDA(cudaGetLastError());
+    }
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStream_t st) {
+    Shape4 fine;
+    for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
+    for (int l = 0; l < p.L; ++l) {
+        k_layout<T, false><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+            py.lv[l], (T*)data, p.lidx[l], p.level<T>(l), 0, fine);
+        MGB_CUDA(cudaGetLastError());
+    }
+    return MGARD_OK;
+}
+
+#define INST(T)                                                                               \
+    template struct Pyramid<T>;                                                               \
+    template mgard_status decompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
+                                               cudaStream_t, double*);                        \
+    template mgard_status recompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
+                                               cudaStream_t);                                 \
+    template mgard_status scatter_levels<T>(const Plan&, const Pyramid<T>&, T*, cudaStream_t); \
+    template mgard_status gather_levels<T>(const Plan&, const T*, Pyramid<T>&, cudaStream_t);  \
+    template mgard_status max_abs<T>(const T*, const T*, int64_t, double*, unsigned*,          \
+                                     cudaStream_t);                                           \
+    template mgard_status mass_norm2<T>(const Plan&, int, const T*, double*, cudaStream_t);    \
+    template mgard_status difference<T>(const T*, const T*, double*, int64_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mgb

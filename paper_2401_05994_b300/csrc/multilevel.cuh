@@ -1,0 +1,81 @@
+// Multilevel decomposition / recomposition on the device (declarations).
+#pragma once
+
+#include <vector>
+
+#include "plan.cuh"
+
+namespace mgb {
+
+// Stream-ordered device allocation that frees itself.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    mgard_status alloc(size_t bytes, cudaStream_t s) {
+        st = s;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("device allocation: ") + cudaGetErrorString(e));
+            return MGARD_ENOMEM;
+        }
+        return MGARD_OK;
+    }
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+// Compact per-level arrays of the pyramid: level l < L has its own
+// row-major array of the level-l grid; level L is the caller's array.
+template <typename T>
+struct Pyramid {
+    std::vector<T*> lv;       // [l] compact array of level l (l < L)
+    DevBuf store;
+    DevBuf temp0, temp1;      // restriction ping-pong buffers
+    mgard_status alloc(const Plan& p, cudaStream_t st);
+};
+
+// Coarse grids with fewer nodes than this run their restriction and
+// tridiagonal solves in double precision.
+constexpr int64_t FP64_SOLVE_NODES = int64_t(1) << 21;
+
+// Decompose `in` (level-L nodal values) into `top` (coefficients on the
+// level-L new nodes; coarse positions untouched) and the pyramid levels.
+// `in` may equal `top`.  If `E` is non-null, E[l] receives u_l^T M_l u_l of
+// every level's nodal values (FP64 accumulation; host array of L+1).
+template <typename T>
+mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
+                               cudaStream_t st, double* E);
+
+// Recompose: `top` holds level-L coefficients (coarse positions ignored),
+// py.lv[l] the coefficients of level l >= 1 (coarse positions ignored) and
+// py.lv[0] the level-0 values.  Writes nodal values to `out` (may equal
+// `top`).  Overwrites the pyramid.
+template <typename T>
+mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& py,
+                               cudaStream_t st);
+
+// In-place layout <-> pyramid (levels below L only).
+template <typename T>
+mgard_status scatter_levels(const Plan& p, const Pyramid<T>& py, T* data, cudaStream_t st);
+template <typename T>
+mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStream_t st);
+
+// Reductions (FP64 results, deterministic order; synchronize the stream).
+template <typename T>
+mgard_status max_abs(const T* a, const T* b, int64_t n, double* out, unsigned* status,
+                     cudaStream_t st);
+template <typename T>
+mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st);
+
+// y = b - a in double (device), for error norms.
+template <typename T>
+mgard_status difference(const T* a, const T* b, double* y, int64_t n, cudaStream_t st);
+
+}  // namespace mgb

@@ -1,0 +1,47 @@
+// Per-shape tables ("plan"): the node hierarchy, interpolation, restriction
+// and tridiagonal factors of every level, and the constants of the error
+// estimators.  Built once per (shape, levels) on the host in FP64 and kept
+// in device memory.
+#pragma once
+
+#include <array>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mgb {
+
+struct Plan {
+    int D = 0;                       // active axes
+    int L = 0;                       // levels above level 0
+    int64_t n4[4] = {1, 1, 1, 1};    // squeezed shape in the 4D view
+    std::vector<std::array<int64_t, 4>> shape;   // [l] level-l shape, l = 0..L
+    std::vector<int64_t> offset;     // [l] symbol offset of level l
+    std::vector<int64_t> count;      // [l] symbols of level l (new nodes)
+    std::vector<double> K;           // [l] correction norm (l >= 1)
+    std::vector<double> mu;          // [l] Gershgorin bound of the level mass matrix
+    std::vector<Level<float>> lf;    // [l] tables of level l (transition l -> l-1 for l >= 1)
+    std::vector<Level<double>> ld;
+    std::vector<LevelIndex> lidx;    // [l] finest positions of level-l nodes
+    void* dbuf = nullptr;
+    int64_t total() const { return n4[0] * n4[1] * n4[2] * n4[3]; }
+    int64_t level_size(int l) const { return shape[l][0] * shape[l][1] * shape[l][2] * shape[l][3]; }
+    template <typename T> const Level<T>& level(int l) const;
+    ~Plan();
+};
+
+template <> inline const Level<float>& Plan::level<float>(int l) const { return lf[l]; }
+template <> inline const Level<double>& Plan::level<double>(int l) const { return ld[l]; }
+
+// Validate a shape and compute the squeezed 4D view; MGARD_ESHAPE on error.
+mgard_status squeeze_shape(int ndim, const int64_t* shape, int64_t n4[4], int* D);
+// Number of levels for a squeezed shape.
+int level_count(const int64_t n4[4], int D, int max_levels);
+// Cached plan (built on first use; device tables on the current device).
+mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out);
+// Bin widths (host) from a plan.
+void bin_widths(const Plan& p, double tol_abs, double s, double* w);
+void release_plans();
+
+}  // namespace mgb

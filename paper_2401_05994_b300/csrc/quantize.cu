@@ -1,0 +1,221 @@
+// Level-wise linear quantization and its inverse, with a fused histogram.
+//
+// Paper, "Software design": every multilevel coefficient is approximated by
+// an integer multiple of its level's bin width.  Symbols are laid out level
+// by level (level 0 first), each level in row-major order of its grid,
+// holding only the nodes new on that level.  |q| < DICT/2 maps to symbol
+// q + DICT/2; larger values escape to symbol 0 with q stored aside.
+#include "quantize.cuh"
+
+namespace mgb {
+
+namespace {
+
+struct QLevel {
+    int64_t n[4];           // level grid shape
+    int64_t nc[4];          // coarse grid shape (rank computation)
+    const int* fcls[4];     // level tables (null: inactive axis or level 0)
+    const int* cbefore[4];
+    const int64_t* pos[4];  // finest positions (in-place layout); null for compact
+    int64_t fine[4];        // finest shape (in-place layout)
+    int64_t sym_off;
+    int tables;             // level >= 1
+};
+
+struct NodeInfo {
+    int64_t addr;
+    int64_t rank;
+    bool skip;
+};
+
+// Position of a level-l node among the nodes new on level l (row-major):
+// its linear index minus the number of coarse-grid nodes before it.
+__device__ inline NodeInfo node_info(const QLevel& q, int64_t lin) {
+    int64_t i[4];
+    unravel4(lin, q.n, i);
+    NodeInfo r;
+    r.skip = false;
+    r.rank = lin;
+    if (q.tables) {
+        bool prefix = true;   // all axes before the current one are coarse
+        int64_t cnt = 0;
+        int64_t tail = q.nc[1] * q.nc[2] * q.nc[3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (a > 0) tail /= q.nc[a];
+            const int* fc = q.fcls[a];
+            if (!fc) continue;
+            if (prefix) cnt += (int64_t)q.cbefore[a][i[a]] * tail;
+            if (fc[i[a]] < 0) prefix = false;
+        }
+        r.skip = prefix;   // a node of the coarser grid
+        r.rank = lin - cnt;
+    }
+    if (q.pos[0]) {
+        int64_t g[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) g[a] = q.pos[a][i[a]];
+        r.addr = ravel4(g, q.fine);
+    } else {
+        r.addr = lin;
+    }
+    return r;
+}
+
+__device__ inline void quantize_value(float c, float inv_w, double w, int& sym, int32_t& qo,
+                                      unsigned& st) {
+    if (!isfinite(c)) {
+        st |= ST_NONFINITE;
+        sym = MGARD_ESC;
+        qo = 0;
+        return;
+    }
+    const float x = __fmul_rn(c, inv_w);
+    const float q = rintf(x);
+    if (fabsf(q) < (float)RADIUS) {
+        sym = (int)q + RADIUS;
+        return;
+    }
+    sym = MGARD_ESC;
+    const double qd = rint((double)c / w);
+    if (fabs(qd) > 2147483647.0) {
+        st |= ST_RANGE;
+        qo = 0;
+    } else {
+        qo = (int32_t)qd;
+    }
+}
+
+__device__ inline void quantize_value(double c, double /*inv_w*/, double w, int& sym, int32_t& qo,
+                                      unsigned& st) {
+    if (!isfinite(c)) {
+        st |= ST_NONFINITE;
+        sym = MGARD_ESC;
+        qo = 0;
+        return;
+    }
+    const double q = rint(c / w);
+    if (fabs(q) < (double)RADIUS) {
+        sym = (int)q + RADIUS;
+        return;
+    }
+    sym = MGARD_ESC;
+    if (fabs(q) > 2147483647.0) {
+        st |= ST_RANGE;
+        qo = 0;
+    } else {
+        qo = (int32_t)q;
+    }
+}
+
+constexpr int QT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel q, T inv_w,
+                                                 double w, uint16_t* __restrict__ sym,
+                                                 int32_t* __restrict__ esc,
+                                                 unsigned long long* __restrict__ hist,
+                                                 unsigned* status) {
+    __shared__ unsigned sh[DICT];
+    for (int k = threadIdx.x; k < DICT; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int64_t N = prod4(q.n);
+    const int lane = threadIdx.x & 31;
+    unsigned st = 0;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < N;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lin = base + threadIdx.x;
+        int s = -1;
+        if (lin < N) {
+            NodeInfo ni = node_info(q, lin);
+            if (!ni.skip) {
+                int32_t qo = 0;
+                quantize_value(c[ni.addr], inv_w, w, s, qo, st);
+                const int64_t p = q.sym_off + ni.rank;
+                sym[p] = (uint16_t)s;
+                if (s == MGARD_ESC) esc[p] = qo;
+            }
+        }
+        // warp-aggregated histogram update: one shared atomic per distinct symbol
+        const unsigned grp = __match_any_sync(0xffffffffu, s);
+        if (s >= 0 && lane == __ffs(grp) - 1) atomicAdd(&sh[s], (unsigned)__popc(grp));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < DICT; k += blockDim.x)
+        if (sh[k]) atomicAdd(&hist[k], (unsigned long long)sh[k]);
+    if (st) atomicOr(status, st);
+}
+
+template <typename T>
+__global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
+                             QLevel q, T wt, double w, T* __restrict__ c) {
+    const int64_t N = prod4(q.n);
+    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        NodeInfo ni = node_info(q, lin);
+        if (ni.skip) {
+            if (!q.pos[0]) c[ni.addr] = T(0);   // compact level array: z = 0 on coarse nodes
+            continue;
+        }
+        const int64_t p = q.sym_off + ni.rank;
+        const int s = sym[p];
+        T v;
+        if (s == MGARD_ESC) v = (T)((double)esc[p] * w);
+        else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
+        else v = (T)((double)(s - RADIUS) * w);
+        c[ni.addr] = v;
+    }
+}
+
+QLevel make_qlevel(const Plan& p, int l, bool inplace) {
+    QLevel q{};
+    for (int a = 0; a < 4; ++a) {
+        q.n[a] = p.shape[l][a];
+        q.nc[a] = l > 0 ? p.shape[l - 1][a] : p.shape[l][a];
+        q.fine[a] = p.n4[a];
+        q.pos[a] = inplace ? p.lidx[l].pos[a] : nullptr;
+        if (l > 0) {
+            q.fcls[a] = p.lf[l].ax[a].fcls;
+            q.cbefore[a] = p.lf[l].ax[a].cbefore;
+        }
+    }
+    q.tables = l > 0 ? 1 : 0;
+    q.sym_off = p.offset[l];
+    return q;
+}
+
+}  // namespace
+
+template <typename T>
+mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, double w,
+                            uint16_t* sym, int32_t* esc, unsigned long long* hist,
+                            unsigned* status, cudaStream_t st) {
+    QLevel q = make_qlevel(p, l, inplace);
+    const T inv_w = (T)(1.0 / w);
+    const int64_t N = p.level_size(l);
+    k_quantize<T><<<grid_for(N, QT, 148LL * 8), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
+                              bool inplace, double w, T* c, cudaStream_t st) {
+    QLevel q = make_qlevel(p, l, inplace);
+    const int64_t N = p.level_size(l);
+    k_dequantize<T><<<grid_for(N, 256), 256, 0, st>>>(sym, esc, q, (T)w, w, c);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+#define INST(T)                                                                                  \
+    template mgard_status quantize_level<T>(const Plan&, int, const T*, bool, double, uint16_t*, \
+                                            int32_t*, unsigned long long*, unsigned*,            \
+                                            cudaStream_t);                                       \
+    template mgard_status dequantize_level<T>(const Plan&, int, const uint16_t*, const int32_t*, \
+                                              bool, double, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mgb

@@ -1,0 +1,22 @@
+// Level-wise quantization (declarations).
+#pragma once
+
+#include "plan.cuh"
+
+namespace mgb {
+
+// Quantize the level-l coefficients of `c` (compact level array when
+// inplace = false, the whole in-place array otherwise) with bin width w;
+// accumulates into `hist` (DICT counters) and ORs ST_* bits into status.
+template <typename T>
+mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, double w,
+                            uint16_t* sym, int32_t* esc, unsigned long long* hist,
+                            unsigned* status, cudaStream_t st);
+
+// Inverse; writes 0 on the positions of coarser nodes in a compact level
+// array and leaves them untouched in the in-place layout.
+template <typename T>
+mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
+                              bool inplace, double w, T* c, cudaStream_t st);
+
+}  // namespace mgb
