@@ -1,0 +1,348 @@
+"""Benchmark: compress + decompress throughput on one B300.
+
+Workload: a 513^3 float32 Gaussian random field (energy spectrum k^-5/3,
+unit variance, seed 1 + rank), relative L-infinity tolerance 1e-3.  One
+step = mgard_compress + mgard_decompress of the field (device buffers,
+input resident in HBM); the metric is field bytes / (compress + decompress
+time) in GB/s.  The 540 MB field is larger than L2 (126 MB), so no flush is
+needed between steps.
+
+Also reported on the same JSON line:
+  e2e          the same metric through the C ABI with pinned HOST buffers
+               (host->device and device->host copies inside the timed region)
+  roofline     achieved algorithmic bytes / time of the dominant kernel,
+               from traced launches (CUDA events on the launch stream),
+               against the measured HBM copy bandwidth
+  cpu_baseline the FP64 oracle on a bounded sample (a 129^3 sub-cube)
+  clocks       SM clocks sampled with nvidia-smi during the timed region
+Multi-GPU: one process per GPU (torchrun), independent replicas with no
+data-path collective; a barrier and a max over ranks frame the timing.
+
+``--impl reference`` times the oracle itself (CPU, bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (513, 513, 513)
+TOL = 1e-3
+BETA = 5.0 / 3.0
+SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
+
+
+def level_shapes(shape):
+    """Level grid shapes (finest first): even positions plus the last one."""
+    out = [tuple(shape)]
+    L = None
+    for n in shape:
+        c, m = 0, n
+        while m > 2:
+            m = m // 2 + 1
+            c += 1
+        L = c if L is None else min(L, c)
+    cur = list(shape)
+    for _ in range(L):
+        cur = [m // 2 + 1 for m in cur]
+        out.append(tuple(cur))
+    return out
+
+
+def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
+    """Bytes each kernel must move per step (one compress + one decompress),
+    summed over its launches: reads of its inputs plus writes of its outputs,
+    counted once (cache re-reads excluded)."""
+    lv = level_shapes(shape)
+    N = int(np.prod(shape))
+    by = {}
+
+    def add(k, v):
+        by[k] = by.get(k, 0.0) + v
+
+    for l in range(len(lv) - 1):
+        n, nc = int(np.prod(lv[l])), int(np.prod(lv[l + 1]))
+        fp64 = nc < (1 << 21)
+        ew = 8 if fp64 else esize
+        # decomposition: coefficient pass reads u_l, writes coefficients + coarse copy
+        add("k_coeff_gather", 2 * n * esize)
+        # restriction chain (compress and decompress each run it once)
+        cur = list(lv[l])
+        src = esize
+        for a in range(3):
+            nin = int(np.prod(cur))
+            cur[a] = lv[l + 1][a]
+            nout = int(np.prod(cur))
+            add("k_restrict", 2 * (nin * src + nout * ew))
+            src = ew
+        # three solves (read+write); the last also reads+writes the coarse array
+        add("k_solve_rows", 2 * (2 * nc * ew + 2 * nc * esize))
+        add("k_solve_lines", 2 * 2 * (2 * nc * ew))
+        # recomposition fill: reads z_l and the coarse array, writes u_l
+        add("k_fill", (2 * n + nc) * esize)
+    add("k_quantize", N * esize + 2 * N)
+    add("k_dequantize", 2 * N + N * esize)
+    add("k_maxabs", N * esize)
+    add("k_chunk_count", 2 * N)
+    add("k_pack", 2 * N + comp_bytes)
+    add("k_decode", comp_bytes + 2 * N + 4 * esc_count)
+    return by
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "50"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                     hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        sm = sorted(r["sm"] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_oracle_sample(u_host: np.ndarray, tol: float, seconds_hint: float = 0.0):
+    """Oracle compress + decompress (its own Huffman decoder included) on a
+    sub-cube; returns (field bytes, seconds, threads)."""
+    from threadpoolctl import threadpool_limits
+    from oracle import huffman, pipeline
+    sub = np.ascontiguousarray(u_host[:SAMPLE, :SAMPLE, :SAMPLE])
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        c = pipeline.compress(sub, tol, math.inf, precision="f32")
+        s = huffman.decode(c["words"], c["word_off"], c["lengths"], len(c["symbols"]))
+        pipeline.decompress(c, symbols=s)
+        dt = time.perf_counter() - t0
+    return sub.size * 4, dt, 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2401_05994_b300 import synth
+    u = synth.gaussian_random_field((SAMPLE + 8,) * 3, beta=BETA, seed=1).numpy()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(u, TOL)
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t, cores = cpu_oracle_sample(u, TOL)
+        tot_b += b
+        tot_t += t
+    gbs = tot_b / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": "compress+decompress GB/s (rel Linf 1e-3)",
+        "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{SAMPLE}^3 sub-cube of a 513^3 f32 GRF k^-5/3, "
+                                                    "rel Linf 1e-3, FP64 CPU oracle"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{SAMPLE}^3 sub-cube per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch.distributed as dist
+    from paper_2401_05994_b300 import binding, build_ext, synth
+    build_ext.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    u = synth.gaussian_random_field(SHAPE, beta=BETA, seed=1 + rank, device=dev)
+    field_bytes = u.numel() * 4
+    bound = binding.compress_bound(SHAPE)
+    comp = torch.empty(bound, dtype=torch.uint8, device=dev)
+    out = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        buf = binding.compress(u, TOL, math.inf, binding.REL, out=comp)
+        binding.decompress(buf, out=out)
+        return buf
+
+    for _ in range(args.warmup):
+        buf = step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    time.sleep(0.2)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        buf = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    t_local = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * args.steps * field_bytes / (ms_max / 1e3) / 1e9
+
+    # verification in FP64 (untimed): the bound holds for this run's output
+    meta = binding.info(buf)
+    err = binding.error_norm(u, out, math.inf)
+    comp_bytes = buf.numel()
+    ratio = field_bytes / comp_bytes
+
+    # roofline of the dominant kernel from traced launches of the same steps
+    binding.timing_report()
+    binding.timing_enable(True)
+    trace_steps = 3
+    for _ in range(trace_steps):
+        step()
+    torch.cuda.synchronize()
+    binding.timing_enable(False)
+    rep = binding.timing_report()
+    from paper_2401_05994_b300.fmt import HEADER_SIZE, header
+    esc_count = header(buf[:HEADER_SIZE].cpu().numpy().tobytes())["noutliers"]
+    algo = algorithmic_bytes(SHAPE, comp_bytes, esc_count)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernel_ms = {k: v[1] / trace_steps for k, v in rep.items()}
+    dom = max(kernel_ms, key=kernel_ms.get) if kernel_ms else None
+    roof = None
+    if dom:
+        ach = algo.get(dom, 0.0) / (kernel_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
+                "kernel_ms_per_step": kernel_ms[dom],
+                "kernel_share": kernel_ms[dom] / sum(kernel_ms.values())}
+
+    # end-to-end through the C ABI with pinned host buffers
+    hu = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+    hu.copy_(u)
+    hcomp = torch.empty(bound, dtype=torch.uint8, pin_memory=True)
+    hout = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+    hu_np, hcomp_np, hout_np = hu.numpy(), hcomp.numpy(), hout.numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        hb = binding.compress(hu_np, TOL, math.inf, binding.REL, out=hcomp_np)
+        binding.decompress(hb, out=hout_np)
+    barrier()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        hb = binding.compress(hu_np, TOL, math.inf, binding.REL, out=hcomp_np)
+        binding.decompress(hb, out=hout_np)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = torch.tensor([f0.elapsed_time(f1)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps * field_bytes / (float(e_ms.item()) / 1e3) / 1e9
+    e2e = {"value": e2e_value, "unit": "GB/s",
+           "h2d_bytes_per_step": field_bytes + hb.nbytes,
+           "d2h_bytes_per_step": hb.nbytes + field_bytes}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        b, t, cores = cpu_oracle_sample(u.cpu().numpy(), TOL)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"{SAMPLE}^3 sub-cube of the field, compress+decompress incl. decode"}
+
+    launches = sum(v[0] for v in rep.values()) // trace_steps * args.steps
+    if rank == 0:
+        line = {
+            "metric": "compress+decompress GB/s (rel Linf 1e-3)", "value": value, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "513^3 f32 Gaussian random field, E(k)~k^-5/3, rel Linf 1e-3",
+                       "global_batch": world, "l2": "input 540 MB > L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clocks,
+            "verify": {"max_abs_error": err, "tol_abs": meta["tol_abs"], "ok": err <= meta["tol_abs"],
+                       "ratio": ratio},
+            "kernels_ms_per_step": {k: round(v, 4) for k, v in sorted(kernel_ms.items(),
+                                                                        key=lambda kv: -kv[1])},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,7 +159,8 @@ mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint
  * `escapes`, which is indexed by symbol position; capacity `outliers_cap`).
  * *nwords and *noutliers (host) receive the totals; synchronizes the
  * stream.  MGARD_ECAPACITY (totals still returned, nothing packed) if a
- * capacity is short; MGARD_EINVAL if a symbol has no code. */
+ * capacity is short; MGARD_EINVAL if a symbol has no code or `symbols` is
+ * not 16-byte aligned (it is read with 16-byte vector loads). */
 mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uint8_t* lengths,
                                   const int32_t* escapes, uint32_t* words, uint64_t words_cap,
                                   uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
@@ -168,7 +169,8 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
 /* Decode n symbols (device output) from a stream produced by
  * mgard_huffman_encode; escapes[position] receives each outlier value.
  * Reads never leave the stream: a chunk that runs past its end or holds an
- * invalid code gives MGARD_ECORRUPT (synchronizes the stream). */
+ * invalid code gives MGARD_ECORRUPT (synchronizes the stream).  `symbols`
+ * must be 16-byte aligned (MGARD_EINVAL otherwise). */
 mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
                                   const uint8_t* lengths, uint64_t n, const int32_t* outliers,
                                   uint64_t noutliers, const uint64_t* esc_off, uint16_t* symbols,
@@ -200,6 +202,16 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
 /* Read the header of a compressed buffer (host or device pointer). */
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
                         mgard_dtype* dtype, double* tol_abs, int* nlevels);
+/* ---- Tracing -------------------------------------------------------------
+ * When enabled, every kernel launch of the library is bracketed by a pair
+ * of CUDA events recorded on its launch stream (adds about a microsecond
+ * per launch; off by default). */
+void mgard_timing_enable(int on);
+/* Waits for the recorded events and writes one line per kernel,
+ * "name launches total_ms", into buf (capacity cap, NUL-terminated); clears
+ * the records.  Returns the size the full report needs. */
+size_t mgard_timing_report(char* buf, size_t cap);
+
 /* Release a buffer allocated by this library (host or device). */
 void mgard_free(void* p);
 /* Drop cached per-shape tables. */

@@ -1,0 +1,334 @@
+"""Thin Python binding of the C ABI in ``include/mgard_b300.h``.
+
+Argument marshalling only: every step runs in ``libmgard_b300.so``.  Device
+arrays are ``torch.Tensor`` on CUDA (contiguous); host arrays are numpy
+arrays or CPU tensors.  The functions carry the C names without the
+``mgard_`` prefix.  If the compiled library is missing this module raises
+on import of the library (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgard_b300.so")
+
+F32, F64 = 0, 1
+ABS, REL = 0, 1
+DICT = 4096
+CHUNK = 1024
+ESC = 0
+
+_c_int64_p = ctypes.POINTER(ctypes.c_int64)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); mirrors include/mgard_b300.h
+SIGNATURES = {
+    "mgard_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mgard_last_error": (ctypes.c_char_p, []),
+    "mgard_version": (ctypes.c_uint32, []),
+    "mgard_levels": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_decompose": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp]),
+    "mgard_recompose": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp]),
+    "mgard_bin_widths": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, _c_double_p, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_norm": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, _c_double_p, _vp]),
+    "mgard_error_norm": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _c_double_p, _vp]),
+    "mgard_quantize": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int,
+                                      _c_double_p, _vp, _vp, _vp, _vp]),
+    "mgard_dequantize": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int,
+                                        _c_double_p, _vp, _vp]),
+    "mgard_huffman_codebook": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mgard_huffman_encode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint64, _vp, _vp,
+                                            _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_uint64), _vp]),
+    "mgard_huffman_decode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64, _vp,
+                                            ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+    "mgard_compress_bound": (ctypes.c_size_t, [ctypes.c_int, _c_int64_p, ctypes.c_int]),
+    "mgard_compress": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
+                                      ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
+    "mgard_decompress": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
+                                  ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_timing_enable": (None, [ctypes.c_int]),
+    "mgard_timing_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+    "mgard_free": (None, [_vp]),
+    "mgard_release_plans": (None, []),
+}
+
+_lib = None
+
+
+class MgardError(RuntimeError):
+    def __init__(self, status: int, text: str):
+        super().__init__(f"{text} (status {status})")
+        self.status = status
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                               "`python -m paper_2401_05994_b300.build_ext`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        L = lib()
+        msg = L.mgard_strerror(status).decode()
+        detail = L.mgard_last_error().decode()
+        raise MgardError(status, f"{msg}: {detail}" if detail else msg)
+
+
+def _shape(shape):
+    shape = [int(s) for s in shape]
+    return len(shape), (ctypes.c_int64 * len(shape))(*shape)
+
+
+def _stream():
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+def _dtype_code(dt) -> int:
+    if dt in (torch.float32, np.float32, np.dtype(np.float32)):
+        return F32
+    if dt in (torch.float64, np.float64, np.dtype(np.float64)):
+        return F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def _ptr(x):
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(type(x))
+
+
+def _require_cuda(t):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("a CUDA tensor is required")
+
+
+# ---- low level --------------------------------------------------------------
+
+def levels(shape, max_levels: int = -1) -> int:
+    nd, sh = _shape(shape)
+    out = ctypes.c_int()
+    _check(lib().mgard_levels(nd, sh, max_levels, ctypes.byref(out)))
+    return out.value
+
+
+def decompose(t: torch.Tensor, max_levels: int = -1) -> torch.Tensor:
+    _require_cuda(t)
+    nd, sh = _shape(t.shape)
+    _check(lib().mgard_decompose(_ptr(t), nd, sh, _dtype_code(t.dtype), max_levels, _stream()))
+    return t
+
+
+def recompose(t: torch.Tensor, max_levels: int = -1) -> torch.Tensor:
+    _require_cuda(t)
+    nd, sh = _shape(t.shape)
+    _check(lib().mgard_recompose(_ptr(t), nd, sh, _dtype_code(t.dtype), max_levels, _stream()))
+    return t
+
+
+def bin_widths(shape, tol_abs: float, s: float = math.inf, max_levels: int = -1) -> np.ndarray:
+    nd, sh = _shape(shape)
+    L = levels(shape, max_levels)
+    w = np.zeros(L + 1)
+    nl = ctypes.c_int()
+    _check(lib().mgard_bin_widths(nd, sh, max_levels, tol_abs, s,
+                                  w.ctypes.data_as(_c_double_p), ctypes.byref(nl)))
+    return w
+
+
+def norm(t: torch.Tensor, s: float = math.inf, max_levels: int = -1) -> float:
+    _require_cuda(t)
+    nd, sh = _shape(t.shape)
+    out = ctypes.c_double()
+    _check(lib().mgard_norm(_ptr(t), nd, sh, _dtype_code(t.dtype), max_levels, s,
+                            ctypes.byref(out), _stream()))
+    return out.value
+
+
+def error_norm(a: torch.Tensor, b: torch.Tensor, s: float = math.inf, max_levels: int = -1) -> float:
+    _require_cuda(a)
+    _require_cuda(b)
+    if a.shape != b.shape or a.dtype != b.dtype:
+        raise ValueError("shape/dtype mismatch")
+    nd, sh = _shape(a.shape)
+    out = ctypes.c_double()
+    _check(lib().mgard_error_norm(_ptr(a), _ptr(b), nd, sh, _dtype_code(a.dtype), max_levels, s,
+                                  ctypes.byref(out), _stream()))
+    return out.value
+
+
+def quantize(coeffs: torch.Tensor, widths, max_levels: int = -1):
+    """Returns (symbols uint16, escapes int32 indexed by symbol position,
+    histogram int64) as CUDA tensors."""
+    _require_cuda(coeffs)
+    nd, sh = _shape(coeffs.shape)
+    n = coeffs.numel()
+    dev = coeffs.device
+    sym = torch.empty(n, dtype=torch.uint16, device=dev)
+    esc = torch.zeros(n, dtype=torch.int32, device=dev)
+    hist = torch.empty(DICT, dtype=torch.int64, device=dev)
+    w = np.ascontiguousarray(widths, dtype=np.float64)
+    _check(lib().mgard_quantize(_ptr(coeffs), nd, sh, _dtype_code(coeffs.dtype), max_levels,
+                                w.ctypes.data_as(_c_double_p), _ptr(sym), _ptr(esc), _ptr(hist),
+                                _stream()))
+    return sym, esc, hist
+
+
+def dequantize(sym: torch.Tensor, esc: torch.Tensor, shape, dtype, widths,
+               max_levels: int = -1, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    _require_cuda(sym)
+    if out is None:
+        out = torch.zeros(tuple(shape), dtype=dtype, device=sym.device)
+    nd, sh = _shape(shape)
+    w = np.ascontiguousarray(widths, dtype=np.float64)
+    _check(lib().mgard_dequantize(_ptr(sym), _ptr(esc), nd, sh, _dtype_code(out.dtype), max_levels,
+                                  w.ctypes.data_as(_c_double_p), _ptr(out), _stream()))
+    return out
+
+
+def huffman_codebook(hist: torch.Tensor):
+    """Code lengths (uint8) and canonical codes (int32 view of uint32)."""
+    _require_cuda(hist)
+    lengths = torch.empty(DICT, dtype=torch.uint8, device=hist.device)
+    codes = torch.empty(DICT, dtype=torch.int32, device=hist.device)
+    _check(lib().mgard_huffman_codebook(_ptr(hist.to(torch.int64).contiguous()), _ptr(lengths),
+                                        _ptr(codes), _stream()))
+    return lengths, codes
+
+
+def huffman_encode(sym: torch.Tensor, lengths: torch.Tensor, esc: torch.Tensor):
+    """Returns (words int32 view of uint32, word_off int64, esc_off int64,
+    outliers int32)."""
+    _require_cuda(sym)
+    n = sym.numel()
+    nchunks = (n + CHUNK - 1) // CHUNK
+    dev = sym.device
+    word_off = torch.empty(max(nchunks, 1), dtype=torch.int64, device=dev)
+    esc_off = torch.empty(max(nchunks, 1), dtype=torch.int64, device=dev)
+    cap_w = n + nchunks + 1
+    words = torch.empty(cap_w, dtype=torch.int32, device=dev)
+    outl = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    nw = ctypes.c_uint64()
+    no = ctypes.c_uint64()
+    _check(lib().mgard_huffman_encode(_ptr(sym), n, _ptr(lengths), _ptr(esc), _ptr(words), cap_w,
+                                      _ptr(word_off), _ptr(esc_off), _ptr(outl), max(n, 1),
+                                      ctypes.byref(nw), ctypes.byref(no), _stream()))
+    return words[:nw.value], word_off[:nchunks], esc_off[:nchunks], outl[:no.value]
+
+
+def huffman_decode(words, word_off, lengths, n: int, outliers, esc_off):
+    _require_cuda(words)
+    dev = words.device
+    sym = torch.empty(max(n, 1), dtype=torch.uint16, device=dev)
+    esc = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+    outliers = outliers if outliers.numel() else torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib().mgard_huffman_decode(_ptr(words), words.numel(), _ptr(word_off), _ptr(lengths), n,
+                                      _ptr(outliers), outliers.numel() if n else 0, _ptr(esc_off),
+                                      _ptr(sym), _ptr(esc), _stream()))
+    return sym[:n], esc[:n]
+
+
+def timing_enable(on: bool = True):
+    lib().mgard_timing_enable(1 if on else 0)
+
+
+def timing_report() -> dict:
+    """{kernel: (launches, total_ms)} of the traced launches (clears them)."""
+    L = lib()
+    need = L.mgard_timing_report(None, 0)
+    buf = ctypes.create_string_buffer(max(need, 1) + 4096)
+    L.mgard_timing_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out
+
+
+# ---- high level -------------------------------------------------------------
+
+def compress_bound(shape, dtype=torch.float32) -> int:
+    nd, sh = _shape(shape)
+    return int(lib().mgard_compress_bound(nd, sh, _dtype_code(dtype)))
+
+
+def compress(field, tol: float, s: float = math.inf, mode: int = REL, out=None):
+    """Compress a CUDA tensor (result: CUDA uint8 tensor) or a host array
+    (numpy / CPU tensor; result: numpy uint8 array).  ``out`` may supply a
+    preallocated buffer of the same kind, at least ``compress_bound`` bytes."""
+    host = not (isinstance(field, torch.Tensor) and field.is_cuda)
+    if isinstance(field, torch.Tensor) and host:
+        field = field.numpy()
+    nd, sh = _shape(field.shape)
+    dt = _dtype_code(field.dtype)
+    if out is None:
+        bound = compress_bound(field.shape, field.dtype)
+        out = np.empty(bound, np.uint8) if host else torch.empty(bound, dtype=torch.uint8,
+                                                                 device=field.device)
+    nbytes = ctypes.c_size_t(out.nbytes if isinstance(out, np.ndarray) else out.numel())
+    p = ctypes.c_void_p(_ptr(out).value)
+    _check(lib().mgard_compress(_ptr(field), nd, sh, dt, float(tol), float(s), int(mode),
+                                ctypes.byref(p), ctypes.byref(nbytes), 1, _stream()))
+    return out[:nbytes.value]
+
+
+def info(buf):
+    nd = ctypes.c_int()
+    shape = (ctypes.c_int64 * 4)()
+    dt = ctypes.c_int()
+    tol_abs = ctypes.c_double()
+    nl = ctypes.c_int()
+    nbytes = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel()
+    _check(lib().mgard_info(_ptr(buf), nbytes, ctypes.byref(nd), shape, ctypes.byref(dt),
+                            ctypes.byref(tol_abs), ctypes.byref(nl)))
+    return dict(shape=tuple(shape[i] for i in range(nd.value)),
+                dtype=torch.float64 if dt.value == F64 else torch.float32,
+                tol_abs=tol_abs.value, nlevels=nl.value)
+
+
+def decompress(buf, out=None):
+    """Inverse of :func:`compress` (same placement rules)."""
+    meta = info(buf)
+    host = isinstance(buf, np.ndarray)
+    if out is None:
+        if host:
+            out = np.empty(meta["shape"], dtype=np.float64 if meta["dtype"] == torch.float64
+                           else np.float32)
+        else:
+            out = torch.empty(meta["shape"], dtype=meta["dtype"], device=buf.device)
+    nbytes = buf.nbytes if host else buf.numel()
+    p = ctypes.c_void_p(_ptr(out).value)
+    _check(lib().mgard_decompress(_ptr(buf), nbytes, ctypes.byref(p), 1, _stream()))
+    return out

@@ -455,7 +455,7 @@ mgard_status mgard_bin_widths(int ndim, const int64_t* shape, int max_levels, do
         return MGARD_EINVAL;
     }
     const Plan* p;
-    MGB_TRY(get_plan(ndim, shape, max_levels, &p));
+    MGB_TRY(get_plan(ndim, shape, max_levels, &p, false));
     bin_widths(*p, tol_abs, s, widths);
     if (nlevels) *nlevels = p->L;
     return MGARD_OK;
@@ -560,6 +560,10 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
                                   void* stream) {
     if ((!symbols && n) || !lengths || !nwords || !noutliers || (n && (!word_off || !esc_off)))
         return MGARD_EINVAL;
+    if (((uintptr_t)symbols & 15) != 0) {
+        set_error("symbols must be 16-byte aligned");
+        return MGARD_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf totals, stat, codes, dt;
     MGB_TRY(totals.alloc(16, st));
@@ -594,6 +598,10 @@ mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const 
                                   int32_t* escapes, void* stream) {
     if (!lengths || (n && (!words || !word_off || !esc_off || !symbols || !escapes)))
         return MGARD_EINVAL;
+    if (((uintptr_t)symbols & 15) != 0) {
+        set_error("symbols must be 16-byte aligned");
+        return MGARD_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf codes, dt, stat;
     MGB_TRY(codes.alloc(DICT * 4, st));

@@ -28,6 +28,26 @@ void set_error(const std::string& msg);
         if (s_ != MGARD_OK) return s_;     \
     } while (0)
 
+// Kernel tracing (timing.cu): a scope that brackets the launches inside it
+// with CUDA events on `st` when mgard_timing_enable(1) is in effect.
+int timing_begin(const char* name, cudaStream_t st);
+void timing_end(int slot, cudaStream_t st);
+struct ScopedTimer {
+    int slot;
+    cudaStream_t st;
+    ScopedTimer(const char* name, cudaStream_t s) : slot(timing_begin(name, s)), st(s) {}
+    ~ScopedTimer() { timing_end(slot, st); }
+};
+#define MGB_CAT2(a, b) a##b
+#define MGB_CAT(a, b) MGB_CAT2(a, b)
+#define MGB_TIMED(name, st) ::mgb::ScopedTimer MGB_CAT(mgb_timer_, __LINE__)(name, st)
+// Launch a kernel inside its own traced scope.
+#define MGB_LAUNCH(name, st, ...)                  \
+    do {                                           \
+        ::mgb::ScopedTimer mgb_launch_timer_(name, st); \
+        __VA_ARGS__;                               \
+    } while (0)
+
 constexpr int DICT = MGARD_DICT;
 constexpr int RADIUS = MGARD_DICT / 2;
 constexpr int CHUNK = MGARD_CHUNK;

@@ -485,7 +485,7 @@ mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, 
                                       (int)smem));
         attr = true;
     }
-    k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths);
+    MGB_LAUNCH("k_codebook", st, k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths));
     MGB_CUDA(cudaGetLastError());
     (void)codes;
     return MGARD_OK;
@@ -493,7 +493,7 @@ mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, 
 
 mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
                             cudaStream_t st) {
-    k_tables<<<1, CB_THREADS, 0, st>>>(lengths, codes, dt);
+    MGB_LAUNCH("k_tables", st, k_tables<<<1, CB_THREADS, 0, st>>>(lengths, codes, dt));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -503,11 +503,11 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
                            unsigned* status, cudaStream_t st) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (nchunks) {
-        k_chunk_count<<<grid_for((int64_t)nchunks, ENC_WARPS, 148LL * 16), ENC_WARPS * 32, 0, st>>>(
-            sym, n, lengths, word_off, esc_off, nchunks, status);
+        MGB_LAUNCH("k_chunk_count", st, k_chunk_count<<<grid_for((int64_t)nchunks, ENC_WARPS, 148LL * 16), ENC_WARPS * 32, 0, st>>>(
+            sym, n, lengths, word_off, esc_off, nchunks, status));
         MGB_CUDA(cudaGetLastError());
     }
-    k_scan2<<<1, 1024, 0, st>>>(word_off, esc_off, nchunks, totals);
+    MGB_LAUNCH("k_scan2", st, k_scan2<<<1, 1024, 0, st>>>(word_off, esc_off, nchunks, totals));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -518,8 +518,8 @@ mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* length
                           cudaStream_t st) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
-        sym, n, lengths, codes, word_off, esc_off, escapes, words, outliers, nchunks);
+    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
+        sym, n, lengths, codes, word_off, esc_off, escapes, words, outliers, nchunks));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -531,8 +531,8 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     const int grid = (int)((nchunks + DEC_THREADS - 1) / DEC_THREADS);
-    k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, dt, n, outliers, noutliers,
-                                          esc_off, sym, escapes, status, nchunks);
+    MGB_LAUNCH("k_decode", st, k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, dt, n, outliers, noutliers,
+                                          esc_off, sym, escapes, status, nchunks));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }

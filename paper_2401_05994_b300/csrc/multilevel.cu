@@ -387,12 +387,12 @@ mgard_status solve_axis(Tw* x, Shape4 s, int a, const Tw* sub, const Tw* inv, co
                 attr_set = true;
             }
             int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
-            k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, m, sub, inv, cp, dst, sign);
+            MGB_LAUNCH("k_solve_rows", st, k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, m, sub, inv, cp, dst, sign));
             MGB_CUDA(cudaGetLastError());
             return MGARD_OK;
         }
     }
-    k_solve_lines<Tw, Tdst><<<grid_for(lines, 128), 128, 0, st>>>(x, s, a, sub, inv, cp, dst, sign);
+    MGB_LAUNCH("k_solve_lines", st, k_solve_lines<Tw, Tdst><<<grid_for(lines, 128), 128, 0, st>>>(x, s, a, sub, inv, cp, dst, sign));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -422,11 +422,11 @@ mgard_status correct_level(const Plan& p, int l, const T* z, T* coarse, void* t0
         const int64_t nout = shape_prod(so);
         Tw* out = bufs[which];
         if (first)
-            k_restrict<T, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
-                (const T*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], mask);
+            MGB_LAUNCH("k_restrict", st, k_restrict<T, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
+                (const T*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], mask));
         else
-            k_restrict<Tw, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
-                (const Tw*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], nomask);
+            MGB_LAUNCH("k_restrict", st, k_restrict<Tw, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
+                (const Tw*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], nomask));
         MGB_CUDA(cudaGetLastError());
         first = false;
         s = so;
@@ -491,7 +491,7 @@ mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStrea
     DevBuf part;
     MGB_TRY(part.alloc(RED_BLOCKS * sizeof(double), st));
     const Level<T>& lv = p.level<T>(l);   // holds the mass tables of level l
-    k_mass_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(u, lv, part.as<double>());
+    MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(u, lv, part.as<double>()));
     MGB_CUDA(cudaGetLastError());
     double h[RED_BLOCKS];
     MGB_CUDA(cudaMemcpyAsync(h, part.p, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -509,7 +509,7 @@ mgard_status max_abs(const T* a, const T* b, int64_t n, double* out, unsigned* s
     MGB_TRY(part.alloc(RED_BLOCKS * sizeof(double), st));
     MGB_TRY(stat.alloc(sizeof(unsigned), st));
     MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
-    k_maxabs<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, part.as<double>(), stat.as<unsigned>());
+    MGB_LAUNCH("k_maxabs", st, k_maxabs<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, part.as<double>(), stat.as<unsigned>()));
     MGB_CUDA(cudaGetLastError());
     double h[RED_BLOCKS];
     unsigned hs = 0;
@@ -525,7 +525,7 @@ mgard_status max_abs(const T* a, const T* b, int64_t n, double* out, unsigned* s
 
 template <typename T>
 mgard_status difference(const T* a, const T* b, double* y, int64_t n, cudaStream_t st) {
-    k_difference<T><<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n);
+    MGB_LAUNCH("k_difference", st, k_difference<T><<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -537,8 +537,8 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         const T* src = l == p.L ? in : py.lv[l];
         T* dst = l == p.L ? top : py.lv[l];
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
-        k_coeff_gather<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(src, dst, py.lv[l - 1],
-                                                                          p.level<T>(l));
+        MGB_LAUNCH("k_coeff_gather", st, k_coeff_gather<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(src, dst, py.lv[l - 1],
+                                                                          p.level<T>(l)));
         MGB_CUDA(cudaGetLastError());
         MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
     }
@@ -558,8 +558,8 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
         const T* z = l == p.L ? top : py.lv[l];
         T* dst = l == p.L ? out : py.lv[l];
         MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st));
-        k_fill<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(z, py.lv[l - 1], dst,
-                                                                  p.level<T>(l));
+        MGB_LAUNCH("k_fill", st, k_fill<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(z, py.lv[l - 1], dst,
+                                                                  p.level<T>(l)));
         MGB_CUDA(cudaGetLastError());
     }
     return MGARD_OK;
@@ -570,8 +570,8 @@ mgard_status scatter_levels(const Plan& p, const Pyramid<T>& py, T* data, cudaSt
     Shape4 fine;
     for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
     for (int l = 0; l < p.L; ++l) {
-        k_layout<T, true><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
-            py.lv[l], data, p.lidx[l], p.level<T>(l), l > 0 ? 1 : 0, fine);
+        MGB_LAUNCH("k_layout", st, k_layout<T, true><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+            py.lv[l], data, p.lidx[l], p.level<T>(l), l > 0 ? 1 : 0, fine));
         MGB_CUDA(cudaGetLastError());
     }
     return MGARD_OK;
@@ -582,8 +582,8 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
     Shape4 fine;
     for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
     for (int l = 0; l < p.L; ++l) {
-        k_layout<T, false><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
-            py.lv[l], (T*)data, p.lidx[l], p.level<T>(l), 0, fine);
+        MGB_LAUNCH("k_layout", st, k_layout<T, false><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+            py.lv[l], (T*)data, p.lidx[l], p.level<T>(l), 0, fine));
         MGB_CUDA(cudaGetLastError());
     }
     return MGARD_OK;

@@ -175,7 +175,7 @@ int level_count(const int64_t n4[4], int D, int max_levels) {
     return L;
 }
 
-static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p) {
+static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool device) {
     p.D = D;
     p.L = L;
     for (int a = 0; a < 4; ++a) p.n4[a] = n4[a];
@@ -306,6 +306,7 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p) {
             o.cpd = blob.add(tcp);
         }
     }
+    if (!device) return MGARD_OK;
     cudaError_t e = cudaMalloc(&p.dbuf, blob.bytes.size());
     if (e != cudaSuccess) {
         set_error(std::string("plan tables: ") + cudaGetErrorString(e));
@@ -358,13 +359,18 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p) {
     return MGARD_OK;
 }
 
-mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out) {
+mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out,
+                      bool device) {
     int64_t n4[4];
     int D;
     MGB_TRY(squeeze_shape(ndim, shape, n4, &D));
     int L = level_count(n4, D, max_levels);
-    int dev = 0;
-    cudaGetDevice(&dev);
+    int dev = -1;   // host-only plans use key -1
+    if (device && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return MGARD_ECUDA;
+    }
     auto key = std::make_tuple(dev, L, n4[0], n4[1], n4[2], n4[3]);
     std::lock_guard<std::mutex> lock(g_mutex);
     auto it = g_plans.find(key);
@@ -373,7 +379,7 @@ mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan
         return MGARD_OK;
     }
     auto p = std::make_unique<Plan>();
-    MGB_TRY(build_plan(n4, D, L, *p));
+    MGB_TRY(build_plan(n4, D, L, *p, device));
     *out = p.get();
     g_plans[key] = std::move(p);
     return MGARD_OK;

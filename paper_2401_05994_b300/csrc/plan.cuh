@@ -39,7 +39,10 @@ mgard_status squeeze_shape(int ndim, const int64_t* shape, int64_t n4[4], int* D
 // Number of levels for a squeezed shape.
 int level_count(const int64_t n4[4], int D, int max_levels);
 // Cached plan (built on first use; device tables on the current device).
-mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out);
+// With device = false only the host-side members (shapes, offsets, K, mu)
+// are filled and nothing touches the GPU.
+mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out,
+                      bool device = true);
 // Bin widths (host) from a plan.
 void bin_widths(const Plan& p, double tol_abs, double s, double* w);
 void release_plans();

@@ -193,7 +193,7 @@ mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, doub
     QLevel q = make_qlevel(p, l, inplace);
     const T inv_w = (T)(1.0 / w);
     const int64_t N = p.level_size(l);
-    k_quantize<T><<<grid_for(N, QT, 148LL * 8), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status);
+    MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid_for(N, QT, 148LL * 8), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -203,7 +203,7 @@ mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const i
                               bool inplace, double w, T* c, cudaStream_t st) {
     QLevel q = make_qlevel(p, l, inplace);
     const int64_t N = p.level_size(l);
-    k_dequantize<T><<<grid_for(N, 256), 256, 0, st>>>(sym, esc, q, (T)w, w, c);
+    MGB_LAUNCH("k_dequantize", st, k_dequantize<T><<<grid_for(N, 256), 256, 0, st>>>(sym, esc, q, (T)w, w, c));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
