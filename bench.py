@@ -146,19 +146,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_oracle_sample(u_host: np.ndarray, tol: float, seconds_hint: float = 0.0):
+_ORACLE_CHILD = r"""
+import math, sys, time, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import huffman, pipeline
+sub = np.load(sys.argv[2])
+t0 = time.perf_counter()
+c = pipeline.compress(sub, float(sys.argv[3]), math.inf, precision="f32")
+s = huffman.decode(c["words"], c["word_off"], c["lengths"], len(c["symbols"]))
+pipeline.decompress(c, symbols=s)
+print(json.dumps({"seconds": time.perf_counter() - t0, "bytes": int(sub.size * 4)}))
+"""
+
+
+def cpu_oracle_sample(u_host: np.ndarray, tol: float):
     """Oracle compress + decompress (its own Huffman decoder included) on a
-    sub-cube; returns (field bytes, seconds, threads)."""
-    from threadpoolctl import threadpool_limits
-    from oracle import huffman, pipeline
+    sub-cube, in a child process pinned to one thread (OMP/BLAS thread
+    counts 1); returns (field bytes, seconds, threads)."""
     sub = np.ascontiguousarray(u_host[:SAMPLE, :SAMPLE, :SAMPLE])
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        c = pipeline.compress(sub, tol, math.inf, precision="f32")
-        s = huffman.decode(c["words"], c["word_off"], c["lengths"], len(c["symbols"]))
-        pipeline.decompress(c, symbols=s)
-        dt = time.perf_counter() - t0
-    return sub.size * 4, dt, 1
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sub.npy")
+        np.save(path, sub)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path, repr(tol)],
+                           env=env, capture_output=True, text=True, check=True)
+    rec = json.loads(r.stdout.strip().splitlines()[-1])
+    return rec["bytes"], rec["seconds"], 1
 
 
 def run_reference(args, rank, world):

@@ -208,8 +208,9 @@ mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shap
  * per launch; off by default). */
 void mgard_timing_enable(int on);
 /* Waits for the recorded events and writes one line per kernel,
- * "name launches total_ms", into buf (capacity cap, NUL-terminated); clears
- * the records.  Returns the size the full report needs. */
+ * "name launches total_ms", into buf (capacity cap, NUL-terminated) and
+ * clears the records.  Returns the size the full report needs; with
+ * buf = NULL only the size is returned and the records are kept. */
 size_t mgard_timing_report(char* buf, size_t cap);
 
 /* Release a buffer allocated by this library (host or device). */

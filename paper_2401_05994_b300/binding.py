@@ -253,9 +253,10 @@ def huffman_decode(words, word_off, lengths, n: int, outliers, esc_off):
     dev = words.device
     sym = torch.empty(max(n, 1), dtype=torch.uint16, device=dev)
     esc = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
-    outliers = outliers if outliers.numel() else torch.zeros(1, dtype=torch.int32, device=dev)
+    nout = outliers.numel()
+    outliers = outliers if nout else torch.zeros(1, dtype=torch.int32, device=dev)
     _check(lib().mgard_huffman_decode(_ptr(words), words.numel(), _ptr(word_off), _ptr(lengths), n,
-                                      _ptr(outliers), outliers.numel() if n else 0, _ptr(esc_off),
+                                      _ptr(outliers), nout, _ptr(esc_off),
                                       _ptr(sym), _ptr(esc), _stream()))
     return sym[:n], esc[:n]
 

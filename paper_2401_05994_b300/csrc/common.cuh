@@ -105,6 +105,25 @@ __host__ __device__ inline int64_t ravel4(const int64_t* i, const int64_t* n) {
     return ((i[0] * n[1] + i[1]) * n[2] + i[2]) * n[3] + i[3];
 }
 
+// 3D launches over a 4D view without per-element integer division: threads
+// of x cover axis 3, grid y covers axis 2, grid z covers axes 0 and 1
+// folded; every level is a grid-stride loop, so any shape fits any grid.
+#define FOR_NODES(n, i0, i1, i2, i3)                                                         \
+    for (int64_t mgb_z_ = blockIdx.z; mgb_z_ < (n)[0] * (n)[1]; mgb_z_ += gridDim.z)          \
+        for (int64_t i0 = mgb_z_ / (n)[1], i1 = mgb_z_ - i0 * (n)[1], i2 = blockIdx.y;        \
+             i2 < (n)[2]; i2 += gridDim.y)                                                    \
+            for (int64_t i3 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i3 < (n)[3];     \
+                 i3 += (int64_t)gridDim.x * blockDim.x)
+
+inline dim3 grid3(const int64_t* n, int bx, int64_t ycap = 65535, int64_t zcap = 65535) {
+    int64_t gx = (n[3] + bx - 1) / bx;
+    if (gx > (1LL << 30)) gx = 1LL << 30;
+    int64_t gy = n[2] < ycap ? n[2] : ycap;
+    int64_t nz = n[0] * n[1];
+    int64_t gz = nz < zcap ? nz : zcap;
+    return dim3((unsigned)(gx < 1 ? 1 : gx), (unsigned)(gy < 1 ? 1 : gy), (unsigned)(gz < 1 ? 1 : gz));
+}
+
 inline int grid_for(int64_t work, int block, int64_t cap = 148LL * 64) {
     int64_t g = (work + block - 1) / block;
     if (g > cap) g = cap;

@@ -36,11 +36,8 @@ __host__ __device__ inline int64_t shape_prod(const Shape4& s) {
 // -- step 1 -----------------------------------------------------------------
 template <typename T>
 __global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Level<T> lv) {
-    const int64_t N = prod4(lv.n);
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i[4];
-        unravel4(lin, lv.n, i);
+    FOR_NODES(lv.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
         int64_t p0[4], p1[4], J[4];
         T w0[4], w1[4];
         int nc[4];
@@ -54,12 +51,12 @@ __global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Leve
             w1[a] = T(0);
             J[a] = i[a];
             if (!fc) continue;
-            int c = fc[i[a]];
+            const int c = fc[i[a]];
             if (c >= 0) {
                 J[a] = c;
             } else {
                 allc = false;
-                int left = -c - 1;
+                const int left = -c - 1;
                 p0[a] = lv.ax[a].rf[left];
                 p1[a] = lv.ax[a].rf[left + 1];
                 w0[a] = lv.ax[a].wl[i[a]];
@@ -67,6 +64,7 @@ __global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Leve
                 nc[a] = 2;
             }
         }
+        const int64_t lin = ravel4(i, lv.n);
         const T u = in[lin];
         if (allc) {
             coarse[ravel4(J, lv.nc)] = u;
@@ -77,10 +75,10 @@ __global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Leve
             for (int c1 = 0; c1 < nc[1]; ++c1)
                 for (int c2 = 0; c2 < nc[2]; ++c2)
                     for (int c3 = 0; c3 < nc[3]; ++c3) {
-                        int64_t q[4] = {c0 ? p1[0] : p0[0], c1 ? p1[1] : p0[1],
-                                        c2 ? p1[2] : p0[2], c3 ? p1[3] : p0[3]};
-                        T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
-                              (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
+                        const int64_t q[4] = {c0 ? p1[0] : p0[0], c1 ? p1[1] : p0[1],
+                                              c2 ? p1[2] : p0[2], c3 ? p1[3] : p0[3]};
+                        const T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
+                                    (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
                         acc += w * in[ravel4(q, lv.n)];
                     }
         out[lin] = u - acc;
@@ -93,15 +91,10 @@ __global__ void k_coeff_gather(const T* in, T* out, T* __restrict__ coarse, Leve
 // even read, so stale values at those positions never matter.
 template <typename Tin, typename Tout>
 __global__ void k_restrict(const Tin* __restrict__ in, Tout* __restrict__ out, Shape4 sin, int a,
-                           const int* __restrict__ rf, const Tout* __restrict__ rw, int64_t nca,
+                           const int* __restrict__ rf, const Tout* __restrict__ rw, Shape4 so,
                            Mask mask) {
-    Shape4 so = sin;
-    so.n[a] = nca;
-    const int64_t N = shape_prod(so);
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        int64_t o[4];
-        unravel4(lin, so.n, o);
+    FOR_NODES(so.n, o0, o1, o2, o3) {
+        const int64_t o[4] = {o0, o1, o2, o3};
         bool others_coarse = true;
         if (mask.on) {
 #pragma unroll
@@ -110,6 +103,11 @@ __global__ void k_restrict(const Tin* __restrict__ in, Tout* __restrict__ out, S
         }
         const int64_t J = o[a];
         const int64_t f = rf[J];
+        int64_t stride = 1;
+        for (int b = 3; b > a; --b) stride *= sin.n[b];
+        int64_t q[4] = {o[0], o[1], o[2], o[3]};
+        q[a] = 0;
+        const int64_t base = ravel4(q, sin.n);
         Tout acc = Tout(0);
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
@@ -118,72 +116,100 @@ __global__ void k_restrict(const Tin* __restrict__ in, Tout* __restrict__ out, S
             const Tout w = rw[J * 5 + t];
             if (w == Tout(0)) continue;
             if (mask.on && others_coarse && mask.fcls[a][ip] >= 0) continue;
-            int64_t q[4] = {o[0], o[1], o[2], o[3]};
-            q[a] = ip;
-            acc += w * (Tout)in[ravel4(q, sin.n)];
+            acc += w * (Tout)in[base + ip * stride];
         }
-        out[lin] = acc;
+        out[ravel4(o, so.n)] = acc;
     }
 }
 
 // -- step 3 (+4) --------------------------------------------------------------
-// One thread per line along axis a (coalesced across the following axes).
+// One thread per line along a non-contiguous axis a: lines are indexed by
+// (outer, inner) with inner contiguous, so a warp reads 32 consecutive
+// elements per step.  Loads are issued 8 at a time ahead of the recurrence.
 template <typename Tw, typename Tdst>
-__global__ void k_solve_lines(Tw* x, Shape4 s, int a, const Tw* __restrict__ sub,
-                              const Tw* __restrict__ inv, const Tw* __restrict__ cp, Tdst* dst,
-                              Tw sign) {
-    const int64_t m = s.n[a];
-    int64_t stride = 1;
-    for (int b = a + 1; b < 4; ++b) stride *= s.n[b];
-    const int64_t lines = shape_prod(s) / m;
-    for (int64_t ln = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ln < lines;
-         ln += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t inner = ln % stride;
-        const int64_t outer = ln / stride;
-        Tw* base = x + outer * m * stride + inner;
-        Tw y = base[0] * inv[0];
-        base[0] = y;
-        for (int64_t k = 1; k < m; ++k) {
-            y = (base[k * stride] - sub[k] * y) * inv[k];
-            base[k * stride] = y;
+__global__ void k_solve_lines(Tw* x, int64_t outer_n, int64_t m, int64_t stride,
+                              const Tw* __restrict__ sub, const Tw* __restrict__ inv,
+                              const Tw* __restrict__ cp, Tdst* dst, Tw sign) {
+    constexpr int U = 8;
+    for (int64_t outer = blockIdx.y; outer < outer_n; outer += gridDim.y)
+        for (int64_t inner = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; inner < stride;
+             inner += (int64_t)gridDim.x * blockDim.x) {
+            Tw* base = x + outer * m * stride + inner;
+            Tw y = Tw(0);
+            for (int64_t k0 = 0; k0 < m; k0 += U) {
+                Tw v[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (k0 + j < m) v[j] = base[(k0 + j) * stride];
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (k0 + j < m) {
+                        y = (v[j] - sub[k0 + j] * y) * inv[k0 + j];
+                        v[j] = y;
+                    }
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (k0 + j < m) base[(k0 + j) * stride] = v[j];
+            }
+            Tdst* d = dst ? dst + outer * m * stride + inner : nullptr;
+            Tw vnext = Tw(0);
+            for (int64_t k1 = m; k1 > 0; k1 -= U) {
+                const int64_t lo = k1 - U > 0 ? k1 - U : 0;
+                Tw v[U], dv[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int64_t k = k1 - 1 - j;
+                    if (k >= lo) {
+                        v[j] = base[k * stride];
+                        if (d) dv[j] = (Tw)d[k * stride];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int64_t k = k1 - 1 - j;
+                    if (k >= lo) {
+                        vnext = (k == m - 1) ? v[j] : v[j] - cp[k] * vnext;
+                        v[j] = vnext;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int64_t k = k1 - 1 - j;
+                    if (k >= lo) {
+                        if (d) d[k * stride] = (Tdst)(dv[j] + sign * v[j]);
+                        else base[k * stride] = v[j];
+                    }
+                }
+            }
         }
-        Tw v = y;
-        Tdst* d = dst ? dst + outer * m * stride + inner : nullptr;
-        if (d) d[(m - 1) * stride] = (Tdst)((Tw)d[(m - 1) * stride] + sign * v);
-        else base[(m - 1) * stride] = v;
-        for (int64_t k = m - 2; k >= 0; --k) {
-            v = base[k * stride] - cp[k] * v;
-            if (d) d[k * stride] = (Tdst)((Tw)d[k * stride] + sign * v);
-            else base[k * stride] = v;
-        }
-    }
 }
 
 // Lines along the contiguous axis: a warp stages 32 lines in shared memory
 // (row stride m+1 keeps the per-thread column walks bank-conflict free).
 template <typename Tw, typename Tdst>
-__global__ void k_solve_rows(Tw* x, int64_t lines, int64_t m, const Tw* __restrict__ sub,
+__global__ void k_solve_rows(Tw* x, int64_t lines, int m, const Tw* __restrict__ sub,
                              const Tw* __restrict__ inv, const Tw* __restrict__ cp, Tdst* dst,
                              Tw sign) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Tw* tile = (Tw*)smem_raw;
-    const int64_t ld = m + 1;
+    const int ld = m + 1;
     const int tid = threadIdx.x;
     for (int64_t l0 = blockIdx.x * 32LL; l0 < lines; l0 += (int64_t)gridDim.x * 32) {
-        const int64_t nl = min((int64_t)32, lines - l0);
+        const int nl = (int)min((int64_t)32, lines - l0);
         const Tw* src = x + l0 * m;
-        for (int64_t e = tid; e < nl * m; e += 32) tile[(e / m) * ld + e % m] = src[e];
+        for (int r = 0; r < nl; ++r)
+            for (int k = tid; k < m; k += 32) tile[r * ld + k] = src[(int64_t)r * m + k];
         __syncwarp();
         if (tid < nl) {
             Tw* r = tile + tid * ld;
             Tw y = r[0] * inv[0];
             r[0] = y;
-            for (int64_t k = 1; k < m; ++k) {
+            for (int k = 1; k < m; ++k) {
                 y = (r[k] - sub[k] * y) * inv[k];
                 r[k] = y;
             }
             Tw v = y;
-            for (int64_t k = m - 2; k >= 0; --k) {
+            for (int k = m - 2; k >= 0; --k) {
                 v = r[k] - cp[k] * v;
                 r[k] = v;
             }
@@ -191,11 +217,15 @@ __global__ void k_solve_rows(Tw* x, int64_t lines, int64_t m, const Tw* __restri
         __syncwarp();
         if (dst) {
             Tdst* d = dst + l0 * m;
-            for (int64_t e = tid; e < nl * m; e += 32)
-                d[e] = (Tdst)((Tw)d[e] + sign * tile[(e / m) * ld + e % m]);
+            for (int r = 0; r < nl; ++r)
+                for (int k = tid; k < m; k += 32) {
+                    const int64_t e = (int64_t)r * m + k;
+                    d[e] = (Tdst)((Tw)d[e] + sign * tile[r * ld + k]);
+                }
         } else {
             Tw* d = x + l0 * m;
-            for (int64_t e = tid; e < nl * m; e += 32) d[e] = tile[(e / m) * ld + e % m];
+            for (int r = 0; r < nl; ++r)
+                for (int k = tid; k < m; k += 32) d[(int64_t)r * m + k] = tile[r * ld + k];
         }
         __syncwarp();
     }
@@ -204,11 +234,8 @@ __global__ void k_solve_rows(Tw* x, int64_t lines, int64_t m, const Tw* __restri
 // -- recomposition fill ------------------------------------------------------
 template <typename T>
 __global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level<T> lv) {
-    const int64_t N = prod4(lv.n);
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i[4];
-        unravel4(lin, lv.n, i);
+    FOR_NODES(lv.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
         int64_t j0[4], j1[4];
         T w0[4], w1[4];
         int nc[4];
@@ -221,7 +248,7 @@ __global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level
             w0[a] = T(1);
             w1[a] = T(0);
             if (!fc) continue;
-            int c = fc[i[a]];
+            const int c = fc[i[a]];
             if (c >= 0) {
                 j0[a] = c;
             } else {
@@ -233,6 +260,7 @@ __global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level
                 nc[a] = 2;
             }
         }
+        const int64_t lin = ravel4(i, lv.n);
         if (allc) {
             out[lin] = coarse[ravel4(j0, lv.nc)];
             continue;
@@ -242,10 +270,10 @@ __global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level
             for (int c1 = 0; c1 < nc[1]; ++c1)
                 for (int c2 = 0; c2 < nc[2]; ++c2)
                     for (int c3 = 0; c3 < nc[3]; ++c3) {
-                        int64_t q[4] = {c0 ? j1[0] : j0[0], c1 ? j1[1] : j0[1],
-                                        c2 ? j1[2] : j0[2], c3 ? j1[3] : j0[3]};
-                        T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
-                              (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
+                        const int64_t q[4] = {c0 ? j1[0] : j0[0], c1 ? j1[1] : j0[1],
+                                              c2 ? j1[2] : j0[2], c3 ? j1[3] : j0[3]};
+                        const T w = (c0 ? w1[0] : w0[0]) * (c1 ? w1[1] : w0[1]) *
+                                    (c2 ? w1[2] : w0[2]) * (c3 ? w1[3] : w0[3]);
                         acc += w * coarse[ravel4(q, lv.nc)];
                     }
         out[lin] = zin[lin] + acc;
@@ -256,11 +284,8 @@ __global__ void k_fill(const T* zin, const T* __restrict__ coarse, T* out, Level
 template <typename T, bool kScatter>
 __global__ void k_layout(T* compact, T* data, LevelIndex li, Level<T> lv, int has_tables,
                          Shape4 fine) {
-    const int64_t N = prod4(li.n);
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i[4];
-        unravel4(lin, li.n, i);
+    FOR_NODES(li.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
         if (has_tables) {
             bool allc = true;
 #pragma unroll
@@ -272,6 +297,7 @@ __global__ void k_layout(T* compact, T* data, LevelIndex li, Level<T> lv, int ha
 #pragma unroll
         for (int a = 0; a < 4; ++a) q[a] = li.pos[a][i[a]];
         const int64_t g = ravel4(q, fine.n);
+        const int64_t lin = ravel4(i, li.n);
         if (kScatter) data[g] = compact[lin];
         else compact[lin] = data[g];
     }
@@ -314,12 +340,9 @@ __global__ void k_maxabs(const T* __restrict__ a, const T* __restrict__ b, int64
 // sum_i u_i (M u)_i with the tensor mass matrix of a level (3^D stencil).
 template <typename T>
 __global__ void k_mass_norm(const T* __restrict__ u, Level<T> lv, double* partial) {
-    const int64_t N = prod4(lv.n);
     double s = 0.0;
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i[4];
-        unravel4(lin, lv.n, i);
+    FOR_NODES(lv.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
         double f[4][3];
         int lo[4], hi[4];
 #pragma unroll
@@ -343,20 +366,21 @@ __global__ void k_mass_norm(const T* __restrict__ u, Level<T> lv, double* partia
             for (int o1 = lo[1]; o1 <= hi[1]; ++o1)
                 for (int o2 = lo[2]; o2 <= hi[2]; ++o2)
                     for (int o3 = lo[3]; o3 <= hi[3]; ++o3) {
-                        int64_t q[4] = {i[0] + o0, i[1] + o1, i[2] + o2, i[3] + o3};
+                        const int64_t q[4] = {i[0] + o0, i[1] + o1, i[2] + o2, i[3] + o3};
                         mu += f[0][o0 + 1] * f[1][o1 + 1] * f[2][o2 + 1] * f[3][o3 + 1] *
                               (double)u[ravel4(q, lv.n)];
                     }
-        s += (double)u[lin] * mu;
+        s += (double)u[ravel4(i, lv.n)] * mu;
     }
     __shared__ double sh[RED_THREADS];
-    sh[threadIdx.x] = s;
+    const int t = threadIdx.x;
+    sh[t] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        if (t < o) sh[t] += sh[t + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+    if (t == 0) partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sh[0];
 }
 
 int max_dyn_smem() {
@@ -387,12 +411,22 @@ mgard_status solve_axis(Tw* x, Shape4 s, int a, const Tw* sub, const Tw* inv, co
                 attr_set = true;
             }
             int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
-            MGB_LAUNCH("k_solve_rows", st, k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, m, sub, inv, cp, dst, sign));
+            MGB_LAUNCH("k_solve_rows", st,
+                       k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, (int)m, sub, inv,
+                                                                      cp, dst, sign));
             MGB_CUDA(cudaGetLastError());
             return MGARD_OK;
         }
     }
-    MGB_LAUNCH("k_solve_lines", st, k_solve_lines<Tw, Tdst><<<grid_for(lines, 128), 128, 0, st>>>(x, s, a, sub, inv, cp, dst, sign));
+    int64_t stride = 1, outer = 1;
+    for (int b = a + 1; b < 4; ++b) stride *= s.n[b];
+    for (int b = 0; b < a; ++b) outer *= s.n[b];
+    const int bx = 128;
+    dim3 grid((unsigned)std::min<int64_t>((stride + bx - 1) / bx, 1LL << 30),
+              (unsigned)std::min<int64_t>(outer, 65535), 1);
+    MGB_LAUNCH("k_solve_lines", st,
+               k_solve_lines<Tw, Tdst><<<grid, bx, 0, st>>>(x, outer, m, stride, sub, inv, cp, dst,
+                                                            sign));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -419,14 +453,13 @@ mgard_status correct_level(const Plan& p, int l, const T* z, T* coarse, void* t0
         if (!lt.ax[a].fcls) continue;
         Shape4 so = s;
         so.n[a] = lt.nc[a];
-        const int64_t nout = shape_prod(so);
         Tw* out = bufs[which];
         if (first)
-            MGB_LAUNCH("k_restrict", st, k_restrict<T, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
-                (const T*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], mask));
+            MGB_LAUNCH("k_restrict", st, k_restrict<T, Tw><<<grid3(so.n, 128), 128, 0, st>>>(
+                (const T*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, so, mask));
         else
-            MGB_LAUNCH("k_restrict", st, k_restrict<Tw, Tw><<<grid_for(nout, 256), 256, 0, st>>>(
-                (const Tw*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, lt.nc[a], nomask));
+            MGB_LAUNCH("k_restrict", st, k_restrict<Tw, Tw><<<grid3(so.n, 128), 128, 0, st>>>(
+                (const Tw*)cur, out, s, a, lw.ax[a].rf, lw.ax[a].rw, so, nomask));
         MGB_CUDA(cudaGetLastError());
         first = false;
         s = so;
@@ -488,16 +521,18 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
 
 template <typename T>
 mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st) {
-    DevBuf part;
-    MGB_TRY(part.alloc(RED_BLOCKS * sizeof(double), st));
     const Level<T>& lv = p.level<T>(l);   // holds the mass tables of level l
-    MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(u, lv, part.as<double>()));
+    const dim3 g = grid3(lv.n, RED_THREADS, 8, 74);   // fixed grid: deterministic partial sums
+    const size_t nb = (size_t)g.x * g.y * g.z;
+    DevBuf part;
+    MGB_TRY(part.alloc(nb * sizeof(double), st));
+    MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<g, RED_THREADS, 0, st>>>(u, lv, part.as<double>()));
     MGB_CUDA(cudaGetLastError());
-    double h[RED_BLOCKS];
-    MGB_CUDA(cudaMemcpyAsync(h, part.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    std::vector<double> h(nb);
+    MGB_CUDA(cudaMemcpyAsync(h.data(), part.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     double s = 0.0;
-    for (int i = 0; i < RED_BLOCKS; ++i) s += h[i];
+    for (size_t i = 0; i < nb; ++i) s += h[i];
     *out = s;
     return MGARD_OK;
 }
@@ -537,7 +572,7 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         const T* src = l == p.L ? in : py.lv[l];
         T* dst = l == p.L ? top : py.lv[l];
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
-        MGB_LAUNCH("k_coeff_gather", st, k_coeff_gather<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(src, dst, py.lv[l - 1],
+        MGB_LAUNCH("k_coeff_gather", st, k_coeff_gather<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(src, dst, py.lv[l - 1],
                                                                           p.level<T>(l)));
         MGB_CUDA(cudaGetLastError());
         MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
@@ -558,7 +593,7 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
         const T* z = l == p.L ? top : py.lv[l];
         T* dst = l == p.L ? out : py.lv[l];
         MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st));
-        MGB_LAUNCH("k_fill", st, k_fill<T><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(z, py.lv[l - 1], dst,
+        MGB_LAUNCH("k_fill", st, k_fill<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(z, py.lv[l - 1], dst,
                                                                   p.level<T>(l)));
         MGB_CUDA(cudaGetLastError());
     }
@@ -570,7 +605,7 @@ mgard_status scatter_levels(const Plan& p, const Pyramid<T>& py, T* data, cudaSt
     Shape4 fine;
     for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
     for (int l = 0; l < p.L; ++l) {
-        MGB_LAUNCH("k_layout", st, k_layout<T, true><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+        MGB_LAUNCH("k_layout", st, k_layout<T, true><<<grid3(p.lidx[l].n, 128), 128, 0, st>>>(
             py.lv[l], data, p.lidx[l], p.level<T>(l), l > 0 ? 1 : 0, fine));
         MGB_CUDA(cudaGetLastError());
     }
@@ -582,7 +617,7 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
     Shape4 fine;
     for (int a = 0; a < 4; ++a) fine.n[a] = p.n4[a];
     for (int l = 0; l < p.L; ++l) {
-        MGB_LAUNCH("k_layout", st, k_layout<T, false><<<grid_for(p.level_size(l), 256), 256, 0, st>>>(
+        MGB_LAUNCH("k_layout", st, k_layout<T, false><<<grid3(p.lidx[l].n, 128), 128, 0, st>>>(
             py.lv[l], (T*)data, p.lidx[l], p.level<T>(l), 0, fine));
         MGB_CUDA(cudaGetLastError());
     }

@@ -13,7 +13,7 @@ namespace {
 
 struct QLevel {
     int64_t n[4];           // level grid shape
-    int64_t nc[4];          // coarse grid shape (rank computation)
+    int64_t tail[4];        // prod_{b > a} of the coarse extents (rank computation)
     const int* fcls[4];     // level tables (null: inactive axis or level 0)
     const int* cbefore[4];
     const int64_t* pos[4];  // finest positions (in-place layout); null for compact
@@ -30,22 +30,19 @@ struct NodeInfo {
 
 // Position of a level-l node among the nodes new on level l (row-major):
 // its linear index minus the number of coarse-grid nodes before it.
-__device__ inline NodeInfo node_info(const QLevel& q, int64_t lin) {
-    int64_t i[4];
-    unravel4(lin, q.n, i);
+__device__ inline NodeInfo node_info(const QLevel& q, const int64_t* i) {
     NodeInfo r;
+    const int64_t lin = ravel4(i, q.n);
     r.skip = false;
     r.rank = lin;
     if (q.tables) {
         bool prefix = true;   // all axes before the current one are coarse
         int64_t cnt = 0;
-        int64_t tail = q.nc[1] * q.nc[2] * q.nc[3];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            if (a > 0) tail /= q.nc[a];
             const int* fc = q.fcls[a];
             if (!fc) continue;
-            if (prefix) cnt += (int64_t)q.cbefore[a][i[a]] * tail;
+            if (prefix) cnt += (int64_t)q.cbefore[a][i[a]] * q.tail[a];
             if (fc[i[a]] < 0) prefix = false;
         }
         r.skip = prefix;   // a node of the coarser grid
@@ -108,7 +105,7 @@ __device__ inline void quantize_value(double c, double /*inv_w*/, double w, int&
     }
 }
 
-constexpr int QT = 256;
+constexpr int QT = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel q, T inv_w,
@@ -119,27 +116,31 @@ __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel
     __shared__ unsigned sh[DICT];
     for (int k = threadIdx.x; k < DICT; k += blockDim.x) sh[k] = 0;
     __syncthreads();
-    const int64_t N = prod4(q.n);
     const int lane = threadIdx.x & 31;
     unsigned st = 0;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < N;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lin = base + threadIdx.x;
-        int s = -1;
-        if (lin < N) {
-            NodeInfo ni = node_info(q, lin);
-            if (!ni.skip) {
-                int32_t qo = 0;
-                quantize_value(c[ni.addr], inv_w, w, s, qo, st);
-                const int64_t p = q.sym_off + ni.rank;
-                sym[p] = (uint16_t)s;
-                if (s == MGARD_ESC) esc[p] = qo;
+    // every loop bound is uniform across the block, so whole warps reach the
+    // warp-aggregated histogram update together
+    for (int64_t z = blockIdx.z; z < q.n[0] * q.n[1]; z += gridDim.z)
+        for (int64_t y = blockIdx.y, i0 = z / q.n[1], i1 = z - i0 * q.n[1]; y < q.n[2];
+             y += gridDim.y)
+            for (int64_t xb = blockIdx.x * (int64_t)blockDim.x; xb < q.n[3];
+                 xb += (int64_t)gridDim.x * blockDim.x) {
+                const int64_t x = xb + threadIdx.x;
+                int s = -1;
+                if (x < q.n[3]) {
+                    const int64_t i[4] = {i0, i1, y, x};
+                    const NodeInfo ni = node_info(q, i);
+                    if (!ni.skip) {
+                        int32_t qo = 0;
+                        quantize_value(c[ni.addr], inv_w, w, s, qo, st);
+                        const int64_t p = q.sym_off + ni.rank;
+                        sym[p] = (uint16_t)s;
+                        if (s == MGARD_ESC) esc[p] = qo;
+                    }
+                }
+                const unsigned grp = __match_any_sync(0xffffffffu, s);
+                if (s >= 0 && lane == __ffs(grp) - 1) atomicAdd(&sh[s], (unsigned)__popc(grp));
             }
-        }
-        // warp-aggregated histogram update: one shared atomic per distinct symbol
-        const unsigned grp = __match_any_sync(0xffffffffu, s);
-        if (s >= 0 && lane == __ffs(grp) - 1) atomicAdd(&sh[s], (unsigned)__popc(grp));
-    }
     __syncthreads();
     for (int k = threadIdx.x; k < DICT; k += blockDim.x)
         if (sh[k]) atomicAdd(&hist[k], (unsigned long long)sh[k]);
@@ -149,10 +150,9 @@ __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel
 template <typename T>
 __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
                              QLevel q, T wt, double w, T* __restrict__ c) {
-    const int64_t N = prod4(q.n);
-    for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        NodeInfo ni = node_info(q, lin);
+    FOR_NODES(q.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
+        const NodeInfo ni = node_info(q, i);
         if (ni.skip) {
             if (!q.pos[0]) c[ni.addr] = T(0);   // compact level array: z = 0 on coarse nodes
             continue;
@@ -169,9 +169,12 @@ __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __
 
 QLevel make_qlevel(const Plan& p, int l, bool inplace) {
     QLevel q{};
+    int64_t nc[4];
+    for (int a = 0; a < 4; ++a) nc[a] = l > 0 ? p.shape[l - 1][a] : p.shape[l][a];
     for (int a = 0; a < 4; ++a) {
         q.n[a] = p.shape[l][a];
-        q.nc[a] = l > 0 ? p.shape[l - 1][a] : p.shape[l][a];
+        q.tail[a] = 1;
+        for (int b = a + 1; b < 4; ++b) q.tail[a] *= nc[b];
         q.fine[a] = p.n4[a];
         q.pos[a] = inplace ? p.lidx[l].pos[a] : nullptr;
         if (l > 0) {
@@ -192,8 +195,7 @@ mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, doub
                             unsigned* status, cudaStream_t st) {
     QLevel q = make_qlevel(p, l, inplace);
     const T inv_w = (T)(1.0 / w);
-    const int64_t N = p.level_size(l);
-    MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid_for(N, QT, 148LL * 8), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status));
+    MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -202,8 +204,7 @@ template <typename T>
 mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               bool inplace, double w, T* c, cudaStream_t st) {
     QLevel q = make_qlevel(p, l, inplace);
-    const int64_t N = p.level_size(l);
-    MGB_LAUNCH("k_dequantize", st, k_dequantize<T><<<grid_for(N, 256), 256, 0, st>>>(sym, esc, q, (T)w, w, c));
+    MGB_LAUNCH("k_dequantize", st, k_dequantize<T><<<grid3(q.n, 128), 128, 0, st>>>(sym, esc, q, (T)w, w, c));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }

@@ -80,9 +80,10 @@ size_t mgard_timing_report(char* buf, size_t cap) {
                       kv.second.second);
         out += line;
     }
+    if (!buf) return out.size() + 1;   // size query: keep the records
     g_recs.clear();
     g_used = 0;
-    if (buf && cap) {
+    if (cap) {
         size_t n = std::min(cap - 1, out.size());
         std::memcpy(buf, out.data(), n);
         buf[n] = 0;
