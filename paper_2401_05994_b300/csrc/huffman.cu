@@ -81,29 +81,40 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
             if (tid == 0) lengths[S.keys[0] & 0xFFF] = 1;
             return;
         }
-        // two-queue merge (serial): leaves 0..n-1, internal nodes n..2n-2
+        // two-queue merge (serial): leaves 0..n-1, internal nodes n..2n-2.  The
+        // next two heads of both queues live in registers and the shared-memory
+        // loads behind them are issued a selection ahead of their use.
         if (tid == 0) {
-            int li = 0, ii = 0, nint = 0;
             const unsigned long long INF = ~0ull;
+            int li = 0, ii = 0, nint = 0;
+            unsigned long long L0 = S.keys[0] >> 12, L1 = n > 1 ? S.keys[1] >> 12 : INF;
+            unsigned long long I0 = INF, I1 = INF;
             for (int k = 0; k < n - 1; ++k) {
                 int ids[2];
                 unsigned long long ws[2];
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const unsigned long long wl = li < n ? (S.keys[li] >> 12) : INF;
-                    const unsigned long long wi = ii < nint ? S.iw[ii] : INF;
-                    if (wl <= wi) {
-                        ids[t] = li++;
-                        ws[t] = wl;
+                    if (L0 <= I0) {
+                        ids[t] = li;
+                        ws[t] = L0;
+                        ++li;
+                        L0 = L1;
+                        L1 = li + 1 < n ? S.keys[li + 1] >> 12 : INF;
                     } else {
-                        ids[t] = n + ii++;
-                        ws[t] = wi;
+                        ids[t] = n + ii;
+                        ws[t] = I0;
+                        ++ii;
+                        I0 = I1;
+                        I1 = ii + 1 < nint ? S.iw[ii + 1] : INF;
                     }
                 }
-                S.iw[nint] = ws[0] + ws[1];
+                const unsigned long long wnew = ws[0] + ws[1];
+                S.iw[nint] = wnew;
                 S.parent[ids[0]] = (short)(n + nint);
                 S.parent[ids[1]] = (short)(n + nint);
                 ++nint;
+                if (nint - ii == 1) I0 = wnew;
+                else if (nint - ii == 2) I1 = wnew;
             }
         }
         __syncthreads();
@@ -147,33 +158,35 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
                                                        uint32_t* __restrict__ codes,
                                                        DecodeTables* __restrict__ dt) {
     __shared__ unsigned long long keys[DICT];
+    __shared__ unsigned wcnt[CB_THREADS / 32][LMAX + 2];   // per-warp length counts
     __shared__ unsigned cnt[LMAX + 2];
     __shared__ unsigned long long fc[LMAX + 2];
     __shared__ unsigned fi[LMAX + 2];
-    __shared__ unsigned long long kraft;
     __shared__ int bad;
-    const int tid = threadIdx.x;
-    if (tid < LMAX + 2) cnt[tid] = 0;
-    if (tid == 0) {
-        kraft = 0;
-        bad = 0;
-    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k < (CB_THREADS / 32) * (LMAX + 2); k += blockDim.x) (&wcnt[0][0])[k] = 0;
+    if (tid == 0) bad = 0;
     __syncthreads();
     for (int s = tid; s < DICT; s += blockDim.x) {
         const unsigned len = lengths[s];
         if (len > LMAX) bad = 1;
-        if (len && len <= LMAX) {
-            atomicAdd(&cnt[len], 1u);
-            atomicAdd(&kraft, 1ull << (LMAX - len));
-            keys[s] = ((unsigned long long)len << 12) | (unsigned)s;
-        } else {
-            keys[s] = KEY_NONE;
-        }
+        const bool ok = len && len <= LMAX;
+        keys[s] = ok ? (((unsigned long long)len << 12) | (unsigned)s) : KEY_NONE;
+        // one shared update per distinct length in the warp
+        const unsigned grp = __match_any_sync(0xffffffffu, ok ? (int)len : -1);
+        if (ok && lane == __ffs(grp) - 1) wcnt[warp][len] += __popc(grp);
+    }
+    __syncthreads();
+    if (tid < LMAX + 2) {
+        unsigned c = 0;
+        for (int w = 0; w < CB_THREADS / 32; ++w) c += wcnt[w][tid];
+        cnt[tid] = c;
     }
     __syncthreads();
     if (tid == 0) {
-        unsigned long long code = 0;
+        unsigned long long code = 0, kraft = 0;
         unsigned idx = 0, maxlen = 0;
+        for (int l = 1; l <= LMAX; ++l) kraft += (unsigned long long)cnt[l] << (LMAX - l);
         for (int l = 1; l <= LMAX; ++l) {
             fc[l] = code;
             fi[l] = idx;
@@ -259,40 +272,126 @@ __global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
     if (nocode) atomicOr(status, ST_NOCODE);
 }
 
-// Exclusive scan of two arrays in place (one CTA); totals[0..1] = sums.
-__global__ void __launch_bounds__(1024) k_scan2(uint64_t* a, uint64_t* b, uint64_t n,
-                                                unsigned long long* totals) {
-    __shared__ unsigned long long sa[1024], sb[1024];
-    const int t = threadIdx.x;
-    const uint64_t seg = (n + 1023) / 1024;
-    const uint64_t lo = min(n, (uint64_t)t * seg), hi = min(n, lo + seg);
-    unsigned long long xa = 0, xb = 0;
-    for (uint64_t i = lo; i < hi; ++i) {
-        xa += a[i];
-        xb += b[i];
+// Exclusive scan of two arrays in place, in three phases: per-tile sums,
+// a scan of the tile sums (one CTA), and per-tile scans with the carry.
+constexpr int SCAN_T = 1024;            // threads per tile block
+constexpr int SCAN_TILE = SCAN_T * 4;   // elements per tile
+
+__device__ inline void block_scan2(unsigned long long& a, unsigned long long& b,
+                                   unsigned long long* sa, unsigned long long* sb) {
+    // inclusive scan of (a, b) across the block; returns inclusive values
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long va = __shfl_up_sync(0xffffffffu, a, o);
+        const unsigned long long vb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) {
+            a += va;
+            b += vb;
+        }
     }
-    sa[t] = xa;
-    sb[t] = xb;
+    if (lane == 31) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned long long va = t >= o ? sa[t - o] : 0, vb = t >= o ? sb[t - o] : 0;
+    if (warp == 0) {
+        const int nw = blockDim.x / 32;
+        unsigned long long xa = lane < nw ? sa[lane] : 0, xb = lane < nw ? sb[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long va = __shfl_up_sync(0xffffffffu, xa, o);
+            const unsigned long long vb = __shfl_up_sync(0xffffffffu, xb, o);
+            if (lane >= o) {
+                xa += va;
+                xb += vb;
+            }
+        }
+        if (lane < nw) {
+            sa[lane] = xa;
+            sb[lane] = xb;
+        }
+    }
+    __syncthreads();
+    if (warp > 0) {
+        a += sa[warp - 1];
+        b += sb[warp - 1];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(const uint64_t* __restrict__ a,
+                                                      const uint64_t* __restrict__ b, uint64_t n,
+                                                      unsigned long long* tsum) {
+    __shared__ unsigned long long sa[32], sb[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    unsigned long long xa = 0, xb = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) {
+            xa += a[base + k];
+            xb += b[base + k];
+        }
+    block_scan2(xa, xb, sa, sb);
+    if (threadIdx.x == blockDim.x - 1) {
+        tsum[2 * blockIdx.x] = xa;
+        tsum[2 * blockIdx.x + 1] = xb;
+    }
+}
+
+// Scan of the tile sums (exclusive, in place); totals[0..1] = grand totals.
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(unsigned long long* tsum, uint64_t ntiles,
+                                                       unsigned long long* totals) {
+    __shared__ unsigned long long sa[32], sb[32];
+    unsigned long long carry_a = 0, carry_b = 0;
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += SCAN_T) {
+        const uint64_t t = t0 + threadIdx.x;
+        const unsigned long long xa = t < ntiles ? tsum[2 * t] : 0, xb = t < ntiles ? tsum[2 * t + 1] : 0;
+        unsigned long long ia = xa, ib = xb;
+        block_scan2(ia, ib, sa, sb);
+        if (t < ntiles) {
+            tsum[2 * t] = carry_a + ia - xa;
+            tsum[2 * t + 1] = carry_b + ib - xb;
+        }
+        __shared__ unsigned long long last[2];
+        if (threadIdx.x == blockDim.x - 1) {
+            last[0] = ia;
+            last[1] = ib;
+        }
         __syncthreads();
-        sa[t] += va;
-        sb[t] += vb;
+        carry_a += last[0];
+        carry_b += last[1];
         __syncthreads();
     }
-    unsigned long long ra = sa[t] - xa, rb = sb[t] - xb;   // exclusive prefix of segment
-    for (uint64_t i = lo; i < hi; ++i) {
-        const unsigned long long va = a[i], vb = b[i];
-        a[i] = ra;
-        b[i] = rb;
-        ra += va;
-        rb += vb;
+    if (threadIdx.x == 0) {
+        totals[0] = carry_a;
+        totals[1] = carry_b;
     }
-    if (t == 1023) {
-        totals[0] = sa[1023];
-        totals[1] = sb[1023];
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint64_t* a, uint64_t* b, uint64_t n,
+                                                       const unsigned long long* tsum) {
+    __shared__ unsigned long long sa[32], sb[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    unsigned long long va[4], vb[4], xa = 0, xb = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        va[k] = base + k < n ? a[base + k] : 0;
+        vb[k] = base + k < n ? b[base + k] : 0;
+        xa += va[k];
+        xb += vb[k];
     }
+    unsigned long long ia = xa, ib = xb;
+    block_scan2(ia, ib, sa, sb);
+    unsigned long long ra = tsum[2 * blockIdx.x] + ia - xa, rb = tsum[2 * blockIdx.x + 1] + ib - xb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) {
+            a[base + k] = ra;
+            b[base + k] = rb;
+            ra += va[k];
+            rb += vb[k];
+        }
 }
 
 constexpr int PACK_WARPS = 4;
@@ -355,18 +454,32 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         for (unsigned k = lane; k <= nw && k <= CHUNK; k += 32) wb[k] = 0;
         __syncwarp();
         const uint64_t eo = esc_off[c];
+        // bits accumulate MSB-first in a 64-bit register; a word shared with a
+        // neighbouring lane (the first and the last one) is merged with an OR
+        {
+            unsigned w = bpos >> 5;
+            int nb = (int)(bpos & 31);      // bits of the current word already owned by the left lane
+            unsigned long long acc = 0;
+            bool first = true;
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < cnt) {
-                const unsigned s = s_loc[k], len = len_s[s];
-                const unsigned w = bpos >> 5, b = bpos & 31;
-                const unsigned long long v = (unsigned long long)code_s[s] << (64 - len - b);
-                atomicOr(&wb[w], (uint32_t)(v >> 32));
-                const uint32_t lo = (uint32_t)v;
-                if (lo) atomicOr(&wb[w + 1], lo);
-                bpos += len;
-                if (s == MGARD_ESC) outliers[eo + epos++] = escapes[base + k];
-            }
+            for (int k = 0; k < 32; ++k)
+                if (k < cnt) {
+                    const unsigned s = s_loc[k], len = len_s[s];
+                    acc = (acc << len) | code_s[s];
+                    nb += (int)len;
+                    if (nb >= 32) {
+                        const uint32_t word = (uint32_t)(acc >> (nb - 32));
+                        if (first) atomicOr(&wb[w], word);
+                        else wb[w] = word;
+                        first = false;
+                        ++w;
+                        nb -= 32;
+                        acc &= (nb ? ((1ull << nb) - 1) : 0ull);
+                    }
+                    if (s == MGARD_ESC) outliers[eo + epos++] = escapes[base + k];
+                }
+            if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
+        }
         __syncwarp();
         const uint64_t wo = word_off[c];
         for (unsigned k = lane; k < nw; k += 32) words[wo + k] = wb[k];
@@ -408,6 +521,9 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
     auto load = [&](uint64_t k) -> uint64_t { return k < end ? (uint64_t)words[k] : 0ull; };
     uint64_t wi = start;
     uint64_t win = (load(wi) << 32) | load(wi + 1);
+    // the next four words are loaded ahead of use
+    uint32_t q0 = (uint32_t)load(wi + 2), q1 = (uint32_t)load(wi + 3), q2 = (uint32_t)load(wi + 4),
+             q3 = (uint32_t)load(wi + 5);
     unsigned off = 0;
     uint64_t bit = start * 32;
     const uint64_t endbit = end * 32;
@@ -446,7 +562,11 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
         off += len;
         if (off >= 32) {
             ++wi;
-            win = (win << 32) | load(wi + 1);
+            win = (win << 32) | q0;
+            q0 = q1;
+            q1 = q2;
+            q2 = q3;
+            q3 = (uint32_t)load(wi + 5);
             off -= 32;
         }
         if (s == MGARD_ESC) {
@@ -507,8 +627,18 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
             sym, n, lengths, word_off, esc_off, nchunks, status));
         MGB_CUDA(cudaGetLastError());
     }
-    MGB_LAUNCH("k_scan2", st, k_scan2<<<1, 1024, 0, st>>>(word_off, esc_off, nchunks, totals));
+    const uint64_t ntiles = (nchunks + SCAN_TILE - 1) / SCAN_TILE;
+    unsigned long long* tsum = nullptr;
+    MGB_CUDA(cudaMallocAsync((void**)&tsum, 16 * (ntiles + 1), st));
+    if (ntiles) {
+        MGB_LAUNCH("k_scan_sums", st, k_scan_sums<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, tsum));
+    }
+    MGB_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<1, SCAN_T, 0, st>>>(tsum, ntiles, totals));
+    if (ntiles) {
+        MGB_LAUNCH("k_scan_apply", st, k_scan_apply<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, tsum));
+    }
     MGB_CUDA(cudaGetLastError());
+    MGB_CUDA(cudaFreeAsync(tsum, st));
     return MGARD_OK;
 }
 

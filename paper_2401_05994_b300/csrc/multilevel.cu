@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "multilevel.cuh"
+#include "rows3.cuh"
 
 namespace mgb {
 
@@ -315,16 +316,28 @@ __global__ void k_difference(const T* __restrict__ a, const T* __restrict__ b,
 constexpr int RED_BLOCKS = 592;
 constexpr int RED_THREADS = 256;
 
+// max |a| (b == null, exact in the data's precision) or max |b - a| (in FP64).
 template <typename T>
 __global__ void k_maxabs(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
                          double* partial, unsigned* status) {
-    double m = 0.0;
     bool bad = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double v = b ? (double)b[i] - (double)a[i] : (double)a[i];
-        if (!isfinite(v)) bad = true;
-        m = fmax(m, fabs(v));
+    double m = 0.0;
+    if (!b) {
+        T mt = T(0);
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const T v = a[i];
+            if (!isfinite(v)) bad = true;
+            mt = fmax(mt, fabs(v));
+        }
+        m = (double)mt;
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double v = (double)b[i] - (double)a[i];
+            if (!isfinite(v)) bad = true;
+            m = fmax(m, fabs(v));
+        }
     }
     __shared__ double sh[RED_THREADS];
     sh[threadIdx.x] = m;
@@ -398,37 +411,11 @@ template <typename Tw, typename Tdst>
 mgard_status solve_axis(Tw* x, Shape4 s, int a, const Tw* sub, const Tw* inv, const Tw* cp,
                         Tdst* dst, Tw sign, cudaStream_t st) {
     const int64_t m = s.n[a];
-    const int64_t lines = shape_prod(s) / m;
-    if (a == 3) {
-        const size_t smem = 32 * (size_t)(m + 1) * sizeof(Tw);
-        const size_t cap = std::min<size_t>((size_t)max_dyn_smem(), 200 * 1024);
-        if (smem <= cap) {
-            static bool attr_set = false;
-            if (!attr_set) {
-                MGB_CUDA(cudaFuncSetAttribute(k_solve_rows<Tw, Tdst>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)cap));
-                attr_set = true;
-            }
-            int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
-            MGB_LAUNCH("k_solve_rows", st,
-                       k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, (int)m, sub, inv,
-                                                                      cp, dst, sign));
-            MGB_CUDA(cudaGetLastError());
-            return MGARD_OK;
-        }
-    }
+    if (a == 3) return solve_contiguous<Tw, Tdst>(x, shape_prod(s) / m, m, sub, inv, cp, dst, sign, st);
     int64_t stride = 1, outer = 1;
     for (int b = a + 1; b < 4; ++b) stride *= s.n[b];
     for (int b = 0; b < a; ++b) outer *= s.n[b];
-    const int bx = 128;
-    dim3 grid((unsigned)std::min<int64_t>((stride + bx - 1) / bx, 1LL << 30),
-              (unsigned)std::min<int64_t>(outer, 65535), 1);
-    MGB_LAUNCH("k_solve_lines", st,
-               k_solve_lines<Tw, Tdst><<<grid, bx, 0, st>>>(x, outer, m, stride, sub, inv, cp, dst,
-                                                            sign));
-    MGB_CUDA(cudaGetLastError());
-    return MGARD_OK;
+    return solve_strided<Tw, Tdst>(x, outer, m, stride, sub, inv, cp, dst, sign, st);
 }
 
 // Steps 2-4 for one level: coarse += sign * M_{l-1}^{-1} P^T M_l z, with z
@@ -486,11 +473,52 @@ bool level_uses_fp64(const Plan& p, int l) {
 template <typename T>
 mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1, T sign,
                      cudaStream_t st) {
-    if (level_uses_fp64<T>(p, l)) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
+    const bool f64 = level_uses_fp64<T>(p, l);
+    if (rows3_ok(p)) {
+        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st);
+        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st);
+    }
+    if (f64) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
     return correct_level<T, T>(p, l, z, coarse, t0, t1, sign, st);
 }
 
 }  // namespace
+
+template <typename Tw, typename Tdst>
+mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
+                           const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
+    const int bx = 128;
+    dim3 grid((unsigned)std::min<int64_t>((stride + bx - 1) / bx, 1LL << 30),
+              (unsigned)std::min<int64_t>(outer, 65535), 1);
+    MGB_LAUNCH("k_solve_lines", st,
+               k_solve_lines<Tw, Tdst><<<grid, bx, 0, st>>>(x, outer, m, stride, sub, inv, cp, dst,
+                                                            sign));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename Tw, typename Tdst>
+mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, const Tw* inv,
+                              const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
+    const size_t smem = 32 * (size_t)(m + 1) * sizeof(Tw);
+    const size_t cap = std::min<size_t>((size_t)max_dyn_smem(), 200 * 1024);
+    if (smem <= cap) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            MGB_CUDA(cudaFuncSetAttribute(k_solve_rows<Tw, Tdst>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+            attr_set = true;
+        }
+        const int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
+        MGB_LAUNCH("k_solve_rows", st,
+                   k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, (int)m, sub, inv, cp,
+                                                                  dst, sign));
+        MGB_CUDA(cudaGetLastError());
+        return MGARD_OK;
+    }
+    // lines too long for shared memory: one thread per line in global memory
+    return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
+}
 
 template <typename T>
 mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
@@ -572,9 +600,14 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         const T* src = l == p.L ? in : py.lv[l];
         T* dst = l == p.L ? top : py.lv[l];
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
-        MGB_LAUNCH("k_coeff_gather", st, k_coeff_gather<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(src, dst, py.lv[l - 1],
-                                                                          p.level<T>(l)));
-        MGB_CUDA(cudaGetLastError());
+        if (rows3_ok(p)) {
+            MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st));
+        } else {
+            MGB_LAUNCH("k_coeff_gather", st,
+                       k_coeff_gather<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(
+                           src, dst, py.lv[l - 1], p.level<T>(l)));
+            MGB_CUDA(cudaGetLastError());
+        }
         MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
     }
     if (E) MGB_TRY(mass_norm2<T>(p, 0, p.L ? py.lv[0] : in, &E[0], st));
@@ -593,9 +626,13 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
         const T* z = l == p.L ? top : py.lv[l];
         T* dst = l == p.L ? out : py.lv[l];
         MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st));
-        MGB_LAUNCH("k_fill", st, k_fill<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(z, py.lv[l - 1], dst,
-                                                                  p.level<T>(l)));
-        MGB_CUDA(cudaGetLastError());
+        if (rows3_ok(p)) {
+            MGB_TRY(rows3_fill<T>(p, l, z, py.lv[l - 1], dst, st));
+        } else {
+            MGB_LAUNCH("k_fill", st, k_fill<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(
+                                         z, py.lv[l - 1], dst, p.level<T>(l)));
+            MGB_CUDA(cudaGetLastError());
+        }
     }
     return MGARD_OK;
 }
@@ -639,5 +676,14 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
 INST(float)
 INST(double)
 #undef INST
+#define INST_SOLVE(Tw, Td)                                                                       \
+    template mgard_status solve_strided<Tw, Td>(Tw*, int64_t, int64_t, int64_t, const Tw*,       \
+                                                const Tw*, const Tw*, Td*, Tw, cudaStream_t);    \
+    template mgard_status solve_contiguous<Tw, Td>(Tw*, int64_t, int64_t, const Tw*, const Tw*,  \
+                                                   const Tw*, Td*, Tw, cudaStream_t);
+INST_SOLVE(float, float)
+INST_SOLVE(double, float)
+INST_SOLVE(double, double)
+#undef INST_SOLVE
 
 }  // namespace mgb

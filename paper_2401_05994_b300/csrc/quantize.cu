@@ -6,6 +6,7 @@
 // holding only the nodes new on that level.  |q| < DICT/2 maps to symbol
 // q + DICT/2; larger values escape to symbol 0 with q stored aside.
 #include "quantize.cuh"
+#include "rows3.cuh"
 
 namespace mgb {
 
@@ -193,6 +194,7 @@ template <typename T>
 mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, double w,
                             uint16_t* sym, int32_t* esc, unsigned long long* hist,
                             unsigned* status, cudaStream_t st) {
+    if (!inplace && rows3_ok(p)) return rows3_quantize<T>(p, l, c, w, sym, esc, hist, status, st);
     QLevel q = make_qlevel(p, l, inplace);
     const T inv_w = (T)(1.0 / w);
     MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status));
@@ -203,6 +205,7 @@ mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, doub
 template <typename T>
 mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               bool inplace, double w, T* c, cudaStream_t st) {
+    if (!inplace && rows3_ok(p)) return rows3_dequantize<T>(p, l, sym, esc, w, c, st);
     QLevel q = make_qlevel(p, l, inplace);
     MGB_LAUNCH("k_dequantize", st, k_dequantize<T><<<grid3(q.n, 128), 128, 0, st>>>(sym, esc, q, (T)w, w, c));
     MGB_CUDA(cudaGetLastError());

@@ -1,0 +1,466 @@
+// Row kernels for grids with at most three active axes (see rows3.cuh).
+//
+// Same mathematics as the generic 4D kernels in multilevel.cu and
+// quantize.cu (paper, "Software design": coefficients, load vector,
+// coarse solve, correction, level-wise quantization); only the work
+// decomposition differs.
+#include <algorithm>
+
+#include "rows3.cuh"
+
+namespace mgb {
+
+namespace {
+
+constexpr int RT = 256;              // threads per block (one x-row at a time)
+constexpr int64_t ROW_BLOCKS = 148 * 8;
+
+inline int row_grid(int64_t rows) { return (int)std::min<int64_t>(std::max<int64_t>(rows, 1), ROW_BLOCKS); }
+
+// Interpolation sources of one index along one axis.
+template <typename T>
+struct Src {
+    int p[2];     // fine positions (decomposition) or coarse indices (fill)
+    T w[2];
+    int n;        // 1 = coarse node, 2 = new node
+    int J;        // coarse index when n == 1
+};
+
+template <typename T>
+__device__ inline Src<T> sources(const AxisT<T>& ax, int i, bool coarse_index) {
+    Src<T> s;
+    if (!ax.fcls) {
+        s.p[0] = i; s.w[0] = T(1); s.n = 1; s.J = i;
+        return s;
+    }
+    const int c = ax.fcls[i];
+    if (c >= 0) {
+        s.p[0] = coarse_index ? c : i; s.w[0] = T(1); s.n = 1; s.J = c;
+    } else {
+        const int left = -c - 1;
+        s.p[0] = coarse_index ? left : ax.rf[left];
+        s.p[1] = coarse_index ? left + 1 : ax.rf[left + 1];
+        s.w[0] = ax.wl[i];
+        s.w[1] = ax.wr[i];
+        s.n = 2;
+        s.J = -1;
+    }
+    return s;
+}
+
+// -- coefficients (decomposition step 1) --------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
+                                               Level<T> lv) {
+    const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+    const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+    const AxisT<T> ax = lv.ax[3];
+    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
+        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+        const Src<T> sz = sources(lv.ax[1], z, false), sy = sources(lv.ax[2], y, false);
+        const T* rows[4];
+        T rw[4];
+        int nr = 0;
+        for (int a = 0; a < sz.n; ++a)
+            for (int b = 0; b < sy.n; ++b) {
+                rows[nr] = in + ((int64_t)sz.p[a] * ny + sy.p[b]) * nx;
+                rw[nr] = sz.w[a] * sy.w[b];
+                ++nr;
+            }
+        const bool rowc = sz.n == 1 && sy.n == 1;
+        const T* urow = in + r * nx;
+        T* orow = out + r * nx;
+        T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
+        for (int x = threadIdx.x; x < nx; x += RT) {
+            const T u = urow[x];
+            const int cx = ax.fcls ? ax.fcls[x] : 0;
+            T acc = T(0);
+            if (cx >= 0) {
+                if (rowc) {
+                    crow[cx] = u;
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nr) acc += rw[k] * rows[k][x];
+            } else {
+                const int left = -cx - 1;
+                const int xl = ax.rf[left], xr = ax.rf[left + 1];
+                const T wl = ax.wl[x], wr = ax.wr[x];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nr) acc += rw[k] * (wl * rows[k][xl] + wr * rows[k][xr]);
+            }
+            orow[x] = u - acc;
+        }
+    }
+}
+
+// -- recomposition fill ---------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
+                                              Level<T> lv) {
+    const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+    const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+    const AxisT<T> ax = lv.ax[3];
+    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
+        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+        const Src<T> sz = sources(lv.ax[1], z, true), sy = sources(lv.ax[2], y, true);
+        const T* rows[4];
+        T rw[4];
+        int nr = 0;
+        for (int a = 0; a < sz.n; ++a)
+            for (int b = 0; b < sy.n; ++b) {
+                rows[nr] = coarse + ((int64_t)sz.p[a] * ncy + sy.p[b]) * ncx;
+                rw[nr] = sz.w[a] * sy.w[b];
+                ++nr;
+            }
+        const bool rowc = sz.n == 1 && sy.n == 1;
+        const T* zrow = zin + r * nx;
+        T* orow = out + r * nx;
+        for (int x = threadIdx.x; x < nx; x += RT) {
+            const int cx = ax.fcls ? ax.fcls[x] : 0;
+            T acc = T(0);
+            if (cx >= 0) {
+                if (rowc) {
+                    orow[x] = rows[0][cx];
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nr) acc += rw[k] * rows[k][cx];
+            } else {
+                const int left = -cx - 1;
+                const T wl = ax.wl[x], wr = ax.wr[x];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nr) acc += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
+            }
+            orow[x] = zrow[x] + acc;
+        }
+    }
+}
+
+// -- restriction along x (first pass: z is zero on coarse nodes) -------------------
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
+                                                    Tout* __restrict__ out, int nz, int ny,
+                                                    int nx, int ncx, const int* __restrict__ rf,
+                                                    const Tout* __restrict__ rw, const int* fz,
+                                                    const int* fy, const int* fx) {
+    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
+        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+        const bool rowc = (!fz || fz[z] >= 0) && (!fy || fy[y] >= 0);
+        const Tin* irow = in + r * nx;
+        Tout* orow = out + r * ncx;
+        for (int J = threadIdx.x; J < ncx; J += RT) {
+            const int f = rf[J];
+            Tout acc = Tout(0);
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                const int ip = f - 2 + t;
+                if (ip < 0 || ip >= nx) continue;
+                if (rowc && fx[ip] >= 0) continue;   // coarse node: z = 0 (not read)
+                acc += rw[J * 5 + t] * (Tout)irow[ip];
+            }
+            orow[J] = acc;
+        }
+    }
+}
+
+// -- restriction along y or z: whole rows combined with per-row weights ----------
+// in: (nouter, m, inner) rows of `nx` elements; out: (nouter, mc, inner).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ in,
+                                                       Tout* __restrict__ out, int nouter, int m,
+                                                       int mc, int inner, int nx,
+                                                       const int* __restrict__ rf,
+                                                       const Tout* __restrict__ rw) {
+    // one output row = (o, J, i); rows of the input at (o, rf[J]-2+t, i)
+    for (int64_t r = blockIdx.x; r < (int64_t)nouter * mc * inner; r += gridDim.x) {
+        const int i = (int)(r % inner);
+        const int64_t oj = r / inner;
+        const int J = (int)(oj % mc);
+        const int o = (int)(oj / mc);
+        const int f = rf[J];
+        const Tin* src[5];
+        Tout w[5];
+        int ns = 0;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const int ip = f - 2 + t;
+            const Tout wt = rw[J * 5 + t];
+            if (ip < 0 || ip >= m || wt == Tout(0)) continue;
+            src[ns] = in + (((int64_t)o * m + ip) * inner + i) * nx;
+            w[ns] = wt;
+            ++ns;
+        }
+        Tout* orow = out + r * nx;
+        for (int x = threadIdx.x; x < nx; x += RT) {
+            Tout acc = Tout(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < ns) acc += w[k] * (Tout)src[k][x];
+            orow[x] = acc;
+        }
+    }
+}
+
+// -- quantization ------------------------------------------------------------------
+constexpr int HCOPIES = 2;
+
+template <typename T>
+__device__ inline void qvalue(T c, T inv_w, double w, int& sym, int32_t& qo, unsigned& st);
+
+template <>
+__device__ inline void qvalue<float>(float c, float inv_w, double w, int& sym, int32_t& qo,
+                                     unsigned& st) {
+    const float q = rintf(__fmul_rn(c, inv_w));
+    if (fabsf(q) < (float)RADIUS) {   // false for NaN and +-Inf
+        sym = (int)q + RADIUS;
+        return;
+    }
+    sym = MGARD_ESC;
+    qo = 0;
+    if (!isfinite(c)) {
+        st |= ST_NONFINITE;
+        return;
+    }
+    const double qd = rint((double)c / w);
+    if (fabs(qd) > 2147483647.0) st |= ST_RANGE;
+    else qo = (int32_t)qd;
+}
+
+template <>
+__device__ inline void qvalue<double>(double c, double, double w, int& sym, int32_t& qo,
+                                      unsigned& st) {
+    const double q = rint(c / w);
+    if (fabs(q) < (double)RADIUS) {
+        sym = (int)q + RADIUS;
+        return;
+    }
+    sym = MGARD_ESC;
+    qo = 0;
+    if (!isfinite(c)) {
+        st |= ST_NONFINITE;
+        return;
+    }
+    if (fabs(q) > 2147483647.0) st |= ST_RANGE;
+    else qo = (int32_t)q;
+}
+
+struct QRow {
+    int nz, ny, nx;
+    int64_t tail_z, tail_y;       // ncy*ncx and ncx
+    const int* fz; const int* fy; const int* fx;
+    const int* cbz; const int* cby; const int* cbx;
+    int64_t sym_off;
+    int tables;
+};
+
+// Per-row rank offset; returns whether the row lies in the coarse grid's
+// (z, y) prefix (then x nodes that are coarse are skipped).
+__device__ inline int64_t row_rank(const QRow& q, int z, int y, bool& rowc) {
+    if (!q.tables) {
+        rowc = false;
+        return 0;
+    }
+    const bool zc = !q.fz || q.fz[z] >= 0;
+    const bool yc = !q.fy || q.fy[y] >= 0;
+    int64_t cnt = 0;
+    if (q.fz) cnt += (int64_t)q.cbz[z] * q.tail_z;
+    if (zc && q.fy) cnt += (int64_t)q.cby[y] * q.tail_y;
+    rowc = zc && yc;
+    return cnt;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow q, T inv_w,
+                                                  double w, uint16_t* __restrict__ sym,
+                                                  int32_t* __restrict__ esc,
+                                                  unsigned long long* __restrict__ hist,
+                                                  unsigned* status) {
+    __shared__ unsigned sh[HCOPIES][DICT];
+    for (int k = threadIdx.x; k < HCOPIES * DICT; k += RT) (&sh[0][0])[k] = 0;
+    __syncthreads();
+    unsigned* my = sh[threadIdx.x & (HCOPIES - 1)];
+    unsigned center = 0;   // the most frequent symbol (q = 0) is counted in a register
+    unsigned st = 0;
+    for (int64_t r = blockIdx.x; r < (int64_t)q.nz * q.ny; r += gridDim.x) {
+        const int z = (int)(r / q.ny), y = (int)(r - (int64_t)z * q.ny);
+        bool rowc;
+        const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
+        const T* crow = c + r * q.nx;
+        for (int x = threadIdx.x; x < q.nx; x += RT) {
+            int64_t p = base + x;
+            if (rowc) {
+                const int cx = q.fx ? q.fx[x] : 0;
+                if (cx >= 0) continue;   // node of the coarser grid
+                p -= q.cbx[x];
+            }
+            int s;
+            int32_t qo;
+            qvalue<T>(crow[x], inv_w, w, s, qo, st);
+            sym[p] = (uint16_t)s;
+            if (s == MGARD_ESC) esc[p] = qo;
+            if (s == RADIUS) ++center;
+            else atomicAdd(&my[s], 1u);
+        }
+    }
+    if (center) atomicAdd(&sh[0][RADIUS], center);
+    __syncthreads();
+    for (int k = threadIdx.x; k < DICT; k += RT) {
+        unsigned v = 0;
+#pragma unroll
+        for (int h = 0; h < HCOPIES; ++h) v += sh[h][k];
+        if (v) atomicAdd(&hist[k], (unsigned long long)v);
+    }
+    if (st) atomicOr(status, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__ sym,
+                                                    const int32_t* __restrict__ esc, QRow q,
+                                                    T wt, double w, T* __restrict__ c) {
+    for (int64_t r = blockIdx.x; r < (int64_t)q.nz * q.ny; r += gridDim.x) {
+        const int z = (int)(r / q.ny), y = (int)(r - (int64_t)z * q.ny);
+        bool rowc;
+        const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
+        T* crow = c + r * q.nx;
+        for (int x = threadIdx.x; x < q.nx; x += RT) {
+            int64_t p = base + x;
+            if (rowc) {
+                const int cx = q.fx ? q.fx[x] : 0;
+                if (cx >= 0) {
+                    crow[x] = T(0);   // z vanishes on the coarser grid
+                    continue;
+                }
+                p -= q.cbx[x];
+            }
+            const int s = sym[p];
+            T v;
+            if (s == MGARD_ESC) v = (T)((double)esc[p] * w);
+            else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
+            else v = (T)((double)(s - RADIUS) * w);
+            crow[x] = v;
+        }
+    }
+}
+
+QRow make_qrow(const Plan& p, int l) {
+    QRow q{};
+    q.nz = (int)p.shape[l][1];
+    q.ny = (int)p.shape[l][2];
+    q.nx = (int)p.shape[l][3];
+    q.tables = l > 0;
+    q.sym_off = p.offset[l];
+    if (l > 0) {
+        const Level<float>& lv = p.lf[l];
+        q.tail_z = lv.nc[2] * lv.nc[3];
+        q.tail_y = lv.nc[3];
+        q.fz = lv.ax[1].fcls; q.cbz = lv.ax[1].cbefore;
+        q.fy = lv.ax[2].fcls; q.cby = lv.ax[2].cbefore;
+        q.fx = lv.ax[3].fcls; q.cbx = lv.ax[3].cbefore;
+    }
+    return q;
+}
+
+}  // namespace
+
+template <typename T>
+mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st) {
+    const Level<T>& lv = p.level<T>(l);
+    MGB_LAUNCH("k3_coeff", st, k3_coeff<T><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(in, out, coarse, lv));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
+                        cudaStream_t st) {
+    const Level<T>& lv = p.level<T>(l);
+    MGB_LAUNCH("k3_fill", st, k3_fill<T><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(z, coarse, out, lv));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T, typename Tw>
+mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
+                           T sign, cudaStream_t st) {
+    const Level<Tw>& lw = p.level<Tw>(l);
+    const Level<T>& lt = p.level<T>(l);
+    const int nz = (int)lt.n[1], ny = (int)lt.n[2], nx = (int)lt.n[3];
+    const int ncz = (int)lt.nc[1], ncy = (int)lt.nc[2], ncx = (int)lt.nc[3];
+    Tw* b0 = (Tw*)t0;
+    Tw* b1 = (Tw*)t1;
+    // x (always active)
+    MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
+        z, b0, nz, ny, nx, ncx, lw.ax[3].rf, lw.ax[3].rw, lt.ax[1].fcls, lt.ax[2].fcls, lt.ax[3].fcls));
+    MGB_CUDA(cudaGetLastError());
+    Tw* cur = b0;
+    Tw* nxt = b1;
+    if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
+        MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
+            cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rf, lw.ax[2].rw));
+        MGB_CUDA(cudaGetLastError());
+        std::swap(cur, nxt);
+    }
+    if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
+        MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
+            cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rf, lw.ax[1].rw));
+        MGB_CUDA(cudaGetLastError());
+        std::swap(cur, nxt);
+    }
+    // solves: z, y (strided lines), then x (contiguous, fused correction add)
+    if (lt.ax[1].fcls)
+        MGB_TRY((solve_strided<Tw, T>(cur, 1, ncz, (int64_t)ncy * ncx, lw.ax[1].tsub, lw.ax[1].tinv,
+                                      lw.ax[1].tcp, (T*)nullptr, (Tw)sign, st)));
+    if (lt.ax[2].fcls)
+        MGB_TRY((solve_strided<Tw, T>(cur, ncz, ncy, ncx, lw.ax[2].tsub, lw.ax[2].tinv,
+                                      lw.ax[2].tcp, (T*)nullptr, (Tw)sign, st)));
+    MGB_TRY((solve_contiguous<Tw, T>(cur, (int64_t)ncz * ncy, ncx, lw.ax[3].tsub, lw.ax[3].tinv,
+                                     lw.ax[3].tcp, coarse, (Tw)sign, st)));
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t* sym,
+                            int32_t* esc, unsigned long long* hist, unsigned* status,
+                            cudaStream_t st) {
+    const QRow q = make_qrow(p, l);
+    const T inv_w = (T)(1.0 / w);
+    MGB_LAUNCH("k3_quantize", st, k3_quantize<T><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+        c, q, inv_w, w, sym, esc, hist, status));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
+                              double w, T* c, cudaStream_t st) {
+    const QRow q = make_qrow(p, l);
+    MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+        sym, esc, q, (T)w, w, c));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+#define INST(T)                                                                                  \
+    template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t);     \
+    template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t); \
+    template mgard_status rows3_quantize<T>(const Plan&, int, const T*, double, uint16_t*,       \
+                                            int32_t*, unsigned long long*, unsigned*,            \
+                                            cudaStream_t);                                       \
+    template mgard_status rows3_dequantize<T>(const Plan&, int, const uint16_t*, const int32_t*, \
+                                              double, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template mgard_status rows3_correct<float, float>(const Plan&, int, const float*, float*, void*,
+                                                  void*, float, cudaStream_t);
+template mgard_status rows3_correct<float, double>(const Plan&, int, const float*, float*, void*,
+                                                   void*, float, cudaStream_t);
+template mgard_status rows3_correct<double, double>(const Plan&, int, const double*, double*,
+                                                    void*, void*, double, cudaStream_t);
+
+}  // namespace mgb

@@ -1,0 +1,41 @@
+// Row kernels for grids of up to three active axes (the 4D view has
+// n[0] == 1): axis 1 = z, axis 2 = y, axis 3 = x (contiguous).  A block
+// walks whole x-rows; everything that depends only on (z, y) -- coarse or
+// new, interpolation sources and weights, rank offsets -- is computed once
+// per row, so the per-element work is a few loads and FMAs with 32-bit
+// offsets inside the row.
+#pragma once
+
+#include "plan.cuh"
+
+namespace mgb {
+
+// True when the row kernels apply: at most three active axes.
+inline bool rows3_ok(const Plan& p) { return p.n4[0] == 1; }
+
+template <typename T>
+mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st);
+template <typename T>
+mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
+                        cudaStream_t st);
+// coarse += sign * M_{l-1}^{-1} P^T M_l z (restriction x, y, z; solves z, y, x)
+template <typename T, typename Tw>
+mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
+                           T sign, cudaStream_t st);
+template <typename T>
+mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t* sym,
+                            int32_t* esc, unsigned long long* hist, unsigned* status,
+                            cudaStream_t st);
+template <typename T>
+mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
+                              double w, T* c, cudaStream_t st);
+
+// Solvers shared with the generic path (multilevel.cu).
+template <typename Tw, typename Tdst>
+mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
+                           const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st);
+template <typename Tw, typename Tdst>
+mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, const Tw* inv,
+                              const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st);
+
+}  // namespace mgb
