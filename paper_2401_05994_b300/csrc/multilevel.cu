@@ -529,15 +529,20 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
         off[l] = total;
         total += ((size_t)p.level_size(l) * sizeof(T) + 255) & ~size_t(255);
     }
+    // restriction intermediates: the generic path shrinks axes 0..3 in order,
+    // the row path shrinks axes 3..0; size for the larger of every prefix
     size_t tmax = 16;
     for (int l = 1; l <= p.L; ++l) {
-        int64_t s[4];
-        for (int a = 0; a < 4; ++a) s[a] = p.shape[l][a];
         const size_t el = level_uses_fp64<T>(p, l) ? 8 : sizeof(T);
-        for (int a = 0; a < 4; ++a) {
-            if (p.n4[a] == 1) continue;
-            s[a] = p.shape[l - 1][a];
-            tmax = std::max(tmax, (size_t)(s[0] * s[1] * s[2] * s[3]) * el);
+        for (int dir = 0; dir < 2; ++dir) {
+            int64_t s[4];
+            for (int a = 0; a < 4; ++a) s[a] = p.shape[l][a];
+            for (int k = 0; k < 4; ++k) {
+                const int a = dir == 0 ? k : 3 - k;
+                if (p.n4[a] == 1) continue;
+                s[a] = p.shape[l - 1][a];
+                tmax = std::max(tmax, (size_t)(s[0] * s[1] * s[2] * s[3]) * el);
+            }
         }
     }
     MGB_TRY(store.alloc(total, st));

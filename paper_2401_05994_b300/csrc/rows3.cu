@@ -12,12 +12,22 @@ namespace mgb {
 
 namespace {
 
-constexpr int RT = 256;              // threads per block (one x-row at a time)
+constexpr int RT = 256;              // threads per block: 8 warps, one x-row per warp
+constexpr int WPB = RT / 32;
 constexpr int64_t ROW_BLOCKS = 148 * 8;
 
-inline int row_grid(int64_t rows) { return (int)std::min<int64_t>(std::max<int64_t>(rows, 1), ROW_BLOCKS); }
+inline int row_grid(int64_t rows) {
+    return (int)std::min<int64_t>(std::max<int64_t>((rows + WPB - 1) / WPB, 1), ROW_BLOCKS);
+}
 
-// Interpolation sources of one index along one axis.
+// Node classes follow from the hierarchy rule (coarse = even positions plus
+// the last one), so positions are arithmetic; only weights come from tables.
+__device__ inline bool is_coarse(int i, int m) { return (i & 1) == 0 || i == m - 1; }
+__device__ inline int coarse_index(int i, int m, int mc) { return i == m - 1 ? mc - 1 : i >> 1; }
+__device__ inline int restrict_center(int J, int m, int mc) { return J == mc - 1 ? m - 1 : 2 * J; }
+__device__ inline int coarse_before(int i) { return (i + 1) >> 1; }
+
+// Interpolation sources of one index along one axis (y or z).
 template <typename T>
 struct Src {
     int p[2];     // fine positions (decomposition) or coarse indices (fill)
@@ -27,19 +37,17 @@ struct Src {
 };
 
 template <typename T>
-__device__ inline Src<T> sources(const AxisT<T>& ax, int i, bool coarse_index) {
+__device__ inline Src<T> sources(const AxisT<T>& ax, int i, int m, int mc, bool coarse_idx) {
     Src<T> s;
-    if (!ax.fcls) {
-        s.p[0] = i; s.w[0] = T(1); s.n = 1; s.J = i;
-        return s;
-    }
-    const int c = ax.fcls[i];
-    if (c >= 0) {
-        s.p[0] = coarse_index ? c : i; s.w[0] = T(1); s.n = 1; s.J = c;
+    if (is_coarse(i, m)) {
+        s.J = coarse_index(i, m, mc);
+        s.p[0] = coarse_idx ? s.J : i;
+        s.w[0] = T(1);
+        s.n = 1;
     } else {
-        const int left = -c - 1;
-        s.p[0] = coarse_index ? left : ax.rf[left];
-        s.p[1] = coarse_index ? left + 1 : ax.rf[left + 1];
+        const int left = (i - 1) >> 1;
+        s.p[0] = coarse_idx ? left : i - 1;
+        s.p[1] = coarse_idx ? left + 1 : i + 1;
         s.w[0] = ax.wl[i];
         s.w[1] = ax.wr[i];
         s.n = 2;
@@ -48,16 +56,23 @@ __device__ inline Src<T> sources(const AxisT<T>& ax, int i, bool coarse_index) {
     return s;
 }
 
+#define WARP_ROWS(rows, r)                                                                    \
+    for (int64_t r = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); r < (rows);             \
+         r += (int64_t)gridDim.x * WPB)
+
 // -- coefficients (decomposition step 1) --------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
                                                Level<T> lv) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
-    const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
-    const AxisT<T> ax = lv.ax[3];
-    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        const Src<T> sz = sources(lv.ax[1], z, false), sy = sources(lv.ax[2], y, false);
+    const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+    const T* __restrict__ wlx = lv.ax[3].wl;
+    const T* __restrict__ wrx = lv.ax[3].wr;
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)nz * ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
+        const Src<T> sz = sources(lv.ax[1], z, nz, ncz, false);
+        const Src<T> sy = sources(lv.ax[2], y, ny, ncy, false);
         const T* rows[4];
         T rw[4];
         int nr = 0;
@@ -71,25 +86,22 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const T* urow = in + r * nx;
         T* orow = out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
-        for (int x = threadIdx.x; x < nx; x += RT) {
+        for (int x = lane; x < nx; x += 32) {
             const T u = urow[x];
-            const int cx = ax.fcls ? ax.fcls[x] : 0;
             T acc = T(0);
-            if (cx >= 0) {
+            if (is_coarse(x, nx)) {
                 if (rowc) {
-                    crow[cx] = u;
+                    crow[coarse_index(x, nx, ncx)] = u;
                     continue;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k < nr) acc += rw[k] * rows[k][x];
             } else {
-                const int left = -cx - 1;
-                const int xl = ax.rf[left], xr = ax.rf[left + 1];
-                const T wl = ax.wl[x], wr = ax.wr[x];
+                const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * (wl * rows[k][xl] + wr * rows[k][xr]);
+                    if (k < nr) acc += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
             }
             orow[x] = u - acc;
         }
@@ -101,11 +113,14 @@ template <typename T>
 __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
                                               Level<T> lv) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
-    const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
-    const AxisT<T> ax = lv.ax[3];
-    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        const Src<T> sz = sources(lv.ax[1], z, true), sy = sources(lv.ax[2], y, true);
+    const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+    const T* __restrict__ wlx = lv.ax[3].wl;
+    const T* __restrict__ wrx = lv.ax[3].wr;
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)nz * ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
+        const Src<T> sz = sources(lv.ax[1], z, nz, ncz, true);
+        const Src<T> sy = sources(lv.ax[2], y, ny, ncy, true);
         const T* rows[4];
         T rw[4];
         int nr = 0;
@@ -118,20 +133,20 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         const bool rowc = sz.n == 1 && sy.n == 1;
         const T* zrow = zin + r * nx;
         T* orow = out + r * nx;
-        for (int x = threadIdx.x; x < nx; x += RT) {
-            const int cx = ax.fcls ? ax.fcls[x] : 0;
+        for (int x = lane; x < nx; x += 32) {
             T acc = T(0);
-            if (cx >= 0) {
+            if (is_coarse(x, nx)) {
+                const int J = coarse_index(x, nx, ncx);
                 if (rowc) {
-                    orow[x] = rows[0][cx];
+                    orow[x] = rows[0][J];
                     continue;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * rows[k][cx];
+                    if (k < nr) acc += rw[k] * rows[k][J];
             } else {
-                const int left = -cx - 1;
-                const T wl = ax.wl[x], wr = ax.wr[x];
+                const int left = (x - 1) >> 1;
+                const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k < nr) acc += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
@@ -145,22 +160,22 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                                                     Tout* __restrict__ out, int nz, int ny,
-                                                    int nx, int ncx, const int* __restrict__ rf,
-                                                    const Tout* __restrict__ rw, const int* fz,
-                                                    const int* fy, const int* fx) {
-    for (int64_t r = blockIdx.x; r < (int64_t)nz * ny; r += gridDim.x) {
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        const bool rowc = (!fz || fz[z] >= 0) && (!fy || fy[y] >= 0);
+                                                    int nx, int ncz, int ncy, int ncx,
+                                                    const Tout* __restrict__ rw) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)nz * ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
+        const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
         const Tin* irow = in + r * nx;
         Tout* orow = out + r * ncx;
-        for (int J = threadIdx.x; J < ncx; J += RT) {
-            const int f = rf[J];
+        for (int J = lane; J < ncx; J += 32) {
+            const int f = restrict_center(J, nx, ncx);
             Tout acc = Tout(0);
 #pragma unroll
             for (int t = 0; t < 5; ++t) {
                 const int ip = f - 2 + t;
                 if (ip < 0 || ip >= nx) continue;
-                if (rowc && fx[ip] >= 0) continue;   // coarse node: z = 0 (not read)
+                if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
                 acc += rw[J * 5 + t] * (Tout)irow[ip];
             }
             orow[J] = acc;
@@ -174,15 +189,15 @@ template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ in,
                                                        Tout* __restrict__ out, int nouter, int m,
                                                        int mc, int inner, int nx,
-                                                       const int* __restrict__ rf,
                                                        const Tout* __restrict__ rw) {
-    // one output row = (o, J, i); rows of the input at (o, rf[J]-2+t, i)
-    for (int64_t r = blockIdx.x; r < (int64_t)nouter * mc * inner; r += gridDim.x) {
-        const int i = (int)(r % inner);
-        const int64_t oj = r / inner;
-        const int J = (int)(oj % mc);
-        const int o = (int)(oj / mc);
-        const int f = rf[J];
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)nouter * mc * inner, r) {
+        const uint32_t ru = (uint32_t)r;
+        const int i = (int)(ru % (uint32_t)inner);
+        const uint32_t oj = ru / (uint32_t)inner;
+        const int J = (int)(oj % (uint32_t)mc);
+        const int o = (int)(oj / (uint32_t)mc);
+        const int f = restrict_center(J, m, mc);
         const Tin* src[5];
         Tout w[5];
         int ns = 0;
@@ -196,7 +211,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
             ++ns;
         }
         Tout* orow = out + r * nx;
-        for (int x = threadIdx.x; x < nx; x += RT) {
+        for (int x = lane; x < nx; x += 32) {
             Tout acc = Tout(0);
 #pragma unroll
             for (int k = 0; k < 5; ++k)
@@ -251,26 +266,24 @@ __device__ inline void qvalue<double>(double c, double, double w, int& sym, int3
 
 struct QRow {
     int nz, ny, nx;
+    int ncz, ncy, ncx;
     int64_t tail_z, tail_y;       // ncy*ncx and ncx
-    const int* fz; const int* fy; const int* fx;
-    const int* cbz; const int* cby; const int* cbx;
     int64_t sym_off;
-    int tables;
+    int tables;                   // level >= 1
 };
 
-// Per-row rank offset; returns whether the row lies in the coarse grid's
-// (z, y) prefix (then x nodes that are coarse are skipped).
+// Rank offset of a row: the number of coarse-grid nodes before its first
+// node in row-major order, except those in the row itself; rowc reports that
+// the row lies in the coarse grid's (z, y) prefix.
 __device__ inline int64_t row_rank(const QRow& q, int z, int y, bool& rowc) {
     if (!q.tables) {
         rowc = false;
         return 0;
     }
-    const bool zc = !q.fz || q.fz[z] >= 0;
-    const bool yc = !q.fy || q.fy[y] >= 0;
-    int64_t cnt = 0;
-    if (q.fz) cnt += (int64_t)q.cbz[z] * q.tail_z;
-    if (zc && q.fy) cnt += (int64_t)q.cby[y] * q.tail_y;
-    rowc = zc && yc;
+    const bool zc = is_coarse(z, q.nz);
+    int64_t cnt = (int64_t)coarse_before(z) * q.tail_z;
+    if (zc) cnt += (int64_t)coarse_before(y) * q.tail_y;
+    rowc = zc && is_coarse(y, q.ny);
     return cnt;
 }
 
@@ -286,17 +299,17 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
     unsigned* my = sh[threadIdx.x & (HCOPIES - 1)];
     unsigned center = 0;   // the most frequent symbol (q = 0) is counted in a register
     unsigned st = 0;
-    for (int64_t r = blockIdx.x; r < (int64_t)q.nz * q.ny; r += gridDim.x) {
-        const int z = (int)(r / q.ny), y = (int)(r - (int64_t)z * q.ny);
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)q.nz * q.ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
         bool rowc;
         const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
         const T* crow = c + r * q.nx;
-        for (int x = threadIdx.x; x < q.nx; x += RT) {
+        for (int x = lane; x < q.nx; x += 32) {
             int64_t p = base + x;
             if (rowc) {
-                const int cx = q.fx ? q.fx[x] : 0;
-                if (cx >= 0) continue;   // node of the coarser grid
-                p -= q.cbx[x];
+                if (is_coarse(x, q.nx)) continue;   // node of the coarser grid
+                p -= coarse_before(x);
             }
             int s;
             int32_t qo;
@@ -322,20 +335,20 @@ template <typename T>
 __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__ sym,
                                                     const int32_t* __restrict__ esc, QRow q,
                                                     T wt, double w, T* __restrict__ c) {
-    for (int64_t r = blockIdx.x; r < (int64_t)q.nz * q.ny; r += gridDim.x) {
-        const int z = (int)(r / q.ny), y = (int)(r - (int64_t)z * q.ny);
+    const int lane = threadIdx.x & 31;
+    WARP_ROWS((int64_t)q.nz * q.ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
         bool rowc;
         const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
         T* crow = c + r * q.nx;
-        for (int x = threadIdx.x; x < q.nx; x += RT) {
+        for (int x = lane; x < q.nx; x += 32) {
             int64_t p = base + x;
             if (rowc) {
-                const int cx = q.fx ? q.fx[x] : 0;
-                if (cx >= 0) {
+                if (is_coarse(x, q.nx)) {
                     crow[x] = T(0);   // z vanishes on the coarser grid
                     continue;
                 }
-                p -= q.cbx[x];
+                p -= coarse_before(x);
             }
             const int s = sym[p];
             T v;
@@ -355,12 +368,11 @@ QRow make_qrow(const Plan& p, int l) {
     q.tables = l > 0;
     q.sym_off = p.offset[l];
     if (l > 0) {
-        const Level<float>& lv = p.lf[l];
-        q.tail_z = lv.nc[2] * lv.nc[3];
-        q.tail_y = lv.nc[3];
-        q.fz = lv.ax[1].fcls; q.cbz = lv.ax[1].cbefore;
-        q.fy = lv.ax[2].fcls; q.cby = lv.ax[2].cbefore;
-        q.fx = lv.ax[3].fcls; q.cbx = lv.ax[3].cbefore;
+        q.ncz = (int)p.shape[l - 1][1];
+        q.ncy = (int)p.shape[l - 1][2];
+        q.ncx = (int)p.shape[l - 1][3];
+        q.tail_z = (int64_t)q.ncy * q.ncx;
+        q.tail_y = q.ncx;
     }
     return q;
 }
@@ -395,19 +407,19 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* b1 = (Tw*)t1;
     // x (always active)
     MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
-        z, b0, nz, ny, nx, ncx, lw.ax[3].rf, lw.ax[3].rw, lt.ax[1].fcls, lt.ax[2].fcls, lt.ax[3].fcls));
+        z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3].rw));
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
     Tw* nxt = b1;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
         MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
-            cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rf, lw.ax[2].rw));
+            cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
         MGB_CUDA(cudaGetLastError());
         std::swap(cur, nxt);
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
         MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
-            cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rf, lw.ax[1].rw));
+            cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
         MGB_CUDA(cudaGetLastError());
         std::swap(cur, nxt);
     }

@@ -10,8 +10,11 @@
 
 namespace mgb {
 
-// True when the row kernels apply: at most three active axes.
-inline bool rows3_ok(const Plan& p) { return p.n4[0] == 1; }
+// True when the row kernels apply: at most three active axes and fewer than
+// 2^31 nodes (row and symbol arithmetic inside a row uses 32 bits).
+inline bool rows3_ok(const Plan& p) {
+    return p.n4[0] == 1 && p.total() < (int64_t(1) << 31);
+}
 
 template <typename T>
 mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st);
