@@ -62,8 +62,9 @@ def level_shapes(shape):
 
 def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
     """Bytes each kernel must move per step (one compress + one decompress),
-    summed over its launches: reads of its inputs plus writes of its outputs,
-    counted once (cache re-reads excluded)."""
+    summed over its launches: one read of every input and one write of every
+    output, counted once (cache re-reads excluded).  Levels whose coarse grid
+    has fewer than 2^21 nodes restrict and solve in 8-byte words."""
     lv = level_shapes(shape)
     N = int(np.prod(shape))
     by = {}
@@ -71,28 +72,22 @@ def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
     def add(k, v):
         by[k] = by.get(k, 0.0) + v
 
+    total_levels = 0
     for l in range(len(lv) - 1):
         n, nc = int(np.prod(lv[l])), int(np.prod(lv[l + 1]))
-        fp64 = nc < (1 << 21)
-        ew = 8 if fp64 else esize
-        # decomposition: coefficient pass reads u_l, writes coefficients + coarse copy
-        add("k_coeff_gather", 2 * n * esize)
-        # restriction chain (compress and decompress each run it once)
-        cur = list(lv[l])
-        src = esize
-        for a in range(3):
-            nin = int(np.prod(cur))
-            cur[a] = lv[l + 1][a]
-            nout = int(np.prod(cur))
-            add("k_restrict", 2 * (nin * src + nout * ew))
-            src = ew
-        # three solves (read+write); the last also reads+writes the coarse array
-        add("k_solve_rows", 2 * (2 * nc * ew + 2 * nc * esize))
-        add("k_solve_lines", 2 * 2 * (2 * nc * ew))
-        # recomposition fill: reads z_l and the coarse array, writes u_l
-        add("k_fill", (2 * n + nc) * esize)
-    add("k_quantize", N * esize + 2 * N)
-    add("k_dequantize", 2 * N + N * esize)
+        total_levels += n
+        ew = 8 if nc < (1 << 21) else esize
+        (nz, ny, nx), (cz, cy, cx) = lv[l], lv[l + 1]
+        add("k3_coeff", 2 * n * esize)                       # read u_l; write coefficients + coarse copy
+        add("k3_fill", (2 * n + nc) * esize)                  # read z_l and coarse; write u_l
+        for _ in range(2):                                    # decomposition and recomposition
+            add("k3_restrict_x", n * esize + nz * ny * cx * ew)
+            add("k3_restrict_rows", (nz * ny * cx + nz * cy * cx) * ew + (nz * cy * cx + nc) * ew)
+            add("k_solve_lines", 2 * 2 * nc * ew)             # z and y solves: read + write
+            add("k_solve_warp", 2 * nc * ew + 2 * nc * esize)  # x solve + coarse update
+    total_levels += int(np.prod(lv[-1]))
+    add("k3_quantize", total_levels * esize + 2 * N + 4 * esc_count)
+    add("k3_dequantize", 2 * N + 4 * esc_count + total_levels * esize)
     add("k_maxabs", N * esize)
     add("k_chunk_count", 2 * N)
     add("k_pack", 2 * N + comp_bytes)
@@ -210,6 +205,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", type=int, default=SHAPE[0],
+                    help="cube edge (default 513); smaller edges are for profiling captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -232,9 +229,10 @@ def main():
         if world > 1:
             dist.barrier()
 
-    u = synth.gaussian_random_field(SHAPE, beta=BETA, seed=1 + rank, device=dev)
+    shape = (args.shape,) * 3
+    u = synth.gaussian_random_field(shape, beta=BETA, seed=1 + rank, device=dev)
     field_bytes = u.numel() * 4
-    bound = binding.compress_bound(SHAPE)
+    bound = binding.compress_bound(shape)
     comp = torch.empty(bound, dtype=torch.uint8, device=dev)
     out = torch.empty_like(u)
     stream = torch.cuda.current_stream()
@@ -285,7 +283,7 @@ def main():
     rep = binding.timing_report()
     from paper_2401_05994_b300.fmt import HEADER_SIZE, header
     esc_count = header(buf[:HEADER_SIZE].cpu().numpy().tobytes())["noutliers"]
-    algo = algorithmic_bytes(SHAPE, comp_bytes, esc_count)
+    algo = algorithmic_bytes(shape, comp_bytes, esc_count)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -304,10 +302,10 @@ def main():
                 "kernel_share": kernel_ms[dom] / sum(kernel_ms.values())}
 
     # end-to-end through the C ABI with pinned host buffers
-    hu = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+    hu = torch.empty(shape, dtype=torch.float32, pin_memory=True)
     hu.copy_(u)
     hcomp = torch.empty(bound, dtype=torch.uint8, pin_memory=True)
-    hout = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+    hout = torch.empty(shape, dtype=torch.float32, pin_memory=True)
     hu_np, hcomp_np, hout_np = hu.numpy(), hcomp.numpy(), hout.numpy()
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
@@ -344,13 +342,13 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "513^3 f32 Gaussian random field, E(k)~k^-5/3, rel Linf 1e-3",
+            "config": {"workload": f"{args.shape}^3 f32 Gaussian random field, E(k)~k^-5/3, rel Linf 1e-3",
                        "global_batch": world, "l2": "input 540 MB > L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks,
             "verify": {"max_abs_error": err, "tol_abs": meta["tol_abs"], "ok": err <= meta["tol_abs"],
-                       "ratio": ratio},
+                       "ratio": ratio, "escapes": int(esc_count)},
             "kernels_ms_per_step": {k: round(v, 4) for k, v in sorted(kernel_ms.items(),
                                                                         key=lambda kv: -kv[1])},
         }

@@ -185,48 +185,101 @@ __global__ void k_solve_lines(Tw* x, int64_t outer_n, int64_t m, int64_t stride,
         }
 }
 
-// Lines along the contiguous axis: a warp stages 32 lines in shared memory
-// (row stride m+1 keeps the per-thread column walks bank-conflict free).
-template <typename Tw, typename Tdst>
-__global__ void k_solve_rows(Tw* x, int64_t lines, int m, const Tw* __restrict__ sub,
-                             const Tw* __restrict__ inv, const Tw* __restrict__ cp, Tdst* dst,
-                             Tw sign) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tw* tile = (Tw*)smem_raw;
-    const int ld = m + 1;
-    const int tid = threadIdx.x;
-    for (int64_t l0 = blockIdx.x * 32LL; l0 < lines; l0 += (int64_t)gridDim.x * 32) {
-        const int nl = (int)min((int64_t)32, lines - l0);
-        const Tw* src = x + l0 * m;
-        for (int r = 0; r < nl; ++r)
-            for (int k = tid; k < m; k += 32) tile[r * ld + k] = src[(int64_t)r * m + k];
+// Lines along the contiguous axis, one warp per line held in registers: lane
+// j owns elements [jE, jE+E).  Both Thomas sweeps are first-order affine
+// recurrences (y_k = alpha_k y_{k-1} + beta_k forward, x_k = gamma_k
+// x_{k+1} + y_k backward), so each lane composes the maps of its segment,
+// the warp scans the compositions with shuffles, and each lane replays its
+// segment from the scanned input.  Global traffic goes through a padded
+// per-warp shared buffer so loads and stores stay coalesced.
+constexpr int SW_WARPS = 4;
+
+template <typename Tw, typename Tdst, int E>
+__global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lines, int m,
+                                                              const Tw* __restrict__ sub,
+                                                              const Tw* __restrict__ inv,
+                                                              const Tw* __restrict__ cp, Tdst* dst,
+                                                              Tw sign) {
+    constexpr int W = E + 1;
+    __shared__ Tw buf[SW_WARPS][32 * W];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Tw* sb = buf[wid];
+    const int k0 = lane * E;
+    for (int64_t ln = (int64_t)blockIdx.x * SW_WARPS + wid; ln < lines;
+         ln += (int64_t)gridDim.x * SW_WARPS) {
+        Tw* row = x + ln * m;
+        for (int e = lane; e < 32 * E; e += 32) sb[(e / E) * W + e % E] = e < m ? row[e] : Tw(0);
         __syncwarp();
-        if (tid < nl) {
-            Tw* r = tile + tid * ld;
-            Tw y = r[0] * inv[0];
-            r[0] = y;
-            for (int k = 1; k < m; ++k) {
-                y = (r[k] - sub[k] * y) * inv[k];
-                r[k] = y;
-            }
-            Tw v = y;
-            for (int k = m - 2; k >= 0; --k) {
-                v = r[k] - cp[k] * v;
-                r[k] = v;
+        Tw v[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[k] = sb[lane * W + k];
+        // forward sweep: compose y -> alpha*y + beta over the segment
+        Tw A = Tw(1), B = Tw(0);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int g = k0 + k;
+            if (g < m) {
+                const Tw al = -sub[g] * inv[g];
+                A = al * A;
+                B = al * B + v[k] * inv[g];
             }
         }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Tw pa = __shfl_up_sync(0xffffffffu, A, o), pb = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) {
+                B = A * pb + B;
+                A = A * pa;
+            }
+        }
+        Tw y = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) y = Tw(0);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int g = k0 + k;
+            if (g < m) {
+                y = (v[k] - sub[g] * y) * inv[g];
+                v[k] = y;
+            }
+        }
+        // backward sweep: compose x -> gamma*x + y from the segment's end
+        A = Tw(1);
+        B = Tw(0);
+#pragma unroll
+        for (int k = E - 1; k >= 0; --k) {
+            const int g = k0 + k;
+            if (g < m) {
+                const Tw ga = -cp[g];
+                A = ga * A;
+                B = ga * B + v[k];
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Tw pa = __shfl_down_sync(0xffffffffu, A, o), pb = __shfl_down_sync(0xffffffffu, B, o);
+            if (lane + o < 32) {
+                B = A * pb + B;
+                A = A * pa;
+            }
+        }
+        Tw xx = __shfl_down_sync(0xffffffffu, B, 1);
+        if (lane == 31) xx = Tw(0);
+#pragma unroll
+        for (int k = E - 1; k >= 0; --k) {
+            const int g = k0 + k;
+            if (g < m) {
+                xx = v[k] - cp[g] * xx;
+                v[k] = xx;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) sb[lane * W + k] = v[k];
         __syncwarp();
         if (dst) {
-            Tdst* d = dst + l0 * m;
-            for (int r = 0; r < nl; ++r)
-                for (int k = tid; k < m; k += 32) {
-                    const int64_t e = (int64_t)r * m + k;
-                    d[e] = (Tdst)((Tw)d[e] + sign * tile[r * ld + k]);
-                }
+            Tdst* d = dst + ln * m;
+            for (int e = lane; e < m; e += 32) d[e] = (Tdst)((Tw)d[e] + sign * sb[(e / E) * W + e % E]);
         } else {
-            Tw* d = x + l0 * m;
-            for (int r = 0; r < nl; ++r)
-                for (int k = tid; k < m; k += 32) d[(int64_t)r * m + k] = tile[r * ld + k];
+            for (int e = lane; e < m; e += 32) row[e] = sb[(e / E) * W + e % E];
         }
         __syncwarp();
     }
@@ -396,17 +449,6 @@ __global__ void k_mass_norm(const T* __restrict__ u, Level<T> lv, double* partia
     if (t == 0) partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sh[0];
 }
 
-int max_dyn_smem() {
-    static int v = -1;
-    if (v < 0) {
-        int dev = 0, x = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        v = x > 0 ? x : 48 * 1024;
-    }
-    return v;
-}
-
 template <typename Tw, typename Tdst>
 mgard_status solve_axis(Tw* x, Shape4 s, int a, const Tw* sub, const Tw* inv, const Tw* cp,
                         Tdst* dst, Tw sign, cudaStream_t st) {
@@ -500,24 +542,20 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
 template <typename Tw, typename Tdst>
 mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, const Tw* inv,
                               const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
-    const size_t smem = 32 * (size_t)(m + 1) * sizeof(Tw);
-    const size_t cap = std::min<size_t>((size_t)max_dyn_smem(), 200 * 1024);
-    if (smem <= cap) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            MGB_CUDA(cudaFuncSetAttribute(k_solve_rows<Tw, Tdst>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-            attr_set = true;
-        }
-        const int grid = (int)std::min<int64_t>((lines + 31) / 32, 148LL * 32);
-        MGB_LAUNCH("k_solve_rows", st,
-                   k_solve_rows<Tw, Tdst><<<grid, 32, smem, st>>>(x, lines, (int)m, sub, inv, cp,
-                                                                  dst, sign));
-        MGB_CUDA(cudaGetLastError());
-        return MGARD_OK;
+    const int grid = (int)std::min<int64_t>((lines + SW_WARPS - 1) / SW_WARPS, 148LL * 16);
+    const int bs = SW_WARPS * 32;
+    if (m <= 256) {
+        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 8><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
+    } else if (m <= 512) {
+        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 16><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
+    } else if (m <= 1024) {
+        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 32><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
+    } else {
+        // long lines: one thread per line in global memory
+        return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
     }
-    // lines too long for shared memory: one thread per line in global memory
-    return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
 }
 
 template <typename T>

@@ -15,6 +15,7 @@ namespace {
 constexpr int RT = 256;              // threads per block: 8 warps, one x-row per warp
 constexpr int WPB = RT / 32;
 constexpr int64_t ROW_BLOCKS = 148 * 8;
+constexpr int U = 4;                 // elements per lane per batch: loads issued before stores
 
 inline int row_grid(int64_t rows) {
     return (int)std::min<int64_t>(std::max<int64_t>((rows + WPB - 1) / WPB, 1), ROW_BLOCKS);
@@ -86,24 +87,33 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const T* urow = in + r * nx;
         T* orow = out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
-        for (int x = lane; x < nx; x += 32) {
-            const T u = urow[x];
-            T acc = T(0);
-            if (is_coarse(x, nx)) {
-                if (rowc) {
-                    crow[coarse_index(x, nx, ncx)] = u;
-                    continue;
+        for (int x0 = lane; x0 < nx; x0 += 32 * U) {
+            T u[U], acc[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                acc[j] = T(0);
+                if (x >= nx) continue;
+                u[j] = urow[x];
+                if (is_coarse(x, nx)) {
+                    if (rowc) continue;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nr) acc[j] += rw[k] * rows[k][x];
+                } else {
+                    const T wl = wlx[x], wr = wrx[x];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nr) acc[j] += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * rows[k][x];
-            } else {
-                const T wl = wlx[x], wr = wrx[x];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
             }
-            orow[x] = u - acc;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                if (x >= nx) continue;
+                if (rowc && is_coarse(x, nx)) crow[coarse_index(x, nx, ncx)] = u[j];
+                else orow[x] = u[j] - acc[j];
+            }
         }
     }
 }
@@ -133,25 +143,36 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         const bool rowc = sz.n == 1 && sy.n == 1;
         const T* zrow = zin + r * nx;
         T* orow = out + r * nx;
-        for (int x = lane; x < nx; x += 32) {
-            T acc = T(0);
-            if (is_coarse(x, nx)) {
-                const int J = coarse_index(x, nx, ncx);
-                if (rowc) {
-                    orow[x] = rows[0][J];
-                    continue;
+        for (int x0 = lane; x0 < nx; x0 += 32 * U) {
+            T v[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                v[j] = T(0);
+                if (x >= nx) continue;
+                if (is_coarse(x, nx)) {
+                    const int J = coarse_index(x, nx, ncx);
+                    if (rowc) {
+                        v[j] = rows[0][J];
+                        continue;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nr) v[j] += rw[k] * rows[k][J];
+                } else {
+                    const int left = (x - 1) >> 1;
+                    const T wl = wlx[x], wr = wrx[x];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nr) v[j] += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * rows[k][J];
-            } else {
-                const int left = (x - 1) >> 1;
-                const T wl = wlx[x], wr = wrx[x];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nr) acc += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
+                v[j] += zrow[x];
             }
-            orow[x] = zrow[x] + acc;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                if (x < nx) orow[x] = v[j];
+            }
         }
     }
 }
@@ -168,17 +189,25 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
         const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
         const Tin* irow = in + r * nx;
         Tout* orow = out + r * ncx;
-        for (int J = lane; J < ncx; J += 32) {
-            const int f = restrict_center(J, nx, ncx);
-            Tout acc = Tout(0);
+        for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
+            Tout acc[U];
 #pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                const int ip = f - 2 + t;
-                if (ip < 0 || ip >= nx) continue;
-                if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
-                acc += rw[J * 5 + t] * (Tout)irow[ip];
+            for (int j = 0; j < U; ++j) {
+                const int J = J0 + 32 * j;
+                acc[j] = Tout(0);
+                if (J >= ncx) continue;
+                const int f = restrict_center(J, nx, ncx);
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    const int ip = f - 2 + t;
+                    if (ip < 0 || ip >= nx) continue;
+                    if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
+                    acc[j] += rw[J * 5 + t] * (Tout)irow[ip];
+                }
             }
-            orow[J] = acc;
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (J0 + 32 * j < ncx) orow[J0 + 32 * j] = acc[j];
         }
     }
 }
@@ -211,12 +240,20 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
             ++ns;
         }
         Tout* orow = out + r * nx;
-        for (int x = lane; x < nx; x += 32) {
-            Tout acc = Tout(0);
+        for (int x0 = lane; x0 < nx; x0 += 32 * U) {
+            Tout acc[U];
 #pragma unroll
-            for (int k = 0; k < 5; ++k)
-                if (k < ns) acc += w[k] * (Tout)src[k][x];
-            orow[x] = acc;
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                acc[j] = Tout(0);
+                if (x >= nx) continue;
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    if (k < ns) acc[j] += w[k] * (Tout)src[k][x];
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (x0 + 32 * j < nx) orow[x0 + 32 * j] = acc[j];
         }
     }
 }
@@ -305,19 +342,31 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
         bool rowc;
         const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
         const T* crow = c + r * q.nx;
-        for (int x = lane; x < q.nx; x += 32) {
-            int64_t p = base + x;
-            if (rowc) {
-                if (is_coarse(x, q.nx)) continue;   // node of the coarser grid
-                p -= coarse_before(x);
+        for (int x0 = lane; x0 < q.nx; x0 += 32 * U) {
+            T v[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                v[j] = T(0);
+                if (x < q.nx && !(rowc && is_coarse(x, q.nx))) v[j] = crow[x];
             }
-            int s;
-            int32_t qo;
-            qvalue<T>(crow[x], inv_w, w, s, qo, st);
-            sym[p] = (uint16_t)s;
-            if (s == MGARD_ESC) esc[p] = qo;
-            if (s == RADIUS) ++center;
-            else atomicAdd(&my[s], 1u);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                if (x >= q.nx) continue;
+                int64_t p = base + x;
+                if (rowc) {
+                    if (is_coarse(x, q.nx)) continue;   // node of the coarser grid
+                    p -= coarse_before(x);
+                }
+                int s;
+                int32_t qo;
+                qvalue<T>(v[j], inv_w, w, s, qo, st);
+                sym[p] = (uint16_t)s;
+                if (s == MGARD_ESC) esc[p] = qo;
+                if (s == RADIUS) ++center;
+                else atomicAdd(&my[s], 1u);
+            }
         }
     }
     if (center) atomicAdd(&sh[0][RADIUS], center);
@@ -341,21 +390,34 @@ __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__
         bool rowc;
         const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
         T* crow = c + r * q.nx;
-        for (int x = lane; x < q.nx; x += 32) {
-            int64_t p = base + x;
-            if (rowc) {
-                if (is_coarse(x, q.nx)) {
-                    crow[x] = T(0);   // z vanishes on the coarser grid
-                    continue;
+        for (int x0 = lane; x0 < q.nx; x0 += 32 * U) {
+            int sv[U];
+            int64_t pv[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                sv[j] = -1;
+                if (x >= q.nx) continue;
+                int64_t p = base + x;
+                if (rowc) {
+                    if (is_coarse(x, q.nx)) continue;   // z vanishes on the coarser grid
+                    p -= coarse_before(x);
                 }
-                p -= coarse_before(x);
+                pv[j] = p;
+                sv[j] = sym[p];
             }
-            const int s = sym[p];
-            T v;
-            if (s == MGARD_ESC) v = (T)((double)esc[p] * w);
-            else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
-            else v = (T)((double)(s - RADIUS) * w);
-            crow[x] = v;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int x = x0 + 32 * j;
+                if (x >= q.nx) continue;
+                const int s = sv[j];
+                T v;
+                if (s < 0) v = T(0);
+                else if (s == MGARD_ESC) v = (T)((double)esc[pv[j]] * w);
+                else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
+                else v = (T)((double)(s - RADIUS) * w);
+                crow[x] = v;
+            }
         }
     }
 }
