@@ -26,7 +26,9 @@ s-norm (finite ``s >= 0``)
 
 Every width is then multiplied by ``1 - 2^-8``.  That margin absorbs the
 rounding of a single-precision quantizer (``x = c * (1/w)`` and ``q * w``
-each rounded to float32 for ``|q| < 2048``), so ``|c - q w| <= w_bound / 2``
+each rounded to float32 for ``|q| < 4096``: at most 0.5 + 4096.5 * 2^-23
+bins for ``q`` plus 4096 * 2^-23 bins for the product, which the margin
+brings back under half of the unscaled width), so ``|c - q w| <= w_bound / 2``
 holds for it too.
 
 Relative tolerances scale by ``max|u|`` (L-infinity) or ``||u||_s``.

@@ -9,13 +9,14 @@ integer multiple of its level's bin width.  Readings fixed here:
   outlier list, in symbol order, as a 32-bit integer.
 * Symbol order: level 0 (all of its nodes), then levels 1..L (only the nodes
   new on that level), each in row-major order of that level's grid.
-* ``precision="f64"`` decides ``q`` in double precision.  ``precision="f32"``
-  takes the decision the way a single-precision quantizer does:
-  ``x = float32(c) * float32(1/w)`` rounded to float32, ``q = rint(x)``; an
-  escape's stored value is still ``rint(c / w)`` in double precision.
-* Dequantization: ``q * w`` in the working precision (``float32(q) *
-  float32(w)`` for f32 symbols), ``float(q * w)`` computed in double for
-  outliers.
+* ``precision="f64"`` decides ``q = rint(c / w)`` in double precision.
+  ``precision="f32"`` takes the decision the way a single-precision
+  quantizer does: ``x = float32(c) * float32(1/w)`` rounded to float32,
+  ``q = rint(x)``; only when ``|q| >= F32_EXACT = 4096`` is the stored value
+  recomputed as ``rint(c / w)`` in double precision.
+* Dequantization: ``q * w`` in the working precision; for f32 data
+  ``float32(q) * float32(w)`` when ``|q| < 4096`` and ``float32(q * w)``
+  (double product) otherwise.
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ DICT = 4096
 R = DICT // 2
 ESC = 0
 QMAX = 2 ** 31 - 1
+F32_EXACT = 4096
 
 
 class ToleranceTooSmall(ValueError):
@@ -46,11 +48,16 @@ def quantize_levels(levels, widths, precision="f64"):
             c32 = c.astype(np.float32)
             x = c32 * np.float32(1.0 / w)
             q = np.rint(x).astype(np.float64)
+            big = np.abs(q) >= F32_EXACT
+            q = np.where(big, np.rint(c64 / w), q)
         else:
             q = np.rint(c64 / w)
         esc = np.abs(q) >= R
+        if precision == "f32":
+            # the escape decision is the float32 one
+            esc = np.abs(np.rint(c.astype(np.float32) * np.float32(1.0 / w))) >= R
         sym = np.where(esc, ESC, q + R).astype(np.uint16)
-        qo = np.rint(c64[esc] / w)
+        qo = q[esc]
         if qo.size and np.max(np.abs(qo)) > QMAX:
             raise ToleranceTooSmall("quantized value exceeds 32-bit range")
         syms.append(sym)
@@ -78,7 +85,10 @@ def dequantize_levels(symbols, outliers, counts, widths, precision="f64"):
         q = s - R
         if precision == "f32":
             c = (q.astype(np.float32) * np.float32(w)).astype(np.float32)
-            c[esc] = (outliers[opos:opos + ne].astype(np.float64) * w).astype(np.float32)
+            qo = outliers[opos:opos + ne].astype(np.int64)
+            small = np.abs(qo) < F32_EXACT
+            c[esc] = np.where(small, qo.astype(np.float32) * np.float32(w),
+                              (qo.astype(np.float64) * w).astype(np.float32))
         else:
             c = q.astype(np.float64) * w
             c[esc] = outliers[opos:opos + ne].astype(np.float64) * w

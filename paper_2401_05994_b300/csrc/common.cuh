@@ -52,6 +52,17 @@ constexpr int DICT = MGARD_DICT;
 constexpr int RADIUS = MGARD_DICT / 2;
 constexpr int CHUNK = MGARD_CHUNK;
 constexpr int LMAX = MGARD_LMAX;
+// float32 quantization: |q| below this many bins is decided and dequantized
+// in float32 (the width margin covers its rounding); larger escapes are
+// decided and dequantized in double.
+constexpr int F32_EXACT = 4096;
+
+template <typename T>
+__device__ inline T dequant_escape(int32_t q, T wt, double w) {
+    if (sizeof(T) == 4 && (q < F32_EXACT && q > -F32_EXACT))
+        return (T)__fmul_rn((float)q, (float)wt);
+    return (T)((double)q * w);
+}
 
 // Device status bits set by kernels and read back by the host.
 enum : unsigned {

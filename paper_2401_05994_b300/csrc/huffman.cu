@@ -13,6 +13,7 @@
 // per chunk.  Decoding runs one thread per chunk with a 12-bit prefix table
 // in shared memory and canonical first-code search for longer codes.
 #include "huffman.cuh"
+#include "multilevel.cuh"
 
 namespace mgb {
 
@@ -196,9 +197,10 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
         }
         const bool valid = !bad && kraft <= (1ull << LMAX);
         for (int l = 0; l < LMAX + 2; ++l) {
-            dt->first_code[l] = (l >= 1 && l <= LMAX) ? (uint32_t)fc[l] : 0;
-            dt->count[l] = (l >= 1 && l <= LMAX) ? cnt[l] : 0;
-            dt->first_index[l] = (l >= 1 && l <= LMAX) ? fi[l] : 0;
+            const bool in = l >= 1 && l <= LMAX;
+            dt->first_code[l] = in ? (uint32_t)fc[l] : 0;
+            dt->first_index[l] = in ? fi[l] : 0;
+            dt->lim[l] = in ? ((fc[l] + cnt[l]) << (LMAX - l)) : 0;
         }
         dt->maxlen = maxlen;
         dt->valid = valid ? 1 : 0;
@@ -219,6 +221,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
     }
     for (int s = tid; s < DICT; s += blockDim.x)
         if (!lengths[s]) codes[s] = 0;
+    __syncthreads();
+    // prefixes of longer codes: the shortest possible length
+    for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) {
+        if (dt->lut[k]) continue;
+        const unsigned long long top = (unsigned long long)k << (32 - LUT_BITS);
+        unsigned l = LUT_BITS + 1;
+        while (l <= LMAX && top >= ((fc[l] + cnt[l]) << (LMAX - l))) ++l;
+        if (l <= LMAX) dt->lut[k] = LUT_LONG | l;   // else no code has this prefix: stays 0
+    }
 }
 
 // -- encoding ------------------------------------------------------------------
@@ -461,6 +472,10 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             int nb = (int)(bpos & 31);      // bits of the current word already owned by the left lane
             unsigned long long acc = 0;
             bool first = true;
+            // escape values are stored one escape late, so each load has
+            // time to arrive before its value is consumed
+            int64_t pend_at = -1;
+            int32_t pend_v = 0;
 #pragma unroll
             for (int k = 0; k < 32; ++k)
                 if (k < cnt) {
@@ -476,8 +491,13 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                         nb -= 32;
                         acc &= (nb ? ((1ull << nb) - 1) : 0ull);
                     }
-                    if (s == MGARD_ESC) outliers[eo + epos++] = escapes[base + k];
+                    if (s == MGARD_ESC) {
+                        if (pend_at >= 0) outliers[pend_at] = pend_v;
+                        pend_at = (int64_t)(eo + epos++);
+                        pend_v = escapes[base + k];
+                    }
                 }
+            if (pend_at >= 0) outliers[pend_at] = pend_v;
             if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
         }
         __syncwarp();
@@ -529,30 +549,28 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
     const uint64_t endbit = end * 32;
     uint32_t pk[4] = {0, 0, 0, 0};
     bool ok = true;
+    int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
     int k = 0;
     for (; k < cnt; ++k) {
         const uint32_t top = (uint32_t)((win << off) >> 32);
-        uint32_t ent = T.lut[top >> (32 - LUT_BITS)];
+        const uint32_t ent = T.lut[top >> (32 - LUT_BITS)];
         unsigned len, s;
-        if (ent) {
+        if (!(ent & LUT_LONG)) {
             len = ent >> 16;
             s = ent & 0xFFFF;
-        } else {
-            len = 0;
-            s = 0;
-            for (unsigned l = LUT_BITS + 1; l <= T.maxlen; ++l) {
-                const uint32_t code = top >> (32 - l);
-                const uint32_t d = code - T.first_code[l];
-                if (d < T.count[l]) {
-                    len = l;
-                    s = T.sorted[T.first_index[l] + d];
-                    break;
-                }
-            }
             if (!len) {
                 ok = false;
                 break;
             }
+        } else {
+            unsigned l = ent & 0xFF;
+            while (l <= T.maxlen && (unsigned long long)top >= T.lim[l]) ++l;
+            if (l > T.maxlen) {
+                ok = false;
+                break;
+            }
+            len = l;
+            s = T.sorted[T.first_index[l] + ((top >> (32 - l)) - T.first_code[l])];
         }
         bit += len;
         if (bit > endbit) {
@@ -574,7 +592,9 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
                 ok = false;
                 break;
             }
-            escapes[first + k] = outliers[e++];
+            escapes[first + k] = next_out;
+            ++e;
+            next_out = e < e_end ? outliers[e] : 0;
         }
         const int slot = k & 7;
         if (slot & 1) pk[slot >> 1] |= s << 16;
@@ -628,8 +648,9 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
         MGB_CUDA(cudaGetLastError());
     }
     const uint64_t ntiles = (nchunks + SCAN_TILE - 1) / SCAN_TILE;
-    unsigned long long* tsum = nullptr;
-    MGB_CUDA(cudaMallocAsync((void**)&tsum, 16 * (ntiles + 1), st));
+    DevBuf tbuf;
+    MGB_TRY(tbuf.alloc(16 * (ntiles + 1), st));
+    unsigned long long* tsum = tbuf.as<unsigned long long>();
     if (ntiles) {
         MGB_LAUNCH("k_scan_sums", st, k_scan_sums<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, tsum));
     }
@@ -638,7 +659,6 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
         MGB_LAUNCH("k_scan_apply", st, k_scan_apply<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, tsum));
     }
     MGB_CUDA(cudaGetLastError());
-    MGB_CUDA(cudaFreeAsync(tsum, st));
     return MGARD_OK;
 }
 

@@ -7,14 +7,19 @@ namespace mgb {
 
 constexpr int LUT_BITS = 12;
 
+constexpr uint32_t LUT_LONG = 0x80000000u;
+
 struct DecodeTables {
-    uint32_t lut[1 << LUT_BITS];   // prefix -> (length << 16) | symbol, 0 if the code is longer
+    // 12-bit prefix -> (length << 16) | symbol for codes of at most 12 bits;
+    // LUT_LONG | l0 when the code is longer (l0 = the shortest length a code
+    // with this prefix can have); 0 when no code starts with the prefix
+    uint32_t lut[1 << LUT_BITS];
+    unsigned long long lim[LMAX + 2];   // lim[l]: first code of length l+1, left-justified in 32 bits
     uint32_t first_code[LMAX + 2];
-    uint32_t count[LMAX + 2];
     uint32_t first_index[LMAX + 2];
-    uint16_t sorted[DICT];         // used symbols in (length, symbol) order
+    uint16_t sorted[DICT];              // used symbols in (length, symbol) order
     uint32_t maxlen;
-    uint32_t valid;                // 0 if the lengths violate the Kraft inequality
+    uint32_t valid;                     // 0 if the lengths violate the Kraft inequality
 };
 
 // Code lengths and canonical codes from a histogram (single CTA).

@@ -13,6 +13,8 @@
 // Recomposition runs 2-3 on the stored coefficients, subtracts the
 // correction and refills the fine grid (k_fill).
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "multilevel.cuh"
 #include "rows3.cuh"

@@ -7,6 +7,10 @@
 
 namespace mgb {
 
+// The library's stream-ordered memory pool on the current device (created
+// on first use, never trimmed, so repeated calls reuse their workspace).
+cudaMemPool_t workspace_pool();
+
 // Stream-ordered device allocation that frees itself.
 struct DevBuf {
     void* p = nullptr;
@@ -20,7 +24,8 @@ struct DevBuf {
     mgard_status alloc(size_t bytes, cudaStream_t s) {
         st = s;
         if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        cudaMemPool_t pool = workspace_pool();
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess) {
             p = nullptr;
             set_error(std::string("device allocation: ") + cudaGetErrorString(e));

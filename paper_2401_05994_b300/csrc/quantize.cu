@@ -75,6 +75,10 @@ __device__ inline void quantize_value(float c, float inv_w, double w, int& sym, 
         return;
     }
     sym = MGARD_ESC;
+    if (fabsf(q) < (float)F32_EXACT) {
+        qo = (int32_t)q;
+        return;
+    }
     const double qd = rint((double)c / w);
     if (fabs(qd) > 2147483647.0) {
         st |= ST_RANGE;
@@ -161,7 +165,7 @@ __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __
         const int64_t p = q.sym_off + ni.rank;
         const int s = sym[p];
         T v;
-        if (s == MGARD_ESC) v = (T)((double)esc[p] * w);
+        if (s == MGARD_ESC) v = dequant_escape<T>(esc[p], wt, w);
         else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
         else v = (T)((double)(s - RADIUS) * w);
         c[ni.addr] = v;

@@ -273,6 +273,10 @@ __device__ inline void qvalue<float>(float c, float inv_w, double w, int& sym, i
         return;
     }
     sym = MGARD_ESC;
+    if (fabsf(q) < (float)F32_EXACT) {   // the float32 decision is exact enough here
+        qo = (int32_t)q;
+        return;
+    }
     qo = 0;
     if (!isfinite(c)) {
         st |= ST_NONFINITE;
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__
                 const int s = sv[j];
                 T v;
                 if (s < 0) v = T(0);
-                else if (s == MGARD_ESC) v = (T)((double)esc[pv[j]] * w);
+                else if (s == MGARD_ESC) v = dequant_escape<T>(esc[pv[j]], wt, w);
                 else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
                 else v = (T)((double)(s - RADIUS) * w);
                 crow[x] = v;

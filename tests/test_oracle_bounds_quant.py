@@ -99,11 +99,14 @@ def test_rounding_ties_to_even_and_escapes():
 def test_dequantized_error_within_half_bound_width(precision):
     rng = np.random.default_rng(8)
     w = 3.7e-3
-    c = rng.uniform(-2100 * w, 2100 * w, 20000)
+    c = rng.uniform(-9000 * w, 9000 * w, 40000)
     if precision == "f32":
         c = c.astype(np.float32)
-    # points near half-integers are the hard cases
+    # points near half-integers are the hard cases, below and above the
+    # float32-exact range of 4096 bins
     c[:2000] = ((rng.integers(-2047, 2047, 2000) + 0.5) * w).astype(c.dtype)
+    c[2000:4000] = ((rng.integers(-4095, 4095, 2000) + 0.5) * w).astype(c.dtype)
+    c[4000:4100] = ((rng.integers(4000, 4200, 100) + 0.5) * w).astype(c.dtype)
     sym, out, _ = quantize.quantize_levels([c], [w], precision)
     back = quantize.dequantize_levels(sym, out, [len(c)], [w], precision)[0]
     err = np.abs(back.astype(np.float64) - c.astype(np.float64))
