@@ -528,6 +528,33 @@ mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void
 
 }  // namespace
 
+cudaMemPool_t workspace_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        uint64_t keep = ~0ull;   // keep freed blocks for reuse instead of unmapping at each sync
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pools[dev] = pool;
+    return pool;
+}
+
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
                            const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
