@@ -166,6 +166,24 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
                                   uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
                                   uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers,
                                   void* stream);
+/* Allocation-free variant of mgard_huffman_encode, for callers that cannot
+ * allocate device memory (code running under an external memory manager, or
+ * where cudaMalloc is not allowed).  The paper has no counterpart.  Same
+ * arguments, results and errors as mgard_huffman_encode; it calls no
+ * allocator.  Its scratch is a fixed device array of 74,320 bytes inside the
+ * library, held by every device that loads the library until the process
+ * exits.  Limits: n <= 2048 * 4096 * 1024 symbols (MGARD_EINVAL beyond).
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the previous call's contents (the call
+ * clears what must start at zero), so calls that overlap on the GPU -- on
+ * different streams or threads -- race and must not be issued. */
+mgard_status mgard_huffman_encode_noalloc(const uint16_t* symbols, uint64_t n,
+                                          const uint8_t* lengths, const int32_t* escapes,
+                                          uint32_t* words, uint64_t words_cap, uint64_t* word_off,
+                                          uint64_t* esc_off, int32_t* outliers,
+                                          uint64_t outliers_cap, uint64_t* nwords,
+                                          uint64_t* noutliers, void* stream);
 /* Decode n symbols (device output) from a stream produced by
  * mgard_huffman_encode; escapes[position] receives each outlier value.
  * Reads never leave the stream: a chunk that runs past its end or holds an

@@ -51,6 +51,10 @@ SIGNATURES = {
     "mgard_huffman_encode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint64, _vp, _vp,
                                             _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_uint64), _vp]),
+    "mgard_huffman_encode_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint64,
+                                                    _vp, _vp, _vp, ctypes.c_uint64,
+                                                    ctypes.POINTER(ctypes.c_uint64),
+                                                    ctypes.POINTER(ctypes.c_uint64), _vp]),
     "mgard_huffman_decode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64, _vp,
                                             ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "mgard_compress_bound": (ctypes.c_size_t, [ctypes.c_int, _c_int64_p, ctypes.c_int]),

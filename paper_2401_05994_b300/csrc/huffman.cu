@@ -12,6 +12,9 @@
 // count pass, an exclusive scan over chunks and a pack pass with one warp
 // per chunk.  Decoding runs one thread per chunk with a 12-bit prefix table
 // in shared memory and canonical first-code search for longer codes.
+#include <map>
+#include <mutex>
+
 #include "huffman.cuh"
 #include "multilevel.cuh"
 
@@ -687,4 +690,116 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
     return MGARD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free encoding.  The paper has no counterpart: this serves callers
+// that cannot allocate device memory at all (code running under an external
+// memory manager or inside a region where cudaMalloc is forbidden).  All
+// scratch lives in one file-scope device array of fixed size; every call on a
+// device shares it.
+namespace {
+
+constexpr uint64_t NOALLOC_MAX_TILES = 2048;   // up to 2048 * 4096 chunks = 8.6e9 symbols
+struct NoAllocScratch {
+    uint32_t codes[DICT];
+    DecodeTables dt;
+    unsigned long long tsum[2 * NOALLOC_MAX_TILES + 2];
+    unsigned long long totals[2];
+    unsigned status;
+};
+
+}  // namespace
+
+// Fixed scratch of sizeof(NoAllocScratch) (74,320 bytes) held by every device
+// that loads the library until the process exits.  In host code the name is
+// only a stand-in for the device address; cudaGetSymbolAddress gives the
+// real one.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+std::map<int, void*> g_noalloc_addr;
+
+// Device address of the scratch on the current device (looked up once per
+// device, with that device current).
+mgard_status noalloc_scratch(NoAllocScratch** out) {
+    int dev = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it == g_noalloc_addr.end()) {
+        void* ptr = nullptr;
+        MGB_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        it = g_noalloc_addr.emplace(dev, ptr).first;
+    }
+    *out = (NoAllocScratch*)it->second;
+    return MGARD_OK;
+}
+
+}  // namespace
+
+}  // namespace mgb
+
+extern "C" mgard_status mgard_huffman_encode_noalloc(
+    const uint16_t* symbols, uint64_t n, const uint8_t* lengths, const int32_t* escapes,
+    uint32_t* words, uint64_t words_cap, uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
+    uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers, void* stream) {
+    using namespace mgb;
+    if ((!symbols && n) || !lengths || !nwords || !noutliers || (n && (!word_off || !esc_off)))
+        return MGARD_EINVAL;
+    if (((uintptr_t)symbols & 15) != 0) {
+        set_error("symbols must be 16-byte aligned");
+        return MGARD_EINVAL;
+    }
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    const uint64_t ntiles = (nchunks + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles > NOALLOC_MAX_TILES) {
+        set_error("mgard_huffman_encode_noalloc: more than 2048 * 4096 * 1024 symbols; use "
+                  "mgard_huffman_encode");
+        return MGARD_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    NoAllocScratch* sc = nullptr;
+    MGB_TRY(noalloc_scratch(&sc));
+    // the scratch keeps the previous call's contents: clear what must start at zero
+    MGB_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(unsigned), st));
+    MGB_CUDA(cudaMemsetAsync(sc->totals, 0, sizeof(sc->totals), st));
+    if (nchunks) {
+        MGB_LAUNCH("k_chunk_count", st,
+                   k_chunk_count<<<grid_for((int64_t)nchunks, ENC_WARPS, 148LL * 16), ENC_WARPS * 32, 0, st>>>(
+                       symbols, n, lengths, word_off, esc_off, nchunks, &sc->status));
+        MGB_LAUNCH("k_scan_sums", st, k_scan_sums<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, sc->tsum));
+    }
+    MGB_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<1, SCAN_T, 0, st>>>(sc->tsum, ntiles, sc->totals));
+    if (nchunks)
+        MGB_LAUNCH("k_scan_apply", st, k_scan_apply<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, sc->tsum));
+    MGB_CUDA(cudaGetLastError());
+    unsigned long long tot[2];
+    unsigned status = 0;
+    MGB_CUDA(cudaMemcpyAsync(tot, sc->totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaMemcpyAsync(&status, &sc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaStreamSynchronize(st));
+    *nwords = tot[0];
+    *noutliers = tot[1];
+    if (status & ST_NOCODE) {
+        set_error("a symbol has no Huffman code");
+        return MGARD_EINVAL;
+    }
+    if (tot[0] > words_cap || tot[1] > outliers_cap) {
+        set_error("encode capacity too small");
+        return MGARD_ECAPACITY;
+    }
+    MGB_LAUNCH("k_tables", st, k_tables<<<1, CB_THREADS, 0, st>>>(lengths, sc->codes, &sc->dt));
+    if (nchunks)
+        MGB_LAUNCH("k_pack", st,
+                   k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
+                       symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, outliers,
+                       nchunks));
+    MGB_CUDA(cudaGetLastError());
+    MGB_CUDA(cudaStreamSynchronize(st));
+    return MGARD_OK;
+}
+
+namespace mgb {
 }  // namespace mgb
