@@ -15,7 +15,10 @@ namespace {
 constexpr int RT = 256;              // threads per block: 8 warps, one x-row per warp
 constexpr int WPB = RT / 32;
 constexpr int64_t ROW_BLOCKS = 148 * 8;
-constexpr int U = 4;                 // elements per lane per batch: loads issued before stores
+// Elements per lane per batch: all loads of a batch are issued before its
+// stores, so a batch covering a whole row puts the entire row in flight.
+// U is chosen per launch from the row length (2, 5, 9 or 17 -> rows of up to
+// 64, 160, 288, 544 elements in one batch).
 
 inline int row_grid(int64_t rows) {
     return (int)std::min<int64_t>(std::max<int64_t>((rows + WPB - 1) / WPB, 1), ROW_BLOCKS);
@@ -57,12 +60,35 @@ __device__ inline Src<T> sources(const AxisT<T>& ax, int i, int m, int mc, bool 
     return s;
 }
 
+inline int pick_u(int64_t nx) {
+    if (nx <= 64) return 2;
+    if (nx <= 160) return 5;
+    if (nx <= 288) return 9;
+    return 17;
+}
+
+template <int V>
+struct UTag {
+    static constexpr int value = V;
+};
+
+// Calls f(UTag<U>{}) with the batch size for row length nx.
+template <typename F>
+void with_u(int64_t nx, F&& f) {
+    switch (pick_u(nx)) {
+        case 2: f(UTag<2>{}); break;
+        case 5: f(UTag<5>{}); break;
+        case 9: f(UTag<9>{}); break;
+        default: f(UTag<17>{}); break;
+    }
+}
+
 #define WARP_ROWS(rows, r)                                                                    \
     for (int64_t r = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); r < (rows);             \
          r += (int64_t)gridDim.x * WPB)
 
 // -- coefficients (decomposition step 1) --------------------------------------
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
                                                Level<T> lv) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
@@ -74,15 +100,15 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const Src<T> sz = sources(lv.ax[1], z, nz, ncz, false);
         const Src<T> sy = sources(lv.ax[2], y, ny, ncy, false);
-        const T* rows[4];
-        T rw[4];
-        int nr = 0;
-        for (int a = 0; a < sz.n; ++a)
-            for (int b = 0; b < sy.n; ++b) {
-                rows[nr] = in + ((int64_t)sz.p[a] * ny + sy.p[b]) * nx;
-                rw[nr] = sz.w[a] * sy.w[b];
-                ++nr;
-            }
+        // up to four source rows (z0|z1) x (y0|y1), fixed slots with warp-uniform use flags
+        const bool zy2 = sy.n == 2, zz2 = sz.n == 2;
+        const T* rows[4] = {in + ((int64_t)sz.p[0] * ny + sy.p[0]) * nx,
+                            in + ((int64_t)sz.p[0] * ny + (zy2 ? sy.p[1] : sy.p[0])) * nx,
+                            in + ((int64_t)(zz2 ? sz.p[1] : sz.p[0]) * ny + sy.p[0]) * nx,
+                            in + ((int64_t)(zz2 ? sz.p[1] : sz.p[0]) * ny + (zy2 ? sy.p[1] : sy.p[0])) * nx};
+        const T rw[4] = {sz.w[0] * sy.w[0], zy2 ? sz.w[0] * sy.w[1] : T(0),
+                         zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
+        const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
         const T* urow = in + r * nx;
         T* orow = out + r * nx;
@@ -99,12 +125,12 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                     if (rowc) continue;
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (k < nr) acc[j] += rw[k] * rows[k][x];
+                        if (use[k]) acc[j] += rw[k] * rows[k][x];
                 } else {
                     const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (k < nr) acc[j] += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
+                        if (use[k]) acc[j] += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
                 }
             }
 #pragma unroll
@@ -119,7 +145,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
 }
 
 // -- recomposition fill ---------------------------------------------------------
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
                                               Level<T> lv) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
@@ -131,15 +157,14 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const Src<T> sz = sources(lv.ax[1], z, nz, ncz, true);
         const Src<T> sy = sources(lv.ax[2], y, ny, ncy, true);
-        const T* rows[4];
-        T rw[4];
-        int nr = 0;
-        for (int a = 0; a < sz.n; ++a)
-            for (int b = 0; b < sy.n; ++b) {
-                rows[nr] = coarse + ((int64_t)sz.p[a] * ncy + sy.p[b]) * ncx;
-                rw[nr] = sz.w[a] * sy.w[b];
-                ++nr;
-            }
+        const bool zy2 = sy.n == 2, zz2 = sz.n == 2;
+        const T* rows[4] = {coarse + ((int64_t)sz.p[0] * ncy + sy.p[0]) * ncx,
+                            coarse + ((int64_t)sz.p[0] * ncy + (zy2 ? sy.p[1] : sy.p[0])) * ncx,
+                            coarse + ((int64_t)(zz2 ? sz.p[1] : sz.p[0]) * ncy + sy.p[0]) * ncx,
+                            coarse + ((int64_t)(zz2 ? sz.p[1] : sz.p[0]) * ncy + (zy2 ? sy.p[1] : sy.p[0])) * ncx};
+        const T rw[4] = {sz.w[0] * sy.w[0], zy2 ? sz.w[0] * sy.w[1] : T(0),
+                         zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
+        const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
         const T* zrow = zin + r * nx;
         T* orow = out + r * nx;
@@ -158,13 +183,13 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (k < nr) v[j] += rw[k] * rows[k][J];
+                        if (use[k]) v[j] += rw[k] * rows[k][J];
                 } else {
                     const int left = (x - 1) >> 1;
                     const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (k < nr) v[j] += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
+                        if (use[k]) v[j] += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
                 }
                 v[j] += zrow[x];
             }
@@ -178,7 +203,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
 }
 
 // -- restriction along x (first pass: z is zero on coarse nodes) -------------------
-template <typename Tin, typename Tout>
+template <typename Tin, typename Tout, int U>
 __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                                                     Tout* __restrict__ out, int nz, int ny,
                                                     int nx, int ncz, int ncy, int ncx,
@@ -214,7 +239,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
 
 // -- restriction along y or z: whole rows combined with per-row weights ----------
 // in: (nouter, m, inner) rows of `nx` elements; out: (nouter, mc, inner).
-template <typename Tin, typename Tout>
+template <typename Tin, typename Tout, int U>
 __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ in,
                                                        Tout* __restrict__ out, int nouter, int m,
                                                        int mc, int inner, int nx,
@@ -227,17 +252,16 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
         const int J = (int)(oj % (uint32_t)mc);
         const int o = (int)(oj / (uint32_t)mc);
         const int f = restrict_center(J, m, mc);
+        // five taps in fixed slots; taps outside the axis get weight 0 and a valid row
         const Tin* src[5];
         Tout w[5];
-        int ns = 0;
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-            const int ip = f - 2 + t;
-            const Tout wt = rw[J * 5 + t];
-            if (ip < 0 || ip >= m || wt == Tout(0)) continue;
-            src[ns] = in + (((int64_t)o * m + ip) * inner + i) * nx;
-            w[ns] = wt;
-            ++ns;
+            int ip = f - 2 + t;
+            const bool ok = ip >= 0 && ip < m;
+            w[t] = ok ? rw[J * 5 + t] : Tout(0);
+            ip = ok ? ip : f;
+            src[t] = in + (((int64_t)o * m + ip) * inner + i) * nx;
         }
         Tout* orow = out + r * nx;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
@@ -248,8 +272,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
                 acc[j] = Tout(0);
                 if (x >= nx) continue;
 #pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    if (k < ns) acc[j] += w[k] * (Tout)src[k][x];
+                for (int k = 0; k < 5; ++k) acc[j] += w[k] * (Tout)src[k][x];
             }
 #pragma unroll
             for (int j = 0; j < U; ++j)
@@ -328,7 +351,7 @@ __device__ inline int64_t row_rank(const QRow& q, int z, int y, bool& rowc) {
     return cnt;
 }
 
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow q, T inv_w,
                                                   double w, uint16_t* __restrict__ sym,
                                                   int32_t* __restrict__ esc,
@@ -384,7 +407,7 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
     if (st) atomicOr(status, st);
 }
 
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__ sym,
                                                     const int32_t* __restrict__ esc, QRow q,
                                                     T wt, double w, T* __restrict__ c) {
@@ -448,7 +471,9 @@ QRow make_qrow(const Plan& p, int l) {
 template <typename T>
 mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st) {
     const Level<T>& lv = p.level<T>(l);
-    MGB_LAUNCH("k3_coeff", st, k3_coeff<T><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(in, out, coarse, lv));
+    with_u(lv.n[3], [&](auto u) {
+        MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(in, out, coarse, lv));
+    });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -457,7 +482,9 @@ template <typename T>
 mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
                         cudaStream_t st) {
     const Level<T>& lv = p.level<T>(l);
-    MGB_LAUNCH("k3_fill", st, k3_fill<T><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(z, coarse, out, lv));
+    with_u(lv.n[3], [&](auto u) {
+        MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(z, coarse, out, lv));
+    });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -472,20 +499,26 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* b0 = (Tw*)t0;
     Tw* b1 = (Tw*)t1;
     // x (always active)
-    MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
-        z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3].rw));
+    with_u(ncx, [&](auto u) {
+        MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
+            z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3].rw));
+    });
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
     Tw* nxt = b1;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
-        MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
-            cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
+        with_u(ncx, [&](auto u) {
+            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
+                cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
+        });
         MGB_CUDA(cudaGetLastError());
         std::swap(cur, nxt);
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
-        MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
-            cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
+        with_u(ncx, [&](auto u) {
+            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
+                cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
+        });
         MGB_CUDA(cudaGetLastError());
         std::swap(cur, nxt);
     }
@@ -507,8 +540,10 @@ mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t
                             cudaStream_t st) {
     const QRow q = make_qrow(p, l);
     const T inv_w = (T)(1.0 / w);
-    MGB_LAUNCH("k3_quantize", st, k3_quantize<T><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
-        c, q, inv_w, w, sym, esc, hist, status));
+    with_u(q.nx, [&](auto u) {
+        MGB_LAUNCH("k3_quantize", st, k3_quantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+            c, q, inv_w, w, sym, esc, hist, status));
+    });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -517,8 +552,10 @@ template <typename T>
 mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               double w, T* c, cudaStream_t st) {
     const QRow q = make_qrow(p, l);
-    MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
-        sym, esc, q, (T)w, w, c));
+    with_u(q.nx, [&](auto u) {
+        MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+            sym, esc, q, (T)w, w, c));
+    });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
