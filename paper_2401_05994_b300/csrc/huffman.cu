@@ -429,28 +429,29 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
          c += (uint64_t)gridDim.x * PACK_WARPS) {
         const uint64_t base = c * CHUNK + lane * 32;
         const int cnt = base >= n ? 0 : (int)min((uint64_t)32, n - base);
-        unsigned s_loc[32];
+        // symbols are read twice (count, then pack); the second read hits L1
+        auto sym_at = [&](int k) -> unsigned { return sym[base + k]; };
         unsigned bits = 0, esc = 0;
         if (cnt == 32) {
             const uint4* v = reinterpret_cast<const uint4*>(sym + base);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint4 w = v[q];
-                s_loc[8 * q + 0] = w.x & 0xFFFF; s_loc[8 * q + 1] = w.x >> 16;
-                s_loc[8 * q + 2] = w.y & 0xFFFF; s_loc[8 * q + 3] = w.y >> 16;
-                s_loc[8 * q + 4] = w.z & 0xFFFF; s_loc[8 * q + 5] = w.z >> 16;
-                s_loc[8 * q + 6] = w.w & 0xFFFF; s_loc[8 * q + 7] = w.w >> 16;
+                const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const unsigned s0 = ww[h] & 0xFFFF, s1 = ww[h] >> 16;
+                    bits += len_s[s0] + len_s[s1];
+                    esc += (s0 == MGARD_ESC) + (s1 == MGARD_ESC);
+                }
             }
         } else {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) s_loc[k] = k < cnt ? sym[base + k] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < cnt) {
-                bits += len_s[s_loc[k]];
-                esc += s_loc[k] == MGARD_ESC;
+            for (int k = 0; k < cnt; ++k) {
+                const unsigned s0 = sym_at(k);
+                bits += len_s[s0];
+                esc += s0 == MGARD_ESC;
             }
+        }
         // warp exclusive scans of bits and escapes
         unsigned ib = bits, ie = esc;
 #pragma unroll
@@ -479,10 +480,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             // time to arrive before its value is consumed
             int64_t pend_at = -1;
             int32_t pend_v = 0;
-#pragma unroll
-            for (int k = 0; k < 32; ++k)
-                if (k < cnt) {
-                    const unsigned s = s_loc[k], len = len_s[s];
+            for (int k = 0; k < cnt; ++k) {
+                    const unsigned s = sym_at(k), len = len_s[s];
                     acc = (acc << len) | code_s[s];
                     nb += (int)len;
                     if (nb >= 32) {

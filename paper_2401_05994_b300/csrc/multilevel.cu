@@ -187,6 +187,96 @@ __global__ void k_solve_lines(Tw* x, int64_t outer_n, int64_t m, int64_t stride,
         }
 }
 
+// Lines along a strided axis, each split into S segments of E elements:
+// thread (lane, warp) owns elements [warp*E, warp*E + E) of line
+// blockIdx.x*32 + lane, so every load and store is coalesced across the 32
+// lines of a warp and a line's S segments run in parallel.  The Thomas sweeps
+// are affine recurrences; each thread composes the map of its segment, the
+// block folds the maps of the preceding (forward) or following (backward)
+// segments through shared memory, and each thread replays its segment.
+template <typename Tw, typename Tdst, int E>
+__global__ void __launch_bounds__(1024) k_solve_seg(Tw* x, int64_t outer_n, int m, int64_t stride,
+                                                    const Tw* __restrict__ sub,
+                                                    const Tw* __restrict__ inv,
+                                                    const Tw* __restrict__ cp, Tdst* dst, Tw sign) {
+    __shared__ Tw sA[32][33], sB[32][33];
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5, S = blockDim.x >> 5;
+    const int k0 = seg * E;
+    for (int64_t outer = blockIdx.y; outer < outer_n; outer += gridDim.y)
+        for (int64_t inner0 = (int64_t)blockIdx.x * 32; inner0 < stride;
+             inner0 += (int64_t)gridDim.x * 32) {
+            const int64_t inner = inner0 + lane;
+            const bool valid = inner < stride;
+            Tw* base = x + outer * m * stride + inner;
+            Tw v[E];
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int g = k0 + k;
+                v[k] = (valid && g < m) ? base[(int64_t)g * stride] : Tw(0);
+            }
+            Tw A = Tw(1), B = Tw(0);
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int g = k0 + k;
+                if (g < m) {
+                    const Tw al = -sub[g] * inv[g];
+                    A = al * A;
+                    B = al * B + v[k] * inv[g];
+                }
+            }
+            sA[seg][lane] = A;
+            sB[seg][lane] = B;
+            __syncthreads();
+            Tw y = Tw(0);
+            for (int s2 = 0; s2 < seg; ++s2) y = sA[s2][lane] * y + sB[s2][lane];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int g = k0 + k;
+                if (g < m) {
+                    y = (v[k] - sub[g] * y) * inv[g];
+                    v[k] = y;
+                }
+            }
+            A = Tw(1);
+            B = Tw(0);
+#pragma unroll
+            for (int k = E - 1; k >= 0; --k) {
+                const int g = k0 + k;
+                if (g < m) {
+                    const Tw ga = -cp[g];
+                    A = ga * A;
+                    B = ga * B + v[k];
+                }
+            }
+            sA[seg][lane] = A;
+            sB[seg][lane] = B;
+            __syncthreads();
+            Tw xx = Tw(0);
+            for (int s2 = S - 1; s2 > seg; --s2) xx = sA[s2][lane] * xx + sB[s2][lane];
+            __syncthreads();
+#pragma unroll
+            for (int k = E - 1; k >= 0; --k) {
+                const int g = k0 + k;
+                if (g < m) {
+                    xx = v[k] - cp[g] * xx;
+                    v[k] = xx;
+                }
+            }
+            if (valid) {
+                Tdst* d = dst ? dst + outer * m * stride + inner : nullptr;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int g = k0 + k;
+                    if (g < m) {
+                        if (d) d[(int64_t)g * stride] = (Tdst)((Tw)d[(int64_t)g * stride] + sign * v[k]);
+                        else base[(int64_t)g * stride] = v[k];
+                    }
+                }
+            }
+        }
+}
+
 // Lines along the contiguous axis, one warp per line held in registers: lane
 // j owns elements [jE, jE+E).  Both Thomas sweeps are first-order affine
 // recurrences (y_k = alpha_k y_{k-1} + beta_k forward, x_k = gamma_k
@@ -558,6 +648,20 @@ cudaMemPool_t workspace_pool() {
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
                            const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
+    // segments of E elements, at most 32 per line (1024-thread blocks); E
+    // stays small enough that a segment and its factors fit in registers
+    const int E = (sizeof(Tw) == 4 && m > 256) ? 16 : 8;
+    if (m <= 32 * E && stride > 1) {
+        const int S = (int)((m + E - 1) / E);
+        dim3 grid((unsigned)std::min<int64_t>((stride + 31) / 32, 1LL << 30),
+                  (unsigned)std::min<int64_t>(outer, 65535), 1);
+        if (E == 8)
+            MGB_LAUNCH("k_solve_seg", st, k_solve_seg<Tw, Tdst, 8><<<grid, 32 * S, 0, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
+        else
+            MGB_LAUNCH("k_solve_seg", st, k_solve_seg<Tw, Tdst, 16><<<grid, 32 * S, 0, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
+        MGB_CUDA(cudaGetLastError());
+        return MGARD_OK;
+    }
     const int bx = 128;
     dim3 grid((unsigned)std::min<int64_t>((stride + bx - 1) / bx, 1LL << 30),
               (unsigned)std::min<int64_t>(outer, 65535), 1);

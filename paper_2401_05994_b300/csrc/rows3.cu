@@ -61,10 +61,9 @@ __device__ inline Src<T> sources(const AxisT<T>& ax, int i, int m, int mc, bool 
 }
 
 inline int pick_u(int64_t nx) {
-    if (nx <= 64) return 2;
-    if (nx <= 160) return 5;
-    if (nx <= 288) return 9;
-    return 17;
+    // larger batches cost registers and occupancy more than they gain in
+    // bytes in flight; the next row is prefetched into L2 instead
+    return nx <= 64 ? 2 : 4;
 }
 
 template <int V>
@@ -75,13 +74,30 @@ struct UTag {
 // Calls f(UTag<U>{}) with the batch size for row length nx.
 template <typename F>
 void with_u(int64_t nx, F&& f) {
-    switch (pick_u(nx)) {
-        case 2: f(UTag<2>{}); break;
-        case 5: f(UTag<5>{}); break;
-        case 9: f(UTag<9>{}); break;
-        default: f(UTag<17>{}); break;
-    }
+    if (pick_u(nx) == 2) f(UTag<2>{});
+    else f(UTag<4>{});
 }
+
+// Ask the TMA unit to pull a row into L2 (no registers are held).  The
+// instruction wants 16-byte boundaries: the start is rounded down (into the
+// previous row, which always exists for a row after the first) and the end is
+// rounded down too, so the range never reaches past the array.
+__device__ inline void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t a = (uintptr_t)p & ~uintptr_t(15);
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~uintptr_t(15);
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
+                     : "memory");
+}
+
+// Lane 0 of a warp prefetches the row the warp will process next.
+#define PREFETCH_NEXT_ROW(base, r, rows, rowlen, esize)                                       \
+    do {                                                                                      \
+        const int64_t nr_ = (r) + (int64_t)gridDim.x * WPB;                                   \
+        if ((threadIdx.x & 31) == 0 && nr_ < (rows))                                          \
+            prefetch_l2((const char*)(base) + nr_ * (int64_t)(rowlen) * (esize),              \
+                        (size_t)(rowlen) * (esize));                                          \
+    } while (0)
 
 #define WARP_ROWS(rows, r)                                                                    \
     for (int64_t r = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); r < (rows);             \
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                          zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
         const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
+        PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* urow = in + r * nx;
         T* orow = out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
@@ -166,6 +183,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                          zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
         const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
+        PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* zrow = zin + r * nx;
         T* orow = out + r * nx;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
@@ -212,6 +230,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
+        PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
         const Tin* irow = in + r * nx;
         Tout* orow = out + r * ncx;
         for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
@@ -368,6 +387,7 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
         const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
         bool rowc;
         const int64_t base = q.sym_off + r * q.nx - row_rank(q, z, y, rowc);
+        PREFETCH_NEXT_ROW(c, r, (int64_t)q.nz * q.ny, q.nx, sizeof(T));
         const T* crow = c + r * q.nx;
         for (int x0 = lane; x0 < q.nx; x0 += 32 * U) {
             T v[U];
