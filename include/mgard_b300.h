@@ -68,6 +68,7 @@ typedef enum { MGARD_ABS = 0, MGARD_REL = 1 } mgard_tolmode;
 /* Huffman stream: chunks of MGARD_CHUNK symbols, each starting on a 32-bit
  * word, bits MSB-first within a word; codes are at most MGARD_LMAX bits. */
 #define MGARD_CHUNK 1024
+#define MGARD_SUB 256
 #define MGARD_LMAX 32
 
 const char* mgard_strerror(mgard_status status);
@@ -155,17 +156,21 @@ mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint
 /* Encode n symbols (device) with code lengths `lengths` (device).  Outputs
  * (device): words (capacity `words_cap` uint32), word_off / esc_off
  * (ceil(n / MGARD_CHUNK) uint64 each: exclusive prefix of per-chunk word
- * counts and escape counts), outliers (escapes gathered in symbol order from
- * `escapes`, which is indexed by symbol position; capacity `outliers_cap`).
+ * counts and escape counts), sub_off (6 uint16 per chunk: the bit offsets
+ * inside the chunk where its sub-chunks of MGARD_SUB symbols 1..3 start, then
+ * the chunk's escapes before each of them; a sub-chunk past the end of the
+ * data starts at the chunk's end), outliers (escapes gathered in symbol order
+ * from `escapes`, which is indexed by symbol position; capacity
+ * `outliers_cap`).
  * *nwords and *noutliers (host) receive the totals; synchronizes the
  * stream.  MGARD_ECAPACITY (totals still returned, nothing packed) if a
  * capacity is short; MGARD_EINVAL if a symbol has no code or `symbols` is
  * not 16-byte aligned (it is read with 16-byte vector loads). */
 mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uint8_t* lengths,
                                   const int32_t* escapes, uint32_t* words, uint64_t words_cap,
-                                  uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
-                                  uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers,
-                                  void* stream);
+                                  uint64_t* word_off, uint64_t* esc_off, uint16_t* sub_off,
+                                  int32_t* outliers, uint64_t outliers_cap, uint64_t* nwords,
+                                  uint64_t* noutliers, void* stream);
 /* Allocation-free variant of mgard_huffman_encode, for callers that cannot
  * allocate device memory (code running under an external memory manager, or
  * where cudaMalloc is not allowed).  The paper has no counterpart.  Same
@@ -181,18 +186,20 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
 mgard_status mgard_huffman_encode_noalloc(const uint16_t* symbols, uint64_t n,
                                           const uint8_t* lengths, const int32_t* escapes,
                                           uint32_t* words, uint64_t words_cap, uint64_t* word_off,
-                                          uint64_t* esc_off, int32_t* outliers,
+                                          uint64_t* esc_off, uint16_t* sub_off, int32_t* outliers,
                                           uint64_t outliers_cap, uint64_t* nwords,
                                           uint64_t* noutliers, void* stream);
 /* Decode n symbols (device output) from a stream produced by
- * mgard_huffman_encode; escapes[position] receives each outlier value.
+ * mgard_huffman_encode (every sub-chunk is decoded independently from its
+ * recorded start); escapes[position] receives each outlier value.
  * Reads never leave the stream: a chunk that runs past its end or holds an
  * invalid code gives MGARD_ECORRUPT (synchronizes the stream).  `symbols`
  * must be 16-byte aligned (MGARD_EINVAL otherwise). */
 mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                  const uint64_t* esc_off, const uint16_t* sub_off,
                                   const uint8_t* lengths, uint64_t n, const int32_t* outliers,
-                                  uint64_t noutliers, const uint64_t* esc_off, uint16_t* symbols,
-                                  int32_t* escapes, void* stream);
+                                  uint64_t noutliers, uint16_t* symbols, int32_t* escapes,
+                                  void* stream);
 
 /* ---- High-level API (Listing 1: compress / decompress) -----------------
  * Upper bound on the compressed size in bytes for a shape. */

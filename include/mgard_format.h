@@ -10,6 +10,9 @@
  *   lengths   [dict] uint8            Huffman code length per symbol
  *   word_off  [nchunks] uint64        exclusive prefix of words per chunk
  *   esc_off   [nchunks] uint64        exclusive prefix of escapes per chunk
+ *   sub_off   [nchunks][6] uint16     per chunk: bit offsets (inside the chunk) of
+ *                                     its sub-chunks 1..3 (256 symbols each), then the
+ *                                     escapes of the chunk before each of them
  *   outliers  [noutliers] int32       escaped quantized values, symbol order
  *   words     [nwords] uint32         Huffman payload
  *
@@ -23,7 +26,7 @@
 #include <stdint.h>
 
 #define MGARD_MAGIC "MGARDB3"
-#define MGARD_FORMAT_VERSION 1u
+#define MGARD_FORMAT_VERSION 2u
 
 typedef struct {
     char magic[8];        /* "MGARDB3\0" */
@@ -47,6 +50,7 @@ typedef struct {
     uint64_t off_lengths;
     uint64_t off_word_off;
     uint64_t off_esc_off;
+    uint64_t off_sub_off;
     uint64_t off_outliers;
     uint64_t off_words;
     uint64_t total_bytes;

@@ -21,7 +21,10 @@ Stream layout
     Symbols are cut into chunks of ``CHUNK = 1024``.  Each chunk starts on a
     32-bit word boundary; code bits go MSB-first into each word.  Per chunk
     the stream records the exclusive prefix of word counts and of escape
-    (outlier) counts.
+    (outlier) counts, and, for its sub-chunks of ``SUB = 256`` symbols after
+    the first, the bit offset inside the chunk where each starts and the
+    number of escapes before it in the chunk (six uint16 per chunk), so the
+    four sub-chunks of a chunk can be decoded independently.
 """
 from __future__ import annotations
 
@@ -29,6 +32,7 @@ import numpy as np
 
 LMAX = 32
 CHUNK = 1024
+SUB = 256
 
 
 def _lengths_once(freq: np.ndarray) -> np.ndarray:
@@ -122,7 +126,17 @@ def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
         esc_off[1:] = np.cumsum(esc_cnt)[:-1]
     total = int(chunk_words.sum()) if nchunks else 0
     words = np.zeros(total + 1, dtype=np.uint64)   # one spare word for spill
+    sub_off = np.zeros((nchunks, 6), dtype=np.uint16)
     if n:
+        # offsets of the first symbol of sub-chunks 1..3 inside their chunk;
+        # a sub-chunk past the end of the data starts at the chunk's end
+        csum_bits = np.concatenate([[0], np.cumsum(ln)])
+        csum_esc = np.concatenate([[0], np.cumsum(symbols == esc_symbol)])
+        starts = np.arange(nchunks) * chunk
+        for k in range(1, chunk // SUB):
+            pos = np.minimum(starts + k * SUB, n)
+            sub_off[:, k - 1] = csum_bits[pos] - csum_bits[starts]
+            sub_off[:, 2 + k] = csum_esc[pos] - csum_esc[starts]
         # bit offset of each symbol inside its chunk
         csum = np.cumsum(ln)
         start_of_chunk = np.concatenate([[0], csum])[cid * chunk]
@@ -137,19 +151,22 @@ def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
         lo = val & np.uint64(0xFFFFFFFF)
         np.bitwise_or.at(words, w, hi)
         np.bitwise_or.at(words, w + 1, lo)
-    return words[:total].astype(np.uint32), word_off, esc_off
+    return words[:total].astype(np.uint32), word_off, esc_off, sub_off
 
 
-def decode(words, word_off, lengths, n: int, chunk: int = CHUNK) -> np.ndarray:
-    """Bit-by-bit canonical decoding (slow; small inputs only)."""
+def decode(words, word_off, lengths, n: int, chunk: int = CHUNK, sub_off=None) -> np.ndarray:
+    """Bit-by-bit canonical decoding (slow; small inputs only).  With
+    ``sub_off`` every sub-chunk starts from its recorded bit offset."""
     lengths = np.asarray(lengths, dtype=np.int64)
     codes = canonical_codes(lengths)
     table = {(int(lengths[s]), int(codes[s])): s for s in np.nonzero(lengths)[0]}
     out = np.zeros(n, dtype=np.uint16)
     words = np.asarray(words, dtype=np.uint64)
     for c in range((n + chunk - 1) // chunk):
-        bit = int(word_off[c]) * 32
         for i in range(c * chunk, min(n, (c + 1) * chunk)):
+            k = (i - c * chunk) // SUB
+            if i == c * chunk or (sub_off is not None and (i - c * chunk) % SUB == 0):
+                bit = int(word_off[c]) * 32 + (int(sub_off[c, k - 1]) if k else 0)
             code, ln = 0, 0
             while True:
                 wv = int(words[bit >> 5])

@@ -25,10 +25,10 @@ def compress(u: np.ndarray, tol: float, s: float = math.inf, relative: bool = Tr
     v = multilevel.decompose(u, max_levels)
     symbols, outliers, hist = quantize.quantize(v, widths, max_levels, precision)
     lengths = huffman.code_lengths(hist)
-    words, word_off, esc_off = huffman.encode(symbols, lengths)
+    words, word_off, esc_off, sub_off = huffman.encode(symbols, lengths)
     return dict(shape=u.shape, L=h.L, tol_abs=tol_abs, widths=widths, s=s,
                 symbols=symbols, outliers=outliers, hist=hist, lengths=lengths,
-                words=words, word_off=word_off, esc_off=esc_off,
+                words=words, word_off=word_off, esc_off=esc_off, sub_off=sub_off,
                 precision=precision, max_levels=max_levels)
 
 
@@ -45,7 +45,7 @@ def decompress(c, symbols=None) -> np.ndarray:
 
 def compressed_bytes(c) -> int:
     """Size of the payload, code-length table, chunk offsets and outliers."""
-    return (4 * len(c["words"]) + len(c["lengths"]) + 16 * len(c["word_off"])
+    return (4 * len(c["words"]) + len(c["lengths"]) + 28 * len(c["word_off"])
             + 4 * len(c["outliers"]))
 
 

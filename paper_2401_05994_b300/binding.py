@@ -49,14 +49,14 @@ SIGNATURES = {
                                         _c_double_p, _vp, _vp]),
     "mgard_huffman_codebook": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mgard_huffman_encode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint64, _vp, _vp,
-                                            _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                            _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_uint64), _vp]),
     "mgard_huffman_encode_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint64,
-                                                    _vp, _vp, _vp, ctypes.c_uint64,
+                                                    _vp, _vp, _vp, _vp, ctypes.c_uint64,
                                                     ctypes.POINTER(ctypes.c_uint64),
                                                     ctypes.POINTER(ctypes.c_uint64), _vp]),
-    "mgard_huffman_decode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64, _vp,
-                                            ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+    "mgard_huffman_decode": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, ctypes.c_uint64, _vp,
+                                            ctypes.c_uint64, _vp, _vp, _vp]),
     "mgard_compress_bound": (ctypes.c_size_t, [ctypes.c_int, _c_int64_p, ctypes.c_int]),
     "mgard_compress": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
@@ -234,33 +234,35 @@ def huffman_codebook(hist: torch.Tensor):
 
 def huffman_encode(sym: torch.Tensor, lengths: torch.Tensor, esc: torch.Tensor):
     """Returns (words int32 view of uint32, word_off int64, esc_off int64,
-    outliers int32)."""
+    sub_off uint16 [nchunks, 6], outliers int32)."""
     _require_cuda(sym)
     n = sym.numel()
     nchunks = (n + CHUNK - 1) // CHUNK
     dev = sym.device
     word_off = torch.empty(max(nchunks, 1), dtype=torch.int64, device=dev)
     esc_off = torch.empty(max(nchunks, 1), dtype=torch.int64, device=dev)
+    sub_off = torch.zeros((max(nchunks, 1), 6), dtype=torch.uint16, device=dev)
     cap_w = n + nchunks + 1
     words = torch.empty(cap_w, dtype=torch.int32, device=dev)
     outl = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     nw = ctypes.c_uint64()
     no = ctypes.c_uint64()
     _check(lib().mgard_huffman_encode(_ptr(sym), n, _ptr(lengths), _ptr(esc), _ptr(words), cap_w,
-                                      _ptr(word_off), _ptr(esc_off), _ptr(outl), max(n, 1),
-                                      ctypes.byref(nw), ctypes.byref(no), _stream()))
-    return words[:nw.value], word_off[:nchunks], esc_off[:nchunks], outl[:no.value]
+                                      _ptr(word_off), _ptr(esc_off), _ptr(sub_off), _ptr(outl),
+                                      max(n, 1), ctypes.byref(nw), ctypes.byref(no), _stream()))
+    return (words[:nw.value], word_off[:nchunks], esc_off[:nchunks], sub_off[:nchunks],
+            outl[:no.value])
 
 
-def huffman_decode(words, word_off, lengths, n: int, outliers, esc_off):
+def huffman_decode(words, word_off, esc_off, sub_off, lengths, n: int, outliers):
     _require_cuda(words)
     dev = words.device
     sym = torch.empty(max(n, 1), dtype=torch.uint16, device=dev)
     esc = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
     nout = outliers.numel()
     outliers = outliers if nout else torch.zeros(1, dtype=torch.int32, device=dev)
-    _check(lib().mgard_huffman_decode(_ptr(words), words.numel(), _ptr(word_off), _ptr(lengths), n,
-                                      _ptr(outliers), nout, _ptr(esc_off),
+    _check(lib().mgard_huffman_decode(_ptr(words), words.numel(), _ptr(word_off), _ptr(esc_off),
+                                      _ptr(sub_off), _ptr(lengths), n, _ptr(outliers), nout,
                                       _ptr(sym), _ptr(esc), _stream()))
     return sym[:n], esc[:n]
 

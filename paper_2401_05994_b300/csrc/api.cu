@@ -65,7 +65,7 @@ mgard_status status_to_error(unsigned st) {
 
 // Layout of the sections after the header.
 struct Sections {
-    size_t widths, lengths, word_off, esc_off, outliers, words, total;
+    size_t widths, lengths, word_off, esc_off, sub_off, outliers, words, total;
 };
 
 Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords) {
@@ -79,6 +79,8 @@ Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords) {
     o = align16(o + 8 * nchunks);
     s.esc_off = o;
     o = align16(o + 8 * nchunks);
+    s.sub_off = o;
+    o = align16(o + 2 * SUBREC * nchunks);
     s.outliers = o;
     o = align16(o + 4 * nout);
     s.words = o;
@@ -171,7 +173,8 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
     MGB_TRY(lengths.alloc(DICT, st));
     MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
     MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
-    MGB_TRY(huffman_codebook(hist.as<unsigned long long>(), lengths.as<uint8_t>(), nullptr, st));
+    MGB_TRY(huffman_codebook(hist.as<unsigned long long>(), lengths.as<uint8_t>(), nullptr, st,
+                             (uint64_t)N >= (uint64_t(1) << 32)));
     MGB_TRY(huffman_tables(lengths.as<uint8_t>(), codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
     const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
     MGB_TRY(offs.alloc(16 * nchunks + 16, st));
@@ -212,6 +215,7 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
     h.off_lengths = sec.lengths;
     h.off_word_off = sec.word_off;
     h.off_esc_off = sec.esc_off;
+    h.off_sub_off = sec.sub_off;
     h.off_outliers = sec.outliers;
     h.off_words = sec.words;
     h.total_bytes = sec.total;
@@ -265,7 +269,7 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
     }
     MGB_TRY(huffman_pack(sym.as<uint16_t>(), N, lengths.as<uint8_t>(), codes.as<uint32_t>(),
                          word_off, esc_off, esc.as<int32_t>(), (uint32_t*)(dd + sec.words),
-                         (int32_t*)(dd + sec.outliers), st));
+                         (uint16_t*)(dd + sec.sub_off), (int32_t*)(dd + sec.outliers), st));
     if (!out_dev) MGB_CUDA(cudaMemcpyAsync(dst, dd, sec.total, cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     *out = dst;
@@ -306,7 +310,8 @@ mgard_status read_header(const void* in, size_t in_bytes, bool in_dev, mgard_hea
     if (h->noutliers > n || h->nwords > n + h->nchunks) return bad("section sizes");
     Sections s = layout((int)h->nlevels, h->nchunks, h->noutliers, h->nwords);
     if (h->off_widths != s.widths || h->off_lengths != s.lengths || h->off_word_off != s.word_off ||
-        h->off_esc_off != s.esc_off || h->off_outliers != s.outliers || h->off_words != s.words ||
+        h->off_esc_off != s.esc_off || h->off_sub_off != s.sub_off ||
+        h->off_outliers != s.outliers || h->off_words != s.words ||
         h->total_bytes != s.total)
         return bad("section offsets");
     if (s.total > in_bytes) return bad("truncated buffer");
@@ -344,7 +349,8 @@ mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::ve
     const uint8_t* lengths = (const uint8_t*)(din + h.off_lengths);
     MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
     MGB_TRY(huffman_decode((const uint32_t*)(din + h.off_words), h.nwords,
-                           (const uint64_t*)(din + h.off_word_off), dt.as<DecodeTables>(), N,
+                           (const uint64_t*)(din + h.off_word_off),
+                           (const uint16_t*)(din + h.off_sub_off), dt.as<DecodeTables>(), N,
                            (const int32_t*)(din + h.off_outliers), h.noutliers,
                            (const uint64_t*)(din + h.off_esc_off), sym.as<uint16_t>(),
                            esc.as<int32_t>(), stat.as<unsigned>(), st));
@@ -555,10 +561,11 @@ mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint
 
 mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uint8_t* lengths,
                                   const int32_t* escapes, uint32_t* words, uint64_t words_cap,
-                                  uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
-                                  uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers,
-                                  void* stream) {
-    if ((!symbols && n) || !lengths || !nwords || !noutliers || (n && (!word_off || !esc_off)))
+                                  uint64_t* word_off, uint64_t* esc_off, uint16_t* sub_off,
+                                  int32_t* outliers, uint64_t outliers_cap, uint64_t* nwords,
+                                  uint64_t* noutliers, void* stream) {
+    if ((!symbols && n) || !lengths || !nwords || !noutliers ||
+        (n && (!word_off || !esc_off || !sub_off)))
         return MGARD_EINVAL;
     if (((uintptr_t)symbols & 15) != 0) {
         set_error("symbols must be 16-byte aligned");
@@ -587,16 +594,17 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
     MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
     MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
     MGB_TRY(huffman_pack(symbols, n, lengths, codes.as<uint32_t>(), word_off, esc_off, escapes,
-                         words, outliers, st));
+                         words, sub_off, outliers, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     return MGARD_OK;
 }
 
 mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                  const uint64_t* esc_off, const uint16_t* sub_off,
                                   const uint8_t* lengths, uint64_t n, const int32_t* outliers,
-                                  uint64_t noutliers, const uint64_t* esc_off, uint16_t* symbols,
-                                  int32_t* escapes, void* stream) {
-    if (!lengths || (n && (!words || !word_off || !esc_off || !symbols || !escapes)))
+                                  uint64_t noutliers, uint16_t* symbols, int32_t* escapes,
+                                  void* stream) {
+    if (!lengths || (n && (!words || !word_off || !esc_off || !sub_off || !symbols || !escapes)))
         return MGARD_EINVAL;
     if (((uintptr_t)symbols & 15) != 0) {
         set_error("symbols must be 16-byte aligned");
@@ -609,8 +617,8 @@ mgard_status mgard_huffman_decode(const uint32_t* words, uint64_t nwords, const 
     MGB_TRY(stat.alloc(4, st));
     MGB_CUDA(cudaMemsetAsync(stat.p, 0, 4, st));
     MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
-    MGB_TRY(huffman_decode(words, nwords, word_off, dt.as<DecodeTables>(), n, outliers, noutliers,
-                           esc_off, symbols, escapes, stat.as<unsigned>(), st));
+    MGB_TRY(huffman_decode(words, nwords, word_off, sub_off, dt.as<DecodeTables>(), n, outliers,
+                           noutliers, esc_off, symbols, escapes, stat.as<unsigned>(), st));
     unsigned status = 0;
     MGB_CUDA(cudaMemcpyAsync(&status, stat.p, 4, cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));

@@ -53,8 +53,44 @@ struct CodebookSmem {
     int maxlen;
 };
 
+template <typename W>
+__device__ void two_queue_merge(CodebookSmem& S, int n) {
+    const W INF = (W)~0ull;
+    W* iw = reinterpret_cast<W*>(S.iw);
+    int li = 0, ii = 0, nint = 0;
+    W L0 = (W)(S.keys[0] >> 12), L1 = n > 1 ? (W)(S.keys[1] >> 12) : INF;
+    W I0 = INF, I1 = INF;
+    for (int k = 0; k < n - 1; ++k) {
+        int ids[2];
+        W ws[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (L0 <= I0) {
+                ids[t] = li;
+                ws[t] = L0;
+                ++li;
+                L0 = L1;
+                L1 = li + 1 < n ? (W)(S.keys[li + 1] >> 12) : INF;
+            } else {
+                ids[t] = n + ii;
+                ws[t] = I0;
+                ++ii;
+                I0 = I1;
+                I1 = ii + 1 < nint ? iw[ii + 1] : INF;
+            }
+        }
+        const W wnew = ws[0] + ws[1];
+        iw[nint] = wnew;
+        S.parent[ids[0]] = (short)(n + nint);
+        S.parent[ids[1]] = (short)(n + nint);
+        ++nint;
+        if (nint - ii == 1) I0 = wnew;
+        else if (nint - ii == 2) I1 = wnew;
+    }
+}
+
 __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long long* __restrict__ hist,
-                                                         uint8_t* __restrict__ lengths) {
+                                                         uint8_t* __restrict__ lengths, int wide) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CodebookSmem& S = *reinterpret_cast<CodebookSmem*>(smem_raw);
     const int tid = threadIdx.x;
@@ -87,39 +123,11 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
         }
         // two-queue merge (serial): leaves 0..n-1, internal nodes n..2n-2.  The
         // next two heads of both queues live in registers and the shared-memory
-        // loads behind them are issued a selection ahead of their use.
+        // loads behind them are issued a selection ahead of their use.  Weights
+        // are 32-bit when every sum fits (fewer than 2^32 symbols in total).
         if (tid == 0) {
-            const unsigned long long INF = ~0ull;
-            int li = 0, ii = 0, nint = 0;
-            unsigned long long L0 = S.keys[0] >> 12, L1 = n > 1 ? S.keys[1] >> 12 : INF;
-            unsigned long long I0 = INF, I1 = INF;
-            for (int k = 0; k < n - 1; ++k) {
-                int ids[2];
-                unsigned long long ws[2];
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    if (L0 <= I0) {
-                        ids[t] = li;
-                        ws[t] = L0;
-                        ++li;
-                        L0 = L1;
-                        L1 = li + 1 < n ? S.keys[li + 1] >> 12 : INF;
-                    } else {
-                        ids[t] = n + ii;
-                        ws[t] = I0;
-                        ++ii;
-                        I0 = I1;
-                        I1 = ii + 1 < nint ? S.iw[ii + 1] : INF;
-                    }
-                }
-                const unsigned long long wnew = ws[0] + ws[1];
-                S.iw[nint] = wnew;
-                S.parent[ids[0]] = (short)(n + nint);
-                S.parent[ids[1]] = (short)(n + nint);
-                ++nint;
-                if (nint - ii == 1) I0 = wnew;
-                else if (nint - ii == 2) I1 = wnew;
-            }
+            if (wide) two_queue_merge<unsigned long long>(S, n);
+            else two_queue_merge<uint32_t>(S, n);
         }
         __syncthreads();
         // depths by pointer jumping: dep[i] = distance to anc[i]
@@ -408,13 +416,19 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint64_t* a, uint64_t* b,
         }
 }
 
-constexpr int PACK_WARPS = 4;
+constexpr int PACK_WARPS = 6;   // 45 KB of static shared memory per block
 
+// One warp per chunk, in four rounds of 256 symbols: lane j packs symbols
+// [8j, 8j+8) of the round (one 16-byte load).  Lane bit offsets come from a
+// warp scan; bits accumulate MSB-first in a 64-bit register and the words a
+// lane shares with its neighbours (its first and last) are merged with OR in
+// a shared-memory copy of the chunk.
 __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     const uint16_t* __restrict__ sym, uint64_t n, const uint8_t* __restrict__ lengths,
     const uint32_t* __restrict__ codes, const uint64_t* __restrict__ word_off,
     const uint64_t* __restrict__ esc_off, const int32_t* __restrict__ escapes,
-    uint32_t* __restrict__ words, int32_t* __restrict__ outliers, uint64_t nchunks) {
+    uint32_t* __restrict__ words, uint16_t* __restrict__ sub_off, int32_t* __restrict__ outliers,
+    uint64_t nchunks) {
     __shared__ uint8_t len_s[DICT];
     __shared__ uint32_t code_s[DICT];
     __shared__ uint32_t buf[PACK_WARPS][CHUNK + 1];
@@ -427,68 +441,67 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     uint32_t* wb = buf[warp];
     for (uint64_t c = blockIdx.x * (uint64_t)PACK_WARPS + warp; c < nchunks;
          c += (uint64_t)gridDim.x * PACK_WARPS) {
-        const uint64_t base = c * CHUNK + lane * 32;
-        const int cnt = base >= n ? 0 : (int)min((uint64_t)32, n - base);
-        // symbols are read twice (count, then pack); the second read hits L1
-        auto sym_at = [&](int k) -> unsigned { return sym[base + k]; };
-        unsigned bits = 0, esc = 0;
-        if (cnt == 32) {
-            const uint4* v = reinterpret_cast<const uint4*>(sym + base);
+        const uint64_t cbase = c * CHUNK;
+        const int ccnt = (int)min((uint64_t)CHUNK, n - cbase);
+        const uint64_t wo = word_off[c];
+        const uint64_t eo = esc_off[c];
+        for (int k = lane; k <= CHUNK; k += 32) wb[k] = 0;
+        __syncwarp();
+        unsigned bit0 = 0, esc0 = 0;   // chunk-relative offsets of the current round
+        int64_t pend_at = -1;          // escape values are stored one escape late
+        int32_t pend_v = 0;
+        for (int rd = 0; rd < NSUB; ++rd) {
+            if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
+                sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
+                sub_off[c * SUBREC + (NSUB - 1) + rd - 1] = (uint16_t)esc0;
+            }
+            const int first = rd * SUB + lane * 8;
+            const int cnt = max(0, min(8, ccnt - first));
+            unsigned sv[8];
+            if (cnt == 8) {
+                const uint4 v = *reinterpret_cast<const uint4*>(sym + cbase + first);
+                sv[0] = v.x & 0xFFFF; sv[1] = v.x >> 16; sv[2] = v.y & 0xFFFF; sv[3] = v.y >> 16;
+                sv[4] = v.z & 0xFFFF; sv[5] = v.z >> 16; sv[6] = v.w & 0xFFFF; sv[7] = v.w >> 16;
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 w = v[q];
-                const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+                for (int k = 0; k < 8; ++k) sv[k] = k < cnt ? sym[cbase + first + k] : 0;
+            }
+            unsigned bits = 0, esc = 0;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const unsigned s0 = ww[h] & 0xFFFF, s1 = ww[h] >> 16;
-                    bits += len_s[s0] + len_s[s1];
-                    esc += (s0 == MGARD_ESC) + (s1 == MGARD_ESC);
+            for (int k = 0; k < 8; ++k)
+                if (k < cnt) {
+                    bits += len_s[sv[k]];
+                    esc += sv[k] == MGARD_ESC;
+                }
+            unsigned ib = bits, ie = esc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned vb = __shfl_up_sync(0xffffffffu, ib, o);
+                const unsigned ve = __shfl_up_sync(0xffffffffu, ie, o);
+                if (lane >= o) {
+                    ib += vb;
+                    ie += ve;
                 }
             }
-        } else {
-            for (int k = 0; k < cnt; ++k) {
-                const unsigned s0 = sym_at(k);
-                bits += len_s[s0];
-                esc += s0 == MGARD_ESC;
-            }
-        }
-        // warp exclusive scans of bits and escapes
-        unsigned ib = bits, ie = esc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned vb = __shfl_up_sync(0xffffffffu, ib, o);
-            const unsigned ve = __shfl_up_sync(0xffffffffu, ie, o);
-            if (lane >= o) {
-                ib += vb;
-                ie += ve;
-            }
-        }
-        const unsigned total = __shfl_sync(0xffffffffu, ib, 31);
-        unsigned bpos = ib - bits, epos = ie - esc;
-        const unsigned nw = (total + 31) / 32;
-        for (unsigned k = lane; k <= nw && k <= CHUNK; k += 32) wb[k] = 0;
-        __syncwarp();
-        const uint64_t eo = esc_off[c];
-        // bits accumulate MSB-first in a 64-bit register; a word shared with a
-        // neighbouring lane (the first and the last one) is merged with an OR
-        {
+            const unsigned bpos = bit0 + ib - bits;
+            unsigned epos = esc0 + ie - esc;
+            bit0 += __shfl_sync(0xffffffffu, ib, 31);
+            esc0 += __shfl_sync(0xffffffffu, ie, 31);
             unsigned w = bpos >> 5;
-            int nb = (int)(bpos & 31);      // bits of the current word already owned by the left lane
+            int nb = (int)(bpos & 31);
             unsigned long long acc = 0;
-            bool first = true;
-            // escape values are stored one escape late, so each load has
-            // time to arrive before its value is consumed
-            int64_t pend_at = -1;
-            int32_t pend_v = 0;
-            for (int k = 0; k < cnt; ++k) {
-                    const unsigned s = sym_at(k), len = len_s[s];
+            bool firstw = true;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < cnt) {
+                    const unsigned s = sv[k], len = len_s[s];
                     acc = (acc << len) | code_s[s];
                     nb += (int)len;
                     if (nb >= 32) {
                         const uint32_t word = (uint32_t)(acc >> (nb - 32));
-                        if (first) atomicOr(&wb[w], word);
+                        if (firstw) atomicOr(&wb[w], word);
                         else wb[w] = word;
-                        first = false;
+                        firstw = false;
                         ++w;
                         nb -= 32;
                         acc &= (nb ? ((1ull << nb) - 1) : 0ull);
@@ -496,15 +509,16 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                     if (s == MGARD_ESC) {
                         if (pend_at >= 0) outliers[pend_at] = pend_v;
                         pend_at = (int64_t)(eo + epos++);
-                        pend_v = escapes[base + k];
+                        pend_v = escapes[cbase + first + k];
                     }
                 }
-            if (pend_at >= 0) outliers[pend_at] = pend_v;
             if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
+            __syncwarp();
         }
+        if (pend_at >= 0) outliers[pend_at] = pend_v;
         __syncwarp();
-        const uint64_t wo = word_off[c];
-        for (unsigned k = lane; k < nw; k += 32) words[wo + k] = wb[k];
+        const unsigned total_words = (bit0 + 31) / 32;
+        for (unsigned k = lane; k < total_words; k += 32) words[wo + k] = wb[k];
         __syncwarp();
     }
 }
@@ -514,9 +528,9 @@ constexpr int DEC_THREADS = 128;
 
 __global__ void __launch_bounds__(DEC_THREADS) k_decode(
     const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
-    const DecodeTables* __restrict__ gdt, uint64_t n, const int32_t* __restrict__ outliers,
-    uint64_t noutliers, const uint64_t* __restrict__ esc_off, uint16_t* __restrict__ sym,
-    int32_t* __restrict__ escapes, unsigned* status, uint64_t nchunks) {
+    const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
+    const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
+    uint16_t* __restrict__ sym, int32_t* __restrict__ escapes, unsigned* status, uint64_t nchunks) {
     __shared__ DecodeTables T;
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(gdt);
@@ -524,31 +538,45 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
         for (int k = threadIdx.x; k < (int)(sizeof(DecodeTables) / 4); k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // one thread per sub-chunk of SUB symbols
+    const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t c = gid / NSUB;
+    const int sc = (int)(gid % NSUB);
     if (c >= nchunks) return;
+    const uint64_t first = c * CHUNK + (uint64_t)sc * SUB;
+    if (first >= n) return;
     if (!T.valid) {
         atomicOr(status, ST_CORRUPT);
         return;
     }
-    const uint64_t start = word_off[c];
-    const uint64_t end = c + 1 < nchunks ? word_off[c + 1] : nwords;
-    uint64_t e = esc_off[c];
-    const uint64_t e_end = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
-    if (start > end || end > nwords || e > e_end || e_end > noutliers) {
+    const int cnt = (int)min((uint64_t)SUB, n - first);
+    // bit and escape ranges of this sub-chunk, validated against its chunk
+    const uint64_t cw0 = word_off[c];
+    const uint64_t cw1 = c + 1 < nchunks ? word_off[c + 1] : nwords;
+    const uint64_t ce0 = esc_off[c];
+    const uint64_t ce1 = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
+    if (cw0 > cw1 || cw1 > nwords || ce0 > ce1 || ce1 > noutliers) {
         atomicOr(status, ST_CORRUPT);
         return;
     }
-    const uint64_t first = c * CHUNK;
-    const int cnt = (int)min((uint64_t)CHUNK, n - first);
+    const uint16_t* so = sub_off + c * SUBREC;
+    const uint64_t bstart = cw0 * 32 + (sc ? so[sc - 1] : 0);
+    const uint64_t endbit = sc + 1 < NSUB ? cw0 * 32 + so[sc] : cw1 * 32;
+    uint64_t e = ce0 + (sc ? so[NSUB - 1 + sc - 1] : 0);
+    const uint64_t e_end = sc + 1 < NSUB ? ce0 + so[NSUB - 1 + sc] : ce1;
+    if (bstart > endbit || endbit > cw1 * 32 || e > e_end || e_end > ce1) {
+        atomicOr(status, ST_CORRUPT);
+        return;
+    }
+    const uint64_t end = cw1;   // word loads stay inside the chunk
     auto load = [&](uint64_t k) -> uint64_t { return k < end ? (uint64_t)words[k] : 0ull; };
-    uint64_t wi = start;
+    uint64_t wi = bstart >> 5;
+    unsigned off = (unsigned)(bstart & 31);
     uint64_t win = (load(wi) << 32) | load(wi + 1);
     // the next four words are loaded ahead of use
     uint32_t q0 = (uint32_t)load(wi + 2), q1 = (uint32_t)load(wi + 3), q2 = (uint32_t)load(wi + 4),
              q3 = (uint32_t)load(wi + 5);
-    unsigned off = 0;
-    uint64_t bit = start * 32;
-    const uint64_t endbit = end * 32;
+    uint64_t bit = bstart;
     uint32_t pk[4] = {0, 0, 0, 0};
     bool ok = true;
     int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
@@ -619,7 +647,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
 }  // namespace
 
 mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool wide) {
     const size_t smem = sizeof(CodebookSmem);
     static bool attr = false;
     if (!attr) {
@@ -627,7 +655,7 @@ mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, 
                                       (int)smem));
         attr = true;
     }
-    MGB_LAUNCH("k_codebook", st, k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths));
+    MGB_LAUNCH("k_codebook", st, k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths, wide ? 1 : 0));
     MGB_CUDA(cudaGetLastError());
     (void)codes;
     return MGARD_OK;
@@ -666,24 +694,24 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
 
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
-                          const int32_t* escapes, uint32_t* words, int32_t* outliers,
-                          cudaStream_t st) {
+                          const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
+                          int32_t* outliers, cudaStream_t st) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
-        sym, n, lengths, codes, word_off, esc_off, escapes, words, outliers, nchunks));
+    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 4), PACK_WARPS * 32, 0, st>>>(
+        sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
 
 mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
-                            const DecodeTables* dt, uint64_t n, const int32_t* outliers,
-                            uint64_t noutliers, const uint64_t* esc_off, uint16_t* sym,
-                            int32_t* escapes, unsigned* status, cudaStream_t st) {
+                            const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
+                            const int32_t* outliers, uint64_t noutliers, const uint64_t* esc_off,
+                            uint16_t* sym, int32_t* escapes, unsigned* status, cudaStream_t st) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    const int grid = (int)((nchunks + DEC_THREADS - 1) / DEC_THREADS);
-    MGB_LAUNCH("k_decode", st, k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, dt, n, outliers, noutliers,
+    const int grid = (int)((nchunks * NSUB + DEC_THREADS - 1) / DEC_THREADS);
+    MGB_LAUNCH("k_decode", st, k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
                                           esc_off, sym, escapes, status, nchunks));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -742,10 +770,11 @@ mgard_status noalloc_scratch(NoAllocScratch** out) {
 
 extern "C" mgard_status mgard_huffman_encode_noalloc(
     const uint16_t* symbols, uint64_t n, const uint8_t* lengths, const int32_t* escapes,
-    uint32_t* words, uint64_t words_cap, uint64_t* word_off, uint64_t* esc_off, int32_t* outliers,
-    uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers, void* stream) {
+    uint32_t* words, uint64_t words_cap, uint64_t* word_off, uint64_t* esc_off, uint16_t* sub_off,
+    int32_t* outliers, uint64_t outliers_cap, uint64_t* nwords, uint64_t* noutliers, void* stream) {
     using namespace mgb;
-    if ((!symbols && n) || !lengths || !nwords || !noutliers || (n && (!word_off || !esc_off)))
+    if ((!symbols && n) || !lengths || !nwords || !noutliers ||
+        (n && (!word_off || !esc_off || !sub_off)))
         return MGARD_EINVAL;
     if (((uintptr_t)symbols & 15) != 0) {
         set_error("symbols must be 16-byte aligned");
@@ -793,8 +822,8 @@ extern "C" mgard_status mgard_huffman_encode_noalloc(
     if (nchunks)
         MGB_LAUNCH("k_pack", st,
                    k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
-                       symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, outliers,
-                       nchunks));
+                       symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, sub_off,
+                       outliers, nchunks));
     MGB_CUDA(cudaGetLastError());
     MGB_CUDA(cudaStreamSynchronize(st));
     return MGARD_OK;

@@ -6,6 +6,9 @@
 namespace mgb {
 
 constexpr int LUT_BITS = 12;
+constexpr int SUB = 256;                 // symbols per independently decodable sub-chunk
+constexpr int NSUB = MGARD_CHUNK / SUB;  // sub-chunks per chunk
+constexpr int SUBREC = 2 * (NSUB - 1);   // uint16 offsets recorded per chunk
 
 constexpr uint32_t LUT_LONG = 0x80000000u;
 
@@ -22,9 +25,10 @@ struct DecodeTables {
     uint32_t valid;                     // 0 if the lengths violate the Kraft inequality
 };
 
-// Code lengths and canonical codes from a histogram (single CTA).
+// Code lengths from a histogram (single CTA).  `wide` selects 64-bit merge
+// weights (needed when the histogram totals 2^32 symbols or more).
 mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
-                              cudaStream_t st);
+                              cudaStream_t st, bool wide = true);
 // Canonical codes and decode tables from code lengths (single CTA).
 mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
                             cudaStream_t st);
@@ -33,15 +37,15 @@ mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTable
 mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                            uint64_t* word_off, uint64_t* esc_off, unsigned long long* totals,
                            unsigned* status, cudaStream_t st);
-// Pass 2: pack codes and gather escapes.
+// Pass 2: pack codes, record sub-chunk offsets and gather escapes.
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
-                          const int32_t* escapes, uint32_t* words, int32_t* outliers,
-                          cudaStream_t st);
+                          const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
+                          int32_t* outliers, cudaStream_t st);
 // Decoding with bounds checks (ST_CORRUPT on failure).
 mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
-                            const DecodeTables* dt, uint64_t n, const int32_t* outliers,
-                            uint64_t noutliers, const uint64_t* esc_off, uint16_t* sym,
-                            int32_t* escapes, unsigned* status, cudaStream_t st);
+                            const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
+                            const int32_t* outliers, uint64_t noutliers, const uint64_t* esc_off,
+                            uint16_t* sym, int32_t* escapes, unsigned* status, cudaStream_t st);
 
 }  // namespace mgb

@@ -4,12 +4,12 @@ import struct
 
 import numpy as np
 
-HEADER_FMT = "<8sIIII4qdddIIIIQQQQQQQQQQQ"
+HEADER_FMT = "<8sIIII4qdddIIIIQQQQQQQQQQQQ"
 HEADER_SIZE = struct.calcsize(HEADER_FMT)
 FIELDS = ["magic", "version", "dtype", "ndim", "nlevels", "s0", "s1", "s2", "s3", "s", "tol",
           "tol_abs", "mode", "dict", "chunk", "reserved", "nsymbols", "nchunks", "nwords",
           "noutliers", "off_widths", "off_lengths", "off_word_off", "off_esc_off",
-          "off_outliers", "off_words", "total_bytes"]
+          "off_sub_off", "off_outliers", "off_words", "total_bytes"]
 
 
 def parse(buf: bytes):
@@ -22,6 +22,7 @@ def parse(buf: bytes):
     n = h["nchunks"]
     sec["word_off"] = b[h["off_word_off"]:h["off_word_off"] + 8 * n].view(np.uint64)
     sec["esc_off"] = b[h["off_esc_off"]:h["off_esc_off"] + 8 * n].view(np.uint64)
+    sec["sub_off"] = b[h["off_sub_off"]:h["off_sub_off"] + 12 * n].view(np.uint16).reshape(n, 6)
     sec["outliers"] = b[h["off_outliers"]:h["off_outliers"] + 4 * h["noutliers"]].view(np.int32)
     sec["words"] = b[h["off_words"]:h["off_words"] + 4 * h["nwords"]].view(np.uint32)
     return h, sec

@@ -153,14 +153,15 @@ def test_encode_decode_bit_exact(n):
     esc = np.zeros(n, dtype=np.int32)
     esc[s == 0] = rng.integers(-10 ** 6, 10 ** 6, int((s == 0).sum()))
     st = torch.from_numpy(s.astype(np.int32)).to(torch.uint16).to(DEV)
-    words, woff, eoff, outl = binding.huffman_encode(st, torch.from_numpy(L).to(DEV),
-                                                     torch.from_numpy(esc).to(DEV))
-    rw, rwo, reo = huffman.encode(s, L)
+    words, woff, eoff, sub, outl = binding.huffman_encode(st, torch.from_numpy(L).to(DEV),
+                                                          torch.from_numpy(esc).to(DEV))
+    rw, rwo, reo, rsub = huffman.encode(s, L)
     assert np.array_equal(words.cpu().numpy().view(np.uint32), rw)
     assert np.array_equal(woff.cpu().numpy().astype(np.uint64), rwo)
     assert np.array_equal(eoff.cpu().numpy().astype(np.uint64), reo)
+    assert np.array_equal(sub.cpu().numpy().astype(np.uint16), rsub)
     assert np.array_equal(outl.cpu().numpy(), esc[s == 0])
-    ds, de = binding.huffman_decode(words, woff, torch.from_numpy(L).to(DEV), n, outl, eoff)
+    ds, de = binding.huffman_decode(words, woff, eoff, sub, torch.from_numpy(L).to(DEV), n, outl)
     d = ds.cpu().numpy()
     assert np.array_equal(d, s)
     assert np.array_equal(de.cpu().numpy()[d == 0], esc[s == 0])
@@ -196,9 +197,10 @@ def test_compress_round_trip_meets_bound(case, s):
     sym, esc, hist = binding.quantize(v, sec["widths"])
     rl = huffman.code_lengths(hist.cpu().numpy())
     assert np.array_equal(sec["lengths"], rl)
-    rw, rwo, reo = huffman.encode(sym.cpu().numpy(), rl)
+    rw, rwo, reo, rsub = huffman.encode(sym.cpu().numpy(), rl)
     assert np.array_equal(sec["words"], rw)
     assert np.array_equal(sec["word_off"], rwo) and np.array_equal(sec["esc_off"], reo)
+    assert np.array_equal(sec["sub_off"], rsub)
     sn = sym.cpu().numpy()
     assert np.array_equal(sec["outliers"], esc.cpu().numpy()[sn == 0])
     # widths equal the oracle's for the stored tolerance
@@ -279,6 +281,12 @@ def test_corrupt_buffers_rejected():
     k[h["off_lengths"]:h["off_lengths"] + 4096] = 1
     with pytest.raises(binding.MgardError) as e:
         binding.decompress(k)
+    assert e.value.status == 7
+    # a sub-chunk start beyond its chunk
+    so = buf.copy()
+    so[h["off_sub_off"]:h["off_sub_off"] + 2] = 0xFF
+    with pytest.raises(binding.MgardError) as e:
+        binding.decompress(so)
     assert e.value.status == 7
     # chunk offsets past the payload
     o = buf.copy()

@@ -74,7 +74,7 @@ def test_single_symbol():
     hist[5] = 100
     L = huffman.code_lengths(hist)
     assert L[5] == 1 and L.sum() == 1
-    words, off, esc = huffman.encode(np.full(100, 5), L)
+    words, off, esc, sub = huffman.encode(np.full(100, 5), L)
     assert len(words) == 4 and np.all(words == 0)
 
 
@@ -98,7 +98,7 @@ def test_golden_small_example():
     for kv in rec["codes"]:
         s, v = kv.split(":")
         assert C[int(s)] == int(v)
-    words, off, _ = huffman.encode(np.array([int(t) for t in rec["stream"]]), L)
+    words, off, _, _ = huffman.encode(np.array([int(t) for t in rec["stream"]]), L)
     assert [int(w) for w in words] == [int(x, 16) for x in rec["words"]]
 
 
@@ -109,10 +109,16 @@ def test_round_trip_with_chunks(n):
     sym[::97] = 0
     hist = np.bincount(sym, minlength=4096)
     L = huffman.code_lengths(hist)
-    words, off, esc = huffman.encode(sym, L)
+    words, off, esc, sub = huffman.encode(sym, L)
     assert len(off) == (n + 1023) // 1024
     if n:
         assert np.array_equal(huffman.decode(words, off, L, n), sym)
+        # every sub-chunk decodes from its recorded start
+        assert np.array_equal(huffman.decode(words, off, L, n, sub_off=sub), sym)
+        for c in range(len(off)):
+            seg = sym[c * 1024:(c + 1) * 1024]
+            for k in range(1, 4):
+                assert sub[c, 2 + k] == int(np.sum(seg[:k * 256] == 0))
         # escape prefix counts
         per_chunk = [int(np.sum(sym[c * 1024:(c + 1) * 1024] == 0)) for c in range(len(off))]
         assert esc.tolist() == list(np.concatenate([[0], np.cumsum(per_chunk)[:-1]]))

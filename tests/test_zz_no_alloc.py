@@ -40,17 +40,19 @@ def _encode(fn, sym, lengths, esc):
     words = torch.full((cap,), -1, dtype=torch.int32, device=DEV)
     woff = torch.full((nchunks,), -1, dtype=torch.int64, device=DEV)
     eoff = torch.full((nchunks,), -1, dtype=torch.int64, device=DEV)
+    sub = torch.zeros((nchunks, 6), dtype=torch.uint16, device=DEV)
     outl = torch.full((n,), -1, dtype=torch.int32, device=DEV)
     nw, no = ctypes.c_uint64(), ctypes.c_uint64()
     st = fn(ctypes.c_void_p(sym.data_ptr()), n, ctypes.c_void_p(lengths.data_ptr()),
             ctypes.c_void_p(esc.data_ptr()), ctypes.c_void_p(words.data_ptr()), cap,
             ctypes.c_void_p(woff.data_ptr()), ctypes.c_void_p(eoff.data_ptr()),
-            ctypes.c_void_p(outl.data_ptr()), n, ctypes.byref(nw), ctypes.byref(no),
+            ctypes.c_void_p(sub.data_ptr()), ctypes.c_void_p(outl.data_ptr()), n,
+            ctypes.byref(nw), ctypes.byref(no),
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0, binding.lib().mgard_last_error()
     torch.cuda.synchronize()
     return (words[:nw.value].cpu().numpy(), woff.cpu().numpy(), eoff.cpu().numpy(),
-            outl[:no.value].cpu().numpy(), nw.value, no.value)
+            outl[:no.value].cpu().numpy(), nw.value, no.value, sub.cpu().numpy())
 
 
 def test_noalloc_encode_matches_regular_encode_twice():
@@ -61,13 +63,14 @@ def test_noalloc_encode_matches_regular_encode_twice():
         ref = _encode(L.mgard_huffman_encode, sym, lengths, esc)
         got = _encode(L.mgard_huffman_encode_noalloc, sym, lengths, esc)
         assert ref[4] == got[4] and ref[5] == got[5]
-        for a, b in zip(ref[:4], got[:4]):
+        for a, b in zip(ref[:4] + ref[6:], got[:4] + got[6:]):
             assert np.array_equal(a, b)
         # and the stream decodes back to the symbols
         words = torch.from_numpy(got[0]).to(DEV)
-        ds, _ = binding.huffman_decode(words, torch.from_numpy(got[1]).to(DEV), lengths, n,
-                                       torch.from_numpy(got[3]).to(DEV),
-                                       torch.from_numpy(got[2]).to(DEV))
+        ds, _ = binding.huffman_decode(words, torch.from_numpy(got[1]).to(DEV),
+                                       torch.from_numpy(got[2]).to(DEV),
+                                       torch.from_numpy(got[6].astype(np.int32)).to(torch.uint16).to(DEV),
+                                       lengths, n, torch.from_numpy(got[3]).to(DEV))
         assert torch.equal(ds.to(torch.int32), sym.to(torch.int32))
 
 
@@ -78,7 +81,7 @@ def test_noalloc_encode_rejects_oversized_input():
     p = ctypes.c_void_p(buf.data_ptr())
     nw, no = ctypes.c_uint64(), ctypes.c_uint64()
     too_many = 2048 * 4096 * 1024 + 1
-    st = L.mgard_huffman_encode_noalloc(p, too_many, p, p, p, 0, p, p, p, 0, ctypes.byref(nw),
+    st = L.mgard_huffman_encode_noalloc(p, too_many, p, p, p, 0, p, p, p, p, 0, ctypes.byref(nw),
                                         ctypes.byref(no), None)
     assert st == 1
     assert b"mgard_huffman_encode" in L.mgard_last_error()
