@@ -245,7 +245,9 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             auto cp = coarse_positions(m);
             int64_t mc = (int64_t)cp.size();
             std::vector<int> fcls(m), cbefore(m);
-            std::vector<double> wl(m, 0.0), wr(m, 0.0);
+            // coarse nodes carry the weights (1, 0) so interpolation can be
+            // evaluated without branching: u(i) = 1 * u(i) + 0 * u(i)
+            std::vector<double> wl(m, 1.0), wr(m, 0.0);
             int64_t J = 0;
             for (int64_t i = 0; i < m; ++i) {
                 cbefore[i] = (int)J;

@@ -78,6 +78,14 @@ void with_u(int64_t nx, F&& f) {
     else f(UTag<4>{});
 }
 
+// Kernels that keep few values per element afford batches of 8.
+template <typename F>
+void with_u8(int64_t nx, F&& f) {
+    if (nx <= 64) f(UTag<2>{});
+    else if (nx <= 160) f(UTag<4>{});
+    else f(UTag<8>{});
+}
+
 // Ask the TMA unit to pull a row into L2 (no registers are held).  The
 // instruction wants 16-byte boundaries: the start is rounded down (into the
 // previous row, which always exists for a row after the first) and the end is
@@ -138,17 +146,12 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 acc[j] = T(0);
                 if (x >= nx) continue;
                 u[j] = urow[x];
-                if (is_coarse(x, nx)) {
-                    if (rowc) continue;
+                // coarse x: neighbours x, x with weights (1, 0); new x: x-1, x+1
+                const int d = is_coarse(x, nx) ? 0 : 1;
+                const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (use[k]) acc[j] += rw[k] * rows[k][x];
-                } else {
-                    const T wl = wlx[x], wr = wrx[x];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (use[k]) acc[j] += rw[k] * (wl * rows[k][x - 1] + wr * rows[k][x + 1]);
-                }
+                for (int k = 0; k < 4; ++k)
+                    if (use[k]) acc[j] += rw[k] * (wl * rows[k][x - d] + wr * rows[k][x + d]);
             }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -193,23 +196,16 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                 const int x = x0 + 32 * j;
                 v[j] = T(0);
                 if (x >= nx) continue;
-                if (is_coarse(x, nx)) {
-                    const int J = coarse_index(x, nx, ncx);
-                    if (rowc) {
-                        v[j] = rows[0][J];
-                        continue;
-                    }
+                // coarse x: coarse index J twice with weights (1, 0); new x: J, J+1
+                const bool cx = is_coarse(x, nx);
+                const int jl = cx ? coarse_index(x, nx, ncx) : (x - 1) >> 1;
+                const int jr = cx ? jl : jl + 1;
+                const T wl = wlx[x], wr = wrx[x];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (use[k]) v[j] += rw[k] * rows[k][J];
-                } else {
-                    const int left = (x - 1) >> 1;
-                    const T wl = wlx[x], wr = wrx[x];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (use[k]) v[j] += rw[k] * (wl * rows[k][left] + wr * rows[k][left + 1]);
-                }
-                v[j] += zrow[x];
+                for (int k = 0; k < 4; ++k)
+                    if (use[k]) v[j] += rw[k] * (wl * rows[k][jl] + wr * rows[k][jr]);
+                // z vanishes on coarse nodes of the coarse grid's rows
+                if (!(rowc && cx)) v[j] += zrow[x];
             }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -519,7 +515,7 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* b0 = (Tw*)t0;
     Tw* b1 = (Tw*)t1;
     // x (always active)
-    with_u(ncx, [&](auto u) {
+    with_u8(ncx, [&](auto u) {
         MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
             z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3].rw));
     });
@@ -527,7 +523,7 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* cur = b0;
     Tw* nxt = b1;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
-        with_u(ncx, [&](auto u) {
+        with_u8(ncx, [&](auto u) {
             MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
                 cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
         });
@@ -535,7 +531,7 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
         std::swap(cur, nxt);
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
-        with_u(ncx, [&](auto u) {
+        with_u8(ncx, [&](auto u) {
             MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
                 cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
         });
@@ -560,7 +556,7 @@ mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t
                             cudaStream_t st) {
     const QRow q = make_qrow(p, l);
     const T inv_w = (T)(1.0 / w);
-    with_u(q.nx, [&](auto u) {
+    with_u8(q.nx, [&](auto u) {
         MGB_LAUNCH("k3_quantize", st, k3_quantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
             c, q, inv_w, w, sym, esc, hist, status));
     });
@@ -572,7 +568,7 @@ template <typename T>
 mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               double w, T* c, cudaStream_t st) {
     const QRow q = make_qrow(p, l);
-    with_u(q.nx, [&](auto u) {
+    with_u8(q.nx, [&](auto u) {
         MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
             sym, esc, q, (T)w, w, c));
     });
