@@ -7,8 +7,8 @@
 //    lengths over LMAX repeat on max(1, count >> k); one used symbol -> 1 bit;
 //  * canonical codes, consecutive in (length, symbol) order;
 //  * chunks of CHUNK symbols, each starting on a 32-bit word, MSB-first.
-// The codebook is built by one CTA (bitonic sorts and pointer jumping are
-// parallel, the queue merge itself is a short serial loop).  Encoding is a
+// The codebook is built by one CTA: bitonic sort of the leaves, the queue
+// merge in doubling rounds (see round_merge) and depths by pointer jumping.  Encoding is a
 // count pass, an exclusive scan over chunks and a pack pass with one warp
 // per chunk.  Decoding runs one thread per chunk with a 12-bit prefix table
 // in shared memory and canonical first-code search for longer codes.
@@ -44,48 +44,127 @@ __device__ void bitonic_sort(unsigned long long* keys, int n) {
 }
 
 struct CodebookSmem {
-    unsigned long long keys[DICT];    // sorted leaves: (weight << 12) | symbol
-    unsigned long long iw[DICT];      // internal node weights
+    unsigned long long keys[DICT];        // sorted leaves: (weight << 12) | symbol
+    unsigned long long iw[DICT];          // internal node weights in creation order
+    unsigned long long pw[2 * DICT];      // one round's picks: weight ...
+    short pid[2 * DICT];                  // ... and node id (leaf j or n + internal k)
     short parent[2 * DICT];
     short anc[2 * DICT];
     unsigned short dep[2 * DICT];
+    unsigned long long pend_w;            // a pick still waiting for its partner
+    int pend_id;
+    int li, ii, m, K;                     // leaves / internals consumed, picks made, internals made
+    unsigned long long bound;
     int n;
     int maxlen;
 };
 
+// First index in [lo, hi) whose weight exceeds w (leaf weights when `leaf`).
 template <typename W>
-__device__ void two_queue_merge(CodebookSmem& S, int n) {
+__device__ __forceinline__ int upper_w(const CodebookSmem& S, const W* I, bool leaf, int lo,
+                                       int hi, W w) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const W v = leaf ? (W)(S.keys[mid] >> 12) : I[mid];
+        if (v <= w) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// First index in [lo, hi) of the internal queue whose weight is not below w.
+template <typename W>
+__device__ __forceinline__ int lower_int(const W* I, int lo, int hi, W w) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (I[mid] < w) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Two-queue Huffman merge, computed in rounds by the whole block.
+//
+// The picks of the serial algorithm (smaller head first, the leaf on equal
+// weight) form one sorted sequence P, the stable merge of the sorted leaves
+// with the internal nodes, where internal k = P[2k] + P[2k+1].  If P[m] is
+// the smallest head, every internal made from picks m, m+1, ... weighs at
+// least 2 P[m]; so every node already present with weight <= 2 P[m] is
+// picked before any of them (leaf first and FIFO on ties), in the order of
+// the merge of the two present runs.  A round takes that whole run at once
+// (ranks by binary search), then pairs consecutive picks into new internal
+// nodes.  The bound at least doubles each round, so there are at most
+// (bits of the total weight) + 1 rounds, and the tree is the serial one.
+template <typename W>
+__device__ void round_merge(CodebookSmem& S, int n) {
     const W INF = (W)~0ull;
-    W* iw = reinterpret_cast<W*>(S.iw);
-    int li = 0, ii = 0, nint = 0;
-    W L0 = (W)(S.keys[0] >> 12), L1 = n > 1 ? (W)(S.keys[1] >> 12) : INF;
-    W I0 = INF, I1 = INF;
-    for (int k = 0; k < n - 1; ++k) {
-        int ids[2];
-        W ws[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            if (L0 <= I0) {
-                ids[t] = li;
-                ws[t] = L0;
-                ++li;
-                L0 = L1;
-                L1 = li + 1 < n ? (W)(S.keys[li + 1] >> 12) : INF;
-            } else {
-                ids[t] = n + ii;
-                ws[t] = I0;
-                ++ii;
-                I0 = I1;
-                I1 = ii + 1 < nint ? iw[ii + 1] : INF;
+    W* I = reinterpret_cast<W*>(S.iw);
+    W* pw = reinterpret_cast<W*>(S.pw);
+    const int tid = threadIdx.x;
+    const int total = 2 * n - 2;
+    if (tid == 0) {
+        S.li = S.ii = S.m = S.K = 0;
+    }
+    __syncthreads();
+    for (int round = 0; round < 2 * 64 + 4; ++round) {
+        if (tid == 0 && S.m < total) {
+            int li = S.li, ii = S.ii, m = S.m, K = S.K;
+            const W hl = li < n ? (W)(S.keys[li] >> 12) : INF;
+            const W hi = ii < K ? I[ii] : INF;
+            const W head = hl <= hi ? hl : hi;
+            S.bound = head > INF / 2 ? (unsigned long long)INF : (unsigned long long)(2 * head);
+            if (m & 1) {   // complete the pair left open by the previous round
+                int id;
+                if (hl <= hi) id = li++;
+                else id = n + ii++;
+                I[K] = (W)S.pend_w + head;
+                S.parent[S.pend_id] = (short)(n + K);
+                S.parent[id] = (short)(n + K);
+                ++K;
+                ++m;
             }
+            S.li = li;
+            S.ii = ii;
+            S.m = m;
+            S.K = K;
         }
-        const W wnew = ws[0] + ws[1];
-        iw[nint] = wnew;
-        S.parent[ids[0]] = (short)(n + nint);
-        S.parent[ids[1]] = (short)(n + nint);
-        ++nint;
-        if (nint - ii == 1) I0 = wnew;
-        else if (nint - ii == 2) I1 = wnew;
+        __syncthreads();
+        const int li = S.li, ii = S.ii, m = S.m, K = S.K;
+        if (m >= total) break;
+        const W B = (W)S.bound;
+        const int lend = upper_w<W>(S, I, true, li, n, B);
+        const int iend = upper_w<W>(S, I, false, ii, K, B);
+        const int r = (lend - li) + (iend - ii);
+        for (int j = li + tid; j < lend; j += blockDim.x) {
+            const W w = (W)(S.keys[j] >> 12);
+            const int rank = (j - li) + (lower_int<W>(I, ii, iend, w) - ii);
+            pw[rank] = w;
+            S.pid[rank] = (short)j;
+        }
+        for (int i = ii + tid; i < iend; i += blockDim.x) {
+            const W w = I[i];
+            const int rank = (i - ii) + (upper_w<W>(S, I, true, li, lend, w) - li);
+            pw[rank] = w;
+            S.pid[rank] = (short)(n + i);
+        }
+        __syncthreads();
+        for (int p = tid; p < r / 2; p += blockDim.x) {
+            const int a = S.pid[2 * p], b = S.pid[2 * p + 1];
+            I[K + p] = pw[2 * p] + pw[2 * p + 1];
+            S.parent[a] = (short)(n + K + p);
+            S.parent[b] = (short)(n + K + p);
+        }
+        if (tid == 0) {
+            if (r & 1) {
+                S.pend_w = (unsigned long long)pw[r - 1];
+                S.pend_id = S.pid[r - 1];
+            }
+            S.li = lend;
+            S.ii = iend;
+            S.m = m + r;
+            S.K = K + r / 2;
+        }
+        __syncthreads();
     }
 }
 
@@ -106,14 +185,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
                 S.keys[s] = KEY_NONE;
             }
         }
-        if (tid == 0) S.maxlen = 0;
+        if (tid == 0) {
+            S.maxlen = 0;
+            S.n = 0;
+        }
         __syncthreads();
         bitonic_sort(S.keys, DICT);   // ends with a barrier
-        if (tid == 0) {
-            int n = 0;
-            while (n < DICT && S.keys[n] != KEY_NONE) ++n;
-            S.n = n;
-        }
+        // number of used symbols: the last used key sits before the first KEY_NONE
+        for (int i = tid; i < DICT; i += blockDim.x)
+            if (S.keys[i] != KEY_NONE && (i + 1 == DICT || S.keys[i + 1] == KEY_NONE)) S.n = i + 1;
         __syncthreads();
         const int n = S.n;
         if (n == 0) return;
@@ -121,15 +201,8 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
             if (tid == 0) lengths[S.keys[0] & 0xFFF] = 1;
             return;
         }
-        // two-queue merge (serial): leaves 0..n-1, internal nodes n..2n-2.  The
-        // next two heads of both queues live in registers and the shared-memory
-        // loads behind them are issued a selection ahead of their use.  Weights
-        // are 32-bit when every sum fits (fewer than 2^32 symbols in total).
-        if (tid == 0) {
-            if (wide) two_queue_merge<unsigned long long>(S, n);
-            else two_queue_merge<uint32_t>(S, n);
-        }
-        __syncthreads();
+        if (wide) round_merge<unsigned long long>(S, n);
+        else round_merge<uint32_t>(S, n);
         // depths by pointer jumping: dep[i] = distance to anc[i]
         const int root = 2 * n - 2;
         for (int i = tid; i <= root; i += blockDim.x) {
@@ -148,11 +221,13 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
             }
             __syncthreads();
             c = 0;
+            bool done = true;
             for (int i = tid; i <= root; i += blockDim.x, ++c) {
                 S.dep[i] = nd[c];
                 S.anc[i] = na[c];
+                done = done && na[c] == root;
             }
-            __syncthreads();
+            if (__syncthreads_and(done)) break;
         }
         int mx = 0;
         for (int i = tid; i < n; i += blockDim.x) mx = max(mx, (int)S.dep[i]);

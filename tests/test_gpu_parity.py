@@ -128,10 +128,29 @@ def _hist_cases():
     h[[0, 7]] = [5, 5]
     out.append(h)
     out.append(np.ones(4096, dtype=np.int64))
+    # many equal weights: ties between leaves and internal nodes everywhere
+    h = np.zeros(4096, dtype=np.int64)
+    sel = rng.choice(4096, 4000, replace=False)
+    h[sel] = rng.integers(1, 4, 4000)
+    out.append(h)
+    h = np.zeros(4096, dtype=np.int64)
+    sel = rng.choice(4096, 3000, replace=False)
+    h[sel] = 2 ** rng.integers(0, 20, 3000)
+    out.append(h)
+    # total above 2^32 (64-bit merge weights)
+    h = np.zeros(4096, dtype=np.int64)
+    h[rng.choice(4096, 64, replace=False)] = rng.integers(2 ** 28, 2 ** 30, 64)
+    out.append(h)
+    # shaped like a quantized field: a sharp peak at the centre and a long tail of ones
+    k = np.arange(4096)
+    h = np.floor(1.0e8 * np.exp(-np.abs(k - 2048) / 6.0)).astype(np.int64)
+    h[h == 0] = 1
+    h[0] = 777
+    out.append(h)
     return out
 
 
-@pytest.mark.parametrize("case", range(10))
+@pytest.mark.parametrize("case", range(14))
 def test_codebook_matches_oracle(case):
     h = _hist_cases()[case]
     lengths, codes = binding.huffman_codebook(torch.from_numpy(h).to(DEV))
