@@ -175,7 +175,7 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
  * allocate device memory (code running under an external memory manager, or
  * where cudaMalloc is not allowed).  The paper has no counterpart.  Same
  * arguments, results and errors as mgard_huffman_encode; it calls no
- * allocator.  Its scratch is a fixed device array of 74,320 bytes inside the
+ * allocator.  Its scratch is a fixed device array of 90,704 bytes inside the
  * library, held by every device that loads the library until the process
  * exits.  Limits: n <= 2048 * 4096 * 1024 symbols (MGARD_EINVAL beyond).
  * The first call on a device looks up that array's device address (with the
@@ -224,6 +224,32 @@ mgard_status mgard_compress(const void* field, int ndim, const int64_t* shape, m
  * Synchronizes the stream before returning. */
 mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
                               int out_preallocated, void* stream);
+/* ---- Batched compression ---------------------------------------------------
+ * Many fields or timesteps of possibly different shapes in one call; the
+ * paper has no batched call, this serves workloads of many small fields,
+ * where launch latency on the coarse levels would dominate.
+ *   fields[i]   device pointer to field i (ndims[i], shapes[i], all `dtype`)
+ *   outs[i]     device buffer of caps[i] bytes, 16-byte aligned; a buffer of
+ *               mgard_compress_bound bytes always suffices
+ *   out_bytes[i] (host) receives the compressed size of field i (the size
+ *               needed when field i failed with MGARD_ECAPACITY)
+ *   statuses[i] (host, may be NULL) receives the status of field i
+ * tol, s, mode as for mgard_compress (one setting for the whole batch).
+ * The fields run on internal streams forked from `stream` (and joined back
+ * into it), so small fields overlap.  With MGARD_BATCH_GRAPH the whole batch
+ * is captured into one CUDA graph the first time and replayed by later calls
+ * with identical arguments (same pointers, shapes and settings); the
+ * library keeps the graph and its workspaces until mgard_release_plans.
+ * Every output is byte-identical to mgard_compress of the same field.
+ * Synchronizes `stream` once, at the end.  Returns MGARD_OK when every
+ * field succeeded, else the status of the first failing field. */
+#define MGARD_BATCH_GRAPH 1
+mgard_status mgard_compress_batch(int n, const void* const* fields, const int* ndims,
+                                  const int64_t* const* shapes, mgard_dtype dtype, double tol,
+                                  double s, mgard_tolmode mode, void* const* outs,
+                                  const size_t* caps, size_t* out_bytes, mgard_status* statuses,
+                                  int flags, void* stream);
+
 /* Read the header of a compressed buffer (host or device pointer). */
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
                         mgard_dtype* dtype, double* tol_abs, int* nlevels);

@@ -16,6 +16,7 @@
 #include "../../include/mgard_format.h"
 #include "huffman.cuh"
 #include "multilevel.cuh"
+#include "pipeline.cuh"
 #include "quantize.cuh"
 
 namespace mgb {
@@ -33,7 +34,6 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 mgard_status check_dtype(mgard_dtype d) {
     if (d != MGARD_F32 && d != MGARD_F64) {
@@ -61,32 +61,6 @@ mgard_status status_to_error(unsigned st) {
         return MGARD_EINVAL;
     }
     return MGARD_OK;
-}
-
-// Layout of the sections after the header.
-struct Sections {
-    size_t widths, lengths, word_off, esc_off, sub_off, outliers, words, total;
-};
-
-Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords) {
-    Sections s;
-    size_t o = align16(sizeof(mgard_header));
-    s.widths = o;
-    o = align16(o + 8 * (size_t)(L + 1));
-    s.lengths = o;
-    o = align16(o + DICT);
-    s.word_off = o;
-    o = align16(o + 8 * nchunks);
-    s.esc_off = o;
-    o = align16(o + 8 * nchunks);
-    s.sub_off = o;
-    o = align16(o + 2 * SUBREC * nchunks);
-    s.outliers = o;
-    o = align16(o + 4 * nout);
-    s.words = o;
-    o = align16(o + 4 * nwords);
-    s.total = o;
-    return s;
 }
 
 double s_norm_from_levels(const std::vector<double>& E, double s) {
@@ -124,7 +98,12 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
                            mgard_tolmode mode, void** out, size_t* out_bytes, int prealloc,
                            cudaStream_t st) {
     const int64_t N = p.total();
-    const int L = p.L;
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    const Sections fx = layout(p.L, nchunks, 0, 0);
+    if (prealloc && (!out || !*out || !out_bytes)) {
+        set_error("preallocated output missing");
+        return MGARD_EINVAL;
+    }
     DevBuf inbuf;
     const T* din = (const T*)field;
     if (!field_dev) {
@@ -132,148 +111,67 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
         MGB_CUDA(cudaMemcpyAsync(inbuf.p, field, N * sizeof(T), cudaMemcpyHostToDevice, st));
         din = inbuf.as<T>();
     }
-    Pyramid<T> py;
-    MGB_TRY(py.alloc(p, st));
-    DevBuf top;
-    MGB_TRY(top.alloc(N * sizeof(T), st));
-    double tol_abs = tol;
-    bool decomposed = false;
-    {
-        unsigned status = 0;
-        double m = 0.0;
-        MGB_TRY(max_abs<T>(din, nullptr, N, &m, &status, st));
-        MGB_TRY(status_to_error(status));
-        if (mode == MGARD_REL) {
-            double nrm = m;
-            if (!std::isinf(s)) {
-                std::vector<double> E(L + 1, 0.0);
-                MGB_TRY(decompose_pyramid<T>(p, din, top.as<T>(), py, st, E.data()));
-                decomposed = true;
-                nrm = s_norm_from_levels(E, s);
-            }
-            tol_abs = nrm > 0.0 ? tol * nrm : tol;   // an all-zero field keeps tol as absolute
-        }
+    CompressWork<T> w;
+    MGB_TRY(w.alloc(p, st));
+    DevBuf metab, scratch;
+    MGB_TRY(metab.alloc(sizeof(CompressMeta), st));
+    // a 16-byte aligned device buffer of the caller is written in place;
+    // anything else goes through a scratch buffer of the worst-case size
+    const bool direct = prealloc && is_device_ptr(*out) && ((uintptr_t)*out & 15) == 0 &&
+                        *out_bytes >= fx.outliers;
+    char* dd;
+    uint64_t cap;
+    if (direct) {
+        dd = (char*)*out;
+        cap = *out_bytes;
+    } else {
+        cap = layout(p.L, nchunks, (uint64_t)N, (uint64_t)N + nchunks).total;
+        MGB_TRY(scratch.alloc(cap, st));
+        dd = scratch.as<char>();
     }
-    if (!decomposed) MGB_TRY(decompose_pyramid<T>(p, din, top.as<T>(), py, st, nullptr));
-    std::vector<double> w(L + 1);
-    bin_widths(p, tol_abs, s, w.data());
-
-    DevBuf sym, esc, hist, stat, lengths, codes, dt, offs, totals;
-    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
-    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
-    MGB_TRY(hist.alloc(DICT * sizeof(unsigned long long), st));
-    MGB_TRY(stat.alloc(sizeof(unsigned), st));
-    MGB_CUDA(cudaMemsetAsync(hist.p, 0, DICT * sizeof(unsigned long long), st));
-    MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
-    for (int l = 0; l <= L; ++l) {
-        const T* lvl = l == L ? (L ? top.as<T>() : din) : py.lv[l];
-        MGB_TRY(quantize_level<T>(p, l, lvl, false, w[l], sym.as<uint16_t>(), esc.as<int32_t>(),
-                                  hist.as<unsigned long long>(), stat.as<unsigned>(), st));
-    }
-    MGB_TRY(lengths.alloc(DICT, st));
-    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
-    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
-    MGB_TRY(huffman_codebook(hist.as<unsigned long long>(), lengths.as<uint8_t>(), nullptr, st,
-                             (uint64_t)N >= (uint64_t(1) << 32)));
-    MGB_TRY(huffman_tables(lengths.as<uint8_t>(), codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
-    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
-    MGB_TRY(offs.alloc(16 * nchunks + 16, st));
-    MGB_TRY(totals.alloc(2 * sizeof(unsigned long long), st));
-    uint64_t* word_off = offs.as<uint64_t>();
-    uint64_t* esc_off = word_off + nchunks;
-    MGB_TRY(huffman_count(sym.as<uint16_t>(), N, lengths.as<uint8_t>(), word_off, esc_off,
-                          totals.as<unsigned long long>(), stat.as<unsigned>(), st));
-    unsigned long long tot[2];
-    unsigned status = 0;
-    MGB_CUDA(cudaMemcpyAsync(tot, totals.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
-    MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    const mgard_header h0 = header_template(p, dtype, ndim, shape, tol, s, mode);
+    MGB_TRY(compress_core<T>(p, din, h0, tol, s, mode, dd, cap, w, metab.as<CompressMeta>(), st));
+    CompressMeta m;
+    MGB_CUDA(cudaMemcpyAsync(&m, metab.p, sizeof(m), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
-    MGB_TRY(status_to_error(status));
-    const uint64_t nwords = tot[0], nout = tot[1];
-    const Sections sec = layout(L, nchunks, nout, nwords);
-
-    // header
-    mgard_header h;
-    std::memset(&h, 0, sizeof(h));
-    std::memcpy(h.magic, MGARD_MAGIC, 8);
-    h.version = MGARD_FORMAT_VERSION;
-    h.dtype = (uint32_t)dtype;
-    h.ndim = (uint32_t)ndim;
-    h.nlevels = (uint32_t)L;
-    for (int i = 0; i < 4; ++i) h.shape[i] = i < ndim ? shape[i] : 1;
-    h.s = s;
-    h.tol = tol;
-    h.tol_abs = tol_abs;
-    h.mode = (uint32_t)mode;
-    h.dict = DICT;
-    h.chunk = CHUNK;
-    h.nsymbols = (uint64_t)N;
-    h.nchunks = nchunks;
-    h.nwords = nwords;
-    h.noutliers = nout;
-    h.off_widths = sec.widths;
-    h.off_lengths = sec.lengths;
-    h.off_word_off = sec.word_off;
-    h.off_esc_off = sec.esc_off;
-    h.off_sub_off = sec.sub_off;
-    h.off_outliers = sec.outliers;
-    h.off_words = sec.words;
-    h.total_bytes = sec.total;
-
-    bool out_dev;
+    MGB_TRY(status_to_error(m.status & ~(unsigned)ST_CAPACITY));
+    if (m.status & ST_CAPACITY) {
+        *out_bytes = m.total;
+        set_error("preallocated output too small");
+        return MGARD_ECAPACITY;
+    }
+    const size_t total = m.total;
+    if (direct) {
+        *out_bytes = total;
+        return MGARD_OK;
+    }
     char* dst;
     if (prealloc) {
-        if (!out || !*out || !out_bytes) {
-            set_error("preallocated output missing");
-            return MGARD_EINVAL;
-        }
-        if (*out_bytes < sec.total) {
-            *out_bytes = sec.total;
+        if (*out_bytes < total) {
+            *out_bytes = total;
             set_error("preallocated output too small");
             return MGARD_ECAPACITY;
         }
         dst = (char*)*out;
-        out_dev = is_device_ptr(dst);
+    } else if (field_dev) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, total);
+        if (e != cudaSuccess) {
+            set_error(std::string("output allocation: ") + cudaGetErrorString(e));
+            return MGARD_ENOMEM;
+        }
+        dst = (char*)q;
     } else {
-        out_dev = field_dev;
-        if (out_dev) {
-            void* q = nullptr;
-            cudaError_t e = cudaMalloc(&q, sec.total);
-            if (e != cudaSuccess) {
-                set_error(std::string("output allocation: ") + cudaGetErrorString(e));
-                return MGARD_ENOMEM;
-            }
-            dst = (char*)q;
-        } else {
-            dst = (char*)std::malloc(sec.total);
-            if (!dst) {
-                set_error("host output allocation failed");
-                return MGARD_ENOMEM;
-            }
+        dst = (char*)std::malloc(total);
+        if (!dst) {
+            set_error("host output allocation failed");
+            return MGARD_ENOMEM;
         }
     }
-    DevBuf stage;
-    char* dd = dst;   // device image of the output
-    if (!out_dev) {
-        MGB_TRY(stage.alloc(sec.total, st));
-        dd = stage.as<char>();
-    }
-    std::vector<char> head(sec.lengths, 0);
-    std::memcpy(head.data(), &h, sizeof(h));
-    std::memcpy(head.data() + sec.widths, w.data(), 8 * (L + 1));
-    MGB_CUDA(cudaMemcpyAsync(dd, head.data(), head.size(), cudaMemcpyHostToDevice, st));
-    MGB_CUDA(cudaMemcpyAsync(dd + sec.lengths, lengths.p, DICT, cudaMemcpyDeviceToDevice, st));
-    if (nchunks) {
-        MGB_CUDA(cudaMemcpyAsync(dd + sec.word_off, word_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
-        MGB_CUDA(cudaMemcpyAsync(dd + sec.esc_off, esc_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
-    }
-    MGB_TRY(huffman_pack(sym.as<uint16_t>(), N, lengths.as<uint8_t>(), codes.as<uint32_t>(),
-                         word_off, esc_off, esc.as<int32_t>(), (uint32_t*)(dd + sec.words),
-                         (uint16_t*)(dd + sec.sub_off), (int32_t*)(dd + sec.outliers), st));
-    if (!out_dev) MGB_CUDA(cudaMemcpyAsync(dst, dd, sec.total, cudaMemcpyDeviceToHost, st));
+    MGB_CUDA(cudaMemcpyAsync(dst, dd, total, cudaMemcpyDefault, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     *out = dst;
-    *out_bytes = sec.total;
+    *out_bytes = total;
     return MGARD_OK;
 }
 
@@ -513,16 +411,19 @@ mgard_status mgard_quantize(const void* coeffs, int ndim, const int64_t* shape, 
             return MGARD_EINVAL;
         }
     cudaStream_t st = (cudaStream_t)stream;
-    DevBuf stat;
+    DevBuf stat, wdev;
     MGB_TRY(stat.alloc(sizeof(unsigned), st));
+    MGB_TRY(wdev.alloc(sizeof(double) * (p->L + 1), st));
+    MGB_CUDA(cudaMemcpyAsync(wdev.p, widths, sizeof(double) * (p->L + 1), cudaMemcpyHostToDevice, st));
     MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
     MGB_CUDA(cudaMemsetAsync(hist, 0, DICT * sizeof(uint64_t), st));
     for (int l = 0; l <= p->L; ++l) {
+        const double* wl = wdev.as<double>() + l;
         if (dtype == MGARD_F32)
-            MGB_TRY(quantize_level<float>(*p, l, (const float*)coeffs, true, widths[l], symbols,
+            MGB_TRY(quantize_level<float>(*p, l, (const float*)coeffs, true, wl, symbols,
                                           escapes, (unsigned long long*)hist, stat.as<unsigned>(), st));
         else
-            MGB_TRY(quantize_level<double>(*p, l, (const double*)coeffs, true, widths[l], symbols,
+            MGB_TRY(quantize_level<double>(*p, l, (const double*)coeffs, true, wl, symbols,
                                            escapes, (unsigned long long*)hist, stat.as<unsigned>(), st));
     }
     unsigned status = 0;
@@ -734,6 +635,9 @@ void mgard_free(void* p) {
     else std::free(p);
 }
 
-void mgard_release_plans(void) { release_plans(); }
+void mgard_release_plans(void) {
+    release_batches();
+    release_plans();
+}
 
 }  // extern "C"

@@ -70,6 +70,7 @@ enum : unsigned {
     ST_RANGE = 2u,
     ST_NOCODE = 4u,
     ST_CORRUPT = 8u,
+    ST_CAPACITY = 16u,   // the output buffer is smaller than the compressed data
 };
 
 // Per-axis tables of one level transition (fine grid of level l, coarse
@@ -88,6 +89,13 @@ struct AxisT {
     const T* tcp;        // [mc] Thomas: c'_J
     const double* mdiag; // [m]  mass matrix of the level-l grid: diagonal
     const double* moff;  // [m]  mass matrix: M[i][i+1] (last entry 0)
+    // Uniform parts of the tables, so row kernels need no per-element table
+    // loads there: for i < ireg the interpolation weights are (1, 0) at even
+    // i and (1/2, 1/2) at odd i; for coarse J in [rlo, rhi) the restriction
+    // window is centred on 2J with weights rwi.
+    int ireg;
+    int rlo, rhi;
+    T rwi[5];
 };
 
 template <typename T>

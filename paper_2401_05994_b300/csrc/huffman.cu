@@ -8,10 +8,11 @@
 //  * canonical codes, consecutive in (length, symbol) order;
 //  * chunks of CHUNK symbols, each starting on a 32-bit word, MSB-first.
 // The codebook is built by one CTA: bitonic sort of the leaves, the queue
-// merge in doubling rounds (see round_merge) and depths by pointer jumping.  Encoding is a
-// count pass, an exclusive scan over chunks and a pack pass with one warp
-// per chunk.  Decoding runs one thread per chunk with a 12-bit prefix table
-// in shared memory and canonical first-code search for longer codes.
+// merge in doubling rounds (see round_merge) and depths by pointer jumping.
+// Encoding is a count pass, an exclusive scan over chunks and a pack pass
+// with one warp per chunk.  Decoding runs one thread per 256-symbol
+// sub-chunk with a 14-bit prefix table in shared memory and a canonical
+// first-code search for longer codes.
 #include <map>
 #include <mutex>
 
@@ -291,7 +292,6 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
         dt->maxlen = maxlen;
         dt->valid = valid ? 1 : 0;
     }
-    for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) dt->lut[k] = 0;
     bitonic_sort(keys, DICT);   // ends with a barrier
     for (int p = tid; p < DICT; p += blockDim.x) {
         const unsigned long long key = keys[p];
@@ -300,21 +300,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
         const uint32_t c = (uint32_t)(fc[len] + (p - fi[len]));
         dt->sorted[p] = (uint16_t)s;
         codes[s] = c;
-        if (len <= LUT_BITS) {
-            const unsigned lo = c << (LUT_BITS - len), hi = (c + 1) << (LUT_BITS - len);
-            for (unsigned e = lo; e < hi && e < (1u << LUT_BITS); ++e) dt->lut[e] = (len << 16) | s;
-        }
     }
     for (int s = tid; s < DICT; s += blockDim.x)
         if (!lengths[s]) codes[s] = 0;
-    __syncthreads();
-    // prefixes of longer codes: the shortest possible length
+    // prefix table: the code under each 14-bit prefix, found from the
+    // canonical limits (every entry costs the same, whatever the lengths)
     for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) {
-        if (dt->lut[k]) continue;
         const unsigned long long top = (unsigned long long)k << (32 - LUT_BITS);
-        unsigned l = LUT_BITS + 1;
-        while (l <= LMAX && top >= ((fc[l] + cnt[l]) << (LMAX - l))) ++l;
-        if (l <= LMAX) dt->lut[k] = LUT_LONG | l;   // else no code has this prefix: stays 0
+        unsigned l = 1;
+        while (l <= LUT_BITS && top >= ((fc[l] + cnt[l]) << (LMAX - l))) ++l;
+        uint16_t ent = 0;
+        if (l <= LUT_BITS) {
+            const unsigned long long idx = fi[l] + ((top >> (32 - l)) - fc[l]);
+            if ((top >> (32 - l)) >= fc[l] && idx < DICT)
+                ent = (uint16_t)((l << 12) | (unsigned)(keys[idx] & 0xFFF));
+        }
+        dt->lut[k] = ent;
     }
 }
 
@@ -503,10 +504,13 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     const uint32_t* __restrict__ codes, const uint64_t* __restrict__ word_off,
     const uint64_t* __restrict__ esc_off, const int32_t* __restrict__ escapes,
     uint32_t* __restrict__ words, uint16_t* __restrict__ sub_off, int32_t* __restrict__ outliers,
-    uint64_t nchunks) {
+    uint64_t nchunks, PackGuard guard) {
     __shared__ uint8_t len_s[DICT];
     __shared__ uint32_t code_s[DICT];
     __shared__ uint32_t buf[PACK_WARPS][CHUNK + 1];
+    if (guard.status && *guard.status) return;   // an earlier step failed: write nothing
+    if (guard.words_byte_off)
+        words = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(words) + *guard.words_byte_off);
     for (int s = threadIdx.x; s < DICT; s += blockDim.x) {
         len_s[s] = lengths[s];
         code_s[s] = codes[s];
@@ -599,137 +603,154 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
 }
 
 // -- decoding ------------------------------------------------------------------
-constexpr int DEC_THREADS = 128;
+constexpr int DEC_THREADS = 256;
+constexpr int DEC_BLOCKS_PER_SM = 6;   // 33 KB of tables per block
 
+// Decoding: one thread per sub-chunk of SUB symbols, in a grid that stays
+// resident (each block copies the prefix table once).  The bit window is a
+// left-justified 64-bit register refilled one word at a time; a symbol costs
+// one shared-memory lookup unless its code is longer than LUT_BITS.  Word
+// loads never leave the chunk, escape reads never leave the chunk's escape
+// range, and a sub-chunk whose code stream does not end where its recorded
+// offsets say (or that meets a prefix with no code) marks the stream corrupt.
 __global__ void __launch_bounds__(DEC_THREADS) k_decode(
     const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
     const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
     const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
     uint16_t* __restrict__ sym, int32_t* __restrict__ escapes, unsigned* status, uint64_t nchunks) {
-    __shared__ DecodeTables T;
+    __shared__ __align__(16) uint16_t lut[1 << LUT_BITS];
+    __shared__ unsigned long long lim[LMAX + 2];
+    __shared__ uint32_t fcode[LMAX + 2], findex[LMAX + 2];
     {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(gdt);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
-        for (int k = threadIdx.x; k < (int)(sizeof(DecodeTables) / 4); k += blockDim.x) dst[k] = src[k];
+        const uint4* src = reinterpret_cast<const uint4*>(gdt->lut);
+        uint4* dst = reinterpret_cast<uint4*>(lut);
+        for (int k = threadIdx.x; k < (int)(sizeof(lut) / 16); k += blockDim.x) dst[k] = src[k];
+        if (threadIdx.x < LMAX + 2) {
+            lim[threadIdx.x] = gdt->lim[threadIdx.x];
+            fcode[threadIdx.x] = gdt->first_code[threadIdx.x];
+            findex[threadIdx.x] = gdt->first_index[threadIdx.x];
+        }
     }
     __syncthreads();
-    // one thread per sub-chunk of SUB symbols
-    const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t c = gid / NSUB;
-    const int sc = (int)(gid % NSUB);
-    if (c >= nchunks) return;
-    const uint64_t first = c * CHUNK + (uint64_t)sc * SUB;
-    if (first >= n) return;
-    if (!T.valid) {
-        atomicOr(status, ST_CORRUPT);
+    const unsigned maxlen = gdt->maxlen;
+    if (!gdt->valid) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(status, ST_CORRUPT);
         return;
     }
-    const int cnt = (int)min((uint64_t)SUB, n - first);
-    // bit and escape ranges of this sub-chunk, validated against its chunk
-    const uint64_t cw0 = word_off[c];
-    const uint64_t cw1 = c + 1 < nchunks ? word_off[c + 1] : nwords;
-    const uint64_t ce0 = esc_off[c];
-    const uint64_t ce1 = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
-    if (cw0 > cw1 || cw1 > nwords || ce0 > ce1 || ce1 > noutliers) {
-        atomicOr(status, ST_CORRUPT);
-        return;
-    }
-    const uint16_t* so = sub_off + c * SUBREC;
-    const uint64_t bstart = cw0 * 32 + (sc ? so[sc - 1] : 0);
-    const uint64_t endbit = sc + 1 < NSUB ? cw0 * 32 + so[sc] : cw1 * 32;
-    uint64_t e = ce0 + (sc ? so[NSUB - 1 + sc - 1] : 0);
-    const uint64_t e_end = sc + 1 < NSUB ? ce0 + so[NSUB - 1 + sc] : ce1;
-    if (bstart > endbit || endbit > cw1 * 32 || e > e_end || e_end > ce1) {
-        atomicOr(status, ST_CORRUPT);
-        return;
-    }
-    const uint64_t end = cw1;   // word loads stay inside the chunk
-    auto load = [&](uint64_t k) -> uint64_t { return k < end ? (uint64_t)words[k] : 0ull; };
-    uint64_t wi = bstart >> 5;
-    unsigned off = (unsigned)(bstart & 31);
-    uint64_t win = (load(wi) << 32) | load(wi + 1);
-    // the next four words are loaded ahead of use
-    uint32_t q0 = (uint32_t)load(wi + 2), q1 = (uint32_t)load(wi + 3), q2 = (uint32_t)load(wi + 4),
-             q3 = (uint32_t)load(wi + 5);
-    uint64_t bit = bstart;
-    uint32_t pk[4] = {0, 0, 0, 0};
+    const uint16_t* __restrict__ sorted = gdt->sorted;
     bool ok = true;
-    int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
-    int k = 0;
-    for (; k < cnt; ++k) {
-        const uint32_t top = (uint32_t)((win << off) >> 32);
-        const uint32_t ent = T.lut[top >> (32 - LUT_BITS)];
-        unsigned len, s;
-        if (!(ent & LUT_LONG)) {
-            len = ent >> 16;
-            s = ent & 0xFFFF;
-            if (!len) {
-                ok = false;
-                break;
-            }
-        } else {
-            unsigned l = ent & 0xFF;
-            while (l <= T.maxlen && (unsigned long long)top >= T.lim[l]) ++l;
-            if (l > T.maxlen) {
-                ok = false;
-                break;
-            }
-            len = l;
-            s = T.sorted[T.first_index[l] + ((top >> (32 - l)) - T.first_code[l])];
-        }
-        bit += len;
-        if (bit > endbit) {
+    const uint64_t nsub = nchunks * NSUB;
+    for (uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gid < nsub;
+         gid += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = gid / NSUB;
+        const int sc = (int)(gid % NSUB);
+        const uint64_t first = c * CHUNK + (uint64_t)sc * SUB;
+        if (first >= n) continue;
+        const int cnt = (int)min((uint64_t)SUB, n - first);
+        // bit and escape ranges of this sub-chunk, validated against its chunk
+        const uint64_t cw0 = word_off[c];
+        const uint64_t cw1 = c + 1 < nchunks ? word_off[c + 1] : nwords;
+        const uint64_t ce0 = esc_off[c];
+        const uint64_t ce1 = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
+        if (cw0 > cw1 || cw1 > nwords || ce0 > ce1 || ce1 > noutliers) {
             ok = false;
-            break;
+            continue;
         }
-        off += len;
-        if (off >= 32) {
-            ++wi;
-            win = (win << 32) | q0;
-            q0 = q1;
-            q1 = q2;
-            q2 = q3;
-            q3 = (uint32_t)load(wi + 5);
-            off -= 32;
+        const uint16_t* so = sub_off + c * SUBREC;
+        const uint64_t bstart = cw0 * 32 + (sc ? so[sc - 1] : 0);
+        const uint64_t endbit = sc + 1 < NSUB ? cw0 * 32 + so[sc] : cw1 * 32;
+        uint64_t e = ce0 + (sc ? so[NSUB - 1 + sc - 1] : 0);
+        const uint64_t e_end = sc + 1 < NSUB ? ce0 + so[NSUB - 1 + sc] : ce1;
+        if (bstart > endbit || endbit > cw1 * 32 || e > e_end || e_end > ce1) {
+            ok = false;
+            continue;
         }
-        if (s == MGARD_ESC) {
-            if (e >= e_end) {
-                ok = false;
-                break;
+        // window: `nb` valid bits, left-justified in `win`
+        uint64_t wi = bstart >> 5;
+        const uint32_t w0 = wi < cw1 ? words[wi] : 0u;
+        ++wi;
+        const unsigned skip = (unsigned)(bstart & 31);
+        uint64_t win = ((uint64_t)w0 << 32) << skip;
+        int nb = 32 - (int)skip;
+        uint64_t used = 0;
+        int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
+        uint32_t pk[4] = {0, 0, 0, 0};
+        int k = 0;
+        for (; k < cnt; ++k) {
+            if (nb <= 32) {
+                const uint32_t w = wi < cw1 ? words[wi] : 0u;
+                ++wi;
+                win |= (uint64_t)w << (32 - nb);
+                nb += 32;
             }
-            escapes[first + k] = next_out;
-            ++e;
-            next_out = e < e_end ? outliers[e] : 0;
+            const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
+            unsigned len, s;
+            if (ent) {
+                len = ent >> 12;
+                s = ent & 0xFFF;
+            } else {
+                const uint32_t top = (uint32_t)(win >> 32);
+                unsigned l = LUT_BITS + 1;
+                while (l <= maxlen && (unsigned long long)top >= lim[l]) ++l;
+                if (l > maxlen) {
+                    ok = false;
+                    break;
+                }
+                len = l;
+                s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
+            }
+            win <<= len;
+            nb -= (int)len;
+            used += len;
+            if (s == MGARD_ESC) {
+                if (e >= e_end) {
+                    ok = false;
+                    break;
+                }
+                escapes[first + k] = next_out;
+                ++e;
+                next_out = e < e_end ? outliers[e] : 0;
+            }
+            const int slot = k & 7;
+            if (slot & 1) pk[slot >> 1] |= s << 16;
+            else pk[slot >> 1] = s;
+            if (slot == 7)
+                *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        const int slot = k & 7;
-        if (slot & 1) pk[slot >> 1] |= s << 16;
-        else pk[slot >> 1] = s;
-        if (slot == 7) {
-            *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-    }
-    if (ok) {
+        if (k < cnt) continue;   // ok already cleared
         const int rem = cnt & 7;   // symbols decoded after the last full group
         for (int r = 0; r < rem; ++r) {
             const uint32_t w = pk[r >> 1];
             sym[first + (cnt - rem) + r] = (uint16_t)((r & 1) ? (w >> 16) : (w & 0xFFFF));
         }
-        if (e != e_end) ok = false;
+        // the codes must end inside the sub-chunk's bit range (exactly at its
+        // end unless padding follows) and use exactly its escapes
+        const uint64_t span = endbit - bstart;
+        if (used > span || (sc + 1 < NSUB && used != span) || e != e_end) ok = false;
     }
     if (!ok) atomicOr(status, ST_CORRUPT);
 }
 
 }  // namespace
 
+mgard_status huffman_prepare() {
+    static std::mutex mu;
+    static std::map<int, bool> done;   // per device
+    int dev = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        MGB_CUDA(cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(CodebookSmem)));
+        done[dev] = true;
+    }
+    return MGARD_OK;
+}
+
 mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
                               cudaStream_t st, bool wide) {
     const size_t smem = sizeof(CodebookSmem);
-    static bool attr = false;
-    if (!attr) {
-        MGB_CUDA(cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        attr = true;
-    }
+    MGB_TRY(huffman_prepare());
     MGB_LAUNCH("k_codebook", st, k_codebook<<<1, CB_THREADS, smem, st>>>(hist, lengths, wide ? 1 : 0));
     MGB_CUDA(cudaGetLastError());
     (void)codes;
@@ -743,9 +764,14 @@ mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTable
     return MGARD_OK;
 }
 
+size_t count_scratch_bytes(uint64_t n) {
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    return 16 * ((nchunks + SCAN_TILE - 1) / SCAN_TILE + 1);
+}
+
 mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                            uint64_t* word_off, uint64_t* esc_off, unsigned long long* totals,
-                           unsigned* status, cudaStream_t st) {
+                           unsigned* status, cudaStream_t st, unsigned long long* scratch) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (nchunks) {
         MGB_LAUNCH("k_chunk_count", st, k_chunk_count<<<grid_for((int64_t)nchunks, ENC_WARPS, 148LL * 16), ENC_WARPS * 32, 0, st>>>(
@@ -754,8 +780,11 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
     }
     const uint64_t ntiles = (nchunks + SCAN_TILE - 1) / SCAN_TILE;
     DevBuf tbuf;
-    MGB_TRY(tbuf.alloc(16 * (ntiles + 1), st));
-    unsigned long long* tsum = tbuf.as<unsigned long long>();
+    unsigned long long* tsum = scratch;
+    if (!tsum) {
+        MGB_TRY(tbuf.alloc(count_scratch_bytes(n), st));
+        tsum = tbuf.as<unsigned long long>();
+    }
     if (ntiles) {
         MGB_LAUNCH("k_scan_sums", st, k_scan_sums<<<(unsigned)ntiles, SCAN_T, 0, st>>>(word_off, esc_off, nchunks, tsum));
     }
@@ -770,11 +799,11 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
                           const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
-                          int32_t* outliers, cudaStream_t st) {
+                          int32_t* outliers, cudaStream_t st, PackGuard guard) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 4), PACK_WARPS * 32, 0, st>>>(
-        sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks));
+        sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -785,7 +814,7 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
                             uint16_t* sym, int32_t* escapes, unsigned* status, cudaStream_t st) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    const int grid = (int)((nchunks * NSUB + DEC_THREADS - 1) / DEC_THREADS);
+    const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
     MGB_LAUNCH("k_decode", st, k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
                                           esc_off, sym, escapes, status, nchunks));
     MGB_CUDA(cudaGetLastError());
@@ -812,7 +841,7 @@ struct NoAllocScratch {
 
 }  // namespace
 
-// Fixed scratch of sizeof(NoAllocScratch) (74,320 bytes) held by every device
+// Fixed scratch of sizeof(NoAllocScratch) (90,704 bytes) held by every device
 // that loads the library until the process exits.  In host code the name is
 // only a stand-in for the device address; cudaGetSymbolAddress gives the
 // real one.
@@ -898,7 +927,7 @@ extern "C" mgard_status mgard_huffman_encode_noalloc(
         MGB_LAUNCH("k_pack", st,
                    k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
                        symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, sub_off,
-                       outliers, nchunks));
+                       outliers, nchunks, PackGuard()));
     MGB_CUDA(cudaGetLastError());
     MGB_CUDA(cudaStreamSynchronize(st));
     return MGARD_OK;

@@ -5,18 +5,15 @@
 
 namespace mgb {
 
-constexpr int LUT_BITS = 12;
+constexpr int LUT_BITS = 14;
 constexpr int SUB = 256;                 // symbols per independently decodable sub-chunk
 constexpr int NSUB = MGARD_CHUNK / SUB;  // sub-chunks per chunk
 constexpr int SUBREC = 2 * (NSUB - 1);   // uint16 offsets recorded per chunk
 
-constexpr uint32_t LUT_LONG = 0x80000000u;
-
 struct DecodeTables {
-    // 12-bit prefix -> (length << 16) | symbol for codes of at most 12 bits;
-    // LUT_LONG | l0 when the code is longer (l0 = the shortest length a code
-    // with this prefix can have); 0 when no code starts with the prefix
-    uint32_t lut[1 << LUT_BITS];
+    // 14-bit prefix -> (length << 12) | symbol for codes of at most 14 bits;
+    // 0 when the code under the prefix is longer (or no code has the prefix)
+    uint16_t lut[1 << LUT_BITS];
     unsigned long long lim[LMAX + 2];   // lim[l]: first code of length l+1, left-justified in 32 bits
     uint32_t first_code[LMAX + 2];
     uint32_t first_index[LMAX + 2];
@@ -25,6 +22,9 @@ struct DecodeTables {
     uint32_t valid;                     // 0 if the lengths violate the Kraft inequality
 };
 
+// One-time per-device setup of the kernels (launch attributes); called by
+// huffman_codebook and, before any stream capture, by batched compression.
+mgard_status huffman_prepare();
 // Code lengths from a histogram (single CTA).  `wide` selects 64-bit merge
 // weights (needed when the histogram totals 2^32 symbols or more).
 mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
@@ -34,14 +34,26 @@ mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTable
                             cudaStream_t st);
 // Pass 1 of encoding: per-chunk word and escape counts and their exclusive
 // prefixes; totals (device, 2 x uint64) receive total words / escapes.
+// `scratch` (device, count_scratch_bytes(n)) may be null: then it is
+// allocated from the workspace pool.
 mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                            uint64_t* word_off, uint64_t* esc_off, unsigned long long* totals,
-                           unsigned* status, cudaStream_t st);
+                           unsigned* status, cudaStream_t st,
+                           unsigned long long* scratch = nullptr);
+size_t count_scratch_bytes(uint64_t n);
+
+// Device-side conditions of the pack pass (both optional): it writes nothing
+// when *status is non-zero, and the payload starts *words_byte_off bytes
+// after `words` (an offset known only on the device).
+struct PackGuard {
+    const unsigned* status = nullptr;
+    const unsigned long long* words_byte_off = nullptr;
+};
 // Pass 2: pack codes, record sub-chunk offsets and gather escapes.
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
                           const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
-                          int32_t* outliers, cudaStream_t st);
+                          int32_t* outliers, cudaStream_t st, PackGuard guard = PackGuard());
 // Decoding with bounds checks (ST_CORRUPT on failure).
 mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
                             const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,

@@ -458,7 +458,7 @@ __global__ void k_difference(const T* __restrict__ a, const T* __restrict__ b,
 }
 
 // -- reductions --------------------------------------------------------------
-constexpr int RED_BLOCKS = 592;
+constexpr int RED_BLOCKS = RED_PARTS;
 constexpr int RED_THREADS = 256;
 
 // max |a| (b == null, exact in the data's precision) or max |b - a| (in FP64).
@@ -723,21 +723,52 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
     return MGARD_OK;
 }
 
+int64_t mass_norm_parts(const Plan& p, int l) {
+    const dim3 g = grid3(p.level<float>(l).n, RED_THREADS, 8, 74);
+    return (int64_t)g.x * g.y * g.z;
+}
+
+int64_t energy_parts_total(const Plan& p) {
+    int64_t t = 0;
+    for (int l = 0; l <= p.L; ++l) t += mass_norm_parts(p, l);
+    return t;
+}
+
+int64_t energy_parts_offset(const Plan& p, int l) {
+    int64_t t = 0;
+    for (int k = 0; k < l; ++k) t += mass_norm_parts(p, k);
+    return t;
+}
+
 template <typename T>
-mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st) {
+mgard_status mass_norm2_partials(const Plan& p, int l, const T* u, double* part, cudaStream_t st) {
     const Level<T>& lv = p.level<T>(l);   // holds the mass tables of level l
     const dim3 g = grid3(lv.n, RED_THREADS, 8, 74);   // fixed grid: deterministic partial sums
-    const size_t nb = (size_t)g.x * g.y * g.z;
+    MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<g, RED_THREADS, 0, st>>>(u, lv, part));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st) {
+    const size_t nb = (size_t)mass_norm_parts(p, l);
     DevBuf part;
     MGB_TRY(part.alloc(nb * sizeof(double), st));
-    MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<g, RED_THREADS, 0, st>>>(u, lv, part.as<double>()));
-    MGB_CUDA(cudaGetLastError());
+    MGB_TRY(mass_norm2_partials<T>(p, l, u, part.as<double>(), st));
     std::vector<double> h(nb);
     MGB_CUDA(cudaMemcpyAsync(h.data(), part.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     double s = 0.0;
     for (size_t i = 0; i < nb; ++i) s += h[i];
     *out = s;
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status max_abs_partials(const T* a, int64_t n, double* part, unsigned* status,
+                              cudaStream_t st) {
+    MGB_LAUNCH("k_maxabs", st, k_maxabs<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, nullptr, n, part, status));
+    MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
 
@@ -771,11 +802,12 @@ mgard_status difference(const T* a, const T* b, double* y, int64_t n, cudaStream
 
 template <typename T>
 mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
-                               cudaStream_t st, double* E) {
+                               cudaStream_t st, double* E, double* Epart) {
     for (int l = p.L; l >= 1; --l) {
         const T* src = l == p.L ? in : py.lv[l];
         T* dst = l == p.L ? top : py.lv[l];
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
+        if (Epart) MGB_TRY(mass_norm2_partials<T>(p, l, src, Epart + energy_parts_offset(p, l), st));
         if (rows3_ok(p)) {
             MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st));
         } else {
@@ -786,7 +818,9 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         }
         MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
     }
-    if (E) MGB_TRY(mass_norm2<T>(p, 0, p.L ? py.lv[0] : in, &E[0], st));
+    const T* u0 = p.L ? py.lv[0] : in;
+    if (E) MGB_TRY(mass_norm2<T>(p, 0, u0, &E[0], st));
+    if (Epart) MGB_TRY(mass_norm2_partials<T>(p, 0, u0, Epart, st));
     return MGARD_OK;
 }
 
@@ -840,7 +874,11 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
 #define INST(T)                                                                               \
     template struct Pyramid<T>;                                                               \
     template mgard_status decompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
-                                               cudaStream_t, double*);                        \
+                                               cudaStream_t, double*, double*);                \
+    template mgard_status max_abs_partials<T>(const T*, int64_t, double*, unsigned*,           \
+                                              cudaStream_t);                                   \
+    template mgard_status mass_norm2_partials<T>(const Plan&, int, const T*, double*,          \
+                                                 cudaStream_t);                        \
     template mgard_status recompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
                                                cudaStream_t);                                 \
     template mgard_status scatter_levels<T>(const Plan&, const Pyramid<T>&, T*, cudaStream_t); \

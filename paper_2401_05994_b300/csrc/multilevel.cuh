@@ -54,9 +54,12 @@ constexpr int64_t FP64_SOLVE_NODES = int64_t(1) << 21;
 // level-L new nodes; coarse positions untouched) and the pyramid levels.
 // `in` may equal `top`.  If `E` is non-null, E[l] receives u_l^T M_l u_l of
 // every level's nodal values (FP64 accumulation; host array of L+1).
+// With `Epart` (device, energy_parts_total(p) doubles) the same energies
+// are left as partial sums on the device instead (no host round trip):
+// level l's partials start at energy_parts_offset(p, l).
 template <typename T>
 mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
-                               cudaStream_t st, double* E);
+                               cudaStream_t st, double* E, double* Epart = nullptr);
 
 // Recompose: `top` holds level-L coefficients (coarse positions ignored),
 // py.lv[l] the coefficients of level l >= 1 (coarse positions ignored) and
@@ -78,6 +81,20 @@ mgard_status max_abs(const T* a, const T* b, int64_t n, double* out, unsigned* s
                      cudaStream_t st);
 template <typename T>
 mgard_status mass_norm2(const Plan& p, int l, const T* u, double* out, cudaStream_t st);
+
+// Launch-only forms for pipelines without host round trips: partial
+// results stay in device memory.  max_abs_partials writes RED_PARTS values
+// (their maximum is max|a|); mass_norm2_partials writes mass_norm_parts(p, l)
+// values (their sum is u^T M_l u).
+constexpr int RED_PARTS = 592;
+template <typename T>
+mgard_status max_abs_partials(const T* a, int64_t n, double* part, unsigned* status,
+                              cudaStream_t st);
+int64_t mass_norm_parts(const Plan& p, int l);
+int64_t energy_parts_total(const Plan& p);
+int64_t energy_parts_offset(const Plan& p, int l);
+template <typename T>
+mgard_status mass_norm2_partials(const Plan& p, int l, const T* u, double* part, cudaStream_t st);
 
 // y = b - a in double (device), for error norms.
 template <typename T>

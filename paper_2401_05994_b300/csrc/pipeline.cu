@@ -1,0 +1,241 @@
+// Compression pipeline without host round trips (see pipeline.cuh).
+//
+// Paper, "Software design" and Listing 1: a relative tolerance is scaled by
+// the norm of the data, the data is decomposed, every coefficient is
+// quantized with its level's bin width and the symbols are Huffman-coded
+// into a self-describing buffer.  Here every step is a launch on one
+// stream; the norm, widths, sizes and header are produced by small device
+// kernels (k_widths, k_finalize) instead of the host.
+#include <cmath>
+#include <cstring>
+
+#include "huffman.cuh"
+#include "pipeline.cuh"
+#include "quantize.cuh"
+
+namespace mgb {
+
+namespace {
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+constexpr int MAXLV = 64;   // levels a header may record
+
+struct WidthArgs {
+    int L;
+    int rel;                      // relative tolerance: scale by the norm of the data
+    int snorm;                    // finite s: the norm comes from the level energies
+    double tol;
+    double den[MAXLV + 1];        // width denominators of every level
+    double f[MAXLV + 1];          // 4^(s l)
+    long long eoff[MAXLV + 2];    // ranges of the energy partial sums of every level
+};
+
+// One warp: norm of the data (relative tolerances), tol_abs and the widths.
+// Norm: max|u| (L-infinity), or sqrt(E_0 + sum_l 4^(s l) max(E_l - E_{l-1}, 0))
+// with E_l = u_l^T M_l u_l (s-norm).  Sums and maxima run in a fixed order,
+// and every lane ends with the same value.
+__global__ void k_widths(WidthArgs a, const double* __restrict__ maxparts,
+                         const double* __restrict__ eparts, CompressMeta* meta,
+                         double* __restrict__ w) {
+    const int lane = threadIdx.x;
+    double nrm = 0.0;
+    if (a.rel) {
+        if (!a.snorm) {
+            double m = 0.0;
+            for (int i = lane; i < RED_PARTS; i += 32) m = fmax(m, maxparts[i]);
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            nrm = m;
+        } else {
+            double total = 0.0, prev = 0.0;
+            for (int l = 0; l <= a.L; ++l) {
+                double e = 0.0;
+                for (long long i = a.eoff[l] + lane; i < a.eoff[l + 1]; i += 32) e += eparts[i];
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+                if (l == 0) total = e;
+                else total += a.f[l] * fmax(e - prev, 0.0);
+                prev = e;
+            }
+            nrm = sqrt(fmax(total, 0.0));
+        }
+    }
+    const double tol_abs = a.rel ? (nrm > 0.0 ? a.tol * nrm : a.tol) : a.tol;
+    for (int l = lane; l <= a.L; l += 32) w[l] = 2.0 * tol_abs / a.den[l] * WIDTH_MARGIN;
+    if (lane == 0) meta->tol_abs = tol_abs;
+}
+
+// Sizes and offsets that follow from the totals of the count pass; the
+// header goes to the front of the buffer.
+__global__ void k_finalize(mgard_header h, const unsigned long long* __restrict__ totals,
+                           CompressMeta* meta, unsigned char* dd, unsigned long long cap) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long nwords = totals[0], nout = totals[1];
+    const unsigned long long off_words = (h.off_outliers + 4 * nout + 15) & ~15ull;
+    const unsigned long long total = (off_words + 4 * nwords + 15) & ~15ull;
+    h.tol_abs = meta->tol_abs;
+    h.nwords = nwords;
+    h.noutliers = nout;
+    h.off_words = off_words;
+    h.total_bytes = total;
+    meta->nwords = nwords;
+    meta->noutliers = nout;
+    meta->off_words = off_words;
+    meta->total = total;
+    if (total > cap) atomicOr(&meta->status, (unsigned)ST_CAPACITY);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(&h);
+    for (size_t i = 0; i < sizeof(h); ++i) dd[i] = src[i];
+}
+
+}  // namespace
+
+Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords) {
+    Sections s;
+    size_t o = align16(sizeof(mgard_header));
+    s.widths = o;
+    o = align16(o + 8 * (size_t)(L + 1));
+    s.lengths = o;
+    o = align16(o + DICT);
+    s.word_off = o;
+    o = align16(o + 8 * nchunks);
+    s.esc_off = o;
+    o = align16(o + 8 * nchunks);
+    s.sub_off = o;
+    o = align16(o + 2 * SUBREC * nchunks);
+    s.outliers = o;
+    o = align16(o + 4 * nout);
+    s.words = o;
+    o = align16(o + 4 * nwords);
+    s.total = o;
+    return s;
+}
+
+template <typename T>
+mgard_status CompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
+    const int64_t N = p.total();
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    MGB_TRY(py.alloc(p, st));
+    MGB_TRY(top.alloc(N * sizeof(T), st));
+    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
+    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    MGB_TRY(hist.alloc(DICT * sizeof(unsigned long long), st));
+    MGB_TRY(lengths.alloc(DICT, st));
+    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(offs.alloc(16 * nchunks + 16, st));
+    MGB_TRY(totals.alloc(2 * sizeof(unsigned long long), st));
+    MGB_TRY(parts.alloc((RED_PARTS + energy_parts_total(p)) * sizeof(double), st));
+    MGB_TRY(scan.alloc(count_scratch_bytes((uint64_t)N), st));
+    return MGARD_OK;
+}
+
+mgard_header header_template(const Plan& p, mgard_dtype dtype, int ndim, const int64_t* shape,
+                             double tol, double s, mgard_tolmode mode) {
+    const uint64_t N = (uint64_t)p.total();
+    const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
+    const Sections fx = layout(p.L, nchunks, 0, 0);
+    mgard_header h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, MGARD_MAGIC, 8);
+    h.version = MGARD_FORMAT_VERSION;
+    h.dtype = (uint32_t)dtype;
+    h.ndim = (uint32_t)ndim;
+    h.nlevels = (uint32_t)p.L;
+    for (int i = 0; i < 4; ++i) h.shape[i] = i < ndim ? shape[i] : 1;
+    h.s = s;
+    h.tol = tol;
+    h.mode = (uint32_t)mode;
+    h.dict = DICT;
+    h.chunk = CHUNK;
+    h.nsymbols = N;
+    h.nchunks = nchunks;
+    h.off_widths = fx.widths;
+    h.off_lengths = fx.lengths;
+    h.off_word_off = fx.word_off;
+    h.off_esc_off = fx.esc_off;
+    h.off_sub_off = fx.sub_off;
+    h.off_outliers = fx.outliers;
+    return h;
+}
+
+template <typename T>
+mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                           double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+    const int64_t N = p.total();
+    const int L = p.L;
+    if (L > MAXLV) {
+        set_error("too many levels");
+        return MGARD_ESHAPE;
+    }
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    const Sections fx = layout(L, nchunks, 0, 0);
+    if (cap < fx.outliers || ((uintptr_t)dd & 15) != 0) {
+        set_error("compress_core: output buffer too small or misaligned");
+        return MGARD_EINVAL;
+    }
+    MGB_CUDA(cudaMemsetAsync(meta, 0, sizeof(CompressMeta), st));
+    MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
+    unsigned* status = &meta->status;
+    double* parts = w.parts.template as<double>();
+    MGB_TRY(max_abs_partials<T>(din, N, parts, status, st));
+    const bool energy = mode == MGARD_REL && !std::isinf(s);
+    MGB_TRY(decompose_pyramid<T>(p, din, w.top.template as<T>(), w.py, st, nullptr,
+                                 energy ? parts + RED_PARTS : nullptr));
+    WidthArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.L = L;
+    a.rel = mode == MGARD_REL;
+    a.snorm = energy;
+    a.tol = tol;
+    width_denominators(p, s, a.den);
+    for (int l = 0; l <= L; ++l) {
+        a.f[l] = energy ? std::pow(4.0, s * (double)l) : 1.0;
+        a.eoff[l] = energy_parts_offset(p, l);
+    }
+    a.eoff[L + 1] = energy_parts_total(p);
+    double* widths = reinterpret_cast<double*>(dd + fx.widths);
+    MGB_LAUNCH("k_widths", st, k_widths<<<1, 32, 0, st>>>(a, parts, parts + RED_PARTS, meta, widths));
+    MGB_CUDA(cudaGetLastError());
+    uint16_t* sym = w.sym.template as<uint16_t>();
+    int32_t* esc = w.esc.template as<int32_t>();
+    for (int l = 0; l <= L; ++l) {
+        const T* lvl = l == L ? (L ? w.top.template as<T>() : din) : w.py.lv[l];
+        MGB_TRY(quantize_level<T>(p, l, lvl, false, widths + l, sym, esc,
+                                  w.hist.template as<unsigned long long>(), status, st));
+    }
+    MGB_TRY(huffman_codebook(w.hist.template as<unsigned long long>(), w.lengths.template as<uint8_t>(), nullptr, st,
+                             (uint64_t)N >= (uint64_t(1) << 32)));
+    MGB_TRY(huffman_tables(w.lengths.template as<uint8_t>(), w.codes.template as<uint32_t>(),
+                           w.dt.template as<DecodeTables>(), st));
+    uint64_t* word_off = w.offs.template as<uint64_t>();
+    uint64_t* esc_off = word_off + nchunks;
+    MGB_TRY(huffman_count(sym, N, w.lengths.template as<uint8_t>(), word_off, esc_off,
+                          w.totals.template as<unsigned long long>(), status, st,
+                          w.scan.template as<unsigned long long>()));
+    MGB_LAUNCH("k_finalize", st, k_finalize<<<1, 32, 0, st>>>(
+        h0, w.totals.template as<unsigned long long>(), meta, reinterpret_cast<unsigned char*>(dd), cap));
+    MGB_CUDA(cudaGetLastError());
+    MGB_CUDA(cudaMemcpyAsync(dd + fx.lengths, w.lengths.p, DICT, cudaMemcpyDeviceToDevice, st));
+    if (nchunks) {
+        MGB_CUDA(cudaMemcpyAsync(dd + fx.word_off, word_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
+        MGB_CUDA(cudaMemcpyAsync(dd + fx.esc_off, esc_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
+    }
+    PackGuard guard;
+    guard.status = status;
+    guard.words_byte_off = &meta->off_words;
+    MGB_TRY(huffman_pack(sym, N, w.lengths.template as<uint8_t>(), w.codes.template as<uint32_t>(), word_off, esc_off,
+                         esc, reinterpret_cast<uint32_t*>(dd), reinterpret_cast<uint16_t*>(dd + fx.sub_off),
+                         reinterpret_cast<int32_t*>(dd + fx.outliers), st, guard));
+    return MGARD_OK;
+}
+
+template struct CompressWork<float>;
+template struct CompressWork<double>;
+template mgard_status compress_core<float>(const Plan&, const float*, const mgard_header&, double,
+                                           double, mgard_tolmode, char*, uint64_t,
+                                           CompressWork<float>&, CompressMeta*, cudaStream_t);
+template mgard_status compress_core<double>(const Plan&, const double*, const mgard_header&, double,
+                                            double, mgard_tolmode, char*, uint64_t,
+                                            CompressWork<double>&, CompressMeta*, cudaStream_t);
+
+}  // namespace mgb

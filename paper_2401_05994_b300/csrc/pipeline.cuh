@@ -1,0 +1,57 @@
+// Compression pipeline that runs entirely in stream order on the device
+// (declarations).  Every value that depends on the data -- the norm behind a
+// relative tolerance, the bin widths, the payload size and the section
+// offsets that follow from it -- is computed and consumed on the device, so
+// a whole compression is one stream of launches with no host round trip and
+// can be captured in a CUDA graph (batched compression uses that).
+#pragma once
+
+#include "../../include/mgard_format.h"
+#include "multilevel.cuh"
+
+namespace mgb {
+
+// Byte offsets of the sections after the header (include/mgard_format.h).
+struct Sections {
+    size_t widths, lengths, word_off, esc_off, sub_off, outliers, words, total;
+};
+Sections layout(int L, uint64_t nchunks, uint64_t nout, uint64_t nwords);
+
+// Results of one compression, written by the device.
+struct CompressMeta {
+    unsigned long long total;       // bytes of the compressed buffer
+    unsigned long long off_words;   // byte offset of the payload
+    unsigned long long nwords, noutliers;
+    double tol_abs;
+    unsigned status;                // ST_* bits; ST_CAPACITY if the buffer is too small
+    unsigned pad;
+};
+
+// Device workspace of one compression, sized for one plan.  Allocated from
+// the library's pool before any capture and reused by every run.
+template <typename T>
+struct CompressWork {
+    Pyramid<T> py;
+    DevBuf top, sym, esc, hist, lengths, codes, dt, offs, totals, parts, scan;
+    mgard_status alloc(const Plan& p, cudaStream_t st);
+};
+
+// The header fields known on the host before the run.
+mgard_header header_template(const Plan& p, mgard_dtype dtype, int ndim, const int64_t* shape,
+                             double tol, double s, mgard_tolmode mode);
+
+// Compress `din` (device, the plan's shape) into `dd` (device, 16-byte
+// aligned, `cap` bytes, cap >= layout(L, nchunks, 0, 0).outliers).  Only
+// launches and device-to-device copies on `st`: the caller reads `*meta`
+// after the stream has reached this point.  When the data does not fit in
+// `cap` bytes, meta->status has ST_CAPACITY, meta->total the size needed and
+// the payload is not written.
+template <typename T>
+mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                           double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
+
+// Drop the cached batches of mgard_compress_batch (graphs and workspaces).
+void release_batches();
+
+}  // namespace mgb

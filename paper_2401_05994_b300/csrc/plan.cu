@@ -217,6 +217,8 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
         size_t fcls, wlf, wrf, wld, wrd, cbefore, rf, rwf, rwd, subf, invf, cpf, subd, invd, cpd,
             mdiag, moff;
         bool active;
+        int ireg = 0, rlo = 0, rhi = 0;
+        double rwi[5] = {0, 0, 0, 0, 0};
     };
     std::vector<std::array<AxisOff, 4>> aoff(L + 1);
     std::vector<std::array<size_t, 4>> ioff(L + 1);
@@ -300,6 +302,23 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             o.rf = blob.add(rfi);
             o.rwf = blob.add(cast<float>(rw));
             o.rwd = blob.add(rw);
+            // uniform stretches (checked entry by entry, so the row kernels'
+            // arithmetic weights equal the tables exactly)
+            int64_t ireg = 0;
+            while (ireg < m && wl[ireg] == ((ireg & 1) ? 0.5 : 1.0) &&
+                   wr[ireg] == ((ireg & 1) ? 0.5 : 0.0))
+                ++ireg;
+            o.ireg = (int)ireg;
+            o.rlo = o.rhi = 0;
+            if (mc > 2 && rf[1] == 2) {
+                int64_t hi = 1;
+                while (hi < mc && rf[hi] == 2 * hi && 2 * hi + 2 < m &&
+                       std::equal(rw.begin() + hi * 5, rw.begin() + hi * 5 + 5, rw.begin() + 5))
+                    ++hi;
+                o.rlo = 1;
+                o.rhi = (int)hi;
+                for (int t = 0; t < 5; ++t) o.rwi[t] = rw[5 + t];
+            }
             o.subf = blob.add(cast<float>(sub));
             o.invf = blob.add(cast<float>(inv));
             o.cpf = blob.add(cast<float>(tcp));
@@ -356,6 +375,13 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             G.ax[a].tsub = (const double*)(base + o.subd);
             G.ax[a].tinv = (const double*)(base + o.invd);
             G.ax[a].tcp = (const double*)(base + o.cpd);
+            F.ax[a].ireg = G.ax[a].ireg = o.ireg;
+            F.ax[a].rlo = G.ax[a].rlo = o.rlo;
+            F.ax[a].rhi = G.ax[a].rhi = o.rhi;
+            for (int t = 0; t < 5; ++t) {
+                F.ax[a].rwi[t] = (float)o.rwi[t];
+                G.ax[a].rwi[t] = o.rwi[t];
+            }
         }
     }
     return MGARD_OK;
@@ -392,21 +418,26 @@ void release_plans() {
     g_plans.clear();
 }
 
-void bin_widths(const Plan& p, double tol_abs, double s, double* w) {
+void width_denominators(const Plan& p, double s, double* den) {
     const int L = p.L;
-    const double margin = 1.0 - std::ldexp(1.0, -8);
     if (std::isinf(s)) {
         double acc = 0.0;
         for (int l = 1; l <= L; ++l) acc += 1.0 + p.K[l];
-        double denom = 1.0 + acc;
-        for (int l = 0; l <= L; ++l) w[l] = 2.0 * tol_abs / denom * margin;
+        const double denom = 1.0 + acc;
+        for (int l = 0; l <= L; ++l) den[l] = denom;
     } else {
         for (int l = 0; l <= L; ++l) {
-            double m = p.D ? p.mu[l] : 1.0;
-            double n = p.D ? (double)p.count[l] : 1.0;
-            w[l] = 2.0 * tol_abs / std::sqrt((double)(L + 1) * std::pow(4.0, s * l) * m * n) * margin;
+            const double m = p.D ? p.mu[l] : 1.0;
+            const double n = p.D ? (double)p.count[l] : 1.0;
+            den[l] = std::sqrt((double)(L + 1) * std::pow(4.0, s * l) * m * n);
         }
     }
+}
+
+void bin_widths(const Plan& p, double tol_abs, double s, double* w) {
+    std::vector<double> den(p.L + 1);
+    width_denominators(p, s, den.data());
+    for (int l = 0; l <= p.L; ++l) w[l] = 2.0 * tol_abs / den[l] * WIDTH_MARGIN;
 }
 
 }  // namespace mgb

@@ -43,7 +43,11 @@ int level_count(const int64_t n4[4], int D, int max_levels);
 // are filled and nothing touches the GPU.
 mgard_status get_plan(int ndim, const int64_t* shape, int max_levels, const Plan** out,
                       bool device = true);
-// Bin widths (host) from a plan.
+// Bin widths (host) from a plan: w[l] = 2 tol_abs / den[l] * WIDTH_MARGIN,
+// with den[l] from width_denominators (the same expression is evaluated on
+// the device when tol_abs is only known there).
+constexpr double WIDTH_MARGIN = 1.0 - 1.0 / 256.0;
+void width_denominators(const Plan& p, double s, double* den);
 void bin_widths(const Plan& p, double tol_abs, double s, double* w);
 void release_plans();
 

@@ -113,14 +113,17 @@ __device__ inline void quantize_value(double c, double /*inv_w*/, double w, int&
 constexpr int QT = 128;
 
 template <typename T>
-__global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel q, T inv_w,
-                                                 double w, uint16_t* __restrict__ sym,
+__global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel q,
+                                                 const double* __restrict__ wp,
+                                                 uint16_t* __restrict__ sym,
                                                  int32_t* __restrict__ esc,
                                                  unsigned long long* __restrict__ hist,
                                                  unsigned* status) {
     __shared__ unsigned sh[DICT];
     for (int k = threadIdx.x; k < DICT; k += blockDim.x) sh[k] = 0;
     __syncthreads();
+    const double w = *wp;
+    const T inv_w = (T)(1.0 / w);
     const int lane = threadIdx.x & 31;
     unsigned st = 0;
     // every loop bound is uniform across the block, so whole warps reach the
@@ -195,13 +198,12 @@ QLevel make_qlevel(const Plan& p, int l, bool inplace) {
 }  // namespace
 
 template <typename T>
-mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, double w,
+mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, const double* w,
                             uint16_t* sym, int32_t* esc, unsigned long long* hist,
                             unsigned* status, cudaStream_t st) {
     if (!inplace && rows3_ok(p)) return rows3_quantize<T>(p, l, c, w, sym, esc, hist, status, st);
     QLevel q = make_qlevel(p, l, inplace);
-    const T inv_w = (T)(1.0 / w);
-    MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, inv_w, w, sym, esc, hist, status));
+    MGB_LAUNCH("k_quantize", st, k_quantize<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, w, sym, esc, hist, status));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -217,7 +219,7 @@ mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const i
 }
 
 #define INST(T)                                                                                  \
-    template mgard_status quantize_level<T>(const Plan&, int, const T*, bool, double, uint16_t*, \
+    template mgard_status quantize_level<T>(const Plan&, int, const T*, bool, const double*, uint16_t*, \
                                             int32_t*, unsigned long long*, unsigned*,            \
                                             cudaStream_t);                                       \
     template mgard_status dequantize_level<T>(const Plan&, int, const uint16_t*, const int32_t*, \

@@ -6,10 +6,11 @@
 namespace mgb {
 
 // Quantize the level-l coefficients of `c` (compact level array when
-// inplace = false, the whole in-place array otherwise) with bin width w;
+// inplace = false, the whole in-place array otherwise) with the bin width
+// *w (device memory, so widths computed on the device need no round trip);
 // accumulates into `hist` (DICT counters) and ORs ST_* bits into status.
 template <typename T>
-mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, double w,
+mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, const double* w,
                             uint16_t* sym, int32_t* esc, unsigned long long* hist,
                             unsigned* status, cudaStream_t st);
 

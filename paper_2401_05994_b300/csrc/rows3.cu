@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
     const T* __restrict__ wrx = lv.ax[3].wr;
+    const int ireg = lv.ax[3].ireg;
     const int lane = threadIdx.x & 31;
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
@@ -148,7 +149,11 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 u[j] = urow[x];
                 // coarse x: neighbours x, x with weights (1, 0); new x: x-1, x+1
                 const int d = is_coarse(x, nx) ? 0 : 1;
-                const T wl = wlx[x], wr = wrx[x];
+                T wl = (x & 1) ? T(0.5) : T(1), wr = (x & 1) ? T(0.5) : T(0);
+                if (x >= ireg) {
+                    wl = wlx[x];
+                    wr = wrx[x];
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (use[k]) acc[j] += rw[k] * (wl * rows[k][x - d] + wr * rows[k][x + d]);
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
     const T* __restrict__ wrx = lv.ax[3].wr;
+    const int ireg = lv.ax[3].ireg;
     const int lane = threadIdx.x & 31;
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
@@ -200,7 +206,11 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                 const bool cx = is_coarse(x, nx);
                 const int jl = cx ? coarse_index(x, nx, ncx) : (x - 1) >> 1;
                 const int jr = cx ? jl : jl + 1;
-                const T wl = wlx[x], wr = wrx[x];
+                T wl = (x & 1) ? T(0.5) : T(1), wr = (x & 1) ? T(0.5) : T(0);
+                if (x >= ireg) {
+                    wl = wlx[x];
+                    wr = wrx[x];
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (use[k]) v[j] += rw[k] * (wl * rows[k][jl] + wr * rows[k][jr]);
@@ -221,8 +231,13 @@ template <typename Tin, typename Tout, int U>
 __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                                                     Tout* __restrict__ out, int nz, int ny,
                                                     int nx, int ncz, int ncy, int ncx,
-                                                    const Tout* __restrict__ rw) {
+                                                    AxisT<Tout> ax) {
     const int lane = threadIdx.x & 31;
+    const Tout* __restrict__ rw = ax.rw;
+    const int rlo = ax.rlo, rhi = ax.rhi;
+    Tout wi[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) wi[t] = ax.rwi[t];
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
@@ -236,6 +251,21 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                 const int J = J0 + 32 * j;
                 acc[j] = Tout(0);
                 if (J >= ncx) continue;
+                if (J >= rlo && J < rhi) {
+                    // uniform window 2J-2 .. 2J+2; on coarse rows the even taps
+                    // are coarse nodes, where z = 0
+                    const Tin* q = irow + 2 * J - 2;
+                    const Tout e0 = rowc ? Tout(0) : (Tout)q[0];
+                    const Tout e2 = rowc ? Tout(0) : (Tout)q[2];
+                    const Tout e4 = rowc ? Tout(0) : (Tout)q[4];
+                    Tout a = wi[0] * e0;
+                    a += wi[1] * (Tout)q[1];
+                    a += wi[2] * e2;
+                    a += wi[3] * (Tout)q[3];
+                    a += wi[4] * e4;
+                    acc[j] = a;
+                    continue;
+                }
                 const int f = restrict_center(J, nx, ncx);
 #pragma unroll
                 for (int t = 0; t < 5; ++t) {
@@ -367,14 +397,17 @@ __device__ inline int64_t row_rank(const QRow& q, int z, int y, bool& rowc) {
 }
 
 template <typename T, int U>
-__global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow q, T inv_w,
-                                                  double w, uint16_t* __restrict__ sym,
+__global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow q,
+                                                  const double* __restrict__ wp,
+                                                  uint16_t* __restrict__ sym,
                                                   int32_t* __restrict__ esc,
                                                   unsigned long long* __restrict__ hist,
                                                   unsigned* status) {
     __shared__ unsigned sh[HCOPIES][DICT];
     for (int k = threadIdx.x; k < HCOPIES * DICT; k += RT) (&sh[0][0])[k] = 0;
     __syncthreads();
+    const double w = *wp;
+    const T inv_w = (T)(1.0 / w);
     unsigned* my = sh[threadIdx.x & (HCOPIES - 1)];
     unsigned center = 0;   // the most frequent symbol (q = 0) is counted in a register
     unsigned st = 0;
@@ -517,7 +550,7 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     // x (always active)
     with_u8(ncx, [&](auto u) {
         MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
-            z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3].rw));
+            z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3]));
     });
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
@@ -551,14 +584,13 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
 }
 
 template <typename T>
-mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t* sym,
+mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
                             cudaStream_t st) {
     const QRow q = make_qrow(p, l);
-    const T inv_w = (T)(1.0 / w);
     with_u8(q.nx, [&](auto u) {
         MGB_LAUNCH("k3_quantize", st, k3_quantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
-            c, q, inv_w, w, sym, esc, hist, status));
+            c, q, w, sym, esc, hist, status));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -579,7 +611,7 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
 #define INST(T)                                                                                  \
     template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t);     \
     template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t); \
-    template mgard_status rows3_quantize<T>(const Plan&, int, const T*, double, uint16_t*,       \
+    template mgard_status rows3_quantize<T>(const Plan&, int, const T*, const double*, uint16_t*,       \
                                             int32_t*, unsigned long long*, unsigned*,            \
                                             cudaStream_t);                                       \
     template mgard_status rows3_dequantize<T>(const Plan&, int, const uint16_t*, const int32_t*, \

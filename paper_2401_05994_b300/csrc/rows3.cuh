@@ -26,7 +26,7 @@ template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
                            T sign, cudaStream_t st);
 template <typename T>
-mgard_status rows3_quantize(const Plan& p, int l, const T* c, double w, uint16_t* sym,
+mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
                             cudaStream_t st);
 template <typename T>

@@ -28,6 +28,11 @@ bool timing_on() { return g_on != 0; }
 
 int timing_begin(const char* name, cudaStream_t st) {
     if (!g_on) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return -1;   // launches captured into a graph are not traced
+    }
     std::lock_guard<std::mutex> lock(g_mu);
     if (g_used == g_pool.size()) {
         cudaEvent_t a, b;
