@@ -62,6 +62,11 @@ SIGNATURES = {
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
     "mgard_decompress": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "mgard_compress_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(_c_int64_p), ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
+                                            ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp]),
     "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
                                   ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
     "mgard_timing_enable": (None, [ctypes.c_int]),
@@ -309,6 +314,44 @@ def compress(field, tol: float, s: float = math.inf, mode: int = REL, out=None):
     _check(lib().mgard_compress(_ptr(field), nd, sh, dt, float(tol), float(s), int(mode),
                                 ctypes.byref(p), ctypes.byref(nbytes), 1, _stream()))
     return out[:nbytes.value]
+
+
+BATCH_GRAPH = 1
+
+
+def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, outs=None,
+                   graph: bool = False, check: bool = True):
+    """Compress a list of CUDA tensors in one call (mgard_compress_batch).
+
+    ``outs``: list of CUDA uint8 tensors (default: ``compress_bound`` bytes
+    each).  Returns ``(views, sizes, statuses)``: the compressed bytes of
+    every field (views into ``outs``), their sizes and per-field status
+    codes.  With ``check`` a failing field raises."""
+    n = len(fields)
+    if n == 0:
+        return [], [], []
+    dt = _dtype_code(fields[0].dtype)
+    for f in fields:
+        _require_cuda(f)
+        if _dtype_code(f.dtype) != dt:
+            raise ValueError("all fields of a batch share one dtype")
+    if outs is None:
+        outs = [torch.empty(compress_bound(f.shape, f.dtype), dtype=torch.uint8, device=f.device)
+                for f in fields]
+    shapes = [_shape(f.shape) for f in fields]
+    fptr = (_vp * n)(*[f.data_ptr() for f in fields])
+    optr = (_vp * n)(*[o.data_ptr() for o in outs])
+    nds = (ctypes.c_int * n)(*[sh[0] for sh in shapes])
+    shp = (_c_int64_p * n)(*[ctypes.cast(sh[1], _c_int64_p) for sh in shapes])
+    caps = (ctypes.c_size_t * n)(*[o.numel() for o in outs])
+    sizes = (ctypes.c_size_t * n)()
+    stats = (ctypes.c_int * n)()
+    st = lib().mgard_compress_batch(n, fptr, nds, shp, dt, float(tol), float(s), int(mode), optr,
+                                    caps, sizes, stats, BATCH_GRAPH if graph else 0, _stream())
+    if check:
+        _check(st)
+    sizes = [int(x) for x in sizes]
+    return [o[:min(z, o.numel())] for o, z in zip(outs, sizes)], sizes, [int(x) for x in stats]
 
 
 def info(buf):

@@ -55,6 +55,8 @@ struct BatchState {
     CompressMeta* metas = nullptr;      // device, one per field
     CompressMeta* hmetas = nullptr;     // pinned host copy
     cudaStream_t side[BATCH_STREAMS] = {};
+    cudaStream_t origin = nullptr;      // capture happens here (the caller's stream may be
+                                        // the legacy default stream, which cannot capture)
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
     cudaGraphExec_t exec = nullptr;
 
@@ -71,6 +73,7 @@ struct BatchState {
             if (side[k]) cudaStreamDestroy(side[k]);
         }
         if (fork) cudaEventDestroy(fork);
+        if (origin) cudaStreamDestroy(origin);
         if (hmetas) cudaFreeHost(hmetas);
         cudaGetLastError();
     }
@@ -82,6 +85,7 @@ struct BatchState {
             MGB_CUDA(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming));
         }
         MGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        MGB_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
         MGB_CUDA(cudaMallocHost(&hmetas, sizeof(CompressMeta) * k.n));
         MGB_CUDA(cudaMallocAsync((void**)&metas, sizeof(CompressMeta) * k.n, side[0]));
         for (int i = 0; i < k.n; ++i) {
@@ -128,11 +132,13 @@ struct BatchState {
         return MGARD_OK;
     }
 
-    mgard_status capture(cudaStream_t st) {
-        MGB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        const mgard_status e = enqueue(st);
+    // Capture fork, fields and join on the internal origin stream; the graph
+    // is then launched on the caller's stream.
+    mgard_status capture() {
+        MGB_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        const mgard_status e = enqueue(origin);
         cudaGraph_t g = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        const cudaError_t ce = cudaStreamEndCapture(origin, &g);
         if (e != MGARD_OK) {
             if (g) cudaGraphDestroy(g);
             return e;
@@ -238,7 +244,7 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         b = g_batches.front().get();
     }
     if (flags & MGARD_BATCH_GRAPH) {
-        if (!b->exec) MGB_TRY(b->capture(st));
+        if (!b->exec) MGB_TRY(b->capture());
         MGB_CUDA(cudaGraphLaunch(b->exec, st));
     } else {
         MGB_TRY(b->enqueue(st));

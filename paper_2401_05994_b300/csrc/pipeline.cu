@@ -81,7 +81,14 @@ __global__ void k_finalize(mgard_header h, const unsigned long long* __restrict_
     meta->noutliers = nout;
     meta->off_words = off_words;
     meta->total = total;
-    if (total > cap) atomicOr(&meta->status, (unsigned)ST_CAPACITY);
+    if (total > cap) {
+        atomicOr(&meta->status, (unsigned)ST_CAPACITY);
+    } else {
+        // alignment gaps after the outliers and after the payload hold zeros,
+        // so the whole buffer is a function of the input
+        for (unsigned long long i = h.off_outliers + 4 * nout; i < off_words; ++i) dd[i] = 0;
+        for (unsigned long long i = off_words + 4 * nwords; i < total; ++i) dd[i] = 0;
+    }
     const unsigned char* src = reinterpret_cast<const unsigned char*>(&h);
     for (size_t i = 0; i < sizeof(h); ++i) dd[i] = src[i];
 }
@@ -174,6 +181,7 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
         return MGARD_EINVAL;
     }
     MGB_CUDA(cudaMemsetAsync(meta, 0, sizeof(CompressMeta), st));
+    MGB_CUDA(cudaMemsetAsync(dd, 0, fx.outliers, st));   // fixed sections, gaps included
     MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
     unsigned* status = &meta->status;
     double* parts = w.parts.template as<double>();
