@@ -213,9 +213,9 @@ def batch_fields(dev, rank=0):
 
 
 def run_batch(args, rank, world, dev, barrier):
-    """Batched workload: one captured graph compresses all 64 fields; each is
-    then decompressed.  Also times the same batch without the graph and as
-    64 separate mgard_compress calls (context for what batching gains)."""
+    """Batched workload: one captured graph compresses all 64 fields, another
+    decompresses them.  Also times the same batch without the graph and as
+    64 separate calls (context for what batching gains)."""
     import torch.distributed as dist
     from paper_2401_05994_b300 import binding
     s_norm, tol = 0.0, 1e-3
@@ -236,9 +236,12 @@ def run_batch(args, rank, world, dev, barrier):
 
     def step():
         views = compress_graph()
+        binding.decompress_batch(views, outs=recs, graph=True)
+        return views
+
+    def decompress_each(views):
         for v, r in zip(views, recs):
             binding.decompress(v, out=r)
-        return views
 
     def timed(fn, steps):
         for _ in range(3):
@@ -266,6 +269,9 @@ def run_batch(args, rank, world, dev, barrier):
     ms_eager = timed(compress_eager, args.steps)
     ms_each = timed(compress_each, max(3, args.steps // 2))
     views = step()
+    ms_dec_graph = timed(lambda: binding.decompress_batch(views, outs=recs, graph=True), args.steps)
+    ms_dec_each = timed(lambda: decompress_each(views), max(3, args.steps // 2))
+    views = step()
     worst = 0.0
     comp = 0
     for f, v, r in zip(fields, views, recs):
@@ -286,6 +292,7 @@ def run_batch(args, rank, world, dev, barrier):
                             "separate_calls": ms_each},
             "compress_gbs": {"graph": gbs(ms_graph), "streams_no_graph": gbs(ms_eager),
                              "separate_calls": gbs(ms_each)},
+            "decompress_ms": {"graph": ms_dec_graph, "separate_calls": ms_dec_each},
             "clocks": clocks,
             "verify": {"worst_error_over_tol": worst, "ok": worst <= 1.0,
                        "ratio": nbytes / comp},

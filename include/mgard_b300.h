@@ -244,11 +244,35 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
  * Synchronizes `stream` once, at the end.  Returns MGARD_OK when every
  * field succeeded, else the status of the first failing field. */
 #define MGARD_BATCH_GRAPH 1
+#define MGARD_BATCH_AUTOTUNE 2   /* run mgard_autotune on every new shape of the batch first */
 mgard_status mgard_compress_batch(int n, const void* const* fields, const int* ndims,
                                   const int64_t* const* shapes, mgard_dtype dtype, double tol,
                                   double s, mgard_tolmode mode, void* const* outs,
                                   const size_t* caps, size_t* out_bytes, mgard_status* statuses,
                                   int flags, void* stream);
+
+/* Batched decompression of buffers made by mgard_compress /
+ * mgard_compress_batch: ins[i] (device, in_bytes[i] bytes) into fields[i]
+ * (device, field_caps[i] bytes, at least the field's size).  The headers
+ * come to the host in one round trip; the buffers then decompress on
+ * internal streams (MGARD_BATCH_GRAPH: from a captured graph, replayed for
+ * identical arguments and headers).  statuses[i] (host, may be NULL):
+ * MGARD_ECORRUPT for a buffer that fails validation, MGARD_ECAPACITY for a
+ * field buffer that is too small; the other buffers still decompress.
+ * Synchronizes `stream`.  Returns MGARD_OK or the first failing status. */
+mgard_status mgard_decompress_batch(int n, const void* const* ins, const size_t* in_bytes,
+                                    void* const* fields, const size_t* field_caps,
+                                    mgard_status* statuses, int flags, void* stream);
+
+/* Autotuner: times every launch shape of the row kernels (elements per
+ * lane per batch 2/4/8, grids sized for 4/8/16 blocks per SM) on each level
+ * of `shape` and keeps the fastest for all later calls on that shape in
+ * this process (kept in the shape's plan; mgard_release_plans forgets it).
+ * Results are bit-identical for every launch shape.  `report` (may be
+ * NULL) receives one line per level and kernel.  Synchronizes `stream`.
+ * Shapes that run on the generic 4D kernels have nothing to tune. */
+mgard_status mgard_autotune(int ndim, const int64_t* shape, mgard_dtype dtype, char* report,
+                            size_t report_cap, void* stream);
 
 /* Read the header of a compressed buffer (host or device pointer). */
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],

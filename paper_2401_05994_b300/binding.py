@@ -62,6 +62,11 @@ SIGNATURES = {
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
     "mgard_decompress": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "mgard_decompress_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
+                                              ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp]),
+    "mgard_autotune": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_char_p,
+                                      ctypes.c_size_t, _vp]),
     "mgard_compress_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(_c_int64_p), ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
@@ -317,10 +322,20 @@ def compress(field, tol: float, s: float = math.inf, mode: int = REL, out=None):
 
 
 BATCH_GRAPH = 1
+BATCH_AUTOTUNE = 2
+
+
+def autotune(shape, dtype=torch.float32) -> str:
+    """Tune the row kernels' launch shapes for ``shape`` (mgard_autotune);
+    returns the tuner's report."""
+    nd, sh = _shape(shape)
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().mgard_autotune(nd, sh, _dtype_code(dtype), buf, len(buf), _stream()))
+    return buf.value.decode()
 
 
 def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, outs=None,
-                   graph: bool = False, check: bool = True):
+                   graph: bool = False, check: bool = True, autotune: bool = False):
     """Compress a list of CUDA tensors in one call (mgard_compress_batch).
 
     ``outs``: list of CUDA uint8 tensors (default: ``compress_bound`` bytes
@@ -347,11 +362,39 @@ def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, out
     sizes = (ctypes.c_size_t * n)()
     stats = (ctypes.c_int * n)()
     st = lib().mgard_compress_batch(n, fptr, nds, shp, dt, float(tol), float(s), int(mode), optr,
-                                    caps, sizes, stats, BATCH_GRAPH if graph else 0, _stream())
+                                    caps, sizes, stats,
+                                    (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0),
+                                    _stream())
     if check:
         _check(st)
     sizes = [int(x) for x in sizes]
     return [o[:min(z, o.numel())] for o, z in zip(outs, sizes)], sizes, [int(x) for x in stats]
+
+
+def decompress_batch(bufs, outs=None, graph: bool = False, check: bool = True):
+    """Decompress a list of CUDA uint8 tensors (mgard_decompress_batch).
+    ``outs``: list of CUDA tensors of the fields' shapes and dtypes (default:
+    allocated from the headers).  Returns ``(outs, statuses)``."""
+    n = len(bufs)
+    if n == 0:
+        return [], []
+    for b in bufs:
+        _require_cuda(b)
+    if outs is None:
+        outs = []
+        for b in bufs:
+            m = info(b)
+            outs.append(torch.empty(m["shape"], dtype=m["dtype"], device=b.device))
+    iptr = (_vp * n)(*[b.data_ptr() for b in bufs])
+    isz = (ctypes.c_size_t * n)(*[b.numel() for b in bufs])
+    optr = (_vp * n)(*[o.data_ptr() for o in outs])
+    ocap = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
+    stats = (ctypes.c_int * n)()
+    st = lib().mgard_decompress_batch(n, iptr, isz, optr, ocap, stats,
+                                      BATCH_GRAPH if graph else 0, _stream())
+    if check:
+        _check(st)
+    return outs, [int(x) for x in stats]
 
 
 def info(buf):

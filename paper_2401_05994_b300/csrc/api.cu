@@ -187,41 +187,17 @@ mgard_status read_header(const void* in, size_t in_bytes, bool in_dev, mgard_hea
     } else {
         std::memcpy(h, in, sizeof(*h));
     }
-    auto bad = [](const char* why) {
-        set_error(std::string("corrupt header: ") + why);
-        return MGARD_ECORRUPT;
-    };
-    if (std::memcmp(h->magic, MGARD_MAGIC, 8) != 0) return bad("magic");
-    if (h->version != MGARD_FORMAT_VERSION) return bad("version");
-    if (h->dtype > 1) return bad("dtype");
-    if (h->ndim < 1 || h->ndim > 4) return bad("ndim");
-    if (h->dict != DICT || h->chunk != CHUNK) return bad("dictionary or chunk size");
-    uint64_t n = 1;
-    for (uint32_t i = 0; i < h->ndim; ++i) {
-        if (h->shape[i] < 1 || h->shape[i] > (int64_t(1) << 40)) return bad("shape");
-        n *= (uint64_t)h->shape[i];
-        if (n > (uint64_t(1) << 40)) return bad("shape");
-    }
-    if (n != h->nsymbols) return bad("symbol count");
-    if (h->nchunks != (n + CHUNK - 1) / CHUNK) return bad("chunk count");
-    if (h->nlevels > 64) return bad("levels");
-    if (h->noutliers > n || h->nwords > n + h->nchunks) return bad("section sizes");
-    Sections s = layout((int)h->nlevels, h->nchunks, h->noutliers, h->nwords);
-    if (h->off_widths != s.widths || h->off_lengths != s.lengths || h->off_word_off != s.word_off ||
-        h->off_esc_off != s.esc_off || h->off_sub_off != s.sub_off ||
-        h->off_outliers != s.outliers || h->off_words != s.words ||
-        h->total_bytes != s.total)
-        return bad("section offsets");
-    if (s.total > in_bytes) return bad("truncated buffer");
-    if (!(h->tol_abs > 0.0) || !std::isfinite(h->tol_abs)) return bad("tolerance");
+    MGB_TRY(check_header(*h, in_bytes));
     widths->resize(h->nlevels + 1);
     if (in_dev)
-        MGB_CUDA(cudaMemcpy(widths->data(), (const char*)in + s.widths, 8 * (h->nlevels + 1),
+        MGB_CUDA(cudaMemcpy(widths->data(), (const char*)in + h->off_widths, 8 * (h->nlevels + 1),
                             cudaMemcpyDeviceToHost));
     else
-        std::memcpy(widths->data(), (const char*)in + s.widths, 8 * (h->nlevels + 1));
-    for (double v : *widths)
-        if (!(v > 0.0) || !std::isfinite(v)) return bad("bin width");
+        std::memcpy(widths->data(), (const char*)in + h->off_widths, 8 * (h->nlevels + 1));
+    if (!widths_valid(widths->data(), (int)h->nlevels)) {
+        set_error("corrupt header: bin width");
+        return MGARD_ECORRUPT;
+    }
     return MGARD_OK;
 }
 
@@ -230,41 +206,25 @@ mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::ve
                              const char* din, void** field, bool out_dev, void* dst,
                              cudaStream_t st) {
     const int64_t N = p.total();
-    const int L = p.L;
-    DevBuf stage;
+    DevBuf stage, stat;
     T* dout = (T*)dst;
     if (!out_dev) {
         MGB_TRY(stage.alloc(N * sizeof(T), st));
         dout = stage.as<T>();
     }
-    DevBuf codes, dt, sym, esc, stat;
-    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
-    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
-    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
-    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    DecompressWork<T> work;
+    MGB_TRY(work.alloc(p, st));
     MGB_TRY(stat.alloc(sizeof(unsigned), st));
     MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
-    const uint8_t* lengths = (const uint8_t*)(din + h.off_lengths);
-    MGB_TRY(huffman_tables(lengths, codes.as<uint32_t>(), dt.as<DecodeTables>(), st));
-    MGB_TRY(huffman_decode((const uint32_t*)(din + h.off_words), h.nwords,
-                           (const uint64_t*)(din + h.off_word_off),
-                           (const uint16_t*)(din + h.off_sub_off), dt.as<DecodeTables>(), N,
-                           (const int32_t*)(din + h.off_outliers), h.noutliers,
-                           (const uint64_t*)(din + h.off_esc_off), sym.as<uint16_t>(),
-                           esc.as<int32_t>(), stat.as<unsigned>(), st));
+    MGB_TRY(decompress_core<T>(p, h, w.data(), din, dout, work, stat.as<unsigned>(), st));
     unsigned status = 0;
     MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     MGB_TRY(status_to_error(status));
-    Pyramid<T> py;
-    MGB_TRY(py.alloc(p, st));
-    for (int l = 0; l <= L; ++l) {
-        T* lvl = l == L ? dout : py.lv[l];
-        MGB_TRY(dequantize_level<T>(p, l, sym.as<uint16_t>(), esc.as<int32_t>(), false, w[l], lvl, st));
+    if (!out_dev) {
+        MGB_CUDA(cudaMemcpyAsync(dst, dout, N * sizeof(T), cudaMemcpyDeviceToHost, st));
+        MGB_CUDA(cudaStreamSynchronize(st));
     }
-    MGB_TRY(recompose_pyramid<T>(p, dout, dout, py, st));
-    if (!out_dev) MGB_CUDA(cudaMemcpyAsync(dst, dout, N * sizeof(T), cudaMemcpyDeviceToHost, st));
-    MGB_CUDA(cudaStreamSynchronize(st));
     *field = dst;
     return MGARD_OK;
 }
@@ -637,6 +597,7 @@ void mgard_free(void* p) {
 
 void mgard_release_plans(void) {
     release_batches();
+    release_decompress_batches();
     release_plans();
 }
 

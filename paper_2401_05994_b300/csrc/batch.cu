@@ -46,6 +46,75 @@ struct BatchKey {
     }
 };
 
+// Internal streams of a batch: work forks from the caller's stream onto
+// `side`, joins back, and graph capture happens on `origin` (the caller's
+// stream may be the legacy default stream, which cannot capture).
+struct Lanes {
+    cudaStream_t side[BATCH_STREAMS] = {};
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    cudaGraphExec_t exec = nullptr;
+
+    mgard_status init() {
+        for (int s = 0; s < BATCH_STREAMS; ++s) {
+            MGB_CUDA(cudaStreamCreateWithFlags(&side[s], cudaStreamNonBlocking));
+            MGB_CUDA(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming));
+        }
+        MGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        MGB_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+        return MGARD_OK;
+    }
+    void destroy() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        for (int k = 0; k < BATCH_STREAMS; ++k) {
+            if (join[k]) cudaEventDestroy(join[k]);
+            if (side[k]) cudaStreamDestroy(side[k]);
+            join[k] = nullptr;
+            side[k] = nullptr;
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (origin) cudaStreamDestroy(origin);
+        fork = nullptr;
+        origin = nullptr;
+        cudaGetLastError();
+    }
+    // Fork from st, run body(i, stream) for every item on the side streams
+    // (round robin), join back into st.
+    template <typename F>
+    mgard_status run(cudaStream_t st, int n, F&& body) {
+        const int nside = std::min(BATCH_STREAMS, std::max(n, 1));
+        MGB_CUDA(cudaEventRecord(fork, st));
+        for (int s = 0; s < nside; ++s) MGB_CUDA(cudaStreamWaitEvent(side[s], fork, 0));
+        for (int i = 0; i < n; ++i) MGB_TRY(body(i, side[i % nside]));
+        for (int s = 0; s < nside; ++s) {
+            MGB_CUDA(cudaEventRecord(join[s], side[s]));
+            MGB_CUDA(cudaStreamWaitEvent(st, join[s], 0));
+        }
+        return MGARD_OK;
+    }
+    // Run through a graph captured on the first call.
+    template <typename F>
+    mgard_status run_graph(cudaStream_t st, int n, F&& body) {
+        if (!exec) {
+            MGB_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+            const mgard_status e = run(origin, n, body);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(origin, &g);
+            if (e != MGARD_OK) {
+                if (g) cudaGraphDestroy(g);
+                return e;
+            }
+            MGB_CUDA(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            MGB_CUDA(ie);
+        }
+        MGB_CUDA(cudaGraphLaunch(exec, st));
+        return MGARD_OK;
+    }
+};
+
 struct BatchState {
     BatchKey key;
     std::vector<const Plan*> plans;
@@ -54,40 +123,26 @@ struct BatchState {
     std::vector<std::unique_ptr<CompressWork<double>>> wd;
     CompressMeta* metas = nullptr;      // device, one per field
     CompressMeta* hmetas = nullptr;     // pinned host copy
-    cudaStream_t side[BATCH_STREAMS] = {};
-    cudaStream_t origin = nullptr;      // capture happens here (the caller's stream may be
-                                        // the legacy default stream, which cannot capture)
-    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
-    cudaGraphExec_t exec = nullptr;
+    Lanes lanes;
 
     ~BatchState() {
-        if (exec) cudaGraphExecDestroy(exec);
         // workspaces free themselves on side[0]; wait for that before the
         // stream goes away
         wf.clear();
         wd.clear();
-        if (metas) cudaFreeAsync(metas, side[0]);
-        if (side[0]) cudaStreamSynchronize(side[0]);
-        for (int k = 0; k < BATCH_STREAMS; ++k) {
-            if (join[k]) cudaEventDestroy(join[k]);
-            if (side[k]) cudaStreamDestroy(side[k]);
-        }
-        if (fork) cudaEventDestroy(fork);
-        if (origin) cudaStreamDestroy(origin);
+        if (metas) cudaFreeAsync(metas, lanes.side[0]);
+        if (lanes.side[0]) cudaStreamSynchronize(lanes.side[0]);
+        lanes.destroy();
         if (hmetas) cudaFreeHost(hmetas);
         cudaGetLastError();
     }
 
     mgard_status init(const BatchKey& k, const int* ndims, const int64_t* const* shapes) {
         key = k;
-        for (int s = 0; s < BATCH_STREAMS; ++s) {
-            MGB_CUDA(cudaStreamCreateWithFlags(&side[s], cudaStreamNonBlocking));
-            MGB_CUDA(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming));
-        }
-        MGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        MGB_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+        MGB_TRY(lanes.init());
+        cudaStream_t s0 = lanes.side[0];
         MGB_CUDA(cudaMallocHost(&hmetas, sizeof(CompressMeta) * k.n));
-        MGB_CUDA(cudaMallocAsync((void**)&metas, sizeof(CompressMeta) * k.n, side[0]));
+        MGB_CUDA(cudaMallocAsync((void**)&metas, sizeof(CompressMeta) * k.n, s0));
         for (int i = 0; i < k.n; ++i) {
             const Plan* p;
             MGB_TRY(get_plan(ndims[i], shapes[i], -1, &p));
@@ -96,58 +151,33 @@ struct BatchState {
                                             k.s, (mgard_tolmode)k.mode));
             if (k.dtype == MGARD_F32) {
                 wf.emplace_back(new CompressWork<float>());
-                MGB_TRY(wf.back()->alloc(*p, side[0]));
+                MGB_TRY(wf.back()->alloc(*p, s0));
             } else {
                 wd.emplace_back(new CompressWork<double>());
-                MGB_TRY(wd.back()->alloc(*p, side[0]));
+                MGB_TRY(wd.back()->alloc(*p, s0));
             }
         }
         MGB_TRY(huffman_prepare());
-        MGB_CUDA(cudaStreamSynchronize(side[0]));
-        return MGARD_OK;
-    }
-
-    // Fork from `st`, every field on a side stream, join back into `st`.
-    mgard_status enqueue(cudaStream_t st) {
-        const int nside = std::min(BATCH_STREAMS, std::max(key.n, 1));
-        MGB_CUDA(cudaEventRecord(fork, st));
-        for (int s = 0; s < nside; ++s) MGB_CUDA(cudaStreamWaitEvent(side[s], fork, 0));
-        for (int i = 0; i < key.n; ++i) {
-            cudaStream_t ss = side[i % nside];
-            char* dd = (char*)key.outs[i];
-            const uint64_t cap = key.caps[i];
-            if (key.dtype == MGARD_F32)
-                MGB_TRY(compress_core<float>(*plans[i], (const float*)key.fields[i], heads[i],
-                                             key.tol, key.s, (mgard_tolmode)key.mode, dd, cap,
-                                             *wf[i], metas + i, ss));
-            else
-                MGB_TRY(compress_core<double>(*plans[i], (const double*)key.fields[i], heads[i],
-                                              key.tol, key.s, (mgard_tolmode)key.mode, dd, cap,
-                                              *wd[i], metas + i, ss));
-        }
-        for (int s = 0; s < nside; ++s) {
-            MGB_CUDA(cudaEventRecord(join[s], side[s]));
-            MGB_CUDA(cudaStreamWaitEvent(st, join[s], 0));
+        MGB_CUDA(cudaStreamSynchronize(s0));
+        if (k.flags & MGARD_BATCH_AUTOTUNE) {   // each distinct shape once, before any capture
+            std::vector<const Plan*> done;
+            for (const Plan* p : plans) {
+                if (std::find(done.begin(), done.end(), p) != done.end()) continue;
+                done.push_back(p);
+                MGB_TRY(autotune_plan(*p, (mgard_dtype)k.dtype, s0, nullptr));
+            }
         }
         return MGARD_OK;
     }
 
-    // Capture fork, fields and join on the internal origin stream; the graph
-    // is then launched on the caller's stream.
-    mgard_status capture() {
-        MGB_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
-        const mgard_status e = enqueue(origin);
-        cudaGraph_t g = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(origin, &g);
-        if (e != MGARD_OK) {
-            if (g) cudaGraphDestroy(g);
-            return e;
-        }
-        MGB_CUDA(ce);
-        const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
-        cudaGraphDestroy(g);
-        MGB_CUDA(ie);
-        return MGARD_OK;
+    mgard_status field(int i, cudaStream_t ss) {
+        char* dd = (char*)key.outs[i];
+        const uint64_t cap = key.caps[i];
+        if (key.dtype == MGARD_F32)
+            return compress_core<float>(*plans[i], (const float*)key.fields[i], heads[i], key.tol,
+                                        key.s, (mgard_tolmode)key.mode, dd, cap, *wf[i], metas + i, ss);
+        return compress_core<double>(*plans[i], (const double*)key.fields[i], heads[i], key.tol,
+                                     key.s, (mgard_tolmode)key.mode, dd, cap, *wd[i], metas + i, ss);
     }
 };
 
@@ -160,6 +190,8 @@ void release_batches() {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     g_batches.clear();
 }
+
+void release_decompress_batches();
 
 }  // namespace mgb
 
@@ -180,7 +212,8 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         return MGARD_EDTYPE;
     }
     if (!(tol > 0.0) || !std::isfinite(tol) || std::isnan(s) || s < 0.0 ||
-        (mode != MGARD_ABS && mode != MGARD_REL) || (flags & ~MGARD_BATCH_GRAPH)) {
+        (mode != MGARD_ABS && mode != MGARD_REL) ||
+        (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_AUTOTUNE))) {
         set_error("tol must be positive and finite, s >= 0 or INFINITY, mode ABS or REL");
         return MGARD_EINVAL;
     }
@@ -243,12 +276,9 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         while (g_batches.size() > BATCH_CACHE) g_batches.pop_back();
         b = g_batches.front().get();
     }
-    if (flags & MGARD_BATCH_GRAPH) {
-        if (!b->exec) MGB_TRY(b->capture());
-        MGB_CUDA(cudaGraphLaunch(b->exec, st));
-    } else {
-        MGB_TRY(b->enqueue(st));
-    }
+    auto body = [b](int i, cudaStream_t ss) { return b->field(i, ss); };
+    if (flags & MGARD_BATCH_GRAPH) MGB_TRY(b->lanes.run_graph(st, n, body));
+    else MGB_TRY(b->lanes.run(st, n, body));
     MGB_CUDA(cudaMemcpyAsync(b->hmetas, b->metas, sizeof(CompressMeta) * n, cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     mgard_status first = MGARD_OK;
@@ -264,6 +294,208 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         if (e != MGARD_OK && first == MGARD_OK) {
             first = e;
             set_error("batched compression: field " + std::to_string(i) + " failed");
+        }
+    }
+    return first;
+}
+
+// ---------------------------------------------------------------------------
+// Batched decompression.  The headers (and bin widths) of all buffers come
+// to the host in one round trip; the rest runs as for compression: one
+// stream-ordered pipeline per buffer over the internal streams, optionally
+// from a captured graph.  The graph bakes in the headers' sizes and widths,
+// so they are part of the cache key.
+namespace mgb {
+namespace {
+
+constexpr size_t HEAD_BYTES = 768;   // header + widths of up to 64 levels
+
+struct DecompressKey {
+    int device = -1;
+    int n = 0, flags = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<const void*> ins;
+    std::vector<size_t> in_bytes;
+    std::vector<void*> outs;
+    std::vector<size_t> caps;
+    std::vector<char> heads;   // HEAD_BYTES per buffer
+    bool operator==(const DecompressKey& o) const {
+        return device == o.device && n == o.n && flags == o.flags && stream == o.stream &&
+               ins == o.ins && in_bytes == o.in_bytes && outs == o.outs && caps == o.caps &&
+               heads == o.heads;
+    }
+};
+
+struct DecompressBatch {
+    DecompressKey key;
+    std::vector<const Plan*> plans;       // null for a buffer whose header failed
+    std::vector<mgard_header> heads;
+    std::vector<std::vector<double>> widths;
+    std::vector<std::unique_ptr<DecompressWork<float>>> wf;
+    std::vector<std::unique_ptr<DecompressWork<double>>> wd;
+    std::vector<int> items;               // buffers that run
+    std::vector<mgard_status> pre;        // result of the host checks, per buffer
+    unsigned* stat = nullptr;             // device, one per buffer
+    unsigned* hstat = nullptr;            // pinned
+    Lanes lanes;
+
+    ~DecompressBatch() {
+        wf.clear();
+        wd.clear();
+        if (stat) cudaFreeAsync(stat, lanes.side[0]);
+        if (lanes.side[0]) cudaStreamSynchronize(lanes.side[0]);
+        lanes.destroy();
+        if (hstat) cudaFreeHost(hstat);
+        cudaGetLastError();
+    }
+
+    mgard_status item(int k, cudaStream_t ss) {
+        const int i = items[k];
+        const mgard_header& h = heads[i];
+        MGB_CUDA(cudaMemsetAsync(stat + i, 0, sizeof(unsigned), ss));
+        if (h.dtype == MGARD_F32)
+            return decompress_core<float>(*plans[i], h, widths[i].data(), (const char*)key.ins[i],
+                                          (float*)key.outs[i], *wf[i], stat + i, ss);
+        return decompress_core<double>(*plans[i], h, widths[i].data(), (const char*)key.ins[i],
+                                       (double*)key.outs[i], *wd[i], stat + i, ss);
+    }
+};
+
+std::list<std::unique_ptr<DecompressBatch>> g_dbatches;
+
+}  // namespace
+
+void release_decompress_batches() {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_dbatches.clear();
+}
+
+}  // namespace mgb
+
+extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
+                                               const size_t* in_bytes, void* const* fields,
+                                               const size_t* field_caps, mgard_status* statuses,
+                                               int flags, void* stream) {
+    if (n < 0 || (n > 0 && (!ins || !in_bytes || !fields || !field_caps))) {
+        set_error("null argument");
+        return MGARD_EINVAL;
+    }
+    if (flags & ~MGARD_BATCH_GRAPH) {
+        set_error("unknown flags");
+        return MGARD_EINVAL;
+    }
+    if (n == 0) return MGARD_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        cudaPointerAttributes a;
+        if (!ins[i] || !fields[i] || cudaPointerGetAttributes(&a, ins[i]) != cudaSuccess ||
+            a.type != cudaMemoryTypeDevice || cudaPointerGetAttributes(&a, fields[i]) != cudaSuccess ||
+            a.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            set_error("batched decompression takes device buffers only");
+            return MGARD_EINVAL;
+        }
+    }
+    DecompressKey key;
+    MGB_CUDA(cudaGetDevice(&key.device));
+    key.n = n;
+    key.flags = flags;
+    key.stream = st;
+    key.heads.assign((size_t)n * HEAD_BYTES, 0);
+    // one round trip for every header
+    {
+        char* pin = nullptr;
+        MGB_CUDA(cudaMallocHost(&pin, (size_t)n * HEAD_BYTES));
+        std::unique_ptr<char, cudaError_t (*)(void*)> guard(pin, cudaFreeHost);
+        for (int i = 0; i < n; ++i) {
+            const size_t k = std::min(in_bytes[i], HEAD_BYTES);
+            if (k) MGB_CUDA(cudaMemcpyAsync(pin + i * HEAD_BYTES, ins[i], k, cudaMemcpyDeviceToHost, st));
+        }
+        MGB_CUDA(cudaStreamSynchronize(st));
+        std::memcpy(key.heads.data(), pin, (size_t)n * HEAD_BYTES);
+    }
+    for (int i = 0; i < n; ++i) {
+        key.ins.push_back(ins[i]);
+        key.in_bytes.push_back(in_bytes[i]);
+        key.outs.push_back(fields[i]);
+        key.caps.push_back(field_caps[i]);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    DecompressBatch* b = nullptr;
+    for (auto it = g_dbatches.begin(); it != g_dbatches.end(); ++it)
+        if ((*it)->key == key) {
+            g_dbatches.splice(g_dbatches.begin(), g_dbatches, it);
+            b = g_dbatches.front().get();
+            break;
+        }
+    if (!b) {
+        std::vector<mgard_status> pre(n, MGARD_OK);
+        std::unique_ptr<DecompressBatch> nb(new DecompressBatch());
+        nb->key = key;
+        MGB_TRY(nb->lanes.init());
+        cudaStream_t s0 = nb->lanes.side[0];
+        MGB_CUDA(cudaMallocHost(&nb->hstat, sizeof(unsigned) * n));
+        MGB_CUDA(cudaMallocAsync((void**)&nb->stat, sizeof(unsigned) * n, s0));
+        nb->plans.assign(n, nullptr);
+        nb->heads.resize(n);
+        nb->widths.resize(n);
+        nb->wf.resize(n);
+        nb->wd.resize(n);
+        for (int i = 0; i < n; ++i) {
+            mgard_header& h = nb->heads[i];
+            std::memcpy(&h, key.heads.data() + i * HEAD_BYTES, sizeof(h));
+            if (in_bytes[i] < sizeof(h) || check_header(h, in_bytes[i]) != MGARD_OK ||
+                h.off_widths + 8 * (h.nlevels + 1) > HEAD_BYTES) {
+                pre[i] = MGARD_ECORRUPT;
+                continue;
+            }
+            nb->widths[i].resize(h.nlevels + 1);
+            std::memcpy(nb->widths[i].data(), key.heads.data() + i * HEAD_BYTES + h.off_widths,
+                        8 * (h.nlevels + 1));
+            const Plan* p;
+            if (!widths_valid(nb->widths[i].data(), (int)h.nlevels) ||
+                get_plan((int)h.ndim, h.shape, -1, &p) != MGARD_OK || p->L != (int)h.nlevels) {
+                pre[i] = MGARD_ECORRUPT;
+                continue;
+            }
+            const size_t need = (size_t)p->total() * (h.dtype == MGARD_F64 ? 8 : 4);
+            if (field_caps[i] < need) {
+                pre[i] = MGARD_ECAPACITY;
+                continue;
+            }
+            nb->plans[i] = p;
+            if (h.dtype == MGARD_F32) {
+                nb->wf[i].reset(new DecompressWork<float>());
+                MGB_TRY(nb->wf[i]->alloc(*p, s0));
+            } else {
+                nb->wd[i].reset(new DecompressWork<double>());
+                MGB_TRY(nb->wd[i]->alloc(*p, s0));
+            }
+            nb->items.push_back(i);
+        }
+        MGB_CUDA(cudaStreamSynchronize(s0));
+        nb->pre = pre;
+        g_dbatches.push_front(std::move(nb));
+        while (g_dbatches.size() > BATCH_CACHE) g_dbatches.pop_back();
+        b = g_dbatches.front().get();
+    }
+    const std::vector<mgard_status>& pre = b->pre;
+    const int m = (int)b->items.size();
+    auto body = [b](int k, cudaStream_t ss) { return b->item(k, ss); };
+    if (m) {
+        if (flags & MGARD_BATCH_GRAPH) MGB_TRY(b->lanes.run_graph(st, m, body));
+        else MGB_TRY(b->lanes.run(st, m, body));
+        MGB_CUDA(cudaMemcpyAsync(b->hstat, b->stat, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, st));
+    }
+    MGB_CUDA(cudaStreamSynchronize(st));
+    mgard_status first = MGARD_OK;
+    for (int i = 0; i < n; ++i) {
+        mgard_status e = pre[i];
+        if (e == MGARD_OK && b->plans[i] && (b->hstat[i] & ST_CORRUPT)) e = MGARD_ECORRUPT;
+        if (statuses) statuses[i] = e;
+        if (e != MGARD_OK && first == MGARD_OK) {
+            first = e;
+            set_error("batched decompression: buffer " + std::to_string(i) + " failed");
         }
     }
     return first;

@@ -89,6 +89,8 @@ struct AxisT {
     const T* tcp;        // [mc] Thomas: c'_J
     const double* mdiag; // [m]  mass matrix of the level-l grid: diagonal
     const double* moff;  // [m]  mass matrix: M[i][i+1] (last entry 0)
+    const T* mdt;        // [m]  the same two tables in T
+    const T* mot;
     // Uniform parts of the tables, so row kernels need no per-element table
     // loads there: for i < ireg the interpolation weights are (1, 0) at even
     // i and (1/2, 1/2) at odd i; for coarse J in [rlo, rhi) the restriction

@@ -618,6 +618,16 @@ mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void
 
 }  // namespace
 
+template <typename T>
+mgard_status correct_coarse(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
+                            T sign, cudaStream_t st) {
+    return correct<T>(p, l, z, coarse, t0, t1, sign, st);
+}
+template mgard_status correct_coarse<float>(const Plan&, int, const float*, float*, void*, void*,
+                                            float, cudaStream_t);
+template mgard_status correct_coarse<double>(const Plan&, int, const double*, double*, void*,
+                                             void*, double, cudaStream_t);
+
 cudaMemPool_t workspace_pool() {
     static std::mutex mu;
     static std::map<int, cudaMemPool_t> pools;
@@ -724,6 +734,7 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
 }
 
 int64_t mass_norm_parts(const Plan& p, int l) {
+    if (rows3_ok(p)) return rows3_mass_norm_blocks(p, l);
     const dim3 g = grid3(p.level<float>(l).n, RED_THREADS, 8, 74);
     return (int64_t)g.x * g.y * g.z;
 }
@@ -742,6 +753,7 @@ int64_t energy_parts_offset(const Plan& p, int l) {
 
 template <typename T>
 mgard_status mass_norm2_partials(const Plan& p, int l, const T* u, double* part, cudaStream_t st) {
+    if (rows3_ok(p)) return rows3_mass_norm<T>(p, l, u, part, st);
     const Level<T>& lv = p.level<T>(l);   // holds the mass tables of level l
     const dim3 g = grid3(lv.n, RED_THREADS, 8, 74);   // fixed grid: deterministic partial sums
     MGB_LAUNCH("k_mass_norm", st, k_mass_norm<T><<<g, RED_THREADS, 0, st>>>(u, lv, part));

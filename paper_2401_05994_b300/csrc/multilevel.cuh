@@ -69,6 +69,13 @@ template <typename T>
 mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& py,
                                cudaStream_t st);
 
+// coarse += sign * M_{l-1}^{-1} P^T M_l z for level l (the correction of a
+// decomposition step, sign = +1, or of a recomposition step, sign = -1);
+// t0, t1 are the pyramid's restriction buffers.
+template <typename T>
+mgard_status correct_coarse(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
+                            T sign, cudaStream_t st);
+
 // In-place layout <-> pyramid (levels below L only).
 template <typename T>
 mgard_status scatter_levels(const Plan& p, const Pyramid<T>& py, T* data, cudaStream_t st);

@@ -237,11 +237,91 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
     return MGARD_OK;
 }
 
+mgard_status check_header(const mgard_header& h, size_t in_bytes) {
+    auto bad = [](const char* why) {
+        set_error(std::string("corrupt header: ") + why);
+        return MGARD_ECORRUPT;
+    };
+    if (std::memcmp(h.magic, MGARD_MAGIC, 8) != 0) return bad("magic");
+    if (h.version != MGARD_FORMAT_VERSION) return bad("version");
+    if (h.dtype > 1) return bad("dtype");
+    if (h.ndim < 1 || h.ndim > 4) return bad("ndim");
+    if (h.dict != DICT || h.chunk != CHUNK) return bad("dictionary or chunk size");
+    uint64_t n = 1;
+    for (uint32_t i = 0; i < h.ndim; ++i) {
+        if (h.shape[i] < 1 || h.shape[i] > (int64_t(1) << 40)) return bad("shape");
+        n *= (uint64_t)h.shape[i];
+        if (n > (uint64_t(1) << 40)) return bad("shape");
+    }
+    if (n != h.nsymbols) return bad("symbol count");
+    if (h.nchunks != (n + CHUNK - 1) / CHUNK) return bad("chunk count");
+    if (h.nlevels > 64) return bad("levels");
+    if (h.noutliers > n || h.nwords > n + h.nchunks) return bad("section sizes");
+    Sections s = layout((int)h.nlevels, h.nchunks, h.noutliers, h.nwords);
+    if (h.off_widths != s.widths || h.off_lengths != s.lengths || h.off_word_off != s.word_off ||
+        h.off_esc_off != s.esc_off || h.off_sub_off != s.sub_off ||
+        h.off_outliers != s.outliers || h.off_words != s.words ||
+        h.total_bytes != s.total)
+        return bad("section offsets");
+    if (s.total > in_bytes) return bad("truncated buffer");
+    if (!(h.tol_abs > 0.0) || !std::isfinite(h.tol_abs)) return bad("tolerance");
+    return MGARD_OK;
+}
+
+bool widths_valid(const double* w, int L) {
+    for (int l = 0; l <= L; ++l)
+        if (!(w[l] > 0.0) || !std::isfinite(w[l])) return false;
+    return true;
+}
+
+template <typename T>
+mgard_status DecompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
+    const int64_t N = p.total();
+    MGB_TRY(py.alloc(p, st));
+    MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
+    MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
+    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status decompress_core(const Plan& p, const mgard_header& h, const double* w,
+                             const char* din, T* dout, DecompressWork<T>& work, unsigned* status,
+                             cudaStream_t st) {
+    const int64_t N = p.total();
+    const int L = p.L;
+    uint16_t* sym = work.sym.template as<uint16_t>();
+    int32_t* esc = work.esc.template as<int32_t>();
+    DecodeTables* dt = work.dt.template as<DecodeTables>();
+    MGB_TRY(huffman_tables((const uint8_t*)(din + h.off_lengths), work.codes.template as<uint32_t>(),
+                           dt, st));
+    MGB_TRY(huffman_decode((const uint32_t*)(din + h.off_words), h.nwords,
+                           (const uint64_t*)(din + h.off_word_off),
+                           (const uint16_t*)(din + h.off_sub_off), dt, N,
+                           (const int32_t*)(din + h.off_outliers), h.noutliers,
+                           (const uint64_t*)(din + h.off_esc_off), sym, esc, status, st));
+    for (int l = 0; l <= L; ++l) {
+        T* lvl = l == L ? dout : work.py.lv[l];
+        MGB_TRY(dequantize_level<T>(p, l, sym, esc, false, w[l], lvl, st));
+    }
+    MGB_TRY(recompose_pyramid<T>(p, dout, dout, work.py, st));
+    return MGARD_OK;
+}
+
 template struct CompressWork<float>;
 template struct CompressWork<double>;
 template mgard_status compress_core<float>(const Plan&, const float*, const mgard_header&, double,
                                            double, mgard_tolmode, char*, uint64_t,
                                            CompressWork<float>&, CompressMeta*, cudaStream_t);
+template struct DecompressWork<float>;
+template struct DecompressWork<double>;
+template mgard_status decompress_core<float>(const Plan&, const mgard_header&, const double*,
+                                             const char*, float*, DecompressWork<float>&,
+                                             unsigned*, cudaStream_t);
+template mgard_status decompress_core<double>(const Plan&, const mgard_header&, const double*,
+                                              const char*, double*, DecompressWork<double>&,
+                                              unsigned*, cudaStream_t);
 template mgard_status compress_core<double>(const Plan&, const double*, const mgard_header&, double,
                                             double, mgard_tolmode, char*, uint64_t,
                                             CompressWork<double>&, CompressMeta*, cudaStream_t);

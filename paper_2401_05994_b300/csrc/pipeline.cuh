@@ -6,6 +6,8 @@
 // can be captured in a CUDA graph (batched compression uses that).
 #pragma once
 
+#include <string>
+
 #include "../../include/mgard_format.h"
 #include "multilevel.cuh"
 
@@ -51,7 +53,36 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
                            double s, mgard_tolmode mode, char* dd, uint64_t cap,
                            CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
 
-// Drop the cached batches of mgard_compress_batch (graphs and workspaces).
+// Host validation of a header read from a buffer of in_bytes bytes
+// (magic, version, sizes and section offsets); MGARD_ECORRUPT on failure.
+mgard_status check_header(const mgard_header& h, size_t in_bytes);
+bool widths_valid(const double* w, int L);
+
+// Device workspace of one decompression.
+template <typename T>
+struct DecompressWork {
+    Pyramid<T> py;
+    DevBuf codes, dt, sym, esc;
+    mgard_status alloc(const Plan& p, cudaStream_t st);
+};
+
+// Decompress the device image `din` (header h and widths w validated on
+// the host) into `dout` (device).  Launches only; a corrupt stream ORs
+// ST_CORRUPT into *status (device) and leaves `dout` meaningless but every
+// access in bounds.
+template <typename T>
+mgard_status decompress_core(const Plan& p, const mgard_header& h, const double* w,
+                             const char* din, T* dout, DecompressWork<T>& work, unsigned* status,
+                             cudaStream_t st);
+
+// Time every launch shape of the row kernels on each level of the plan's
+// shape and keep the fastest in the plan (tune.cu); `report` receives one
+// line per level and kernel.
+mgard_status autotune_plan(const Plan& p, mgard_dtype dtype, cudaStream_t st, std::string* report);
+
+// Drop the cached batches of mgard_compress_batch / mgard_decompress_batch
+// (graphs and workspaces).
 void release_batches();
+void release_decompress_batches();
 
 }  // namespace mgb

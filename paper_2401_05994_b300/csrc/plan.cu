@@ -211,11 +211,12 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
     }
     p.K.assign(L + 1, 1.0);
     p.mu.assign(L + 1, 1.0);
+    p.tune.assign(L + 1, std::array<RowCfg, RK_COUNT>());
 
     Blob blob;
     struct AxisOff {
         size_t fcls, wlf, wrf, wld, wrd, cbefore, rf, rwf, rwd, subf, invf, cpf, subd, invd, cpd,
-            mdiag, moff;
+            mdiag, moff, mdiagf, mofff;
         bool active;
         int ireg = 0, rlo = 0, rhi = 0;
         double rwi[5] = {0, 0, 0, 0, 0};
@@ -243,6 +244,8 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             p.mu[l] *= gmax;
             o.mdiag = blob.add(mdiag);
             o.moff = blob.add(moff);
+            o.mdiagf = blob.add(cast<float>(mdiag));
+            o.mofff = blob.add(cast<float>(moff));
             if (l == 0) continue;
             auto cp = coarse_positions(m);
             int64_t mc = (int64_t)cp.size();
@@ -359,6 +362,10 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             if (!o.active) continue;
             F.ax[a].mdiag = G.ax[a].mdiag = (const double*)(base + o.mdiag);
             F.ax[a].moff = G.ax[a].moff = (const double*)(base + o.moff);
+            F.ax[a].mdt = (const float*)(base + o.mdiagf);
+            F.ax[a].mot = (const float*)(base + o.mofff);
+            G.ax[a].mdt = (const double*)(base + o.mdiag);
+            G.ax[a].mot = (const double*)(base + o.moff);
             if (l == 0) continue;
             F.ax[a].fcls = G.ax[a].fcls = (const int*)(base + o.fcls);
             F.ax[a].cbefore = G.ax[a].cbefore = (const int*)(base + o.cbefore);

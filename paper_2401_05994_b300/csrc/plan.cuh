@@ -12,6 +12,14 @@
 
 namespace mgb {
 
+// Launch shape of a row kernel: elements per lane per batch (2, 4 or 8) and
+// resident blocks per SM the grid is sized for; 0 = the built-in choice.
+enum RowKind { RK_COEFF = 0, RK_FILL, RK_RX, RK_RROWS, RK_QUANT, RK_DEQUANT, RK_COUNT };
+struct RowCfg {
+    int u = 0;
+    int bpsm = 0;
+};
+
 struct Plan {
     int D = 0;                       // active axes
     int L = 0;                       // levels above level 0
@@ -25,6 +33,12 @@ struct Plan {
     std::vector<Level<double>> ld;
     std::vector<LevelIndex> lidx;    // [l] finest positions of level-l nodes
     void* dbuf = nullptr;
+    // launch shapes chosen by the autotuner, per level and row kernel (set by
+    // autotune_plan; every choice gives bit-identical results)
+    mutable std::vector<std::array<RowCfg, RK_COUNT>> tune;
+    RowCfg row_cfg(int l, int kind) const {
+        return l >= 0 && l < (int)tune.size() ? tune[l][kind] : RowCfg();
+    }
     int64_t total() const { return n4[0] * n4[1] * n4[2] * n4[3]; }
     int64_t level_size(int l) const { return shape[l][0] * shape[l][1] * shape[l][2] * shape[l][3]; }
     template <typename T> const Level<T>& level(int l) const;

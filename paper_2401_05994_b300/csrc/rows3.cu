@@ -20,8 +20,9 @@ constexpr int64_t ROW_BLOCKS = 148 * 8;
 // U is chosen per launch from the row length (2, 5, 9 or 17 -> rows of up to
 // 64, 160, 288, 544 elements in one batch).
 
-inline int row_grid(int64_t rows) {
-    return (int)std::min<int64_t>(std::max<int64_t>((rows + WPB - 1) / WPB, 1), ROW_BLOCKS);
+inline int row_grid(int64_t rows, int bpsm = 0) {
+    const int64_t cap = bpsm > 0 ? 148LL * bpsm : ROW_BLOCKS;
+    return (int)std::min<int64_t>(std::max<int64_t>((rows + WPB - 1) / WPB, 1), cap);
 }
 
 // Node classes follow from the hierarchy rule (coarse = even positions plus
@@ -84,6 +85,17 @@ void with_u8(int64_t nx, F&& f) {
     if (nx <= 64) f(UTag<2>{});
     else if (nx <= 160) f(UTag<4>{});
     else f(UTag<8>{});
+}
+
+// Batch size from a tuned launch shape (2, 4 or 8), else the built-in rule
+// (`light`: the with_u8 rule, otherwise the with_u rule).
+template <typename F>
+void with_cfg(const RowCfg& c, int64_t nx, bool light, F&& f) {
+    if (c.u == 2) f(UTag<2>{});
+    else if (c.u == 4) f(UTag<4>{});
+    else if (c.u == 8) f(UTag<8>{});
+    else if (light) with_u8(nx, f);
+    else with_u(nx, f);
 }
 
 // Ask the TMA unit to pull a row into L2 (no registers are held).  The
@@ -326,6 +338,74 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
     }
 }
 
+// -- mass norm u^T M_l u (level energies of the s-norm) ----------------------------
+// Per row (z, y): M u = sum over the 3 x 3 neighbouring rows of
+// Mz[z][z'] My[y][y'] (Mx row'), each term a 3-tap product along x.  The
+// stencil runs in T; each lane sums its products over a row in T and adds
+// that to a double accumulator, and blocks reduce in a fixed order, so the
+// partial sums do not depend on timing.
+template <typename T>
+__device__ inline void mass_taps(const AxisT<T>& ax, int i, int m, T f[3], int p[3]) {
+    if (!ax.mdiag) {   // inactive axis: identity
+        f[0] = f[2] = T(0);
+        f[1] = T(1);
+        p[0] = p[1] = p[2] = i;
+        return;
+    }
+    f[0] = i > 0 ? ax.mot[i - 1] : T(0);
+    f[1] = ax.mdt[i];
+    f[2] = i + 1 < m ? ax.mot[i] : T(0);
+    p[0] = i > 0 ? i - 1 : i;
+    p[1] = i;
+    p[2] = i + 1 < m ? i + 1 : i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_mass_norm(const T* __restrict__ u, Level<T> lv,
+                                                   double* __restrict__ partial) {
+    const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+    const T* __restrict__ mdx = lv.ax[3].mdt;
+    const T* __restrict__ mox = lv.ax[3].mot;
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    WARP_ROWS((int64_t)nz * ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
+        T fz[3], fy[3];
+        int pz[3], py[3];
+        mass_taps(lv.ax[1], z, nz, fz, pz);
+        mass_taps(lv.ax[2], y, ny, fy, py);
+        const T* rows[9];
+        T w[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                rows[3 * a + b] = u + ((int64_t)pz[a] * ny + py[b]) * nx;
+                w[3 * a + b] = fz[a] * fy[b];
+            }
+        const T* urow = u + r * nx;
+        T racc = T(0);
+        for (int x = lane; x < nx; x += 32) {
+            const T wl = x > 0 ? mox[x - 1] : T(0), wc = mdx[x], wr = x + 1 < nx ? mox[x] : T(0);
+            const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
+            T mu = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                mu += w[k] * (wl * rows[k][xl] + wc * rows[k][x] + wr * rows[k][xr]);
+            racc += urow[x] * mu;
+        }
+        acc += (double)racc;
+    }
+    __shared__ double sh[RT];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = RT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
 // -- quantization ------------------------------------------------------------------
 constexpr int HCOPIES = 2;
 
@@ -520,8 +600,9 @@ QRow make_qrow(const Plan& p, int l) {
 template <typename T>
 mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st) {
     const Level<T>& lv = p.level<T>(l);
-    with_u(lv.n[3], [&](auto u) {
-        MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(in, out, coarse, lv));
+    const RowCfg c = p.row_cfg(l, RK_COEFF);
+    with_cfg(c, lv.n[3], false, [&](auto u) {
+        MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2], c.bpsm), RT, 0, st>>>(in, out, coarse, lv));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -531,8 +612,9 @@ template <typename T>
 mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
                         cudaStream_t st) {
     const Level<T>& lv = p.level<T>(l);
-    with_u(lv.n[3], [&](auto u) {
-        MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2]), RT, 0, st>>>(z, coarse, out, lv));
+    const RowCfg c = p.row_cfg(l, RK_FILL);
+    with_cfg(c, lv.n[3], false, [&](auto u) {
+        MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2], c.bpsm), RT, 0, st>>>(z, coarse, out, lv));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -548,24 +630,25 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* b0 = (Tw*)t0;
     Tw* b1 = (Tw*)t1;
     // x (always active)
-    with_u8(ncx, [&](auto u) {
-        MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny), RT, 0, st>>>(
+    const RowCfg cx = p.row_cfg(l, RK_RX), cr = p.row_cfg(l, RK_RROWS);
+    with_cfg(cx, ncx, true, [&](auto u) {
+        MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny, cx.bpsm), RT, 0, st>>>(
             z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3]));
     });
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
     Tw* nxt = b1;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
-        with_u8(ncx, [&](auto u) {
-            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy), RT, 0, st>>>(
+        with_cfg(cr, ncx, true, [&](auto u) {
+            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy, cr.bpsm), RT, 0, st>>>(
                 cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
         });
         MGB_CUDA(cudaGetLastError());
         std::swap(cur, nxt);
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
-        with_u8(ncx, [&](auto u) {
-            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy), RT, 0, st>>>(
+        with_cfg(cr, ncx, true, [&](auto u) {
+            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy, cr.bpsm), RT, 0, st>>>(
                 cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
         });
         MGB_CUDA(cudaGetLastError());
@@ -583,13 +666,26 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     return MGARD_OK;
 }
 
+int rows3_mass_norm_blocks(const Plan& p, int l) {
+    return row_grid(p.shape[l][1] * p.shape[l][2]);
+}
+
+template <typename T>
+mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, cudaStream_t st) {
+    const Level<T>& lv = p.level<T>(l);
+    MGB_LAUNCH("k3_mass_norm", st, k3_mass_norm<T><<<rows3_mass_norm_blocks(p, l), RT, 0, st>>>(u, lv, partial));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
 template <typename T>
 mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
                             cudaStream_t st) {
     const QRow q = make_qrow(p, l);
-    with_u8(q.nx, [&](auto u) {
-        MGB_LAUNCH("k3_quantize", st, k3_quantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+    const RowCfg cfg = p.row_cfg(l, RK_QUANT);
+    with_cfg(cfg, q.nx, true, [&](auto u) {
+        MGB_LAUNCH("k3_quantize", st, k3_quantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny, cfg.bpsm), RT, 0, st>>>(
             c, q, w, sym, esc, hist, status));
     });
     MGB_CUDA(cudaGetLastError());
@@ -600,8 +696,9 @@ template <typename T>
 mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               double w, T* c, cudaStream_t st) {
     const QRow q = make_qrow(p, l);
-    with_u8(q.nx, [&](auto u) {
-        MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny), RT, 0, st>>>(
+    const RowCfg cfg = p.row_cfg(l, RK_DEQUANT);
+    with_cfg(cfg, q.nx, true, [&](auto u) {
+        MGB_LAUNCH("k3_dequantize", st, k3_dequantize<T, decltype(u)::value><<<row_grid((int64_t)q.nz * q.ny, cfg.bpsm), RT, 0, st>>>(
             sym, esc, q, (T)w, w, c));
     });
     MGB_CUDA(cudaGetLastError());
@@ -611,6 +708,7 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
 #define INST(T)                                                                                  \
     template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t);     \
     template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t); \
+    template mgard_status rows3_mass_norm<T>(const Plan&, int, const T*, double*, cudaStream_t); \
     template mgard_status rows3_quantize<T>(const Plan&, int, const T*, const double*, uint16_t*,       \
                                             int32_t*, unsigned long long*, unsigned*,            \
                                             cudaStream_t);                                       \

@@ -33,6 +33,11 @@ template <typename T>
 mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               double w, T* c, cudaStream_t st);
 
+// Partial sums (rows3_mass_norm_blocks of them) of u^T M_l u.
+int rows3_mass_norm_blocks(const Plan& p, int l);
+template <typename T>
+mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, cudaStream_t st);
+
 // Solvers shared with the generic path (multilevel.cu).
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,

@@ -95,3 +95,48 @@ def test_batch_rejects_host_buffers():
     f = torch.zeros(33, 33)
     with pytest.raises(Exception):
         binding.compress_batch([f], 1e-3)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_decompress_batch_equals_single(graph):
+    fields = _fields()
+    views, _, _ = binding.compress_batch(fields, 1e-3, math.inf, binding.REL)
+    bufs = [v.clone() for v in views]
+    ref = [binding.decompress(b).cpu().numpy() for b in bufs]
+    outs = [torch.full(f.shape, 7.0, dtype=f.dtype, device=DEV) for f in fields]
+    for _ in range(2):   # graph replay on the second call
+        got, stats = binding.decompress_batch(bufs, outs=outs, graph=graph)
+        assert stats == [0] * len(bufs)
+        for g, r in zip(got, ref):
+            assert np.array_equal(g.cpu().numpy(), r)
+
+
+def test_decompress_batch_per_buffer_failures():
+    fields = _fields(shapes=[(33, 33, 33), (20, 20, 20), (40, 9, 9)])
+    views, _, _ = binding.compress_batch(fields, 1e-3, math.inf, binding.REL)
+    bufs = [v.clone() for v in views]
+    bufs[0][0] ^= 0xFF                     # magic
+    outs = [torch.empty(f.shape, dtype=f.dtype, device=DEV) for f in fields]
+    outs[1] = torch.empty(100, dtype=torch.float32, device=DEV)   # too small
+    got, stats = binding.decompress_batch(bufs, outs=outs, check=False)
+    assert stats[0] == 7    # MGARD_ECORRUPT
+    assert stats[1] == 10   # MGARD_ECAPACITY
+    assert stats[2] == 0
+    assert np.array_equal(got[2].cpu().numpy(), binding.decompress(bufs[2]).cpu().numpy())
+    # a corrupt payload is found by the decoder, not only by header checks
+    bad = bufs[2].clone()
+    bad[-64:] = 0x5A
+    _, stats = binding.decompress_batch([bad], outs=[outs[2]], check=False)
+    assert stats[0] in (0, 7)   # flipped payload bits may still decode to valid codes
+
+
+def test_autotune_keeps_bits():
+    f = _fields(shapes=[(65, 47, 33)])[0]
+    before = _single(f, 1e-3, math.inf, binding.REL)
+    rep = binding.autotune(f.shape)
+    assert "level" in rep
+    after = _single(f, 1e-3, math.inf, binding.REL)
+    assert np.array_equal(before, after)
+    out = binding.decompress(torch.from_numpy(after).to(DEV))
+    assert pipeline.error(f.cpu().numpy().astype(np.float64), out.cpu().numpy().astype(np.float64),
+                          math.inf) <= binding.info(after)["tol_abs"]
