@@ -1,0 +1,127 @@
+"""Pins of the predictor oracle (features, MLP, Adam) against facts that do
+not come from the oracle itself: a hand-evaluated network, central finite
+differences of the loss, the closed form of Adam's first step, learning a
+linear map, and features of fields whose coefficients are known exactly."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import multilevel, predictor
+
+
+def _params(nin, h, rng, scale=0.7):
+    ntrain, ntot = predictor.sizes(nin, h)
+    p = np.zeros(ntot)
+    p[:ntrain] = rng.standard_normal(ntrain) * scale
+    p[ntrain:ntrain + nin] = rng.standard_normal(nin) * 0.1   # mu
+    p[ntrain + nin:] = rng.uniform(0.5, 2.0, nin)              # sd
+    return p
+
+
+def test_forward_hand_evaluated():
+    nin, h = 2, 2
+    # W1 = I, b1 = (0, -1), W2 = [[1, 1], [0, 1]], b2 = 0, w3 = (1, 2), b3 = 0.5
+    p = np.array([1, 0, 0, 1, 0, -1, 1, 1, 0, 1, 0, 0, 1, 2, 0.5, 0, 0, 1, 1], dtype=float)
+    # x = (3, 0.5): z1 = (3, -0.5) -> h1 = (3, 0) -> z2 = (3, 0) -> y = 3 + 0.5
+    assert predictor.forward(p, np.array([[3.0, 0.5]]), nin, h)[0] == 3.5
+    # x = (-1, 4): z1 = (-1, 3) -> h1 = (0, 3) -> z2 = (3, 3) -> y = 3 + 6 + 0.5
+    assert predictor.forward(p, np.array([[-1.0, 4.0]]), nin, h)[0] == 9.5
+    # standardization: mu = (1, 1), sd = (2, 0) (sd 0 -> 1): x = (7, 1) -> xn = (3, 0)
+    q = p.copy()
+    q[15:17] = 1.0
+    q[17:19] = [2.0, 0.0]
+    assert predictor.forward(q, np.array([[7.0, 1.0]]), nin, h)[0] == 3.5
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gradient_matches_central_differences(seed):
+    rng = np.random.default_rng(seed)
+    nin, h, B = 7, 5, 9
+    p = _params(nin, h, rng)
+    x = rng.standard_normal((B, nin))
+    t = rng.standard_normal(B)
+    loss, g = predictor.loss_grad(p, x, t, nin, h)
+    ntrain, _ = predictor.sizes(nin, h)
+    assert g.shape == (ntrain,)
+    assert np.isclose(loss, np.mean((predictor.forward(p, x, nin, h) - t) ** 2), rtol=1e-14)
+    eps = 1e-6
+    num = np.zeros(ntrain)
+    for k in range(ntrain):
+        a, b = p.copy(), p.copy()
+        a[k] += eps
+        b[k] -= eps
+        la = np.mean((predictor.forward(a, x, nin, h) - t) ** 2)
+        lb = np.mean((predictor.forward(b, x, nin, h) - t) ** 2)
+        num[k] = (la - lb) / (2 * eps)
+    assert np.max(np.abs(num - g)) <= 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(10)
+    g = rng.standard_normal(8)
+    lr, eps = 1e-2, 1e-8
+    q, m, v = predictor.adam_step(p, g, np.zeros(8), np.zeros(8), 1, lr, eps=eps)
+    # bias-corrected moments after one step are g and g^2
+    assert np.allclose(q[:8], p[:8] - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    assert np.array_equal(q[8:], p[8:])
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_training_learns_a_linear_map():
+    rng = np.random.default_rng(4)
+    nin, h, B = 3, 16, 64
+    x = rng.standard_normal((B, nin))
+    t = 1.5 * x[:, 0] - 0.5 * x[:, 2] + 0.25
+    ntrain, ntot = predictor.sizes(nin, h)
+    p = predictor.set_norm(np.concatenate([rng.standard_normal(ntrain) * 0.3, np.zeros(2 * nin)]),
+                           x, nin, h)
+    m = np.zeros(ntrain)
+    v = np.zeros(ntrain)
+    l0, _ = predictor.loss_grad(p, x, t, nin, h)
+    for step in range(1, 801):
+        loss, g = predictor.loss_grad(p, x, t, nin, h)
+        p, m, v = predictor.adam_step(p, g, m, v, step, 1e-2)
+    assert loss < 1e-3 * l0
+
+
+def test_features_of_a_constant_field():
+    u = np.full((9, 9, 9), 2.5)
+    v = multilevel.decompose(u)
+    f = predictor.features(v, 2.5, 3, 10.0)
+    L = 3                                          # 9 -> 5 -> 3 -> 2
+    per = predictor.PER_LEVEL
+    for slot in range(L + 1):
+        base = slot * per
+        lvl = L - slot
+        n = 2 ** 3 if lvl == 0 else [8, 27, 125, 729][lvl] - [8, 27, 125, 729][lvl - 1]
+        assert f[base] == pytest.approx(math.log10(n))
+        if lvl == 0:    # |c| = a: below no threshold, log ratio 0
+            assert f[base + 1] == pytest.approx(0.0, abs=1e-12)
+            assert f[base + 2] == pytest.approx(0.0, abs=1e-12)
+            assert np.all(f[base + 3:base + per] == 0.0)
+        else:           # exact zeros: clamped to 1e-12 a, below every threshold
+            assert f[base + 1] == pytest.approx(-12.0, abs=1e-9)
+            assert f[base + 2] == pytest.approx(0.0, abs=1e-9)
+            assert np.all(f[base + 3:base + per] == 1.0)
+    assert np.all(f[(L + 1) * per:predictor.NLEV * per] == 0.0)
+    g = predictor.NLEV * per
+    assert list(f[g:]) == [3, 3, pytest.approx(math.log10(729)), 1.0]
+
+
+def test_features_of_a_single_spike():
+    # 1D, 9 nodes, u = e_1: node 1 is new on the finest level and its coarse
+    # neighbours hold 0, so the finest coefficients are exactly (1, 0, 0, 0):
+    # r = (0, -12, -12, -12), mean -9, population std sqrt(108 - 81) and
+    # three of four coefficients below every threshold.
+    u = np.zeros(9)
+    u[1] = 1.0
+    v = multilevel.decompose(u)
+    f = predictor.features(v, 1.0, 1, 2.0)
+    assert f[0] == pytest.approx(math.log10(4))
+    assert f[1] == pytest.approx(-9.0)
+    assert f[2] == pytest.approx(math.sqrt(27.0))
+    assert np.all(f[3:3 + predictor.NTHR] == 0.75)
+    g = predictor.NLEV * predictor.PER_LEVEL
+    assert list(f[g:]) == [1, 3, pytest.approx(math.log10(9)), pytest.approx(math.log10(2))]
