@@ -25,6 +25,13 @@ Stream layout
     the first, the bit offset inside the chunk where each starts and the
     number of escapes before it in the chunk (six uint16 per chunk), so the
     four sub-chunks of a chunk can be decoded independently.
+Fill chunks
+    With ``fill_symbol`` given (the compressor passes the symbol of q = 0),
+    a chunk whose every symbol is ``fill_symbol`` is stored with no payload
+    words and zero sub-chunk offsets; a decoder recognises it by its word
+    count of 0 (any other nonempty chunk needs at least one word, since every
+    code has at least one bit).  This keeps smooth regions from costing a bit
+    per symbol.
 """
 from __future__ import annotations
 
@@ -101,11 +108,12 @@ def canonical_codes(lengths) -> np.ndarray:
     return codes
 
 
-def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
+def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK, fill_symbol=None):
     """Chunked MSB-first packing.
 
-    Returns ``(words uint32, word_offsets uint64, esc_offsets uint64)``;
-    the offset arrays have one entry per chunk (exclusive prefixes)."""
+    Returns ``(words uint32, word_offsets uint64, esc_offsets uint64,
+    sub_offsets uint16 [nchunks, 6])``; the offset arrays have one entry per
+    chunk (exclusive prefixes)."""
     symbols = np.asarray(symbols, dtype=np.int64)
     lengths = np.asarray(lengths, dtype=np.int64)
     codes = canonical_codes(lengths).astype(np.uint64)
@@ -115,6 +123,10 @@ def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
     if n and np.any(ln == 0):
         raise ValueError("symbol without a code")
     cid = np.arange(n) // chunk
+    if fill_symbol is not None and n:
+        not_fill = np.bincount(cid, weights=(symbols != fill_symbol), minlength=nchunks)
+        fill_chunk = not_fill == 0
+        ln = np.where(fill_chunk[cid], 0, ln)      # fill chunks emit no bits
     chunk_bits = np.bincount(cid, weights=ln, minlength=nchunks).astype(np.int64)
     chunk_words = (chunk_bits + 31) // 32
     word_off = np.zeros(nchunks, dtype=np.uint64)
@@ -142,11 +154,12 @@ def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
         start_of_chunk = np.concatenate([[0], csum])[cid * chunk]
         bit_in_chunk = csum - ln - start_of_chunk
         gbit = word_off[cid].astype(np.int64) * 32 + bit_in_chunk
-        w = gbit >> 5
-        b = gbit & 31
+        emit = ln > 0
+        w = gbit[emit] >> 5
+        b = gbit[emit] & 31
         # place the code in a 64-bit window starting at word w (MSB first)
-        sh = (64 - ln - b).astype(np.uint64)
-        val = codes[symbols] << sh
+        sh = (64 - ln[emit] - b).astype(np.uint64)
+        val = codes[symbols[emit]] << sh
         hi = val >> np.uint64(32)
         lo = val & np.uint64(0xFFFFFFFF)
         np.bitwise_or.at(words, w, hi)
@@ -154,15 +167,22 @@ def encode(symbols, lengths, esc_symbol: int = 0, chunk: int = CHUNK):
     return words[:total].astype(np.uint32), word_off, esc_off, sub_off
 
 
-def decode(words, word_off, lengths, n: int, chunk: int = CHUNK, sub_off=None) -> np.ndarray:
+def decode(words, word_off, lengths, n: int, chunk: int = CHUNK, sub_off=None,
+           fill_symbol=None) -> np.ndarray:
     """Bit-by-bit canonical decoding (slow; small inputs only).  With
-    ``sub_off`` every sub-chunk starts from its recorded bit offset."""
+    ``sub_off`` every sub-chunk starts from its recorded bit offset; with
+    ``fill_symbol`` a chunk of zero words holds only that symbol."""
     lengths = np.asarray(lengths, dtype=np.int64)
     codes = canonical_codes(lengths)
     table = {(int(lengths[s]), int(codes[s])): s for s in np.nonzero(lengths)[0]}
     out = np.zeros(n, dtype=np.uint16)
     words = np.asarray(words, dtype=np.uint64)
-    for c in range((n + chunk - 1) // chunk):
+    nchunks = (n + chunk - 1) // chunk
+    for c in range(nchunks):
+        nw = (int(word_off[c + 1]) if c + 1 < nchunks else len(words)) - int(word_off[c])
+        if fill_symbol is not None and nw == 0:
+            out[c * chunk:min(n, (c + 1) * chunk)] = fill_symbol
+            continue
         for i in range(c * chunk, min(n, (c + 1) * chunk)):
             k = (i - c * chunk) // SUB
             if i == c * chunk or (sub_off is not None and (i - c * chunk) % SUB == 0):

@@ -25,7 +25,8 @@ def compress(u: np.ndarray, tol: float, s: float = math.inf, relative: bool = Tr
     v = multilevel.decompose(u, max_levels)
     symbols, outliers, hist = quantize.quantize(v, widths, max_levels, precision)
     lengths = huffman.code_lengths(hist)
-    words, word_off, esc_off, sub_off = huffman.encode(symbols, lengths)
+    words, word_off, esc_off, sub_off = huffman.encode(symbols, lengths,
+                                                        fill_symbol=quantize.R)
     return dict(shape=u.shape, L=h.L, tol_abs=tol_abs, widths=widths, s=s,
                 symbols=symbols, outliers=outliers, hist=hist, lengths=lengths,
                 words=words, word_off=word_off, esc_off=esc_off, sub_off=sub_off,
@@ -35,7 +36,7 @@ def compress(u: np.ndarray, tol: float, s: float = math.inf, relative: bool = Tr
 def decompress(c, symbols=None) -> np.ndarray:
     if symbols is None:
         symbols = huffman.decode(c["words"], c["word_off"], c["lengths"],
-                                 len(c["symbols"]))
+                                 len(c["symbols"]), fill_symbol=quantize.R)
     counts = quantize.level_counts(c["shape"], c["max_levels"])
     levels = quantize.dequantize_levels(symbols, c["outliers"], counts,
                                         c["widths"], c["precision"])

@@ -122,3 +122,22 @@ def test_round_trip_with_chunks(n):
         # escape prefix counts
         per_chunk = [int(np.sum(sym[c * 1024:(c + 1) * 1024] == 0)) for c in range(len(off))]
         assert esc.tolist() == list(np.concatenate([[0], np.cumsum(per_chunk)[:-1]]))
+
+
+def test_fill_chunks_take_no_words():
+    # chunk 0: only the fill symbol; chunk 1: mixed; chunk 2 (partial): only fill
+    L = np.zeros(4096, dtype=np.int64)
+    L[[2048, 2047, 2049]] = [1, 2, 2]
+    sym = np.full(1024 * 2 + 300, 2048)
+    sym[1024 + 5] = 2047
+    sym[1024 + 900] = 2049
+    words, off, esc, sub = huffman.encode(sym, L, fill_symbol=2048)
+    # the mixed chunk alone: 1022 one-bit codes + two 2-bit codes = 1026 bits
+    assert len(words) == (1026 + 31) // 32
+    assert list(off) == [0, 0, len(words)]
+    assert np.all(sub[0] == 0) and np.all(sub[2] == 0)
+    assert np.array_equal(huffman.decode(words, off, L, len(sym), fill_symbol=2048), sym)
+    assert np.array_equal(huffman.decode(words, off, L, len(sym), sub_off=sub, fill_symbol=2048), sym)
+    # without the rule every chunk pays one bit per symbol
+    w2, _, _, _ = huffman.encode(sym, L)
+    assert len(w2) == 32 + (1026 + 31) // 32 + (300 + 31) // 32
