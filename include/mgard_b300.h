@@ -161,7 +161,8 @@ mgard_status mgard_huffman_codebook(const uint64_t* hist, uint8_t* lengths, uint
  * the chunk's escapes before each of them; a sub-chunk past the end of the
  * data starts at the chunk's end), outliers (escapes gathered in symbol order
  * from `escapes`, which is indexed by symbol position; capacity
- * `outliers_cap`).
+ * `outliers_cap`).  A chunk whose symbols are all MGARD_DICT/2 (q = 0) is
+ * stored with no words and zero sub-chunk offsets.
  * *nwords and *noutliers (host) receive the totals; synchronizes the
  * stream.  MGARD_ECAPACITY (totals still returned, nothing packed) if a
  * capacity is short; MGARD_EINVAL if a symbol has no code or `symbols` is
@@ -273,6 +274,78 @@ mgard_status mgard_decompress_batch(int n, const void* const* ins, const size_t*
  * Shapes that run on the generic 4D kernels have nothing to tune. */
 mgard_status mgard_autotune(int ndim, const int64_t* shape, mgard_dtype dtype, char* report,
                             size_t report_cap, void* stream);
+
+/* ---- Ratio-targeted compression and the learned tolerance predictor -----
+ * No counterpart in the paper.  A "sizer" decomposes a field once and then
+ * gives the exact compressed size at any tolerance (quantization, codebook
+ * and count pass; no packing), the predictor's features, and the final
+ * compression, all from that one decomposition.  The field (device) must
+ * stay unchanged while the sizer lives. */
+typedef struct mgard_sizer_s mgard_sizer;
+mgard_status mgard_sizer_create(const void* field, int ndim, const int64_t* shape,
+                                mgard_dtype dtype, double s, mgard_sizer** out, void* stream);
+/* Exact size in bytes of mgard_compress(field, tol, s, mode); synchronizes. */
+mgard_status mgard_sizer_size(mgard_sizer* z, double tol, mgard_tolmode mode, size_t* bytes,
+                              void* stream);
+/* Predictor inputs (device, MGARD_NFEAT floats): per level, finest first
+ * (at most 12 levels, missing ones zero): log10 of the coefficient count,
+ * mean and standard deviation of r = log10(max(|c|, 1e-12 a) / a) with
+ * a = max|u|, and the fractions of |c| below 10^(-j/2) a for j = 0..14;
+ * then the number of active axes, L, log10 N and log10(target_ratio). */
+#define MGARD_NFEAT 220
+mgard_status mgard_sizer_features(mgard_sizer* z, double target_ratio, float* features,
+                                  void* stream);
+/* mgard_compress at `tol` from the sizer's decomposition into `out` (device,
+ * 16-byte aligned, *out_bytes capacity in, size out). */
+mgard_status mgard_sizer_compress(mgard_sizer* z, double tol, mgard_tolmode mode, void* out,
+                                  size_t* out_bytes, void* stream);
+void mgard_sizer_free(mgard_sizer* z);
+
+/* Network: MGARD_NFEAT inputs standardized as (x - mean) / max(sd, 0.05)
+ * -> 2 x MGARD_MLP_HIDDEN relu
+ * units -> 1 output (log10 of the relative tolerance).  Parameters (device
+ * floats): W1 [H, NFEAT] row-major, b1, W2 [H, H], b2, w3, b3 (the first
+ * MGARD_MLP_NTRAIN, trained), then the inputs' mean and standard deviation. */
+#define MGARD_MLP_HIDDEN 64
+#define MGARD_MLP_NTRAIN (MGARD_MLP_HIDDEN * MGARD_NFEAT + \
+                          MGARD_MLP_HIDDEN * MGARD_MLP_HIDDEN + 3 * MGARD_MLP_HIDDEN + 1)
+#define MGARD_MLP_NPARAM (MGARD_MLP_NTRAIN + 2 * MGARD_NFEAT)
+/* He-uniform weights from a counter-based generator (splitmix64), zero
+ * biases, identity standardization. */
+mgard_status mgard_mlp_init(float* params, uint64_t seed, void* stream);
+/* Set the standardization to the mean / standard deviation of x [B, NFEAT]. */
+mgard_status mgard_mlp_set_norm(float* params, const float* x, int B, void* stream);
+/* y [B] = network(x [B, NFEAT]); all device pointers. */
+mgard_status mgard_mlp_forward(const float* params, const float* x, int B, float* y,
+                               void* stream);
+/* Mean squared error over the batch and its gradient (MGARD_MLP_NTRAIN
+ * floats) by backpropagation; loss may be NULL. */
+mgard_status mgard_mlp_loss_grad(const float* params, const float* x, const float* t, int B,
+                                 float* grad, float* loss, void* stream);
+/* Adam (bias-corrected) on the first n parameters; t counts from 1. */
+mgard_status mgard_adam_step(float* params, const float* grad, float* m, float* v, int n,
+                             float lr, float beta1, float beta2, float eps, int t, void* stream);
+/* `steps` full-batch steps of loss_grad + Adam(lr, 0.9, 0.999, 1e-8),
+ * Adam's step counter continuing from t0; losses[k] (device, may be NULL)
+ * receives the loss before step k. */
+mgard_status mgard_mlp_train(float* params, float* m, float* v, const float* x, const float* t,
+                             int B, int steps, int t0, float lr, float* losses, void* stream);
+
+/* Compress `field` (device) with the relative tolerance whose compressed
+ * size is within rel_err of field_bytes / target_ratio.  With params
+ * (device, MGARD_MLP_NPARAM) the network proposes the tolerance and a
+ * bracketed bisection on log10(tol) corrects it if needed; with params =
+ * NULL the bisection starts from [1e-7, 1].  Every probe is an exact
+ * size from one shared decomposition; *passes counts them.  The error
+ * bound of the chosen tolerance holds as for mgard_compress: the target
+ * only selects tol.  *tol_used receives it; out (device, 16-byte aligned)
+ * gets the buffer (*out_bytes: capacity in, size out).  When no tolerance
+ * in [1e-9, 1] reaches the target within rel_err, the closest probe is used
+ * and MGARD_OK is still returned (check the size). */
+mgard_status mgard_compress_to_ratio(const void* field, int ndim, const int64_t* shape,
+                                     mgard_dtype dtype, double target_ratio, double s,
+                                     const float* params, double rel_err, double* tol_used,
+                                     void* out, size_t* out_bytes, int* passes, void* stream);
 
 /* Read the header of a compressed buffer (host or device pointer). */
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],

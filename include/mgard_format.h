@@ -14,7 +14,8 @@
  *                                     its sub-chunks 1..3 (256 symbols each), then the
  *                                     escapes of the chunk before each of them
  *   outliers  [noutliers] int32       escaped quantized values, symbol order
- *   words     [nwords] uint32         Huffman payload
+ *   words     [nwords] uint32         Huffman payload; a chunk of no words holds
+ *                                     only the symbol of q = 0 (MGARD_DICT/2)
  *
  * Every section starts at the byte offset recorded in the header, a
  * multiple of 16.  Decompression rejects a buffer whose magic, version,

@@ -17,7 +17,8 @@ then four global inputs: number of active axes D, L, log10 N and
 log10(target ratio).  ``NFEAT = NLEV * 18 + 4 = 220``.
 
 Network (``forward``): x is standardized with per-input mean mu and standard
-deviation sd (sd below 1e-6 is replaced by 1), then
+deviation sd, floored at SD_FLOOR = 0.05 so that inputs that barely vary in
+the training set do not turn small differences into large inputs, then
 h1 = relu(W1 xn + b1), h2 = relu(W2 h1 + b2), y = w3 . h2 + b3, with
 64 hidden units per layer and relu'(0) = 0.  Loss: mean squared error
 (1/B) sum_b (y_b - t_b)^2.  ``loss_grad`` is hand-written backpropagation;
@@ -91,9 +92,11 @@ def unpack(p, nin=NFEAT, h=H):
     return W1, b1, W2, b2, w3, b3, mu, sd
 
 
+SD_FLOOR = 0.05
+
+
 def standardize(x, mu, sd):
-    sd = np.where(sd < 1e-6, 1.0, sd)
-    return (x - mu) / sd
+    return (x - mu) / np.maximum(sd, SD_FLOOR)
 
 
 def forward(p, x, nin=NFEAT, h=H):

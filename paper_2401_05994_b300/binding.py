@@ -65,6 +65,25 @@ SIGNATURES = {
     "mgard_decompress_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
                                               ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
                                               ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp]),
+    "mgard_sizer_create": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(_vp), _vp]),
+    "mgard_sizer_size": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t), _vp]),
+    "mgard_sizer_features": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
+    "mgard_sizer_compress": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp,
+                                            ctypes.POINTER(ctypes.c_size_t), _vp]),
+    "mgard_sizer_free": (None, [_vp]),
+    "mgard_mlp_init": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
+    "mgard_mlp_set_norm": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "mgard_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "mgard_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "mgard_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp]),
+    "mgard_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_float, _vp, _vp]),
+    "mgard_compress_to_ratio": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, _vp, ctypes.c_double, _c_double_p, _vp,
+                                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
+                                               _vp]),
     "mgard_autotune": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_char_p,
                                       ctypes.c_size_t, _vp]),
     "mgard_compress_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
@@ -395,6 +414,119 @@ def decompress_batch(bufs, outs=None, graph: bool = False, check: bool = True):
     if check:
         _check(st)
     return outs, [int(x) for x in stats]
+
+
+# ---- ratio targeting and the tolerance predictor ----------------------------
+NFEAT = 220
+MLP_HIDDEN = 64
+MLP_NTRAIN = MLP_HIDDEN * NFEAT + MLP_HIDDEN * MLP_HIDDEN + 3 * MLP_HIDDEN + 1
+MLP_NPARAM = MLP_NTRAIN + 2 * NFEAT
+
+
+class Sizer:
+    """One decomposition of a CUDA field; exact compressed sizes, predictor
+    features and the final compression at any tolerance (mgard_sizer_*).
+    The field must not change while the sizer is open."""
+
+    def __init__(self, field, s: float = math.inf):
+        _require_cuda(field)
+        self.field = field
+        nd, sh = _shape(field.shape)
+        h = _vp()
+        _check(lib().mgard_sizer_create(field.data_ptr(), nd, sh, _dtype_code(field.dtype), float(s),
+                                        ctypes.byref(h), _stream()))
+        self.h = h
+
+    def size(self, tol: float, mode: int = REL) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().mgard_sizer_size(self.h, float(tol), int(mode), ctypes.byref(b), _stream()))
+        return int(b.value)
+
+    def features(self, target_ratio: float, out=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(NFEAT, dtype=torch.float32, device=self.field.device)
+        _check(lib().mgard_sizer_features(self.h, float(target_ratio), out.data_ptr(), _stream()))
+        return out
+
+    def compress(self, tol: float, mode: int = REL, out=None):
+        if out is None:
+            out = torch.empty(compress_bound(self.field.shape, self.field.dtype), dtype=torch.uint8,
+                              device=self.field.device)
+        n = ctypes.c_size_t(out.numel())
+        _check(lib().mgard_sizer_compress(self.h, float(tol), int(mode), out.data_ptr(),
+                                          ctypes.byref(n), _stream()))
+        return out[:n.value]
+
+    def close(self):
+        if self.h:
+            lib().mgard_sizer_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_init(seed: int = 0, device="cuda") -> torch.Tensor:
+    p = torch.empty(MLP_NPARAM, dtype=torch.float32, device=device)
+    _check(lib().mgard_mlp_init(p.data_ptr(), int(seed), _stream()))
+    return p
+
+
+def mlp_set_norm(params: torch.Tensor, x: torch.Tensor):
+    _check(lib().mgard_mlp_set_norm(params.data_ptr(), x.data_ptr(), x.shape[0], _stream()))
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    x = x.contiguous()
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().mgard_mlp_forward(params.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(), _stream()))
+    return y
+
+
+def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, t: torch.Tensor):
+    x, t = x.contiguous(), t.contiguous()
+    g = torch.empty(MLP_NTRAIN, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().mgard_mlp_loss_grad(params.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
+                                     g.data_ptr(), loss.data_ptr(), _stream()))
+    return loss, g
+
+
+def adam_step(params, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib().mgard_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                 grad.numel(), lr, beta1, beta2, eps, int(t), _stream()))
+
+
+def mlp_train(params, m, v, x, t, steps: int, t0: int = 0, lr: float = 1e-3) -> torch.Tensor:
+    x, t = x.contiguous(), t.contiguous()
+    losses = torch.empty(max(steps, 1), dtype=torch.float32, device=x.device)
+    _check(lib().mgard_mlp_train(params.data_ptr(), m.data_ptr(), v.data_ptr(), x.data_ptr(),
+                                 t.data_ptr(), x.shape[0], int(steps), int(t0), float(lr),
+                                 losses.data_ptr(), _stream()))
+    return losses[:steps]
+
+
+def compress_to_ratio(field, target_ratio: float, s: float = math.inf, params=None,
+                      rel_err: float = 0.05, out=None):
+    """Compress a CUDA field at the relative tolerance that reaches
+    ``target_ratio`` within ``rel_err`` (mgard_compress_to_ratio).  Returns
+    ``(buffer view, tol, passes)``."""
+    _require_cuda(field)
+    nd, sh = _shape(field.shape)
+    if out is None:
+        out = torch.empty(compress_bound(field.shape, field.dtype), dtype=torch.uint8, device=field.device)
+    n = ctypes.c_size_t(out.numel())
+    tol = ctypes.c_double()
+    passes = ctypes.c_int()
+    _check(lib().mgard_compress_to_ratio(field.data_ptr(), nd, sh, _dtype_code(field.dtype),
+                                         float(target_ratio), float(s),
+                                         params.data_ptr() if params is not None else None,
+                                         float(rel_err), ctypes.byref(tol), out.data_ptr(),
+                                         ctypes.byref(n), ctypes.byref(passes), _stream()))
+    return out[:n.value], tol.value, passes.value
 
 
 def info(buf):

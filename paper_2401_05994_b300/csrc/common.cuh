@@ -73,6 +73,16 @@ enum : unsigned {
     ST_CAPACITY = 16u,   // the output buffer is smaller than the compressed data
 };
 
+// Partial statistics of one block over a level's coefficients (features of
+// the tolerance predictor): sums of r = log10(max(|c|, 1e-12 a) / a) and r^2,
+// and hist[k] = coefficients below exactly k of the thresholds 10^(-j/2) a,
+// j = 0..FEAT_BINS-2.
+constexpr int FEAT_BINS = 16;
+struct FeatPart {
+    double sum, sum2;
+    unsigned long long hist[FEAT_BINS];
+};
+
 // Per-axis tables of one level transition (fine grid of level l, coarse
 // grid of level l-1).  Pointers are device addresses; for an inactive axis
 // (extent 1) they are null and the axis is treated as "always coarse".

@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
          c += (uint64_t)gridDim.x * ENC_WARPS) {
         const uint64_t base = c * CHUNK + lane * 32;
         unsigned bits = 0, esc = 0;
+        bool fill = true;
         if (base + 32 <= n) {
             const uint4* v = reinterpret_cast<const uint4*>(sym + base);
 #pragma unroll
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
                     nocode |= (l0 == 0) | (l1 == 0);
                     bits += l0 + l1;
                     esc += (s0 == MGARD_ESC) + (s1 == MGARD_ESC);
+                    fill = fill && ww[h] == FILL_PAIR;
                 }
             }
         } else {
@@ -355,6 +357,7 @@ __global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
                 nocode |= l == 0;
                 bits += l;
                 esc += s == MGARD_ESC;
+                fill = fill && s == FILL_SYMBOL;
             }
         }
 #pragma unroll
@@ -362,8 +365,9 @@ __global__ void __launch_bounds__(ENC_WARPS * 32) k_chunk_count(
             bits += __shfl_xor_sync(0xffffffffu, bits, o);
             esc += __shfl_xor_sync(0xffffffffu, esc, o);
         }
+        fill = __all_sync(0xffffffffu, fill);
         if (lane == 0) {
-            wcnt[c] = (bits + 31) / 32;
+            wcnt[c] = fill ? 0 : (bits + 31) / 32;   // a chunk of the zero symbol only: no words
             ecnt[c] = esc;
         }
     }
@@ -529,6 +533,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         unsigned bit0 = 0, esc0 = 0;   // chunk-relative offsets of the current round
         int64_t pend_at = -1;          // escape values are stored one escape late
         int32_t pend_v = 0;
+        bool fill = true;              // every symbol of the chunk is the zero symbol
         for (int rd = 0; rd < NSUB; ++rd) {
             if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
                 sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
@@ -551,6 +556,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                 if (k < cnt) {
                     bits += len_s[sv[k]];
                     esc += sv[k] == MGARD_ESC;
+                    fill = fill && sv[k] == FILL_SYMBOL;
                 }
             unsigned ib = bits, ie = esc;
 #pragma unroll
@@ -596,6 +602,11 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         }
         if (pend_at >= 0) outliers[pend_at] = pend_v;
         __syncwarp();
+        if (__all_sync(0xffffffffu, fill)) {   // stored without words; offsets 0
+            if (lane < SUBREC) sub_off[c * SUBREC + lane] = 0;
+            __syncwarp();
+            continue;
+        }
         const unsigned total_words = (bit0 + 31) / 32;
         for (unsigned k = lane; k < total_words; k += 32) words[wo + k] = wb[k];
         __syncwarp();
@@ -654,6 +665,14 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
         const uint64_t ce1 = c + 1 < nchunks ? esc_off[c + 1] : noutliers;
         if (cw0 > cw1 || cw1 > nwords || ce0 > ce1 || ce1 > noutliers) {
             ok = false;
+            continue;
+        }
+        if (cw1 == cw0) {   // a chunk without words holds only the zero symbol
+            if (ce1 != ce0) {
+                ok = false;
+                continue;
+            }
+            for (int k = 0; k < cnt; ++k) sym[first + k] = (uint16_t)FILL_SYMBOL;
             continue;
         }
         const uint16_t* so = sub_off + c * SUBREC;

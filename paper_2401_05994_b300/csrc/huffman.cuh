@@ -6,6 +6,9 @@
 namespace mgb {
 
 constexpr int LUT_BITS = 14;
+// A chunk made only of this symbol (q = 0) is stored with no payload words.
+constexpr unsigned FILL_SYMBOL = MGARD_DICT / 2;
+constexpr unsigned FILL_PAIR = FILL_SYMBOL | (FILL_SYMBOL << 16);
 constexpr int SUB = 256;                 // symbols per independently decodable sub-chunk
 constexpr int NSUB = MGARD_CHUNK / SUB;  // sub-chunks per chunk
 constexpr int SUBREC = 2 * (NSUB - 1);   // uint16 offsets recorded per chunk

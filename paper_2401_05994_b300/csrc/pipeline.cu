@@ -64,6 +64,11 @@ __global__ void k_widths(WidthArgs a, const double* __restrict__ maxparts,
     if (lane == 0) meta->tol_abs = tol_abs;
 }
 
+// Status bits of an encoding pass start clear (those of the input check stay).
+__global__ void k_meta_reset(CompressMeta* meta) {
+    if (threadIdx.x == 0) meta->status &= (unsigned)ST_NONFINITE;
+}
+
 // Sizes and offsets that follow from the totals of the count pass; the
 // header goes to the front of the buffer.
 __global__ void k_finalize(mgard_header h, const unsigned long long* __restrict__ totals,
@@ -81,6 +86,7 @@ __global__ void k_finalize(mgard_header h, const unsigned long long* __restrict_
     meta->noutliers = nout;
     meta->off_words = off_words;
     meta->total = total;
+    if (!dd) return;   // size only
     if (total > cap) {
         atomicOr(&meta->status, (unsigned)ST_CAPACITY);
     } else {
@@ -132,6 +138,7 @@ mgard_status CompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
     MGB_TRY(totals.alloc(2 * sizeof(unsigned long long), st));
     MGB_TRY(parts.alloc((RED_PARTS + energy_parts_total(p)) * sizeof(double), st));
     MGB_TRY(scan.alloc(count_scratch_bytes((uint64_t)N), st));
+    MGB_TRY(wdev.alloc(8 * (p.L + 1), st));
     return MGARD_OK;
 }
 
@@ -165,30 +172,34 @@ mgard_header header_template(const Plan& p, mgard_dtype dtype, int ndim, const i
 }
 
 template <typename T>
-mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
-                           double s, mgard_tolmode mode, char* dd, uint64_t cap,
-                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tolmode mode,
+                                CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
     const int64_t N = p.total();
-    const int L = p.L;
-    if (L > MAXLV) {
+    if (p.L > MAXLV) {
         set_error("too many levels");
         return MGARD_ESHAPE;
     }
-    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
-    const Sections fx = layout(L, nchunks, 0, 0);
-    if (cap < fx.outliers || ((uintptr_t)dd & 15) != 0) {
-        set_error("compress_core: output buffer too small or misaligned");
-        return MGARD_EINVAL;
-    }
     MGB_CUDA(cudaMemsetAsync(meta, 0, sizeof(CompressMeta), st));
-    MGB_CUDA(cudaMemsetAsync(dd, 0, fx.outliers, st));   // fixed sections, gaps included
-    MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
-    unsigned* status = &meta->status;
     double* parts = w.parts.template as<double>();
-    MGB_TRY(max_abs_partials<T>(din, N, parts, status, st));
+    MGB_TRY(max_abs_partials<T>(din, N, parts, &meta->status, st));
     const bool energy = mode == MGARD_REL && !std::isinf(s);
     MGB_TRY(decompose_pyramid<T>(p, din, w.top.template as<T>(), w.py, st, nullptr,
                                  energy ? parts + RED_PARTS : nullptr));
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                             double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                             CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+    const int64_t N = p.total();
+    const int L = p.L;
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    MGB_LAUNCH("k_meta_reset", st, k_meta_reset<<<1, 32, 0, st>>>(meta));
+    MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
+    unsigned* status = &meta->status;
+    double* parts = w.parts.template as<double>();
+    const bool energy = mode == MGARD_REL && !std::isinf(s);
     WidthArgs a;
     std::memset(&a, 0, sizeof(a));
     a.L = L;
@@ -201,7 +212,7 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
         a.eoff[l] = energy_parts_offset(p, l);
     }
     a.eoff[L + 1] = energy_parts_total(p);
-    double* widths = reinterpret_cast<double*>(dd + fx.widths);
+    double* widths = w.wdev.template as<double>();
     MGB_LAUNCH("k_widths", st, k_widths<<<1, 32, 0, st>>>(a, parts, parts + RED_PARTS, meta, widths));
     MGB_CUDA(cudaGetLastError());
     uint16_t* sym = w.sym.template as<uint16_t>();
@@ -211,8 +222,8 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
         MGB_TRY(quantize_level<T>(p, l, lvl, false, widths + l, sym, esc,
                                   w.hist.template as<unsigned long long>(), status, st));
     }
-    MGB_TRY(huffman_codebook(w.hist.template as<unsigned long long>(), w.lengths.template as<uint8_t>(), nullptr, st,
-                             (uint64_t)N >= (uint64_t(1) << 32)));
+    MGB_TRY(huffman_codebook(w.hist.template as<unsigned long long>(), w.lengths.template as<uint8_t>(),
+                             nullptr, st, (uint64_t)N >= (uint64_t(1) << 32)));
     MGB_TRY(huffman_tables(w.lengths.template as<uint8_t>(), w.codes.template as<uint32_t>(),
                            w.dt.template as<DecodeTables>(), st));
     uint64_t* word_off = w.offs.template as<uint64_t>();
@@ -223,18 +234,47 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
     MGB_LAUNCH("k_finalize", st, k_finalize<<<1, 32, 0, st>>>(
         h0, w.totals.template as<unsigned long long>(), meta, reinterpret_cast<unsigned char*>(dd), cap));
     MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, CompressMeta* meta,
+                           cudaStream_t st) {
+    const int64_t N = p.total();
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
+    const Sections fx = layout(p.L, nchunks, 0, 0);
+    uint64_t* word_off = w.offs.template as<uint64_t>();
+    uint64_t* esc_off = word_off + nchunks;
+    MGB_CUDA(cudaMemcpyAsync(dd + fx.widths, w.wdev.p, 8 * (p.L + 1), cudaMemcpyDeviceToDevice, st));
     MGB_CUDA(cudaMemcpyAsync(dd + fx.lengths, w.lengths.p, DICT, cudaMemcpyDeviceToDevice, st));
     if (nchunks) {
         MGB_CUDA(cudaMemcpyAsync(dd + fx.word_off, word_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
         MGB_CUDA(cudaMemcpyAsync(dd + fx.esc_off, esc_off, 8 * nchunks, cudaMemcpyDeviceToDevice, st));
     }
     PackGuard guard;
-    guard.status = status;
+    guard.status = &meta->status;
     guard.words_byte_off = &meta->off_words;
-    MGB_TRY(huffman_pack(sym, N, w.lengths.template as<uint8_t>(), w.codes.template as<uint32_t>(), word_off, esc_off,
-                         esc, reinterpret_cast<uint32_t*>(dd), reinterpret_cast<uint16_t*>(dd + fx.sub_off),
+    MGB_TRY(huffman_pack(w.sym.template as<uint16_t>(), N, w.lengths.template as<uint8_t>(),
+                         w.codes.template as<uint32_t>(), word_off, esc_off, w.esc.template as<int32_t>(),
+                         reinterpret_cast<uint32_t*>(dd), reinterpret_cast<uint16_t*>(dd + fx.sub_off),
                          reinterpret_cast<int32_t*>(dd + fx.outliers), st, guard));
     return MGARD_OK;
+}
+
+template <typename T>
+mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                           double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+    const uint64_t N = (uint64_t)p.total();
+    const Sections fx = layout(p.L, (N + CHUNK - 1) / CHUNK, 0, 0);
+    if (cap < fx.outliers || ((uintptr_t)dd & 15) != 0) {
+        set_error("compress_core: output buffer too small or misaligned");
+        return MGARD_EINVAL;
+    }
+    MGB_CUDA(cudaMemsetAsync(dd, 0, fx.outliers, st));   // fixed sections, gaps included
+    MGB_TRY(compress_decompose<T>(p, din, s, mode, w, meta, st));
+    MGB_TRY(compress_encode<T>(p, din, h0, tol, s, mode, dd, cap, w, meta, st));
+    return compress_pack<T>(p, dd, w, meta, st);
 }
 
 mgard_status check_header(const mgard_header& h, size_t in_bytes) {
@@ -311,6 +351,17 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
 
 template struct CompressWork<float>;
 template struct CompressWork<double>;
+#define INST_PHASES(T)                                                                            \
+    template mgard_status compress_decompose<T>(const Plan&, const T*, double, mgard_tolmode,     \
+                                                CompressWork<T>&, CompressMeta*, cudaStream_t);   \
+    template mgard_status compress_encode<T>(const Plan&, const T*, const mgard_header&, double,  \
+                                             double, mgard_tolmode, char*, uint64_t,              \
+                                             CompressWork<T>&, CompressMeta*, cudaStream_t);      \
+    template mgard_status compress_pack<T>(const Plan&, char*, CompressWork<T>&, CompressMeta*,   \
+                                           cudaStream_t);
+INST_PHASES(float)
+INST_PHASES(double)
+#undef INST_PHASES
 template mgard_status compress_core<float>(const Plan&, const float*, const mgard_header&, double,
                                            double, mgard_tolmode, char*, uint64_t,
                                            CompressWork<float>&, CompressMeta*, cudaStream_t);

@@ -34,7 +34,7 @@ struct CompressMeta {
 template <typename T>
 struct CompressWork {
     Pyramid<T> py;
-    DevBuf top, sym, esc, hist, lengths, codes, dt, offs, totals, parts, scan;
+    DevBuf top, sym, esc, hist, lengths, codes, dt, offs, totals, parts, scan, wdev;
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 
@@ -79,6 +79,25 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
 // shape and keep the fastest in the plan (tune.cu); `report` receives one
 // line per level and kernel.
 mgard_status autotune_plan(const Plan& p, mgard_dtype dtype, cudaStream_t st, std::string* report);
+
+// The three phases of compress_core, for callers that encode one
+// decomposition at several tolerances (ratio targeting):
+//  decompose  norm partials (max|u|, level energies) and the decomposition
+//             into the workspace; resets *meta;
+//  encode     widths, quantization, codebook and the count pass: *meta gets
+//             the exact compressed size; with dd != null the header is
+//             written and ST_CAPACITY reflects `cap`;
+//  pack       the remaining sections and the payload into dd.
+template <typename T>
+mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tolmode mode,
+                                CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
+template <typename T>
+mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                             double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                             CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
+template <typename T>
+mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, CompressMeta* meta,
+                           cudaStream_t st);
 
 // Drop the cached batches of mgard_compress_batch / mgard_decompress_batch
 // (graphs and workspaces).

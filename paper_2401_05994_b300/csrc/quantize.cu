@@ -175,6 +175,46 @@ __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __
     }
 }
 
+// Coefficient statistics of one level (predictor features; the row kernel
+// k3_features computes the same on shapes of up to three axes).
+template <typename T>
+__global__ void __launch_bounds__(QT) k_features(const T* __restrict__ c, QLevel q,
+                                                 const double* __restrict__ amax,
+                                                 FeatPart* __restrict__ part) {
+    __shared__ unsigned hist[FEAT_BINS];
+    if (threadIdx.x < FEAT_BINS) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const double a = *amax > 0.0 ? *amax : 1.0;
+    const float inv_a = (float)(1.0 / a);
+    double sum = 0.0, sum2 = 0.0;
+    FOR_NODES(q.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
+        const NodeInfo ni = node_info(q, i);
+        if (ni.skip) continue;
+        const float rr = log10f(fmaxf(fabsf((float)c[ni.addr]) * inv_a, 1e-12f));
+        sum += (double)rr;
+        sum2 += (double)rr * (double)rr;
+        atomicAdd(&hist[min(max((int)ceilf(-2.f * rr), 0), FEAT_BINS - 1)], 1u);
+    }
+    __shared__ double sh[2][QT];
+    sh[0][threadIdx.x] = sum;
+    sh[1][threadIdx.x] = sum2;
+    __syncthreads();
+    for (int o = QT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (threadIdx.x < FEAT_BINS) part[b].hist[threadIdx.x] = hist[threadIdx.x];
+    if (threadIdx.x == 0) {
+        part[b].sum = sh[0][0];
+        part[b].sum2 = sh[1][0];
+    }
+}
+
 QLevel make_qlevel(const Plan& p, int l, bool inplace) {
     QLevel q{};
     int64_t nc[4];
@@ -196,6 +236,27 @@ QLevel make_qlevel(const Plan& p, int l, bool inplace) {
 }
 
 }  // namespace
+
+int64_t feature_blocks(const Plan& p, int l) {
+    if (rows3_ok(p)) return rows3_feature_blocks(p, l);
+    const QLevel q = make_qlevel(p, l, false);
+    const dim3 g = grid3(q.n, QT, 32, 32);
+    return (int64_t)g.x * g.y * g.z;
+}
+
+template <typename T>
+mgard_status level_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
+                            cudaStream_t st) {
+    if (rows3_ok(p)) return rows3_features<T>(p, l, c, amax, part, st);
+    const QLevel q = make_qlevel(p, l, false);
+    MGB_LAUNCH("k_features", st, k_features<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, amax, part));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+template mgard_status level_features<float>(const Plan&, int, const float*, const double*,
+                                            FeatPart*, cudaStream_t);
+template mgard_status level_features<double>(const Plan&, int, const double*, const double*,
+                                             FeatPart*, cudaStream_t);
 
 template <typename T>
 mgard_status quantize_level(const Plan& p, int l, const T* c, bool inplace, const double* w,

@@ -20,4 +20,12 @@ template <typename T>
 mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               bool inplace, double w, T* c, cudaStream_t st);
 
+// Statistics of the level-l coefficients of a compact level array (the
+// features of the tolerance predictor): feature_blocks(p, l) FeatPart
+// records, reduced in a fixed order by the caller.  amax: device max|u|.
+int64_t feature_blocks(const Plan& p, int l);
+template <typename T>
+mgard_status level_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
+                            cudaStream_t st);
+
 }  // namespace mgb

@@ -536,6 +536,58 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
     if (st) atomicOr(status, st);
 }
 
+// -- coefficient statistics (predictor features) -------------------------------------
+// Per level: sum and sum of squares of r = log10(max(|c|, 1e-12 a) / a) and a
+// histogram of k = number of thresholds 10^(-j/2) a (j = 0..14) above |c|.
+// One partial record per block, reduced in a fixed order afterwards.
+template <typename T>
+__global__ void __launch_bounds__(RT) k3_features(const T* __restrict__ c, QRow q,
+                                                  const double* __restrict__ amax,
+                                                  FeatPart* __restrict__ part) {
+    __shared__ unsigned hist[WPB][FEAT_BINS];
+    for (int k = threadIdx.x; k < WPB * FEAT_BINS; k += RT) (&hist[0][0])[k] = 0;
+    __syncthreads();
+    const double a = *amax > 0.0 ? *amax : 1.0;
+    const float inv_a = (float)(1.0 / a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sum = 0.0, sum2 = 0.0;
+    WARP_ROWS((int64_t)q.nz * q.ny, r) {
+        const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
+        bool rowc;
+        (void)row_rank(q, z, y, rowc);
+        const T* crow = c + r * q.nx;
+        for (int x = lane; x < q.nx; x += 32) {
+            if (rowc && is_coarse(x, q.nx)) continue;   // node of the coarser grid
+            const float rr = log10f(fmaxf(fabsf((float)crow[x]) * inv_a, 1e-12f));
+            // double sums: the variance is a difference of two of them
+            sum += (double)rr;
+            sum2 += (double)rr * (double)rr;
+            const int k = min(max((int)ceilf(-2.f * rr), 0), FEAT_BINS - 1);
+            atomicAdd(&hist[warp][k], 1u);
+        }
+    }
+    __shared__ double sh[2][RT];
+    sh[0][threadIdx.x] = sum;
+    sh[1][threadIdx.x] = sum2;
+    __syncthreads();
+    for (int o = RT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < FEAT_BINS) {
+        unsigned long long h = 0;
+        for (int w = 0; w < WPB; ++w) h += hist[w][threadIdx.x];
+        part[blockIdx.x].hist[threadIdx.x] = h;
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x].sum = sh[0][0];
+        part[blockIdx.x].sum2 = sh[1][0];
+    }
+}
+
 template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__ sym,
                                                     const int32_t* __restrict__ esc, QRow q,
@@ -678,6 +730,19 @@ mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, 
     return MGARD_OK;
 }
 
+int rows3_feature_blocks(const Plan& p, int l) {
+    return row_grid(p.shape[l][1] * p.shape[l][2]);
+}
+
+template <typename T>
+mgard_status rows3_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
+                            cudaStream_t st) {
+    const QRow q = make_qrow(p, l);
+    MGB_LAUNCH("k3_features", st, k3_features<T><<<rows3_feature_blocks(p, l), RT, 0, st>>>(c, q, amax, part));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
 template <typename T>
 mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
@@ -709,6 +774,8 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
     template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t);     \
     template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t); \
     template mgard_status rows3_mass_norm<T>(const Plan&, int, const T*, double*, cudaStream_t); \
+    template mgard_status rows3_features<T>(const Plan&, int, const T*, const double*, FeatPart*, \
+                                            cudaStream_t);                                       \
     template mgard_status rows3_quantize<T>(const Plan&, int, const T*, const double*, uint16_t*,       \
                                             int32_t*, unsigned long long*, unsigned*,            \
                                             cudaStream_t);                                       \

@@ -38,6 +38,13 @@ int rows3_mass_norm_blocks(const Plan& p, int l);
 template <typename T>
 mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, cudaStream_t st);
 
+// Coefficient statistics of level l (predictor features): one FeatPart per
+// block (rows3_feature_blocks of them); amax (device) holds max|u|.
+template <typename T>
+mgard_status rows3_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
+                            cudaStream_t st);
+int rows3_feature_blocks(const Plan& p, int l);
+
 // Solvers shared with the generic path (multilevel.cu).
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,

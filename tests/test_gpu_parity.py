@@ -162,11 +162,16 @@ def test_codebook_matches_oracle(case):
     assert np.array_equal(got[used], rc[used])
 
 
-@pytest.mark.parametrize("n", [1, 1023, 1024, 1025, 70001])
+@pytest.mark.parametrize("n", [1, 1023, 1024, 1025, 70001, 9000])
 def test_encode_decode_bit_exact(n):
     rng = np.random.default_rng(n)
     s = np.minimum(rng.geometric(0.05, n) + 2040, 4095).astype(np.uint16)
     s[rng.random(n) < 0.01] = 0
+    if n == 9000:   # chunks of the zero symbol only (stored without words), incl. the last
+        s[1024:3072] = 2048
+        s[8192:] = 2048
+    elif n == 70001:
+        s[5 * 1024:6 * 1024] = 2048
     hist = np.bincount(s, minlength=4096)
     L = huffman.code_lengths(hist)
     esc = np.zeros(n, dtype=np.int32)
@@ -174,7 +179,7 @@ def test_encode_decode_bit_exact(n):
     st = torch.from_numpy(s.astype(np.int32)).to(torch.uint16).to(DEV)
     words, woff, eoff, sub, outl = binding.huffman_encode(st, torch.from_numpy(L).to(DEV),
                                                           torch.from_numpy(esc).to(DEV))
-    rw, rwo, reo, rsub = huffman.encode(s, L)
+    rw, rwo, reo, rsub = huffman.encode(s, L, fill_symbol=2048)
     assert np.array_equal(words.cpu().numpy().view(np.uint32), rw)
     assert np.array_equal(woff.cpu().numpy().astype(np.uint64), rwo)
     assert np.array_equal(eoff.cpu().numpy().astype(np.uint64), reo)
@@ -216,7 +221,7 @@ def test_compress_round_trip_meets_bound(case, s):
     sym, esc, hist = binding.quantize(v, sec["widths"])
     rl = huffman.code_lengths(hist.cpu().numpy())
     assert np.array_equal(sec["lengths"], rl)
-    rw, rwo, reo, rsub = huffman.encode(sym.cpu().numpy(), rl)
+    rw, rwo, reo, rsub = huffman.encode(sym.cpu().numpy(), rl, fill_symbol=2048)
     assert np.array_equal(sec["words"], rw)
     assert np.array_equal(sec["word_off"], rwo) and np.array_equal(sec["esc_off"], reo)
     assert np.array_equal(sec["sub_off"], rsub)

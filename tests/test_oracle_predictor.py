@@ -27,11 +27,16 @@ def test_forward_hand_evaluated():
     assert predictor.forward(p, np.array([[3.0, 0.5]]), nin, h)[0] == 3.5
     # x = (-1, 4): z1 = (-1, 3) -> h1 = (0, 3) -> z2 = (3, 3) -> y = 3 + 6 + 0.5
     assert predictor.forward(p, np.array([[-1.0, 4.0]]), nin, h)[0] == 9.5
-    # standardization: mu = (1, 1), sd = (2, 0) (sd 0 -> 1): x = (7, 1) -> xn = (3, 0)
+    # standardization: mu = (1, 1), sd = (2, 0) (floored): x = (7, 1) -> xn = (3, 0)
     q = p.copy()
     q[15:17] = 1.0
     q[17:19] = [2.0, 0.0]
     assert predictor.forward(q, np.array([[7.0, 1.0]]), nin, h)[0] == 3.5
+    # the floor: sd = (2, 0), x = (7, 1.01) -> xn = (3, 0.01 / 0.05) = (3, 0.2) ->
+    # z1 = (3, -0.8) -> h1 = (3, 0) -> y = 3.5
+    assert predictor.forward(q, np.array([[7.0, 1.01]]), nin, h)[0] == pytest.approx(3.5)
+    # x = (1, 1.2) -> xn = (0, 4) -> z1 = (0, 3) -> h1 = (0, 3) -> z2 = (3, 3) -> y = 9.5
+    assert predictor.forward(q, np.array([[1.0, 1.2]]), nin, h)[0] == pytest.approx(9.5)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
