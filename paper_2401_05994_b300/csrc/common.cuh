@@ -64,6 +64,16 @@ __device__ inline T dequant_escape(int32_t q, T wt, double w) {
     return (T)((double)q * w);
 }
 
+// Levels a plan may have (a header records at most 64).
+constexpr int MAX_LEVELS = 64;
+
+// Symbol offsets of the levels in symbol order: level l holds symbols
+// [off[l], off[l+1]); off[L+1] is the total.
+struct LevelOffsets {
+    int L;
+    long long off[MAX_LEVELS + 2];
+};
+
 // Device status bits set by kernels and read back by the host.
 enum : unsigned {
     ST_NONFINITE = 1u,

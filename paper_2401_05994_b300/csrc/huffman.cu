@@ -13,6 +13,7 @@
 // with one warp per chunk.  Decoding runs one thread per 256-symbol
 // sub-chunk with a 14-bit prefix table in shared memory and a canonical
 // first-code search for longer codes.
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -624,11 +625,27 @@ constexpr int DEC_BLOCKS_PER_SM = 6;   // 33 KB of tables per block
 // loads never leave the chunk, escape reads never leave the chunk's escape
 // range, and a sub-chunk whose code stream does not end where its recorded
 // offsets say (or that meets a prefix with no code) marks the stream corrupt.
+__device__ inline void store8(float* p, const float* v) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ inline void store8(double* p, const double* v) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+__device__ inline void store8(uint16_t*, const uint16_t*) {}
+
+// OutT = uint16_t: symbols to `sym`, escape values to `escapes` (indexed by
+// symbol position).  OutT = float or double: the dequantized coefficient of
+// every symbol to `vals` (symbol order), with the widths of DeqArgs.
+template <typename OutT>
 __global__ void __launch_bounds__(DEC_THREADS) k_decode(
     const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
     const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
     const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
-    uint16_t* __restrict__ sym, int32_t* __restrict__ escapes, unsigned* status, uint64_t nchunks) {
+    uint16_t* __restrict__ sym, int32_t* __restrict__ escapes, OutT* __restrict__ vals,
+    DeqArgs dq, unsigned* status, uint64_t nchunks) {
+    constexpr bool SYM = sizeof(OutT) == 2;
     __shared__ __align__(16) uint16_t lut[1 << LUT_BITS];
     __shared__ unsigned long long lim[LMAX + 2];
     __shared__ uint32_t fcode[LMAX + 2], findex[LMAX + 2];
@@ -672,7 +689,10 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
                 ok = false;
                 continue;
             }
-            for (int k = 0; k < cnt; ++k) sym[first + k] = (uint16_t)FILL_SYMBOL;
+            if (SYM)
+                for (int k = 0; k < cnt; ++k) sym[first + k] = (uint16_t)FILL_SYMBOL;
+            else
+                for (int k = 0; k < cnt; ++k) vals[first + k] = OutT(0);
             continue;
         }
         const uint16_t* so = sub_off + c * SUBREC;
@@ -694,6 +714,14 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
         uint64_t used = 0;
         int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
         uint32_t pk[4] = {0, 0, 0, 0};
+        OutT vk[8];
+        // level of the current symbol (dequantizing output)
+        int lvl = 0;
+        long long lvl_end = 0;
+        if (!SYM) {
+            while (lvl < dq.lo.L && (long long)first >= dq.lo.off[lvl + 1]) ++lvl;
+            lvl_end = dq.lo.off[lvl + 1];
+        }
         int k = 0;
         for (; k < cnt; ++k) {
             if (nb <= 32) {
@@ -721,26 +749,42 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
             win <<= len;
             nb -= (int)len;
             used += len;
+            int32_t qesc = 0;
             if (s == MGARD_ESC) {
                 if (e >= e_end) {
                     ok = false;
                     break;
                 }
-                escapes[first + k] = next_out;
+                qesc = next_out;
+                if (SYM) escapes[first + k] = next_out;
                 ++e;
                 next_out = e < e_end ? outliers[e] : 0;
             }
             const int slot = k & 7;
-            if (slot & 1) pk[slot >> 1] |= s << 16;
-            else pk[slot >> 1] = s;
-            if (slot == 7)
-                *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            if (SYM) {
+                if (slot & 1) pk[slot >> 1] |= s << 16;
+                else pk[slot >> 1] = s;
+                if (slot == 7)
+                    *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            } else {
+                while (lvl < dq.lo.L && (long long)(first + k) >= lvl_end) lvl_end = dq.lo.off[++lvl + 1];
+                OutT v;
+                if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.w[lvl]);
+                else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), dq.wf[lvl]);
+                else v = (OutT)((double)((int)s - RADIUS) * dq.w[lvl]);
+                vk[slot] = v;
+                if (slot == 7) store8(vals + first + k - 7, vk);
+            }
         }
         if (k < cnt) continue;   // ok already cleared
         const int rem = cnt & 7;   // symbols decoded after the last full group
         for (int r = 0; r < rem; ++r) {
-            const uint32_t w = pk[r >> 1];
-            sym[first + (cnt - rem) + r] = (uint16_t)((r & 1) ? (w >> 16) : (w & 0xFFFF));
+            if (SYM) {
+                const uint32_t w = pk[r >> 1];
+                sym[first + (cnt - rem) + r] = (uint16_t)((r & 1) ? (w >> 16) : (w & 0xFFFF));
+            } else {
+                vals[first + (cnt - rem) + r] = vk[r];
+            }
         }
         // the codes must end inside the sub-chunk's bit range (exactly at its
         // end unless padding follows) and use exactly its escapes
@@ -834,11 +878,36 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
-    MGB_LAUNCH("k_decode", st, k_decode<<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
-                                          esc_off, sym, escapes, status, nchunks));
+    DeqArgs dq;
+    std::memset(&dq, 0, sizeof(dq));
+    MGB_LAUNCH("k_decode", st, k_decode<uint16_t><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
+                                          esc_off, sym, escapes, nullptr, dq, status, nchunks));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
+
+template <typename T>
+mgard_status huffman_decode_values(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                   const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
+                                   const int32_t* outliers, uint64_t noutliers,
+                                   const uint64_t* esc_off, const DeqArgs& dq, T* vals,
+                                   unsigned* status, cudaStream_t st) {
+    const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    if (!nchunks) return MGARD_OK;
+    const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
+    MGB_LAUNCH("k_decode", st, k_decode<T><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
+                                          esc_off, nullptr, nullptr, vals, dq, status, nchunks));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+template mgard_status huffman_decode_values<float>(const uint32_t*, uint64_t, const uint64_t*,
+                                                   const uint16_t*, const DecodeTables*, uint64_t,
+                                                   const int32_t*, uint64_t, const uint64_t*,
+                                                   const DeqArgs&, float*, unsigned*, cudaStream_t);
+template mgard_status huffman_decode_values<double>(const uint32_t*, uint64_t, const uint64_t*,
+                                                    const uint16_t*, const DecodeTables*, uint64_t,
+                                                    const int32_t*, uint64_t, const uint64_t*,
+                                                    const DeqArgs&, double*, unsigned*, cudaStream_t);
 
 
 // ---------------------------------------------------------------------------

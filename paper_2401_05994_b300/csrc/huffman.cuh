@@ -57,10 +57,26 @@ mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* length
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
                           const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
                           int32_t* outliers, cudaStream_t st, PackGuard guard = PackGuard());
+// Widths for decoding straight to dequantized values: level l's symbols
+// [lo.off[l], lo.off[l+1]) dequantize with w[l] (wf[l] = float(w[l])).
+struct DeqArgs {
+    LevelOffsets lo;
+    double w[MAX_LEVELS + 1];
+    float wf[MAX_LEVELS + 1];
+};
 // Decoding with bounds checks (ST_CORRUPT on failure).
 mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
                             const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
                             const int32_t* outliers, uint64_t noutliers, const uint64_t* esc_off,
                             uint16_t* sym, int32_t* escapes, unsigned* status, cudaStream_t st);
+
+// Decoding straight to dequantized coefficients in symbol order (vals, n
+// values), as the dequantization of the decoded symbols would give them.
+template <typename T>
+mgard_status huffman_decode_values(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
+                                   const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
+                                   const int32_t* outliers, uint64_t noutliers,
+                                   const uint64_t* esc_off, const DeqArgs& dq, T* vals,
+                                   unsigned* status, cudaStream_t st);
 
 }  // namespace mgb

@@ -606,11 +606,11 @@ bool level_uses_fp64(const Plan& p, int l) {
 
 template <typename T>
 mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1, T sign,
-                     cudaStream_t st) {
+                     cudaStream_t st, int64_t zoff = -1) {
     const bool f64 = level_uses_fp64<T>(p, l);
     if (rows3_ok(p)) {
-        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st);
-        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st);
+        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st, zoff);
+        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st, zoff);
     }
     if (f64) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
     return correct_level<T, T>(p, l, z, coarse, t0, t1, sign, st);
@@ -814,42 +814,56 @@ mgard_status difference(const T* a, const T* b, double* y, int64_t n, cudaStream
 
 template <typename T>
 mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
-                               cudaStream_t st, double* E, double* Epart) {
+                               cudaStream_t st, double* E, double* Epart, T* zs) {
+    if (zs && !rows3_ok(p)) {
+        set_error("symbol-order coefficients need the row kernels");
+        return MGARD_EINVAL;
+    }
     for (int l = p.L; l >= 1; --l) {
         const T* src = l == p.L ? in : py.lv[l];
-        T* dst = l == p.L ? top : py.lv[l];
+        T* dst = zs ? zs : (l == p.L ? top : py.lv[l]);
+        const int64_t zoff = zs ? p.offset[l] : -1;
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
         if (Epart) MGB_TRY(mass_norm2_partials<T>(p, l, src, Epart + energy_parts_offset(p, l), st));
         if (rows3_ok(p)) {
-            MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st));
+            MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st, zoff));
         } else {
             MGB_LAUNCH("k_coeff_gather", st,
                        k_coeff_gather<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(
                            src, dst, py.lv[l - 1], p.level<T>(l)));
             MGB_CUDA(cudaGetLastError());
         }
-        MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st));
+        MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st, zoff));
     }
     const T* u0 = p.L ? py.lv[0] : in;
     if (E) MGB_TRY(mass_norm2<T>(p, 0, u0, &E[0], st));
     if (Epart) MGB_TRY(mass_norm2_partials<T>(p, 0, u0, Epart, st));
+    if (zs)   // level 0 leads the symbol order
+        MGB_CUDA(cudaMemcpyAsync(zs, u0, p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
     return MGARD_OK;
 }
 
 template <typename T>
 mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& py,
-                               cudaStream_t st) {
+                               cudaStream_t st, const T* zs) {
+    if (zs && !rows3_ok(p)) {
+        set_error("symbol-order coefficients need the row kernels");
+        return MGARD_EINVAL;
+    }
     if (p.L == 0) {
-        if (out != top)
-            MGB_CUDA(cudaMemcpyAsync(out, top, p.total() * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        const T* src = zs ? zs : top;
+        if (out != src)
+            MGB_CUDA(cudaMemcpyAsync(out, src, p.total() * sizeof(T), cudaMemcpyDeviceToDevice, st));
         return MGARD_OK;
     }
+    if (zs) MGB_CUDA(cudaMemcpyAsync(py.lv[0], zs, p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
     for (int l = 1; l <= p.L; ++l) {
-        const T* z = l == p.L ? top : py.lv[l];
+        const T* z = zs ? zs : (l == p.L ? top : py.lv[l]);
+        const int64_t zoff = zs ? p.offset[l] : -1;
         T* dst = l == p.L ? out : py.lv[l];
-        MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st));
+        MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st, zoff));
         if (rows3_ok(p)) {
-            MGB_TRY(rows3_fill<T>(p, l, z, py.lv[l - 1], dst, st));
+            MGB_TRY(rows3_fill<T>(p, l, z, py.lv[l - 1], dst, st, zoff));
         } else {
             MGB_LAUNCH("k_fill", st, k_fill<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(
                                          z, py.lv[l - 1], dst, p.level<T>(l)));
@@ -886,13 +900,13 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
 #define INST(T)                                                                               \
     template struct Pyramid<T>;                                                               \
     template mgard_status decompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
-                                               cudaStream_t, double*, double*);                \
+                                               cudaStream_t, double*, double*, T*);            \
     template mgard_status max_abs_partials<T>(const T*, int64_t, double*, unsigned*,           \
                                               cudaStream_t);                                   \
     template mgard_status mass_norm2_partials<T>(const Plan&, int, const T*, double*,          \
                                                  cudaStream_t);                        \
     template mgard_status recompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
-                                               cudaStream_t);                                 \
+                                               cudaStream_t, const T*);                       \
     template mgard_status scatter_levels<T>(const Plan&, const Pyramid<T>&, T*, cudaStream_t); \
     template mgard_status gather_levels<T>(const Plan&, const T*, Pyramid<T>&, cudaStream_t);  \
     template mgard_status max_abs<T>(const T*, const T*, int64_t, double*, unsigned*,          \

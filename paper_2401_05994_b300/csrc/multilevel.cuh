@@ -56,18 +56,25 @@ constexpr int64_t FP64_SOLVE_NODES = int64_t(1) << 21;
 // every level's nodal values (FP64 accumulation; host array of L+1).
 // With `Epart` (device, energy_parts_total(p) doubles) the same energies
 // are left as partial sums on the device instead (no host round trip):
-// level l's partials start at energy_parts_offset(p, l).
+// level l's partials start at energy_parts_offset(p, l).  With `zs` (device,
+// N values; row-kernel shapes only) every level's coefficients, and the
+// level-0 values first, go to zs in symbol order (level 0, then the nodes
+// new on levels 1..L, row-major per level) instead of `top` and the
+// pyramid; `top` is then unused.
 template <typename T>
 mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
-                               cudaStream_t st, double* E, double* Epart = nullptr);
+                               cudaStream_t st, double* E, double* Epart = nullptr,
+                               T* zs = nullptr);
 
 // Recompose: `top` holds level-L coefficients (coarse positions ignored),
 // py.lv[l] the coefficients of level l >= 1 (coarse positions ignored) and
 // py.lv[0] the level-0 values.  Writes nodal values to `out` (may equal
 // `top`).  Overwrites the pyramid.
+// With `zs` the coefficients (and level-0 values) are read from an array
+// in symbol order, as decompose_pyramid writes them; `top` is then unused.
 template <typename T>
 mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& py,
-                               cudaStream_t st);
+                               cudaStream_t st, const T* zs = nullptr);
 
 // coarse += sign * M_{l-1}^{-1} P^T M_l z for level l (the correction of a
 // decomposition step, sign = +1, or of a recomposition step, sign = -1);

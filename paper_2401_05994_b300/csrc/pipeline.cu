@@ -12,6 +12,7 @@
 #include "huffman.cuh"
 #include "pipeline.cuh"
 #include "quantize.cuh"
+#include "rows3.cuh"
 
 namespace mgb {
 
@@ -183,8 +184,11 @@ mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tol
     double* parts = w.parts.template as<double>();
     MGB_TRY(max_abs_partials<T>(din, N, parts, &meta->status, st));
     const bool energy = mode == MGARD_REL && !std::isinf(s);
-    MGB_TRY(decompose_pyramid<T>(p, din, w.top.template as<T>(), w.py, st, nullptr,
-                                 energy ? parts + RED_PARTS : nullptr));
+    // shapes on the row kernels keep every level's coefficients in symbol
+    // order in `top` (quantization then streams through it)
+    T* top = w.top.template as<T>();
+    MGB_TRY(decompose_pyramid<T>(p, din, top, w.py, st, nullptr, energy ? parts + RED_PARTS : nullptr,
+                                 rows3_ok(p) ? top : nullptr));
     return MGARD_OK;
 }
 
@@ -217,10 +221,15 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
     MGB_CUDA(cudaGetLastError());
     uint16_t* sym = w.sym.template as<uint16_t>();
     int32_t* esc = w.esc.template as<int32_t>();
-    for (int l = 0; l <= L; ++l) {
-        const T* lvl = l == L ? (L ? w.top.template as<T>() : din) : w.py.lv[l];
-        MGB_TRY(quantize_level<T>(p, l, lvl, false, widths + l, sym, esc,
-                                  w.hist.template as<unsigned long long>(), status, st));
+    if (rows3_ok(p)) {
+        MGB_TRY(quantize_stream<T>(p, w.top.template as<T>(), widths, sym, esc,
+                                   w.hist.template as<unsigned long long>(), status, st));
+    } else {
+        for (int l = 0; l <= L; ++l) {
+            const T* lvl = l == L ? (L ? w.top.template as<T>() : din) : w.py.lv[l];
+            MGB_TRY(quantize_level<T>(p, l, lvl, false, widths + l, sym, esc,
+                                      w.hist.template as<unsigned long long>(), status, st));
+        }
     }
     MGB_TRY(huffman_codebook(w.hist.template as<unsigned long long>(), w.lengths.template as<uint8_t>(),
                              nullptr, st, (uint64_t)N >= (uint64_t(1) << 32)));
@@ -320,8 +329,12 @@ mgard_status DecompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
     MGB_TRY(py.alloc(p, st));
     MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
     MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
-    MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
-    MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    if (rows3_ok(p)) {   // decoded straight to coefficients in symbol order
+        MGB_TRY(zs.alloc(N * sizeof(T), st));
+    } else {
+        MGB_TRY(sym.alloc(N * sizeof(uint16_t), st));
+        MGB_TRY(esc.alloc(N * sizeof(int32_t), st));
+    }
     return MGARD_OK;
 }
 
@@ -331,16 +344,36 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
                              cudaStream_t st) {
     const int64_t N = p.total();
     const int L = p.L;
-    uint16_t* sym = work.sym.template as<uint16_t>();
-    int32_t* esc = work.esc.template as<int32_t>();
     DecodeTables* dt = work.dt.template as<DecodeTables>();
     MGB_TRY(huffman_tables((const uint8_t*)(din + h.off_lengths), work.codes.template as<uint32_t>(),
                            dt, st));
-    MGB_TRY(huffman_decode((const uint32_t*)(din + h.off_words), h.nwords,
-                           (const uint64_t*)(din + h.off_word_off),
-                           (const uint16_t*)(din + h.off_sub_off), dt, N,
-                           (const int32_t*)(din + h.off_outliers), h.noutliers,
-                           (const uint64_t*)(din + h.off_esc_off), sym, esc, status, st));
+    const uint32_t* words = (const uint32_t*)(din + h.off_words);
+    const uint64_t* woff = (const uint64_t*)(din + h.off_word_off);
+    const uint16_t* soff = (const uint16_t*)(din + h.off_sub_off);
+    const int32_t* outl = (const int32_t*)(din + h.off_outliers);
+    const uint64_t* eoff = (const uint64_t*)(din + h.off_esc_off);
+    if (rows3_ok(p)) {
+        // decode straight to coefficients in symbol order, recompose from there
+        if (L > MAX_LEVELS) {
+            set_error("too many levels");
+            return MGARD_ECORRUPT;
+        }
+        DeqArgs dq;
+        std::memset(&dq, 0, sizeof(dq));
+        dq.lo = level_offsets(p);
+        for (int l = 0; l <= L; ++l) {
+            dq.w[l] = w[l];
+            dq.wf[l] = (float)w[l];
+        }
+        T* zs = work.zs.template as<T>();
+        MGB_TRY(huffman_decode_values<T>(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff,
+                                         dq, zs, status, st));
+        return recompose_pyramid<T>(p, nullptr, dout, work.py, st, zs);
+    }
+    uint16_t* sym = work.sym.template as<uint16_t>();
+    int32_t* esc = work.esc.template as<int32_t>();
+    MGB_TRY(huffman_decode(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff, sym, esc,
+                           status, st));
     for (int l = 0; l <= L; ++l) {
         T* lvl = l == L ? dout : work.py.lv[l];
         MGB_TRY(dequantize_level<T>(p, l, sym, esc, false, w[l], lvl, st));

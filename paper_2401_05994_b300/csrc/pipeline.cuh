@@ -62,7 +62,7 @@ bool widths_valid(const double* w, int L);
 template <typename T>
 struct DecompressWork {
     Pyramid<T> py;
-    DevBuf codes, dt, sym, esc;
+    DevBuf codes, dt, sym, esc, zs;   // zs (row-kernel shapes) or sym + esc
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 

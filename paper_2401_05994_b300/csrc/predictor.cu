@@ -15,6 +15,7 @@
 
 #include "predictor.cuh"
 #include "quantize.cuh"
+#include "rows3.cuh"
 
 namespace mgb {
 
@@ -221,11 +222,14 @@ mgard_status mgard_sizer_features(mgard_sizer* z, double target_ratio, float* fe
         const int l = L - slot;
         a.count[slot] = (double)p.count[l];
         const int64_t nb = feature_blocks(p, l);
+        // row-kernel shapes keep the coefficients in symbol order in `top`
         if (z->dtype == MGARD_F32) {
-            const float* lvl = l == L ? (L ? z->wf->top.as<float>() : (const float*)z->field) : z->wf->py.lv[l];
+            const float* lvl = rows3_ok(p) ? z->wf->top.as<float>() + p.offset[l]
+                                           : (l == L ? (L ? z->wf->top.as<float>() : (const float*)z->field) : z->wf->py.lv[l]);
             MGB_TRY(level_features<float>(p, l, lvl, z->amax.as<double>(), parts + off, st));
         } else {
-            const double* lvl = l == L ? (L ? z->wd->top.as<double>() : (const double*)z->field) : z->wd->py.lv[l];
+            const double* lvl = rows3_ok(p) ? z->wd->top.as<double>() + p.offset[l]
+                                            : (l == L ? (L ? z->wd->top.as<double>() : (const double*)z->field) : z->wd->py.lv[l]);
             MGB_TRY(level_features<double>(p, l, lvl, z->amax.as<double>(), parts + off, st));
         }
         off += nb;

@@ -5,6 +5,8 @@
 // by level (level 0 first), each level in row-major order of its grid,
 // holding only the nodes new on that level.  |q| < DICT/2 maps to symbol
 // q + DICT/2; larger values escape to symbol 0 with q stored aside.
+#include <cstring>
+
 #include "quantize.cuh"
 #include "rows3.cuh"
 
@@ -215,6 +217,132 @@ __global__ void __launch_bounds__(QT) k_features(const T* __restrict__ c, QLevel
     }
 }
 
+// Quantization of coefficients held in symbol order (all levels in one
+// pass): eight consecutive values per thread with vector loads and one
+// 16-byte store of their symbols; the level of each value comes from the
+// offsets (a group may straddle two levels).  Same decisions as k_quantize.
+constexpr int QS_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
+    const T* __restrict__ zs, int64_t n, LevelOffsets lo, const double* __restrict__ wdev,
+    uint16_t* __restrict__ sym, int32_t* __restrict__ esc, unsigned long long* __restrict__ hist,
+    unsigned* status) {
+    __shared__ unsigned sh[2][DICT];
+    __shared__ double ws[MAX_LEVELS + 1];
+    __shared__ T iws[MAX_LEVELS + 1];
+    for (int k = threadIdx.x; k < 2 * DICT; k += QS_THREADS) (&sh[0][0])[k] = 0;
+    for (int l = threadIdx.x; l <= lo.L; l += QS_THREADS) {
+        ws[l] = wdev[l];
+        iws[l] = (T)(1.0 / wdev[l]);
+    }
+    __syncthreads();
+    unsigned* my = sh[threadIdx.x & 1];
+    unsigned center = 0, st = 0;
+    for (int64_t g = blockIdx.x * (int64_t)QS_THREADS + threadIdx.x; g * 8 < n;
+         g += (int64_t)gridDim.x * QS_THREADS) {
+        const int64_t i0 = g * 8;
+        int l = 0;
+        while (l < lo.L && i0 >= lo.off[l + 1]) ++l;
+        T v[8];
+        const bool full = i0 + 8 <= n;
+        if (full) {
+            if (sizeof(T) == 4) {
+                const float4 a = reinterpret_cast<const float4*>(zs + i0)[0];
+                const float4 b = reinterpret_cast<const float4*>(zs + i0)[1];
+                v[0] = (T)a.x; v[1] = (T)a.y; v[2] = (T)a.z; v[3] = (T)a.w;
+                v[4] = (T)b.x; v[5] = (T)b.y; v[6] = (T)b.z; v[7] = (T)b.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double2 a = reinterpret_cast<const double2*>(zs + i0)[k];
+                    v[2 * k] = (T)a.x;
+                    v[2 * k + 1] = (T)a.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? zs[i0 + k] : T(0);
+        }
+        uint32_t packed[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t i = i0 + k;
+            if (i >= n) break;
+            while (l < lo.L && i >= lo.off[l + 1]) ++l;
+            int s;
+            int32_t qo = 0;
+            quantize_value(v[k], iws[l], ws[l], s, qo, st);
+            packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
+            if (s == MGARD_ESC) esc[i] = qo;
+            if (s == RADIUS) ++center;
+            else atomicAdd(&my[s], 1u);
+        }
+        if (full) {
+            *reinterpret_cast<uint4*>(sym + i0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        } else {
+            for (int k = 0; k < 8 && i0 + k < n; ++k)
+                sym[i0 + k] = (uint16_t)(packed[k >> 1] >> (16 * (k & 1)));
+        }
+    }
+    if (center) atomicAdd(&sh[0][RADIUS], center);
+    __syncthreads();
+    for (int k = threadIdx.x; k < DICT; k += QS_THREADS) {
+        const unsigned v = sh[0][k] + sh[1][k];
+        if (v) atomicAdd(&hist[k], (unsigned long long)v);
+    }
+    if (st) atomicOr(status, st);
+}
+
+// The same statistics over a contiguous run of coefficients (one level in
+// symbol order).
+constexpr int FR_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(FR_THREADS) k_features_range(const T* __restrict__ c, int64_t n,
+                                                               const double* __restrict__ amax,
+                                                               FeatPart* __restrict__ part) {
+    __shared__ unsigned hist[FR_THREADS / 32][FEAT_BINS];
+    for (int k = threadIdx.x; k < (FR_THREADS / 32) * FEAT_BINS; k += FR_THREADS) (&hist[0][0])[k] = 0;
+    __syncthreads();
+    const double a = *amax > 0.0 ? *amax : 1.0;
+    const float inv_a = (float)(1.0 / a);
+    const int warp = threadIdx.x >> 5;
+    double sum = 0.0, sum2 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)FR_THREADS + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * FR_THREADS) {
+        const float rr = log10f(fmaxf(fabsf((float)c[i]) * inv_a, 1e-12f));
+        sum += (double)rr;
+        sum2 += (double)rr * (double)rr;
+        atomicAdd(&hist[warp][min(max((int)ceilf(-2.f * rr), 0), FEAT_BINS - 1)], 1u);
+    }
+    __shared__ double sh[2][FR_THREADS];
+    sh[0][threadIdx.x] = sum;
+    sh[1][threadIdx.x] = sum2;
+    __syncthreads();
+    for (int o = FR_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < FEAT_BINS) {
+        unsigned long long h = 0;
+        for (int w = 0; w < FR_THREADS / 32; ++w) h += hist[w][threadIdx.x];
+        part[blockIdx.x].hist[threadIdx.x] = h;
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x].sum = sh[0][0];
+        part[blockIdx.x].sum2 = sh[1][0];
+    }
+}
+
+int64_t range_feature_blocks(int64_t n) {
+    const int64_t b = (n + 8 * FR_THREADS - 1) / (8 * FR_THREADS);
+    return b < 1 ? 1 : (b > 148 * 4 ? 148 * 4 : b);
+}
+
 QLevel make_qlevel(const Plan& p, int l, bool inplace) {
     QLevel q{};
     int64_t nc[4];
@@ -237,8 +365,36 @@ QLevel make_qlevel(const Plan& p, int l, bool inplace) {
 
 }  // namespace
 
+LevelOffsets level_offsets(const Plan& p) {
+    LevelOffsets lo;
+    std::memset(&lo, 0, sizeof(lo));
+    lo.L = p.L;
+    for (int l = 0; l <= p.L; ++l) lo.off[l] = p.offset[l];
+    lo.off[p.L + 1] = p.total();
+    return lo;
+}
+
+template <typename T>
+mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16_t* sym,
+                             int32_t* esc, unsigned long long* hist, unsigned* status,
+                             cudaStream_t st) {
+    const int64_t n = p.total();
+    if (p.L > MAX_LEVELS) {
+        set_error("too many levels");
+        return MGARD_ESHAPE;
+    }
+    MGB_LAUNCH("k_quantize_stream", st, k_quantize_stream<T><<<grid_for((n + 7) / 8, QS_THREADS, 148LL * 8), QS_THREADS, 0, st>>>(
+                                            zs, n, level_offsets(p), w, sym, esc, hist, status));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+template mgard_status quantize_stream<float>(const Plan&, const float*, const double*, uint16_t*,
+                                             int32_t*, unsigned long long*, unsigned*, cudaStream_t);
+template mgard_status quantize_stream<double>(const Plan&, const double*, const double*, uint16_t*,
+                                              int32_t*, unsigned long long*, unsigned*, cudaStream_t);
+
 int64_t feature_blocks(const Plan& p, int l) {
-    if (rows3_ok(p)) return rows3_feature_blocks(p, l);
+    if (rows3_ok(p)) return range_feature_blocks(p.count[l]);
     const QLevel q = make_qlevel(p, l, false);
     const dim3 g = grid3(q.n, QT, 32, 32);
     return (int64_t)g.x * g.y * g.z;
@@ -247,7 +403,12 @@ int64_t feature_blocks(const Plan& p, int l) {
 template <typename T>
 mgard_status level_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
                             cudaStream_t st) {
-    if (rows3_ok(p)) return rows3_features<T>(p, l, c, amax, part, st);
+    if (rows3_ok(p)) {   // c: the level's run of coefficients in symbol order
+        MGB_LAUNCH("k_features_range", st, k_features_range<T><<<(int)range_feature_blocks(p.count[l]), FR_THREADS, 0, st>>>(
+                                               c, p.count[l], amax, part));
+        MGB_CUDA(cudaGetLastError());
+        return MGARD_OK;
+    }
     const QLevel q = make_qlevel(p, l, false);
     MGB_LAUNCH("k_features", st, k_features<T><<<grid3(q.n, QT, 32, 32), QT, 0, st>>>(c, q, amax, part));
     MGB_CUDA(cudaGetLastError());

@@ -20,9 +20,20 @@ template <typename T>
 mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const int32_t* esc,
                               bool inplace, double w, T* c, cudaStream_t st);
 
-// Statistics of the level-l coefficients of a compact level array (the
-// features of the tolerance predictor): feature_blocks(p, l) FeatPart
-// records, reduced in a fixed order by the caller.  amax: device max|u|.
+// Quantization of all levels' coefficients held in symbol order (zs, N
+// values; w: device widths of levels 0..L).  Same symbols, escapes and
+// histogram as quantize_level over the levels.
+LevelOffsets level_offsets(const Plan& p);
+template <typename T>
+mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16_t* sym,
+                             int32_t* esc, unsigned long long* hist, unsigned* status,
+                             cudaStream_t st);
+
+// Statistics of the level-l coefficients (the features of the tolerance
+// predictor): feature_blocks(p, l) FeatPart records, reduced in a fixed
+// order by the caller.  amax: device max|u|.  `c`: for shapes on the row
+// kernels the level's run of coefficients in symbol order, otherwise its
+// compact level array.
 int64_t feature_blocks(const Plan& p, int l);
 template <typename T>
 mgard_status level_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,

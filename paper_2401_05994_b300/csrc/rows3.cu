@@ -32,6 +32,20 @@ __device__ inline int coarse_index(int i, int m, int mc) { return i == m - 1 ? m
 __device__ inline int restrict_center(int J, int m, int mc) { return J == mc - 1 ? m - 1 : 2 * J; }
 __device__ inline int coarse_before(int i) { return (i + 1) >> 1; }
 
+// Coefficients of level l in symbol order (ZS kernels): the nodes new on the
+// level, row-major, starting at symbol offset `zoff`.  Row (z, y) of the level
+// grid starts at zoff + r nx minus the coarse-grid nodes before it; on a row
+// whose z and y are both coarse only the odd positions are new, so its x
+// lands at x - coarse_before(x).
+__device__ inline int64_t zs_row_base(int64_t zoff, int64_t r, int nx, int z, int y, int nz,
+                                      int ny, int ncy, int ncx) {
+    const bool zc = (z & 1) == 0 || z == nz - 1;
+    int64_t before = (int64_t)coarse_before(z) * ncy * ncx;
+    if (zc) before += (int64_t)coarse_before(y) * ncx;
+    (void)ny;
+    return zoff + r * nx - before;
+}
+
 // Interpolation sources of one index along one axis (y or z).
 template <typename T>
 struct Src {
@@ -124,9 +138,9 @@ __device__ inline void prefetch_l2(const void* p, size_t bytes) {
          r += (int64_t)gridDim.x * WPB)
 
 // -- coefficients (decomposition step 1) --------------------------------------
-template <typename T, int U>
+template <typename T, int U, bool ZS>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
-                                               Level<T> lv) {
+                                               Level<T> lv, int64_t zoff) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const bool rowc = sz.n == 1 && sy.n == 1;
         PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* urow = in + r * nx;
-        T* orow = out + r * nx;
+        T* orow = ZS ? out + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             T u[U], acc[U];
@@ -175,16 +189,16 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 const int x = x0 + 32 * j;
                 if (x >= nx) continue;
                 if (rowc && is_coarse(x, nx)) crow[coarse_index(x, nx, ncx)] = u[j];
-                else orow[x] = u[j] - acc[j];
+                else orow[(ZS && rowc) ? x - coarse_before(x) : x] = u[j] - acc[j];
             }
         }
     }
 }
 
 // -- recomposition fill ---------------------------------------------------------
-template <typename T, int U>
+template <typename T, int U, bool ZS>
 __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
-                                              Level<T> lv) {
+                                              Level<T> lv, int64_t zoff) {
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
@@ -204,8 +218,8 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                          zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
         const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
-        PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
-        const T* zrow = zin + r * nx;
+        if (!ZS) PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
+        const T* zrow = ZS ? zin + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : zin + r * nx;
         T* orow = out + r * nx;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             T v[U];
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                 for (int k = 0; k < 4; ++k)
                     if (use[k]) v[j] += rw[k] * (wl * rows[k][jl] + wr * rows[k][jr]);
                 // z vanishes on coarse nodes of the coarse grid's rows
-                if (!(rowc && cx)) v[j] += zrow[x];
+                if (!(rowc && cx)) v[j] += zrow[(ZS && rowc) ? x - coarse_before(x) : x];
             }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -239,11 +253,11 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
 }
 
 // -- restriction along x (first pass: z is zero on coarse nodes) -------------------
-template <typename Tin, typename Tout, int U>
+template <typename Tin, typename Tout, int U, bool ZS>
 __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                                                     Tout* __restrict__ out, int nz, int ny,
                                                     int nx, int ncz, int ncy, int ncx,
-                                                    AxisT<Tout> ax) {
+                                                    AxisT<Tout> ax, int64_t zoff) {
     const int lane = threadIdx.x & 31;
     const Tout* __restrict__ rw = ax.rw;
     const int rlo = ax.rlo, rhi = ax.rhi;
@@ -253,9 +267,11 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
-        PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
-        const Tin* irow = in + r * nx;
+        if (!ZS) PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
+        const Tin* irow = ZS ? in + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : in + r * nx;
         Tout* orow = out + r * ncx;
+        // symbol order on a coarse row holds only the odd positions: ip -> (ip - 1) / 2
+        const int sh = (ZS && rowc) ? 1 : 0;
         for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
             Tout acc[U];
 #pragma unroll
@@ -266,14 +282,23 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                 if (J >= rlo && J < rhi) {
                     // uniform window 2J-2 .. 2J+2; on coarse rows the even taps
                     // are coarse nodes, where z = 0
-                    const Tin* q = irow + 2 * J - 2;
-                    const Tout e0 = rowc ? Tout(0) : (Tout)q[0];
-                    const Tout e2 = rowc ? Tout(0) : (Tout)q[2];
-                    const Tout e4 = rowc ? Tout(0) : (Tout)q[4];
+                    Tout e0, e1, e2, e3, e4;
+                    if (ZS && rowc) {   // odd taps 2J-1, 2J+1 at J-1, J
+                        e0 = e2 = e4 = Tout(0);
+                        e1 = (Tout)irow[J - 1];
+                        e3 = (Tout)irow[J];
+                    } else {
+                        const Tin* q = irow + 2 * J - 2;
+                        e0 = rowc ? Tout(0) : (Tout)q[0];
+                        e1 = (Tout)q[1];
+                        e2 = rowc ? Tout(0) : (Tout)q[2];
+                        e3 = (Tout)q[3];
+                        e4 = rowc ? Tout(0) : (Tout)q[4];
+                    }
                     Tout a = wi[0] * e0;
-                    a += wi[1] * (Tout)q[1];
+                    a += wi[1] * e1;
                     a += wi[2] * e2;
-                    a += wi[3] * (Tout)q[3];
+                    a += wi[3] * e3;
                     a += wi[4] * e4;
                     acc[j] = a;
                     continue;
@@ -284,7 +309,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                     const int ip = f - 2 + t;
                     if (ip < 0 || ip >= nx) continue;
                     if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
-                    acc[j] += rw[J * 5 + t] * (Tout)irow[ip];
+                    acc[j] += rw[J * 5 + t] * (Tout)irow[sh ? (ip - 1) >> 1 : ip];
                 }
             }
 #pragma unroll
@@ -536,58 +561,6 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
     if (st) atomicOr(status, st);
 }
 
-// -- coefficient statistics (predictor features) -------------------------------------
-// Per level: sum and sum of squares of r = log10(max(|c|, 1e-12 a) / a) and a
-// histogram of k = number of thresholds 10^(-j/2) a (j = 0..14) above |c|.
-// One partial record per block, reduced in a fixed order afterwards.
-template <typename T>
-__global__ void __launch_bounds__(RT) k3_features(const T* __restrict__ c, QRow q,
-                                                  const double* __restrict__ amax,
-                                                  FeatPart* __restrict__ part) {
-    __shared__ unsigned hist[WPB][FEAT_BINS];
-    for (int k = threadIdx.x; k < WPB * FEAT_BINS; k += RT) (&hist[0][0])[k] = 0;
-    __syncthreads();
-    const double a = *amax > 0.0 ? *amax : 1.0;
-    const float inv_a = (float)(1.0 / a);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double sum = 0.0, sum2 = 0.0;
-    WARP_ROWS((int64_t)q.nz * q.ny, r) {
-        const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
-        bool rowc;
-        (void)row_rank(q, z, y, rowc);
-        const T* crow = c + r * q.nx;
-        for (int x = lane; x < q.nx; x += 32) {
-            if (rowc && is_coarse(x, q.nx)) continue;   // node of the coarser grid
-            const float rr = log10f(fmaxf(fabsf((float)crow[x]) * inv_a, 1e-12f));
-            // double sums: the variance is a difference of two of them
-            sum += (double)rr;
-            sum2 += (double)rr * (double)rr;
-            const int k = min(max((int)ceilf(-2.f * rr), 0), FEAT_BINS - 1);
-            atomicAdd(&hist[warp][k], 1u);
-        }
-    }
-    __shared__ double sh[2][RT];
-    sh[0][threadIdx.x] = sum;
-    sh[1][threadIdx.x] = sum2;
-    __syncthreads();
-    for (int o = RT / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < FEAT_BINS) {
-        unsigned long long h = 0;
-        for (int w = 0; w < WPB; ++w) h += hist[w][threadIdx.x];
-        part[blockIdx.x].hist[threadIdx.x] = h;
-    }
-    if (threadIdx.x == 0) {
-        part[blockIdx.x].sum = sh[0][0];
-        part[blockIdx.x].sum2 = sh[1][0];
-    }
-}
-
 template <typename T, int U>
 __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__ sym,
                                                     const int32_t* __restrict__ esc, QRow q,
@@ -650,11 +623,16 @@ QRow make_qrow(const Plan& p, int l) {
 }  // namespace
 
 template <typename T>
-mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st) {
+mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st,
+                         int64_t zoff) {
     const Level<T>& lv = p.level<T>(l);
     const RowCfg c = p.row_cfg(l, RK_COEFF);
+    const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
     with_cfg(c, lv.n[3], false, [&](auto u) {
-        MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2], c.bpsm), RT, 0, st>>>(in, out, coarse, lv));
+        if (zoff >= 0)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value, true><<<g, RT, 0, st>>>(in, out, coarse, lv, zoff));
+        else
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -662,11 +640,15 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
 
 template <typename T>
 mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, int64_t zoff) {
     const Level<T>& lv = p.level<T>(l);
     const RowCfg c = p.row_cfg(l, RK_FILL);
+    const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
     with_cfg(c, lv.n[3], false, [&](auto u) {
-        MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value><<<row_grid(lv.n[1] * lv.n[2], c.bpsm), RT, 0, st>>>(z, coarse, out, lv));
+        if (zoff >= 0)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value, true><<<g, RT, 0, st>>>(z, coarse, out, lv, zoff));
+        else
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value, false><<<g, RT, 0, st>>>(z, coarse, out, lv, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -674,7 +656,7 @@ mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* ou
 
 template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
-                           T sign, cudaStream_t st) {
+                           T sign, cudaStream_t st, int64_t zoff) {
     const Level<Tw>& lw = p.level<Tw>(l);
     const Level<T>& lt = p.level<T>(l);
     const int nz = (int)lt.n[1], ny = (int)lt.n[2], nx = (int)lt.n[3];
@@ -683,9 +665,14 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     Tw* b1 = (Tw*)t1;
     // x (always active)
     const RowCfg cx = p.row_cfg(l, RK_RX), cr = p.row_cfg(l, RK_RROWS);
+    const int gx = row_grid((int64_t)nz * ny, cx.bpsm);
     with_cfg(cx, ncx, true, [&](auto u) {
-        MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ny, cx.bpsm), RT, 0, st>>>(
-            z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3]));
+        if (zoff >= 0)
+            MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value, true><<<gx, RT, 0, st>>>(
+                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], zoff));
+        else
+            MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value, false><<<gx, RT, 0, st>>>(
+                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], 0));
     });
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
@@ -730,19 +717,6 @@ mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, 
     return MGARD_OK;
 }
 
-int rows3_feature_blocks(const Plan& p, int l) {
-    return row_grid(p.shape[l][1] * p.shape[l][2]);
-}
-
-template <typename T>
-mgard_status rows3_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
-                            cudaStream_t st) {
-    const QRow q = make_qrow(p, l);
-    MGB_LAUNCH("k3_features", st, k3_features<T><<<rows3_feature_blocks(p, l), RT, 0, st>>>(c, q, amax, part));
-    MGB_CUDA(cudaGetLastError());
-    return MGARD_OK;
-}
-
 template <typename T>
 mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
@@ -771,11 +745,11 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
 }
 
 #define INST(T)                                                                                  \
-    template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t);     \
-    template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t); \
+    template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t,      \
+                                         int64_t);                                              \
+    template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t,  \
+                                        int64_t);                                               \
     template mgard_status rows3_mass_norm<T>(const Plan&, int, const T*, double*, cudaStream_t); \
-    template mgard_status rows3_features<T>(const Plan&, int, const T*, const double*, FeatPart*, \
-                                            cudaStream_t);                                       \
     template mgard_status rows3_quantize<T>(const Plan&, int, const T*, const double*, uint16_t*,       \
                                             int32_t*, unsigned long long*, unsigned*,            \
                                             cudaStream_t);                                       \
@@ -785,10 +759,10 @@ INST(float)
 INST(double)
 #undef INST
 template mgard_status rows3_correct<float, float>(const Plan&, int, const float*, float*, void*,
-                                                  void*, float, cudaStream_t);
+                                                  void*, float, cudaStream_t, int64_t);
 template mgard_status rows3_correct<float, double>(const Plan&, int, const float*, float*, void*,
-                                                   void*, float, cudaStream_t);
+                                                  void*, float, cudaStream_t, int64_t);
 template mgard_status rows3_correct<double, double>(const Plan&, int, const double*, double*,
-                                                    void*, void*, double, cudaStream_t);
+                                                    void*, void*, double, cudaStream_t, int64_t);
 
 }  // namespace mgb

@@ -16,15 +16,20 @@ inline bool rows3_ok(const Plan& p) {
     return p.n4[0] == 1 && p.total() < (int64_t(1) << 31);
 }
 
+// With zoff >= 0 the level's coefficients are read from (coeff: written
+// to) an array in symbol order, starting at symbol offset zoff: the nodes new
+// on the level in row-major order (see zs_row_base); otherwise they sit in
+// the level's own row-major array.
 template <typename T>
-mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st);
+mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st,
+                         int64_t zoff = -1);
 template <typename T>
 mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
-                        cudaStream_t st);
+                        cudaStream_t st, int64_t zoff = -1);
 // coarse += sign * M_{l-1}^{-1} P^T M_l z (restriction x, y, z; solves z, y, x)
 template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
-                           T sign, cudaStream_t st);
+                           T sign, cudaStream_t st, int64_t zoff = -1);
 template <typename T>
 mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,
@@ -37,13 +42,6 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
 int rows3_mass_norm_blocks(const Plan& p, int l);
 template <typename T>
 mgard_status rows3_mass_norm(const Plan& p, int l, const T* u, double* partial, cudaStream_t st);
-
-// Coefficient statistics of level l (predictor features): one FeatPart per
-// block (rows3_feature_blocks of them); amax (device) holds max|u|.
-template <typename T>
-mgard_status rows3_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
-                            cudaStream_t st);
-int rows3_feature_blocks(const Plan& p, int l);
 
 // Solvers shared with the generic path (multilevel.cu).
 template <typename Tw, typename Tdst>

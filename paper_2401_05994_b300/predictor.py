@@ -44,17 +44,22 @@ def sweep(field: torch.Tensor, taus=TAUS, s: float = math.inf):
     return xs, t, ratios
 
 
+def samples(field: torch.Tensor, taus=TAUS, s: float = math.inf):
+    """Training samples of one field.  Tolerances below the point where the
+    ratio starts to rise are dropped: there many tolerances give the same
+    ratio and the inverse map the network learns is undefined."""
+    x, t, r = sweep(field, taus, s)
+    keep = [k for k in range(len(r)) if r[k] > 1.02 * r[0] and (k == 0 or r[k] > 1.002 * r[k - 1])]
+    idx = torch.tensor(keep, dtype=torch.long, device=x.device)
+    return x[idx], t[idx]
+
+
 def dataset(fields, taus=TAUS, s: float = math.inf):
-    """Samples of all fields.  Tolerances below the point where the ratio
-    starts to rise are dropped: there many tolerances give the same ratio
-    and the inverse map the network learns is undefined."""
     xs, ts = [], []
     for f in fields:
-        x, t, r = sweep(f, taus, s)
-        keep = [k for k in range(len(r)) if r[k] > 1.02 * r[0] and (k == 0 or r[k] > 1.002 * r[k - 1])]
-        idx = torch.tensor(keep, dtype=torch.long, device=x.device)
-        xs.append(x[idx])
-        ts.append(t[idx])
+        x, t = samples(f, taus, s)
+        xs.append(x)
+        ts.append(t)
     return torch.cat(xs), torch.cat(ts)
 
 
