@@ -41,6 +41,11 @@ SHAPE = (513, 513, 513)
 TOL = 1e-3
 BETA = 5.0 / 3.0
 SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
+# DRAM bytes (read + write) of one launch from ncu captures of a smaller case
+# (profiles/), with the elements that launch processed; scaled to the bench
+# workload by elements (the traffic of these kernels grows in proportion).
+# Valid for the kernel versions captured; kernels without a capture report null.
+NCU_TRAFFIC = {"k_decode": (131.132160e6 + 175.089408e6, 385 ** 3)}
 
 
 def level_shapes(shape):
@@ -481,8 +486,12 @@ def main():
     roof = None
     if dom:
         ach = algo.get(dom, 0.0) / (kernel_ms[dom] / 1e3) / 1e9
+        traffic = None
+        if dom in NCU_TRAFFIC and rep.get(dom, (0,))[0] == trace_steps:   # one launch per step
+            b, n0 = NCU_TRAFFIC[dom]
+            traffic = b * int(np.prod(shape)) / n0
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
+                "frac": ach / hbm, "traffic": traffic, "peak_source": peak_src,
                 "kernel_ms_per_step": kernel_ms[dom],
                 "kernel_share": kernel_ms[dom] / sum(kernel_ms.values())}
 

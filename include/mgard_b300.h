@@ -246,6 +246,7 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
  * field succeeded, else the status of the first failing field. */
 #define MGARD_BATCH_GRAPH 1
 #define MGARD_BATCH_AUTOTUNE 2   /* run mgard_autotune on every new shape of the batch first */
+#define MGARD_BATCH_REPEAT 4     /* capture and replay a graph once an identical call repeats */
 mgard_status mgard_compress_batch(int n, const void* const* fields, const int* ndims,
                                   const int64_t* const* shapes, mgard_dtype dtype, double tol,
                                   double s, mgard_tolmode mode, void* const* outs,

@@ -513,6 +513,22 @@ mgard_status mgard_compress(const void* field, int ndim, const int64_t* shape, m
     MGB_TRY(get_plan(ndim, shape, -1, &p));
     cudaStream_t st = (cudaStream_t)stream;
     const bool dev = is_device_ptr(field);
+    // device field into a device buffer: the one-field batch path, which keeps
+    // the workspace and replays a captured graph when the same call repeats
+    if (dev && out_preallocated && out && *out && out_bytes && is_device_ptr(*out) &&
+        ((uintptr_t)*out & 15) == 0) {
+        const uint64_t N = (uint64_t)p->total();
+        if (*out_bytes >= layout(p->L, (N + CHUNK - 1) / CHUNK, 0, 0).outliers) {
+            const void* f = field;
+            const int64_t* shp = shape;
+            size_t cap = *out_bytes, bytes = 0;
+            mgard_status fst = MGARD_OK;
+            const mgard_status r = mgard_compress_batch(1, &f, &ndim, &shp, dtype, tol, s, mode, out,
+                                                        &cap, &bytes, &fst, MGARD_BATCH_REPEAT, stream);
+            if (r == MGARD_OK || r == MGARD_ECAPACITY) *out_bytes = bytes;
+            return r;
+        }
+    }
     if (dtype == MGARD_F32)
         return compress_impl<float>(*p, field, dev, dtype, ndim, shape, tol, s, mode, out, out_bytes,
                                     out_preallocated, st);
@@ -528,6 +544,15 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field, int
     }
     cudaStream_t st = (cudaStream_t)stream;
     const bool in_dev = is_device_ptr(in);
+    // device buffer into a device field: the one-buffer batch path (see
+    // mgard_compress)
+    if (in_dev && out_preallocated && *field && is_device_ptr(*field)) {
+        const void* i = in;
+        const size_t cap = ~size_t(0);   // the caller guarantees room for the field
+        mgard_status fst = MGARD_OK;
+        return mgard_decompress_batch(1, &i, &in_bytes, field, &cap, &fst, MGARD_BATCH_REPEAT,
+                                      stream);
+    }
     mgard_header h;
     std::vector<double> w;
     MGB_TRY(read_header(in, in_bytes, in_dev, &h, &w, st));

@@ -54,6 +54,7 @@ struct Lanes {
     cudaStream_t origin = nullptr;
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
     cudaGraphExec_t exec = nullptr;
+    int runs = 0;   // calls served so far
 
     mgard_status init() {
         for (int s = 0; s < BATCH_STREAMS; ++s) {
@@ -181,6 +182,14 @@ struct BatchState {
     }
 };
 
+// Graphs are used when asked for, or (MGARD_BATCH_REPEAT) from the second
+// identical call on; never while kernel tracing is on (graph launches are not
+// traced).
+bool use_graph(int flags, const Lanes& lanes) {
+    if (timing_on()) return false;
+    return (flags & MGARD_BATCH_GRAPH) || ((flags & MGARD_BATCH_REPEAT) && lanes.runs > 0);
+}
+
 std::mutex g_batch_mu;
 std::list<std::unique_ptr<BatchState>> g_batches;   // most recently used first
 
@@ -213,7 +222,7 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
     }
     if (!(tol > 0.0) || !std::isfinite(tol) || std::isnan(s) || s < 0.0 ||
         (mode != MGARD_ABS && mode != MGARD_REL) ||
-        (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_AUTOTUNE))) {
+        (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_AUTOTUNE | MGARD_BATCH_REPEAT))) {
         set_error("tol must be positive and finite, s >= 0 or INFINITY, mode ABS or REL");
         return MGARD_EINVAL;
     }
@@ -277,8 +286,9 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         b = g_batches.front().get();
     }
     auto body = [b](int i, cudaStream_t ss) { return b->field(i, ss); };
-    if (flags & MGARD_BATCH_GRAPH) MGB_TRY(b->lanes.run_graph(st, n, body));
+    if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph(st, n, body));
     else MGB_TRY(b->lanes.run(st, n, body));
+    ++b->lanes.runs;
     MGB_CUDA(cudaMemcpyAsync(b->hmetas, b->metas, sizeof(CompressMeta) * n, cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     mgard_status first = MGARD_OK;
@@ -293,7 +303,12 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         if (statuses) statuses[i] = e;
         if (e != MGARD_OK && first == MGARD_OK) {
             first = e;
-            set_error("batched compression: field " + std::to_string(i) + " failed");
+            const char* why = e == MGARD_ENONFINITE ? "input holds NaN or Inf"
+                              : e == MGARD_ERANGE   ? "tolerance too small: a quantized value exceeds the 32-bit range"
+                              : e == MGARD_ECAPACITY ? "output buffer too small"
+                                                     : "a symbol has no Huffman code";
+            set_error(n == 1 ? std::string(why)
+                             : "batched compression: field " + std::to_string(i) + ": " + why);
         }
     }
     return first;
@@ -380,7 +395,7 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
         set_error("null argument");
         return MGARD_EINVAL;
     }
-    if (flags & ~MGARD_BATCH_GRAPH) {
+    if (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_REPEAT)) {
         set_error("unknown flags");
         return MGARD_EINVAL;
     }
@@ -483,8 +498,9 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
     const int m = (int)b->items.size();
     auto body = [b](int k, cudaStream_t ss) { return b->item(k, ss); };
     if (m) {
-        if (flags & MGARD_BATCH_GRAPH) MGB_TRY(b->lanes.run_graph(st, m, body));
+        if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph(st, m, body));
         else MGB_TRY(b->lanes.run(st, m, body));
+        ++b->lanes.runs;
         MGB_CUDA(cudaMemcpyAsync(b->hstat, b->stat, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, st));
     }
     MGB_CUDA(cudaStreamSynchronize(st));
@@ -495,7 +511,10 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
         if (statuses) statuses[i] = e;
         if (e != MGARD_OK && first == MGARD_OK) {
             first = e;
-            set_error("batched decompression: buffer " + std::to_string(i) + " failed");
+            // a header failure keeps the reason check_header gave (one buffer)
+            if (n > 1 || b->plans[i])
+                set_error("batched decompression: buffer " + std::to_string(i) +
+                          (e == MGARD_ECAPACITY ? ": field buffer too small" : ": corrupt stream"));
         }
     }
     return first;

@@ -31,6 +31,7 @@ void set_error(const std::string& msg);
 // Kernel tracing (timing.cu): a scope that brackets the launches inside it
 // with CUDA events on `st` when mgard_timing_enable(1) is in effect.
 int timing_begin(const char* name, cudaStream_t st);
+bool timing_on();
 void timing_end(int slot, cudaStream_t st);
 struct ScopedTimer {
     int slot;

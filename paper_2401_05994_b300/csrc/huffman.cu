@@ -704,10 +704,15 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
             ok = false;
             continue;
         }
-        // window: `nb` valid bits, left-justified in `win`
+        // window: `nb` valid bits, left-justified in `win`; the next eight
+        // words wait in f[] (loaded eight refills ahead of their use, so the
+        // latency of a load is covered by the decoding of about 20 symbols)
         uint64_t wi = bstart >> 5;
         const uint32_t w0 = wi < cw1 ? words[wi] : 0u;
         ++wi;
+        uint32_t f[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) f[q] = wi + q < cw1 ? words[wi + q] : 0u;
         const unsigned skip = (unsigned)(bstart & 31);
         uint64_t win = ((uint64_t)w0 << 32) << skip;
         int nb = 32 - (int)skip;
@@ -722,63 +727,76 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
             while (lvl < dq.lo.L && (long long)first >= dq.lo.off[lvl + 1]) ++lvl;
             lvl_end = dq.lo.off[lvl + 1];
         }
-        int k = 0;
-        for (; k < cnt; ++k) {
-            if (nb <= 32) {
-                const uint32_t w = wi < cw1 ? words[wi] : 0u;
-                ++wi;
-                win |= (uint64_t)w << (32 - nb);
-                nb += 32;
-            }
-            const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
-            unsigned len, s;
-            if (ent) {
-                len = ent >> 12;
-                s = ent & 0xFFF;
-            } else {
-                const uint32_t top = (uint32_t)(win >> 32);
-                unsigned l = LUT_BITS + 1;
-                while (l <= maxlen && (unsigned long long)top >= lim[l]) ++l;
-                if (l > maxlen) {
-                    ok = false;
-                    break;
+        // groups of eight symbols, unrolled so that the per-group buffers
+        // (pk, vk) stay in registers
+        bool bad = false;
+        for (int k0 = 0; k0 < cnt && !bad; k0 += 8) {
+#pragma unroll
+            for (int slot = 0; slot < 8; ++slot) {
+                const int k = k0 + slot;
+                if (k >= cnt || bad) continue;
+                if (nb <= 32) {
+                    win |= (uint64_t)f[0] << (32 - nb);
+                    nb += 32;
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) f[q] = f[q + 1];
+                    f[7] = wi + 8 < cw1 ? words[wi + 8] : 0u;
+                    ++wi;
                 }
-                len = l;
-                s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
-            }
-            win <<= len;
-            nb -= (int)len;
-            used += len;
-            int32_t qesc = 0;
-            if (s == MGARD_ESC) {
-                if (e >= e_end) {
-                    ok = false;
-                    break;
+                const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
+                unsigned len, s;
+                if (ent) {
+                    len = ent >> 12;
+                    s = ent & 0xFFF;
+                } else {
+                    const uint32_t top = (uint32_t)(win >> 32);
+                    unsigned l = LUT_BITS + 1;
+                    while (l <= maxlen && (unsigned long long)top >= lim[l]) ++l;
+                    if (l > maxlen) {
+                        bad = true;
+                        continue;
+                    }
+                    len = l;
+                    s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
                 }
-                qesc = next_out;
-                if (SYM) escapes[first + k] = next_out;
-                ++e;
-                next_out = e < e_end ? outliers[e] : 0;
+                win <<= len;
+                nb -= (int)len;
+                used += len;
+                int32_t qesc = 0;
+                if (s == MGARD_ESC) {
+                    if (e >= e_end) {
+                        bad = true;
+                        continue;
+                    }
+                    qesc = next_out;
+                    if (SYM) escapes[first + k] = next_out;
+                    ++e;
+                    next_out = e < e_end ? outliers[e] : 0;
+                }
+                if (SYM) {
+                    if (slot & 1) pk[slot >> 1] |= s << 16;
+                    else pk[slot >> 1] = s;
+                } else {
+                    while (lvl < dq.lo.L && (long long)(first + k) >= lvl_end) lvl_end = dq.lo.off[++lvl + 1];
+                    OutT v;
+                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.w[lvl]);
+                    else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), dq.wf[lvl]);
+                    else v = (OutT)((double)((int)s - RADIUS) * dq.w[lvl]);
+                    vk[slot] = v;
+                }
             }
-            const int slot = k & 7;
-            if (SYM) {
-                if (slot & 1) pk[slot >> 1] |= s << 16;
-                else pk[slot >> 1] = s;
-                if (slot == 7)
-                    *reinterpret_cast<uint4*>(sym + first + k - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            } else {
-                while (lvl < dq.lo.L && (long long)(first + k) >= lvl_end) lvl_end = dq.lo.off[++lvl + 1];
-                OutT v;
-                if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.w[lvl]);
-                else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), dq.wf[lvl]);
-                else v = (OutT)((double)((int)s - RADIUS) * dq.w[lvl]);
-                vk[slot] = v;
-                if (slot == 7) store8(vals + first + k - 7, vk);
-            }
+            if (bad || k0 + 8 > cnt) continue;
+            if (SYM) *reinterpret_cast<uint4*>(sym + first + k0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            else store8(vals + first + k0, vk);
         }
-        if (k < cnt) continue;   // ok already cleared
+        if (bad) {
+            ok = false;
+            continue;
+        }
         const int rem = cnt & 7;   // symbols decoded after the last full group
-        for (int r = 0; r < rem; ++r) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (r >= rem) continue;
             if (SYM) {
                 const uint32_t w = pk[r >> 1];
                 sym[first + (cnt - rem) + r] = (uint16_t)((r & 1) ? (w >> 16) : (w & 0xFFFF));

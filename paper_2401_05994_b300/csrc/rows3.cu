@@ -133,6 +133,24 @@ __device__ inline void prefetch_l2(const void* p, size_t bytes) {
                         (size_t)(rowlen) * (esize));                                          \
     } while (0)
 
+// The same for rows of coefficients in symbol order (ZS kernels): the next
+// row starts at zs_row_base and is at most nx long; the range is clipped to
+// the level's run [zoff, zoff + count) of the array.
+#define PREFETCH_NEXT_ZS_ROW(base, zoff, r, nz, ny, nx, ncz, ncy, ncx, esize)                 \
+    do {                                                                                      \
+        const int64_t nr_ = (r) + (int64_t)gridDim.x * WPB;                                   \
+        if ((threadIdx.x & 31) == 0 && nr_ < (int64_t)(nz) * (ny)) {                          \
+            const int z_ = (int)((uint32_t)nr_ / (uint32_t)(ny));                             \
+            const int y_ = (int)(nr_ - (int64_t)z_ * (ny));                                   \
+            const int64_t b_ = zs_row_base(zoff, nr_, nx, z_, y_, nz, ny, ncy, ncx);          \
+            const int64_t end_ = (zoff) + (int64_t)(nz) * (ny) * (nx) -                        \
+                                 (int64_t)(ncz) * (ncy) * (ncx);                               \
+            const int64_t len_ = b_ + (nx) < end_ ? (nx) : end_ - b_;                         \
+            if (len_ > 0)                                                                     \
+                prefetch_l2((const char*)(base) + b_ * (esize), (size_t)len_ * (esize));      \
+        }                                                                                     \
+    } while (0)
+
 #define WARP_ROWS(rows, r)                                                                    \
     for (int64_t r = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); r < (rows);             \
          r += (int64_t)gridDim.x * WPB)
@@ -218,7 +236,8 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                          zz2 ? sz.w[1] * sy.w[0] : T(0), (zz2 && zy2) ? sz.w[1] * sy.w[1] : T(0)};
         const bool use[4] = {true, zy2, zz2, zz2 && zy2};
         const bool rowc = sz.n == 1 && sy.n == 1;
-        if (!ZS) PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
+        if (ZS) PREFETCH_NEXT_ZS_ROW(zin, zoff, r, nz, ny, nx, ncz, ncy, ncx, sizeof(T));
+        else PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* zrow = ZS ? zin + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : zin + r * nx;
         T* orow = out + r * nx;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
@@ -267,7 +286,8 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
     WARP_ROWS((int64_t)nz * ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
         const bool rowc = is_coarse(z, nz) && is_coarse(y, ny);
-        if (!ZS) PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
+        if (ZS) PREFETCH_NEXT_ZS_ROW(in, zoff, r, nz, ny, nx, ncz, ncy, ncx, sizeof(Tin));
+        else PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
         const Tin* irow = ZS ? in + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : in + r * nx;
         Tout* orow = out + r * ncx;
         // symbol order on a coarse row holds only the odd positions: ip -> (ip - 1) / 2
