@@ -535,6 +535,23 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         int64_t pend_at = -1;          // escape values are stored one escape late
         int32_t pend_v = 0;
         bool fill = true;              // every symbol of the chunk is the zero symbol
+        // all of the lane's symbols of the chunk are loaded up front (one
+        // memory latency per chunk instead of one per round)
+        uint4 raw[NSUB];
+#pragma unroll
+        for (int rd = 0; rd < NSUB; ++rd) {
+            const int first = rd * SUB + lane * 8;
+            if (first + 8 <= ccnt) {
+                raw[rd] = *reinterpret_cast<const uint4*>(sym + cbase + first);
+            } else {
+                unsigned t[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] = first + k < ccnt ? sym[cbase + first + k] : 0;
+                raw[rd] = make_uint4(t[0] | (t[1] << 16), t[2] | (t[3] << 16), t[4] | (t[5] << 16),
+                                     t[6] | (t[7] << 16));
+            }
+        }
+#pragma unroll
         for (int rd = 0; rd < NSUB; ++rd) {
             if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
                 sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
@@ -543,13 +560,10 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             const int first = rd * SUB + lane * 8;
             const int cnt = max(0, min(8, ccnt - first));
             unsigned sv[8];
-            if (cnt == 8) {
-                const uint4 v = *reinterpret_cast<const uint4*>(sym + cbase + first);
+            {
+                const uint4 v = raw[rd];
                 sv[0] = v.x & 0xFFFF; sv[1] = v.x >> 16; sv[2] = v.y & 0xFFFF; sv[3] = v.y >> 16;
                 sv[4] = v.z & 0xFFFF; sv[5] = v.z >> 16; sv[6] = v.w & 0xFFFF; sv[7] = v.w >> 16;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) sv[k] = k < cnt ? sym[cbase + first + k] : 0;
             }
             unsigned bits = 0, esc = 0;
 #pragma unroll
@@ -883,7 +897,7 @@ mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* length
                           int32_t* outliers, cudaStream_t st, PackGuard guard) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 4), PACK_WARPS * 32, 0, st>>>(
+    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
         sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;

@@ -231,19 +231,27 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
     __shared__ unsigned sh[2][DICT];
     __shared__ double ws[MAX_LEVELS + 1];
     __shared__ T iws[MAX_LEVELS + 1];
+    __shared__ long long offs[MAX_LEVELS + 2];
     for (int k = threadIdx.x; k < 2 * DICT; k += QS_THREADS) (&sh[0][0])[k] = 0;
     for (int l = threadIdx.x; l <= lo.L; l += QS_THREADS) {
         ws[l] = wdev[l];
         iws[l] = (T)(1.0 / wdev[l]);
     }
+    for (int l = threadIdx.x; l <= lo.L + 1; l += QS_THREADS) offs[l] = lo.off[l];
     __syncthreads();
+    const int L = lo.L;
     unsigned* my = sh[threadIdx.x & 1];
     unsigned center = 0, st = 0;
     for (int64_t g = blockIdx.x * (int64_t)QS_THREADS + threadIdx.x; g * 8 < n;
          g += (int64_t)gridDim.x * QS_THREADS) {
         const int64_t i0 = g * 8;
+        // the level of the group's first value; its width stays in registers
+        // until a value crosses into the next level (rare)
         int l = 0;
-        while (l < lo.L && i0 >= lo.off[l + 1]) ++l;
+        while (l < L && i0 >= offs[l + 1]) ++l;
+        long long lend = offs[l + 1];
+        double wl = ws[l];
+        T iwl = iws[l];
         T v[8];
         const bool full = i0 + 8 <= n;
         if (full) {
@@ -269,10 +277,15 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
         for (int k = 0; k < 8; ++k) {
             const int64_t i = i0 + k;
             if (i >= n) break;
-            while (l < lo.L && i >= lo.off[l + 1]) ++l;
+            if (i >= lend) {
+                while (l < L && i >= offs[l + 1]) ++l;
+                lend = offs[l + 1];
+                wl = ws[l];
+                iwl = iws[l];
+            }
             int s;
             int32_t qo = 0;
-            quantize_value(v[k], iws[l], ws[l], s, qo, st);
+            quantize_value(v[k], iwl, wl, s, qo, st);
             packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
             if (s == MGARD_ESC) esc[i] = qo;
             if (s == RADIUS) ++center;

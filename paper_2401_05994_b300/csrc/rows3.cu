@@ -14,7 +14,7 @@ namespace {
 
 constexpr int RT = 256;              // threads per block: 8 warps, one x-row per warp
 constexpr int WPB = RT / 32;
-constexpr int64_t ROW_BLOCKS = 148 * 8;
+constexpr int64_t ROW_BLOCKS = 148 * 16;   // the autotuner prefers 16 resident blocks per SM on large levels
 // Elements per lane per batch: all loads of a batch are issued before its
 // stores, so a batch covering a whole row puts the entire row in flight.
 // U is chosen per launch from the row length (2, 5, 9 or 17 -> rows of up to

@@ -1,0 +1,163 @@
+"""Full-size checks in the launch configuration the benchmark times.
+
+The oracle cannot decompose a 513^3 or 1025^3 field in seconds, so these
+tests check what holds at any size and what the oracle can compute one value
+at a time:
+
+* the FP64 error of compress + decompress is within the bound (L-infinity
+  and s = 0), measured on the device and on sampled points on the host;
+* finest-level coefficients at sampled nodes equal the oracle's local
+  definition c = u - (mean of the coarse neighbours along the node's new
+  axes): on the finest grid every spacing is 1, so the interpolation
+  weights are 1/2 per new axis;
+* the quantized symbols of those nodes, at their places in symbol order
+  (level 0, then the nodes new on each level, row-major), equal the
+  float32 quantization rule applied to the sampled coefficients.
+
+Workloads: the 513^3 k^-5/3 field of the benchmark (rel L-infinity 1e-3),
+and the 1025^3 field with 50 Gaussian blobs at rel 1e-4 (L-infinity and L2).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2401_05994_b300 import binding, synth
+from paper_2401_05994_b300.fmt import parse
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _sample_new_nodes(shape, k, rng):
+    """k random nodes of the finest grid that are new on it (not on the next
+    coarser grid, whose positions are the even ones plus the last)."""
+    out = []
+    while len(out) < k:
+        i = tuple(int(rng.integers(0, n)) for n in shape)
+        coarse = all(x % 2 == 0 or x == n - 1 for x, n in zip(i, shape))
+        if not coarse:
+            out.append(i)
+    return out
+
+
+def _neighbour_sets(shape, nodes):
+    """For every node: the list of coarse neighbours along its new axes (odd
+    index, not the last one) -- 2^k of them for k new axes."""
+    sets = []
+    for i in nodes:
+        new = [d for d, (x, n) in enumerate(zip(i, shape)) if x % 2 == 1 and x != n - 1]
+        nb = []
+        for mask in range(1 << len(new)):
+            j = list(i)
+            for b, d in enumerate(new):
+                j[d] += 1 if (mask >> b) & 1 else -1
+            nb.append(tuple(j))
+        sets.append(nb)
+    return sets
+
+
+def _gather(t, idx):
+    ii = torch.tensor(idx, device=t.device)
+    return t[ii[:, 0], ii[:, 1], ii[:, 2]].double().cpu().numpy()
+
+
+def _symbol_index(shape, i, offset_L):
+    """Place of finest-grid node i among the symbols: offset of the finest
+    level plus the number of its new nodes before i in row-major order."""
+    nz, ny, nx = shape
+    z, y, x = i
+    cz = lambda n, m: (m + 1) // 2 if m < n else (n + 1) // 2      # coarse positions < m
+    ncy, ncx = (ny + 1) // 2 + (ny % 2 == 0), (nx + 1) // 2 + (nx % 2 == 0)
+    lin = (z * ny + y) * nx + x
+    coarse_before = cz(nz, z) * ncy * ncx
+    zc = z % 2 == 0 or z == nz - 1
+    yc = y % 2 == 0 or y == ny - 1
+    if zc:
+        coarse_before += cz(ny, y) * ncx
+        if yc:
+            coarse_before += cz(nx, x)
+    return offset_L + lin - coarse_before
+
+
+def _check_field(u, tol, s, nsamples=4000, seed=0):
+    shape = tuple(u.shape)
+    comp = torch.empty(binding.compress_bound(shape), dtype=torch.uint8, device=DEV)
+    out = torch.empty_like(u)
+    for _ in range(2):   # the second identical call replays the captured graph
+        buf = binding.compress(u, tol, s, binding.REL, out=comp)
+        binding.decompress(buf, out=out)
+    meta = binding.info(buf)
+    err = binding.error_norm(u, out, s)
+    assert err <= meta["tol_abs"], (err, meta["tol_abs"])
+    rng = np.random.default_rng(seed)
+    # sampled pointwise errors in FP64 on the host (L-infinity runs)
+    nodes = _sample_new_nodes(shape, nsamples, rng)
+    idx = torch.tensor(nodes, device=DEV)
+    uu = u[idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    oo = out[idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    if math.isinf(s):
+        assert np.max(np.abs(uu - oo)) <= meta["tol_abs"]
+    return buf, meta, nodes
+
+
+def _check_coefficients_and_symbols(u, buf, meta, nodes, s, symbols=True):
+    shape = tuple(u.shape)
+    v = binding.decompose(u.clone())
+    umax = float(u.abs().max())
+    # the oracle's local definition, in FP64 from the sampled input values
+    sets = _neighbour_sets(shape, nodes)
+    flat = [j for nb in sets for j in nb]
+    vals = _gather(u, flat)
+    centre = _gather(u, nodes)
+    ref, k = [], 0
+    for c, nb in zip(centre, sets):
+        ref.append(c - vals[k:k + len(nb)].mean())
+        k += len(nb)
+    ref = np.array(ref)
+    got = _gather(v, nodes)
+    del v
+    cmax = float(np.max(np.abs(ref)))
+    assert np.max(np.abs(got - ref)) <= max(1e-5 * cmax, 8 * 2.0 ** -24 * umax)
+    if not symbols:
+        return
+    # symbols of the sampled finest-level coefficients, read back from the
+    # compressed stream itself (decoded by the library's decoder)
+    h, sec = parse(buf.cpu().numpy().tobytes())
+    t = lambda a: torch.from_numpy(np.array(a)).to(DEV)
+    sym, _ = binding.huffman_decode(t(sec["words"]), t(sec["word_off"]), t(sec["esc_off"]),
+                                    t(sec["sub_off"]), t(sec["lengths"]), int(np.prod(shape)),
+                                    t(sec["outliers"]))
+    sv = sym.cpu().numpy()
+    w = sec["widths"]
+    L = len(w) - 1
+    offset_L = _coarse_count(shape)
+    inv = np.float32(1.0 / w[L])
+    for i, c in zip(nodes, got):
+        p = _symbol_index(shape, i, offset_L)
+        q = float(np.rint(np.float32(c) * inv))
+        expect = int(q) + 2048 if abs(q) < 2048 else 0
+        assert int(sv[p]) == expect, (i, p, q)
+
+
+def _coarse_count(shape):
+    """Nodes of the next coarser grid (the symbols before the finest level)."""
+    return int(np.prod([(n + 1) // 2 + (n % 2 == 0) for n in shape]))
+
+
+def test_bench_workload_513():
+    u = synth.gaussian_random_field((513, 513, 513), seed=1, device=DEV).contiguous()
+    binding.autotune(u.shape)
+    buf, meta, nodes = _check_field(u, 1e-3, math.inf)
+    _check_coefficients_and_symbols(u, buf, meta, nodes[:1500], math.inf)
+
+
+@pytest.mark.parametrize("s", [math.inf, 0.0])
+def test_blobs_1025(s):
+    u = synth.blobs_field((1025, 1025, 1025), seed=5, device=DEV).contiguous()
+    buf, meta, nodes = _check_field(u, 1e-4, s, nsamples=2000, seed=1)
+    ratio = u.numel() * 4 / buf.numel()
+    assert ratio > 1.0
+    if math.isinf(s):
+        _check_coefficients_and_symbols(u, buf, meta, nodes[:800], s, symbols=False)
