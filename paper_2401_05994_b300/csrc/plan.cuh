@@ -18,6 +18,8 @@ enum RowKind { RK_COEFF = 0, RK_FILL, RK_RX, RK_RROWS, RK_QUANT, RK_DEQUANT, RK_
 struct RowCfg {
     int u = 0;
     int bpsm = 0;
+    int stage = -1;   // coefficient and fill kernels: 0 interpolate per element, 1 stage in
+                      // shared memory, -1 the built-in choice (stage where the rows fit)
 };
 
 struct Plan {

@@ -32,6 +32,29 @@ __device__ inline int coarse_index(int i, int m, int mc) { return i == m - 1 ? m
 __device__ inline int restrict_center(int J, int m, int mc) { return J == mc - 1 ? m - 1 : 2 * J; }
 __device__ inline int coarse_before(int i) { return (i + 1) >> 1; }
 
+// Rounding spelled out, so the staged and per-element forms of the
+// interpolation (below) give the same bits whatever the compiler contracts.
+__device__ inline float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ inline double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ inline double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The up-to-four coarse source rows of a row combined along z and y at fine
+// x position xf: sum_k rw[k] rows[k][xf] over the rows in use (row 0 always).
+template <typename T>
+__device__ inline T combine_rows(const T* const rows[4], const T rw[4], const bool use[4], int xf) {
+    T a = rmul(rw[0], rows[0][xf]);
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (use[k]) a = rfma(rw[k], rows[k][xf], a);
+    return a;
+}
+
+// Interpolation along x between the combined values at the two coarse
+// neighbours (for a coarse x both are the node itself, with weights 1, 0).
+template <typename T>
+__device__ inline T lerp_x(T wl, T rl, T wr, T rr) { return rfma(wl, rl, rmul(wr, rr)); }
+
 // Coefficients of level l in symbol order (ZS kernels): the nodes new on the
 // level, row-major, starting at symbol offset `zoff`.  Row (z, y) of the level
 // grid starts at zoff + r nx minus the coarse-grid nodes before it; on a row
@@ -156,9 +179,12 @@ __device__ inline void prefetch_l2(const void* p, size_t bytes) {
          r += (int64_t)gridDim.x * WPB)
 
 // -- coefficients (decomposition step 1) --------------------------------------
-template <typename T, int U, bool ZS>
+// STAGE: as in the fill kernel, the source rows are combined along y and z
+// at the coarse x positions into a shared-memory row R first.
+template <typename T, int U, bool ZS, bool STAGE>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
                                                Level<T> lv, int64_t zoff) {
+    extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
@@ -183,6 +209,12 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const T* urow = in + r * nx;
         T* orow = ZS ? out + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
+        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ncx;
+        if (STAGE) {
+            // coarse node J sits at fine x = 2J, the last one at nx - 1
+            for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, min(2 * j, nx - 1));
+            __syncwarp();
+        }
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             T u[U], acc[U];
 #pragma unroll
@@ -192,15 +224,20 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 if (x >= nx) continue;
                 u[j] = urow[x];
                 // coarse x: neighbours x, x with weights (1, 0); new x: x-1, x+1
-                const int d = is_coarse(x, nx) ? 0 : 1;
+                const bool cx = is_coarse(x, nx);
+                const int d = cx ? 0 : 1;
                 T wl = (x & 1) ? T(0.5) : T(1), wr = (x & 1) ? T(0.5) : T(0);
                 if (x >= ireg) {
                     wl = wlx[x];
                     wr = wrx[x];
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (use[k]) acc[j] += rw[k] * (wl * rows[k][x - d] + wr * rows[k][x + d]);
+                if (STAGE) {
+                    const int jl = cx ? coarse_index(x, nx, ncx) : (x - 1) >> 1;
+                    acc[j] = lerp_x(wl, R[jl], wr, R[cx ? jl : jl + 1]);
+                } else {
+                    acc[j] = lerp_x(wl, combine_rows(rows, rw, use, x - d), wr,
+                                    combine_rows(rows, rw, use, x + d));
+                }
             }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -210,13 +247,19 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 else orow[(ZS && rowc) ? x - coarse_before(x) : x] = u[j] - acc[j];
             }
         }
+        if (STAGE) __syncwarp();   // R is rewritten by the warp's next row
     }
 }
 
 // -- recomposition fill ---------------------------------------------------------
-template <typename T, int U, bool ZS>
+// STAGE: the up-to-four coarse rows are first combined along y and z into
+// one row R of the coarse x grid in shared memory (each coarse value loaded
+// once), and the x interpolation then reads R; otherwise every element
+// interpolates each coarse row itself.
+template <typename T, int U, bool ZS, bool STAGE>
 __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
                                               Level<T> lv, int64_t zoff) {
+    extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const T* __restrict__ wlx = lv.ax[3].wl;
@@ -240,6 +283,11 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         else PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* zrow = ZS ? zin + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : zin + r * nx;
         T* orow = out + r * nx;
+        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ncx;
+        if (STAGE) {
+            for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, j);
+            __syncwarp();
+        }
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             T v[U];
 #pragma unroll
@@ -256,9 +304,8 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                     wl = wlx[x];
                     wr = wrx[x];
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (use[k]) v[j] += rw[k] * (wl * rows[k][jl] + wr * rows[k][jr]);
+                if (STAGE) v[j] = lerp_x(wl, R[jl], wr, R[jr]);
+                else v[j] = lerp_x(wl, combine_rows(rows, rw, use, jl), wr, combine_rows(rows, rw, use, jr));
                 // z vanishes on coarse nodes of the coarse grid's rows
                 if (!(rowc && cx)) v[j] += zrow[(ZS && rowc) ? x - coarse_before(x) : x];
             }
@@ -268,6 +315,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                 if (x < nx) orow[x] = v[j];
             }
         }
+        if (STAGE) __syncwarp();   // R is rewritten by the warp's next row
     }
 }
 
@@ -640,6 +688,15 @@ QRow make_qrow(const Plan& p, int l) {
     return q;
 }
 
+// Shared memory of a staged coefficient or fill launch (one coarse x-row
+// per warp), or 0 when the launch shape asks for per-element interpolation
+// or the rows do not fit the default 48 KB.
+template <typename T>
+size_t stage_bytes(const Level<T>& lv, const RowCfg& c) {
+    const size_t b = (size_t)WPB * (size_t)lv.nc[3] * sizeof(T);
+    return c.stage != 0 && b <= 48 * 1024 ? b : 0;
+}
+
 }  // namespace
 
 template <typename T>
@@ -648,11 +705,17 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
     const Level<T>& lv = p.level<T>(l);
     const RowCfg c = p.row_cfg(l, RK_COEFF);
     const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
+    const size_t sm = stage_bytes<T>(lv, c);
     with_cfg(c, lv.n[3], false, [&](auto u) {
-        if (zoff >= 0)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value, true><<<g, RT, 0, st>>>(in, out, coarse, lv, zoff));
+        constexpr int U = decltype(u)::value;
+        if (zoff >= 0 && sm)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true><<<g, RT, sm, st>>>(in, out, coarse, lv, zoff));
+        else if (zoff >= 0)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false><<<g, RT, 0, st>>>(in, out, coarse, lv, zoff));
+        else if (sm)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true><<<g, RT, sm, st>>>(in, out, coarse, lv, 0));
         else
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, decltype(u)::value, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -664,11 +727,17 @@ mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* ou
     const Level<T>& lv = p.level<T>(l);
     const RowCfg c = p.row_cfg(l, RK_FILL);
     const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
+    const size_t sm = stage_bytes<T>(lv, c);
     with_cfg(c, lv.n[3], false, [&](auto u) {
-        if (zoff >= 0)
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value, true><<<g, RT, 0, st>>>(z, coarse, out, lv, zoff));
+        constexpr int U = decltype(u)::value;
+        if (zoff >= 0 && sm)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, true><<<g, RT, sm, st>>>(z, coarse, out, lv, zoff));
+        else if (zoff >= 0)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, false><<<g, RT, 0, st>>>(z, coarse, out, lv, zoff));
+        else if (sm)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, true><<<g, RT, sm, st>>>(z, coarse, out, lv, 0));
         else
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, decltype(u)::value, false><<<g, RT, 0, st>>>(z, coarse, out, lv, 0));
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, false><<<g, RT, 0, st>>>(z, coarse, out, lv, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;

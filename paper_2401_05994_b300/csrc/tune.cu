@@ -3,7 +3,8 @@
 // For every level of a shape and every row kernel (coefficients, fill,
 // restriction along x, restriction along y/z, quantization,
 // dequantization) the tuner times each launch shape -- 2, 4 or 8 elements
-// per lane per batch, grids sized for 4, 8 or 16 resident blocks per SM --
+// per lane per batch, grids sized for 4, 8 or 16 resident blocks per SM, and
+// for the coefficient and fill kernels rows staged in shared memory or not --
 // on workspace buffers holding a decomposed synthetic field, and keeps the
 // fastest in the shape's plan.  Launch shapes change only how rows are
 // spread over warps, never the arithmetic, so every choice gives the same
@@ -94,12 +95,15 @@ mgard_status tune_impl(const Plan& p, cudaStream_t st, std::string& rep) {
             const RowCfg keep = slot;
             float best = 1e30f, base = 0.f;
             RowCfg pick = keep;
+            const int nstage = (kind == RK_COEFF || kind == RK_FILL) ? 2 : 1;
             for (int ui = -1; ui < 3 && err == MGARD_OK; ++ui) {
-                for (int bi = 0; bi < 3 && err == MGARD_OK; ++bi) {
-                    if (ui < 0 && bi > 0) break;   // ui = -1: the built-in choice
+                for (int bs = 0; bs < 3 * nstage && err == MGARD_OK; ++bs) {
+                    const int bi = bs % 3;
+                    if (ui < 0 && bs > 0) break;   // ui = -1: the built-in choice
                     RowCfg c;
                     c.u = ui < 0 ? 0 : U_CAND[ui];
                     c.bpsm = ui < 0 ? 0 : B_CAND[bi];
+                    c.stage = (ui < 0 || nstage == 1) ? -1 : 1 - bs / 3;
                     slot = c;
                     if ((err = run(l, kind)) != MGARD_OK) break;   // warm-up
                     cudaEventRecord(e0, st);
@@ -118,8 +122,9 @@ mgard_status tune_impl(const Plan& p, cudaStream_t st, std::string& rep) {
             }
             slot = err == MGARD_OK ? pick : keep;
             char line[160];
-            std::snprintf(line, sizeof(line), "level %d %-13s u=%d blocks/SM=%d %.4f ms (built-in %.4f ms)\n",
-                          l, KIND_NAME[kind], pick.u, pick.bpsm, best, base);
+            std::snprintf(line, sizeof(line),
+                          "level %d %-13s u=%d blocks/SM=%d stage=%d %.4f ms (built-in %.4f ms)\n",
+                          l, KIND_NAME[kind], pick.u, pick.bpsm, pick.stage, best, base);
             rep += line;
         }
     }
