@@ -129,7 +129,10 @@ mgard_status mgard_error_norm(const void* a, const void* b, int ndim, const int6
  * that level's grid): n = product of the extents symbols in total.  F32 data
  * decides q = rint(float(c) * float(1/w)) in float; F64 data
  * q = rint(c / w) in double.  |q| < MGARD_DICT/2 -> symbol q + MGARD_DICT/2,
- * else MGARD_ESC and escapes[position] = rint(c / w) (double, as int32).
+ * else MGARD_ESC and escapes[position] = q, where for F32 data with
+ * |q| >= MGARD_DICT the escape is recomputed as rint(c / w) in double (the
+ * kernels reach the same integer through two-float arithmetic where it
+ * provably agrees).
  * hist (device, MGARD_DICT uint64) is overwritten with symbol counts.
  * symbols, escapes: device arrays of n entries.  Synchronizes the stream;
  * MGARD_ERANGE if some |rint(c/w)| > 2^31-1, MGARD_ENONFINITE for NaN/Inf. */
@@ -138,7 +141,8 @@ mgard_status mgard_quantize(const void* coeffs, int ndim, const int64_t* shape, 
                             int32_t* escapes, uint64_t* hist, void* stream);
 /* Inverse: writes the in-place coefficient array (device pointer) from
  * symbols and escapes (device, n entries each): c = q * w (float32 product
- * for F32 symbols; double product rounded to the dtype for escapes). */
+ * for F32 symbols and escapes with |q| < MGARD_DICT; otherwise the double
+ * product rounded to the dtype). */
 mgard_status mgard_dequantize(const uint16_t* symbols, const int32_t* escapes, int ndim,
                               const int64_t* shape, mgard_dtype dtype, int max_levels,
                               const double* widths, void* coeffs, void* stream);

@@ -58,10 +58,82 @@ constexpr int LMAX = MGARD_LMAX;
 // decided and dequantized in double.
 constexpr int F32_EXACT = 4096;
 
+// Escapes of F32_EXACT bins or more follow double-precision rules: the
+// quotient q = rint(fl64(c / w)) and the value fl32(fl64(q * w)).  B300 runs
+// FP64 at about two lanes per clock per SM, and under SIMT a warp pays for a
+// lane's FP64 branch in nearly every group of symbols, so the float path
+// takes these decisions in two-float arithmetic (error below 2^-45 relative)
+// whenever that error bound proves the double computation rounds the same
+// way, and falls back to double otherwise (well under 0.1% of typical
+// escapes).  The result is the double rule's, bit for bit.
+struct WidthSplit {
+    float hi, lo;   // w = hi + lo + r with |r| <= 2^-48 w; hi = 0: no split (always double)
+};
+__host__ __device__ inline WidthSplit split_width(double w) {
+    WidthSplit s{0.f, 0.f};
+    if (w >= 0x1p-60 && w <= 0x1p60) {
+        s.hi = (float)w;
+        s.lo = (float)(w - (double)s.hi);
+    }
+    return s;
+}
+
+// q = rint(fl64(c / w)) for a finite float c; false when it leaves int32
+// (the caller flags the range error).
+__device__ inline bool quant_big(float c, WidthSplit ws, double w, int32_t& qo) {
+    const float q0 = __fdiv_rn(c, ws.hi);   // hi = 0 gives +-inf: double path
+    if (fabsf(q0) < 0x1p21f) {
+        // t = c / w = q0 + q1 + e with |e| < 2^-23: the remainder of q0
+        // against both parts of w, divided by the leading part
+        const float r = __fmaf_rn(-q0, ws.hi, c);
+        const float r2 = __fmaf_rn(-q0, ws.lo, r);
+        const float q1 = __fdiv_rn(r2, ws.hi);
+        const float k0 = rintf(q0);
+        const float f = __fadd_rn(__fsub_rn(q0, k0), q1);   // q0 - k0 is exact
+        const float n = rintf(f);
+        const float g = __fsub_rn(f, n);                    // t - (k0 + n) = g +- 2^-22
+        if (fabsf(g) < 0.5f - 0x1p-16f) {                   // no half-integer within reach
+            qo = (int32_t)k0 + (int32_t)n;
+            return true;
+        }
+    }
+    const double qd = rint((double)c / w);
+    if (fabs(qd) > 2147483647.0) return false;
+    qo = (int32_t)qd;
+    return true;
+}
+
+// fl32(fl64(q * w)).
+__device__ inline float dequant_big(int32_t q, WidthSplit ws, double w) {
+    if (q > -(1 << 24) && q < (1 << 24)) {
+        // q * w = p0 + s + e with |e| < 2^-46 |q w| (q is exact in float)
+        const float qf = (float)q;
+        const float p0 = __fmul_rn(qf, ws.hi);
+        const float e0 = __fmaf_rn(qf, ws.hi, -p0);
+        const float s = __fmaf_rn(qf, ws.lo, e0);
+        const float f = __fadd_rn(p0, s);
+        // exact error of that sum (Knuth's two-sum)
+        const float bb = __fsub_rn(f, p0);
+        const float err = __fadd_rn(__fsub_rn(p0, __fsub_rn(f, bb)), __fsub_rn(s, bb));
+        const unsigned b = __float_as_uint(f);
+        const unsigned ex = (b >> 23) & 0xFFu;
+        // f rounds q * w and its double rounding alike when p0 + s stays
+        // 2^-16 ulp away from the midpoints f +- ulp/2 (equal spacing on
+        // both sides: f not a power of two; normal range with room below)
+        if (ex >= 64u && ex < 255u && (b & 0x7FFFFFu) != 0u) {
+            const float lim = __uint_as_float((ex - 24u) << 23) * (1.f - 0x1p-15f);
+            if (fabsf(err) < lim) return f;
+        }
+    }
+    return (float)((double)q * w);
+}
+
 template <typename T>
-__device__ inline T dequant_escape(int32_t q, T wt, double w) {
-    if (sizeof(T) == 4 && (q < F32_EXACT && q > -F32_EXACT))
-        return (T)__fmul_rn((float)q, (float)wt);
+__device__ inline T dequant_escape(int32_t q, T wt, WidthSplit ws, double w) {
+    if (sizeof(T) == 4) {
+        if (q < F32_EXACT && q > -F32_EXACT) return (T)__fmul_rn((float)q, (float)wt);
+        return (T)dequant_big(q, ws, w);
+    }
     return (T)((double)q * w);
 }
 

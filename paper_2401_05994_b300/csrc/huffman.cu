@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
                 } else {
                     while (lvl < dq.lo.L && (long long)(first + k) >= lvl_end) lvl_end = dq.lo.off[++lvl + 1];
                     OutT v;
-                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.w[lvl]);
+                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.ws[lvl], dq.w[lvl]);
                     else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), dq.wf[lvl]);
                     else v = (OutT)((double)((int)s - RADIUS) * dq.w[lvl]);
                     vk[slot] = v;

@@ -63,6 +63,7 @@ struct DeqArgs {
     LevelOffsets lo;
     double w[MAX_LEVELS + 1];
     float wf[MAX_LEVELS + 1];
+    WidthSplit ws[MAX_LEVELS + 1];   // split_width(w[l])
 };
 // Decoding with bounds checks (ST_CORRUPT on failure).
 mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,

@@ -364,6 +364,7 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
         for (int l = 0; l <= L; ++l) {
             dq.w[l] = w[l];
             dq.wf[l] = (float)w[l];
+            dq.ws[l] = split_width(w[l]);
         }
         T* zs = work.zs.template as<T>();
         MGB_TRY(huffman_decode_values<T>(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff,

@@ -62,8 +62,8 @@ __device__ inline NodeInfo node_info(const QLevel& q, const int64_t* i) {
     return r;
 }
 
-__device__ inline void quantize_value(float c, float inv_w, double w, int& sym, int32_t& qo,
-                                      unsigned& st) {
+__device__ inline void quantize_value(float c, float inv_w, WidthSplit ws, double w, int& sym,
+                                      int32_t& qo, unsigned& st) {
     if (!isfinite(c)) {
         st |= ST_NONFINITE;
         sym = MGARD_ESC;
@@ -81,17 +81,14 @@ __device__ inline void quantize_value(float c, float inv_w, double w, int& sym, 
         qo = (int32_t)q;
         return;
     }
-    const double qd = rint((double)c / w);
-    if (fabs(qd) > 2147483647.0) {
+    if (!quant_big(c, ws, w, qo)) {
         st |= ST_RANGE;
         qo = 0;
-    } else {
-        qo = (int32_t)qd;
     }
 }
 
-__device__ inline void quantize_value(double c, double /*inv_w*/, double w, int& sym, int32_t& qo,
-                                      unsigned& st) {
+__device__ inline void quantize_value(double c, double /*inv_w*/, WidthSplit, double w, int& sym,
+                                      int32_t& qo, unsigned& st) {
     if (!isfinite(c)) {
         st |= ST_NONFINITE;
         sym = MGARD_ESC;
@@ -126,6 +123,7 @@ __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel
     __syncthreads();
     const double w = *wp;
     const T inv_w = (T)(1.0 / w);
+    const WidthSplit ws = split_width(w);
     const int lane = threadIdx.x & 31;
     unsigned st = 0;
     // every loop bound is uniform across the block, so whole warps reach the
@@ -142,7 +140,7 @@ __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel
                     const NodeInfo ni = node_info(q, i);
                     if (!ni.skip) {
                         int32_t qo = 0;
-                        quantize_value(c[ni.addr], inv_w, w, s, qo, st);
+                        quantize_value(c[ni.addr], inv_w, ws, w, s, qo, st);
                         const int64_t p = q.sym_off + ni.rank;
                         sym[p] = (uint16_t)s;
                         if (s == MGARD_ESC) esc[p] = qo;
@@ -160,6 +158,7 @@ __global__ void __launch_bounds__(QT) k_quantize(const T* __restrict__ c, QLevel
 template <typename T>
 __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
                              QLevel q, T wt, double w, T* __restrict__ c) {
+    const WidthSplit ws = split_width(w);
     FOR_NODES(q.n, i0, i1, i2, i3) {
         const int64_t i[4] = {i0, i1, i2, i3};
         const NodeInfo ni = node_info(q, i);
@@ -170,7 +169,7 @@ __global__ void k_dequantize(const uint16_t* __restrict__ sym, const int32_t* __
         const int64_t p = q.sym_off + ni.rank;
         const int s = sym[p];
         T v;
-        if (s == MGARD_ESC) v = dequant_escape<T>(esc[p], wt, w);
+        if (s == MGARD_ESC) v = dequant_escape<T>(esc[p], wt, ws, w);
         else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
         else v = (T)((double)(s - RADIUS) * w);
         c[ni.addr] = v;
@@ -231,11 +230,13 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
     __shared__ unsigned sh[2][DICT];
     __shared__ double ws[MAX_LEVELS + 1];
     __shared__ T iws[MAX_LEVELS + 1];
+    __shared__ WidthSplit wss[MAX_LEVELS + 1];
     __shared__ long long offs[MAX_LEVELS + 2];
     for (int k = threadIdx.x; k < 2 * DICT; k += QS_THREADS) (&sh[0][0])[k] = 0;
     for (int l = threadIdx.x; l <= lo.L; l += QS_THREADS) {
         ws[l] = wdev[l];
         iws[l] = (T)(1.0 / wdev[l]);
+        wss[l] = split_width(wdev[l]);
     }
     for (int l = threadIdx.x; l <= lo.L + 1; l += QS_THREADS) offs[l] = lo.off[l];
     __syncthreads();
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
         long long lend = offs[l + 1];
         double wl = ws[l];
         T iwl = iws[l];
+        WidthSplit wsl = wss[l];
         T v[8];
         const bool full = i0 + 8 <= n;
         if (full) {
@@ -282,10 +284,11 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
                 lend = offs[l + 1];
                 wl = ws[l];
                 iwl = iws[l];
+                wsl = wss[l];
             }
             int s;
             int32_t qo = 0;
-            quantize_value(v[k], iwl, wl, s, qo, st);
+            quantize_value(v[k], iwl, wsl, wl, s, qo, st);
             packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
             if (s == MGARD_ESC) esc[i] = qo;
             if (s == RADIUS) ++center;

@@ -503,11 +503,12 @@ __global__ void __launch_bounds__(RT) k3_mass_norm(const T* __restrict__ u, Leve
 constexpr int HCOPIES = 2;
 
 template <typename T>
-__device__ inline void qvalue(T c, T inv_w, double w, int& sym, int32_t& qo, unsigned& st);
+__device__ inline void qvalue(T c, T inv_w, WidthSplit ws, double w, int& sym, int32_t& qo,
+                              unsigned& st);
 
 template <>
-__device__ inline void qvalue<float>(float c, float inv_w, double w, int& sym, int32_t& qo,
-                                     unsigned& st) {
+__device__ inline void qvalue<float>(float c, float inv_w, WidthSplit ws, double w, int& sym,
+                                     int32_t& qo, unsigned& st) {
     const float q = rintf(__fmul_rn(c, inv_w));
     if (fabsf(q) < (float)RADIUS) {   // false for NaN and +-Inf
         sym = (int)q + RADIUS;
@@ -523,14 +524,15 @@ __device__ inline void qvalue<float>(float c, float inv_w, double w, int& sym, i
         st |= ST_NONFINITE;
         return;
     }
-    const double qd = rint((double)c / w);
-    if (fabs(qd) > 2147483647.0) st |= ST_RANGE;
-    else qo = (int32_t)qd;
+    if (!quant_big(c, ws, w, qo)) {
+        st |= ST_RANGE;
+        qo = 0;
+    }
 }
 
 template <>
-__device__ inline void qvalue<double>(double c, double, double w, int& sym, int32_t& qo,
-                                      unsigned& st) {
+__device__ inline void qvalue<double>(double c, double, WidthSplit, double w, int& sym,
+                                      int32_t& qo, unsigned& st) {
     const double q = rint(c / w);
     if (fabs(q) < (double)RADIUS) {
         sym = (int)q + RADIUS;
@@ -581,6 +583,7 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
     __syncthreads();
     const double w = *wp;
     const T inv_w = (T)(1.0 / w);
+    const WidthSplit ws = split_width(w);
     unsigned* my = sh[threadIdx.x & (HCOPIES - 1)];
     unsigned center = 0;   // the most frequent symbol (q = 0) is counted in a register
     unsigned st = 0;
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(RT) k3_quantize(const T* __restrict__ c, QRow 
                 }
                 int s;
                 int32_t qo;
-                qvalue<T>(v[j], inv_w, w, s, qo, st);
+                qvalue<T>(v[j], inv_w, ws, w, s, qo, st);
                 sym[p] = (uint16_t)s;
                 if (s == MGARD_ESC) esc[p] = qo;
                 if (s == RADIUS) ++center;
@@ -634,6 +637,7 @@ __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__
                                                     const int32_t* __restrict__ esc, QRow q,
                                                     T wt, double w, T* __restrict__ c) {
     const int lane = threadIdx.x & 31;
+    const WidthSplit ws = split_width(w);
     WARP_ROWS((int64_t)q.nz * q.ny, r) {
         const int z = (int)((uint32_t)r / (uint32_t)q.ny), y = (int)(r - (int64_t)z * q.ny);
         bool rowc;
@@ -662,7 +666,7 @@ __global__ void __launch_bounds__(RT) k3_dequantize(const uint16_t* __restrict__
                 const int s = sv[j];
                 T v;
                 if (s < 0) v = T(0);
-                else if (s == MGARD_ESC) v = dequant_escape<T>(esc[pv[j]], wt, w);
+                else if (s == MGARD_ESC) v = dequant_escape<T>(esc[pv[j]], wt, ws, w);
                 else if (sizeof(T) == 4) v = (T)__fmul_rn((float)(s - RADIUS), (float)wt);
                 else v = (T)((double)(s - RADIUS) * w);
                 crow[x] = v;
