@@ -99,13 +99,14 @@ def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
         n, nc = int(np.prod(lv[l])), int(np.prod(lv[l + 1]))
         ew = 8 if nc < (1 << 21) else esize
         (nz, ny, nx), (cz, cy, cx) = lv[l], lv[l + 1]
-        add("k3_coeff", 2 * n * esize)                       # read u_l; write coefficients + coarse copy
+        # read u_l; write coefficients + coarse copy + (fused) the rows restricted along x
+        add("k3_coeff", 2 * n * esize + nz * ny * cx * ew)
         add("k3_fill", (2 * n + nc) * esize)                  # read coefficients and coarse; write u_l
+        add("k3_restrict_x", n * esize + nz * ny * cx * ew)   # recomposition only
         for _ in range(2):                                    # decomposition and recomposition
-            add("k3_restrict_x", n * esize + nz * ny * cx * ew)
             add("k3_restrict_rows", (nz * ny * cx + nz * cy * cx) * ew + (nz * cy * cx + nc) * ew)
-            add("k_solve_seg", 2 * 2 * nc * ew)               # z and y solves: read + write
-            add("k_solve_lines", 2 * 2 * nc * ew)             # (same solves on the generic path)
+            add("k_solve_tile", 2 * 2 * nc * ew)              # z and y solves: read + write
+            add("k_solve_lines", 2 * 2 * nc * ew)             # (same solves, lines over 1056 nodes)
             add("k_solve_warp", 2 * nc * ew + 2 * nc * esize)  # x solve + coarse update
     add("k_quantize_stream", N * esize + 2 * N + 4 * esc_count)
     add("k3_quantize", N * esize + 2 * N + 4 * esc_count)

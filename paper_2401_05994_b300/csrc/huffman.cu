@@ -243,33 +243,64 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
     }
 }
 
+// Canonical codes and decoding tables from the code lengths, one block.
+// A symbol's place in (length, symbol) order is fi[len] plus the number of
+// lower symbols of the same length: counts per 32-symbol chunk (one warp
+// match each), an exclusive scan over the chunks per length (one warp per
+// length), and the rank inside the chunk give it without a sort.
 __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict__ lengths,
                                                        uint32_t* __restrict__ codes,
                                                        DecodeTables* __restrict__ dt) {
-    __shared__ unsigned long long keys[DICT];
-    __shared__ unsigned wcnt[CB_THREADS / 32][LMAX + 2];   // per-warp length counts
+    constexpr int NCH = DICT / 32;                 // chunks of 32 symbols
+    constexpr int PER = DICT / CB_THREADS;         // symbols per thread
+    static_assert(NCH == 4 * 32 && PER * CB_THREADS == DICT && LMAX <= CB_THREADS / 32,
+                  "chunk scan layout");
+    __shared__ unsigned cc[NCH][LMAX + 2];         // chunk counts, then exclusive prefixes
+    __shared__ uint16_t ssym[DICT];                // used symbols in (length, symbol) order
     __shared__ unsigned cnt[LMAX + 2];
     __shared__ unsigned long long fc[LMAX + 2];
     __shared__ unsigned fi[LMAX + 2];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < (CB_THREADS / 32) * (LMAX + 2); k += blockDim.x) (&wcnt[0][0])[k] = 0;
+    for (int k = tid; k < NCH * (LMAX + 2); k += blockDim.x) (&cc[0][0])[k] = 0;
+    for (int k = tid; k < DICT; k += blockDim.x) ssym[k] = 0;
+    if (tid < LMAX + 2) cnt[tid] = 0;
     if (tid == 0) bad = 0;
     __syncthreads();
-    for (int s = tid; s < DICT; s += blockDim.x) {
+    unsigned mylen[PER], myrank[PER];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int s = it * CB_THREADS + tid;   // a warp holds one chunk
         const unsigned len = lengths[s];
         if (len > LMAX) bad = 1;
         const bool ok = len && len <= LMAX;
-        keys[s] = ok ? (((unsigned long long)len << 12) | (unsigned)s) : KEY_NONE;
-        // one shared update per distinct length in the warp
         const unsigned grp = __match_any_sync(0xffffffffu, ok ? (int)len : -1);
-        if (ok && lane == __ffs(grp) - 1) wcnt[warp][len] += __popc(grp);
+        mylen[it] = ok ? len : 0u;
+        myrank[it] = __popc(grp & ((1u << lane) - 1u));
+        if (ok && lane == __ffs(grp) - 1) cc[s >> 5][len] = __popc(grp);
     }
     __syncthreads();
-    if (tid < LMAX + 2) {
-        unsigned c = 0;
-        for (int w = 0; w < CB_THREADS / 32; ++w) c += wcnt[w][tid];
-        cnt[tid] = c;
+    if (warp < LMAX) {   // warp w scans length w + 1 over the chunks (4 per lane)
+        const int l = warp + 1;
+        unsigned v[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = cc[lane * 4 + j][l];
+            sum += v[j];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        unsigned run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cc[lane * 4 + j][l] = run;
+            run += v[j];
+        }
+        if (lane == 31) cnt[l] = incl;
     }
     __syncthreads();
     if (tid == 0) {
@@ -293,17 +324,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
         dt->maxlen = maxlen;
         dt->valid = valid ? 1 : 0;
     }
-    bitonic_sort(keys, DICT);   // ends with a barrier
-    for (int p = tid; p < DICT; p += blockDim.x) {
-        const unsigned long long key = keys[p];
-        if (key == KEY_NONE) continue;
-        const unsigned s = key & 0xFFF, len = (unsigned)(key >> 12);
-        const uint32_t c = (uint32_t)(fc[len] + (p - fi[len]));
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int s = it * CB_THREADS + tid;
+        const unsigned len = mylen[it];
+        if (!len) {
+            codes[s] = 0;
+            continue;
+        }
+        const unsigned rank = cc[s >> 5][len] + myrank[it];
+        const unsigned p = fi[len] + rank;
+        ssym[p] = (uint16_t)s;
         dt->sorted[p] = (uint16_t)s;
-        codes[s] = c;
+        codes[s] = (uint32_t)(fc[len] + rank);
     }
-    for (int s = tid; s < DICT; s += blockDim.x)
-        if (!lengths[s]) codes[s] = 0;
+    __syncthreads();
     // prefix table: the code under each 14-bit prefix, found from the
     // canonical limits (every entry costs the same, whatever the lengths)
     for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) {
@@ -314,7 +350,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
         if (l <= LUT_BITS) {
             const unsigned long long idx = fi[l] + ((top >> (32 - l)) - fc[l]);
             if ((top >> (32 - l)) >= fc[l] && idx < DICT)
-                ent = (uint16_t)((l << 12) | (unsigned)(keys[idx] & 0xFFF));
+                ent = (uint16_t)((l << 12) | (unsigned)ssym[idx]);
         }
         dt->lut[k] = ent;
     }
@@ -718,15 +754,15 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
             ok = false;
             continue;
         }
-        // window: `nb` valid bits, left-justified in `win`; the next eight
-        // words wait in f[] (loaded eight refills ahead of their use, so the
-        // latency of a load is covered by the decoding of about 20 symbols)
+        // window: `nb` valid bits, left-justified in `win`; the next two
+        // words wait in f[] (loaded two refills ahead of their use; a longer
+        // queue covered more latency but cost more moves than it saved)
         uint64_t wi = bstart >> 5;
         const uint32_t w0 = wi < cw1 ? words[wi] : 0u;
         ++wi;
-        uint32_t f[8];
+        uint32_t f[2];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) f[q] = wi + q < cw1 ? words[wi + q] : 0u;
+        for (int q = 0; q < 2; ++q) f[q] = wi + q < cw1 ? words[wi + q] : 0u;
         const unsigned skip = (unsigned)(bstart & 31);
         uint64_t win = ((uint64_t)w0 << 32) << skip;
         int nb = 32 - (int)skip;
@@ -735,12 +771,21 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
         uint32_t pk[4] = {0, 0, 0, 0};
         OutT vk[8];
         // level of the current symbol (dequantizing output)
-        int lvl = 0;
-        long long lvl_end = 0;
-        if (!SYM) {
-            while (lvl < dq.lo.L && (long long)first >= dq.lo.off[lvl + 1]) ++lvl;
-            lvl_end = dq.lo.off[lvl + 1];
-        }
+        // (level, its widths and the sub-chunk index where the next level
+        // starts) stay in registers; the boundary test is one compare
+        int lvl = 0, next_lvl = 1 << 30;
+        float cwf = 0.f;
+        double cw = 0.0;
+        WidthSplit cws{0.f, 0.f};
+        auto enter_level = [&](long long i) {
+            while (lvl < dq.lo.L && i >= dq.lo.off[lvl + 1]) ++lvl;
+            const long long rel = dq.lo.off[lvl + 1] - (long long)first;
+            next_lvl = (int)(rel < (long long)SUB + 1 ? rel : (long long)SUB + 1);
+            cwf = dq.wf[lvl];
+            cw = dq.w[lvl];
+            cws = dq.ws[lvl];
+        };
+        if (!SYM) enter_level((long long)first);
         // groups of eight symbols, unrolled so that the per-group buffers
         // (pk, vk) stay in registers
         bool bad = false;
@@ -752,9 +797,8 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
                 if (nb <= 32) {
                     win |= (uint64_t)f[0] << (32 - nb);
                     nb += 32;
-#pragma unroll
-                    for (int q = 0; q < 7; ++q) f[q] = f[q + 1];
-                    f[7] = wi + 8 < cw1 ? words[wi + 8] : 0u;
+                    f[0] = f[1];
+                    f[1] = wi + 2 < cw1 ? words[wi + 2] : 0u;
                     ++wi;
                 }
                 const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
@@ -791,11 +835,11 @@ __global__ void __launch_bounds__(DEC_THREADS) k_decode(
                     if (slot & 1) pk[slot >> 1] |= s << 16;
                     else pk[slot >> 1] = s;
                 } else {
-                    while (lvl < dq.lo.L && (long long)(first + k) >= lvl_end) lvl_end = dq.lo.off[++lvl + 1];
+                    if (k >= next_lvl) enter_level((long long)(first + k));
                     OutT v;
-                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)dq.wf[lvl], dq.ws[lvl], dq.w[lvl]);
-                    else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), dq.wf[lvl]);
-                    else v = (OutT)((double)((int)s - RADIUS) * dq.w[lvl]);
+                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)cwf, cws, cw);
+                    else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), cwf);
+                    else v = (OutT)((double)((int)s - RADIUS) * cw);
                     vk[slot] = v;
                 }
             }

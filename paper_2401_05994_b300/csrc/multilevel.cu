@@ -187,54 +187,91 @@ __global__ void k_solve_lines(Tw* x, int64_t outer_n, int64_t m, int64_t stride,
         }
 }
 
-// Lines along a strided axis, each split into S segments of E elements:
-// thread (lane, warp) owns elements [warp*E, warp*E + E) of line
-// blockIdx.x*32 + lane, so every load and store is coalesced across the 32
-// lines of a warp and a line's S segments run in parallel.  The Thomas sweeps
-// are affine recurrences; each thread composes the map of its segment, the
-// block folds the maps of the preceding (forward) or following (backward)
-// segments through shared memory, and each thread replays its segment.
+// Lines along a strided axis, 32 adjacent lines (consecutive inner
+// positions) per tile.  The block copies the tile, m rows of 32 elements
+// each read as one coalesced warp access, into shared memory (row pitch 33),
+// every warp solves lines of the tile with the warp-scan scheme of
+// k_solve_warp (lane j owns elements [jE, jE+E) of the line; E odd, so the
+// column reads are free of bank conflicts), and the block writes the tile
+// back.  A lane's Thomas factors stay in registers across lines and tiles.
+constexpr int ST_WARPS = 8;
+
 template <typename Tw, typename Tdst, int E>
-__global__ void __launch_bounds__(1024) k_solve_seg(Tw* x, int64_t outer_n, int m, int64_t stride,
-                                                    const Tw* __restrict__ sub,
-                                                    const Tw* __restrict__ inv,
-                                                    const Tw* __restrict__ cp, Tdst* dst, Tw sign) {
-    __shared__ Tw sA[32][33], sB[32][33];
-    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5, S = blockDim.x >> 5;
-    const int k0 = seg * E;
-    for (int64_t outer = blockIdx.y; outer < outer_n; outer += gridDim.y)
-        for (int64_t inner0 = (int64_t)blockIdx.x * 32; inner0 < stride;
-             inner0 += (int64_t)gridDim.x * 32) {
-            const int64_t inner = inner0 + lane;
-            const bool valid = inner < stride;
-            Tw* base = x + outer * m * stride + inner;
+__global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t outer_n, int m,
+                                                              int64_t stride,
+                                                              const Tw* __restrict__ sub,
+                                                              const Tw* __restrict__ inv,
+                                                              const Tw* __restrict__ cp, Tdst* dst,
+                                                              Tw sign) {
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    Tw* t = reinterpret_cast<Tw*>(tile_raw);   // [m][33]
+    constexpr bool REG = sizeof(Tw) * E <= 72;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k0 = lane * E;
+    Tw ts[E], ti[E], tc[E];
+    if constexpr (REG) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int g = k0 + k;
+            ts[k] = g < m ? sub[g] : Tw(0);
+            ti[k] = g < m ? inv[g] : Tw(0);
+            tc[k] = g < m ? cp[g] : Tw(0);
+        }
+    }
+    auto SUB = [&](int k) -> Tw { if constexpr (REG) return ts[k]; else return sub[k0 + k]; };
+    auto INV = [&](int k) -> Tw { if constexpr (REG) return ti[k]; else return inv[k0 + k]; };
+    auto CP = [&](int k) -> Tw { if constexpr (REG) return tc[k]; else return cp[k0 + k]; };
+    const int64_t ntx = (stride + 31) / 32;
+    const int64_t ntiles = outer_n * ntx;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t outer = tile / ntx;
+        const int64_t inner0 = (tile - outer * ntx) * 32;
+        const int nl = (int)(stride - inner0 < 32 ? stride - inner0 : 32);   // lines in the tile
+        const int64_t off = outer * m * stride + inner0;
+        Tw* base = x + off;
+        // asynchronous element copies: every row of the tile is in flight at once
+        for (int k = wid; k < m; k += ST_WARPS) {
+            Tw* dstp = &t[k * 33 + lane];
+            if (lane < nl) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dstp);
+                const Tw* src = base + (int64_t)k * stride + lane;
+                if (sizeof(Tw) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+            } else {
+                *dstp = Tw(0);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        for (int l = wid; l < nl; l += ST_WARPS) {
             Tw v[E];
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const int g = k0 + k;
-                v[k] = (valid && g < m) ? base[(int64_t)g * stride] : Tw(0);
-            }
+            for (int k = 0; k < E; ++k) v[k] = k0 + k < m ? t[(k0 + k) * 33 + l] : Tw(0);
             Tw A = Tw(1), B = Tw(0);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int g = k0 + k;
-                if (g < m) {
-                    const Tw al = -sub[g] * inv[g];
+                if (k0 + k < m) {
+                    const Tw al = -SUB(k) * INV(k);
                     A = al * A;
-                    B = al * B + v[k] * inv[g];
+                    B = al * B + v[k] * INV(k);
                 }
             }
-            sA[seg][lane] = A;
-            sB[seg][lane] = B;
-            __syncthreads();
-            Tw y = Tw(0);
-            for (int s2 = 0; s2 < seg; ++s2) y = sA[s2][lane] * y + sB[s2][lane];
-            __syncthreads();
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const Tw pa = __shfl_up_sync(0xffffffffu, A, o), pb = __shfl_up_sync(0xffffffffu, B, o);
+                if (lane >= o) {
+                    B = A * pb + B;
+                    A = A * pa;
+                }
+            }
+            Tw y = __shfl_up_sync(0xffffffffu, B, 1);
+            if (lane == 0) y = Tw(0);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int g = k0 + k;
-                if (g < m) {
-                    y = (v[k] - sub[g] * y) * inv[g];
+                if (k0 + k < m) {
+                    y = (v[k] - SUB(k) * y) * INV(k);
                     v[k] = y;
                 }
             }
@@ -242,39 +279,44 @@ __global__ void __launch_bounds__(1024) k_solve_seg(Tw* x, int64_t outer_n, int 
             B = Tw(0);
 #pragma unroll
             for (int k = E - 1; k >= 0; --k) {
-                const int g = k0 + k;
-                if (g < m) {
-                    const Tw ga = -cp[g];
+                if (k0 + k < m) {
+                    const Tw ga = -CP(k);
                     A = ga * A;
                     B = ga * B + v[k];
                 }
             }
-            sA[seg][lane] = A;
-            sB[seg][lane] = B;
-            __syncthreads();
-            Tw xx = Tw(0);
-            for (int s2 = S - 1; s2 > seg; --s2) xx = sA[s2][lane] * xx + sB[s2][lane];
-            __syncthreads();
 #pragma unroll
-            for (int k = E - 1; k >= 0; --k) {
-                const int g = k0 + k;
-                if (g < m) {
-                    xx = v[k] - cp[g] * xx;
-                    v[k] = xx;
+            for (int o = 1; o < 32; o <<= 1) {
+                const Tw pa = __shfl_down_sync(0xffffffffu, A, o), pb = __shfl_down_sync(0xffffffffu, B, o);
+                if (lane + o < 32) {
+                    B = A * pb + B;
+                    A = A * pa;
                 }
             }
-            if (valid) {
-                Tdst* d = dst ? dst + outer * m * stride + inner : nullptr;
+            Tw xx = __shfl_down_sync(0xffffffffu, B, 1);
+            if (lane == 31) xx = Tw(0);
 #pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const int g = k0 + k;
-                    if (g < m) {
-                        if (d) d[(int64_t)g * stride] = (Tdst)((Tw)d[(int64_t)g * stride] + sign * v[k]);
-                        else base[(int64_t)g * stride] = v[k];
-                    }
+            for (int k = E - 1; k >= 0; --k) {
+                if (k0 + k < m) {
+                    xx = v[k] - CP(k) * xx;
+                    t[(k0 + k) * 33 + l] = xx;
                 }
             }
         }
+        __syncthreads();
+        if (lane < nl) {
+            if (dst) {
+                Tdst* d = dst + off;
+                for (int k = wid; k < m; k += ST_WARPS) {
+                    const int64_t i = (int64_t)k * stride + lane;
+                    d[i] = (Tdst)((Tw)d[i] + sign * t[k * 33 + lane]);
+                }
+            } else {
+                for (int k = wid; k < m; k += ST_WARPS) base[(int64_t)k * stride + lane] = t[k * 33 + lane];
+            }
+        }
+        __syncthreads();   // the next tile overwrites t
+    }
 }
 
 // Lines along the contiguous axis, one warp per line held in registers: lane
@@ -283,7 +325,12 @@ __global__ void __launch_bounds__(1024) k_solve_seg(Tw* x, int64_t outer_n, int 
 // x_{k+1} + y_k backward), so each lane composes the maps of its segment,
 // the warp scans the compositions with shuffles, and each lane replays its
 // segment from the scanned input.  Global traffic goes through a padded
-// per-warp shared buffer so loads and stores stay coalesced.
+// per-warp shared buffer so loads and stores stay coalesced.  E is odd
+// (conflict-free segment reads) and the smallest with 32E >= m, so lines of
+// 2^k + 1 nodes keep nearly every lane busy.  A lane's Thomas factors are
+// the same for every line: they stay in registers (in shared memory for the
+// widest segments), and the next line's loads are issued before the current
+// line is solved.
 constexpr int SW_WARPS = 4;
 
 template <typename Tw, typename Tdst, int E>
@@ -293,15 +340,63 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
                                                               const Tw* __restrict__ cp, Tdst* dst,
                                                               Tw sign) {
     constexpr int W = E + 1;
+    constexpr bool REG = sizeof(Tw) * E <= 72;
     __shared__ Tw buf[SW_WARPS][32 * W];
+    __shared__ Tw tab[3][REG ? 1 : 32 * E];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Tw* sb = buf[wid];
     const int k0 = lane * E;
-    for (int64_t ln = (int64_t)blockIdx.x * SW_WARPS + wid; ln < lines;
-         ln += (int64_t)gridDim.x * SW_WARPS) {
-        Tw* row = x + ln * m;
-        for (int e = lane; e < 32 * E; e += 32) sb[(e / E) * W + e % E] = e < m ? row[e] : Tw(0);
+    Tw ts[REG ? E : 1], ti[REG ? E : 1], tc[REG ? E : 1];
+    if constexpr (REG) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int g = k0 + k;
+            ts[k] = g < m ? sub[g] : Tw(0);
+            ti[k] = g < m ? inv[g] : Tw(0);
+            tc[k] = g < m ? cp[g] : Tw(0);
+        }
+    } else {
+        for (int g = threadIdx.x; g < 32 * E; g += blockDim.x) {
+            tab[0][g] = g < m ? sub[g] : Tw(0);
+            tab[1][g] = g < m ? inv[g] : Tw(0);
+            tab[2][g] = g < m ? cp[g] : Tw(0);
+        }
+        __syncthreads();
+    }
+    auto SUB = [&](int k) -> Tw { if constexpr (REG) return ts[k]; else return tab[0][k0 + k]; };
+    auto INV = [&](int k) -> Tw { if constexpr (REG) return ti[k]; else return tab[1][k0 + k]; };
+    auto CP = [&](int k) -> Tw { if constexpr (REG) return tc[k]; else return tab[2][k0 + k]; };
+
+    const int64_t step = (int64_t)gridDim.x * SW_WARPS;
+    int64_t ln = (int64_t)blockIdx.x * SW_WARPS + wid;
+    // row element e = lane + 32 j (j < E, so 32E >= m covers the row)
+    Tw nv[E];
+    auto load_row = [&](int64_t l) {
+        const Tw* row = x + l * m;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int e = lane + 32 * j;
+            nv[j] = (l < lines && e < m) ? row[e] : Tw(0);
+        }
+    };
+    load_row(ln);
+    for (; ln < lines; ln += step) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int e = lane + 32 * j;
+            sb[(e / E) * W + e % E] = nv[j];
+        }
         __syncwarp();
+        Tdst* d = dst ? dst + ln * m : nullptr;
+        Tdst dv[E];
+        if (d) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int e = lane + 32 * j;
+                dv[j] = e < m ? d[e] : Tdst(0);
+            }
+        }
+        load_row(ln + step);   // in flight while this line is solved
         Tw v[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) v[k] = sb[lane * W + k];
@@ -309,11 +404,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
         Tw A = Tw(1), B = Tw(0);
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-            const int g = k0 + k;
-            if (g < m) {
-                const Tw al = -sub[g] * inv[g];
+            if (k0 + k < m) {
+                const Tw al = -SUB(k) * INV(k);
                 A = al * A;
-                B = al * B + v[k] * inv[g];
+                B = al * B + v[k] * INV(k);
             }
         }
 #pragma unroll
@@ -328,9 +422,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
         if (lane == 0) y = Tw(0);
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-            const int g = k0 + k;
-            if (g < m) {
-                y = (v[k] - sub[g] * y) * inv[g];
+            if (k0 + k < m) {
+                y = (v[k] - SUB(k) * y) * INV(k);
                 v[k] = y;
             }
         }
@@ -339,9 +432,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
         B = Tw(0);
 #pragma unroll
         for (int k = E - 1; k >= 0; --k) {
-            const int g = k0 + k;
-            if (g < m) {
-                const Tw ga = -cp[g];
+            if (k0 + k < m) {
+                const Tw ga = -CP(k);
                 A = ga * A;
                 B = ga * B + v[k];
             }
@@ -358,20 +450,22 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
         if (lane == 31) xx = Tw(0);
 #pragma unroll
         for (int k = E - 1; k >= 0; --k) {
-            const int g = k0 + k;
-            if (g < m) {
-                xx = v[k] - cp[g] * xx;
+            if (k0 + k < m) {
+                xx = v[k] - CP(k) * xx;
                 v[k] = xx;
             }
         }
 #pragma unroll
         for (int k = 0; k < E; ++k) sb[lane * W + k] = v[k];
         __syncwarp();
-        if (dst) {
-            Tdst* d = dst + ln * m;
-            for (int e = lane; e < m; e += 32) d[e] = (Tdst)((Tw)d[e] + sign * sb[(e / E) * W + e % E]);
-        } else {
-            for (int e = lane; e < m; e += 32) row[e] = sb[(e / E) * W + e % E];
+        Tw* row = x + ln * m;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int e = lane + 32 * j;
+            if (e >= m) continue;
+            const Tw r = sb[(e / E) * W + e % E];
+            if (d) d[e] = (Tdst)((Tw)dv[j] + sign * r);
+            else row[e] = r;
         }
         __syncwarp();
     }
@@ -606,11 +700,11 @@ bool level_uses_fp64(const Plan& p, int l) {
 
 template <typename T>
 mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1, T sign,
-                     cudaStream_t st, int64_t zoff = -1) {
+                     cudaStream_t st, int64_t zoff = -1, bool x_done = false) {
     const bool f64 = level_uses_fp64<T>(p, l);
     if (rows3_ok(p)) {
-        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st, zoff);
-        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st, zoff);
+        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done);
+        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done);
     }
     if (f64) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
     return correct_level<T, T>(p, l, z, coarse, t0, t1, sign, st);
@@ -655,22 +749,48 @@ cudaMemPool_t workspace_pool() {
     return pool;
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory (beyond the default
+// 48 KB), once per kernel and device.
+mgard_status allow_dynamic_smem(const void* kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return MGARD_OK;
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{kern, dev}];
+    if (have < bytes) {
+        MGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        have = bytes;
+    }
+    return MGARD_OK;
+}
+
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
                            const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
-    // segments of E elements, at most 32 per line (1024-thread blocks); E
-    // stays small enough that a segment and its factors fit in registers
-    const int E = (sizeof(Tw) == 4 && m > 256) ? 16 : 8;
-    if (m <= 32 * E && stride > 1) {
-        const int S = (int)((m + E - 1) / E);
-        dim3 grid((unsigned)std::min<int64_t>((stride + 31) / 32, 1LL << 30),
-                  (unsigned)std::min<int64_t>(outer, 65535), 1);
-        if (E == 8)
-            MGB_LAUNCH("k_solve_seg", st, k_solve_seg<Tw, Tdst, 8><<<grid, 32 * S, 0, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
-        else
-            MGB_LAUNCH("k_solve_seg", st, k_solve_seg<Tw, Tdst, 16><<<grid, 32 * S, 0, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
-        MGB_CUDA(cudaGetLastError());
-        return MGARD_OK;
+    // tiles of 32 lines in shared memory while a tile fits
+    const size_t tile_bytes = (size_t)m * 33 * sizeof(Tw);
+    if (stride > 1 && m <= 1056 && tile_bytes <= 200 * 1024) {
+        const int64_t ntiles = outer * ((stride + 31) / 32);
+        const int grid = (int)std::min<int64_t>(ntiles, 148LL * 4);
+        bool launched = false;
+        auto go = [&](auto kern) -> mgard_status {
+            MGB_TRY(allow_dynamic_smem((const void*)kern, tile_bytes));
+            MGB_LAUNCH("k_solve_tile", st, kern<<<grid, ST_WARPS * 32, tile_bytes, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
+            launched = true;
+            return MGARD_OK;
+        };
+        if (m <= 32) MGB_TRY(go(k_solve_tile<Tw, Tdst, 1>));
+        else if (m <= 96) MGB_TRY(go(k_solve_tile<Tw, Tdst, 3>));
+        else if (m <= 160) MGB_TRY(go(k_solve_tile<Tw, Tdst, 5>));
+        else if (m <= 288) MGB_TRY(go(k_solve_tile<Tw, Tdst, 9>));
+        else if (m <= 544) MGB_TRY(go(k_solve_tile<Tw, Tdst, 17>));
+        else MGB_TRY(go(k_solve_tile<Tw, Tdst, 33>));
+        if (launched) {
+            MGB_CUDA(cudaGetLastError());
+            return MGARD_OK;
+        }
     }
     const int bx = 128;
     dim3 grid((unsigned)std::min<int64_t>((stride + bx - 1) / bx, 1LL << 30),
@@ -687,16 +807,25 @@ mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, co
                               const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>((lines + SW_WARPS - 1) / SW_WARPS, 148LL * 16);
     const int bs = SW_WARPS * 32;
-    if (m <= 256) {
-        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 8><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
-    } else if (m <= 512) {
-        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 16><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
-    } else if (m <= 1024) {
-        MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, 32><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign));
-    } else {
+#define MGB_SOLVE_WARP(EV) \
+    MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, EV><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign))
+    if (m <= 32) MGB_SOLVE_WARP(1);
+    else if (m <= 96) MGB_SOLVE_WARP(3);
+    else if (m <= 160) MGB_SOLVE_WARP(5);
+    else if (m <= 288) MGB_SOLVE_WARP(9);
+    else if (m <= 544) MGB_SOLVE_WARP(17);
+    else {
+        bool done = false;
+        if constexpr (sizeof(Tw) == 4) {   // double tables of this width would pass 48 KB
+            if (m <= 1056) {
+                MGB_SOLVE_WARP(33);
+                done = true;
+            }
+        }
         // long lines: one thread per line in global memory
-        return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
+        if (!done) return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
     }
+#undef MGB_SOLVE_WARP
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -825,15 +954,18 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         const int64_t zoff = zs ? p.offset[l] : -1;
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
         if (Epart) MGB_TRY(mass_norm2_partials<T>(p, l, src, Epart + energy_parts_offset(p, l), st));
+        bool x_done = false;   // the coefficient kernel restricted along x into temp0
         if (rows3_ok(p)) {
-            MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st, zoff));
+            MGB_TRY(rows3_coeff<T>(p, l, src, dst, py.lv[l - 1], st, zoff, py.temp0.p,
+                                   level_uses_fp64<T>(p, l), &x_done));
         } else {
             MGB_LAUNCH("k_coeff_gather", st,
                        k_coeff_gather<T><<<grid3(p.level<T>(l).n, 128), 128, 0, st>>>(
                            src, dst, py.lv[l - 1], p.level<T>(l)));
             MGB_CUDA(cudaGetLastError());
         }
-        MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st, zoff));
+        MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st, zoff,
+                           x_done));
     }
     const T* u0 = p.L ? py.lv[0] : in;
     if (E) MGB_TRY(mass_norm2<T>(p, 0, u0, &E[0], st));

@@ -179,11 +179,48 @@ __device__ inline void prefetch_l2(const void* p, size_t bytes) {
          r += (int64_t)gridDim.x * WPB)
 
 // -- coefficients (decomposition step 1) --------------------------------------
+// The x restriction of one fine row at coarse index J: the five-tap window
+// of P^T M_l around fine 2J (uniform weights rwi for J in [rlo, rhi), else
+// the table rw[J*5 ..]), with fetch(ip) giving z at fine x = ip.  On rows of
+// the coarser grid (rowc) z vanishes at coarse x positions: in the uniform
+// window those are the even taps, elsewhere they are skipped.
+template <typename Tout, typename F>
+__device__ inline Tout restrict_row_at(int J, int nx, int ncx, bool rowc, const Tout wi[5],
+                                       int rlo, int rhi, const Tout* __restrict__ rw, F fetch) {
+    if (J >= rlo && J < rhi) {
+        const Tout e0 = rowc ? Tout(0) : fetch(2 * J - 2);
+        const Tout e1 = fetch(2 * J - 1);
+        const Tout e2 = rowc ? Tout(0) : fetch(2 * J);
+        const Tout e3 = fetch(2 * J + 1);
+        const Tout e4 = rowc ? Tout(0) : fetch(2 * J + 2);
+        Tout a = wi[0] * e0;
+        a += wi[1] * e1;
+        a += wi[2] * e2;
+        a += wi[3] * e3;
+        a += wi[4] * e4;
+        return a;
+    }
+    const int f = restrict_center(J, nx, ncx);
+    Tout acc = Tout(0);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int ip = f - 2 + t;
+        if (ip < 0 || ip >= nx) continue;
+        if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
+        acc += rw[J * 5 + t] * fetch(ip);
+    }
+    return acc;
+}
+
 // STAGE: as in the fill kernel, the source rows are combined along y and z
-// at the coarse x positions into a shared-memory row R first.
-template <typename T, int U, bool ZS, bool STAGE>
+// at the coarse x positions into a shared-memory row R first.  RX: the row's
+// coefficients are also kept in shared memory (zero at coarse nodes of the
+// coarser grid's rows) and restricted along x into rx (rows of ncx values in
+// Tw), the first step of the coarse-grid correction.
+template <typename T, int U, bool ZS, bool STAGE, bool RX, typename Tw>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
-                                               Level<T> lv, int64_t zoff) {
+                                               Level<T> lv, int64_t zoff, Tw* __restrict__ rx,
+                                               AxisT<Tw> axw) {
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
@@ -209,7 +246,8 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const T* urow = in + r * nx;
         T* orow = ZS ? out + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
-        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ncx;
+        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ((STAGE ? ncx : 0) + (RX ? nx : 0));
+        T* Z = R + (STAGE ? ncx : 0);
         if (STAGE) {
             // coarse node J sits at fine x = 2J, the last one at nx - 1
             for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, min(2 * j, nx - 1));
@@ -243,11 +281,27 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
             for (int j = 0; j < U; ++j) {
                 const int x = x0 + 32 * j;
                 if (x >= nx) continue;
-                if (rowc && is_coarse(x, nx)) crow[coarse_index(x, nx, ncx)] = u[j];
-                else orow[(ZS && rowc) ? x - coarse_before(x) : x] = u[j] - acc[j];
+                if (rowc && is_coarse(x, nx)) {
+                    crow[coarse_index(x, nx, ncx)] = u[j];
+                    if (RX) Z[x] = T(0);
+                } else {
+                    const T c = u[j] - acc[j];
+                    orow[(ZS && rowc) ? x - coarse_before(x) : x] = c;
+                    if (RX) Z[x] = c;
+                }
             }
         }
-        if (STAGE) __syncwarp();   // R is rewritten by the warp's next row
+        if (RX) {
+            __syncwarp();
+            Tw wi[5];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) wi[t] = axw.rwi[t];
+            Tw* xrow = rx + r * ncx;
+            for (int J = lane; J < ncx; J += 32)
+                xrow[J] = restrict_row_at<Tw>(J, nx, ncx, rowc, wi, axw.rlo, axw.rhi, axw.rw,
+                                              [&](int ip) { return (Tw)Z[ip]; });
+        }
+        if (STAGE || RX) __syncwarp();   // R and Z are rewritten by the warp's next row
     }
 }
 
@@ -347,38 +401,9 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                 const int J = J0 + 32 * j;
                 acc[j] = Tout(0);
                 if (J >= ncx) continue;
-                if (J >= rlo && J < rhi) {
-                    // uniform window 2J-2 .. 2J+2; on coarse rows the even taps
-                    // are coarse nodes, where z = 0
-                    Tout e0, e1, e2, e3, e4;
-                    if (ZS && rowc) {   // odd taps 2J-1, 2J+1 at J-1, J
-                        e0 = e2 = e4 = Tout(0);
-                        e1 = (Tout)irow[J - 1];
-                        e3 = (Tout)irow[J];
-                    } else {
-                        const Tin* q = irow + 2 * J - 2;
-                        e0 = rowc ? Tout(0) : (Tout)q[0];
-                        e1 = (Tout)q[1];
-                        e2 = rowc ? Tout(0) : (Tout)q[2];
-                        e3 = (Tout)q[3];
-                        e4 = rowc ? Tout(0) : (Tout)q[4];
-                    }
-                    Tout a = wi[0] * e0;
-                    a += wi[1] * e1;
-                    a += wi[2] * e2;
-                    a += wi[3] * e3;
-                    a += wi[4] * e4;
-                    acc[j] = a;
-                    continue;
-                }
-                const int f = restrict_center(J, nx, ncx);
-#pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    const int ip = f - 2 + t;
-                    if (ip < 0 || ip >= nx) continue;
-                    if (rowc && is_coarse(ip, nx)) continue;   // coarse node: z = 0 (not read)
-                    acc[j] += rw[J * 5 + t] * (Tout)irow[sh ? (ip - 1) >> 1 : ip];
-                }
+                acc[j] = restrict_row_at<Tout>(J, nx, ncx, rowc, wi, rlo, rhi, rw, [&](int ip) {
+                    return (Tout)irow[sh ? (ip - 1) >> 1 : ip];
+                });
             }
 #pragma unroll
             for (int j = 0; j < U; ++j)
@@ -705,21 +730,41 @@ size_t stage_bytes(const Level<T>& lv, const RowCfg& c) {
 
 template <typename T>
 mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st,
-                         int64_t zoff) {
+                         int64_t zoff, void* rx, bool rx_f64, bool* fused) {
     const Level<T>& lv = p.level<T>(l);
     const RowCfg c = p.row_cfg(l, RK_COEFF);
     const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
     const size_t sm = stage_bytes<T>(lv, c);
+    // the fused x restriction keeps the row's coefficients beside the staged row
+    const size_t smx = sm + (size_t)WPB * (size_t)lv.n[3] * sizeof(T);
+    const bool fuse = rx && sm && smx <= 48 * 1024;
+    if (fused) *fused = fuse;
     with_cfg(c, lv.n[3], false, [&](auto u) {
         constexpr int U = decltype(u)::value;
+        const int64_t zo = zoff >= 0 ? zoff : 0;
+        if (fuse) {
+            auto go = [&](auto tw) {
+                using Tw = decltype(tw);
+                Tw* x = (Tw*)rx;
+                const AxisT<Tw> ax = p.level<Tw>(l).ax[3];
+                if (zoff >= 0)
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                else
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+            };
+            if (rx_f64) go(double(0));
+            else go(T(0));
+            return;
+        }
+        const AxisT<T> none{};
         if (zoff >= 0 && sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true><<<g, RT, sm, st>>>(in, out, coarse, lv, zoff));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
         else if (zoff >= 0)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false><<<g, RT, 0, st>>>(in, out, coarse, lv, zoff));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false, false, T><<<g, RT, 0, st>>>(in, out, coarse, lv, zo, nullptr, none));
         else if (sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true><<<g, RT, sm, st>>>(in, out, coarse, lv, 0));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
         else
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false, false, T><<<g, RT, 0, st>>>(in, out, coarse, lv, 0, nullptr, none));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -749,7 +794,7 @@ mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* ou
 
 template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
-                           T sign, cudaStream_t st, int64_t zoff) {
+                           T sign, cudaStream_t st, int64_t zoff, bool x_done) {
     const Level<Tw>& lw = p.level<Tw>(l);
     const Level<T>& lt = p.level<T>(l);
     const int nz = (int)lt.n[1], ny = (int)lt.n[2], nx = (int)lt.n[3];
@@ -759,7 +804,7 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     // x (always active)
     const RowCfg cx = p.row_cfg(l, RK_RX), cr = p.row_cfg(l, RK_RROWS);
     const int gx = row_grid((int64_t)nz * ny, cx.bpsm);
-    with_cfg(cx, ncx, true, [&](auto u) {
+    if (!x_done) with_cfg(cx, ncx, true, [&](auto u) {
         if (zoff >= 0)
             MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value, true><<<gx, RT, 0, st>>>(
                 z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], zoff));
@@ -839,7 +884,7 @@ mgard_status rows3_dequantize(const Plan& p, int l, const uint16_t* sym, const i
 
 #define INST(T)                                                                                  \
     template mgard_status rows3_coeff<T>(const Plan&, int, const T*, T*, T*, cudaStream_t,      \
-                                         int64_t);                                              \
+                                         int64_t, void*, bool, bool*);                          \
     template mgard_status rows3_fill<T>(const Plan&, int, const T*, const T*, T*, cudaStream_t,  \
                                         int64_t);                                               \
     template mgard_status rows3_mass_norm<T>(const Plan&, int, const T*, double*, cudaStream_t); \
@@ -852,10 +897,10 @@ INST(float)
 INST(double)
 #undef INST
 template mgard_status rows3_correct<float, float>(const Plan&, int, const float*, float*, void*,
-                                                  void*, float, cudaStream_t, int64_t);
+                                                  void*, float, cudaStream_t, int64_t, bool);
 template mgard_status rows3_correct<float, double>(const Plan&, int, const float*, float*, void*,
-                                                  void*, float, cudaStream_t, int64_t);
+                                                  void*, float, cudaStream_t, int64_t, bool);
 template mgard_status rows3_correct<double, double>(const Plan&, int, const double*, double*,
-                                                    void*, void*, double, cudaStream_t, int64_t);
+                                                    void*, void*, double, cudaStream_t, int64_t, bool);
 
 }  // namespace mgb

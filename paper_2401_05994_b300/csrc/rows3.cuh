@@ -20,16 +20,21 @@ inline bool rows3_ok(const Plan& p) {
 // to) an array in symbol order, starting at symbol offset zoff: the nodes new
 // on the level in row-major order (see zs_row_base); otherwise they sit in
 // the level's own row-major array.
+// With rx set, the kernel may also restrict the coefficients along x into
+// rx (the first step of rows3_correct, in double when rx_f64, else in T);
+// *fused reports whether it did (the launch shape needs staged rows that fit).
 template <typename T>
 mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, cudaStream_t st,
-                         int64_t zoff = -1);
+                         int64_t zoff = -1, void* rx = nullptr, bool rx_f64 = false,
+                         bool* fused = nullptr);
 template <typename T>
 mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* out,
                         cudaStream_t st, int64_t zoff = -1);
 // coarse += sign * M_{l-1}^{-1} P^T M_l z (restriction x, y, z; solves z, y, x)
+// x_done: t0 already holds the restriction along x (from rows3_coeff).
 template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
-                           T sign, cudaStream_t st, int64_t zoff = -1);
+                           T sign, cudaStream_t st, int64_t zoff = -1, bool x_done = false);
 template <typename T>
 mgard_status rows3_quantize(const Plan& p, int l, const T* c, const double* w, uint16_t* sym,
                             int32_t* esc, unsigned long long* hist, unsigned* status,

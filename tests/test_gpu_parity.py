@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda"
 
 SHAPES = [(1000,), (9,), (129, 129), (33, 20), (47, 65, 33), (17, 17, 17), (9, 6, 5, 7),
-          (1, 40, 1, 27), (7, 2), (1,), (3, 3, 3)]
+          (1, 40, 1, 27), (7, 2), (1,), (3, 3, 3), (2000,), (5, 1100)]
 
 
 def _field(shape, dtype, seed=0):
