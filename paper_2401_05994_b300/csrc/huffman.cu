@@ -539,7 +539,12 @@ constexpr int PACK_WARPS = 6;   // 45 KB of static shared memory per block
 // [8j, 8j+8) of the round (one 16-byte load).  Lane bit offsets come from a
 // warp scan; bits accumulate MSB-first in a 64-bit register and the words a
 // lane shares with its neighbours (its first and last) are merged with OR in
-// a shared-memory copy of the chunk.
+// a shared-memory copy of the chunk.  COMPACT: escape values arrive
+// compacted per sub-chunk (escapes[s * SUB + r], as the streaming quantizer
+// writes them) and each round copies its run to the outlier section with
+// coalesced accesses; otherwise escapes[] is indexed by symbol position and
+// gathered.
+template <bool COMPACT>
 __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     const uint16_t* __restrict__ sym, uint64_t n, const uint8_t* __restrict__ lengths,
     const uint32_t* __restrict__ codes, const uint64_t* __restrict__ word_off,
@@ -621,8 +626,12 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             }
             const unsigned bpos = bit0 + ib - bits;
             unsigned epos = esc0 + ie - esc;
+            const unsigned rtot = __shfl_sync(0xffffffffu, ie, 31);   // escapes of the round
+            if (COMPACT)
+                for (unsigned k = lane; k < rtot; k += 32)
+                    outliers[eo + esc0 + k] = escapes[cbase + rd * SUB + k];
             bit0 += __shfl_sync(0xffffffffu, ib, 31);
-            esc0 += __shfl_sync(0xffffffffu, ie, 31);
+            esc0 += rtot;
             unsigned w = bpos >> 5;
             int nb = (int)(bpos & 31);
             unsigned long long acc = 0;
@@ -642,7 +651,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                         nb -= 32;
                         acc &= (nb ? ((1ull << nb) - 1) : 0ull);
                     }
-                    if (s == MGARD_ESC) {
+                    if (!COMPACT && s == MGARD_ESC) {
                         if (pend_at >= 0) outliers[pend_at] = pend_v;
                         pend_at = (int64_t)(eo + epos++);
                         pend_v = escapes[cbase + first + k];
@@ -651,7 +660,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
             __syncwarp();
         }
-        if (pend_at >= 0) outliers[pend_at] = pend_v;
+        if (!COMPACT && pend_at >= 0) outliers[pend_at] = pend_v;
         __syncwarp();
         if (__all_sync(0xffffffffu, fill)) {   // stored without words; offsets 0
             if (lane < SUBREC) sub_off[c * SUBREC + lane] = 0;
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
 
 // -- decoding ------------------------------------------------------------------
 constexpr int DEC_THREADS = 256;
-constexpr int DEC_BLOCKS_PER_SM = 6;   // 33 KB of tables per block
+constexpr int DEC_BLOCKS_PER_SM = 5;   // 33 KB of tables per block; registers capped to fit 5
 
 // Decoding: one thread per sub-chunk of SUB symbols, in a grid that stays
 // resident (each block copies the prefix table once).  The bit window is a
@@ -689,7 +698,7 @@ __device__ inline void store8(uint16_t*, const uint16_t*) {}
 // symbol position).  OutT = float or double: the dequantized coefficient of
 // every symbol to `vals` (symbol order), with the widths of DeqArgs.
 template <typename OutT>
-__global__ void __launch_bounds__(DEC_THREADS) k_decode(
+__global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
     const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
     const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
     const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
@@ -938,11 +947,16 @@ mgard_status huffman_count(const uint16_t* sym, uint64_t n, const uint8_t* lengt
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
                           const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
-                          int32_t* outliers, cudaStream_t st, PackGuard guard) {
+                          int32_t* outliers, cudaStream_t st, PackGuard guard, bool compact) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    MGB_LAUNCH("k_pack", st, k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
-        sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
+    const int grid = grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8);
+    if (compact)
+        MGB_LAUNCH("k_pack", st, k_pack<true><<<grid, PACK_WARPS * 32, 0, st>>>(
+            sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
+    else
+        MGB_LAUNCH("k_pack", st, k_pack<false><<<grid, PACK_WARPS * 32, 0, st>>>(
+            sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -1089,7 +1103,7 @@ extern "C" mgard_status mgard_huffman_encode_noalloc(
     MGB_LAUNCH("k_tables", st, k_tables<<<1, CB_THREADS, 0, st>>>(lengths, sc->codes, &sc->dt));
     if (nchunks)
         MGB_LAUNCH("k_pack", st,
-                   k_pack<<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
+                   k_pack<false><<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
                        symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, sub_off,
                        outliers, nchunks, PackGuard()));
     MGB_CUDA(cudaGetLastError());

@@ -52,11 +52,14 @@ struct PackGuard {
     const unsigned* status = nullptr;
     const unsigned long long* words_byte_off = nullptr;
 };
-// Pass 2: pack codes, record sub-chunk offsets and gather escapes.
+// Pass 2: pack codes, record sub-chunk offsets and gather escapes.  The
+// escape values are indexed by symbol position, or with `compact` stored per
+// sub-chunk in order (escapes[s * 256 + r] for the r-th escape of sub-chunk s).
 mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* lengths,
                           const uint32_t* codes, const uint64_t* word_off, const uint64_t* esc_off,
                           const int32_t* escapes, uint32_t* words, uint16_t* sub_off,
-                          int32_t* outliers, cudaStream_t st, PackGuard guard = PackGuard());
+                          int32_t* outliers, cudaStream_t st, PackGuard guard = PackGuard(),
+                          bool compact = false);
 // Widths for decoding straight to dequantized values: level l's symbols
 // [lo.off[l], lo.off[l+1]) dequantize with w[l] (wf[l] = float(w[l])).
 struct DeqArgs {

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "multilevel.cuh"
 #include "rows3.cuh"
@@ -187,9 +188,99 @@ __global__ void k_solve_lines(Tw* x, int64_t outer_n, int64_t m, int64_t stride,
         }
 }
 
-// Lines along a strided axis, 32 adjacent lines (consecutive inner
-// positions) per tile.  The block copies the tile, m rows of 32 elements
-// each read as one coalesced warp access, into shared memory (row pitch 33),
+// One line solved by a warp: lane j holds elements [k0, k0+E) of the line
+// (k0 = jE) in v and replaces them with the solution of the tridiagonal
+// system.  Both Thomas sweeps are first-order affine recurrences (y_k =
+// alpha_k y_{k-1} + beta_k forward, x_k = gamma_k x_{k+1} + y_k backward),
+// so each lane composes the maps of its segment, the warp scans the
+// compositions with shuffles, and each lane replays its segment from the
+// scanned input.  SUB/INV/CP(k) give the factors of element k0 + k.
+template <typename Tw, int E, typename FS, typename FI, typename FC>
+__device__ inline void warp_thomas(Tw (&v)[E], int k0, int m, int lane, FS SUB, FI INV, FC CP) {
+    Tw A = Tw(1), B = Tw(0);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if (k0 + k < m) {
+            const Tw al = -SUB(k) * INV(k);
+            A = al * A;
+            B = al * B + v[k] * INV(k);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Tw pa = __shfl_up_sync(0xffffffffu, A, o), pb = __shfl_up_sync(0xffffffffu, B, o);
+        if (lane >= o) {
+            B = A * pb + B;
+            A = A * pa;
+        }
+    }
+    Tw y = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) y = Tw(0);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if (k0 + k < m) {
+            y = (v[k] - SUB(k) * y) * INV(k);
+            v[k] = y;
+        }
+    }
+    A = Tw(1);
+    B = Tw(0);
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+        if (k0 + k < m) {
+            const Tw ga = -CP(k);
+            A = ga * A;
+            B = ga * B + v[k];
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Tw pa = __shfl_down_sync(0xffffffffu, A, o), pb = __shfl_down_sync(0xffffffffu, B, o);
+        if (lane + o < 32) {
+            B = A * pb + B;
+            A = A * pa;
+        }
+    }
+    Tw xx = __shfl_down_sync(0xffffffffu, B, 1);
+    if (lane == 31) xx = Tw(0);
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+        if (k0 + k < m) {
+            xx = v[k] - CP(k) * xx;
+            v[k] = xx;
+        }
+    }
+}
+
+// A lane's Thomas factors for elements [k0, k0+E) of lines of m nodes, in
+// registers when they are few (REG), else read from global memory.
+template <typename Tw, int E, bool REG_ = (sizeof(Tw) * E <= 72)>
+struct LaneFactors {
+    static constexpr bool REG = REG_;
+    Tw s[REG ? E : 1], i[REG ? E : 1], c[REG ? E : 1];
+    const Tw *gs, *gi, *gc;
+    int k0;
+    __device__ LaneFactors(const Tw* sub, const Tw* inv, const Tw* cp, int k0_, int m)
+        : gs(sub), gi(inv), gc(cp), k0(k0_) {
+        if constexpr (REG) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int g = k0 + k;
+                s[k] = g < m ? sub[g] : Tw(0);
+                i[k] = g < m ? inv[g] : Tw(0);
+                c[k] = g < m ? cp[g] : Tw(0);
+            }
+        }
+    }
+    __device__ Tw SUB(int k) const { if constexpr (REG) return s[k]; else return gs[k0 + k]; }
+    __device__ Tw INV(int k) const { if constexpr (REG) return i[k]; else return gi[k0 + k]; }
+    __device__ Tw CP(int k) const { if constexpr (REG) return c[k]; else return gc[k0 + k]; }
+};
+
+// Lines along a strided axis, 32 consecutive lines (in (outer, inner)
+// order) per tile.  The block copies the tile, m rows of 32 elements each
+// read as one warp access (coalesced within an outer index), into shared
+// memory (row pitch 33),
 // every warp solves lines of the tile with the warp-scan scheme of
 // k_solve_warp (lane j owns elements [jE, jE+E) of the line; E odd, so the
 // column reads are free of bank conflicts), and the block writes the tile
@@ -205,36 +296,26 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
                                                               Tw sign) {
     extern __shared__ __align__(16) unsigned char tile_raw[];
     Tw* t = reinterpret_cast<Tw*>(tile_raw);   // [m][33]
-    constexpr bool REG = sizeof(Tw) * E <= 72;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k0 = lane * E;
-    Tw ts[E], ti[E], tc[E];
-    if constexpr (REG) {
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int g = k0 + k;
-            ts[k] = g < m ? sub[g] : Tw(0);
-            ti[k] = g < m ? inv[g] : Tw(0);
-            tc[k] = g < m ? cp[g] : Tw(0);
-        }
-    }
-    auto SUB = [&](int k) -> Tw { if constexpr (REG) return ts[k]; else return sub[k0 + k]; };
-    auto INV = [&](int k) -> Tw { if constexpr (REG) return ti[k]; else return inv[k0 + k]; };
-    auto CP = [&](int k) -> Tw { if constexpr (REG) return tc[k]; else return cp[k0 + k]; };
-    const int64_t ntx = (stride + 31) / 32;
-    const int64_t ntiles = outer_n * ntx;
+    const LaneFactors<Tw, E> F(sub, inv, cp, k0, m);
+    // lines are numbered (outer, inner) row-major; a tile is 32 consecutive
+    // lines, so a tile may span two outer indices but is never short
+    const int64_t nlines = outer_n * stride;
+    const int64_t ntiles = (nlines + 31) / 32;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t outer = tile / ntx;
-        const int64_t inner0 = (tile - outer * ntx) * 32;
-        const int nl = (int)(stride - inner0 < 32 ? stride - inner0 : 32);   // lines in the tile
-        const int64_t off = outer * m * stride + inner0;
+        const int64_t l0 = tile * 32;
+        const int nl = (int)(nlines - l0 < 32 ? nlines - l0 : 32);   // lines in the tile
+        const int64_t mine = l0 + (lane < nl ? lane : 0);            // this lane's line
+        const int64_t outer = mine / stride, inner = mine - outer * stride;
+        const int64_t off = outer * m * stride + inner;
         Tw* base = x + off;
         // asynchronous element copies: every row of the tile is in flight at once
         for (int k = wid; k < m; k += ST_WARPS) {
             Tw* dstp = &t[k * 33 + lane];
             if (lane < nl) {
                 const unsigned sa = (unsigned)__cvta_generic_to_shared(dstp);
-                const Tw* src = base + (int64_t)k * stride + lane;
+                const Tw* src = base + (int64_t)k * stride;
                 if (sizeof(Tw) == 4)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
                 else
@@ -249,73 +330,120 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
             Tw v[E];
 #pragma unroll
             for (int k = 0; k < E; ++k) v[k] = k0 + k < m ? t[(k0 + k) * 33 + l] : Tw(0);
-            Tw A = Tw(1), B = Tw(0);
+            warp_thomas<Tw, E>(v, k0, m, lane, [&](int k) { return F.SUB(k); },
+                               [&](int k) { return F.INV(k); }, [&](int k) { return F.CP(k); });
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if (k0 + k < m) {
-                    const Tw al = -SUB(k) * INV(k);
-                    A = al * A;
-                    B = al * B + v[k] * INV(k);
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const Tw pa = __shfl_up_sync(0xffffffffu, A, o), pb = __shfl_up_sync(0xffffffffu, B, o);
-                if (lane >= o) {
-                    B = A * pb + B;
-                    A = A * pa;
-                }
-            }
-            Tw y = __shfl_up_sync(0xffffffffu, B, 1);
-            if (lane == 0) y = Tw(0);
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if (k0 + k < m) {
-                    y = (v[k] - SUB(k) * y) * INV(k);
-                    v[k] = y;
-                }
-            }
-            A = Tw(1);
-            B = Tw(0);
-#pragma unroll
-            for (int k = E - 1; k >= 0; --k) {
-                if (k0 + k < m) {
-                    const Tw ga = -CP(k);
-                    A = ga * A;
-                    B = ga * B + v[k];
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const Tw pa = __shfl_down_sync(0xffffffffu, A, o), pb = __shfl_down_sync(0xffffffffu, B, o);
-                if (lane + o < 32) {
-                    B = A * pb + B;
-                    A = A * pa;
-                }
-            }
-            Tw xx = __shfl_down_sync(0xffffffffu, B, 1);
-            if (lane == 31) xx = Tw(0);
-#pragma unroll
-            for (int k = E - 1; k >= 0; --k) {
-                if (k0 + k < m) {
-                    xx = v[k] - CP(k) * xx;
-                    t[(k0 + k) * 33 + l] = xx;
-                }
-            }
+            for (int k = 0; k < E; ++k)
+                if (k0 + k < m) t[(k0 + k) * 33 + l] = v[k];
         }
         __syncthreads();
         if (lane < nl) {
             if (dst) {
                 Tdst* d = dst + off;
                 for (int k = wid; k < m; k += ST_WARPS) {
-                    const int64_t i = (int64_t)k * stride + lane;
+                    const int64_t i = (int64_t)k * stride;
                     d[i] = (Tdst)((Tw)d[i] + sign * t[k * 33 + lane]);
                 }
             } else {
-                for (int k = wid; k < m; k += ST_WARPS) base[(int64_t)k * stride + lane] = t[k * 33 + lane];
+                for (int k = wid; k < m; k += ST_WARPS) base[(int64_t)k * stride] = t[k * 33 + lane];
             }
         }
         __syncthreads();   // the next tile overwrites t
+    }
+}
+
+// Restriction and solve along one strided axis in a single pass.  The
+// correction M_{l-1}^{-1} P^T M_l is a tensor product of one operator per
+// axis, Mc_a^{-1} P_a^T M_a, and factors on different axes commute, so an
+// axis may be restricted and solved before the next axis is restricted.
+// in: (outer, m, inner), out: (outer, mc, inner).  A tile is 32 consecutive
+// lines in (outer, inner) order: their m input rows are copied into
+// shared memory (cp.async), each output row J takes the five-tap window of
+// P_a^T M_a around fine row f(J) (weights rw[J*5 + t], taps outside the
+// axis weigh 0), and each warp solves columns of the restricted tile with
+// warp_thomas before the block writes it out.
+template <typename Tw, int E>
+__global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
+    const Tw* __restrict__ in, Tw* __restrict__ out, int64_t outer_n, int m, int mc,
+    int64_t inner, AxisT<Tw> ax) {
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    Tw* ti = reinterpret_cast<Tw*>(tile_raw);   // [m][33] fine rows
+    Tw* to = ti + (size_t)m * 33;                // [mc][33] restricted rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k0 = lane * E;
+    const LaneFactors<Tw, E> F(ax.tsub, ax.tinv, ax.tcp, k0, mc);
+    const Tw* __restrict__ rw = ax.rw;
+    Tw wi[5];   // the window's weights where they are uniform (J in [rlo, rhi))
+#pragma unroll
+    for (int t = 0; t < 5; ++t) wi[t] = ax.rwi[t];
+    const int64_t gstep = (int64_t)ST_WARPS * inner;             // ST_WARPS rows, elements
+    const unsigned sstep = ST_WARPS * 33 * (unsigned)sizeof(Tw);  // ST_WARPS rows, bytes
+    // lines are numbered (outer, inner) row-major; a tile is 32 consecutive
+    // lines, so a tile may span two outer indices but is never short
+    const int64_t nlines = outer_n * inner;
+    const int64_t ntiles = (nlines + 31) / 32;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t l0 = tile * 32;
+        const int nl = (int)(nlines - l0 < 32 ? nlines - l0 : 32);
+        const int64_t mine = l0 + (lane < nl ? lane : 0);   // this lane's line
+        const int64_t o = mine / inner, i = mine - o * inner;
+        if (lane < nl) {
+            const Tw* g = in + o * m * inner + i + (int64_t)wid * inner;
+            unsigned sa = (unsigned)__cvta_generic_to_shared(&ti[wid * 33 + lane]);
+#pragma unroll 4
+            for (int k = wid; k < m; k += ST_WARPS, g += gstep, sa += sstep) {
+                if (sizeof(Tw) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+            }
+        } else {
+            for (int k = wid; k < m; k += ST_WARPS) ti[k * 33 + lane] = Tw(0);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        for (int J = wid; J < mc; J += ST_WARPS) {
+            Tw acc;
+            if (J >= ax.rlo && J < ax.rhi) {   // window 2J-2 .. 2J+2, uniform weights
+                const Tw* q = &ti[(2 * J - 2) * 33 + lane];
+                acc = wi[0] * q[0];
+                acc += wi[1] * q[33];
+                acc += wi[2] * q[66];
+                acc += wi[3] * q[99];
+                acc += wi[4] * q[132];
+            } else {
+                const int f = J == mc - 1 ? m - 1 : 2 * J;   // fine row under coarse row J
+                acc = Tw(0);
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    int ip = f - 2 + t;
+                    const bool ok = ip >= 0 && ip < m;
+                    const Tw w = ok ? rw[J * 5 + t] : Tw(0);
+                    ip = ok ? ip : f;
+                    acc += w * ti[ip * 33 + lane];
+                }
+            }
+            to[J * 33 + lane] = acc;
+        }
+        __syncthreads();
+        for (int l = wid; l < nl; l += ST_WARPS) {
+            Tw v[E];
+#pragma unroll
+            for (int k = 0; k < E; ++k) v[k] = k0 + k < mc ? to[(k0 + k) * 33 + l] : Tw(0);
+            warp_thomas<Tw, E>(v, k0, mc, lane, [&](int k) { return F.SUB(k); },
+                               [&](int k) { return F.INV(k); }, [&](int k) { return F.CP(k); });
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if (k0 + k < mc) to[(k0 + k) * 33 + l] = v[k];
+        }
+        __syncthreads();
+        if (lane < nl) {
+            Tw* dst = out + o * mc * inner + i + (int64_t)wid * inner;
+            const Tw* sp = &to[wid * 33 + lane];
+#pragma unroll 4
+            for (int k = wid; k < mc; k += ST_WARPS, dst += gstep, sp += ST_WARPS * 33) *dst = *sp;
+        }
+        __syncthreads();   // the next tile overwrites both buffers
     }
 }
 
@@ -328,8 +456,8 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
 // per-warp shared buffer so loads and stores stay coalesced.  E is odd
 // (conflict-free segment reads) and the smallest with 32E >= m, so lines of
 // 2^k + 1 nodes keep nearly every lane busy.  A lane's Thomas factors are
-// the same for every line: they stay in registers (in shared memory for the
-// widest segments), and the next line's loads are issued before the current
+// the same for every line: they stay in registers (the widest segments read
+// them through L1), and the next line's loads are issued before the current
 // line is solved.
 constexpr int SW_WARPS = 4;
 
@@ -340,33 +468,11 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
                                                               const Tw* __restrict__ cp, Tdst* dst,
                                                               Tw sign) {
     constexpr int W = E + 1;
-    constexpr bool REG = sizeof(Tw) * E <= 72;
     __shared__ Tw buf[SW_WARPS][32 * W];
-    __shared__ Tw tab[3][REG ? 1 : 32 * E];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Tw* sb = buf[wid];
     const int k0 = lane * E;
-    Tw ts[REG ? E : 1], ti[REG ? E : 1], tc[REG ? E : 1];
-    if constexpr (REG) {
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int g = k0 + k;
-            ts[k] = g < m ? sub[g] : Tw(0);
-            ti[k] = g < m ? inv[g] : Tw(0);
-            tc[k] = g < m ? cp[g] : Tw(0);
-        }
-    } else {
-        for (int g = threadIdx.x; g < 32 * E; g += blockDim.x) {
-            tab[0][g] = g < m ? sub[g] : Tw(0);
-            tab[1][g] = g < m ? inv[g] : Tw(0);
-            tab[2][g] = g < m ? cp[g] : Tw(0);
-        }
-        __syncthreads();
-    }
-    auto SUB = [&](int k) -> Tw { if constexpr (REG) return ts[k]; else return tab[0][k0 + k]; };
-    auto INV = [&](int k) -> Tw { if constexpr (REG) return ti[k]; else return tab[1][k0 + k]; };
-    auto CP = [&](int k) -> Tw { if constexpr (REG) return tc[k]; else return tab[2][k0 + k]; };
-
+    const LaneFactors<Tw, E> F(sub, inv, cp, k0, m);
     const int64_t step = (int64_t)gridDim.x * SW_WARPS;
     int64_t ln = (int64_t)blockIdx.x * SW_WARPS + wid;
     // row element e = lane + 32 j (j < E, so 32E >= m covers the row)
@@ -400,61 +506,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
         Tw v[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) v[k] = sb[lane * W + k];
-        // forward sweep: compose y -> alpha*y + beta over the segment
-        Tw A = Tw(1), B = Tw(0);
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            if (k0 + k < m) {
-                const Tw al = -SUB(k) * INV(k);
-                A = al * A;
-                B = al * B + v[k] * INV(k);
-            }
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const Tw pa = __shfl_up_sync(0xffffffffu, A, o), pb = __shfl_up_sync(0xffffffffu, B, o);
-            if (lane >= o) {
-                B = A * pb + B;
-                A = A * pa;
-            }
-        }
-        Tw y = __shfl_up_sync(0xffffffffu, B, 1);
-        if (lane == 0) y = Tw(0);
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            if (k0 + k < m) {
-                y = (v[k] - SUB(k) * y) * INV(k);
-                v[k] = y;
-            }
-        }
-        // backward sweep: compose x -> gamma*x + y from the segment's end
-        A = Tw(1);
-        B = Tw(0);
-#pragma unroll
-        for (int k = E - 1; k >= 0; --k) {
-            if (k0 + k < m) {
-                const Tw ga = -CP(k);
-                A = ga * A;
-                B = ga * B + v[k];
-            }
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const Tw pa = __shfl_down_sync(0xffffffffu, A, o), pb = __shfl_down_sync(0xffffffffu, B, o);
-            if (lane + o < 32) {
-                B = A * pb + B;
-                A = A * pa;
-            }
-        }
-        Tw xx = __shfl_down_sync(0xffffffffu, B, 1);
-        if (lane == 31) xx = Tw(0);
-#pragma unroll
-        for (int k = E - 1; k >= 0; --k) {
-            if (k0 + k < m) {
-                xx = v[k] - CP(k) * xx;
-                v[k] = xx;
-            }
-        }
+        warp_thomas<Tw, E>(v, k0, m, lane, [&](int k) { return F.SUB(k); },
+                           [&](int k) { return F.INV(k); }, [&](int k) { return F.CP(k); });
 #pragma unroll
         for (int k = 0; k < E; ++k) sb[lane * W + k] = v[k];
         __syncwarp();
@@ -766,17 +819,44 @@ mgard_status allow_dynamic_smem(const void* kern, size_t bytes) {
     return MGARD_OK;
 }
 
+// A grid of persistent blocks: as many as stay resident at once (all SMs,
+// the occupancy of `kern` at this block size and shared memory), at most
+// `work` of them.  Launching more would leave a tail of blocks that start
+// only when others finish.
+mgard_status resident_grid(const void* kern, int threads, size_t smem, int64_t work, int* grid) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+    int dev = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kern, threads, smem, dev);
+    auto it = cache.find(key);
+    int per = 0;
+    if (it == cache.end()) {
+        int sms = 0, nb = 0;
+        MGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem));
+        per = std::max(1, sms * nb);
+        cache[key] = per;
+    } else {
+        per = it->second;
+    }
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(work, per));
+    return MGARD_OK;
+}
+
 template <typename Tw, typename Tdst>
 mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, const Tw* sub,
                            const Tw* inv, const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
     // tiles of 32 lines in shared memory while a tile fits
     const size_t tile_bytes = (size_t)m * 33 * sizeof(Tw);
     if (stride > 1 && m <= 1056 && tile_bytes <= 200 * 1024) {
-        const int64_t ntiles = outer * ((stride + 31) / 32);
-        const int grid = (int)std::min<int64_t>(ntiles, 148LL * 4);
+        const int64_t ntiles = (outer * stride + 31) / 32;
         bool launched = false;
         auto go = [&](auto kern) -> mgard_status {
             MGB_TRY(allow_dynamic_smem((const void*)kern, tile_bytes));
+            int grid = 0;
+            MGB_TRY(resident_grid((const void*)kern, ST_WARPS * 32, tile_bytes, ntiles, &grid));
             MGB_LAUNCH("k_solve_tile", st, kern<<<grid, ST_WARPS * 32, tile_bytes, st>>>(x, outer, (int)m, stride, sub, inv, cp, dst, sign));
             launched = true;
             return MGARD_OK;
@@ -800,6 +880,31 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
                                                             sign));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
+}
+
+template <typename Tw>
+mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
+                                    int64_t inner, const AxisT<Tw>& ax, cudaStream_t st,
+                                    bool* done) {
+    *done = false;
+    const size_t bytes = (size_t)(m + mc) * 33 * sizeof(Tw);
+    if (inner < 2 || mc > 1056 || bytes > 200 * 1024) return MGARD_OK;   // separate passes
+    const int64_t ntiles = (outer * inner + 31) / 32;
+    auto go = [&](auto kern) -> mgard_status {
+        MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
+        int grid = 0;
+        MGB_TRY(resident_grid((const void*)kern, ST_WARPS * 32, bytes, ntiles, &grid));
+        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, ST_WARPS * 32, bytes, st>>>(in, out, outer, (int)m, (int)mc, inner, ax));
+        MGB_CUDA(cudaGetLastError());
+        *done = true;
+        return MGARD_OK;
+    };
+    if (mc <= 32) return go(k_restrict_solve<Tw, 1>);
+    if (mc <= 96) return go(k_restrict_solve<Tw, 3>);
+    if (mc <= 160) return go(k_restrict_solve<Tw, 5>);
+    if (mc <= 288) return go(k_restrict_solve<Tw, 9>);
+    if (mc <= 544) return go(k_restrict_solve<Tw, 17>);
+    return go(k_restrict_solve<Tw, 33>);
 }
 
 template <typename Tw, typename Tdst>
@@ -1057,5 +1162,11 @@ INST_SOLVE(float, float)
 INST_SOLVE(double, float)
 INST_SOLVE(double, double)
 #undef INST_SOLVE
+template mgard_status restrict_solve_strided<float>(const float*, float*, int64_t, int64_t, int64_t,
+                                                    int64_t, const AxisT<float>&, cudaStream_t,
+                                                    bool*);
+template mgard_status restrict_solve_strided<double>(const double*, double*, int64_t, int64_t,
+                                                     int64_t, int64_t, const AxisT<double>&,
+                                                     cudaStream_t, bool*);
 
 }  // namespace mgb

@@ -266,7 +266,8 @@ mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, Compress
     MGB_TRY(huffman_pack(w.sym.template as<uint16_t>(), N, w.lengths.template as<uint8_t>(),
                          w.codes.template as<uint32_t>(), word_off, esc_off, w.esc.template as<int32_t>(),
                          reinterpret_cast<uint32_t*>(dd), reinterpret_cast<uint16_t*>(dd + fx.sub_off),
-                         reinterpret_cast<int32_t*>(dd + fx.outliers), st, guard));
+                         reinterpret_cast<int32_t*>(dd + fx.outliers), st, guard,
+                         rows3_ok(p)));   // the streaming quantizer compacts escapes per chunk
     return MGARD_OK;
 }
 

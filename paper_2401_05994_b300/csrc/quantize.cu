@@ -7,6 +7,7 @@
 // q + DICT/2; larger values escape to symbol 0 with q stored aside.
 #include <cstring>
 
+#include "huffman.cuh"
 #include "quantize.cuh"
 #include "rows3.cuh"
 
@@ -220,7 +221,12 @@ __global__ void __launch_bounds__(QT) k_features(const T* __restrict__ c, QLevel
 // pass): eight consecutive values per thread with vector loads and one
 // 16-byte store of their symbols; the level of each value comes from the
 // offsets (a group may straddle two levels).  Same decisions as k_quantize.
+// Escape values are stored compacted per Huffman sub-chunk (256 symbols, the
+// span of one warp per iteration): the r-th escape of sub-chunk s (in symbol
+// order) at esc[s * 256 + r], placed by a warp scan of the lanes' counts.
 constexpr int QS_THREADS = 256;
+constexpr int QS_SUB = SUB;   // symbols per Huffman sub-chunk
+static_assert(QS_SUB == 32 * 8, "a warp covers one sub-chunk per iteration");
 
 template <typename T>
 __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
@@ -241,11 +247,16 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
     for (int l = threadIdx.x; l <= lo.L + 1; l += QS_THREADS) offs[l] = lo.off[l];
     __syncthreads();
     const int L = lo.L;
+    const int lane = threadIdx.x & 31;
     unsigned* my = sh[threadIdx.x & 1];
     unsigned center = 0, st = 0;
-    for (int64_t g = blockIdx.x * (int64_t)QS_THREADS + threadIdx.x; g * 8 < n;
-         g += (int64_t)gridDim.x * QS_THREADS) {
+    // block-uniform trip count (the escape scan needs whole warps)
+    for (int64_t gb = blockIdx.x * (int64_t)QS_THREADS; gb * 8 < n;
+         gb += (int64_t)gridDim.x * QS_THREADS) {
+        const int64_t g = gb + threadIdx.x;
         const int64_t i0 = g * 8;
+        int32_t qe[8];
+        unsigned ne = 0;   // escapes among this thread's values, in order in qe
         // the level of the group's first value; its width stays in registers
         // until a value crosses into the next level (rare)
         int l = 0;
@@ -256,7 +267,10 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
         WidthSplit wsl = wss[l];
         T v[8];
         const bool full = i0 + 8 <= n;
-        if (full) {
+        if (i0 >= n) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = T(0);
+        } else if (full) {
             if (sizeof(T) == 4) {
                 const float4 a = reinterpret_cast<const float4*>(zs + i0)[0];
                 const float4 b = reinterpret_cast<const float4*>(zs + i0)[1];
@@ -290,7 +304,12 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
             int32_t qo = 0;
             quantize_value(v[k], iwl, wsl, wl, s, qo, st);
             packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
-            if (s == MGARD_ESC) esc[i] = qo;
+            if (s == MGARD_ESC) {   // the value goes to slot ne (slots 0..ne-1 hold earlier escapes)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j == (int)ne) qe[j] = qo;
+                ++ne;
+            }
             if (s == RADIUS) ++center;
             else atomicAdd(&my[s], 1u);
         }
@@ -299,6 +318,20 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
         } else {
             for (int k = 0; k < 8 && i0 + k < n; ++k)
                 sym[i0 + k] = (uint16_t)(packed[k >> 1] >> (16 * (k & 1)));
+        }
+        // place of this thread's first escape inside its sub-chunk: exclusive
+        // scan over the warp
+        unsigned inc = ne;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (ne) {
+            int32_t* dst = esc + (i0 & ~(int64_t)(QS_SUB - 1)) + (inc - ne);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < (int)ne) dst[j] = qe[j];
         }
     }
     if (center) atomicAdd(&sh[0][RADIUS], center);

@@ -21,8 +21,10 @@ mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const i
                               bool inplace, double w, T* c, cudaStream_t st);
 
 // Quantization of all levels' coefficients held in symbol order (zs, N
-// values; w: device widths of levels 0..L).  Same symbols, escapes and
-// histogram as quantize_level over the levels.
+// values; w: device widths of levels 0..L).  Same symbols, escape values and
+// histogram as quantize_level over the levels, but the escapes are stored
+// compacted per Huffman sub-chunk: the r-th escape of sub-chunk s at
+// esc[s * (MGARD_CHUNK / MGARD_NSUB) + r] (huffman_pack's `compact` layout).
 LevelOffsets level_offsets(const Plan& p);
 template <typename T>
 mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16_t* sym,

@@ -32,6 +32,15 @@ __device__ inline int coarse_index(int i, int m, int mc) { return i == m - 1 ? m
 __device__ inline int restrict_center(int J, int m, int mc) { return J == mc - 1 ? m - 1 : 2 * J; }
 __device__ inline int coarse_before(int i) { return (i + 1) >> 1; }
 
+// Row loops take 32 * U elements per pass (U per lane).  Extents of 2^k + 1
+// would leave a last pass of one element that costs a full pass of latency,
+// so a remainder of at most one warp width joins the pass before it: this
+// pass (starting at element `base`) takes U + 1 elements per lane when the
+// row ends within 32 elements after it.
+__device__ inline bool absorbs_tail(int base, int n, int U) {
+    return base + 32 * U < n && base + 32 * (U + 1) >= n;
+}
+
 // Rounding spelled out, so the staged and per-element forms of the
 // interpolation (below) give the same bits whatever the compiler contracts.
 __device__ inline float rmul(float a, float b) { return __fmul_rn(a, b); }
@@ -254,12 +263,13 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
             __syncwarp();
         }
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
-            T u[U], acc[U];
+            const bool tail = absorbs_tail(x0 - lane, nx, U);
+            T u[U + 1], acc[U + 1];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
+            for (int j = 0; j < U + 1; ++j) {
                 const int x = x0 + 32 * j;
                 acc[j] = T(0);
-                if (x >= nx) continue;
+                if (x >= nx || (j == U && !tail)) continue;
                 u[j] = urow[x];
                 // coarse x: neighbours x, x with weights (1, 0); new x: x-1, x+1
                 const bool cx = is_coarse(x, nx);
@@ -278,9 +288,9 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                 }
             }
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
+            for (int j = 0; j < U + 1; ++j) {
                 const int x = x0 + 32 * j;
-                if (x >= nx) continue;
+                if (x >= nx || (j == U && !tail)) continue;
                 if (rowc && is_coarse(x, nx)) {
                     crow[coarse_index(x, nx, ncx)] = u[j];
                     if (RX) Z[x] = T(0);
@@ -290,6 +300,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                     if (RX) Z[x] = c;
                 }
             }
+            if (tail) break;
         }
         if (RX) {
             __syncwarp();
@@ -343,12 +354,13 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
             __syncwarp();
         }
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
-            T v[U];
+            const bool tail = absorbs_tail(x0 - lane, nx, U);
+            T v[U + 1];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
+            for (int j = 0; j < U + 1; ++j) {
                 const int x = x0 + 32 * j;
                 v[j] = T(0);
-                if (x >= nx) continue;
+                if (x >= nx || (j == U && !tail)) continue;
                 // coarse x: coarse index J twice with weights (1, 0); new x: J, J+1
                 const bool cx = is_coarse(x, nx);
                 const int jl = cx ? coarse_index(x, nx, ncx) : (x - 1) >> 1;
@@ -364,10 +376,11 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
                 if (!(rowc && cx)) v[j] += zrow[(ZS && rowc) ? x - coarse_before(x) : x];
             }
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
+            for (int j = 0; j < U + 1; ++j) {
                 const int x = x0 + 32 * j;
-                if (x < nx) orow[x] = v[j];
+                if (x < nx && (j < U || tail)) orow[x] = v[j];
             }
+            if (tail) break;
         }
         if (STAGE) __syncwarp();   // R is rewritten by the warp's next row
     }
@@ -395,19 +408,21 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
         // symbol order on a coarse row holds only the odd positions: ip -> (ip - 1) / 2
         const int sh = (ZS && rowc) ? 1 : 0;
         for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
-            Tout acc[U];
+            const bool tail = absorbs_tail(J0 - lane, ncx, U);
+            Tout acc[U + 1];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
+            for (int j = 0; j < U + 1; ++j) {
                 const int J = J0 + 32 * j;
                 acc[j] = Tout(0);
-                if (J >= ncx) continue;
+                if (J >= ncx || (j == U && !tail)) continue;
                 acc[j] = restrict_row_at<Tout>(J, nx, ncx, rowc, wi, rlo, rhi, rw, [&](int ip) {
                     return (Tout)irow[sh ? (ip - 1) >> 1 : ip];
                 });
             }
 #pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (J0 + 32 * j < ncx) orow[J0 + 32 * j] = acc[j];
+            for (int j = 0; j < U + 1; ++j)
+                if (J0 + 32 * j < ncx && (j < U || tail)) orow[J0 + 32 * j] = acc[j];
+            if (tail) break;
         }
     }
 }
@@ -815,27 +830,39 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
     Tw* nxt = b1;
+    // y, then z: each axis restricted and, where its tiles fit, solved in the
+    // same pass (the per-axis factors of the correction commute)
+    bool y_solved = false, z_solved = false;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
-        with_cfg(cr, ncx, true, [&](auto u) {
-            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy, cr.bpsm), RT, 0, st>>>(
-                cur, nxt, nz, ny, ncy, 1, ncx, lw.ax[2].rw));
-        });
-        MGB_CUDA(cudaGetLastError());
+        const AxisT<Tw>& a = lw.ax[2];
+        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, nz, ny, ncy, ncx, a, st, &y_solved));
+        if (!y_solved) {
+            with_cfg(cr, ncx, true, [&](auto u) {
+                MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy, cr.bpsm), RT, 0, st>>>(
+                    cur, nxt, nz, ny, ncy, 1, ncx, a.rw));
+            });
+            MGB_CUDA(cudaGetLastError());
+        }
         std::swap(cur, nxt);
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
-        with_cfg(cr, ncx, true, [&](auto u) {
-            MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy, cr.bpsm), RT, 0, st>>>(
-                cur, nxt, 1, nz, ncz, ncy, ncx, lw.ax[1].rw));
-        });
-        MGB_CUDA(cudaGetLastError());
+        const AxisT<Tw>& a = lw.ax[1];
+        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, 1, nz, ncz, (int64_t)ncy * ncx, a, st,
+                                           &z_solved));
+        if (!z_solved) {
+            with_cfg(cr, ncx, true, [&](auto u) {
+                MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy, cr.bpsm), RT, 0, st>>>(
+                    cur, nxt, 1, nz, ncz, ncy, ncx, a.rw));
+            });
+            MGB_CUDA(cudaGetLastError());
+        }
         std::swap(cur, nxt);
     }
-    // solves: z, y (strided lines), then x (contiguous, fused correction add)
-    if (lt.ax[1].fcls)
+    // remaining solves: z, y (strided lines), then x (contiguous, fused correction add)
+    if (lt.ax[1].fcls && !z_solved)
         MGB_TRY((solve_strided<Tw, T>(cur, 1, ncz, (int64_t)ncy * ncx, lw.ax[1].tsub, lw.ax[1].tinv,
                                       lw.ax[1].tcp, (T*)nullptr, (Tw)sign, st)));
-    if (lt.ax[2].fcls)
+    if (lt.ax[2].fcls && !y_solved)
         MGB_TRY((solve_strided<Tw, T>(cur, ncz, ncy, ncx, lw.ax[2].tsub, lw.ax[2].tinv,
                                       lw.ax[2].tcp, (T*)nullptr, (Tw)sign, st)));
     MGB_TRY((solve_contiguous<Tw, T>(cur, (int64_t)ncz * ncy, ncx, lw.ax[3].tsub, lw.ax[3].tinv,

@@ -55,5 +55,14 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
 template <typename Tw, typename Tdst>
 mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, const Tw* inv,
                               const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st);
+// Restriction along a strided axis (in: (outer, m, inner) -> out: (outer,
+// mc, inner), the axis' weights rw[J*5 + t] on fine rows f(J)-2 .. f(J)+2,
+// uniform rwi inside [rlo, rhi)) followed by the tridiagonal solve along it
+// (the axis' Thomas factors), in one pass over shared-memory tiles.
+// *done is false (and nothing runs) when a tile would not fit.
+template <typename Tw>
+mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
+                                    int64_t inner, const AxisT<Tw>& ax, cudaStream_t st,
+                                    bool* done);
 
 }  // namespace mgb
