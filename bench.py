@@ -41,11 +41,12 @@ SHAPE = (513, 513, 513)
 TOL = 1e-3
 BETA = 5.0 / 3.0
 SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
-# DRAM bytes (read + write) of one launch from ncu captures of a smaller case
-# (profiles/), with the elements that launch processed; scaled to the bench
-# workload by elements (the traffic of these kernels grows in proportion).
-# Valid for the kernel versions captured; kernels without a capture report null.
-NCU_TRAFFIC = {}   # the decoder changed since its last capture
+# DRAM bytes (read + write) of all launches of a kernel in one compress +
+# decompress step, from an ncu capture of a smaller cube (profiles/), with
+# that cube's element count; scaled to the bench workload by elements (the
+# traffic of these kernels grows in proportion) and divided by the launches
+# per step.  Valid for the kernel versions captured; others report null.
+NCU_TRAFFIC = {}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -571,11 +572,14 @@ def main():
     if dom:
         ach = algo.get(dom, 0.0) / (kernel_ms[dom] / 1e3) / 1e9
         traffic = None
-        if dom in NCU_TRAFFIC and rep.get(dom, (0,))[0] == trace_steps:   # one launch per step
+        if dom in NCU_TRAFFIC:
             b, n0 = NCU_TRAFFIC[dom]
-            traffic = b * int(np.prod(shape)) / n0
+            launches_per_step = rep[dom][0] / trace_steps
+            traffic = b * int(np.prod(shape)) / n0 / launches_per_step
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": traffic, "peak_source": peak_src,
+                "launches_per_step": rep[dom][0] / trace_steps,
+                "algorithmic_bytes_per_launch": algo.get(dom, 0.0) / (rep[dom][0] / trace_steps),
                 "kernel_ms_per_step": kernel_ms[dom],
                 "kernel_share": kernel_ms[dom] / sum(kernel_ms.values())}
 

@@ -360,18 +360,34 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
 // lines in (outer, inner) order: their m input rows are copied into
 // shared memory (cp.async), each output row J takes the five-tap window of
 // P_a^T M_a around fine row f(J) (weights rw[J*5 + t], taps outside the
-// axis weigh 0), and each warp solves columns of the restricted tile with
-// warp_thomas before the block writes it out.
-template <typename Tw, int E>
+// axis weigh 0), and the restricted tile is solved along its columns before
+// the block writes it out.  The solve: lane l owns column l and warp w a
+// segment of at most K rows.  Both Thomas sweeps are affine recurrences
+// (y_k = al_k y_{k-1} + v_k inv_k with al_k = -a_k inv_k forward, x_k =
+// -c'_k x_{k+1} + y_k backward), so each thread composes its segment's map
+// in registers, the maps of the preceding (forward) or following (backward)
+// segments are folded through shared memory, and each thread replays its
+// segment.
+template <typename Tw, int K>
 __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
     const Tw* __restrict__ in, Tw* __restrict__ out, int64_t outer_n, int m, int mc,
     int64_t inner, AxisT<Tw> ax) {
     extern __shared__ __align__(16) unsigned char tile_raw[];
     Tw* ti = reinterpret_cast<Tw*>(tile_raw);   // [m][33] fine rows
     Tw* to = ti + (size_t)m * 33;                // [mc][33] restricted rows
+    Tw* sal = to + (size_t)mc * 33;              // [mc] -a_k inv_k
+    Tw* sinv = sal + mc;                         // [mc] inv_k
+    Tw* sga = sinv + mc;                         // [mc] -c'_k
+    __shared__ Tw sA[ST_WARPS][32], sB[ST_WARPS][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int k0 = lane * E;
-    const LaneFactors<Tw, E> F(ax.tsub, ax.tinv, ax.tcp, k0, mc);
+    for (int k = threadIdx.x; k < mc; k += blockDim.x) {
+        sal[k] = -ax.tsub[k] * ax.tinv[k];
+        sinv[k] = ax.tinv[k];
+        sga[k] = -ax.tcp[k];
+    }
+    const int seg = (mc + ST_WARPS - 1) / ST_WARPS;   // rows per warp (<= K)
+    const int r0 = wid * seg;
+    const int cnt = max(0, min(seg, mc - r0));
     const Tw* __restrict__ rw = ax.rw;
     Tw wi[5];   // the window's weights where they are uniform (J in [rlo, rhi))
 #pragma unroll
@@ -426,15 +442,54 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
             to[J * 33 + lane] = acc;
         }
         __syncthreads();
-        for (int l = wid; l < nl; l += ST_WARPS) {
-            Tw v[E];
+        {
+            Tw v[K];
 #pragma unroll
-            for (int k = 0; k < E; ++k) v[k] = k0 + k < mc ? to[(k0 + k) * 33 + l] : Tw(0);
-            warp_thomas<Tw, E>(v, k0, mc, lane, [&](int k) { return F.SUB(k); },
-                               [&](int k) { return F.INV(k); }, [&](int k) { return F.CP(k); });
+            for (int j = 0; j < K; ++j) v[j] = j < cnt ? to[(r0 + j) * 33 + lane] : Tw(0);
+            Tw A = Tw(1), B = Tw(0);   // forward map of the segment: y_in -> A y_in + B
 #pragma unroll
-            for (int k = 0; k < E; ++k)
-                if (k0 + k < mc) to[(k0 + k) * 33 + l] = v[k];
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) {
+                    const Tw al = sal[r0 + j], w = v[j] * sinv[r0 + j];
+                    v[j] = w;
+                    A = al * A;
+                    B = al * B + w;
+                }
+            sA[wid][lane] = A;
+            sB[wid][lane] = B;
+            __syncthreads();
+            Tw y = Tw(0);
+            for (int s2 = 0; s2 < wid; ++s2) y = sA[s2][lane] * y + sB[s2][lane];
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) {
+                    y = sal[r0 + j] * y + v[j];
+                    v[j] = y;
+                }
+            A = Tw(1);   // backward map: x at the segment's end -> x at its start
+            B = Tw(0);
+#pragma unroll
+            for (int j = K - 1; j >= 0; --j)
+                if (j < cnt) {
+                    const Tw ga = sga[r0 + j];
+                    A = ga * A;
+                    B = ga * B + v[j];
+                }
+            __syncthreads();   // every thread has read the forward maps
+            sA[wid][lane] = A;
+            sB[wid][lane] = B;
+            __syncthreads();
+            Tw x = Tw(0);
+            for (int s2 = ST_WARPS - 1; s2 > wid; --s2) x = sA[s2][lane] * x + sB[s2][lane];
+#pragma unroll
+            for (int j = K - 1; j >= 0; --j)
+                if (j < cnt) {
+                    x = sga[r0 + j] * x + v[j];
+                    v[j] = x;
+                }
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) to[(r0 + j) * 33 + lane] = v[j];
         }
         __syncthreads();
         if (lane < nl) {
@@ -887,8 +942,8 @@ mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_
                                     int64_t inner, const AxisT<Tw>& ax, cudaStream_t st,
                                     bool* done) {
     *done = false;
-    const size_t bytes = (size_t)(m + mc) * 33 * sizeof(Tw);
-    if (inner < 2 || mc > 1056 || bytes > 200 * 1024) return MGARD_OK;   // separate passes
+    const size_t bytes = ((size_t)(m + mc) * 33 + 3 * (size_t)mc) * sizeof(Tw);
+    if (inner < 2 || mc > 520 || bytes > 200 * 1024) return MGARD_OK;   // separate passes
     const int64_t ntiles = (outer * inner + 31) / 32;
     auto go = [&](auto kern) -> mgard_status {
         MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
@@ -899,12 +954,13 @@ mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_
         *done = true;
         return MGARD_OK;
     };
-    if (mc <= 32) return go(k_restrict_solve<Tw, 1>);
-    if (mc <= 96) return go(k_restrict_solve<Tw, 3>);
-    if (mc <= 160) return go(k_restrict_solve<Tw, 5>);
-    if (mc <= 288) return go(k_restrict_solve<Tw, 9>);
-    if (mc <= 544) return go(k_restrict_solve<Tw, 17>);
-    return go(k_restrict_solve<Tw, 33>);
+    // K: rows per warp segment, ceil(mc / ST_WARPS) at most
+    if (mc <= 16) return go(k_restrict_solve<Tw, 2>);
+    if (mc <= 32) return go(k_restrict_solve<Tw, 4>);
+    if (mc <= 64) return go(k_restrict_solve<Tw, 8>);
+    if (mc <= 136) return go(k_restrict_solve<Tw, 17>);
+    if (mc <= 264) return go(k_restrict_solve<Tw, 33>);
+    return go(k_restrict_solve<Tw, 65>);
 }
 
 template <typename Tw, typename Tdst>

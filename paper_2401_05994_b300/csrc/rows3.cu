@@ -133,13 +133,14 @@ void with_u8(int64_t nx, F&& f) {
     else f(UTag<8>{});
 }
 
-// Batch size from a tuned launch shape (2, 4 or 8), else the built-in rule
+// Batch size from a tuned launch shape (2, 4, 8 or 16), else the built-in rule
 // (`light`: the with_u8 rule, otherwise the with_u rule).
 template <typename F>
 void with_cfg(const RowCfg& c, int64_t nx, bool light, F&& f) {
     if (c.u == 2) f(UTag<2>{});
     else if (c.u == 4) f(UTag<4>{});
     else if (c.u == 8) f(UTag<8>{});
+    else if (c.u == 16) f(UTag<16>{});
     else if (light) with_u8(nx, f);
     else with_u(nx, f);
 }

@@ -2,7 +2,7 @@
 //
 // For every level of a shape and every row kernel (coefficients, fill,
 // restriction along x, restriction along y/z, quantization,
-// dequantization) the tuner times each launch shape -- 2, 4 or 8 elements
+// dequantization) the tuner times each launch shape -- 2, 4, 8 or 16 elements
 // per lane per batch, grids sized for 4, 8 or 16 resident blocks per SM, and
 // for the coefficient and fill kernels rows staged in shared memory or not --
 // on workspace buffers holding a decomposed synthetic field, and keeps the
@@ -39,7 +39,7 @@ __global__ void k_tune_fill(T* u, int64_t n) {
     }
 }
 
-const int U_CAND[] = {2, 4, 8};
+const int U_CAND[] = {2, 4, 8, 16};
 const int B_CAND[] = {4, 8, 16};
 const char* KIND_NAME[RK_COUNT] = {"coeff", "fill", "restrict_x", "restrict_rows", "quantize",
                                    "dequantize"};
@@ -96,7 +96,7 @@ mgard_status tune_impl(const Plan& p, cudaStream_t st, std::string& rep) {
             float best = 1e30f, base = 0.f;
             RowCfg pick = keep;
             const int nstage = (kind == RK_COEFF || kind == RK_FILL) ? 2 : 1;
-            for (int ui = -1; ui < 3 && err == MGARD_OK; ++ui) {
+            for (int ui = -1; ui < 4 && err == MGARD_OK; ++ui) {
                 for (int bs = 0; bs < 3 * nstage && err == MGARD_OK; ++bs) {
                     const int bi = bs % 3;
                     if (ui < 0 && bs > 0) break;   // ui = -1: the built-in choice
