@@ -227,10 +227,15 @@ __device__ inline Tout restrict_row_at(int J, int nx, int ncx, bool rowc, const 
 // coefficients are also kept in shared memory (zero at coarse nodes of the
 // coarser grid's rows) and restricted along x into rx (rows of ncx values in
 // Tw), the first step of the coarse-grid correction.
-template <typename T, int U, bool ZS, bool STAGE, bool RX, typename Tw>
+// PAIR (with STAGE, on an odd extent whose interpolation weights are the
+// uniform ones everywhere): lane p takes the node pair (2p, 2p+1), the
+// coarse node and the new node after it, so parity, coarse index and
+// weights are known without per-element tests; same arithmetic, same bits.
+template <typename T, int U, bool ZS, bool STAGE, bool RX, typename Tw, bool PAIR>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
                                                Level<T> lv, int64_t zoff, Tw* __restrict__ rx,
                                                AxisT<Tw> axw) {
+    static_assert(!PAIR || STAGE, "pairs read the staged row");
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
@@ -263,6 +268,41 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
             for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, min(2 * j, nx - 1));
             __syncwarp();
         }
+        if (PAIR) {
+            for (int p0 = lane; p0 < ncx; p0 += 32 * U) {
+                const bool tail = absorbs_tail(p0 - lane, ncx, U);
+                T u0[U + 1], u1[U + 1];
+#pragma unroll
+                for (int j = 0; j < U + 1; ++j) {   // loads first
+                    const int p = p0 + 32 * j;
+                    if (p >= ncx || (j == U && !tail)) continue;
+                    u0[j] = urow[2 * p];
+                    if (p + 1 < ncx) u1[j] = urow[2 * p + 1];
+                }
+#pragma unroll
+                for (int j = 0; j < U + 1; ++j) {
+                    const int p = p0 + 32 * j;
+                    if (p >= ncx || (j == U && !tail)) continue;
+                    const T r0 = R[p];
+                    // coarse x = 2p: the interpolant is R[p] itself
+                    const T a0 = lerp_x(T(1), r0, T(0), r0);
+                    if (rowc) {
+                        crow[p] = u0[j];
+                        if (RX) Z[2 * p] = T(0);
+                    } else {
+                        const T c = u0[j] - a0;
+                        orow[2 * p] = c;
+                        if (RX) Z[2 * p] = c;
+                    }
+                    if (p + 1 < ncx) {   // new x = 2p + 1 between coarse p and p + 1
+                        const T c = u1[j] - lerp_x(T(0.5), r0, T(0.5), R[p + 1]);
+                        orow[(ZS && rowc) ? p : 2 * p + 1] = c;
+                        if (RX) Z[2 * p + 1] = c;
+                    }
+                }
+                if (tail) break;
+            }
+        } else
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             const bool tail = absorbs_tail(x0 - lane, nx, U);
             T u[U + 1], acc[U + 1];
@@ -322,9 +362,10 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
 // one row R of the coarse x grid in shared memory (each coarse value loaded
 // once), and the x interpolation then reads R; otherwise every element
 // interpolates each coarse row itself.
-template <typename T, int U, bool ZS, bool STAGE>
+template <typename T, int U, bool ZS, bool STAGE, bool PAIR>
 __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict__ coarse, T* out,
                                               Level<T> lv, int64_t zoff) {
+    static_assert(!PAIR || STAGE, "pairs read the staged row");
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
@@ -354,6 +395,30 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
             for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, j);
             __syncwarp();
         }
+        if (PAIR) {   // lane p: coarse x = 2p and new x = 2p + 1 (see k3_coeff)
+            for (int p0 = lane; p0 < ncx; p0 += 32 * U) {
+                const bool tail = absorbs_tail(p0 - lane, ncx, U);
+                T z0[U + 1], z1[U + 1];
+#pragma unroll
+                for (int j = 0; j < U + 1; ++j) {   // loads first
+                    const int p = p0 + 32 * j;
+                    if (p >= ncx || (j == U && !tail)) continue;
+                    if (!rowc) z0[j] = zrow[2 * p];
+                    if (p + 1 < ncx) z1[j] = zrow[(ZS && rowc) ? p : 2 * p + 1];
+                }
+#pragma unroll
+                for (int j = 0; j < U + 1; ++j) {
+                    const int p = p0 + 32 * j;
+                    if (p >= ncx || (j == U && !tail)) continue;
+                    const T r0 = R[p];
+                    T v0 = lerp_x(T(1), r0, T(0), r0);
+                    if (!rowc) v0 += z0[j];   // z vanishes on coarse nodes of the coarse grid's rows
+                    orow[2 * p] = v0;
+                    if (p + 1 < ncx) orow[2 * p + 1] = lerp_x(T(0.5), r0, T(0.5), R[p + 1]) + z1[j];
+                }
+                if (tail) break;
+            }
+        } else
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             const bool tail = absorbs_tail(x0 - lane, nx, U);
             T v[U + 1];
@@ -742,6 +807,14 @@ size_t stage_bytes(const Level<T>& lv, const RowCfg& c) {
     return c.stage != 0 && b <= 48 * 1024 ? b : 0;
 }
 
+// The pair paths of the coefficient and fill kernels: an odd extent along x
+// (coarse nodes at the even x, the last one included) with the uniform
+// interpolation weights everywhere.
+template <typename T>
+bool pair_ok(const Level<T>& lv) {
+    return (lv.n[3] & 1) && lv.n[3] >= 3 && lv.ax[3].ireg >= lv.n[3];
+}
+
 }  // namespace
 
 template <typename T>
@@ -754,6 +827,7 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
     // the fused x restriction keeps the row's coefficients beside the staged row
     const size_t smx = sm + (size_t)WPB * (size_t)lv.n[3] * sizeof(T);
     const bool fuse = rx && sm && smx <= 48 * 1024;
+    const bool pair = sm && pair_ok(lv);
     if (fused) *fused = fuse;
     with_cfg(c, lv.n[3], false, [&](auto u) {
         constexpr int U = decltype(u)::value;
@@ -763,24 +837,32 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
                 using Tw = decltype(tw);
                 Tw* x = (Tw*)rx;
                 const AxisT<Tw> ax = p.level<Tw>(l).ax[3];
-                if (zoff >= 0)
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                if (zoff >= 0 && pair)
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                else if (zoff >= 0)
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                else if (pair)
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
                 else
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
             };
             if (rx_f64) go(double(0));
             else go(T(0));
             return;
         }
         const AxisT<T> none{};
-        if (zoff >= 0 && sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
+        if (zoff >= 0 && pair)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
+        else if (zoff >= 0 && sm)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
         else if (zoff >= 0)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false, false, T><<<g, RT, 0, st>>>(in, out, coarse, lv, zo, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, zo, nullptr, none));
+        else if (pair)
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
         else if (sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
         else
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false, false, T><<<g, RT, 0, st>>>(in, out, coarse, lv, 0, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0, nullptr, none));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -793,16 +875,21 @@ mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* ou
     const RowCfg c = p.row_cfg(l, RK_FILL);
     const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
     const size_t sm = stage_bytes<T>(lv, c);
+    const bool pair = sm && pair_ok(lv);
     with_cfg(c, lv.n[3], false, [&](auto u) {
         constexpr int U = decltype(u)::value;
-        if (zoff >= 0 && sm)
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, true><<<g, RT, sm, st>>>(z, coarse, out, lv, zoff));
+        if (zoff >= 0 && pair)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, true, true><<<g, RT, sm, st>>>(z, coarse, out, lv, zoff));
+        else if (zoff >= 0 && sm)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, true, false><<<g, RT, sm, st>>>(z, coarse, out, lv, zoff));
         else if (zoff >= 0)
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, false><<<g, RT, 0, st>>>(z, coarse, out, lv, zoff));
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, true, false, false><<<g, RT, 0, st>>>(z, coarse, out, lv, zoff));
+        else if (pair)
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, true, true><<<g, RT, sm, st>>>(z, coarse, out, lv, 0));
         else if (sm)
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, true><<<g, RT, sm, st>>>(z, coarse, out, lv, 0));
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, true, false><<<g, RT, sm, st>>>(z, coarse, out, lv, 0));
         else
-            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, false><<<g, RT, 0, st>>>(z, coarse, out, lv, 0));
+            MGB_LAUNCH("k3_fill", st, k3_fill<T, U, false, false, false><<<g, RT, 0, st>>>(z, coarse, out, lv, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
