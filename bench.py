@@ -86,8 +86,7 @@ def level_shapes(shape):
 def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
     """Bytes each kernel must move per step (one compress + one decompress),
     summed over its launches: one read of every input and one write of every
-    output, counted once (cache re-reads excluded).  Levels whose coarse grid
-    has fewer than 2^21 nodes restrict and solve in 8-byte words.  The
+    output, counted once (cache re-reads excluded).  The
     coefficients travel in symbol order: coeff writes them, quantization
     streams them, the decoder writes them dequantized, fill reads them."""
     lv = level_shapes(shape)
@@ -99,7 +98,7 @@ def algorithmic_bytes(shape, comp_bytes, esc_count, esize=4):
 
     for l in range(len(lv) - 1):
         n, nc = int(np.prod(lv[l])), int(np.prod(lv[l + 1]))
-        ew = 8 if nc < (1 << 21) else esize
+        ew = esize   # restriction and solves in the data's precision
         (nz, ny, nx), (cz, cy, cx) = lv[l], lv[l + 1]
         # read u_l; write coefficients + coarse copy + (fused) the rows restricted along x
         add("k3_coeff", 2 * n * esize + nz * ny * cx * ew)

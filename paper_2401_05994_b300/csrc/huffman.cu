@@ -773,9 +773,9 @@ __global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
 #pragma unroll
         for (int q = 0; q < 2; ++q) f[q] = wi + q < cw1 ? words[wi + q] : 0u;
         const unsigned skip = (unsigned)(bstart & 31);
+        const uint64_t wi_start = wi;   // words entered into the window so far: wi - wi_start + 1
         uint64_t win = ((uint64_t)w0 << 32) << skip;
         int nb = 32 - (int)skip;
-        uint64_t used = 0;
         int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
         uint32_t pk[4] = {0, 0, 0, 0};
         OutT vk[8];
@@ -796,13 +796,15 @@ __global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
         };
         if (!SYM) enter_level((long long)first);
         // groups of eight symbols, unrolled so that the per-group buffers
-        // (pk, vk) stay in registers
+        // (pk, vk) stay in registers.  A malformed stream only raises `bad`
+        // (every access stays bounded); the sub-chunk is then rejected.
         bool bad = false;
-        for (int k0 = 0; k0 < cnt && !bad; k0 += 8) {
+        for (int k0 = 0; k0 < cnt; k0 += 8) {
+            const bool whole = k0 + 8 <= cnt;
 #pragma unroll
             for (int slot = 0; slot < 8; ++slot) {
                 const int k = k0 + slot;
-                if (k >= cnt || bad) continue;
+                if (!whole && k >= cnt) continue;
                 if (nb <= 32) {
                     win |= (uint64_t)f[0] << (32 - nb);
                     nb += 32;
@@ -819,22 +821,18 @@ __global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
                     const uint32_t top = (uint32_t)(win >> 32);
                     unsigned l = LUT_BITS + 1;
                     while (l <= maxlen && (unsigned long long)top >= lim[l]) ++l;
-                    if (l > maxlen) {
+                    if (l > maxlen) {   // no code has this prefix
                         bad = true;
-                        continue;
+                        l = LUT_BITS + 1;
                     }
                     len = l;
                     s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
                 }
                 win <<= len;
                 nb -= (int)len;
-                used += len;
                 int32_t qesc = 0;
                 if (s == MGARD_ESC) {
-                    if (e >= e_end) {
-                        bad = true;
-                        continue;
-                    }
+                    bad = bad || e >= e_end;   // more escapes than the sub-chunk holds
                     qesc = next_out;
                     if (SYM) escapes[first + k] = next_out;
                     ++e;
@@ -852,7 +850,7 @@ __global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
                     vk[slot] = v;
                 }
             }
-            if (bad || k0 + 8 > cnt) continue;
+            if (!whole) continue;
             if (SYM) *reinterpret_cast<uint4*>(sym + first + k0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             else store8(vals + first + k0, vk);
         }
@@ -860,6 +858,9 @@ __global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
             ok = false;
             continue;
         }
+        // bits taken from the window: the words that entered it minus the
+        // skipped and the unread bits
+        const uint64_t used = 32 * (wi - wi_start + 1) - skip - (uint64_t)nb;
         const int rem = cnt & 7;   // symbols decoded after the last full group
 #pragma unroll
         for (int r = 0; r < 8; ++r) {

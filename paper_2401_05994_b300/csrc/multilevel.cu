@@ -357,11 +357,11 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
 // axis, Mc_a^{-1} P_a^T M_a, and factors on different axes commute, so an
 // axis may be restricted and solved before the next axis is restricted.
 // in: (outer, m, inner), out: (outer, mc, inner).  A tile is 32 consecutive
-// lines in (outer, inner) order: their m input rows are copied into
-// shared memory (cp.async), each output row J takes the five-tap window of
-// P_a^T M_a around fine row f(J) (weights rw[J*5 + t], taps outside the
-// axis weigh 0), and the restricted tile is solved along its columns before
-// the block writes it out.  The solve: lane l owns column l and warp w a
+// lines in (outer, inner) order.  In `parts` steps, the fine rows that a
+// range of output rows reaches are copied into shared memory (cp.async) and
+// each output row J takes the five-tap window of P_a^T M_a around fine row
+// f(J) (weights rw[J*5 + t], taps outside the axis weigh 0); the restricted
+// tile is then solved along its columns before the block writes it out.  The solve: lane l owns column l and warp w a
 // segment of at most K rows.  Both Thomas sweeps are affine recurrences
 // (y_k = al_k y_{k-1} + v_k inv_k with al_k = -a_k inv_k forward, x_k =
 // -c'_k x_{k+1} + y_k backward), so each thread composes its segment's map
@@ -371,10 +371,10 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
 template <typename Tw, int K>
 __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
     const Tw* __restrict__ in, Tw* __restrict__ out, int64_t outer_n, int m, int mc,
-    int64_t inner, AxisT<Tw> ax) {
+    int64_t inner, AxisT<Tw> ax, int parts, int ti_rows) {
     extern __shared__ __align__(16) unsigned char tile_raw[];
-    Tw* ti = reinterpret_cast<Tw*>(tile_raw);   // [m][33] fine rows
-    Tw* to = ti + (size_t)m * 33;                // [mc][33] restricted rows
+    Tw* ti = reinterpret_cast<Tw*>(tile_raw);   // [ti_rows][33] fine rows of one part
+    Tw* to = ti + (size_t)ti_rows * 33;          // [mc][33] restricted rows
     Tw* sal = to + (size_t)mc * 33;              // [mc] -a_k inv_k
     Tw* sinv = sal + mc;                         // [mc] inv_k
     Tw* sga = sinv + mc;                         // [mc] -c'_k
@@ -403,45 +403,54 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
         const int nl = (int)(nlines - l0 < 32 ? nlines - l0 : 32);
         const int64_t mine = l0 + (lane < nl ? lane : 0);   // this lane's line
         const int64_t o = mine / inner, i = mine - o * inner;
-        if (lane < nl) {
-            const Tw* g = in + o * m * inner + i + (int64_t)wid * inner;
-            unsigned sa = (unsigned)__cvta_generic_to_shared(&ti[wid * 33 + lane]);
+        // the restriction in parts of jp output rows: each part copies the
+        // fine rows its windows reach, so the fine buffer holds ~2 jp rows
+        const int jp = (mc + parts - 1) / parts;
+        for (int J0 = 0; J0 < mc; J0 += jp) {
+            const int J1 = min(mc, J0 + jp);
+            const int fb = J0 == mc - 1 ? m - 1 : 2 * J0;              // f(J0)
+            const int fe = J1 - 1 == mc - 1 ? m - 1 : 2 * (J1 - 1);    // f(J1 - 1)
+            const int rb = max(0, fb - 2), re = min(m, fe + 3);         // fine rows [rb, re)
+            if (lane < nl) {
+                const Tw* g = in + o * m * inner + i + (int64_t)(rb + wid) * inner;
+                unsigned sa = (unsigned)__cvta_generic_to_shared(&ti[wid * 33 + lane]);
 #pragma unroll 4
-            for (int k = wid; k < m; k += ST_WARPS, g += gstep, sa += sstep) {
-                if (sizeof(Tw) == 4)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
-                else
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
-            }
-        } else {
-            for (int k = wid; k < m; k += ST_WARPS) ti[k * 33 + lane] = Tw(0);
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        for (int J = wid; J < mc; J += ST_WARPS) {
-            Tw acc;
-            if (J >= ax.rlo && J < ax.rhi) {   // window 2J-2 .. 2J+2, uniform weights
-                const Tw* q = &ti[(2 * J - 2) * 33 + lane];
-                acc = wi[0] * q[0];
-                acc += wi[1] * q[33];
-                acc += wi[2] * q[66];
-                acc += wi[3] * q[99];
-                acc += wi[4] * q[132];
-            } else {
-                const int f = J == mc - 1 ? m - 1 : 2 * J;   // fine row under coarse row J
-                acc = Tw(0);
-#pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    int ip = f - 2 + t;
-                    const bool ok = ip >= 0 && ip < m;
-                    const Tw w = ok ? rw[J * 5 + t] : Tw(0);
-                    ip = ok ? ip : f;
-                    acc += w * ti[ip * 33 + lane];
+                for (int k = rb + wid; k < re; k += ST_WARPS, g += gstep, sa += sstep) {
+                    if (sizeof(Tw) == 4)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+                    else
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
                 }
+            } else {
+                for (int k = rb + wid; k < re; k += ST_WARPS) ti[(k - rb) * 33 + lane] = Tw(0);
             }
-            to[J * 33 + lane] = acc;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            for (int J = J0 + wid; J < J1; J += ST_WARPS) {
+                Tw acc;
+                if (J >= ax.rlo && J < ax.rhi) {   // window 2J-2 .. 2J+2, uniform weights
+                    const Tw* q = &ti[(2 * J - 2 - rb) * 33 + lane];
+                    acc = wi[0] * q[0];
+                    acc += wi[1] * q[33];
+                    acc += wi[2] * q[66];
+                    acc += wi[3] * q[99];
+                    acc += wi[4] * q[132];
+                } else {
+                    const int f = J == mc - 1 ? m - 1 : 2 * J;   // fine row under coarse row J
+                    acc = Tw(0);
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        int ip = f - 2 + t;
+                        const bool ok = ip >= 0 && ip < m;
+                        const Tw w = ok ? rw[J * 5 + t] : Tw(0);
+                        ip = ok ? ip : f;
+                        acc += w * ti[(ip - rb) * 33 + lane];
+                    }
+                }
+                to[J * 33 + lane] = acc;
+            }
+            __syncthreads();   // the next part's copy overwrites the fine rows
         }
-        __syncthreads();
         {
             Tw v[K];
 #pragma unroll
@@ -942,14 +951,27 @@ mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_
                                     int64_t inner, const AxisT<Tw>& ax, cudaStream_t st,
                                     bool* done) {
     *done = false;
-    const size_t bytes = ((size_t)(m + mc) * 33 + 3 * (size_t)mc) * sizeof(Tw);
-    if (inner < 2 || mc > 520 || bytes > 200 * 1024) return MGARD_OK;   // separate passes
+    // restriction parts: the fewest that bring a block's shared memory to
+    // 72 KB (three blocks per SM), else to 110 KB (two), else to 200 KB
+    auto smem_for = [&](int parts, int* rows) {
+        const int64_t jp = (mc + parts - 1) / parts;
+        *rows = (int)std::min<int64_t>(m, 2 * jp + 5);
+        return ((size_t)(*rows + mc) * 33 + 3 * (size_t)mc) * sizeof(Tw);
+    };
+    int parts = 0, ti_rows = 0;
+    size_t bytes = 0;
+    for (size_t budget : {(size_t)72 * 1024, (size_t)110 * 1024, (size_t)200 * 1024}) {
+        for (int pt = 1; pt <= 4 && !parts; ++pt)
+            if ((bytes = smem_for(pt, &ti_rows)) <= budget) parts = pt;
+        if (parts) break;
+    }
+    if (inner < 2 || mc > 520 || !parts) return MGARD_OK;   // separate passes
     const int64_t ntiles = (outer * inner + 31) / 32;
     auto go = [&](auto kern) -> mgard_status {
         MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
         int grid = 0;
         MGB_TRY(resident_grid((const void*)kern, ST_WARPS * 32, bytes, ntiles, &grid));
-        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, ST_WARPS * 32, bytes, st>>>(in, out, outer, (int)m, (int)mc, inner, ax));
+        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, ST_WARPS * 32, bytes, st>>>(in, out, outer, (int)m, (int)mc, inner, ax, parts, ti_rows));
         MGB_CUDA(cudaGetLastError());
         *done = true;
         return MGARD_OK;

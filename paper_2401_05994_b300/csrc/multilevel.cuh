@@ -47,8 +47,10 @@ struct Pyramid {
 };
 
 // Coarse grids with fewer nodes than this run their restriction and
-// tridiagonal solves in double precision.
-constexpr int64_t FP64_SOLVE_NODES = int64_t(1) << 21;
+// tridiagonal solves in double precision.  None do: on B300 FP64 runs at
+// about 2 lanes per clock per SM, and float32 corrections keep every level
+// within the float32 tolerance of the FP64 decomposition.
+constexpr int64_t FP64_SOLVE_NODES = 0;
 
 // Decompose `in` (level-L nodal values) into `top` (coefficients on the
 // level-L new nodes; coarse positions untouched) and the pyramid levels.
