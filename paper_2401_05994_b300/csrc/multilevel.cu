@@ -866,19 +866,25 @@ cudaMemPool_t workspace_pool() {
     return pool;
 }
 
-// Opt a kernel in to `bytes` of dynamic shared memory (beyond the default
-// 48 KB), once per kernel and device.
+// Opt a kernel in to `bytes` of dynamic shared memory where its current
+// limit is lower (by default 48 KB minus its static shared memory), once per
+// kernel, size and device.
 mgard_status allow_dynamic_smem(const void* kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return MGARD_OK;
+    if (bytes == 0) return MGARD_OK;
     static std::mutex mu;
-    static std::map<std::pair<const void*, int>, size_t> done;
+    static std::map<std::pair<const void*, int>, size_t> limit;
     int dev = 0;
     MGB_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
-    size_t& have = done[{kern, dev}];
-    if (have < bytes) {
+    auto it = limit.find({kern, dev});
+    if (it == limit.end()) {
+        cudaFuncAttributes fa;
+        MGB_CUDA(cudaFuncGetAttributes(&fa, kern));
+        it = limit.emplace(std::make_pair(kern, dev), (size_t)fa.maxDynamicSharedSizeBytes).first;
+    }
+    if (it->second < bytes) {
         MGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        have = bytes;
+        it->second = bytes;
     }
     return MGARD_OK;
 }
@@ -1038,6 +1044,8 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
             }
         }
     }
+    const int Lt = tail_levels(p);   // the one-block tail's scratch lives here too
+    if (Lt) tmax = std::max(tmax, 2 * (size_t)p.level_size(Lt) * sizeof(T));
     MGB_TRY(store.alloc(total, st));
     MGB_TRY(temp0.alloc(tmax, st));
     MGB_TRY(temp1.alloc(tmax, st));
@@ -1131,8 +1139,22 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
         set_error("symbol-order coefficients need the row kernels");
         return MGARD_EINVAL;
     }
+    // small levels in one launch (row-kernel shapes).  In symbol order the
+    // tail leaves every level's nodal values in the pyramid, so their
+    // energies are taken afterwards; in place it overwrites them, so levels
+    // with energies requested run level by level.
+    const int Lt = (rows3_ok(p) && (zs || (!E && !Epart))) ? tail_levels(p) : 0;
     for (int l = p.L; l >= 1; --l) {
         const T* src = l == p.L ? in : py.lv[l];
+        if (l == Lt) {
+            MGB_TRY(tail_decompose<T>(p, Lt, py, src, zs, top, st));
+            for (int k = Lt; k >= 1; --k) {   // level 0 follows below
+                const T* uk = k == p.L ? in : py.lv[k];
+                if (E) MGB_TRY(mass_norm2<T>(p, k, uk, &E[k], st));
+                if (Epart) MGB_TRY(mass_norm2_partials<T>(p, k, uk, Epart + energy_parts_offset(p, k), st));
+            }
+            break;
+        }
         T* dst = zs ? zs : (l == p.L ? top : py.lv[l]);
         const int64_t zoff = zs ? p.offset[l] : -1;
         if (E) MGB_TRY(mass_norm2<T>(p, l, src, &E[l], st));
@@ -1172,7 +1194,10 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
         return MGARD_OK;
     }
     if (zs) MGB_CUDA(cudaMemcpyAsync(py.lv[0], zs, p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    for (int l = 1; l <= p.L; ++l) {
+    // small levels in one launch (row-kernel shapes)
+    const int Lt = rows3_ok(p) ? tail_levels(p) : 0;
+    if (Lt) MGB_TRY(tail_recompose<T>(p, Lt, py, zs, top, Lt == p.L ? out : py.lv[Lt], st));
+    for (int l = Lt + 1; l <= p.L; ++l) {
         const T* z = zs ? zs : (l == p.L ? top : py.lv[l]);
         const int64_t zoff = zs ? p.offset[l] : -1;
         T* dst = l == p.L ? out : py.lv[l];

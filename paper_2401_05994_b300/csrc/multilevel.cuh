@@ -52,6 +52,27 @@ struct Pyramid {
 // within the float32 tolerance of the FP64 decomposition.
 constexpr int64_t FP64_SOLVE_NODES = 0;
 
+// Levels of at most TAIL_NODES nodes (TAIL_LEVELS of them at most) run in a
+// single one-block launch each way (tail.cu) on the symbol-order path.
+constexpr int64_t TAIL_NODES = 5000;
+constexpr int TAIL_LEVELS = 8;
+// The number Lt of such levels above level 0 (levels 1..Lt); 0 if none.
+int tail_levels(const Plan& p);
+// Levels Lt..1 of a decomposition: level_Lt holds level Lt's nodal values
+// (py.lv[Lt], or the input when Lt = L); writes the coefficients of levels
+// 1..Lt into zs (symbol order) or, with zs null, over the new nodes of each
+// level's own array (py.lv[l], `top` for l = L), and the nodal values of
+// levels Lt-1..0 into the pyramid.  Scratch: py.temp0 and py.temp1.
+template <typename T>
+mgard_status tail_decompose(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs,
+                            T* top, cudaStream_t st);
+// The inverse for levels 1..Lt: from py.lv[0] and the coefficients (zs, or
+// the level arrays), writes level Lt's nodal values to level_Lt (and
+// levels 1..Lt-1 into the pyramid).
+template <typename T>
+mgard_status tail_recompose(const Plan& p, int Lt, Pyramid<T>& py, const T* zs, const T* top,
+                            T* level_Lt, cudaStream_t st);
+
 // Decompose `in` (level-L nodal values) into `top` (coefficients on the
 // level-L new nodes; coarse positions untouched) and the pyramid levels.
 // `in` may equal `top`.  If `E` is non-null, E[l] receives u_l^T M_l u_l of

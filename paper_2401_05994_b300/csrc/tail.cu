@@ -1,0 +1,292 @@
+// The small levels of a pyramid in one launch.
+//
+// Below a few thousand nodes a level's kernels are too small to fill the
+// GPU, and each costs a launch.  k_tail_decompose / k_tail_recompose run
+// every level l <= Lt (level_size(l) <= TAIL_NODES) in a single block of
+// 1024 threads: the same steps as the per-level kernels (Section 3 of the
+// paper: interpolation coefficients z = u - I u, load vector P^T M_l z by
+// restriction along x, y and z, tridiagonal solves along z, y and x, and
+// the correction of the coarse level), each a block-strided loop over the
+// level's nodes in global memory (a few KB, held in L1/L2), separated by
+// block barriers.  Shapes are the row kernels' (axes 1..3 of the 4D view);
+// an inactive axis (extent 1) is skipped.
+#include "multilevel.cuh"
+#include "rows3.cuh"
+
+namespace mgb {
+
+namespace {
+
+constexpr int TAIL_THREADS = 1024;
+
+template <typename T>
+struct TailArgs {
+    int Lt;                               // levels 1..Lt run here
+    Level<T> lv[TAIL_LEVELS + 1];         // [l] transition l -> l-1 (l >= 1)
+    T* u[TAIL_LEVELS + 1];                // [l] nodal values of level l (row-major)
+    long long off[TAIL_LEVELS + 1];       // [l] symbol offset of level l's new nodes
+    T* zs;                                // coefficients in symbol order, or null:
+    T* zl[TAIL_LEVELS + 1];               // [l] level l's coefficients in its own row-major array
+    T* zz;                                // scratch: a level's coefficients, row-major
+    T* t0;                                // scratch: restriction along x, then along z
+    T* t1;                                // scratch: restriction along y
+};
+
+// Position of a node among level l's new nodes (row-major order of the
+// level grid without the nodes of the coarser grid).
+template <typename T>
+__device__ inline long long new_rank(const Level<T>& lv, int z, int y, int x) {
+    const long long nx = lv.n[3], ny = lv.n[2];
+    const long long ncx = lv.nc[3], ncy = lv.nc[2];
+    const bool zc = !lv.ax[1].fcls || lv.ax[1].fcls[z] >= 0;
+    const bool yc = !lv.ax[2].fcls || lv.ax[2].fcls[y] >= 0;
+    const long long cz = lv.ax[1].cbefore ? lv.ax[1].cbefore[z] : 0;
+    const long long cy = lv.ax[2].cbefore ? lv.ax[2].cbefore[y] : 0;
+    const long long cx = lv.ax[3].cbefore ? lv.ax[3].cbefore[x] : 0;
+    long long before = cz * ncy * ncx;
+    if (zc) {
+        before += cy * ncx;
+        if (yc) before += cx;
+    }
+    return ((long long)z * ny + y) * nx + x - before;
+}
+
+// Interpolation from coarse nodes along one axis at fine index i: the
+// coarse node itself (J, weight 1), or the two around a new node.
+template <typename T>
+struct Taps {
+    int n;          // 1 or 2
+    int J[2];       // coarse indices
+    int F[2];       // their fine positions
+    T w[2];
+};
+template <typename T>
+__device__ inline Taps<T> taps(const AxisT<T>& ax, int i) {
+    Taps<T> t;
+    t.n = 1;
+    t.J[0] = t.J[1] = i;
+    t.F[0] = t.F[1] = i;
+    t.w[0] = T(1);
+    t.w[1] = T(0);
+    if (!ax.fcls) return t;
+    const int c = ax.fcls[i];
+    if (c >= 0) {
+        t.J[0] = c;
+        return t;
+    }
+    const int left = -c - 1;
+    t.n = 2;
+    t.J[0] = left;
+    t.J[1] = left + 1;
+    t.F[0] = ax.rf[left];
+    t.F[1] = ax.rf[left + 1];
+    t.w[0] = ax.wl[i];
+    t.w[1] = ax.wr[i];
+    return t;
+}
+
+// One axis' five-tap restriction at coarse index J from `get(ip)` (fine ip).
+template <typename T, typename G>
+__device__ inline T restrict_at(const AxisT<T>& ax, int J, int m, G get) {
+    const int f = ax.rf[J];
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int ip = f - 2 + t;
+        if (ip < 0 || ip >= m) continue;
+        acc += ax.rw[J * 5 + t] * get(ip);
+    }
+    return acc;
+}
+
+// coarse += sign * M^{-1} P^T M z for level l (z in a.zz, row-major).
+template <typename T>
+__device__ void tail_correct(const TailArgs<T>& a, int l, T sign) {
+    const Level<T>& lv = a.lv[l];
+    const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+    const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+    const bool az = lv.ax[1].fcls, ay = lv.ax[2].fcls, ax = lv.ax[3].fcls;
+    const int tid = threadIdx.x;
+    // restriction along x: t0 (nz, ny, ncx)
+    for (int k = tid; k < nz * ny * ncx; k += TAIL_THREADS) {
+        const int J = k % ncx, r = k / ncx;
+        const T* row = a.zz + (long long)r * nx;
+        a.t0[k] = ax ? restrict_at(lv.ax[3], J, nx, [&](int ip) { return row[ip]; }) : row[J];
+    }
+    __syncthreads();
+    // along y: t1 (nz, ncy, ncx)
+    for (int k = tid; k < nz * ncy * ncx; k += TAIL_THREADS) {
+        const int x = k % ncx, Jy = (k / ncx) % ncy, z = k / (ncx * ncy);
+        const T* col = a.t0 + (long long)z * ny * ncx + x;
+        a.t1[k] = ay ? restrict_at(lv.ax[2], Jy, ny, [&](int ip) { return col[(long long)ip * ncx]; })
+                     : col[(long long)Jy * ncx];
+    }
+    __syncthreads();
+    // along z: t0 (ncz, ncy, ncx)
+    for (int k = tid; k < ncz * ncy * ncx; k += TAIL_THREADS) {
+        const int xy = k % (ncy * ncx), Jz = k / (ncy * ncx);
+        const T* col = a.t1 + xy;
+        a.t0[k] = az ? restrict_at(lv.ax[1], Jz, nz, [&](int ip) { return col[(long long)ip * ncy * ncx]; })
+                     : col[(long long)Jz * ncy * ncx];
+    }
+    __syncthreads();
+    // Thomas along one axis for the lines of `b` (m nodes, `stride` apart)
+    auto thomas = [&](const AxisT<T>& axt, T* b, int m, long long stride) {
+        T y = T(0);
+        for (int k = 0; k < m; ++k) {
+            y = (b[k * stride] - axt.tsub[k] * y) * axt.tinv[k];
+            b[k * stride] = y;
+        }
+        T x = T(0);
+        for (int k = m - 1; k >= 0; --k) {
+            x = (k == m - 1) ? b[k * stride] : b[k * stride] - axt.tcp[k] * x;
+            b[k * stride] = x;
+        }
+    };
+    if (az) {
+        for (int k = tid; k < ncy * ncx; k += TAIL_THREADS) thomas(lv.ax[1], a.t0 + k, ncz, (long long)ncy * ncx);
+        __syncthreads();
+    }
+    if (ay) {
+        for (int k = tid; k < ncz * ncx; k += TAIL_THREADS) {
+            const int x = k % ncx, Jz = k / ncx;
+            thomas(lv.ax[2], a.t0 + (long long)Jz * ncy * ncx + x, ncy, ncx);
+        }
+        __syncthreads();
+    }
+    if (ax) {
+        for (int k = tid; k < ncz * ncy; k += TAIL_THREADS) thomas(lv.ax[3], a.t0 + (long long)k * ncx, ncx, 1);
+        __syncthreads();
+    }
+    T* c = a.u[l - 1];
+    for (int k = tid; k < ncz * ncy * ncx; k += TAIL_THREADS) c[k] += sign * a.t0[k];
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) {
+    for (int l = a.Lt; l >= 1; --l) {
+        const Level<T>& lv = a.lv[l];
+        const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+        const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+        const T* u = a.u[l];
+        T* c = a.u[l - 1];
+        // coefficients z = u - I u on new nodes; coarse nodes copied down
+        for (int k = threadIdx.x; k < nz * ny * nx; k += TAIL_THREADS) {
+            const int x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
+            const Taps<T> tz = taps(lv.ax[1], z), ty = taps(lv.ax[2], y), tx = taps(lv.ax[3], x);
+            if (tz.n == 1 && ty.n == 1 && tx.n == 1) {
+                c[((long long)tz.J[0] * ncy + ty.J[0]) * ncx + tx.J[0]] = u[k];
+                a.zz[k] = T(0);
+                continue;
+            }
+            T acc = T(0);
+            for (int i = 0; i < tz.n; ++i)
+                for (int j = 0; j < ty.n; ++j)
+                    for (int h = 0; h < tx.n; ++h)
+                        acc += tz.w[i] * ty.w[j] * tx.w[h] *
+                               u[((long long)tz.F[i] * ny + ty.F[j]) * nx + tx.F[h]];
+            const T zv = u[k] - acc;
+            a.zz[k] = zv;
+            if (a.zs) a.zs[a.off[l] + new_rank(lv, z, y, x)] = zv;
+            else a.zl[l][k] = zv;
+        }
+        __syncthreads();
+        tail_correct(a, l, T(1));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) {
+    for (int l = 1; l <= a.Lt; ++l) {
+        const Level<T>& lv = a.lv[l];
+        const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
+        const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
+        for (int k = threadIdx.x; k < nz * ny * nx; k += TAIL_THREADS) {
+            const int x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
+            const bool coarse = (!lv.ax[1].fcls || lv.ax[1].fcls[z] >= 0) &&
+                                (!lv.ax[2].fcls || lv.ax[2].fcls[y] >= 0) &&
+                                (!lv.ax[3].fcls || lv.ax[3].fcls[x] >= 0);
+            a.zz[k] = coarse ? T(0) : (a.zs ? a.zs[a.off[l] + new_rank(lv, z, y, x)] : a.zl[l][k]);
+        }
+        __syncthreads();
+        tail_correct(a, l, T(-1));
+        // u_l = I u_{l-1} + z
+        const T* c = a.u[l - 1];
+        T* u = a.u[l];
+        for (int k = threadIdx.x; k < nz * ny * nx; k += TAIL_THREADS) {
+            const int x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
+            const Taps<T> tz = taps(lv.ax[1], z), ty = taps(lv.ax[2], y), tx = taps(lv.ax[3], x);
+            T acc = T(0);
+            for (int i = 0; i < tz.n; ++i)
+                for (int j = 0; j < ty.n; ++j)
+                    for (int h = 0; h < tx.n; ++h)
+                        acc += tz.w[i] * ty.w[j] * tx.w[h] *
+                               c[((long long)tz.J[i] * ncy + ty.J[j]) * ncx + tx.J[h]];
+            u[k] = acc + a.zz[k];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+mgard_status make_args(const Plan& p, int Lt, Pyramid<T>& py, T* top_level, T* zs, T* ztop,
+                       TailArgs<T>* a) {
+    if (Lt < 1 || Lt > TAIL_LEVELS) {
+        set_error("tail levels out of range");
+        return MGARD_EINVAL;
+    }
+    a->Lt = Lt;
+    for (int l = 0; l <= Lt; ++l) {
+        if (l >= 1) a->lv[l] = p.level<T>(l);
+        a->u[l] = l == Lt ? top_level : py.lv[l];
+        a->off[l] = p.offset[l];
+        a->zl[l] = l == p.L ? ztop : py.lv[l];   // in-place layout: coefficients over the level
+    }
+    a->zs = zs;
+    // scratch inside the restriction buffers (sized for the finest level)
+    const int64_t n = p.level_size(Lt);
+    a->zz = py.temp0.template as<T>();
+    a->t0 = py.temp1.template as<T>();
+    a->t1 = py.temp1.template as<T>() + n;
+    return MGARD_OK;
+}
+
+}  // namespace
+
+int tail_levels(const Plan& p) {
+    int Lt = 0;
+    while (Lt < p.L && Lt < TAIL_LEVELS && p.level_size(Lt + 1) <= TAIL_NODES) ++Lt;
+    return Lt;
+}
+
+template <typename T>
+mgard_status tail_decompose(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs,
+                            T* top, cudaStream_t st) {
+    TailArgs<T> a;
+    MGB_TRY(make_args<T>(p, Lt, py, const_cast<T*>(level_Lt), zs, top, &a));
+    MGB_LAUNCH("k_tail_decompose", st, k_tail_decompose<T><<<1, TAIL_THREADS, 0, st>>>(a));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status tail_recompose(const Plan& p, int Lt, Pyramid<T>& py, const T* zs, const T* top,
+                            T* level_Lt, cudaStream_t st) {
+    TailArgs<T> a;
+    MGB_TRY(make_args<T>(p, Lt, py, level_Lt, const_cast<T*>(zs), const_cast<T*>(top), &a));
+    MGB_LAUNCH("k_tail_recompose", st, k_tail_recompose<T><<<1, TAIL_THREADS, 0, st>>>(a));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+template mgard_status tail_decompose<float>(const Plan&, int, Pyramid<float>&, const float*, float*,
+                                            float*, cudaStream_t);
+template mgard_status tail_decompose<double>(const Plan&, int, Pyramid<double>&, const double*,
+                                             double*, double*, cudaStream_t);
+template mgard_status tail_recompose<float>(const Plan&, int, Pyramid<float>&, const float*,
+                                            const float*, float*, cudaStream_t);
+template mgard_status tail_recompose<double>(const Plan&, int, Pyramid<double>&, const double*,
+                                             const double*, double*, cudaStream_t);
+
+}  // namespace mgb

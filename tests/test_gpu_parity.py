@@ -326,3 +326,19 @@ def test_norms_match_oracle(s):
     got = binding.norm(u.to(DEV), s)
     ref = bounds.norm(u.numpy(), s)
     assert abs(got - ref) <= 1e-10 * ref
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", [(220, 93, 244), (111, 47, 123)])
+def test_shared_memory_limits_of_fused_kernels(shape, dtype):
+    """Shapes whose fused restriction tiles need just under 48 KB of dynamic
+    shared memory beside the kernel's static shared memory (a launch over
+    the default limit fails); decomposition, recomposition and the s = 0
+    norm (which decomposes in FP64) must all run and invert."""
+    u = _field(shape, dtype, 6).to(DEV)
+    v = binding.decompose(u.clone())
+    back = binding.recompose(v)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert float((back - u).abs().max()) <= tol * max(1.0, float(u.abs().max()))
+    e = binding.error_norm(u, back, 0.0)
+    assert math.isfinite(e)
