@@ -52,6 +52,10 @@ struct Pyramid {
 // within the float32 tolerance of the FP64 decomposition.
 constexpr int64_t FP64_SOLVE_NODES = 0;
 
+// Opt a kernel in to `bytes` of dynamic shared memory where its current
+// limit (48 KB minus its static shared memory by default) is lower.
+mgard_status allow_dynamic_smem(const void* kern, size_t bytes);
+
 // Levels of at most TAIL_NODES nodes (TAIL_LEVELS of them at most) run in a
 // single one-block launch each way (tail.cu) on the symbol-order path.
 constexpr int64_t TAIL_NODES = 5000;

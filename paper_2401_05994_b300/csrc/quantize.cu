@@ -65,19 +65,18 @@ __device__ inline NodeInfo node_info(const QLevel& q, const int64_t* i) {
 
 __device__ inline void quantize_value(float c, float inv_w, WidthSplit ws, double w, int& sym,
                                       int32_t& qo, unsigned& st) {
-    if (!isfinite(c)) {
-        st |= ST_NONFINITE;
-        sym = MGARD_ESC;
-        qo = 0;
-        return;
-    }
     const float x = __fmul_rn(c, inv_w);
     const float q = rintf(x);
-    if (fabsf(q) < (float)RADIUS) {
+    if (fabsf(q) < (float)RADIUS) {   // false for NaN and +-Inf, which are tested below
         sym = (int)q + RADIUS;
         return;
     }
     sym = MGARD_ESC;
+    if (!isfinite(c)) {
+        st |= ST_NONFINITE;
+        qo = 0;
+        return;
+    }
     if (fabsf(q) < (float)F32_EXACT) {
         qo = (int32_t)q;
         return;
@@ -289,11 +288,13 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
             for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? zs[i0 + k] : T(0);
         }
         uint32_t packed[4] = {0, 0, 0, 0};
+        // the usual group lies inside one level and inside the array
+        const bool plain = full && i0 + 8 <= lend;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int64_t i = i0 + k;
-            if (i >= n) break;
-            if (i >= lend) {
+            if (!plain && i >= n) break;
+            if (!plain && i >= lend) {
                 while (l < L && i >= offs[l + 1]) ++l;
                 lend = offs[l + 1];
                 wl = ws[l];

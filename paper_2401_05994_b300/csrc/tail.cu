@@ -7,9 +7,14 @@
 // paper: interpolation coefficients z = u - I u, load vector P^T M_l z by
 // restriction along x, y and z, tridiagonal solves along z, y and x, and
 // the correction of the coarse level), each a block-strided loop over the
-// level's nodes in global memory (a few KB, held in L1/L2), separated by
-// block barriers.  Shapes are the row kernels' (axes 1..3 of the 4D view);
-// an inactive axis (extent 1) is skipped.
+// level's nodes, separated by block barriers.  Every level's nodal values
+// and the scratch arrays live in shared memory (a few tens of KB); global
+// memory sees the top level's values coming in, the coefficients going out
+// and the pyramid's arrays written back.  Shapes are the row kernels' (axes
+// 1..3 of the 4D view); an inactive axis (extent 1) is skipped.
+#include <algorithm>
+#include <cstring>
+
 #include "multilevel.cuh"
 #include "rows3.cuh"
 
@@ -23,13 +28,20 @@ template <typename T>
 struct TailArgs {
     int Lt;                               // levels 1..Lt run here
     Level<T> lv[TAIL_LEVELS + 1];         // [l] transition l -> l-1 (l >= 1)
-    T* u[TAIL_LEVELS + 1];                // [l] nodal values of level l (row-major)
+    T* g[TAIL_LEVELS + 1];                // [l] level l's array in global memory
+    int size[TAIL_LEVELS + 1];            // [l] nodes of level l
     long long off[TAIL_LEVELS + 1];       // [l] symbol offset of level l's new nodes
     T* zs;                                // coefficients in symbol order, or null:
     T* zl[TAIL_LEVELS + 1];               // [l] level l's coefficients in its own row-major array
-    T* zz;                                // scratch: a level's coefficients, row-major
-    T* t0;                                // scratch: restriction along x, then along z
-    T* t1;                                // scratch: restriction along y
+    int su[TAIL_LEVELS + 1];              // shared-memory offsets (elements): level l's values,
+    int szz, st0, st1;                    // a level's coefficients, restriction scratch
+};
+
+// Views of the shared-memory arrays.
+template <typename T>
+struct TailMem {
+    T* u[TAIL_LEVELS + 1];
+    T *zz, *t0, *t1;
 };
 
 // Position of a node among level l's new nodes (row-major order of the
@@ -99,10 +111,10 @@ __device__ inline T restrict_at(const AxisT<T>& ax, int J, int m, G get) {
     return acc;
 }
 
-// coarse += sign * M^{-1} P^T M z for level l (z in a.zz, row-major).
+// coarse += sign * M^{-1} P^T M z for level l (z in m.zz, row-major).
 template <typename T>
-__device__ void tail_correct(const TailArgs<T>& a, int l, T sign) {
-    const Level<T>& lv = a.lv[l];
+__device__ void tail_correct(const TailArgs<T>& ga, const TailMem<T>& a, int l, T sign) {
+    const Level<T>& lv = ga.lv[l];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
     const int ncz = (int)lv.nc[1], ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
     const bool az = lv.ax[1].fcls, ay = lv.ax[2].fcls, ax = lv.ax[3].fcls;
@@ -164,20 +176,35 @@ __device__ void tail_correct(const TailArgs<T>& a, int l, T sign) {
 }
 
 template <typename T>
+__device__ inline TailMem<T> tail_mem(const TailArgs<T>& a) {
+    extern __shared__ __align__(16) unsigned char tail_raw[];
+    T* base = reinterpret_cast<T*>(tail_raw);
+    TailMem<T> m;
+    for (int l = 0; l <= TAIL_LEVELS; ++l) m.u[l] = base + a.su[l];
+    m.zz = base + a.szz;
+    m.t0 = base + a.st0;
+    m.t1 = base + a.st1;
+    return m;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) {
+    const TailMem<T> m = tail_mem(a);
+    for (int k = threadIdx.x; k < a.size[a.Lt]; k += TAIL_THREADS) m.u[a.Lt][k] = a.g[a.Lt][k];
+    __syncthreads();
     for (int l = a.Lt; l >= 1; --l) {
         const Level<T>& lv = a.lv[l];
         const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
         const int ncy = (int)lv.nc[2], ncx = (int)lv.nc[3];
-        const T* u = a.u[l];
-        T* c = a.u[l - 1];
+        const T* u = m.u[l];
+        T* c = m.u[l - 1];
         // coefficients z = u - I u on new nodes; coarse nodes copied down
         for (int k = threadIdx.x; k < nz * ny * nx; k += TAIL_THREADS) {
             const int x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
             const Taps<T> tz = taps(lv.ax[1], z), ty = taps(lv.ax[2], y), tx = taps(lv.ax[3], x);
             if (tz.n == 1 && ty.n == 1 && tx.n == 1) {
                 c[((long long)tz.J[0] * ncy + ty.J[0]) * ncx + tx.J[0]] = u[k];
-                a.zz[k] = T(0);
+                m.zz[k] = T(0);
                 continue;
             }
             T acc = T(0);
@@ -187,17 +214,27 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) 
                         acc += tz.w[i] * ty.w[j] * tx.w[h] *
                                u[((long long)tz.F[i] * ny + ty.F[j]) * nx + tx.F[h]];
             const T zv = u[k] - acc;
-            a.zz[k] = zv;
+            m.zz[k] = zv;
             if (a.zs) a.zs[a.off[l] + new_rank(lv, z, y, x)] = zv;
             else a.zl[l][k] = zv;
         }
         __syncthreads();
-        tail_correct(a, l, T(1));
+        tail_correct(a, m, l, T(1));
+    }
+    // the pyramid's arrays: every level's nodal values in symbol order (the
+    // caller may take level energies from them); in place only level 0,
+    // whose array is not also a coefficient array
+    for (int l = 0; l < a.Lt; ++l) {
+        if (!a.zs && l > 0) break;
+        for (int k = threadIdx.x; k < a.size[l]; k += TAIL_THREADS) a.g[l][k] = m.u[l][k];
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) {
+    const TailMem<T> m = tail_mem(a);
+    for (int k = threadIdx.x; k < a.size[0]; k += TAIL_THREADS) m.u[0][k] = a.g[0][k];
+    __syncthreads();
     for (int l = 1; l <= a.Lt; ++l) {
         const Level<T>& lv = a.lv[l];
         const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
@@ -207,13 +244,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) 
             const bool coarse = (!lv.ax[1].fcls || lv.ax[1].fcls[z] >= 0) &&
                                 (!lv.ax[2].fcls || lv.ax[2].fcls[y] >= 0) &&
                                 (!lv.ax[3].fcls || lv.ax[3].fcls[x] >= 0);
-            a.zz[k] = coarse ? T(0) : (a.zs ? a.zs[a.off[l] + new_rank(lv, z, y, x)] : a.zl[l][k]);
+            m.zz[k] = coarse ? T(0) : (a.zs ? a.zs[a.off[l] + new_rank(lv, z, y, x)] : a.zl[l][k]);
         }
         __syncthreads();
-        tail_correct(a, l, T(-1));
+        tail_correct(a, m, l, T(-1));
         // u_l = I u_{l-1} + z
-        const T* c = a.u[l - 1];
-        T* u = a.u[l];
+        const T* c = m.u[l - 1];
+        T* u = m.u[l];
         for (int k = threadIdx.x; k < nz * ny * nx; k += TAIL_THREADS) {
             const int x = k % nx, y = (k / nx) % ny, z = k / (nx * ny);
             const Taps<T> tz = taps(lv.ax[1], z), ty = taps(lv.ax[2], y), tx = taps(lv.ax[3], x);
@@ -223,32 +260,47 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) 
                     for (int h = 0; h < tx.n; ++h)
                         acc += tz.w[i] * ty.w[j] * tx.w[h] *
                                c[((long long)tz.J[i] * ncy + ty.J[j]) * ncx + tx.J[h]];
-            u[k] = acc + a.zz[k];
+            u[k] = acc + m.zz[k];
         }
         __syncthreads();
     }
+    for (int k = threadIdx.x; k < a.size[a.Lt]; k += TAIL_THREADS) a.g[a.Lt][k] = m.u[a.Lt][k];
 }
 
 template <typename T>
 mgard_status make_args(const Plan& p, int Lt, Pyramid<T>& py, T* top_level, T* zs, T* ztop,
-                       TailArgs<T>* a) {
+                       TailArgs<T>* a, size_t* smem) {
     if (Lt < 1 || Lt > TAIL_LEVELS) {
         set_error("tail levels out of range");
         return MGARD_EINVAL;
     }
+    std::memset(a, 0, sizeof(*a));
     a->Lt = Lt;
+    int off = 0;
+    int64_t t0max = 1, t1max = 1;
     for (int l = 0; l <= Lt; ++l) {
-        if (l >= 1) a->lv[l] = p.level<T>(l);
-        a->u[l] = l == Lt ? top_level : py.lv[l];
+        a->g[l] = l == Lt ? top_level : py.lv[l];
+        a->size[l] = (int)p.level_size(l);
         a->off[l] = p.offset[l];
         a->zl[l] = l == p.L ? ztop : py.lv[l];   // in-place layout: coefficients over the level
+        a->su[l] = off;
+        off += a->size[l];
+        if (l >= 1) {
+            a->lv[l] = p.level<T>(l);
+            const Level<T>& lv = a->lv[l];
+            t0max = std::max<int64_t>(t0max, lv.n[1] * lv.n[2] * lv.nc[3]);
+            t1max = std::max<int64_t>(t1max, lv.n[1] * lv.nc[2] * lv.nc[3]);
+        }
     }
+    for (int l = Lt + 1; l <= TAIL_LEVELS; ++l) a->su[l] = 0;
+    a->szz = off;
+    off += a->size[Lt];
+    a->st0 = off;
+    off += (int)t0max;
+    a->st1 = off;
+    off += (int)t1max;
     a->zs = zs;
-    // scratch inside the restriction buffers (sized for the finest level)
-    const int64_t n = p.level_size(Lt);
-    a->zz = py.temp0.template as<T>();
-    a->t0 = py.temp1.template as<T>();
-    a->t1 = py.temp1.template as<T>() + n;
+    *smem = (size_t)off * sizeof(T);
     return MGARD_OK;
 }
 
@@ -264,8 +316,10 @@ template <typename T>
 mgard_status tail_decompose(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs,
                             T* top, cudaStream_t st) {
     TailArgs<T> a;
-    MGB_TRY(make_args<T>(p, Lt, py, const_cast<T*>(level_Lt), zs, top, &a));
-    MGB_LAUNCH("k_tail_decompose", st, k_tail_decompose<T><<<1, TAIL_THREADS, 0, st>>>(a));
+    size_t smem = 0;
+    MGB_TRY(make_args<T>(p, Lt, py, const_cast<T*>(level_Lt), zs, top, &a, &smem));
+    MGB_TRY(allow_dynamic_smem((const void*)k_tail_decompose<T>, smem));
+    MGB_LAUNCH("k_tail_decompose", st, k_tail_decompose<T><<<1, TAIL_THREADS, smem, st>>>(a));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -274,8 +328,10 @@ template <typename T>
 mgard_status tail_recompose(const Plan& p, int Lt, Pyramid<T>& py, const T* zs, const T* top,
                             T* level_Lt, cudaStream_t st) {
     TailArgs<T> a;
-    MGB_TRY(make_args<T>(p, Lt, py, level_Lt, const_cast<T*>(zs), const_cast<T*>(top), &a));
-    MGB_LAUNCH("k_tail_recompose", st, k_tail_recompose<T><<<1, TAIL_THREADS, 0, st>>>(a));
+    size_t smem = 0;
+    MGB_TRY(make_args<T>(p, Lt, py, level_Lt, const_cast<T*>(zs), const_cast<T*>(top), &a, &smem));
+    MGB_TRY(allow_dynamic_smem((const void*)k_tail_recompose<T>, smem));
+    MGB_LAUNCH("k_tail_recompose", st, k_tail_recompose<T><<<1, TAIL_THREADS, smem, st>>>(a));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
