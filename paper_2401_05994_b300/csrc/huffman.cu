@@ -27,22 +27,54 @@ namespace {
 constexpr int CB_THREADS = 1024;
 constexpr unsigned long long KEY_NONE = ~0ull;
 
-__device__ void bitonic_sort(unsigned long long* keys, int n) {
-    for (int k = 2; k <= n; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const unsigned long long a = keys[i], b = keys[ixj];
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[ixj] = a;
-                    }
-                }
+// Ascending sort of DICT 64-bit keys by the whole block (a multiple of 32
+// threads): every warp sorts runs of 32 keys in registers with a shuffle
+// bitonic network, then log2(DICT/32) merge passes double the run length,
+// each key placed by one binary search in the partner run (ties: the left
+// run first, so equal keys keep their order).  `tmp` holds DICT keys; the
+// result ends in `keys`.  Ends with a barrier.
+__device__ void block_sort(unsigned long long* keys, unsigned long long* tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int run = warp; run < DICT / 32; run += nw) {
+        unsigned long long k = keys[run * 32 + lane];
+#pragma unroll
+        for (int len = 2; len <= 32; len <<= 1)
+#pragma unroll
+            for (int j = len >> 1; j > 0; j >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, j);
+                const bool up = (lane & len) == 0, lower = (lane & j) == 0;
+                k = (lower == up) ? (o < k ? o : k) : (o > k ? o : k);
             }
-            __syncthreads();
+        keys[run * 32 + lane] = k;
+    }
+    __syncthreads();
+    unsigned long long* src = keys;
+    unsigned long long* dst = tmp;
+    for (int w = 32; w < DICT; w <<= 1) {
+        for (int i = threadIdx.x; i < DICT; i += blockDim.x) {
+            const int base = i & ~(2 * w - 1), pos = i - base;
+            const bool right = pos >= w;
+            const int own = right ? pos - w : pos;
+            const unsigned long long* other = src + base + (right ? 0 : w);
+            const unsigned long long k = src[i];
+            int lo = 0, hi = w;   // partner keys before k: < k (left run), <= k (right run)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const unsigned long long v = other[mid];
+                if (right ? v <= k : v < k) lo = mid + 1;
+                else hi = mid;
+            }
+            dst[base + own + lo] = k;
         }
+        __syncthreads();
+        unsigned long long* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != keys) {
+        for (int i = threadIdx.x; i < DICT; i += blockDim.x) keys[i] = src[i];
+        __syncthreads();
+    }
 }
 
 struct CodebookSmem {
@@ -192,7 +224,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
             S.n = 0;
         }
         __syncthreads();
-        bitonic_sort(S.keys, DICT);   // ends with a barrier
+        block_sort(S.keys, S.pw);   // pw is free until the merge rounds; ends with a barrier
         // number of used symbols: the last used key sits before the first KEY_NONE
         for (int i = tid; i < DICT; i += blockDim.x)
             if (S.keys[i] != KEY_NONE && (i + 1 == DICT || S.keys[i + 1] == KEY_NONE)) S.n = i + 1;
@@ -606,14 +638,16 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                 sv[0] = v.x & 0xFFFF; sv[1] = v.x >> 16; sv[2] = v.y & 0xFFFF; sv[3] = v.y >> 16;
                 sv[4] = v.z & 0xFFFF; sv[5] = v.z >> 16; sv[6] = v.w & 0xFFFF; sv[7] = v.w >> 16;
             }
-            unsigned bits = 0, esc = 0;
+            unsigned bits = 0, esc = 0, ln[8];   // code lengths, looked up once
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < 8; ++k) {
+                ln[k] = k < cnt ? len_s[sv[k]] : 0u;
+                bits += ln[k];
                 if (k < cnt) {
-                    bits += len_s[sv[k]];
                     esc += sv[k] == MGARD_ESC;
                     fill = fill && sv[k] == FILL_SYMBOL;
                 }
+            }
             unsigned ib = bits, ie = esc;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -639,7 +673,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (k < cnt) {
-                    const unsigned s = sv[k], len = len_s[s];
+                    const unsigned s = sv[k], len = ln[k];
                     acc = (acc << len) | code_s[s];
                     nb += (int)len;
                     if (nb >= 32) {
