@@ -342,3 +342,26 @@ def test_shared_memory_limits_of_fused_kernels(shape, dtype):
     assert float((back - u).abs().max()) <= tol * max(1.0, float(u.abs().max()))
     e = binding.error_norm(u, back, 0.0)
     assert math.isfinite(e)
+
+
+@pytest.mark.parametrize("shape", [(20001,), (3, 4001), (1100, 9, 5), (600, 3, 130)])
+def test_fallback_paths_match_oracle(shape):
+    """Shapes that leave the main kernels: lines of more than 1056 nodes
+    (one thread per line), strided axes whose restriction tiles would not
+    fit in shared memory (separate restriction and tile solve), and long
+    thin grids.  FP64 decomposition against the oracle, FP32 per level,
+    and a compress/decompress round trip within the bound."""
+    u64 = _field(shape, torch.float64, 8)
+    ref = multilevel.decompose(u64.numpy())
+    got = binding.decompose(u64.to(DEV).clone()).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, float(np.max(np.abs(u64.numpy()))))
+    u = u64.to(torch.float32)
+    got32 = binding.decompose(u.to(DEV).clone()).cpu().double().numpy()
+    umax = float(u.abs().max())
+    for err, cmax in _per_level_error(got32, ref, shape):
+        assert err <= max(1e-5 * cmax, 8 * 2.0 ** -24 * umax)
+    ud = u.to(DEV)
+    buf = binding.compress(ud, 1e-3, math.inf)
+    out = binding.decompress(buf)
+    err = pipeline.error(u.double().numpy(), out.cpu().double().numpy(), math.inf)
+    assert err <= binding.info(buf)["tol_abs"]
