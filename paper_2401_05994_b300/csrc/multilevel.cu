@@ -398,32 +398,49 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
     // lines, so a tile may span two outer indices but is never short
     const int64_t nlines = outer_n * inner;
     const int64_t ntiles = (nlines + 31) / 32;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the restriction in parts of jp output rows: each part copies the fine
+    // rows its windows reach, so the fine buffer holds ~2 jp rows
+    const int jp = (mc + parts - 1) / parts;
+    auto part_rows = [&](int J0, int* rb, int* re) {
+        const int J1 = min(mc, J0 + jp);
+        const int fb = J0 == mc - 1 ? m - 1 : 2 * J0;              // f(J0)
+        const int fe = J1 - 1 == mc - 1 ? m - 1 : 2 * (J1 - 1);    // f(J1 - 1)
+        *rb = max(0, fb - 2);                                       // fine rows [rb, re)
+        *re = min(m, fe + 3);
+    };
+    // this lane's line of a tile, and the copy of fine rows [rb, re) of it
+    auto line_of = [&](int64_t tile, int* nl, int64_t* o, int64_t* i) {
         const int64_t l0 = tile * 32;
-        const int nl = (int)(nlines - l0 < 32 ? nlines - l0 : 32);
-        const int64_t mine = l0 + (lane < nl ? lane : 0);   // this lane's line
-        const int64_t o = mine / inner, i = mine - o * inner;
-        // the restriction in parts of jp output rows: each part copies the
-        // fine rows its windows reach, so the fine buffer holds ~2 jp rows
-        const int jp = (mc + parts - 1) / parts;
+        *nl = (int)(nlines - l0 < 32 ? nlines - l0 : 32);
+        const int64_t mine = l0 + (lane < *nl ? lane : 0);
+        *o = mine / inner;
+        *i = mine - *o * inner;
+    };
+    auto copy_rows = [&](int nl, int64_t o, int64_t i, int rb, int re) {
+        if (lane < nl) {
+            const Tw* g = in + o * m * inner + i + (int64_t)(rb + wid) * inner;
+            unsigned sa = (unsigned)__cvta_generic_to_shared(&ti[wid * 33 + lane]);
+#pragma unroll 4
+            for (int k = rb + wid; k < re; k += ST_WARPS, g += gstep, sa += sstep) {
+                if (sizeof(Tw) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+            }
+        } else {
+            for (int k = rb + wid; k < re; k += ST_WARPS) ti[(k - rb) * 33 + lane] = Tw(0);
+        }
+    };
+    bool ahead = false;   // the first part of this tile is already being copied
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int nl;
+        int64_t o, i;
+        line_of(tile, &nl, &o, &i);
         for (int J0 = 0; J0 < mc; J0 += jp) {
             const int J1 = min(mc, J0 + jp);
-            const int fb = J0 == mc - 1 ? m - 1 : 2 * J0;              // f(J0)
-            const int fe = J1 - 1 == mc - 1 ? m - 1 : 2 * (J1 - 1);    // f(J1 - 1)
-            const int rb = max(0, fb - 2), re = min(m, fe + 3);         // fine rows [rb, re)
-            if (lane < nl) {
-                const Tw* g = in + o * m * inner + i + (int64_t)(rb + wid) * inner;
-                unsigned sa = (unsigned)__cvta_generic_to_shared(&ti[wid * 33 + lane]);
-#pragma unroll 4
-                for (int k = rb + wid; k < re; k += ST_WARPS, g += gstep, sa += sstep) {
-                    if (sizeof(Tw) == 4)
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
-                    else
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
-                }
-            } else {
-                for (int k = rb + wid; k < re; k += ST_WARPS) ti[(k - rb) * 33 + lane] = Tw(0);
-            }
+            int rb, re;
+            part_rows(J0, &rb, &re);
+            if (!(J0 == 0 && ahead)) copy_rows(nl, o, i, rb, re);
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
             for (int J = J0 + wid; J < J1; J += ST_WARPS) {
@@ -450,6 +467,19 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
                 to[J * 33 + lane] = acc;
             }
             __syncthreads();   // the next part's copy overwrites the fine rows
+        }
+        // the fine rows are free now: the next tile's first part streams in
+        // while this tile is solved and written out
+        {
+            const int64_t next = tile + gridDim.x;
+            ahead = next < ntiles;
+            if (ahead) {
+                int nl2, rb, re;
+                int64_t o2, i2;
+                line_of(next, &nl2, &o2, &i2);
+                part_rows(0, &rb, &re);
+                copy_rows(nl2, o2, i2, rb, re);
+            }
         }
         {
             Tw v[K];
