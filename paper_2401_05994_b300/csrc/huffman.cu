@@ -708,8 +708,11 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
 }
 
 // -- decoding ------------------------------------------------------------------
-constexpr int DEC_THREADS = 256;
-constexpr int DEC_BLOCKS_PER_SM = 5;   // 33 KB of tables per block; registers capped to fit 5
+constexpr int DEC_THREADS = 640;
+constexpr int DEC_BLOCKS_PER_SM = 2;   // 33 KB of tables per block; registers capped to fit 2
+// Two blocks of 640 threads (40 warps per SM, as five blocks of 256 would
+// give) hold two copies of the decode tables instead of five, so more of
+// the SM's shared L1 stays cache for the threads' payload words.
 
 // Decoding: one thread per sub-chunk of SUB symbols, in a grid that stays
 // resident (each block copies the prefix table once).  The bit window is a
@@ -732,7 +735,7 @@ __device__ inline void store8(uint16_t*, const uint16_t*) {}
 // symbol position).  OutT = float or double: the dequantized coefficient of
 // every symbol to `vals` (symbol order), with the widths of DeqArgs.
 template <typename OutT>
-__global__ void __launch_bounds__(DEC_THREADS, 5) k_decode(
+__global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
     const uint32_t* __restrict__ words, uint64_t nwords, const uint64_t* __restrict__ word_off,
     const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
     const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
