@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
          gb += (int64_t)gridDim.x * QS_THREADS) {
         const int64_t g = gb + threadIdx.x;
         const int64_t i0 = g * 8;
-        int32_t qe[8];
-        unsigned ne = 0;   // escapes among this thread's values, in order in qe
+        int32_t qe[8];      // escape values by slot
+        unsigned emask = 0;  // slots holding escapes
         // the level of the group's first value; its width stays in registers
         // until a value crosses into the next level (rare)
         int l = 0;
@@ -305,12 +305,8 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
             int32_t qo = 0;
             quantize_value(v[k], iwl, wsl, wl, s, qo, st);
             packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
-            if (s == MGARD_ESC) {   // the value goes to slot ne (slots 0..ne-1 hold earlier escapes)
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j == (int)ne) qe[j] = qo;
-                ++ne;
-            }
+            qe[k] = qo;
+            emask |= (unsigned)(s == MGARD_ESC) << k;
             if (s == RADIUS) ++center;
             else atomicAdd(&my[s], 1u);
         }
@@ -322,17 +318,18 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
         }
         // place of this thread's first escape inside its sub-chunk: exclusive
         // scan over the warp
+        const unsigned ne = __popc(emask);
         unsigned inc = ne;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += t;
         }
-        if (ne) {
+        if (emask) {
             int32_t* dst = esc + (i0 & ~(int64_t)(QS_SUB - 1)) + (inc - ne);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < (int)ne) dst[j] = qe[j];
+            for (int k = 0; k < 8; ++k)   // escapes in slot order
+                if ((emask >> k) & 1u) *dst++ = qe[k];
         }
     }
     if (center) atomicAdd(&sh[0][RADIUS], center);
