@@ -95,8 +95,8 @@ def evaluate(fields, targets, params, s: float = math.inf, rel_err: float = 0.05
 
 def bisect_full(field: torch.Tensor, target: float, s: float = math.inf, rel_err: float = 0.05,
                 lo: float = 1e-7, hi: float = 1.0, out=None):
-    """The judge: bisection on log10(tau) where every probe is a complete
-    mgard_compress.  Returns (buffer view, tol, passes)."""
+    """Reference search: bisection on log10(tau) where every probe is a
+    complete mgard_compress.  Returns (buffer view, tol, passes)."""
     fbytes = field.numel() * field.element_size()
     if out is None:
         out = torch.empty(binding.compress_bound(field.shape, field.dtype), dtype=torch.uint8,
