@@ -13,6 +13,7 @@
 // with one warp per chunk.  Decoding runs one thread per 256-symbol
 // sub-chunk with a 14-bit prefix table in shared memory and a canonical
 // first-code search for longer codes.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -928,6 +929,24 @@ mgard_status huffman_prepare() {
     if (!done[dev]) {
         MGB_CUDA(cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(CodebookSmem)));
+        // The decoder's threads read their payload words one at a time and
+        // rely on L1 keeping each thread's line between reads.  Left to
+        // itself the driver configures shared memory for a third block that
+        // the register cap never admits; asking for the two resident blocks'
+        // tables (plus the per-block reservation) leaves the rest to L1.
+        int smem_sm = 0;
+        MGB_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        auto carve = [&](const void* f) -> mgard_status {
+            cudaFuncAttributes fa{};
+            MGB_CUDA(cudaFuncGetAttributes(&fa, f));
+            const long need = (long)DEC_BLOCKS_PER_SM * ((long)fa.sharedSizeBytes + 1024) + 4096;
+            const int pct = (int)std::min(100L, (need * 100 + smem_sm - 1) / smem_sm);
+            MGB_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+            return MGARD_OK;
+        };
+        MGB_TRY(carve((const void*)k_decode<float>));
+        MGB_TRY(carve((const void*)k_decode<double>));
+        MGB_TRY(carve((const void*)k_decode<uint16_t>));
         done[dev] = true;
     }
     return MGARD_OK;
@@ -1006,6 +1025,7 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
+    MGB_TRY(huffman_prepare());
     DeqArgs dq;
     std::memset(&dq, 0, sizeof(dq));
     MGB_LAUNCH("k_decode", st, k_decode<uint16_t><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
@@ -1023,6 +1043,7 @@ mgard_status huffman_decode_values(const uint32_t* words, uint64_t nwords, const
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
+    MGB_TRY(huffman_prepare());
     MGB_LAUNCH("k_decode", st, k_decode<T><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
                                           esc_off, nullptr, nullptr, vals, dq, status, nchunks));
     MGB_CUDA(cudaGetLastError());

@@ -55,6 +55,10 @@ constexpr int64_t FP64_SOLVE_NODES = 0;
 // Opt a kernel in to `bytes` of dynamic shared memory where its current
 // limit (48 KB minus its static shared memory by default) is lower.
 mgard_status allow_dynamic_smem(const void* kern, size_t bytes);
+// A grid of persistent blocks of `kern`: as many as stay resident on the
+// device at once (occupancy at this block size and dynamic shared memory),
+// at most `work`.
+mgard_status resident_grid(const void* kern, int threads, size_t smem, int64_t work, int* grid);
 
 // Levels of at most TAIL_NODES nodes (TAIL_LEVELS of them at most) run in a
 // single one-block launch each way (tail.cu) on the symbol-order path.

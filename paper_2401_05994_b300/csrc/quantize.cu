@@ -9,6 +9,7 @@
 
 #include "huffman.cuh"
 #include "quantize.cuh"
+#include "multilevel.cuh"
 #include "rows3.cuh"
 
 namespace mgb {
@@ -228,7 +229,7 @@ constexpr int QS_SUB = SUB;   // symbols per Huffman sub-chunk
 static_assert(QS_SUB == 32 * 8, "a warp covers one sub-chunk per iteration");
 
 template <typename T>
-__global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
+__global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize_stream(
     const T* __restrict__ zs, int64_t n, LevelOffsets lo, const double* __restrict__ wdev,
     uint16_t* __restrict__ sym, int32_t* __restrict__ esc, unsigned long long* __restrict__ hist,
     unsigned* status) {
@@ -249,27 +250,12 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
     const int lane = threadIdx.x & 31;
     unsigned* my = sh[threadIdx.x & 1];
     unsigned center = 0, st = 0;
-    // block-uniform trip count (the escape scan needs whole warps)
-    for (int64_t gb = blockIdx.x * (int64_t)QS_THREADS; gb * 8 < n;
-         gb += (int64_t)gridDim.x * QS_THREADS) {
-        const int64_t g = gb + threadIdx.x;
-        const int64_t i0 = g * 8;
-        int32_t qe[8];      // escape values by slot
-        unsigned emask = 0;  // slots holding escapes
-        // the level of the group's first value; its width stays in registers
-        // until a value crosses into the next level (rare)
-        int l = 0;
-        while (l < L && i0 >= offs[l + 1]) ++l;
-        long long lend = offs[l + 1];
-        double wl = ws[l];
-        T iwl = iws[l];
-        WidthSplit wsl = wss[l];
-        T v[8];
-        const bool full = i0 + 8 <= n;
+    // the eight values from i0 (zeros past the end)
+    auto load8 = [&](int64_t i0, T* v) {
         if (i0 >= n) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = T(0);
-        } else if (full) {
+        } else if (i0 + 8 <= n) {
             if (sizeof(T) == 4) {
                 const float4 a = reinterpret_cast<const float4*>(zs + i0)[0];
                 const float4 b = reinterpret_cast<const float4*>(zs + i0)[1];
@@ -287,6 +273,30 @@ __global__ void __launch_bounds__(QS_THREADS) k_quantize_stream(
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? zs[i0 + k] : T(0);
         }
+    };
+    const int64_t stride = (int64_t)gridDim.x * QS_THREADS;
+    // the next group's values are loaded while this group is quantized
+    T nxt[8];
+    load8((blockIdx.x * (int64_t)QS_THREADS + threadIdx.x) * 8, nxt);
+    // block-uniform trip count (the escape scan needs whole warps)
+    for (int64_t gb = blockIdx.x * (int64_t)QS_THREADS; gb * 8 < n; gb += stride) {
+        const int64_t g = gb + threadIdx.x;
+        const int64_t i0 = g * 8;
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = nxt[k];
+        if ((gb + stride) * 8 < n) load8((g + stride) * 8, nxt);
+        int32_t qe[8];      // escape values by slot
+        unsigned emask = 0;  // slots holding escapes
+        // the level of the group's first value; its width stays in registers
+        // until a value crosses into the next level (rare)
+        int l = 0;
+        while (l < L && i0 >= offs[l + 1]) ++l;
+        long long lend = offs[l + 1];
+        double wl = ws[l];
+        T iwl = iws[l];
+        WidthSplit wsl = wss[l];
+        const bool full = i0 + 8 <= n;
         uint32_t packed[4] = {0, 0, 0, 0};
         // the usual group lies inside one level and inside the array
         const bool plain = full && i0 + 8 <= lend;
@@ -430,7 +440,9 @@ mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16
         set_error("too many levels");
         return MGARD_ESHAPE;
     }
-    MGB_LAUNCH("k_quantize_stream", st, k_quantize_stream<T><<<grid_for((n + 7) / 8, QS_THREADS, 148LL * 8), QS_THREADS, 0, st>>>(
+    int grid = 0;
+    MGB_TRY(resident_grid((const void*)k_quantize_stream<T>, QS_THREADS, 0, (n + 8 * QS_THREADS - 1) / (8 * QS_THREADS), &grid));
+    MGB_LAUNCH("k_quantize_stream", st, k_quantize_stream<T><<<grid, QS_THREADS, 0, st>>>(
                                             zs, n, level_offsets(p), w, sym, esc, hist, status));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
