@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize
         }
     };
     const int64_t stride = (int64_t)gridDim.x * QS_THREADS;
+    // a thread's groups come in increasing order, so its level only moves
+    // forward: the search resumes where the previous group left it
+    int lcur = 0;
     // the next group's values are loaded while this group is quantized
     T nxt[8];
     load8((blockIdx.x * (int64_t)QS_THREADS + threadIdx.x) * 8, nxt);
@@ -290,8 +293,8 @@ __global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize
         unsigned emask = 0;  // slots holding escapes
         // the level of the group's first value; its width stays in registers
         // until a value crosses into the next level (rare)
-        int l = 0;
-        while (l < L && i0 >= offs[l + 1]) ++l;
+        while (lcur < L && i0 >= offs[lcur + 1]) ++lcur;
+        int l = lcur;
         long long lend = offs[l + 1];
         double wl = ws[l];
         T iwl = iws[l];
@@ -300,6 +303,33 @@ __global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize
         uint32_t packed[4] = {0, 0, 0, 0};
         // the usual group lies inside one level and inside the array
         const bool plain = full && i0 + 8 <= lend;
+        if (sizeof(T) == 4 && plain) {
+            // quantize_value's decisions without per-value branches: a
+            // value escapes when |q| reaches RADIUS (or is NaN), and only
+            // non-finite values and |q| >= 2^12 take the longer rules
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float q = rintf(__fmul_rn((float)v[k], (float)iwl));
+                const float a = fabsf(q);
+                const bool e = !(a < (float)RADIUS);
+                int32_t qo = (int32_t)q;
+                if (e && !(a < (float)F32_EXACT)) {
+                    if (!isfinite((float)v[k])) {
+                        st |= ST_NONFINITE;
+                        qo = 0;
+                    } else if (!quant_big((float)v[k], wsl, wl, qo)) {
+                        st |= ST_RANGE;
+                        qo = 0;
+                    }
+                }
+                const int s = e ? (int)MGARD_ESC : (int)q + RADIUS;
+                packed[k >> 1] |= (uint32_t)s << (16 * (k & 1));
+                qe[k] = qo;
+                emask |= (unsigned)e << k;
+                if (s == RADIUS) ++center;
+                else atomicAdd(&my[s], 1u);
+            }
+        } else
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int64_t i = i0 + k;
