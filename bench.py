@@ -46,8 +46,8 @@ SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
 # that cube's element count; scaled to the bench workload by elements (the
 # traffic of these kernels grows in proportion) and divided by the launches
 # per step.  Valid for the kernel versions captured; others report null.
-NCU_TRAFFIC = {"k_restrict_solve": (393.890560e6 + 41.451520e6, 385 ** 3),
-               "k_decode": (140.102912e6 + 178.025472e6, 385 ** 3)}
+NCU_TRAFFIC = {"k_restrict_solve": (393.995008e6 + 37.135360e6, 385 ** 3),
+               "k_decode": (141.046016e6 + 178.209280e6, 385 ** 3)}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
