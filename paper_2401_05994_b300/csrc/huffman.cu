@@ -566,17 +566,21 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint64_t* a, uint64_t* b,
         }
 }
 
-constexpr int PACK_WARPS = 6;   // 45 KB of static shared memory per block
+constexpr int PACK_WARPS = 8;
+constexpr int PACK_WB = SUB + 4;   // one round's words (256 codes of <= 32 bits) and the carried word
 
 // One warp per chunk, in four rounds of 256 symbols: lane j packs symbols
 // [8j, 8j+8) of the round (one 16-byte load).  Lane bit offsets come from a
 // warp scan; bits accumulate MSB-first in a 64-bit register and the words a
 // lane shares with its neighbours (its first and last) are merged with OR in
-// a shared-memory copy of the chunk.  COMPACT: escape values arrive
-// compacted per sub-chunk (escapes[s * SUB + r], as the streaming quantizer
-// writes them) and each round copies its run to the outlier section with
-// coalesced accesses; otherwise escapes[] is indexed by symbol position and
-// gathered.
+// a shared-memory buffer of the round's words.  After each round its
+// complete words go out (coalesced) and the partial last word is carried
+// into the next round's buffer.  A chunk of the zero symbol only (found
+// from the symbols loaded up front) gets no words.  COMPACT: escape values
+// arrive compacted per sub-chunk (escapes[s * SUB + r], as the streaming
+// quantizer writes them) and each round copies its run to the outlier
+// section with coalesced accesses; otherwise escapes[] is indexed by symbol
+// position and gathered.
 template <bool COMPACT>
 __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     const uint16_t* __restrict__ sym, uint64_t n, const uint8_t* __restrict__ lengths,
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
     uint64_t nchunks, PackGuard guard) {
     __shared__ uint8_t len_s[DICT];
     __shared__ uint32_t code_s[DICT];
-    __shared__ uint32_t buf[PACK_WARPS][CHUNK + 1];
+    __shared__ uint32_t buf[PACK_WARPS][PACK_WB];
     if (guard.status && *guard.status) return;   // an earlier step failed: write nothing
     if (guard.words_byte_off)
         words = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(words) + *guard.words_byte_off);
@@ -603,30 +607,40 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         const int ccnt = (int)min((uint64_t)CHUNK, n - cbase);
         const uint64_t wo = word_off[c];
         const uint64_t eo = esc_off[c];
-        for (int k = lane; k <= CHUNK; k += 32) wb[k] = 0;
-        __syncwarp();
-        unsigned bit0 = 0, esc0 = 0;   // chunk-relative offsets of the current round
-        int64_t pend_at = -1;          // escape values are stored one escape late
-        int32_t pend_v = 0;
-        bool fill = true;              // every symbol of the chunk is the zero symbol
         // all of the lane's symbols of the chunk are loaded up front (one
         // memory latency per chunk instead of one per round)
         uint4 raw[NSUB];
+        bool fill = true;   // every symbol of the lane is the zero symbol
 #pragma unroll
         for (int rd = 0; rd < NSUB; ++rd) {
             const int first = rd * SUB + lane * 8;
             if (first + 8 <= ccnt) {
                 raw[rd] = *reinterpret_cast<const uint4*>(sym + cbase + first);
+                fill = fill && raw[rd].x == FILL_PAIR && raw[rd].y == FILL_PAIR &&
+                       raw[rd].z == FILL_PAIR && raw[rd].w == FILL_PAIR;
             } else {
                 unsigned t[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) t[k] = first + k < ccnt ? sym[cbase + first + k] : 0;
+                for (int k = 0; k < 8; ++k) {
+                    t[k] = first + k < ccnt ? sym[cbase + first + k] : 0;
+                    if (first + k < ccnt) fill = fill && t[k] == FILL_SYMBOL;
+                }
                 raw[rd] = make_uint4(t[0] | (t[1] << 16), t[2] | (t[3] << 16), t[4] | (t[5] << 16),
                                      t[6] | (t[7] << 16));
             }
         }
+        if (__all_sync(0xffffffffu, fill)) {   // stored without words; offsets 0
+            if (lane < SUBREC) sub_off[c * SUBREC + lane] = 0;
+            continue;
+        }
+        unsigned bit0 = 0, esc0 = 0;   // chunk-relative offsets of the current round
+        uint32_t carry = 0;            // the partial word the round starts in
+        int64_t pend_at = -1;          // escape values are stored one escape late
+        int32_t pend_v = 0;
 #pragma unroll
         for (int rd = 0; rd < NSUB; ++rd) {
+            for (int k = lane; k < PACK_WB; k += 32) wb[k] = k == 0 ? carry : 0u;
+            __syncwarp();
             if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
                 sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
                 sub_off[c * SUBREC + (NSUB - 1) + rd - 1] = (uint16_t)esc0;
@@ -644,10 +658,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
             for (int k = 0; k < 8; ++k) {
                 ln[k] = k < cnt ? len_s[sv[k]] : 0u;
                 bits += ln[k];
-                if (k < cnt) {
-                    esc += sv[k] == MGARD_ESC;
-                    fill = fill && sv[k] == FILL_SYMBOL;
-                }
+                if (k < cnt) esc += sv[k] == MGARD_ESC;
             }
             unsigned ib = bits, ie = esc;
 #pragma unroll
@@ -659,6 +670,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                     ie += ve;
                 }
             }
+            const unsigned base = bit0 >> 5;   // the round's first word in the chunk
             const unsigned bpos = bit0 + ib - bits;
             unsigned epos = esc0 + ie - esc;
             const unsigned rtot = __shfl_sync(0xffffffffu, ie, 31);   // escapes of the round
@@ -667,7 +679,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                     outliers[eo + esc0 + k] = escapes[cbase + rd * SUB + k];
             bit0 += __shfl_sync(0xffffffffu, ib, 31);
             esc0 += rtot;
-            unsigned w = bpos >> 5;
+            unsigned w = (bpos >> 5) - base;
             int nb = (int)(bpos & 31);
             unsigned long long acc = 0;
             bool firstw = true;
@@ -694,16 +706,14 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
                 }
             if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
             __syncwarp();
-        }
-        if (!COMPACT && pend_at >= 0) outliers[pend_at] = pend_v;
-        __syncwarp();
-        if (__all_sync(0xffffffffu, fill)) {   // stored without words; offsets 0
-            if (lane < SUBREC) sub_off[c * SUBREC + lane] = 0;
+            // the round's complete words; the word holding its end carries over
+            const unsigned nfull = (bit0 >> 5) - base;
+            for (unsigned k = lane; k < nfull; k += 32) words[wo + base + k] = wb[k];
+            carry = wb[nfull];
             __syncwarp();
-            continue;
         }
-        const unsigned total_words = (bit0 + 31) / 32;
-        for (unsigned k = lane; k < total_words; k += 32) words[wo + k] = wb[k];
+        if ((bit0 & 31) && lane == 0) words[wo + (bit0 >> 5)] = carry;
+        if (!COMPACT && pend_at >= 0) outliers[pend_at] = pend_v;
         __syncwarp();
     }
 }
@@ -1007,7 +1017,9 @@ mgard_status huffman_pack(const uint16_t* sym, uint64_t n, const uint8_t* length
                           int32_t* outliers, cudaStream_t st, PackGuard guard, bool compact) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
-    const int grid = grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8);
+    int grid = 0;
+    MGB_TRY(resident_grid(compact ? (const void*)k_pack<true> : (const void*)k_pack<false>, PACK_WARPS * 32, 0,
+                          (int64_t)((nchunks + PACK_WARPS - 1) / PACK_WARPS), &grid));
     if (compact)
         MGB_LAUNCH("k_pack", st, k_pack<true><<<grid, PACK_WARPS * 32, 0, st>>>(
             sym, n, lengths, codes, word_off, esc_off, escapes, words, sub_off, outliers, nchunks, guard));
