@@ -374,11 +374,20 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
     }
     __syncthreads();
     // prefix table: the code under each 14-bit prefix, found from the
-    // canonical limits (every entry costs the same, whatever the lengths)
+    // canonical limits (every entry costs the same, whatever the lengths).
+    // lim[l], the first code of length l + 1 left-justified, never
+    // decreases with l, so a prefix's length is one plus the number of
+    // limits it reaches; for l <= 14 the limits are multiples of 2^18 and
+    // compare exactly with the prefix in 14-bit units.
+    unsigned lim14[LUT_BITS + 1];
+#pragma unroll
+    for (int l = 1; l <= LUT_BITS; ++l)
+        lim14[l] = (unsigned)(((fc[l] + cnt[l]) << (LMAX - l)) >> (32 - LUT_BITS));
     for (int k = tid; k < (1 << LUT_BITS); k += blockDim.x) {
         const unsigned long long top = (unsigned long long)k << (32 - LUT_BITS);
         unsigned l = 1;
-        while (l <= LUT_BITS && top >= ((fc[l] + cnt[l]) << (LMAX - l))) ++l;
+#pragma unroll
+        for (int j = 1; j <= LUT_BITS; ++j) l += (unsigned)k >= lim14[j];
         uint16_t ent = 0;
         if (l <= LUT_BITS) {
             const unsigned long long idx = fi[l] + ((top >> (32 - l)) - fc[l]);
