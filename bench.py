@@ -325,7 +325,7 @@ def run_batch(args, rank, world, dev, barrier):
 def run_ratio(args, rank, world, dev):
     """Ratio-targeted compression of an advected field series (256x384x384
     float32, k^-5/3, shift + decay per step): the network is trained on
-    steps 0-59 (tolerance sweeps from the method itself) and judged on steps
+    steps 0-59 (tolerance sweeps from the method itself) and evaluated on steps
     60-99 against bisection with one shared decomposition and against
     bisection over full compress passes."""
     from paper_2401_05994_b300 import predictor, synth
@@ -375,7 +375,7 @@ def run_ratio(args, rank, world, dev):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "advected 256x384x384 f32 k^-5/3 series, train steps 0-59, "
-                                   "judge steps 60-99, rel Linf", "step_stride": step_stride,
+                                   "eval steps 60-99, rel Linf", "step_stride": step_stride,
                        "targets": targets,
                        "training_samples": int(x.shape[0])},
             "methods": summ,
