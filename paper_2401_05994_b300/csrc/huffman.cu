@@ -7,12 +7,13 @@
 //    lengths over LMAX repeat on max(1, count >> k); one used symbol -> 1 bit;
 //  * canonical codes, consecutive in (length, symbol) order;
 //  * chunks of CHUNK symbols, each starting on a 32-bit word, MSB-first.
-// The codebook is built by one CTA: bitonic sort of the leaves, the queue
-// merge in doubling rounds (see round_merge) and depths by pointer jumping.
+// The codebook is built by one CTA: a sort of the leaves (warp bitonic
+// networks on runs of 32, then merge passes), the queue merge in doubling
+// rounds (see round_merge) and depths by pointer jumping.
 // Encoding is a count pass, an exclusive scan over chunks and a pack pass
-// with one warp per chunk.  Decoding runs one thread per 256-symbol
-// sub-chunk with a 14-bit prefix table in shared memory and a canonical
-// first-code search for longer codes.
+// with one warp per chunk (a shared-memory buffer of one round's words).
+// Decoding runs one thread per 256-symbol sub-chunk with a 14-bit prefix
+// table in shared memory and a canonical first-code search for longer codes.
 #include <algorithm>
 #include <cstring>
 #include <map>
