@@ -181,11 +181,11 @@ print(json.dumps({"seconds": time.perf_counter() - t0, "bytes": int(sub.size * 4
 """
 
 
-def cpu_oracle_sample(u_host: np.ndarray, tol: float):
-    """Oracle compress + decompress (its own Huffman decoder included) on a
-    sub-cube, in a child process pinned to one thread (OMP/BLAS thread
+def cpu_oracle_sample(u_host: np.ndarray, tol: float, edge: int = SAMPLE):
+    """Oracle compress + decompress (its own Huffman decoder included) on an
+    edge^3 sub-cube, in a child process pinned to one thread (OMP/BLAS thread
     counts 1); returns (field bytes, seconds, threads)."""
-    sub = np.ascontiguousarray(u_host[:SAMPLE, :SAMPLE, :SAMPLE])
+    sub = np.ascontiguousarray(u_host[:edge, :edge, :edge])
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "sub.npy")
         np.save(path, sub)
@@ -197,16 +197,35 @@ def cpu_oracle_sample(u_host: np.ndarray, tol: float):
     return rec["bytes"], rec["seconds"], 1
 
 
+# seconds of oracle work the reference arm spends over all of its steps
+REF_BUDGET_S = 120.0
+# oracle seconds per compress + decompress of a SAMPLE^3 sub-cube on one core
+REF_SAMPLE_S = 7.0
+
+
+def reference_edge(steps: int, warmup: int) -> int:
+    """Edge of the per-step sub-cube: the largest 2^k + 1 (at most SAMPLE)
+    whose estimated oracle time (proportional to the node count) keeps the
+    whole run within REF_BUDGET_S, so any --steps / --warmup ends in a few
+    minutes."""
+    per_step = REF_BUDGET_S / max(1, steps + warmup)
+    for edge in (SAMPLE, 97, 65, 49, 33):
+        if edge <= SAMPLE and REF_SAMPLE_S * (edge / SAMPLE) ** 3 <= per_step:
+            return edge
+    return 17
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_2401_05994_b300 import synth
+    edge = reference_edge(args.steps, args.warmup)
     u = synth.gaussian_random_field((SAMPLE + 8,) * 3, beta=BETA, seed=1).numpy()
     for _ in range(args.warmup):
-        cpu_oracle_sample(u, TOL)
+        cpu_oracle_sample(u, TOL, edge)
     tot_b, tot_t = 0, 0.0
     for _ in range(args.steps):
-        b, t, cores = cpu_oracle_sample(u, TOL)
+        b, t, cores = cpu_oracle_sample(u, TOL, edge)
         tot_b += b
         tot_t += t
     gbs = tot_b / tot_t / 1e9
@@ -215,10 +234,11 @@ def run_reference(args, rank, world):
         "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"{SAMPLE}^3 sub-cube of a 513^3 f32 GRF k^-5/3, "
+        "data": "synthetic", "config": {"workload": f"{edge}^3 sub-cube of a 513^3 f32 GRF k^-5/3, "
                                                     "rel Linf 1e-3, FP64 CPU oracle"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{SAMPLE}^3 sub-cube per step"},
+                         "sample": f"{edge}^3 sub-cube per step (edge chosen so that all steps "
+                                   f"take about {REF_BUDGET_S:.0f} s of oracle time)"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
