@@ -2,6 +2,8 @@
 against brute-force operators, the bound on adversarial and random
 quantization errors, rounding rules and the symbol layout."""
 import math
+import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -84,6 +86,73 @@ def test_s0_norm_is_l2_norm_of_p1_function():
     u = 2.0 * x - 3.0
     exact = ((2 * 8 - 3) ** 3 - (-3) ** 3) / (3 * 2.0)   # int_0^8 (2x-3)^2 dx
     assert abs(bounds.s_norm(u, 0.0) ** 2 - exact) < 1e-10
+
+
+def _snorm_golden():
+    """Rows of tests/golden/snorm_1d.txt: hand-derived level energies of two
+    fine-grid hats on x = 0..4 and the s-norm and width values built from
+    them (derivations in the file)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "snorm_1d.txt")
+    cases, widths = [], []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = [t.strip() for t in line.split("|")]
+        if parts[0] == "widths":
+            widths.append((float(parts[1]), float(parts[2]),
+                           [float(Fraction(t)) for t in parts[3].split()]))
+        else:
+            cases.append((parts[0], np.array([float(t) for t in parts[1].split()]),
+                          [float(Fraction(t)) for t in parts[2].split()],
+                          [float(Fraction(t)) for t in parts[3].split()]))
+    return cases, widths
+
+
+def test_level_energies_match_hand_projections():
+    """||Q_l u||^2 for l = 0, 1, 2 equals the values solved by hand from the
+    normal equations of each level (pins the projections and the mass norm
+    independently of the oracle's own operators)."""
+    cases, _ = _snorm_golden()
+    h = grid.hierarchy((5,))
+    for _, u, E, _ in cases:
+        Q = multilevel.projections(u)
+        got = [multilevel.mass_norm2(h, l, Q[l]) for l in range(h.L + 1)]
+        assert np.allclose(got, E, rtol=0, atol=1e-14), (got, E)
+
+
+@pytest.mark.parametrize("k,s", [(0, 0.0), (1, 0.5), (2, 1.0)])
+def test_s_norm_level_weighting_matches_golden(k, s):
+    """The level weighting 4^{s l} with l = 0 the coarsest: the hand values
+    separate it from 4^{s (L - l)} and 2^{s l}, and case B has all three
+    level terms nonzero."""
+    cases, _ = _snorm_golden()
+    for name, u, _, S2 in cases:
+        assert abs(bounds.s_norm(u, s) ** 2 - S2[k]) < 1e-13, (name, s)
+
+
+@pytest.mark.parametrize("k,s", [(0, 0.0), (1, 0.5), (2, 1.0)])
+def test_s_norm_of_separable_2d_field_is_product_of_1d_energies(k, s):
+    """On the tensor-product grid 5 x 5 the projection of f(x) g(y) is
+    Q_l f (x) Q_l g, so the level energies multiply: the 2D s-norm follows
+    from the two 1D golden rows with no further derivation."""
+    cases, _ = _snorm_golden()
+    (_, fa, Ea, _), (_, fb, Eb, _) = cases
+    u = np.outer(fa, fb)
+    E = [a * b for a, b in zip(Ea, Eb)]
+    exp = E[0] + sum(4.0 ** (s * l) * (E[l] - E[l - 1]) for l in (1, 2))
+    assert abs(bounds.s_norm(u, s) ** 2 - exp) < 1e-13
+
+
+def test_s_norm_bin_widths_match_golden():
+    """w_l = 2 tau / sqrt((L+1) 4^{s l} mu_l n_l) with the Gershgorin bounds
+    mu_l and new-node counts n_l worked out by hand for the shape (5,)."""
+    _, widths = _snorm_golden()
+    for s, tau, w2 in widths:
+        w = bounds.bin_widths((5,), tau, s) / bounds.WIDTH_MARGIN
+        assert np.allclose(w ** 2, w2, rtol=1e-14, atol=0), (s, w ** 2, w2)
+    h = grid.hierarchy((5,))
+    assert [bounds.mu(h, l) for l in range(3)] == [2.0, 2.0, 1.0]
+    assert [h.new_count(l) for l in range(3)] == [2, 1, 2]
 
 
 def test_rounding_ties_to_even_and_escapes():
