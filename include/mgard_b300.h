@@ -20,8 +20,9 @@
  *    last one; L = min over axes of the number of such coarsenings before an
  *    axis has two nodes (capped by max_levels when max_levels >= 0).
  *  - dtype selects float (MGARD_F32) or double (MGARD_F64) data.  F32 data is
- *    decomposed in float with float accumulation; the restriction and
- *    tridiagonal solves of coarse grids (fewer than 2^21 nodes) run in double.
+ *    decomposed in float with float accumulation on every level, the
+ *    restriction and tridiagonal solves of the coarse grids included; F64
+ *    data in double.  Error norms and verification are always double.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *    stream-ordered.  Functions documented as taking device pointers require
  *    pointers to device (or managed) memory of the current device.
@@ -74,6 +75,11 @@ typedef enum { MGARD_ABS = 0, MGARD_REL = 1 } mgard_tolmode;
 const char* mgard_strerror(mgard_status status);
 /* Text of the most recent failure in the calling thread ("" if none). */
 const char* mgard_last_error(void);
+/* Number of CUDA allocation calls (device memory, the stream-ordered
+ * workspace pool, pinned host memory) the library has made in this process
+ * so far.  For diagnostics and tests: a caller can check that a sequence of
+ * calls allocated nothing. */
+uint64_t mgard_device_allocations(void);
 /* Library version as 0xMMmmpp. */
 uint32_t mgard_version(void);
 
@@ -183,6 +189,7 @@ mgard_status mgard_huffman_encode(const uint16_t* symbols, uint64_t n, const uin
  * allocator.  Its scratch is a fixed device array of 90,704 bytes inside the
  * library, held by every device that loads the library until the process
  * exits.  Limits: n <= 2048 * 4096 * 1024 symbols (MGARD_EINVAL beyond).
+ * Like mgard_huffman_encode it synchronizes the stream to return the totals.
  * The first call on a device looks up that array's device address (with the
  * device current); make that first call before any stream capture.  All
  * calls share the array and it keeps the previous call's contents (the call

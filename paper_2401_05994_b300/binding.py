@@ -34,6 +34,7 @@ SIGNATURES = {
     "mgard_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mgard_last_error": (ctypes.c_char_p, []),
     "mgard_version": (ctypes.c_uint32, []),
+    "mgard_device_allocations": (ctypes.c_uint64, []),
     "mgard_levels": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mgard_decompose": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp]),
     "mgard_recompose": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp]),

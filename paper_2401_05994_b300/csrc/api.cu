@@ -8,6 +8,7 @@
 //   compress:   [norm] -> decompose -> widths -> quantize+histogram ->
 //               codebook -> count/scan -> pack -> header
 //   decompress: header checks -> tables -> decode -> dequantize -> recompose
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -155,6 +156,7 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
         dst = (char*)*out;
     } else if (field_dev) {
         void* q = nullptr;
+        count_device_alloc();
         cudaError_t e = cudaMalloc(&q, total);
         if (e != cudaSuccess) {
             set_error(std::string("output allocation: ") + cudaGetErrorString(e));
@@ -233,6 +235,11 @@ mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::ve
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+namespace {
+std::atomic<uint64_t> g_device_allocs{0};
+}
+void count_device_alloc() { g_device_allocs.fetch_add(1, std::memory_order_relaxed); }
+
 }  // namespace mgb
 
 using namespace mgb;
@@ -258,6 +265,10 @@ const char* mgard_strerror(mgard_status s) {
 }
 
 const char* mgard_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t mgard_device_allocations(void) {
+    return mgb::g_device_allocs.load(std::memory_order_relaxed);
+}
 
 uint32_t mgard_version(void) { return 0x010000u; }
 
@@ -583,6 +594,7 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field, int
     } else {
         out_dev = in_dev;
         if (out_dev) {
+            count_device_alloc();
             cudaError_t e = cudaMalloc(&dst, nbytes);
             if (e != cudaSuccess) {
                 set_error(std::string("output allocation: ") + cudaGetErrorString(e));

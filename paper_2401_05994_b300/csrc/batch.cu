@@ -142,7 +142,9 @@ struct BatchState {
         key = k;
         MGB_TRY(lanes.init());
         cudaStream_t s0 = lanes.side[0];
+        count_device_alloc();
         MGB_CUDA(cudaMallocHost(&hmetas, sizeof(CompressMeta) * k.n));
+        count_device_alloc();
         MGB_CUDA(cudaMallocAsync((void**)&metas, sizeof(CompressMeta) * k.n, s0));
         for (int i = 0; i < k.n; ++i) {
             const Plan* p;
@@ -420,6 +422,7 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
     // one round trip for every header
     {
         char* pin = nullptr;
+        count_device_alloc();
         MGB_CUDA(cudaMallocHost(&pin, (size_t)n * HEAD_BYTES));
         std::unique_ptr<char, cudaError_t (*)(void*)> guard(pin, cudaFreeHost);
         for (int i = 0; i < n; ++i) {
@@ -449,7 +452,9 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
         nb->key = key;
         MGB_TRY(nb->lanes.init());
         cudaStream_t s0 = nb->lanes.side[0];
+        count_device_alloc();
         MGB_CUDA(cudaMallocHost(&nb->hstat, sizeof(unsigned) * n));
+        count_device_alloc();
         MGB_CUDA(cudaMallocAsync((void**)&nb->stat, sizeof(unsigned) * n, s0));
         nb->plans.assign(n, nullptr);
         nb->heads.resize(n);

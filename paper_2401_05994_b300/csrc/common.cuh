@@ -12,6 +12,9 @@ namespace mgb {
 
 // Last-error text, per host thread.
 void set_error(const std::string& msg);
+// Adds one to the count of CUDA allocations (device, pool or pinned host) the
+// library has asked for; every allocation call site calls it first.
+void count_device_alloc();
 
 #define MGB_CUDA(call)                                                              \
     do {                                                                            \

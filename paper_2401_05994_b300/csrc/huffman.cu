@@ -1105,6 +1105,8 @@ struct NoAllocScratch {
 // only a stand-in for the device address; cudaGetSymbolAddress gives the
 // real one.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+static_assert(sizeof(NoAllocScratch) == 90704,
+              "the documented size of the allocation-free scratch (90,704 bytes) is stale");
 
 namespace {
 
@@ -1182,11 +1184,15 @@ extern "C" mgard_status mgard_huffman_encode_noalloc(
         return MGARD_ECAPACITY;
     }
     MGB_LAUNCH("k_tables", st, k_tables<<<1, CB_THREADS, 0, st>>>(lengths, sc->codes, &sc->dt));
-    if (nchunks)
+    if (nchunks) {
+        int pgrid = 0;
+        MGB_TRY(resident_grid((const void*)k_pack<false>, PACK_WARPS * 32, 0,
+                              ((int64_t)nchunks + PACK_WARPS - 1) / PACK_WARPS, &pgrid));
         MGB_LAUNCH("k_pack", st,
-                   k_pack<false><<<grid_for((int64_t)nchunks, PACK_WARPS, 148LL * 8), PACK_WARPS * 32, 0, st>>>(
+                   k_pack<false><<<pgrid, PACK_WARPS * 32, 0, st>>>(
                        symbols, n, lengths, sc->codes, word_off, esc_off, escapes, words, sub_off,
                        outliers, nchunks, PackGuard()));
+    }
     MGB_CUDA(cudaGetLastError());
     MGB_CUDA(cudaStreamSynchronize(st));
     return MGARD_OK;

@@ -25,6 +25,7 @@ struct DevBuf {
         st = s;
         if (bytes == 0) bytes = 16;
         cudaMemPool_t pool = workspace_pool();
+        count_device_alloc();
         cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess) {
             p = nullptr;

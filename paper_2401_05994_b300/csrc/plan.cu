@@ -331,6 +331,7 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
         }
     }
     if (!device) return MGARD_OK;
+    count_device_alloc();
     cudaError_t e = cudaMalloc(&p.dbuf, blob.bytes.size());
     if (e != cudaSuccess) {
         set_error(std::string("plan tables: ") + cudaGetErrorString(e));

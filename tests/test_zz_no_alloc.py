@@ -5,8 +5,9 @@ memory (for example code running under another framework's memory manager, or
 where cudaMalloc is not permitted).  It keeps its scratch in a fixed device
 array inside the library instead.  These checks call both entry points
 through the C ABI on the same inputs and require identical streams, twice in a
-row (the second call must not see stale scratch from the first).  The file is
-named so that pytest collects it last.
+row (the second call must not see stale scratch from the first), and check
+with the library's allocation counter that those calls allocated nothing.  The
+file is named so that pytest collects it last.
 """
 import ctypes
 
@@ -57,11 +58,16 @@ def _encode(fn, sym, lengths, esc):
 
 def test_noalloc_encode_matches_regular_encode_twice():
     L = binding.lib()
+    L.mgard_device_allocations.restype = ctypes.c_uint64
     # a large call first, then a smaller one with a different code table
-    for n, seed in ((3_000_001, 1), (70_001, 2)):
-        sym, lengths, esc = _inputs(n, seed)
-        ref = _encode(L.mgard_huffman_encode, sym, lengths, esc)
-        got = _encode(L.mgard_huffman_encode_noalloc, sym, lengths, esc)
+    cases = [_inputs(n, seed) for n, seed in ((3_000_001, 1), (70_001, 2))]
+    refs = [_encode(L.mgard_huffman_encode, *c) for c in cases]
+    # the library makes no allocation of any kind during the two calls
+    allocs = L.mgard_device_allocations()
+    gots = [_encode(L.mgard_huffman_encode_noalloc, *c) for c in cases]
+    assert L.mgard_device_allocations() == allocs
+    for (sym, lengths, esc), ref, got in zip(cases, refs, gots):
+        n = sym.numel()
         assert ref[4] == got[4] and ref[5] == got[5]
         for a, b in zip(ref[:4] + ref[6:], got[:4] + got[6:]):
             assert np.array_equal(a, b)
