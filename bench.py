@@ -41,13 +41,17 @@ SHAPE = (513, 513, 513)
 TOL = 1e-3
 BETA = 5.0 / 3.0
 SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
-# DRAM bytes (read + write) of all launches of a kernel in one compress +
-# decompress step, from an ncu capture of a smaller cube (profiles/), with
-# that cube's element count; scaled to the bench workload by elements (the
-# traffic of these kernels grows in proportion) and divided by the launches
-# per step.  Valid for the kernel versions captured; others report null.
-NCU_TRAFFIC = {"k_restrict_solve": (393.995008e6 + 37.135360e6, 385 ** 3),
-               "k_decode": (141.046016e6 + 178.209280e6, 385 ** 3)}
+# DRAM bytes (read, write) of all launches of a kernel in one compress +
+# decompress step of the 513^3 workload, and those launches, from one ncu
+# capture of the same command (profiles/dram_traffic_513cube.md; one pass per
+# launch).  Valid for the kernel versions captured.
+NCU_TRAFFIC_513 = {
+    "k_restrict_solve": (930.9e6, 241.1e6, 20), "k_decode": (331.8e6, 496.8e6, 1),
+    "k3_coeff": (662.1e6, 805.7e6, 5), "k_pack": (353.1e6, 189.4e6, 1),
+    "k3_fill": (618.1e6, 513.3e6, 5), "k3_restrict_x": (542.2e6, 236.1e6, 6),
+    "k_quantize_stream": (553.5e6, 281.8e6, 1), "k_solve_warp": (311.1e6, 32.7e6, 10),
+    "k_maxabs": (540.1e6, 3.0e6, 1), "k_chunk_count": (270.2e6, 1.5e6, 1),
+}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -630,13 +634,17 @@ def main():
     roof = None
     if dom:
         ach = algo.get(dom, 0.0) / (kernel_ms[dom] / 1e3) / 1e9
-        traffic = None
-        if dom in NCU_TRAFFIC:
-            b, n0 = NCU_TRAFFIC[dom]
-            launches_per_step = rep[dom][0] / trace_steps
-            traffic = b * int(np.prod(shape)) / n0 / launches_per_step
+        launches_per_step = rep[dom][0] / trace_steps
+        traffic = dram_ach = None
+        if dom in NCU_TRAFFIC_513 and shape == SHAPE and args.spectrum == "energy":
+            rd, wr, nl = NCU_TRAFFIC_513[dom]
+            if nl == launches_per_step:
+                traffic = (rd + wr) / nl
+                dram_ach = (rd + wr) / (kernel_ms[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": traffic, "peak_source": peak_src,
+                "frac": ach / hbm, "frac_basis": "algorithmic bytes",
+                "traffic": traffic, "dram_achieved": dram_ach,
+                "frac_dram": dram_ach / hbm if dram_ach else None, "peak_source": peak_src,
                 "launches_per_step": rep[dom][0] / trace_steps,
                 "algorithmic_bytes_per_launch": algo.get(dom, 0.0) / (rep[dom][0] / trace_steps),
                 "kernel_ms_per_step": kernel_ms[dom],
