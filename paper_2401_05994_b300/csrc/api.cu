@@ -45,6 +45,10 @@ mgard_status check_dtype(mgard_dtype d) {
 }
 
 mgard_status status_to_error(unsigned st) {
+    if (st & ST_TIMEOUT) {
+        set_error("a bounded device wait (tensor-copy barrier) gave up");
+        return MGARD_ETIMEOUT;
+    }
     if (st & ST_NONFINITE) {
         set_error("input holds NaN or Inf");
         return MGARD_ENONFINITE;

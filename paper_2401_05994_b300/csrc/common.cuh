@@ -157,6 +157,7 @@ enum : unsigned {
     ST_NOCODE = 4u,
     ST_CORRUPT = 8u,
     ST_CAPACITY = 16u,   // the output buffer is smaller than the compressed data
+    ST_TIMEOUT = 32u,    // a bounded device wait gave up
 };
 
 // Partial statistics of one block over a level's coefficients (features of

@@ -17,8 +17,11 @@
 #include <mutex>
 #include <tuple>
 
+#include <cudaTypedefs.h>
+
 #include "multilevel.cuh"
 #include "rows3.cuh"
+#include "tma.cuh"
 
 namespace mgb {
 
@@ -352,6 +355,62 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_solve_tile(Tw* x, int64_t out
     }
 }
 
+// The column solve of a restricted tile (to, mc rows of 32 columns, pitch
+// 33): lane l owns column l, warp w rows [r0, r0 + cnt) in registers; the
+// segment maps are folded through sA/sB (see k_restrict_solve).
+template <typename Tw, int K>
+__device__ inline void solve_columns(Tw* to, const Tw* sal, const Tw* sinv, const Tw* sga,
+                                     Tw (*sA)[32], Tw (*sB)[32], int r0, int cnt, int lane,
+                                     int wid) {
+    Tw v[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = j < cnt ? to[(r0 + j) * 33 + lane] : Tw(0);
+    Tw A = Tw(1), B = Tw(0);   // forward map of the segment: y_in -> A y_in + B
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (j < cnt) {
+            const Tw al = sal[r0 + j], w = v[j] * sinv[r0 + j];
+            v[j] = w;
+            A = al * A;
+            B = al * B + w;
+        }
+    sA[wid][lane] = A;
+    sB[wid][lane] = B;
+    __syncthreads();
+    Tw y = Tw(0);
+    for (int s2 = 0; s2 < wid; ++s2) y = sA[s2][lane] * y + sB[s2][lane];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (j < cnt) {
+            y = sal[r0 + j] * y + v[j];
+            v[j] = y;
+        }
+    A = Tw(1);   // backward map: x at the segment's end -> x at its start
+    B = Tw(0);
+#pragma unroll
+    for (int j = K - 1; j >= 0; --j)
+        if (j < cnt) {
+            const Tw ga = sga[r0 + j];
+            A = ga * A;
+            B = ga * B + v[j];
+        }
+    __syncthreads();   // every thread has read the forward maps
+    sA[wid][lane] = A;
+    sB[wid][lane] = B;
+    __syncthreads();
+    Tw x = Tw(0);
+    for (int s2 = ST_WARPS - 1; s2 > wid; --s2) x = sA[s2][lane] * x + sB[s2][lane];
+#pragma unroll
+    for (int j = K - 1; j >= 0; --j)
+        if (j < cnt) {
+            x = sga[r0 + j] * x + v[j];
+            v[j] = x;
+        }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (j < cnt) to[(r0 + j) * 33 + lane] = v[j];
+}
+
 // Restriction and solve along one strided axis in a single pass.  The
 // correction M_{l-1}^{-1} P^T M_l is a tensor product of one operator per
 // axis, Mc_a^{-1} P_a^T M_a, and factors on different axes commute, so an
@@ -481,55 +540,7 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
                 copy_rows(nl2, o2, i2, rb, re);
             }
         }
-        {
-            Tw v[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) v[j] = j < cnt ? to[(r0 + j) * 33 + lane] : Tw(0);
-            Tw A = Tw(1), B = Tw(0);   // forward map of the segment: y_in -> A y_in + B
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (j < cnt) {
-                    const Tw al = sal[r0 + j], w = v[j] * sinv[r0 + j];
-                    v[j] = w;
-                    A = al * A;
-                    B = al * B + w;
-                }
-            sA[wid][lane] = A;
-            sB[wid][lane] = B;
-            __syncthreads();
-            Tw y = Tw(0);
-            for (int s2 = 0; s2 < wid; ++s2) y = sA[s2][lane] * y + sB[s2][lane];
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (j < cnt) {
-                    y = sal[r0 + j] * y + v[j];
-                    v[j] = y;
-                }
-            A = Tw(1);   // backward map: x at the segment's end -> x at its start
-            B = Tw(0);
-#pragma unroll
-            for (int j = K - 1; j >= 0; --j)
-                if (j < cnt) {
-                    const Tw ga = sga[r0 + j];
-                    A = ga * A;
-                    B = ga * B + v[j];
-                }
-            __syncthreads();   // every thread has read the forward maps
-            sA[wid][lane] = A;
-            sB[wid][lane] = B;
-            __syncthreads();
-            Tw x = Tw(0);
-            for (int s2 = ST_WARPS - 1; s2 > wid; --s2) x = sA[s2][lane] * x + sB[s2][lane];
-#pragma unroll
-            for (int j = K - 1; j >= 0; --j)
-                if (j < cnt) {
-                    x = sga[r0 + j] * x + v[j];
-                    v[j] = x;
-                }
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (j < cnt) to[(r0 + j) * 33 + lane] = v[j];
-        }
+        solve_columns<Tw, K>(to, sal, sinv, sga, sA, sB, r0, cnt, lane, wid);
         __syncthreads();
         if (lane < nl) {
             Tw* dst = out + o * mc * inner + i + (int64_t)wid * inner;
@@ -538,6 +549,133 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve(
             for (int k = wid; k < mc; k += ST_WARPS, dst += gstep, sp += ST_WARPS * 33) *dst = *sp;
         }
         __syncthreads();   // the next tile overwrites both buffers
+    }
+}
+
+// The same pass with its tiles staged by the tensor-memory accelerator.  A
+// tile is 32 adjacent lines of one outer index (columns i0 .. i0+31 of the
+// (outer, m, inner) array; inner is padded to 16 bytes, so i0 * size is a
+// multiple of 16), and each part of a tile (the fine rows of jp output rows)
+// is one box of `br` rows starting two rows above the part's first centre;
+// rows outside the axis and columns past `inner` arrive as zeros.  Two
+// buffers alternate: while the block restricts one part, thread 0 has
+// already asked for the next, so the copies run behind the arithmetic with
+// no thread issuing element copies.  Each wait on a buffer's barrier gives up
+// after a bounded number of polls: the block then sets ST_TIMEOUT in
+// *status, waits (bounded again) for the copies it has in flight and
+// returns.
+constexpr uint32_t TMA_MAX_POLLS = 1u << 22;
+
+template <typename Tw, int K>
+__global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve_tma(
+    const __grid_constant__ CUtensorMap tin, Tw* __restrict__ out, int64_t outer_n, int m, int mc,
+    int64_t inner, AxisT<Tw> ax, int jp, int br, unsigned* status) {
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)tma_raw + 127) & ~(uintptr_t)127);
+    Tw* fb = reinterpret_cast<Tw*>(base);        // [2][br][32] fine rows, as the boxes land
+    Tw* to = fb + 2 * (size_t)br * 32;           // [mc][33] restricted rows
+    Tw* sal = to + (size_t)mc * 33;              // [mc] -a_k inv_k
+    Tw* sinv = sal + mc;                         // [mc] inv_k
+    Tw* sga = sinv + mc;                         // [mc] -c'_k
+    uint64_t* bar = reinterpret_cast<uint64_t*>(((uintptr_t)(sga + mc) + 7) & ~(uintptr_t)7);
+    __shared__ Tw sA[ST_WARPS][32], sB[ST_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < mc; k += blockDim.x) {
+        sal[k] = -ax.tsub[k] * ax.tinv[k];
+        sinv[k] = ax.tinv[k];
+        sga[k] = -ax.tcp[k];
+    }
+    const int seg = (mc + ST_WARPS - 1) / ST_WARPS;   // rows per warp (<= K)
+    const int r0 = wid * seg;
+    const int cnt = max(0, min(seg, mc - r0));
+    const Tw* __restrict__ rw = ax.rw;
+    Tw wi[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) wi[t] = ax.rwi[t];
+    const int parts = (mc + jp - 1) / jp;
+    const int64_t tpo = (inner + 31) / 32;   // tiles per outer index
+    const int64_t ntiles = outer_n * tpo;
+    const uint32_t box_bytes = (uint32_t)br * 32u * (uint32_t)sizeof(Tw);
+    const int64_t gstep = (int64_t)ST_WARPS * inner;
+    auto centre = [&](int J) { return J == mc - 1 ? m - 1 : 2 * J; };   // fine row of coarse J
+    // job q: part q % parts of the block's tile q / parts, into buffer q & 1
+    auto issue = [&](int64_t q) {
+        const int64_t tile = blockIdx.x + (q / parts) * (int64_t)gridDim.x;
+        if (tile >= ntiles) return;
+        const int p = (int)(q % parts);
+        const int64_t o = tile / tpo;
+        const int i0 = (int)((tile - o * tpo) * 32);
+        uint64_t* b = &bar[q & 1];
+        mbar_expect_tx(b, box_bytes);
+        tma_load_3d(fb + (size_t)(q & 1) * br * 32, &tin, i0, centre(p * jp) - 2, (int)o, b);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        issue(0);
+        issue(1);
+    }
+    int64_t q = 0;   // the next job to consume
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const int64_t o = tile / tpo;
+        const int64_t i0 = (tile - o * tpo) * 32;
+        const int nl = (int)min((int64_t)32, inner - i0);   // columns inside the array
+        for (int p = 0; p < parts; ++p, ++q) {
+            const int J0 = p * jp, J1 = min(mc, J0 + jp);
+            const int f0 = centre(J0) - 2;   // fine row of the box's first row
+            const bool ok = mbar_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1), TMA_MAX_POLLS);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const Tw* ti = fb + (size_t)(q & 1) * br * 32;
+            for (int J = J0 + wid; J < J1; J += ST_WARPS) {
+                Tw acc;
+                if (J >= ax.rlo && J < ax.rhi) {   // window 2J-2 .. 2J+2, uniform weights
+                    const Tw* r = &ti[(2 * J - 2 - f0) * 32 + lane];
+                    acc = wi[0] * r[0];
+                    acc += wi[1] * r[32];
+                    acc += wi[2] * r[64];
+                    acc += wi[3] * r[96];
+                    acc += wi[4] * r[128];
+                } else {
+                    const int f = centre(J);
+                    acc = Tw(0);
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const int ip = f - 2 + t;   // rows outside the axis arrived as zeros
+                        const Tw w = (ip >= 0 && ip < m) ? rw[J * 5 + t] : Tw(0);
+                        acc += w * ti[(ip - f0) * 32 + lane];
+                    }
+                }
+                to[J * 33 + lane] = acc;
+            }
+            __syncthreads();   // the buffer is free: the job two ahead streams into it
+            if (threadIdx.x == 0) issue(q + 2);
+        }
+        if (failed) break;
+        solve_columns<Tw, K>(to, sal, sinv, sga, sA, sB, r0, cnt, lane, wid);
+        __syncthreads();
+        if (lane < nl) {
+            Tw* dst = out + o * mc * inner + i0 + lane + (int64_t)wid * inner;
+            const Tw* sp = &to[wid * 33 + lane];
+#pragma unroll 4
+            for (int k = wid; k < mc; k += ST_WARPS, dst += gstep, sp += ST_WARPS * 33) *dst = *sp;
+        }
+        __syncthreads();   // the next tile overwrites the restricted rows
+    }
+    if (failed && threadIdx.x == 0) {
+        atomicOr(status, (unsigned)ST_TIMEOUT);
+        // the copies of jobs q and q + 1 may still be in flight
+        for (int64_t r = q; r < q + 2; ++r) {
+            const int64_t tile = blockIdx.x + (r / parts) * (int64_t)gridDim.x;
+            if (tile < ntiles) mbar_wait(&bar[r & 1], (uint32_t)((r >> 1) & 1), TMA_MAX_POLLS);
+        }
     }
 }
 
@@ -560,7 +698,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
                                                               const Tw* __restrict__ sub,
                                                               const Tw* __restrict__ inv,
                                                               const Tw* __restrict__ cp, Tdst* dst,
-                                                              Tw sign) {
+                                                              Tw sign, int64_t pitch) {
     constexpr int W = E + 1;
     __shared__ Tw buf[SW_WARPS][32 * W];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -572,7 +710,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
     // row element e = lane + 32 j (j < E, so 32E >= m covers the row)
     Tw nv[E];
     auto load_row = [&](int64_t l) {
-        const Tw* row = x + l * m;
+        const Tw* row = x + l * pitch;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const int e = lane + 32 * j;
@@ -605,7 +743,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_solve_warp(Tw* x, int64_t lin
 #pragma unroll
         for (int k = 0; k < E; ++k) sb[lane * W + k] = v[k];
         __syncwarp();
-        Tw* row = x + ln * m;
+        Tw* row = x + ln * pitch;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const int e = lane + 32 * j;
@@ -869,11 +1007,15 @@ bool level_uses_fp64(const Plan& p, int l) {
 
 template <typename T>
 mgard_status correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1, T sign,
-                     cudaStream_t st, int64_t zoff = -1, bool x_done = false) {
+                     cudaStream_t st, int64_t zoff = -1, bool x_done = false,
+                     unsigned* status = nullptr) {
     const bool f64 = level_uses_fp64<T>(p, l);
     if (rows3_ok(p)) {
-        if (f64) return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done);
-        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done);
+        if (!status) status = fallback_status();
+        if (!status) return MGARD_ECUDA;
+        if (f64)
+            return rows3_correct<T, double>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done, status);
+        return rows3_correct<T, T>(p, l, z, coarse, t0, t1, sign, st, zoff, x_done, status);
     }
     if (f64) return correct_level<T, double>(p, l, z, coarse, t0, t1, sign, st);
     return correct_level<T, T>(p, l, z, coarse, t0, t1, sign, st);
@@ -921,6 +1063,62 @@ cudaMemPool_t workspace_pool() {
 // Opt a kernel in to `bytes` of dynamic shared memory where its current
 // limit is lower (by default 48 KB minus its static shared memory), once per
 // kernel, size and device.
+// Status word of kernels run without a caller's status (file-scope device
+// array; its device address is looked up once per device, with that device
+// current).
+static __device__ unsigned g_fallback_status;
+
+unsigned* fallback_status() {
+    static std::mutex mu;
+    static std::map<int, unsigned*> addr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = addr.find(dev);
+    if (it != addr.end()) return it->second;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fallback_status) != cudaSuccess) {
+        set_error("status word: cudaGetSymbolAddress failed");
+        return nullptr;
+    }
+    addr[dev] = (unsigned*)p;
+    return (unsigned*)p;
+}
+
+mgard_status encode_tensor_map_3d(CUtensorMap* map, const void* base, int elem_bytes,
+                                  const uint64_t dims[3], const uint64_t strides[2],
+                                  const uint32_t box[3]) {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!encode) {
+            cudaDriverEntryPointQueryResult q{};
+            void* fn = nullptr;
+            const cudaError_t e =
+                cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+                set_error("cuTensorMapEncodeTiled is not available");
+                return MGARD_ECUDA;
+            }
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        }
+    }
+    const cuuint64_t gd[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gs[2] = {strides[0], strides[1]};
+    const cuuint32_t bd[3] = {box[0], box[1], box[2]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = encode(map, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              3, const_cast<void*>(base), gd, gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled rejected the tile map");
+        return MGARD_EINVAL;
+    }
+    return MGARD_OK;
+}
+
 mgard_status allow_dynamic_smem(const void* kern, size_t bytes) {
     if (bytes == 0) return MGARD_OK;
     static std::mutex mu;
@@ -1004,11 +1202,68 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
     return MGARD_OK;
 }
 
+// The TMA-staged pass: the fewest parts whose box (2 jp + 5 rows, at most
+// 256) and shared memory fit three blocks per SM (72 KB), else two (110 KB),
+// else one (200 KB).  *done stays false when the rows are not 16-byte aligned
+// or no split fits.
+template <typename Tw>
+mgard_status restrict_solve_tma(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
+                                int64_t inner, const AxisT<Tw>& ax, cudaStream_t st, bool* done,
+                                unsigned* status) {
+    if (!status || (inner * (int64_t)sizeof(Tw)) % 16 != 0 || ((uintptr_t)in & 15) != 0 ||
+        inner > (int64_t(1) << 31) || outer > (int64_t(1) << 31))
+        return MGARD_OK;
+    auto smem_for = [&](int parts, int* jp, int* br) {
+        *jp = (int)((mc + parts - 1) / parts);
+        *br = 2 * *jp + 5;
+        return (size_t)(2 * (size_t)*br * 32 + (size_t)mc * 33 + 3 * (size_t)mc) * sizeof(Tw) +
+               32 + 128;   // barriers and their alignment, and the slack for 128-byte alignment
+    };
+    int parts = 0, jp = 0, br = 0;
+    size_t bytes = 0;
+    for (size_t budget : {(size_t)72 * 1024, (size_t)110 * 1024, (size_t)200 * 1024}) {
+        for (int pt = 1; pt <= 32 && !parts; ++pt) {
+            bytes = smem_for(pt, &jp, &br);
+            if (br <= 256 && bytes <= budget) parts = pt;
+        }
+        if (parts) break;
+    }
+    if (!parts) return MGARD_OK;
+    CUtensorMap map;
+    const uint64_t dims[3] = {(uint64_t)inner, (uint64_t)m, (uint64_t)outer};
+    const uint64_t strides[2] = {(uint64_t)inner * sizeof(Tw), (uint64_t)(m * inner) * sizeof(Tw)};
+    const uint32_t box[3] = {32u, (uint32_t)br, 1u};
+    if (encode_tensor_map_3d(&map, in, (int)sizeof(Tw), dims, strides, box) != MGARD_OK) {
+        cudaGetLastError();
+        return MGARD_OK;   // the cp.async form runs instead
+    }
+    const int64_t ntiles = outer * ((inner + 31) / 32);
+    auto go = [&](auto kern) -> mgard_status {
+        MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
+        int grid = 0;
+        MGB_TRY(resident_grid((const void*)kern, ST_WARPS * 32, bytes, ntiles, &grid));
+        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, ST_WARPS * 32, bytes, st>>>(map, out, outer, (int)m, (int)mc, inner, ax, jp, br, status));
+        MGB_CUDA(cudaGetLastError());
+        *done = true;
+        return MGARD_OK;
+    };
+    if (mc <= 16) return go(k_restrict_solve_tma<Tw, 2>);
+    if (mc <= 32) return go(k_restrict_solve_tma<Tw, 4>);
+    if (mc <= 64) return go(k_restrict_solve_tma<Tw, 8>);
+    if (mc <= 136) return go(k_restrict_solve_tma<Tw, 17>);
+    if (mc <= 264) return go(k_restrict_solve_tma<Tw, 33>);
+    return go(k_restrict_solve_tma<Tw, 65>);
+}
+
 template <typename Tw>
 mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
                                     int64_t inner, const AxisT<Tw>& ax, cudaStream_t st,
-                                    bool* done) {
+                                    bool* done, unsigned* status) {
     *done = false;
+    if (inner >= 2 && mc <= 520) {
+        MGB_TRY(restrict_solve_tma<Tw>(in, out, outer, m, mc, inner, ax, st, done, status));
+        if (*done) return MGARD_OK;
+    }
     // restriction parts: the fewest that bring a block's shared memory to
     // 72 KB (three blocks per SM), else to 110 KB (two), else to 200 KB
     auto smem_for = [&](int parts, int* rows) {
@@ -1045,11 +1300,12 @@ mgard_status restrict_solve_strided(const Tw* in, Tw* out, int64_t outer, int64_
 
 template <typename Tw, typename Tdst>
 mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, const Tw* inv,
-                              const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st) {
+                              const Tw* cp, Tdst* dst, Tw sign, cudaStream_t st, int64_t pitch) {
+    if (pitch <= 0) pitch = m;
     const int grid = (int)std::min<int64_t>((lines + SW_WARPS - 1) / SW_WARPS, 148LL * 16);
     const int bs = SW_WARPS * 32;
 #define MGB_SOLVE_WARP(EV) \
-    MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, EV><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign))
+    MGB_LAUNCH("k_solve_warp", st, k_solve_warp<Tw, Tdst, EV><<<grid, bs, 0, st>>>(x, lines, (int)m, sub, inv, cp, dst, sign, pitch))
     if (m <= 32) MGB_SOLVE_WARP(1);
     else if (m <= 96) MGB_SOLVE_WARP(3);
     else if (m <= 160) MGB_SOLVE_WARP(5);
@@ -1064,7 +1320,13 @@ mgard_status solve_contiguous(Tw* x, int64_t lines, int64_t m, const Tw* sub, co
             }
         }
         // long lines: one thread per line in global memory
-        if (!done) return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
+        if (!done) {   // rx_pitch keeps lines this long dense
+            if (pitch != m) {
+                set_error("solve_contiguous: padded lines over 1056 nodes");
+                return MGARD_EINVAL;
+            }
+            return solve_strided<Tw, Tdst>(x, lines, m, 1, sub, inv, cp, dst, sign, st);
+        }
     }
 #undef MGB_SOLVE_WARP
     MGB_CUDA(cudaGetLastError());
@@ -1092,6 +1354,9 @@ mgard_status Pyramid<T>::alloc(const Plan& p, cudaStream_t st) {
                 const int a = dir == 0 ? k : 3 - k;
                 if (p.n4[a] == 1) continue;
                 s[a] = p.shape[l - 1][a];
+                // the row path pads its rows of the coarse x extent (rx_pitch)
+                if (dir == 1 && a == 3 && rows3_ok(p))
+                    s[a] = el == 8 ? rx_pitch<double>(s[a]) : rx_pitch<float>(s[a]);
                 tmax = std::max(tmax, (size_t)(s[0] * s[1] * s[2] * s[3]) * el);
             }
         }
@@ -1222,7 +1487,7 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
             MGB_CUDA(cudaGetLastError());
         }
         MGB_TRY(correct<T>(p, l, dst, py.lv[l - 1], py.temp0.p, py.temp1.p, T(1), st, zoff,
-                           x_done));
+                           x_done, py.status));
     }
     const T* u0 = p.L ? py.lv[0] : in;
     if (E) MGB_TRY(mass_norm2<T>(p, 0, u0, &E[0], st));
@@ -1253,7 +1518,8 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
         const T* z = zs ? zs : (l == p.L ? top : py.lv[l]);
         const int64_t zoff = zs ? p.offset[l] : -1;
         T* dst = l == p.L ? out : py.lv[l];
-        MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st, zoff));
+        MGB_TRY(correct<T>(p, l, z, py.lv[l - 1], py.temp0.p, py.temp1.p, T(-1), st, zoff, false,
+                           py.status));
         if (rows3_ok(p)) {
             MGB_TRY(rows3_fill<T>(p, l, z, py.lv[l - 1], dst, st, zoff));
         } else {
@@ -1312,16 +1578,16 @@ INST(double)
     template mgard_status solve_strided<Tw, Td>(Tw*, int64_t, int64_t, int64_t, const Tw*,       \
                                                 const Tw*, const Tw*, Td*, Tw, cudaStream_t);    \
     template mgard_status solve_contiguous<Tw, Td>(Tw*, int64_t, int64_t, const Tw*, const Tw*,  \
-                                                   const Tw*, Td*, Tw, cudaStream_t);
+                                                   const Tw*, Td*, Tw, cudaStream_t, int64_t);
 INST_SOLVE(float, float)
 INST_SOLVE(double, float)
 INST_SOLVE(double, double)
 #undef INST_SOLVE
 template mgard_status restrict_solve_strided<float>(const float*, float*, int64_t, int64_t, int64_t,
                                                     int64_t, const AxisT<float>&, cudaStream_t,
-                                                    bool*);
+                                                    bool*, unsigned*);
 template mgard_status restrict_solve_strided<double>(const double*, double*, int64_t, int64_t,
                                                      int64_t, int64_t, const AxisT<double>&,
-                                                     cudaStream_t, bool*);
+                                                     cudaStream_t, bool*, unsigned*);
 
 }  // namespace mgb

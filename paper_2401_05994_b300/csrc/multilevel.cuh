@@ -44,6 +44,9 @@ struct Pyramid {
     std::vector<T*> lv;       // [l] compact array of level l (l < L)
     DevBuf store;
     DevBuf temp0, temp1;      // restriction ping-pong buffers
+    // device status word for kernels' bounded waits (ST_TIMEOUT); null: the
+    // library's per-device fallback word
+    unsigned* status = nullptr;
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 
@@ -56,6 +59,10 @@ constexpr int64_t FP64_SOLVE_NODES = 0;
 // Opt a kernel in to `bytes` of dynamic shared memory where its current
 // limit (48 KB minus its static shared memory by default) is lower.
 mgard_status allow_dynamic_smem(const void* kern, size_t bytes);
+// The per-device status word that kernels with bounded waits use when the
+// caller has none of its own (device address; set-up on first use).
+unsigned* fallback_status();
+
 // A grid of persistent blocks of `kern`: as many as stay resident on the
 // device at once (occupancy at this block size and dynamic shared memory),
 // at most `work`.

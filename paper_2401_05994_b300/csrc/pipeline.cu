@@ -67,7 +67,7 @@ __global__ void k_widths(WidthArgs a, const double* __restrict__ maxparts,
 
 // Status bits of an encoding pass start clear (those of the input check stay).
 __global__ void k_meta_reset(CompressMeta* meta) {
-    if (threadIdx.x == 0) meta->status &= (unsigned)ST_NONFINITE;
+    if (threadIdx.x == 0) meta->status &= (unsigned)(ST_NONFINITE | ST_TIMEOUT);
 }
 
 // Sizes and offsets that follow from the totals of the count pass; the
@@ -187,6 +187,7 @@ mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tol
     // shapes on the row kernels keep every level's coefficients in symbol
     // order in `top` (quantization then streams through it)
     T* top = w.top.template as<T>();
+    w.py.status = &meta->status;
     MGB_TRY(decompose_pyramid<T>(p, din, top, w.py, st, nullptr, energy ? parts + RED_PARTS : nullptr,
                                  rows3_ok(p) ? top : nullptr));
     return MGARD_OK;
@@ -343,6 +344,7 @@ template <typename T>
 mgard_status decompress_core(const Plan& p, const mgard_header& h, const double* w,
                              const char* din, T* dout, DecompressWork<T>& work, unsigned* status,
                              cudaStream_t st) {
+    work.py.status = status;
     const int64_t N = p.total();
     const int L = p.L;
     DecodeTables* dt = work.dt.template as<DecodeTables>();

@@ -234,7 +234,7 @@ __device__ inline Tout restrict_row_at(int J, int nx, int ncx, bool rowc, const 
 template <typename T, int U, bool ZS, bool STAGE, bool RX, typename Tw, bool PAIR>
 __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restrict__ coarse,
                                                Level<T> lv, int64_t zoff, Tw* __restrict__ rx,
-                                               AxisT<Tw> axw) {
+                                               AxisT<Tw> axw, int xpitch) {
     static_assert(!PAIR || STAGE, "pairs read the staged row");
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int nz = (int)lv.n[1], ny = (int)lv.n[2], nx = (int)lv.n[3];
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
             Tw wi[5];
 #pragma unroll
             for (int t = 0; t < 5; ++t) wi[t] = axw.rwi[t];
-            Tw* xrow = rx + r * ncx;
+            Tw* xrow = rx + r * xpitch;
             for (int J = lane; J < ncx; J += 32)
                 xrow[J] = restrict_row_at<Tw>(J, nx, ncx, rowc, wi, axw.rlo, axw.rhi, axw.rw,
                                               [&](int ip) { return (Tw)Z[ip]; });
@@ -457,7 +457,7 @@ template <typename Tin, typename Tout, int U, bool ZS>
 __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
                                                     Tout* __restrict__ out, int nz, int ny,
                                                     int nx, int ncz, int ncy, int ncx,
-                                                    AxisT<Tout> ax, int64_t zoff) {
+                                                    AxisT<Tout> ax, int64_t zoff, int opitch) {
     const int lane = threadIdx.x & 31;
     const Tout* __restrict__ rw = ax.rw;
     const int rlo = ax.rlo, rhi = ax.rhi;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
         if (ZS) PREFETCH_NEXT_ZS_ROW(in, zoff, r, nz, ny, nx, ncz, ncy, ncx, sizeof(Tin));
         else PREFETCH_NEXT_ROW(in, r, (int64_t)nz * ny, nx, sizeof(Tin));
         const Tin* irow = ZS ? in + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : in + r * nx;
-        Tout* orow = out + r * ncx;
+        Tout* orow = out + r * opitch;
         // symbol order on a coarse row holds only the odd positions: ip -> (ip - 1) / 2
         const int sh = (ZS && rowc) ? 1 : 0;
         for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
@@ -499,7 +499,7 @@ template <typename Tin, typename Tout, int U>
 __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ in,
                                                        Tout* __restrict__ out, int nouter, int m,
                                                        int mc, int inner, int nx,
-                                                       const Tout* __restrict__ rw) {
+                                                       const Tout* __restrict__ rw, int pitch) {
     const int lane = threadIdx.x & 31;
     WARP_ROWS((int64_t)nouter * mc * inner, r) {
         const uint32_t ru = (uint32_t)r;
@@ -517,9 +517,9 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
             const bool ok = ip >= 0 && ip < m;
             w[t] = ok ? rw[J * 5 + t] : Tout(0);
             ip = ok ? ip : f;
-            src[t] = in + (((int64_t)o * m + ip) * inner + i) * nx;
+            src[t] = in + (((int64_t)o * m + ip) * inner + i) * pitch;
         }
-        Tout* orow = out + r * nx;
+        Tout* orow = out + r * pitch;
         for (int x0 = lane; x0 < nx; x0 += 32 * U) {
             Tout acc[U];
 #pragma unroll
@@ -838,13 +838,13 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
                 Tw* x = (Tw*)rx;
                 const AxisT<Tw> ax = p.level<Tw>(l).ax[3];
                 if (zoff >= 0 && pair)
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax, (int)rx_pitch<Tw>(lv.nc[3])));
                 else if (zoff >= 0)
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax, (int)rx_pitch<Tw>(lv.nc[3])));
                 else if (pair)
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, true><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax, (int)rx_pitch<Tw>(lv.nc[3])));
                 else
-                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax));
+                    MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, true, Tw, false><<<g, RT, smx, st>>>(in, out, coarse, lv, zo, x, ax, (int)rx_pitch<Tw>(lv.nc[3])));
             };
             if (rx_f64) go(double(0));
             else go(T(0));
@@ -852,17 +852,17 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
         }
         const AxisT<T> none{};
         if (zoff >= 0 && pair)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none, 0));
         else if (zoff >= 0 && sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, zo, nullptr, none, 0));
         else if (zoff >= 0)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, zo, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, true, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, zo, nullptr, none, 0));
         else if (pair)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, true><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none, 0));
         else if (sm)
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, true, false, T, false><<<g, RT, sm, st>>>(in, out, coarse, lv, 0, nullptr, none, 0));
         else
-            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0, nullptr, none));
+            MGB_LAUNCH("k3_coeff", st, k3_coeff<T, U, false, false, false, T, false><<<g, RT, 0, st>>>(in, out, coarse, lv, 0, nullptr, none, 0));
     });
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
@@ -897,23 +897,24 @@ mgard_status rows3_fill(const Plan& p, int l, const T* z, const T* coarse, T* ou
 
 template <typename T, typename Tw>
 mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0, void* t1,
-                           T sign, cudaStream_t st, int64_t zoff, bool x_done) {
+                           T sign, cudaStream_t st, int64_t zoff, bool x_done, unsigned* status) {
     const Level<Tw>& lw = p.level<Tw>(l);
     const Level<T>& lt = p.level<T>(l);
     const int nz = (int)lt.n[1], ny = (int)lt.n[2], nx = (int)lt.n[3];
     const int ncz = (int)lt.nc[1], ncy = (int)lt.nc[2], ncx = (int)lt.nc[3];
     Tw* b0 = (Tw*)t0;
     Tw* b1 = (Tw*)t1;
+    const int64_t P = rx_pitch<Tw>(ncx);   // row pitch of the intermediates
     // x (always active)
     const RowCfg cx = p.row_cfg(l, RK_RX), cr = p.row_cfg(l, RK_RROWS);
     const int gx = row_grid((int64_t)nz * ny, cx.bpsm);
     if (!x_done) with_cfg(cx, ncx, true, [&](auto u) {
         if (zoff >= 0)
             MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value, true><<<gx, RT, 0, st>>>(
-                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], zoff));
+                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], zoff, (int)P));
         else
             MGB_LAUNCH("k3_restrict_x", st, k3_restrict_x<T, Tw, decltype(u)::value, false><<<gx, RT, 0, st>>>(
-                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], 0));
+                z, b0, nz, ny, nx, ncz, ncy, ncx, lw.ax[3], 0, (int)P));
     });
     MGB_CUDA(cudaGetLastError());
     Tw* cur = b0;
@@ -923,11 +924,11 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     bool y_solved = false, z_solved = false;
     if (lt.ax[2].fcls) {   // y: rows (z, Jy) of length ncx
         const AxisT<Tw>& a = lw.ax[2];
-        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, nz, ny, ncy, ncx, a, st, &y_solved));
+        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, nz, ny, ncy, P, a, st, &y_solved, status));
         if (!y_solved) {
             with_cfg(cr, ncx, true, [&](auto u) {
                 MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)nz * ncy, cr.bpsm), RT, 0, st>>>(
-                    cur, nxt, nz, ny, ncy, 1, ncx, a.rw));
+                    cur, nxt, nz, ny, ncy, 1, ncx, a.rw, (int)P));
             });
             MGB_CUDA(cudaGetLastError());
         }
@@ -935,12 +936,12 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     }
     if (lt.ax[1].fcls) {   // z: rows (Jz, y) of length ncx
         const AxisT<Tw>& a = lw.ax[1];
-        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, 1, nz, ncz, (int64_t)ncy * ncx, a, st,
-                                           &z_solved));
+        MGB_TRY(restrict_solve_strided<Tw>(cur, nxt, 1, nz, ncz, (int64_t)ncy * P, a, st,
+                                           &z_solved, status));
         if (!z_solved) {
             with_cfg(cr, ncx, true, [&](auto u) {
                 MGB_LAUNCH("k3_restrict_rows", st, k3_restrict_rows<Tw, Tw, decltype(u)::value><<<row_grid((int64_t)ncz * ncy, cr.bpsm), RT, 0, st>>>(
-                    cur, nxt, 1, nz, ncz, ncy, ncx, a.rw));
+                    cur, nxt, 1, nz, ncz, ncy, ncx, a.rw, (int)P));
             });
             MGB_CUDA(cudaGetLastError());
         }
@@ -948,13 +949,13 @@ mgard_status rows3_correct(const Plan& p, int l, const T* z, T* coarse, void* t0
     }
     // remaining solves: z, y (strided lines), then x (contiguous, fused correction add)
     if (lt.ax[1].fcls && !z_solved)
-        MGB_TRY((solve_strided<Tw, T>(cur, 1, ncz, (int64_t)ncy * ncx, lw.ax[1].tsub, lw.ax[1].tinv,
+        MGB_TRY((solve_strided<Tw, T>(cur, 1, ncz, (int64_t)ncy * P, lw.ax[1].tsub, lw.ax[1].tinv,
                                       lw.ax[1].tcp, (T*)nullptr, (Tw)sign, st)));
     if (lt.ax[2].fcls && !y_solved)
-        MGB_TRY((solve_strided<Tw, T>(cur, ncz, ncy, ncx, lw.ax[2].tsub, lw.ax[2].tinv,
+        MGB_TRY((solve_strided<Tw, T>(cur, ncz, ncy, P, lw.ax[2].tsub, lw.ax[2].tinv,
                                       lw.ax[2].tcp, (T*)nullptr, (Tw)sign, st)));
     MGB_TRY((solve_contiguous<Tw, T>(cur, (int64_t)ncz * ncy, ncx, lw.ax[3].tsub, lw.ax[3].tinv,
-                                     lw.ax[3].tcp, coarse, (Tw)sign, st)));
+                                     lw.ax[3].tcp, coarse, (Tw)sign, st, P)));
     return MGARD_OK;
 }
 
@@ -1012,10 +1013,13 @@ INST(float)
 INST(double)
 #undef INST
 template mgard_status rows3_correct<float, float>(const Plan&, int, const float*, float*, void*,
-                                                  void*, float, cudaStream_t, int64_t, bool);
+                                                  void*, float, cudaStream_t, int64_t, bool,
+                                                  unsigned*);
 template mgard_status rows3_correct<float, double>(const Plan&, int, const float*, float*, void*,
-                                                  void*, float, cudaStream_t, int64_t, bool);
+                                                  void*, float, cudaStream_t, int64_t, bool,
+                                                  unsigned*);
 template mgard_status rows3_correct<double, double>(const Plan&, int, const double*, double*,
-                                                    void*, void*, double, cudaStream_t, int64_t, bool);
+                                                    void*, void*, double, cudaStream_t, int64_t,
+                                                    bool, unsigned*);
 
 }  // namespace mgb
