@@ -25,7 +25,7 @@ namespace mgb {
 
 namespace {
 
-constexpr int BATCH_STREAMS = 8;
+constexpr int BATCH_STREAMS = 32;
 constexpr size_t BATCH_CACHE = 4;
 
 struct BatchKey {
