@@ -26,6 +26,10 @@ quantize    level-wise quantization to dictionary symbols + outliers
 huffman     deterministic Huffman code lengths, canonical codes, chunked
             MSB-first bit packing and decoding
 pipeline    compress / decompress on top of the above, plus verification
+mdr         refactoring: bit-plane segments of every level's coefficients,
+            their L-infinity error estimate, greedy plane requests and
+            reconstruction
+predictor   features, MLP and Adam of the learned tolerance predictor
 
 Parity status: every function here is pinned by the CPU tests in
 ``tests/test_oracle_*.py`` (identities, brute-force dense projections,
