@@ -362,6 +362,78 @@ mgard_status mgard_compress_to_ratio(const void* field, int ndim, const int64_t*
 /* Read the header of a compressed buffer (host or device pointer). */
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
                         mgard_dtype* dtype, double* tol_abs, int* nlevels);
+/* ---- Refactoring: progressive retrieval ----------------------------------
+ * Paper: "Software design" (the refactoring pipeline: the multilevel
+ * coefficients are encoded into precision segments, an error estimate is
+ * kept per segment, and retrieval picks segments greedily until the
+ * requested error is met) and "APIs" (MDRefactor, MDRequest, MDReconstruct).
+ *
+ * A refactored buffer is an mgard_mdr_header followed, for every level l
+ * (l = 0 the coarsest), by the level's sign plane and its `planes` magnitude
+ * planes (plane 0 the most significant), each level[l].words uint32 words,
+ * starting at byte level[l].offset (16-byte aligned).  The coefficients of a
+ * level are in level order (level 0's nodes, then the nodes new on each
+ * level, row-major in the level grid); coefficient 32 w + i sits in bit i of
+ * word w.  Plane b holds bit planes-1-b of q = floor(|c| 2^(planes -
+ * exponent)); the sign plane holds c < 0.  Reading P planes of a level
+ * reconstructs every coefficient within 2^(exponent - P) (0 when q's first P
+ * bits are 0, else the middle of the truncation interval).  The L-infinity
+ * error of the recomposed field is then at most sum_l weight_l
+ * 2^(exponent_l - P_l) in exact arithmetic (weight_0 = 1, weight_l = 1 + K_l
+ * as in the compressor's bound; all-zero levels count 0); the float
+ * arithmetic of decomposition and recomposition adds its own rounding.
+ * Grids of up to three active axes (MGARD_ESHAPE otherwise). */
+#define MGARD_MDR_MAX_LEVELS 64
+typedef struct {
+    uint64_t count;      /* coefficients of the level */
+    uint64_t offset;     /* byte offset of the level's sign plane in the buffer */
+    uint32_t words;      /* words per plane: ceil(count / 32) */
+    int32_t exponent;    /* every |c| < 2^exponent (0 for an all-zero level) */
+    uint32_t nonzero;    /* 0 if every coefficient of the level is 0 */
+    uint32_t reserved;
+    double weight;       /* weight of the level's errors in the estimate */
+} mgard_mdr_level;
+
+typedef struct {
+    char magic[8];       /* "MGARDMDR" */
+    uint32_t version;    /* 1 */
+    uint32_t dtype;      /* mgard_dtype of the field */
+    uint32_t ndim;
+    uint32_t nlevels;    /* L + 1 */
+    uint32_t planes;     /* magnitude planes per level, 1..32 */
+    uint32_t reserved;
+    int64_t shape[4];
+    double max_abs;      /* max |u| of the refactored field */
+    uint64_t total_bytes;
+    mgard_mdr_level level[MGARD_MDR_MAX_LEVELS + 1];
+} mgard_mdr_header;
+
+/* Bytes of a refactored buffer of this shape at most. */
+size_t mgard_refactor_bound(int ndim, const int64_t* shape, int planes);
+/* MDRefactor: decompose `field` (device) and write the header and every
+ * level's sign and magnitude planes to `out` (device, 16-byte aligned;
+ * *out_bytes: capacity in, size out; MGARD_ECAPACITY with the size if
+ * short).  planes in 1..32.  MGARD_ENONFINITE for NaN/Inf input.
+ * Synchronizes the stream. */
+mgard_status mgard_refactor(const void* field, int ndim, const int64_t* shape, mgard_dtype dtype,
+                            int planes, void* out, size_t* out_bytes, void* stream);
+/* MDRequest (host only): the planes to read per level (planes_per_level,
+ * host array of header->nlevels) for an absolute L-infinity tolerance,
+ * chosen greedily: while the estimate exceeds tol, add the next plane of
+ * the level whose plane lowers the estimate most per byte (the first plane
+ * of a level also costs its sign plane; ties to the lower level).  *bytes
+ * receives the size of the selected planes, *estimate the estimate.  If
+ * every plane is selected and the estimate still exceeds tol, all planes
+ * are returned with MGARD_EBOUND. */
+mgard_status mgard_request(const mgard_mdr_header* header, double tol, int32_t* planes_per_level,
+                           uint64_t* bytes, double* estimate);
+/* MDReconstruct: decode planes_per_level[l] planes of every level from
+ * `refactored` (device; only the header and the selected planes are read)
+ * and recompose into `field` (device, the header's shape and dtype).
+ * Synchronizes the stream. */
+mgard_status mgard_reconstruct(const void* refactored, const int32_t* planes_per_level,
+                               void* field, void* stream);
+
 /* ---- Tracing -------------------------------------------------------------
  * When enabled, every kernel launch of the library is bracketed by a pair
  * of CUDA events recorded on its launch stream (adds about a microsecond

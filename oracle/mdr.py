@@ -121,8 +121,12 @@ def level_bound(e: int, P: int, nonzero: bool) -> float:
 
 
 def estimate(r, P) -> float:
-    return float(sum(w * level_bound(e, p, nz)
-                     for w, e, p, nz in zip(r["weights"], r["exponents"], P, r["nonzero"])))
+    """sum_l w_l d_l, added left to right in level order (each term is exact:
+    a power of two times w_l)."""
+    total = 0.0
+    for w, e, p, nz in zip(r["weights"], r["exponents"], P, r["nonzero"]):
+        total += float(w) * level_bound(e, p, nz)
+    return total
 
 
 def request(r, tol: float):

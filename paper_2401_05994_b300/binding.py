@@ -9,6 +9,7 @@ on import of the library (there is no fallback path).
 from __future__ import annotations
 
 import ctypes
+import struct
 import math
 import os
 from typing import Optional
@@ -92,6 +93,12 @@ SIGNATURES = {
                                             ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp),
                                             ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                             ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp]),
+    "mgard_refactor_bound": (ctypes.c_size_t, [ctypes.c_int, _c_int64_p, ctypes.c_int]),
+    "mgard_refactor": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp,
+                                      ctypes.POINTER(ctypes.c_size_t), _vp]),
+    "mgard_request": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_uint64), _c_double_p]),
+    "mgard_reconstruct": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), _vp, _vp]),
     "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
                                   ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
     "mgard_timing_enable": (None, [ctypes.c_int]),
@@ -557,4 +564,74 @@ def decompress(buf, out=None):
     nbytes = buf.nbytes if host else buf.numel()
     p = ctypes.c_void_p(_ptr(out).value)
     _check(lib().mgard_decompress(_ptr(buf), nbytes, ctypes.byref(p), 1, _stream()))
+    return out
+
+
+# -- refactoring (progressive retrieval) ------------------------------------
+MDR_HEADER_FMT = "<8s6I4qdQ"
+MDR_LEVEL_FMT = "<QQIiIId"
+MDR_MAX_LEVELS = 64
+MDR_HEADER_SIZE = (struct.calcsize(MDR_HEADER_FMT)
+                   + (MDR_MAX_LEVELS + 1) * struct.calcsize(MDR_LEVEL_FMT))
+
+
+def mdr_header(buf) -> dict:
+    """Parsed header of a refactored buffer (device tensor or bytes); the
+    raw header bytes are under "raw"."""
+    raw = (buf[:MDR_HEADER_SIZE].cpu().numpy().tobytes() if isinstance(buf, torch.Tensor)
+           else bytes(buf[:MDR_HEADER_SIZE]))
+    f = struct.unpack_from(MDR_HEADER_FMT, raw, 0)
+    h = dict(magic=f[0], version=f[1], dtype=f[2], ndim=f[3], nlevels=f[4], planes=f[5],
+             shape=tuple(f[7:7 + f[3]]), max_abs=f[11], total_bytes=f[12], raw=raw)
+    base = struct.calcsize(MDR_HEADER_FMT)
+    size = struct.calcsize(MDR_LEVEL_FMT)
+    h["levels"] = []
+    for l in range(h["nlevels"]):
+        c, off, words, e, nz, _, w = struct.unpack_from(MDR_LEVEL_FMT, raw, base + l * size)
+        h["levels"].append(dict(count=c, offset=off, words=words, exponent=e, nonzero=bool(nz),
+                                weight=w))
+    return h
+
+
+def refactor_bound(shape, planes: int = 32) -> int:
+    nd, sh = _shape(shape)
+    return int(lib().mgard_refactor_bound(nd, sh, planes))
+
+
+def refactor(field: torch.Tensor, planes: int = 32):
+    """MDRefactor of a CUDA tensor: (device uint8 buffer, parsed header)."""
+    _require_cuda(field)
+    nd, sh = _shape(field.shape)
+    cap = refactor_bound(field.shape, planes)
+    out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+    nbytes = ctypes.c_size_t(cap)
+    _check(lib().mgard_refactor(_ptr(field.contiguous()), nd, sh, _dtype_code(field.dtype), planes,
+                                _ptr(out), ctypes.byref(nbytes), _stream()))
+    out = out[:nbytes.value]
+    return out, mdr_header(out)
+
+
+def request(header: dict, tol: float):
+    """MDRequest: (planes per level, bytes of those planes, estimate)."""
+    raw = ctypes.create_string_buffer(header["raw"], len(header["raw"]))
+    n = header["nlevels"]
+    P = (ctypes.c_int32 * n)()
+    nb = ctypes.c_uint64()
+    est = ctypes.c_double()
+    st = lib().mgard_request(ctypes.cast(raw, ctypes.c_void_p), float(tol), P, ctypes.byref(nb),
+                             ctypes.byref(est))
+    if st not in (0, 8):   # MGARD_EBOUND still returns every plane
+        _check(st)
+    return list(P), nb.value, est.value
+
+
+def reconstruct(buf: torch.Tensor, planes, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """MDReconstruct from a refactored device buffer with `planes` per level."""
+    _require_cuda(buf)
+    h = mdr_header(buf)
+    dt = torch.float32 if h["dtype"] == 0 else torch.float64
+    if out is None:
+        out = torch.empty(h["shape"], dtype=dt, device=buf.device)
+    P = (ctypes.c_int32 * len(planes))(*[int(p) for p in planes])
+    _check(lib().mgard_reconstruct(_ptr(buf), P, _ptr(out), _stream()))
     return out
