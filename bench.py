@@ -46,11 +46,11 @@ SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
 # capture of the same command (profiles/dram_traffic_513cube.md; one pass per
 # launch).  Valid for the kernel versions captured.
 NCU_TRAFFIC_513 = {
-    "k_restrict_solve": (930.9e6, 241.1e6, 20), "k_decode": (331.8e6, 496.8e6, 1),
-    "k3_coeff": (662.1e6, 805.7e6, 5), "k_pack": (353.1e6, 189.4e6, 1),
-    "k3_fill": (618.1e6, 513.3e6, 5), "k3_restrict_x": (542.2e6, 236.1e6, 6),
-    "k_quantize_stream": (553.5e6, 281.8e6, 1), "k_solve_warp": (311.1e6, 32.7e6, 10),
-    "k_maxabs": (540.1e6, 3.0e6, 1), "k_chunk_count": (270.2e6, 1.5e6, 1),
+    "k_restrict_solve": (943.0e6, 251.9e6, 20), "k_decode": (332.2e6, 497.2e6, 1),
+    "k3_coeff": (671.6e6, 812.0e6, 5), "k_pack": (353.1e6, 189.1e6, 1),
+    "k3_fill": (618.0e6, 515.0e6, 5), "k3_restrict_x": (560.0e6, 242.5e6, 8),
+    "k_quantize_stream": (553.4e6, 282.5e6, 1), "k_solve_warp": (313.3e6, 33.9e6, 10),
+    "k_maxabs": (540.1e6, 3.3e6, 1), "k_chunk_count": (270.1e6, 1.4e6, 1),
 }
 
 
@@ -442,6 +442,79 @@ def run_ratio(args, rank, world, dev):
         }))
 
 
+def run_precision(args, rank, dev):
+    """Float32 against float64 on the configured fields (not timed): per level
+    the largest difference between the float32 and the float64 coefficients
+    (relative to the level's largest float64 coefficient, and in bins of the
+    rel 1e-3 width), the share of quantized indices that differ at every
+    tolerance of the sweep, and the FP64-measured error of float32
+    compress + decompress against its bound.  The reference is the library's
+    own float64 decomposition, which the parity tests hold to the FP64 oracle
+    within 1e-11 of max|u|."""
+    from paper_2401_05994_b300 import binding, synth
+    if rank != 0:
+        return
+    cases = [("513^3 f32 GRF, E(k)~k^-5/3", (args.shape,) * 3,
+              lambda: synth.gaussian_random_field((args.shape,) * 3, beta=BETA, seed=1, device=dev),
+              (1e-2, 1e-3, 1e-4, 1e-5), math.inf),
+             ("1025^3 f32, k^-5/3 + 50 blobs (L-inf)", (1025,) * 3,
+              lambda: synth.blobs_field((1025,) * 3, seed=5, device=dev), (1e-4,), math.inf)]
+    out = []
+    for name, shape, make, tols, s in cases:
+        u = make().contiguous()
+        v32 = binding.decompose(u.clone())
+        v64 = binding.decompose(u.double())
+        umax = float(u.abs().max())
+        w3 = binding.bin_widths(shape, 1e-3 * umax, s)[0]
+        L = binding.levels(shape)
+        # level of every node in the in-place layout: the coarsest level on which
+        # the node exists (even positions plus the last, level by level)
+        lev = torch.zeros(shape, dtype=torch.int8, device=dev)
+        for d, n in enumerate(shape):
+            idx = torch.arange(n, device=dev)
+            lv_d = torch.full((n,), L, dtype=torch.int8, device=dev)
+            pos, m = idx.clone(), n
+            alive = torch.ones(n, dtype=torch.bool, device=dev)
+            for k in range(L, 0, -1):
+                coarse = alive & ((pos % 2 == 0) | (pos == m - 1))
+                lv_d = torch.where(coarse, torch.full_like(lv_d, k - 1), lv_d)
+                alive = coarse
+                pos = torch.where(pos == m - 1, torch.full_like(pos, (m // 2 + 1) - 1), pos // 2)
+                m = m // 2 + 1
+            view = [1] * len(shape)
+            view[d] = n
+            lv_d = lv_d.view(view)
+            lev = torch.maximum(lev, lv_d) if d else lv_d.expand(shape).clone()
+        per_level = []
+        for l in range(L + 1):
+            mask = lev == l
+            a = v32[mask].double()
+            b = v64[mask]
+            cm = float(b.abs().max())
+            dm = float((a - b).abs().max())
+            per_level.append({"level": l, "nodes": int(mask.sum()), "max_abs_diff": dm,
+                              "rel_to_level_max": dm / cm if cm else 0.0, "bins_at_1e-3": dm / w3})
+        del lev
+        sweep = []
+        for tol in tols:
+            w = binding.bin_widths(shape, tol * umax, s)
+            s32, _, _ = binding.quantize(v32, w)
+            s64, _, _ = binding.quantize(v64, w)
+            mism = int((s32 != s64).sum())
+            buf = binding.compress(u, tol, s)
+            rec = binding.decompress(buf)
+            err = binding.error_norm(u, rec, s)
+            meta = binding.info(buf)
+            sweep.append({"tol_rel": tol, "index_mismatch": mism, "index_mismatch_frac": mism / u.numel(),
+                          "max_error": err, "tol_abs": meta["tol_abs"], "error_over_bound": err / meta["tol_abs"],
+                          "ratio": u.numel() * 4 / buf.numel()})
+            del buf, rec
+        out.append({"case": name, "levels": per_level, "sweep": sweep})
+        del u, v32, v64
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "float32 against float64 (untimed)", "cases": out}))
+
+
 def run_refactor(args, rank, world, dev, barrier):
     """Refactoring for progressive retrieval of the 513^3 field: refactor
     (decomposition plus 32 bit planes per level) timed as field GB/s, then
@@ -571,7 +644,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the row-kernel autotuner (mgard_autotune) before timing")
     ap.add_argument("--workload", default="cube",
-                    choices=["cube", "batch64", "ratio", "blobs1025", "refactor"],
+                    choices=["cube", "batch64", "ratio", "blobs1025", "refactor", "precision"],
                     help="cube: one 513^3 field (the headline); batch64: 64 uneven fields "
                          "through batched compression")
     args = ap.parse_args()
@@ -598,6 +671,11 @@ def main():
 
     if args.workload == "blobs1025":
         run_blobs(args, rank, world, dev, barrier)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == "precision":
+        run_precision(args, rank, dev)
         if world > 1:
             dist.destroy_process_group()
         return
