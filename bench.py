@@ -343,6 +343,12 @@ def run_batch(args, rank, world, dev, barrier):
     time.sleep(0.2)
     ms = timed(step, args.steps)
     clocks = sampler.stop()
+    if args.profile_step:   # one compression of the batch inside a profiler range
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        compress_graph()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     ms_graph = timed(compress_graph, args.steps)
     ms_eager = timed(compress_eager, args.steps)
     ms_each = timed(compress_each, max(3, args.steps // 2))

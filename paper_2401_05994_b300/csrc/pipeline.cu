@@ -26,6 +26,7 @@ struct WidthArgs {
     int L;
     int rel;                      // relative tolerance: scale by the norm of the data
     int snorm;                    // finite s: the norm comes from the level energies
+    int finest;                   // s = 0: the level sums telescope to E_L alone
     double tol;
     double den[MAXLV + 1];        // width denominators of every level
     double f[MAXLV + 1];          // 4^(s l)
@@ -34,8 +35,8 @@ struct WidthArgs {
 
 // One warp: norm of the data (relative tolerances), tol_abs and the widths.
 // Norm: max|u| (L-infinity), or sqrt(E_0 + sum_l 4^(s l) max(E_l - E_{l-1}, 0))
-// with E_l = u_l^T M_l u_l (s-norm).  Sums and maxima run in a fixed order,
-// and every lane ends with the same value.
+// with E_l = u_l^T M_l u_l (s-norm; for s = 0 the sum is E_L alone).  Sums and
+// maxima run in a fixed order, and every lane ends with the same value.
 __global__ void k_widths(WidthArgs a, const double* __restrict__ maxparts,
                          const double* __restrict__ eparts, CompressMeta* meta,
                          double* __restrict__ w) {
@@ -47,6 +48,11 @@ __global__ void k_widths(WidthArgs a, const double* __restrict__ maxparts,
             for (int i = lane; i < RED_PARTS; i += 32) m = fmax(m, maxparts[i]);
             for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
             nrm = m;
+        } else if (a.finest) {   // ||u||_0^2 = E_L (the L2 norm of the interpolant)
+            double e = 0.0;
+            for (long long i = a.eoff[a.L] + lane; i < a.eoff[a.L + 1]; i += 32) e += eparts[i];
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            nrm = sqrt(fmax(e, 0.0));
         } else {
             double total = 0.0, prev = 0.0;
             for (int l = 0; l <= a.L; ++l) {
@@ -184,11 +190,17 @@ mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tol
     double* parts = w.parts.template as<double>();
     MGB_TRY(max_abs_partials<T>(din, N, parts, &meta->status, st));
     const bool energy = mode == MGARD_REL && !std::isinf(s);
+    // s = 0: sum_l (E_l - E_{l-1}) telescopes to E_L = u^T M_L u, the energy
+    // of the input itself; other s need every level's energy
+    const bool finest = energy && s == 0.0;
+    if (finest)
+        MGB_TRY(mass_norm2_partials<T>(p, p.L, din, parts + RED_PARTS + energy_parts_offset(p, p.L), st));
     // shapes on the row kernels keep every level's coefficients in symbol
     // order in `top` (quantization then streams through it)
     T* top = w.top.template as<T>();
     w.py.status = &meta->status;
-    MGB_TRY(decompose_pyramid<T>(p, din, top, w.py, st, nullptr, energy ? parts + RED_PARTS : nullptr,
+    MGB_TRY(decompose_pyramid<T>(p, din, top, w.py, st, nullptr,
+                                 energy && !finest ? parts + RED_PARTS : nullptr,
                                  rows3_ok(p) ? top : nullptr));
     return MGARD_OK;
 }
@@ -210,6 +222,7 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
     a.L = L;
     a.rel = mode == MGARD_REL;
     a.snorm = energy;
+    a.finest = energy && s == 0.0;
     a.tol = tol;
     width_denominators(p, s, a.den);
     for (int l = 0; l <= L; ++l) {

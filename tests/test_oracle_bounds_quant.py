@@ -88,6 +88,20 @@ def test_s0_norm_is_l2_norm_of_p1_function():
     assert abs(bounds.s_norm(u, 0.0) ** 2 - exact) < 1e-10
 
 
+
+@pytest.mark.parametrize("shape", [(33,), (17, 9), (9, 10, 11)])
+def test_s0_norm_telescopes_to_the_finest_energy(shape):
+    """The level increments E_l - E_{l-1} are squared norms of differences of
+    nested L2 projections, so none is negative and for s = 0 their sum is
+    E_L = u^T M_L u: the norm needs the finest energy alone."""
+    u = np.random.default_rng(len(shape)).standard_normal(shape).cumsum(axis=0)
+    h = grid.hierarchy(shape)
+    Q = bounds.projections(u)
+    E = [bounds.mass_norm2(h, l, Q[l]) for l in range(h.L + 1)]
+    assert all(E[l] >= E[l - 1] * (1 - 1e-12) for l in range(1, h.L + 1))
+    EL = bounds.mass_norm2(h, h.L, u)
+    assert abs(bounds.s_norm(u, 0.0) ** 2 - EL) <= 1e-12 * EL
+
 def _snorm_golden():
     """Rows of tests/golden/snorm_1d.txt: hand-derived level energies of two
     fine-grid hats on x = 0..4 and the s-norm and width values built from
