@@ -29,6 +29,8 @@ pipeline    compress / decompress on top of the above, plus verification
 mdr         refactoring: bit-plane segments of every level's coefficients,
             their L-infinity error estimate, greedy plane requests and
             reconstruction
+qoi         linear quantities of interest: representer, dual norm and the
+            tolerance that bounds a QoI's error
 predictor   features, MLP and Adam of the learned tolerance predictor
 
 Parity status: every function here is pinned by the CPU tests in
