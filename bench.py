@@ -575,6 +575,93 @@ def run_refactor(args, rank, world, dev, barrier):
         }))
 
 
+def qoi_weights(shape, dev):
+    """Weights of the QoI workload's functionals on an n^3 grid (FP64):
+    the average over the central 64^3 box, a Gaussian-weighted average
+    (sigma 32 cells) about the centre, the average over the middle z-plane
+    and the value at the central node."""
+    n = shape[0]
+    c = n // 2
+    out = {}
+    g = torch.zeros(shape, dtype=torch.float64, device=dev)
+    g[c - 32:c + 32, c - 32:c + 32, c - 32:c + 32] = 1.0
+    out["box64_average"] = g / g.sum()
+    x = (torch.arange(n, dtype=torch.float64, device=dev) - c) ** 2
+    g = torch.exp(-(x[:, None, None] + x[None, :, None] + x[None, None, :]) / (2.0 * 32.0 ** 2))
+    out["gaussian_average"] = g / g.sum()
+    g = torch.zeros(shape, dtype=torch.float64, device=dev)
+    g[c] = 1.0
+    out["plane_average"] = g / g.sum()
+    g = torch.zeros(shape, dtype=torch.float64, device=dev)
+    g[c, c, c] = 1.0
+    out["point_value"] = g
+    return out
+
+
+def run_qoi(args, rank, world, dev, barrier):
+    """Linear-QoI error control on the 513^3 field: for each functional and
+    s in {0, 1, inf} the dual norm (its time), the s-norm tolerance that
+    keeps the QoI's error within 1e-2 or 1e-3 max|u|, the compression time and
+    ratio at that tolerance, and the QoI's error after decompression (FP64,
+    on the device).  The headline value is QoI-controlled compression of the
+    box average at s = 0, dual norm included, in field GB/s."""
+    from paper_2401_05994_b300 import binding, synth
+    shape = (args.shape,) * 3
+    u = synth.gaussian_random_field(shape, beta=BETA, seed=1 + rank, device=dev)
+    nbytes = u.numel() * 4
+    umax = float(u.abs().max())
+    comp = torch.empty(binding.compress_bound(shape), dtype=torch.uint8, device=dev)
+    out = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(a.elapsed_time(b) / steps, world, dev), r
+
+    rows = []
+    headline = None
+    for name, g in qoi_weights(shape, dev).items():
+        q0 = binding.qoi_value(u, g)
+        for s in (0.0, 1.0, math.inf):
+            ms_norm, nq = timed(lambda: binding.qoi_norm(g, s), max(1, args.steps // 5))
+            for rel in (1e-2, 1e-3):
+                tol_q = rel * umax
+                tol = tol_q / nq
+                ms_c, buf = timed(lambda: binding.compress(u, tol, s, binding.ABS, out=comp), args.steps)
+                binding.decompress(buf, out=out)
+                err = abs(binding.qoi_value(out, g) - q0)
+                rows.append({"qoi": name, "s": "inf" if math.isinf(s) else s, "qoi_tol_rel": rel,
+                             "dual_norm": nq, "tol_snorm": tol, "dual_norm_ms": ms_norm,
+                             "compress_ms": ms_c, "ratio": nbytes / buf.numel(), "qoi_error": err,
+                             "qoi_tol": tol_q, "ok": err <= tol_q})
+            if name == "box64_average" and s == 0.0:
+                ms_q, _ = timed(lambda: binding.compress_qoi(u, g, 1e-3 * umax, 0.0, out=comp),
+                                args.steps)
+                headline = ms_q
+        del g
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "QoI-controlled compress GB/s (box average, s = 0, dual norm included)",
+            "value": job_gbs(nbytes, 1, world, headline), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": headline,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.shape}^3 f32 Gaussian random field, E(k)~k^-5/3; "
+                                   "QoI tolerances 1e-2 and 1e-3 max|u|",
+                       "parallelism": f"replicas x{world}"},
+            "cases": rows}))
+
+
 def run_blobs(args, rank, world, dev, barrier):
     """1025^3 float32 multi-scale field (k^-5/3 background + 50 Gaussian
     blobs, 4.3 GB): compression (decompose + quantize + Huffman) and
@@ -650,7 +737,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the row-kernel autotuner (mgard_autotune) before timing")
     ap.add_argument("--workload", default="cube",
-                    choices=["cube", "batch64", "ratio", "blobs1025", "refactor", "precision"],
+                    choices=["cube", "batch64", "ratio", "blobs1025", "refactor", "precision", "qoi"],
                     help="cube: one 513^3 field (the headline); batch64: 64 uneven fields "
                          "through batched compression")
     args = ap.parse_args()
@@ -682,6 +769,11 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args, rank, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == "qoi":
+        run_qoi(args, rank, world, dev, barrier)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -434,6 +434,42 @@ mgard_status mgard_request(const mgard_mdr_header* header, double tol, int32_t* 
 mgard_status mgard_reconstruct(const void* refactored, const int32_t* planes_per_level,
                                void* field, void* stream);
 
+/* ---- Linear quantities of interest ("Software design": guarantees on
+ * quantities derived from the data; "Application impact", plasma physics) -
+ * A linear QoI is Q(v) = sum_p g_p v_p with FP64 weights g: device memory,
+ * one weight per grid node, row-major in the field's shape.  Its
+ * representer is the P1 function r with M_L r = g (M_L the finest grid's
+ * mass matrix, unit spacing), so Q(e) = <r, e>_{L2}; splitting both over the
+ * level spaces (Q_l - Q_{l-1}) V_L gives |Q(e)| <= ||Q||_{-s} ||e||_s with
+ * ||Q||_{-s} = ||r||_{-s}, the s-norm with -s in place of s.  For
+ * s = INFINITY the dual norm is ||g||_1 (|Q(e)| <= ||g||_1 max|e|).
+ * MGARD_ENONFINITE when g holds NaN or Inf. */
+
+/* r = M_L^{-1} g (device, N doubles; r may equal g): one FP64 tridiagonal
+ * solve per line along every active axis.  Stream-ordered after a check of
+ * the weights (which synchronizes). */
+mgard_status mgard_qoi_representer(const double* g, int ndim, const int64_t* shape, double* r,
+                                   void* stream);
+/* *norm = ||Q||_{-s} (host) on the hierarchy of max_levels levels (-1: all,
+ * as mgard_compress uses); s >= 0 or INFINITY, else MGARD_EINVAL.  The
+ * representer's level energies come from the FP64 decomposition.
+ * Synchronizes the stream. */
+mgard_status mgard_qoi_norm(const double* g, int ndim, const int64_t* shape, int max_levels,
+                            double s, double* norm, void* stream);
+/* *value = Q(field) = sum_p g_p field_p accumulated in FP64 in a fixed
+ * order (field: device, dtype).  Synchronizes the stream. */
+mgard_status mgard_qoi_value(const void* field, const double* g, int ndim, const int64_t* shape,
+                             mgard_dtype dtype, double* value, void* stream);
+/* Compress so that |Q(decompress(out)) - Q(field)| <= tol_qoi: mgard_compress
+ * with the absolute s-norm tolerance tol_qoi / ||Q||_{-s} (written to
+ * *tol_used when non-null).  field, out, out_bytes, out_preallocated and the
+ * ownership of the output are those of mgard_compress; g is device memory.
+ * MGARD_EINVAL for tol_qoi <= 0, s < 0 or weights that are all zero. */
+mgard_status mgard_compress_qoi(const void* field, int ndim, const int64_t* shape,
+                                mgard_dtype dtype, const double* g, double tol_qoi, double s,
+                                void** out, size_t* out_bytes, int out_preallocated,
+                                double* tol_used, void* stream);
+
 /* ---- Tracing -------------------------------------------------------------
  * When enabled, every kernel launch of the library is bracketed by a pair
  * of CUDA events recorded on its launch stream (adds about a microsecond

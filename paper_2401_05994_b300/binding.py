@@ -99,6 +99,13 @@ SIGNATURES = {
     "mgard_request": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_uint64), _c_double_p]),
     "mgard_reconstruct": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), _vp, _vp]),
+    "mgard_qoi_representer": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, _vp, _vp]),
+    "mgard_qoi_norm": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                      _c_double_p, _vp]),
+    "mgard_qoi_value": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int64_p, ctypes.c_int, _c_double_p, _vp]),
+    "mgard_compress_qoi": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, _vp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.c_int, _c_double_p, _vp]),
     "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
                                   ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
     "mgard_timing_enable": (None, [ctypes.c_int]),
@@ -346,6 +353,59 @@ def compress(field, tol: float, s: float = math.inf, mode: int = REL, out=None):
     _check(lib().mgard_compress(_ptr(field), nd, sh, dt, float(tol), float(s), int(mode),
                                 ctypes.byref(p), ctypes.byref(nbytes), 1, _stream()))
     return out[:nbytes.value]
+
+
+def _weights(g: torch.Tensor, shape) -> torch.Tensor:
+    if not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.float64):
+        raise TypeError("QoI weights must be a CUDA float64 tensor")
+    if tuple(g.shape) != tuple(shape):
+        raise ValueError("QoI weights must have the field's shape")
+    return g.contiguous()
+
+
+def qoi_representer(g: torch.Tensor) -> torch.Tensor:
+    """r = M_L^{-1} g on the grid of ``g`` (mgard_qoi_representer)."""
+    g = _weights(g, g.shape)
+    r = torch.empty_like(g)
+    nd, sh = _shape(g.shape)
+    _check(lib().mgard_qoi_representer(_ptr(g), nd, sh, _ptr(r), _stream()))
+    return r
+
+
+def qoi_norm(g: torch.Tensor, s: float, max_levels: int = -1) -> float:
+    """Dual norm ||Q||_{-s} of the QoI with weights ``g`` (||g||_1 for s = inf)."""
+    g = _weights(g, g.shape)
+    nd, sh = _shape(g.shape)
+    out = ctypes.c_double()
+    _check(lib().mgard_qoi_norm(_ptr(g), nd, sh, int(max_levels), float(s), ctypes.byref(out), _stream()))
+    return out.value
+
+
+def qoi_value(field: torch.Tensor, g: torch.Tensor) -> float:
+    """Q(field) = sum g * field in FP64 (mgard_qoi_value)."""
+    g = _weights(g, field.shape)
+    field = field.contiguous()
+    nd, sh = _shape(field.shape)
+    out = ctypes.c_double()
+    _check(lib().mgard_qoi_value(_ptr(field), _ptr(g), nd, sh, _dtype_code(field.dtype),
+                                 ctypes.byref(out), _stream()))
+    return out.value
+
+
+def compress_qoi(field: torch.Tensor, g: torch.Tensor, tol_qoi: float, s: float, out=None):
+    """Compress a CUDA tensor so that the QoI's error stays within ``tol_qoi``
+    (mgard_compress_qoi).  Returns ``(bytes, tol_used)``."""
+    g = _weights(g, field.shape)
+    nd, sh = _shape(field.shape)
+    if out is None:
+        out = torch.empty(compress_bound(field.shape, field.dtype), dtype=torch.uint8, device=field.device)
+    nbytes = ctypes.c_size_t(out.numel())
+    p = ctypes.c_void_p(_ptr(out).value)
+    tol_used = ctypes.c_double()
+    _check(lib().mgard_compress_qoi(_ptr(field), nd, sh, _dtype_code(field.dtype), _ptr(g), float(tol_qoi),
+                                    float(s), ctypes.byref(p), ctypes.byref(nbytes), 1,
+                                    ctypes.byref(tol_used), _stream()))
+    return out[:nbytes.value], tol_used.value
 
 
 BATCH_GRAPH = 1
