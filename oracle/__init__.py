@@ -31,6 +31,8 @@ mdr         refactoring: bit-plane segments of every level's coefficients,
             reconstruction
 qoi         linear quantities of interest: representer, dual norm and the
             tolerance that bounds a QoI's error
+region      region-adaptive L-infinity bounds: far-field tails of the
+            correction operators, dilated boxes and per-node widths
 predictor   features, MLP and Adam of the learned tolerance predictor
 
 Parity status: every function here is pinned by the CPU tests in
