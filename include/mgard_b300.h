@@ -228,7 +228,8 @@ size_t mgard_compress_bound(int ndim, const int64_t* shape, mgard_dtype dtype);
 mgard_status mgard_compress(const void* field, int ndim, const int64_t* shape, mgard_dtype dtype,
                             double tol, double s, mgard_tolmode mode, void** out,
                             size_t* out_bytes, int out_preallocated, void* stream);
-/* Decompress a buffer made by mgard_compress (host or device pointer).
+/* Decompress a buffer made by mgard_compress or mgard_compress_regions
+ * (host or device pointer).
  * out_preallocated = 0: *field receives a new buffer (device memory if the
  * compressed buffer is on the device) to be released with mgard_free;
  * = 1: *field is the caller's buffer (host or device), large enough for the
@@ -469,6 +470,53 @@ mgard_status mgard_compress_qoi(const void* field, int ndim, const int64_t* shap
                                 mgard_dtype dtype, const double* g, double tol_qoi, double s,
                                 void** out, size_t* out_bytes, int out_preallocated,
                                 double* tol_used, void* stream);
+
+/* ---- Region-adaptive error bounds ("Application impact", Earth and
+ * cosmological science: tighter errors kept in chosen regions) ----------
+ * A box is an inclusive index range per axis of the field's shape as passed
+ * (entries beyond ndim ignored) with its own absolute tolerance tol, at
+ * most the background tolerance.  The compressed field then satisfies
+ * |u~(p) - u(p)| <= the smallest tol of the boxes holding p, and <= the
+ * background tolerance everywhere (L-infinity).
+ *
+ * Rule (rigorous, from the recomposition's error propagation): a node
+ * first appearing on level l gets the bin width w 2^-k, w the uniform
+ * L-infinity width of the background tolerance and k the largest k_r of the
+ * boxes whose dilation on level l contains it (0 if none).  Dilation along
+ * an axis: H_0 on level 0 and (rho + 1) H_l + H_{l-1} above, H_l the largest
+ * spacing of level-l nodes.  rho is the smallest radius (0..48) at which the
+ * far-field rows of the correction operators M_{l-1}^{-1} P^T M_l, weighted
+ * by the background width, cost at most 1/8 of the tightest box's
+ * tolerance; k_r the smallest k with 2^-k tol <= tol_r - that far-field
+ * error.  Scaling a coefficient by 2^k is exact, so the compressor scales
+ * and quantizes with w, and the decompressor scales back. */
+#define MGARD_MAX_REGIONS 8
+typedef struct {
+    int64_t lo[4];
+    int64_t hi[4];
+    double tol;
+} mgard_region;
+
+/* Host only: the radius rho and every box's exponent k_r (nregions
+ * entries) for these boxes and background tolerance tol.  MGARD_EINVAL for
+ * more than 8 boxes, boxes outside the field, box tolerances outside
+ * (0, tol] or too small to reach (k above 60); MGARD_ESHAPE for a grid
+ * without levels. */
+mgard_status mgard_region_plan(int ndim, const int64_t* shape, double tol,
+                               const mgard_region* regions, int nregions, int* rho, int32_t* k);
+/* The exponent k of every node (device, N bytes, row-major).  Synchronizes. */
+mgard_status mgard_region_exponents(int ndim, const int64_t* shape, double tol,
+                                    const mgard_region* regions, int nregions, uint8_t* k,
+                                    void* stream);
+/* Compress with region-adaptive bounds: background tolerance tol
+ * (absolute, L-infinity) and the boxes.  The output (format in
+ * include/mgard_format.h: a region header, then an ordinary buffer) is
+ * self-describing; mgard_decompress and mgard_info read it.  field, out,
+ * out_bytes, out_preallocated and ownership as mgard_compress. */
+mgard_status mgard_compress_regions(const void* field, int ndim, const int64_t* shape,
+                                    mgard_dtype dtype, double tol, const mgard_region* regions,
+                                    int nregions, void** out, size_t* out_bytes,
+                                    int out_preallocated, void* stream);
 
 /* ---- Tracing -------------------------------------------------------------
  * When enabled, every kernel launch of the library is bracketed by a pair

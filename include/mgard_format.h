@@ -57,4 +57,37 @@ typedef struct {
     uint64_t total_bytes;
 } mgard_header;
 
+/*
+ * Region-adaptive buffers (mgard_compress_regions) wrap an ordinary buffer:
+ *
+ *   mgard_region_header               (fixed size, below)
+ *   inner     [inner_bytes]           an mgard_compress buffer (L-infinity,
+ *                                     absolute tolerance = the background
+ *                                     tolerance) at byte MGARD_REGION_INNER
+ *
+ * whose coefficients were scaled by 2^k of their node before quantization
+ * (k from the boxes, rho and k below, dilated per level as
+ * include/mgard_b300.h describes); decompression scales them back.
+ */
+#define MGARD_REGION_MAGIC "MGARDRG"
+#define MGARD_REGION_VERSION 1u
+#define MGARD_REGION_SLOTS 8
+
+typedef struct {
+    char magic[8];        /* "MGARDRG\0" */
+    uint32_t version;     /* MGARD_REGION_VERSION */
+    uint32_t nregions;    /* 0 .. MGARD_REGION_SLOTS */
+    int32_t rho;          /* radius of the near field, level-l nodes */
+    int32_t k[MGARD_REGION_SLOTS];   /* width exponent of every box */
+    uint32_t reserved;
+    double tol;           /* background tolerance (absolute) */
+    struct {
+        int64_t lo[4], hi[4];   /* inclusive index box, axes as passed */
+        double tol;
+    } box[MGARD_REGION_SLOTS];
+    uint64_t inner_bytes;
+} mgard_region_header;
+
+#define MGARD_REGION_INNER ((sizeof(mgard_region_header) + 15) & ~(size_t)15)
+
 #endif /* MGARD_FORMAT_H */

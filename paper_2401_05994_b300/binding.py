@@ -106,6 +106,13 @@ SIGNATURES = {
     "mgard_compress_qoi": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, _vp, ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t),
                                           ctypes.c_int, _c_double_p, _vp]),
+    "mgard_region_plan": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_double, _vp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int32)]),
+    "mgard_region_exponents": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_double, _vp, ctypes.c_int,
+                                              _vp, _vp]),
+    "mgard_compress_regions": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                              _vp, ctypes.c_int, ctypes.POINTER(_vp),
+                                              ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
     "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
                                   ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
     "mgard_timing_enable": (None, [ctypes.c_int]),
@@ -406,6 +413,59 @@ def compress_qoi(field: torch.Tensor, g: torch.Tensor, tol_qoi: float, s: float,
                                     float(s), ctypes.byref(p), ctypes.byref(nbytes), 1,
                                     ctypes.byref(tol_used), _stream()))
     return out[:nbytes.value], tol_used.value
+
+
+class Region(ctypes.Structure):
+    """mgard_region: inclusive index box (axes as passed) and its tolerance."""
+    _fields_ = [("lo", ctypes.c_int64 * 4), ("hi", ctypes.c_int64 * 4), ("tol", ctypes.c_double)]
+
+
+def _regions(regions):
+    """[(lo, hi, tol), ...] -> ctypes array of mgard_region."""
+    arr = (Region * max(1, len(regions)))()
+    for r, (lo, hi, tol) in enumerate(regions):
+        for d in range(len(lo)):
+            arr[r].lo[d] = int(lo[d])
+            arr[r].hi[d] = int(hi[d])
+        arr[r].tol = float(tol)
+    return arr
+
+
+def region_plan(shape, tol: float, regions):
+    """(rho, [k_r]) of mgard_region_plan."""
+    nd, sh = _shape(shape)
+    arr = _regions(regions)
+    rho = ctypes.c_int()
+    k = (ctypes.c_int32 * max(1, len(regions)))()
+    _check(lib().mgard_region_plan(nd, sh, float(tol), ctypes.cast(arr, _vp), len(regions),
+                                   ctypes.byref(rho), k))
+    return rho.value, [int(k[i]) for i in range(len(regions))]
+
+
+def region_exponents(shape, tol: float, regions, device="cuda") -> torch.Tensor:
+    """Width exponent of every node (CUDA uint8 tensor of ``shape``)."""
+    nd, sh = _shape(shape)
+    arr = _regions(regions)
+    out = torch.empty(tuple(shape), dtype=torch.uint8, device=device)
+    _check(lib().mgard_region_exponents(nd, sh, float(tol), ctypes.cast(arr, _vp), len(regions),
+                                        _ptr(out), _stream()))
+    return out
+
+
+def compress_regions(field: torch.Tensor, tol: float, regions, out=None):
+    """Region-adaptive compression of a CUDA tensor (mgard_compress_regions):
+    background absolute L-infinity tolerance ``tol``, boxes ``[(lo, hi, tol_r)]``."""
+    nd, sh = _shape(field.shape)
+    arr = _regions(regions)
+    if out is None:
+        out = torch.empty(compress_bound(field.shape, field.dtype) + 1024, dtype=torch.uint8,
+                          device=field.device)
+    nbytes = ctypes.c_size_t(out.numel())
+    p = ctypes.c_void_p(_ptr(out).value)
+    _check(lib().mgard_compress_regions(_ptr(field), nd, sh, _dtype_code(field.dtype), float(tol),
+                                        ctypes.cast(arr, _vp), len(regions), ctypes.byref(p),
+                                        ctypes.byref(nbytes), 1, _stream()))
+    return out[:nbytes.value]
 
 
 BATCH_GRAPH = 1

@@ -19,6 +19,7 @@
 #include "multilevel.cuh"
 #include "pipeline.cuh"
 #include "quantize.cuh"
+#include "region.cuh"
 
 namespace mgb {
 
@@ -97,11 +98,15 @@ mgard_status norm_impl(const Plan& p, const T* data, double s, double* out, cuda
     return MGARD_OK;
 }
 
+// With `rh` the output is the region header (inner_bytes filled in here)
+// followed by the buffer, whose coefficients are scaled by `rs`.
 template <typename T>
 mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mgard_dtype dtype,
                            int ndim, const int64_t* shape, double tol, double s,
                            mgard_tolmode mode, void** out, size_t* out_bytes, int prealloc,
-                           cudaStream_t st) {
+                           cudaStream_t st, const RegionScale* rs = nullptr,
+                           mgard_region_header* rh = nullptr) {
+    const size_t pre = rh ? MGARD_REGION_INNER : 0;
     const int64_t N = p.total();
     const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
     const Sections fx = layout(p.L, nchunks, 0, 0);
@@ -123,30 +128,36 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
     // a 16-byte aligned device buffer of the caller is written in place;
     // anything else goes through a scratch buffer of the worst-case size
     const bool direct = prealloc && is_device_ptr(*out) && ((uintptr_t)*out & 15) == 0 &&
-                        *out_bytes >= fx.outliers;
+                        *out_bytes >= pre + fx.outliers;
     char* dd;
     uint64_t cap;
     if (direct) {
-        dd = (char*)*out;
-        cap = *out_bytes;
+        dd = (char*)*out + pre;
+        cap = *out_bytes - pre;
     } else {
         cap = layout(p.L, nchunks, (uint64_t)N, (uint64_t)N + nchunks).total;
         MGB_TRY(scratch.alloc(cap, st));
         dd = scratch.as<char>();
     }
     const mgard_header h0 = header_template(p, dtype, ndim, shape, tol, s, mode);
-    MGB_TRY(compress_core<T>(p, din, h0, tol, s, mode, dd, cap, w, metab.as<CompressMeta>(), st));
+    MGB_TRY(compress_core<T>(p, din, h0, tol, s, mode, dd, cap, w, metab.as<CompressMeta>(), st, rs));
     CompressMeta m;
     MGB_CUDA(cudaMemcpyAsync(&m, metab.p, sizeof(m), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     MGB_TRY(status_to_error(m.status & ~(unsigned)ST_CAPACITY));
     if (m.status & ST_CAPACITY) {
-        *out_bytes = m.total;
+        *out_bytes = pre + m.total;
         set_error("preallocated output too small");
         return MGARD_ECAPACITY;
     }
-    const size_t total = m.total;
+    const size_t total = pre + m.total;
+    if (rh) rh->inner_bytes = m.total;
     if (direct) {
+        if (rh) {
+            MGB_CUDA(cudaMemcpyAsync(*out, rh, sizeof(*rh), cudaMemcpyHostToDevice, st));
+            MGB_CUDA(cudaMemsetAsync((char*)*out + sizeof(*rh), 0, pre - sizeof(*rh), st));
+            MGB_CUDA(cudaStreamSynchronize(st));
+        }
         *out_bytes = total;
         return MGARD_OK;
     }
@@ -174,7 +185,12 @@ mgard_status compress_impl(const Plan& p, const void* field, bool field_dev, mga
             return MGARD_ENOMEM;
         }
     }
-    MGB_CUDA(cudaMemcpyAsync(dst, dd, total, cudaMemcpyDefault, st));
+    if (rh) {
+        char head[MGARD_REGION_INNER] = {};
+        std::memcpy(head, rh, sizeof(*rh));
+        MGB_CUDA(cudaMemcpyAsync(dst, head, pre, cudaMemcpyDefault, st));
+    }
+    MGB_CUDA(cudaMemcpyAsync(dst + pre, dd, m.total, cudaMemcpyDefault, st));
     MGB_CUDA(cudaStreamSynchronize(st));
     *out = dst;
     *out_bytes = total;
@@ -210,7 +226,7 @@ mgard_status read_header(const void* in, size_t in_bytes, bool in_dev, mgard_hea
 template <typename T>
 mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::vector<double>& w,
                              const char* din, void** field, bool out_dev, void* dst,
-                             cudaStream_t st) {
+                             cudaStream_t st, const RegionScale* rs) {
     const int64_t N = p.total();
     DevBuf stage, stat;
     T* dout = (T*)dst;
@@ -222,7 +238,7 @@ mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::ve
     MGB_TRY(work.alloc(p, st));
     MGB_TRY(stat.alloc(sizeof(unsigned), st));
     MGB_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(unsigned), st));
-    MGB_TRY(decompress_core<T>(p, h, w.data(), din, dout, work, stat.as<unsigned>(), st));
+    MGB_TRY(decompress_core<T>(p, h, w.data(), din, dout, work, stat.as<unsigned>(), st, rs));
     unsigned status = 0;
     MGB_CUDA(cudaMemcpyAsync(&status, stat.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));
@@ -233,6 +249,123 @@ mgard_status decompress_impl(const Plan& p, const mgard_header& h, const std::ve
     }
     *field = dst;
     return MGARD_OK;
+}
+
+// Decompress an ordinary buffer (device or host), optionally with region
+// scaling of its coefficients.
+mgard_status decompress_buffer(const void* in, size_t in_bytes, bool in_dev, void** field,
+                               int prealloc, cudaStream_t st, const RegionScale* rs) {
+    mgard_header h;
+    std::vector<double> w;
+    MGB_TRY(read_header(in, in_bytes, in_dev, &h, &w, st));
+    const Plan* p;
+    MGB_TRY(get_plan((int)h.ndim, h.shape, -1, &p));
+    if (p->L != (int)h.nlevels) {
+        set_error("corrupt header: level count");
+        return MGARD_ECORRUPT;
+    }
+    const size_t nbytes = (size_t)p->total() * ((h.dtype == MGARD_F64) ? 8 : 4);
+    // device image of the compressed buffer
+    DevBuf inbuf;
+    const char* din = (const char*)in;
+    if (!in_dev) {
+        MGB_TRY(inbuf.alloc(h.total_bytes, st));
+        MGB_CUDA(cudaMemcpyAsync(inbuf.p, in, h.total_bytes, cudaMemcpyHostToDevice, st));
+        din = inbuf.as<char>();
+    }
+    void* dst;
+    bool out_dev;
+    if (prealloc) {
+        if (!*field) {
+            set_error("preallocated output missing");
+            return MGARD_EINVAL;
+        }
+        dst = *field;
+        out_dev = is_device_ptr(dst);
+    } else {
+        out_dev = in_dev;
+        if (out_dev) {
+            count_device_alloc();
+            cudaError_t e = cudaMalloc(&dst, nbytes);
+            if (e != cudaSuccess) {
+                set_error(std::string("output allocation: ") + cudaGetErrorString(e));
+                return MGARD_ENOMEM;
+            }
+        } else {
+            dst = std::malloc(nbytes);
+            if (!dst) return MGARD_ENOMEM;
+        }
+    }
+    mgard_status r;
+    if (h.dtype == MGARD_F32) r = decompress_impl<float>(*p, h, w, din, field, out_dev, dst, st, rs);
+    else r = decompress_impl<double>(*p, h, w, din, field, out_dev, dst, st, rs);
+    if (r != MGARD_OK && !prealloc) mgard_free(dst);
+    return r;
+}
+
+
+bool region_magic(const void* in, size_t in_bytes, bool in_dev, cudaStream_t st) {
+    char m[8] = {};
+    if (in_bytes < 8) return false;
+    if (in_dev) {
+        if (cudaMemcpyAsync(m, in, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    } else {
+        std::memcpy(m, in, 8);
+    }
+    return std::memcmp(m, MGARD_REGION_MAGIC, 8) == 0;
+}
+
+// The region header of a buffer, checked, and the boxes as mgard_region.
+mgard_status read_region_header(const void* in, size_t in_bytes, bool in_dev,
+                                mgard_region_header* rh, mgard_region* boxes, cudaStream_t st) {
+    if (in_bytes < MGARD_REGION_INNER) {
+        set_error("region buffer too small");
+        return MGARD_ECORRUPT;
+    }
+    if (in_dev) {
+        MGB_CUDA(cudaMemcpyAsync(rh, in, sizeof(*rh), cudaMemcpyDeviceToHost, st));
+        MGB_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(rh, in, sizeof(*rh));
+    }
+    if (std::memcmp(rh->magic, MGARD_REGION_MAGIC, 8) != 0 || rh->version != MGARD_REGION_VERSION ||
+        rh->nregions > MGARD_REGION_SLOTS || rh->rho < 0 || rh->rho > Plan::RHO_MAX ||
+        rh->inner_bytes > in_bytes - MGARD_REGION_INNER || !(rh->tol > 0.0) ||
+        !std::isfinite(rh->tol)) {
+        set_error("corrupt region header");
+        return MGARD_ECORRUPT;
+    }
+    for (uint32_t r = 0; r < rh->nregions; ++r) {
+        for (int a = 0; a < 4; ++a) {
+            boxes[r].lo[a] = rh->box[r].lo[a];
+            boxes[r].hi[a] = rh->box[r].hi[a];
+        }
+        boxes[r].tol = rh->box[r].tol;
+    }
+    return MGARD_OK;
+}
+
+mgard_status decompress_regions(const void* in, size_t in_bytes, bool in_dev, void** field,
+                                int prealloc, cudaStream_t st) {
+    mgard_region_header rh;
+    mgard_region boxes[MGARD_REGION_SLOTS];
+    MGB_TRY(read_region_header(in, in_bytes, in_dev, &rh, boxes, st));
+    const char* inner = (const char*)in + MGARD_REGION_INNER;
+    mgard_header h;
+    std::vector<double> w;
+    MGB_TRY(read_header(inner, rh.inner_bytes, in_dev, &h, &w, st));
+    const Plan* p;
+    MGB_TRY(get_plan((int)h.ndim, h.shape, -1, &p));
+    RegionScale rs;
+    if (region_table(*p, (int)h.ndim, h.shape, rh.rho, rh.k, boxes, (int)rh.nregions, &rs) != MGARD_OK) {
+        set_error("corrupt region header: boxes");
+        return MGARD_ECORRUPT;
+    }
+    return decompress_buffer(inner, rh.inner_bytes, in_dev, field, prealloc, st, &rs);
 }
 
 }  // namespace
@@ -559,68 +692,74 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field, int
     }
     cudaStream_t st = (cudaStream_t)stream;
     const bool in_dev = is_device_ptr(in);
+    if (!in_dev && in_bytes >= 8 && std::memcmp(in, MGARD_REGION_MAGIC, 8) == 0)
+        return decompress_regions(in, in_bytes, in_dev, field, out_preallocated, st);
     // device buffer into a device field: the one-buffer batch path (see
-    // mgard_compress)
+    // mgard_compress); a region buffer fails its header check there
     if (in_dev && out_preallocated && *field && is_device_ptr(*field)) {
         const void* i = in;
         const size_t cap = ~size_t(0);   // the caller guarantees room for the field
         mgard_status fst = MGARD_OK;
-        return mgard_decompress_batch(1, &i, &in_bytes, field, &cap, &fst, MGARD_BATCH_REPEAT,
-                                      stream);
+        const mgard_status r = mgard_decompress_batch(1, &i, &in_bytes, field, &cap, &fst,
+                                                      MGARD_BATCH_REPEAT, stream);
+        if (r == MGARD_ECORRUPT && region_magic(in, in_bytes, in_dev, st))
+            return decompress_regions(in, in_bytes, in_dev, field, out_preallocated, st);
+        return r;
     }
-    mgard_header h;
-    std::vector<double> w;
-    MGB_TRY(read_header(in, in_bytes, in_dev, &h, &w, st));
+    if (in_dev && region_magic(in, in_bytes, in_dev, st))
+        return decompress_regions(in, in_bytes, in_dev, field, out_preallocated, st);
+    return decompress_buffer(in, in_bytes, in_dev, field, out_preallocated, st, nullptr);
+}
+
+mgard_status mgard_compress_regions(const void* field, int ndim, const int64_t* shape,
+                                    mgard_dtype dtype, double tol, const mgard_region* regions,
+                                    int nregions, void** out, size_t* out_bytes,
+                                    int out_preallocated, void* stream) {
+    MGB_TRY(check_dtype(dtype));
+    if (!field || !out || !out_bytes || (out_preallocated && !*out)) {
+        set_error("null argument");
+        return MGARD_EINVAL;
+    }
     const Plan* p;
-    MGB_TRY(get_plan((int)h.ndim, h.shape, -1, &p));
-    if (p->L != (int)h.nlevels) {
-        set_error("corrupt header: level count");
-        return MGARD_ECORRUPT;
-    }
-    const size_t nbytes = (size_t)p->total() * ((h.dtype == MGARD_F64) ? 8 : 4);
-    // device image of the compressed buffer
-    DevBuf inbuf;
-    const char* din = (const char*)in;
-    if (!in_dev) {
-        MGB_TRY(inbuf.alloc(h.total_bytes, st));
-        MGB_CUDA(cudaMemcpyAsync(inbuf.p, in, h.total_bytes, cudaMemcpyHostToDevice, st));
-        din = inbuf.as<char>();
-    }
-    void* dst;
-    bool out_dev;
-    if (out_preallocated) {
-        if (!*field) {
-            set_error("preallocated output missing");
-            return MGARD_EINVAL;
+    MGB_TRY(get_plan(ndim, shape, -1, &p));
+    mgard_region_header rh;
+    std::memset(&rh, 0, sizeof(rh));
+    MGB_TRY(region_params(*p, ndim, shape, tol, regions, nregions, &rh.rho, rh.k));
+    RegionScale rs;
+    MGB_TRY(region_table(*p, ndim, shape, rh.rho, rh.k, regions, nregions, &rs));
+    std::memcpy(rh.magic, MGARD_REGION_MAGIC, 8);
+    rh.version = MGARD_REGION_VERSION;
+    rh.nregions = (uint32_t)nregions;
+    rh.tol = tol;
+    for (int r = 0; r < nregions; ++r) {
+        for (int d = 0; d < ndim; ++d) {
+            rh.box[r].lo[d] = regions[r].lo[d];
+            rh.box[r].hi[d] = regions[r].hi[d];
         }
-        dst = *field;
-        out_dev = is_device_ptr(dst);
-    } else {
-        out_dev = in_dev;
-        if (out_dev) {
-            count_device_alloc();
-            cudaError_t e = cudaMalloc(&dst, nbytes);
-            if (e != cudaSuccess) {
-                set_error(std::string("output allocation: ") + cudaGetErrorString(e));
-                return MGARD_ENOMEM;
-            }
-        } else {
-            dst = std::malloc(nbytes);
-            if (!dst) return MGARD_ENOMEM;
-        }
+        rh.box[r].tol = regions[r].tol;
     }
-    mgard_status r;
-    if (h.dtype == MGARD_F32) r = decompress_impl<float>(*p, h, w, din, field, out_dev, dst, st);
-    else r = decompress_impl<double>(*p, h, w, din, field, out_dev, dst, st);
-    if (r != MGARD_OK && !out_preallocated) mgard_free(dst);
-    return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(field);
+    if (dtype == MGARD_F32)
+        return compress_impl<float>(*p, field, dev, dtype, ndim, shape, tol, INFINITY, MGARD_ABS, out,
+                                    out_bytes, out_preallocated, st, &rs, &rh);
+    return compress_impl<double>(*p, field, dev, dtype, ndim, shape, tol, INFINITY, MGARD_ABS, out,
+                                 out_bytes, out_preallocated, st, &rs, &rh);
 }
 
 mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shape[4],
                         mgard_dtype* dtype, double* tol_abs, int* nlevels) {
     mgard_header h;
     std::vector<double> w;
-    MGB_TRY(read_header(in, in_bytes, is_device_ptr(in), &h, &w, nullptr));
+    const bool in_dev = is_device_ptr(in);
+    if (in && region_magic(in, in_bytes, in_dev, nullptr)) {   // the wrapped buffer's fields
+        mgard_region_header rh;
+        mgard_region boxes[MGARD_REGION_SLOTS];
+        MGB_TRY(read_region_header(in, in_bytes, in_dev, &rh, boxes, nullptr));
+        in = (const char*)in + MGARD_REGION_INNER;
+        in_bytes = rh.inner_bytes;
+    }
+    MGB_TRY(read_header(in, in_bytes, in_dev, &h, &w, nullptr));
     if (ndim) *ndim = (int)h.ndim;
     if (shape)
         for (int i = 0; i < 4; ++i) shape[i] = h.shape[i];

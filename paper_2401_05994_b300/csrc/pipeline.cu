@@ -288,7 +288,8 @@ mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, Compress
 template <typename T>
 mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
                            double s, mgard_tolmode mode, char* dd, uint64_t cap,
-                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st,
+                           const RegionScale* rs) {
     const uint64_t N = (uint64_t)p.total();
     const Sections fx = layout(p.L, (N + CHUNK - 1) / CHUNK, 0, 0);
     if (cap < fx.outliers || ((uintptr_t)dd & 15) != 0) {
@@ -297,6 +298,16 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
     }
     MGB_CUDA(cudaMemsetAsync(dd, 0, fx.outliers, st));   // fixed sections, gaps included
     MGB_TRY(compress_decompose<T>(p, din, s, mode, w, meta, st));
+    if (rs) {   // region-adaptive widths: coefficients scaled by 2^k of their node
+        if (p.L < 1) {
+            set_error("regions need at least one level");
+            return MGARD_ESHAPE;
+        }
+        std::vector<T*> lv(p.L + 1);
+        for (int l = 0; l < p.L; ++l) lv[l] = w.py.lv[l];
+        lv[p.L] = w.top.template as<T>();
+        MGB_TRY(region_scale<T>(p, *rs, rows3_ok(p) ? w.top.template as<T>() : nullptr, lv.data(), 1, st));
+    }
     MGB_TRY(compress_encode<T>(p, din, h0, tol, s, mode, dd, cap, w, meta, st));
     return compress_pack<T>(p, dd, w, meta, st);
 }
@@ -356,7 +367,7 @@ mgard_status DecompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
 template <typename T>
 mgard_status decompress_core(const Plan& p, const mgard_header& h, const double* w,
                              const char* din, T* dout, DecompressWork<T>& work, unsigned* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, const RegionScale* rs) {
     work.py.status = status;
     const int64_t N = p.total();
     const int L = p.L;
@@ -385,16 +396,19 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
         T* zs = work.zs.template as<T>();
         MGB_TRY(huffman_decode_values<T>(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff,
                                          dq, zs, status, st));
+        if (rs) MGB_TRY(region_scale<T>(p, *rs, zs, nullptr, -1, st));
         return recompose_pyramid<T>(p, nullptr, dout, work.py, st, zs);
     }
     uint16_t* sym = work.sym.template as<uint16_t>();
     int32_t* esc = work.esc.template as<int32_t>();
     MGB_TRY(huffman_decode(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff, sym, esc,
                            status, st));
+    std::vector<T*> lv(L + 1);
     for (int l = 0; l <= L; ++l) {
-        T* lvl = l == L ? dout : work.py.lv[l];
-        MGB_TRY(dequantize_level<T>(p, l, sym, esc, false, w[l], lvl, st));
+        lv[l] = l == L ? dout : work.py.lv[l];
+        MGB_TRY(dequantize_level<T>(p, l, sym, esc, false, w[l], lv[l], st));
     }
+    if (rs) MGB_TRY(region_scale<T>(p, *rs, nullptr, lv.data(), -1, st));
     MGB_TRY(recompose_pyramid<T>(p, dout, dout, work.py, st));
     return MGARD_OK;
 }
@@ -414,17 +428,19 @@ INST_PHASES(double)
 #undef INST_PHASES
 template mgard_status compress_core<float>(const Plan&, const float*, const mgard_header&, double,
                                            double, mgard_tolmode, char*, uint64_t,
-                                           CompressWork<float>&, CompressMeta*, cudaStream_t);
+                                           CompressWork<float>&, CompressMeta*, cudaStream_t,
+                                           const RegionScale*);
 template struct DecompressWork<float>;
 template struct DecompressWork<double>;
 template mgard_status decompress_core<float>(const Plan&, const mgard_header&, const double*,
                                              const char*, float*, DecompressWork<float>&,
-                                             unsigned*, cudaStream_t);
+                                             unsigned*, cudaStream_t, const RegionScale*);
 template mgard_status decompress_core<double>(const Plan&, const mgard_header&, const double*,
                                               const char*, double*, DecompressWork<double>&,
-                                              unsigned*, cudaStream_t);
+                                              unsigned*, cudaStream_t, const RegionScale*);
 template mgard_status compress_core<double>(const Plan&, const double*, const mgard_header&, double,
                                             double, mgard_tolmode, char*, uint64_t,
-                                            CompressWork<double>&, CompressMeta*, cudaStream_t);
+                                            CompressWork<double>&, CompressMeta*, cudaStream_t,
+                                            const RegionScale*);
 
 }  // namespace mgb

@@ -10,6 +10,7 @@
 
 #include "../../include/mgard_format.h"
 #include "multilevel.cuh"
+#include "quantize.cuh"
 
 namespace mgb {
 
@@ -48,10 +49,13 @@ mgard_header header_template(const Plan& p, mgard_dtype dtype, int ndim, const i
 // after the stream has reached this point.  When the data does not fit in
 // `cap` bytes, meta->status has ST_CAPACITY, meta->total the size needed and
 // the payload is not written.
+// With `rs`, region-adaptive widths (quantize.cuh): the coefficients are
+// scaled by 2^k of their node between decomposition and quantization.
 template <typename T>
 mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
                            double s, mgard_tolmode mode, char* dd, uint64_t cap,
-                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
+                           CompressWork<T>& w, CompressMeta* meta, cudaStream_t st,
+                           const RegionScale* rs = nullptr);
 
 // Host validation of a header read from a buffer of in_bytes bytes
 // (magic, version, sizes and section offsets); MGARD_ECORRUPT on failure.
@@ -70,10 +74,11 @@ struct DecompressWork {
 // the host) into `dout` (device).  Launches only; a corrupt stream ORs
 // ST_CORRUPT into *status (device) and leaves `dout` meaningless but every
 // access in bounds.
+// With `rs`, the dequantized coefficients are scaled back by 2^-k.
 template <typename T>
 mgard_status decompress_core(const Plan& p, const mgard_header& h, const double* w,
                              const char* din, T* dout, DecompressWork<T>& work, unsigned* status,
-                             cudaStream_t st);
+                             cudaStream_t st, const RegionScale* rs = nullptr);
 
 // Time every launch shape of the row kernels on each level of the plan's
 // shape and keep the fastest in the plan (tune.cu); `report` receives one

@@ -99,8 +99,10 @@ void unit_solve(const std::vector<double>& xc, int64_t J, int64_t lo, int64_t hi
 // evaluated exactly for axes of up to 2048 coarse nodes; longer axes
 // evaluate the rows near both ends and one interior row (interior rows of a
 // uniform spacing are identical) with a +-300 window.
+// With `tail` (RHO_MAX + 1 entries) also the largest row sum of the entries
+// more than rho level-l nodes from the row's coarse node, for every rho.
 double correction_norm(const std::vector<double>& xc, const std::vector<int64_t>& rf,
-                       const std::vector<double>& rw, int64_t m) {
+                       const std::vector<double>& rw, int64_t m, double* tail = nullptr) {
     int64_t mc = (int64_t)xc.size();
     std::vector<int64_t> rows;
     const int64_t W = 300;
@@ -129,6 +131,18 @@ double correction_norm(const std::vector<double>& xc, const std::vector<int64_t>
         double sum = 0.0;
         for (double v : row) sum += std::fabs(v);
         best = std::max(best, sum);
+        if (tail) {
+            double by[Plan::RHO_MAX + 2] = {};
+            for (int64_t i = flo; i <= fhi; ++i) {
+                const int64_t d = std::min<int64_t>(std::llabs(i - rf[J]), Plan::RHO_MAX + 1);
+                by[d] += std::fabs(row[i - flo]);
+            }
+            double far = 0.0;   // entries farther than rho
+            for (int rho = Plan::RHO_MAX; rho >= 0; --rho) {
+                far += by[rho + 1];
+                tail[rho] = std::max(tail[rho], far);
+            }
+        }
     }
     return best;
 }
@@ -210,6 +224,13 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
         off += p.count[l];
     }
     p.K.assign(L + 1, 1.0);
+    p.Kax.assign(L + 1, {1.0, 1.0, 1.0, 1.0});
+    p.tails.assign(L + 1, std::vector<double>(4 * (Plan::RHO_MAX + 1), 0.0));
+    p.hmax.assign(L + 1, {0, 0, 0, 0});
+    for (int l = 0; l <= L; ++l)
+        for (int a = 0; a < 4; ++a)
+            for (size_t i = 1; i < idx[l][a].size(); ++i)
+                p.hmax[l][a] = std::max(p.hmax[l][a], idx[l][a][i] - idx[l][a][i - 1]);
     p.mu.assign(L + 1, 1.0);
     p.tune.assign(L + 1, std::array<RowCfg, RK_COUNT>());
 
@@ -294,7 +315,8 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             for (int64_t c = 0; c < mc; ++c) xc[c] = x[cp[c]];
             std::vector<double> sub, inv, tcp;
             thomas(xc, sub, inv, tcp);
-            p.K[l] *= correction_norm(xc, rf, rw, m);
+            p.Kax[l][a] = correction_norm(xc, rf, rw, m, p.tails[l].data() + a * (Plan::RHO_MAX + 1));
+            p.K[l] *= p.Kax[l][a];
             std::vector<int> rfi(rf.begin(), rf.end());
             o.fcls = blob.add(fcls);
             o.cbefore = blob.add(cbefore);

@@ -30,6 +30,15 @@ struct Plan {
     std::vector<int64_t> offset;     // [l] symbol offset of level l
     std::vector<int64_t> count;      // [l] symbols of level l (new nodes)
     std::vector<double> K;           // [l] correction norm (l >= 1)
+    // region-adaptive bounds: per level and axis of the 4D view, the row-sum
+    // norm of the 1D correction operator (their product is K[l]; 1 on
+    // inactive axes), its far-field row sums tails[l][a * (RHO_MAX + 1) + rho]
+    // (entries more than rho level-l nodes from the row's coarse node), and
+    // the largest spacing of the level-l nodes in input-grid units
+    static constexpr int RHO_MAX = 48;
+    std::vector<std::array<double, 4>> Kax;
+    std::vector<std::vector<double>> tails;
+    std::vector<std::array<int64_t, 4>> hmax;
     std::vector<double> mu;          // [l] Gershgorin bound of the level mass matrix
     std::vector<Level<float>> lf;    // [l] tables of level l (transition l -> l-1 for l >= 1)
     std::vector<Level<double>> ld;

@@ -539,4 +539,95 @@ INST(float)
 INST(double)
 #undef INST
 
+// -- region-adaptive widths -------------------------------------------------
+
+namespace {
+
+__device__ inline int region_k(const RegionLevel& rg, const int64_t* g) {
+    int k = 0;
+    for (int r = 0; r < rg.n; ++r) {
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) in = in && g[a] >= rg.lo[r][a] && g[a] <= rg.hi[r][a];
+        if (in) k = max(k, rg.k[r]);
+    }
+    return k;
+}
+
+// 2^e as an exact float / double (|e| well inside the normal range).
+__device__ inline float pow2(float, int e) { return __int_as_float((127 + e) << 23); }
+__device__ inline double pow2(double, int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Scale the level-l coefficients (symbol order at q.sym_off + rank, or the
+// compact level array) by 2^(sign k) of their node.
+template <typename T>
+__global__ void k_region_scale(T* __restrict__ c, QLevel q, LevelIndex li, RegionLevel rg,
+                               int sign, int symbol_order) {
+    FOR_NODES(q.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
+        const NodeInfo ni = node_info(q, i);
+        if (ni.skip) continue;
+        int64_t g[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) g[a] = li.pos[a][i[a]];
+        const int k = region_k(rg, g);
+        if (!k) continue;
+        T* v = c + (symbol_order ? q.sym_off + ni.rank : ni.addr);
+        *v *= pow2(T(0), sign * k);
+    }
+}
+
+// k of every node of level l, written at its input-grid position.
+__global__ void k_region_exponents(uint8_t* __restrict__ out, QLevel q, LevelIndex li,
+                                   RegionLevel rg) {
+    FOR_NODES(q.n, i0, i1, i2, i3) {
+        const int64_t i[4] = {i0, i1, i2, i3};
+        const NodeInfo ni = node_info(q, i);
+        if (ni.skip) continue;
+        int64_t g[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) g[a] = li.pos[a][i[a]];
+        out[ravel4(g, q.fine)] = (uint8_t)region_k(rg, g);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+mgard_status region_scale(const Plan& p, const RegionScale& rs, T* zs, T* const* levels, int sign,
+                          cudaStream_t st) {
+    if ((int)rs.lv.size() != p.L + 1) {
+        set_error("region table does not match the levels");
+        return MGARD_EINVAL;
+    }
+    for (int l = 0; l <= p.L; ++l) {
+        if (!rs.lv[l].n) continue;
+        const QLevel q = make_qlevel(p, l, false);
+        T* c = zs ? zs : levels[l];
+        MGB_LAUNCH("k_region_scale", st, k_region_scale<T><<<grid3(q.n, 128), 128, 0, st>>>(
+                                             c, q, p.lidx[l], rs.lv[l], sign, zs ? 1 : 0));
+        MGB_CUDA(cudaGetLastError());
+    }
+    return MGARD_OK;
+}
+template mgard_status region_scale<float>(const Plan&, const RegionScale&, float*, float* const*,
+                                          int, cudaStream_t);
+template mgard_status region_scale<double>(const Plan&, const RegionScale&, double*, double* const*,
+                                           int, cudaStream_t);
+
+mgard_status region_exponents(const Plan& p, const RegionScale& rs, uint8_t* k, cudaStream_t st) {
+    if ((int)rs.lv.size() != p.L + 1) {
+        set_error("region table does not match the levels");
+        return MGARD_EINVAL;
+    }
+    for (int l = 0; l <= p.L; ++l) {
+        QLevel q = make_qlevel(p, l, false);
+        for (int a = 0; a < 4; ++a) q.fine[a] = p.n4[a];
+        MGB_LAUNCH("k_region_exponents", st, k_region_exponents<<<grid3(q.n, 128), 128, 0, st>>>(
+                                                 k, q, p.lidx[l], rs.lv[l]));
+        MGB_CUDA(cudaGetLastError());
+    }
+    return MGARD_OK;
+}
+
 }  // namespace mgb

@@ -1,6 +1,8 @@
 // Level-wise quantization (declarations).
 #pragma once
 
+#include <vector>
+
 #include "plan.cuh"
 
 namespace mgb {
@@ -40,5 +42,28 @@ int64_t feature_blocks(const Plan& p, int l);
 template <typename T>
 mgard_status level_features(const Plan& p, int l, const T* c, const double* amax, FeatPart* part,
                             cudaStream_t st);
+
+// Region-adaptive widths: on level l a node at input-grid position g (4D
+// view) takes the width w_l 2^-k with k the largest k[r] of the boxes
+// lo[r] <= g <= hi[r] (boxes already dilated for that level), 0 if none.
+// The compressor scales such a coefficient by 2^k before quantizing with
+// w_l (the same integer, exactly) and the decompressor by 2^-k after
+// dequantizing.
+constexpr int REGION_MAX = 8;
+struct RegionLevel {
+    int n;
+    int k[REGION_MAX];
+    int64_t lo[REGION_MAX][4], hi[REGION_MAX][4];
+};
+struct RegionScale {
+    std::vector<RegionLevel> lv;   // [l], l = 0..L
+};
+// Multiply every level's coefficients by 2^(sign k): zs (symbol order, all
+// levels) when non-null, else the compact level arrays levels[l] (l = 0..L).
+template <typename T>
+mgard_status region_scale(const Plan& p, const RegionScale& rs, T* zs, T* const* levels, int sign,
+                          cudaStream_t st);
+// The exponent k of every node of the input grid (row-major, N bytes).
+mgard_status region_exponents(const Plan& p, const RegionScale& rs, uint8_t* k, cudaStream_t st);
 
 }  // namespace mgb
