@@ -518,6 +518,33 @@ mgard_status mgard_compress_regions(const void* field, int ndim, const int64_t* 
                                     int nregions, void** out, size_t* out_bytes,
                                     int out_preallocated, void* stream);
 
+/* ---- Out-of-core compression ("Software architecture": the out-of-core
+ * module that chunks arrays to fit device memory) ------------------------
+ * A host field (pinned memory gives full overlap of the PCIe copies with
+ * the kernels; pageable memory works too) is cut along its first axis into
+ * nblocks blocks of as equal sizes as possible (1 <= nblocks <= shape[0]);
+ * every block is compressed independently with the L-infinity bound (ABS,
+ * or REL against max|u| of the whole field from a first streaming pass), so
+ * the whole field keeps it.  Two internal streams alternate over the blocks:
+ * one block's kernels run while the next block's host-to-device copy and
+ * the previous block's device-to-host copy proceed.  Device memory: about
+ * two blocks' input, output and workspace, independent of the field size.
+ * Format: include/mgard_format.h (mgard_ooc_header, block offsets, then one
+ * ordinary buffer per block).  mgard_decompress (host buffer, host field)
+ * and mgard_info read it; decompression is pipelined the same way. */
+
+/* Bytes an out-of-core buffer of this shape can need at most. */
+size_t mgard_compress_ooc_bound(int ndim, const int64_t* shape, mgard_dtype dtype,
+                                int64_t nblocks);
+/* field and *out are host memory.  out_preallocated = 0: *out receives a
+ * malloc'd buffer (release with mgard_free); = 1: *out_bytes is the
+ * capacity (MGARD_ECAPACITY with the size needed when short).  MGARD_EINVAL
+ * for device pointers or bad block counts.  Synchronizes the stream. */
+mgard_status mgard_compress_ooc(const void* field, int ndim, const int64_t* shape,
+                                mgard_dtype dtype, double tol, mgard_tolmode mode,
+                                int64_t nblocks, void** out, size_t* out_bytes,
+                                int out_preallocated, void* stream);
+
 /* ---- Tracing -------------------------------------------------------------
  * When enabled, every kernel launch of the library is bracketed by a pair
  * of CUDA events recorded on its launch stream (adds about a microsecond

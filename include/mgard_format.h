@@ -90,4 +90,35 @@ typedef struct {
 
 #define MGARD_REGION_INNER ((sizeof(mgard_region_header) + 15) & ~(size_t)15)
 
+/*
+ * Out-of-core buffers (mgard_compress_ooc) hold independent blocks of the
+ * field along its first axis:
+ *
+ *   mgard_ooc_header                  (fixed size, below)
+ *   offsets   [nblocks + 1] uint64    byte offset of every block's buffer
+ *                                     (16-byte aligned; the last entry is
+ *                                     total_bytes)
+ *   blocks                            one mgard_compress buffer per block
+ *                                     (L-infinity, absolute tolerance tol_abs)
+ *
+ * Block b covers first-axis indices [b q + min(b, r), (b + 1) q + min(b + 1, r))
+ * with q = shape[0] / nblocks and r = shape[0] % nblocks.
+ */
+#define MGARD_OOC_MAGIC "MGARDOC"
+#define MGARD_OOC_VERSION 1u
+
+typedef struct {
+    char magic[8];        /* "MGARDOC\0" */
+    uint32_t version;     /* MGARD_OOC_VERSION */
+    uint32_t dtype;
+    uint32_t ndim;
+    uint32_t nblocks;
+    int64_t shape[4];
+    double tol;           /* requested tolerance */
+    double tol_abs;       /* absolute L-infinity tolerance of every block */
+    uint32_t mode;        /* mgard_tolmode of tol */
+    uint32_t reserved;
+    uint64_t total_bytes;
+} mgard_ooc_header;
+
 #endif /* MGARD_FORMAT_H */

@@ -33,6 +33,7 @@ qoi         linear quantities of interest: representer, dual norm and the
             tolerance that bounds a QoI's error
 region      region-adaptive L-infinity bounds: far-field tails of the
             correction operators, dilated boxes and per-node widths
+ooc         out-of-core blocking along the first axis
 predictor   features, MLP and Adam of the learned tolerance predictor
 
 Parity status: every function here is pinned by the CPU tests in

@@ -113,6 +113,10 @@ SIGNATURES = {
     "mgard_compress_regions": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
                                               _vp, ctypes.c_int, ctypes.POINTER(_vp),
                                               ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
+    "mgard_compress_ooc_bound": (ctypes.c_size_t, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int64]),
+    "mgard_compress_ooc": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int64, ctypes.POINTER(_vp),
+                                          ctypes.POINTER(ctypes.c_size_t), ctypes.c_int, _vp]),
     "mgard_info": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), _c_int64_p,
                                   ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
     "mgard_timing_enable": (None, [ctypes.c_int]),
@@ -466,6 +470,47 @@ def compress_regions(field: torch.Tensor, tol: float, regions, out=None):
                                         ctypes.cast(arr, _vp), len(regions), ctypes.byref(p),
                                         ctypes.byref(nbytes), 1, _stream()))
     return out[:nbytes.value]
+
+
+def compress_ooc_bound(shape, dtype, nblocks: int) -> int:
+    nd, sh = _shape(shape)
+    return int(lib().mgard_compress_ooc_bound(nd, sh, _dtype_code(dtype), int(nblocks)))
+
+
+def compress_ooc(field, tol: float, nblocks: int, mode: int = ABS, out=None):
+    """Out-of-core compression of a host array (numpy or CPU tensor, pinned
+    for overlapped copies) in ``nblocks`` blocks along the first axis
+    (mgard_compress_ooc).  ``out``: a host uint8 buffer (numpy or CPU tensor)
+    of at least ``compress_ooc_bound`` bytes; returns the used prefix."""
+    if isinstance(field, torch.Tensor):
+        if field.is_cuda:
+            raise TypeError("out-of-core compression takes a host field")
+        dtype = field.dtype
+    else:
+        dtype = field.dtype
+    nd, sh = _shape(field.shape)
+    if out is None:
+        out = np.empty(compress_ooc_bound(field.shape, dtype, nblocks), np.uint8)
+    nbytes = ctypes.c_size_t(out.nbytes if isinstance(out, np.ndarray) else out.numel())
+    p = ctypes.c_void_p(_ptr(out).value)
+    _check(lib().mgard_compress_ooc(_ptr(field), nd, sh, _dtype_code(dtype), float(tol), int(mode),
+                                    int(nblocks), ctypes.byref(p), ctypes.byref(nbytes), 1, _stream()))
+    return out[:nbytes.value]
+
+
+OOC_HEADER_FMT = "<8s4I4qddIIQ"
+
+
+def ooc_blocks(buf) -> list:
+    """(offset, end) of every block's buffer inside an out-of-core buffer."""
+    raw = bytes(buf[:4096].tolist() if isinstance(buf, torch.Tensor) else buf[:4096])
+    head = struct.unpack_from(OOC_HEADER_FMT, raw)
+    nb = head[4]
+    size = struct.calcsize(OOC_HEADER_FMT)
+    allb = bytes(buf[:size + 8 * (nb + 1)].tolist() if isinstance(buf, torch.Tensor)
+                 else buf[:size + 8 * (nb + 1)])
+    offs = struct.unpack_from(f"<{nb + 1}Q", allb, size)
+    return [(offs[b], offs[b + 1]) for b in range(nb)]
 
 
 BATCH_GRAPH = 1

@@ -45,29 +45,6 @@ mgard_status check_dtype(mgard_dtype d) {
     return MGARD_OK;
 }
 
-mgard_status status_to_error(unsigned st) {
-    if (st & ST_TIMEOUT) {
-        set_error("a bounded device wait (tensor-copy barrier) gave up");
-        return MGARD_ETIMEOUT;
-    }
-    if (st & ST_NONFINITE) {
-        set_error("input holds NaN or Inf");
-        return MGARD_ENONFINITE;
-    }
-    if (st & ST_RANGE) {
-        set_error("tolerance too small: a quantized value exceeds the 32-bit range");
-        return MGARD_ERANGE;
-    }
-    if (st & ST_CORRUPT) {
-        set_error("compressed stream is corrupt");
-        return MGARD_ECORRUPT;
-    }
-    if (st & ST_NOCODE) {
-        set_error("a symbol has no Huffman code");
-        return MGARD_EINVAL;
-    }
-    return MGARD_OK;
-}
 
 double s_norm_from_levels(const std::vector<double>& E, double s) {
     double total = E[0];
@@ -369,6 +346,30 @@ mgard_status decompress_regions(const void* in, size_t in_bytes, bool in_dev, vo
 }
 
 }  // namespace
+
+mgard_status status_to_error(unsigned st) {
+    if (st & ST_TIMEOUT) {
+        set_error("a bounded device wait (tensor-copy barrier) gave up");
+        return MGARD_ETIMEOUT;
+    }
+    if (st & ST_NONFINITE) {
+        set_error("input holds NaN or Inf");
+        return MGARD_ENONFINITE;
+    }
+    if (st & ST_RANGE) {
+        set_error("tolerance too small: a quantized value exceeds the 32-bit range");
+        return MGARD_ERANGE;
+    }
+    if (st & ST_CORRUPT) {
+        set_error("compressed stream is corrupt");
+        return MGARD_ECORRUPT;
+    }
+    if (st & ST_NOCODE) {
+        set_error("a symbol has no Huffman code");
+        return MGARD_EINVAL;
+    }
+    return MGARD_OK;
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -694,6 +695,8 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field, int
     const bool in_dev = is_device_ptr(in);
     if (!in_dev && in_bytes >= 8 && std::memcmp(in, MGARD_REGION_MAGIC, 8) == 0)
         return decompress_regions(in, in_bytes, in_dev, field, out_preallocated, st);
+    if (!in_dev && is_ooc_buffer(in, in_bytes))
+        return decompress_ooc(in, in_bytes, field, out_preallocated, st);
     // device buffer into a device field: the one-buffer batch path (see
     // mgard_compress); a region buffer fails its header check there
     if (in_dev && out_preallocated && *field && is_device_ptr(*field)) {
@@ -752,6 +755,19 @@ mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shap
     mgard_header h;
     std::vector<double> w;
     const bool in_dev = is_device_ptr(in);
+    if (!in_dev && is_ooc_buffer(in, in_bytes)) {   // the field's shape, the blocks' tolerance
+        mgard_ooc_header oh;
+        MGB_TRY(ooc_info(in, in_bytes, &oh));
+        const uint64_t first = *(const uint64_t*)((const char*)in + sizeof(oh));
+        MGB_TRY(read_header((const char*)in + first, in_bytes - first, false, &h, &w, nullptr));
+        if (ndim) *ndim = (int)oh.ndim;
+        if (shape)
+            for (int i = 0; i < 4; ++i) shape[i] = oh.shape[i];
+        if (dtype) *dtype = (mgard_dtype)oh.dtype;
+        if (tol_abs) *tol_abs = oh.tol_abs;
+        if (nlevels) *nlevels = (int)h.nlevels;
+        return MGARD_OK;
+    }
     if (in && region_magic(in, in_bytes, in_dev, nullptr)) {   // the wrapped buffer's fields
         mgard_region_header rh;
         mgard_region boxes[MGARD_REGION_SLOTS];

@@ -57,6 +57,9 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
                            CompressWork<T>& w, CompressMeta* meta, cudaStream_t st,
                            const RegionScale* rs = nullptr);
 
+// Map device status bits (ST_*) to an mgard_status with its message.
+mgard_status status_to_error(unsigned st);
+
 // Host validation of a header read from a buffer of in_bytes bytes
 // (magic, version, sizes and section offsets); MGARD_ECORRUPT on failure.
 mgard_status check_header(const mgard_header& h, size_t in_bytes);
@@ -103,6 +106,13 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
 template <typename T>
 mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, CompressMeta* meta,
                            cudaStream_t st);
+
+// Out-of-core buffers (ooc.cu), read by mgard_decompress and mgard_info on
+// host memory.
+bool is_ooc_buffer(const void* in, size_t in_bytes);
+mgard_status ooc_info(const void* in, size_t in_bytes, mgard_ooc_header* h);
+mgard_status decompress_ooc(const void* in, size_t in_bytes, void** field, int prealloc,
+                            cudaStream_t st);
 
 // Drop the cached batches of mgard_compress_batch / mgard_decompress_batch
 // (graphs and workspaces).
