@@ -312,6 +312,10 @@ def run_batch(args, rank, world, dev, barrier):
     def compress_eager():
         return binding.compress_batch(fields, tol, s_norm, binding.REL, outs=outs, graph=False)[0]
 
+    def compress_persistent():   # all codebooks in one persistent launch between two phases
+        return binding.compress_batch(fields, tol, s_norm, binding.REL, outs=outs, graph=True,
+                                      persistent=True)[0]
+
     def compress_each():
         return [binding.compress(f, tol, s_norm, binding.REL, out=o) for f, o in zip(fields, outs)]
 
@@ -350,6 +354,7 @@ def run_batch(args, rank, world, dev, barrier):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     ms_graph = timed(compress_graph, args.steps)
+    ms_persistent = timed(compress_persistent, args.steps)
     ms_eager = timed(compress_eager, args.steps)
     ms_each = timed(compress_each, max(3, args.steps // 2))
     views = step()
@@ -372,10 +377,10 @@ def run_batch(args, rank, world, dev, barrier):
             "config": {"workload": "64 f32 GRF fields, extents U{33..300}, k^-a a~U[2,11/3], "
                                    f"{nbytes / 1e9:.3f} GB, s=0 rel 1e-3",
                        "l2": "batch larger than L2, no flush", "parallelism": f"replicas x{world}"},
-            "compress_ms": {"graph": ms_graph, "streams_no_graph": ms_eager,
-                            "separate_calls": ms_each},
-            "compress_gbs": {"graph": gbs(ms_graph), "streams_no_graph": gbs(ms_eager),
-                             "separate_calls": gbs(ms_each)},
+            "compress_ms": {"graph": ms_graph, "graph_persistent_codebooks": ms_persistent,
+                            "streams_no_graph": ms_eager, "separate_calls": ms_each},
+            "compress_gbs": {"graph": gbs(ms_graph), "graph_persistent_codebooks": gbs(ms_persistent),
+                             "streams_no_graph": gbs(ms_eager), "separate_calls": gbs(ms_each)},
             "decompress_ms": {"graph": ms_dec_graph, "separate_calls": ms_dec_each},
             "clocks": clocks,
             "verify": {"worst_error_over_tol": worst, "ok": worst <= 1.0,

@@ -515,6 +515,7 @@ def ooc_blocks(buf) -> list:
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
+BATCH_PERSISTENT = 8
 
 
 def autotune(shape, dtype=torch.float32) -> str:
@@ -527,7 +528,8 @@ def autotune(shape, dtype=torch.float32) -> str:
 
 
 def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, outs=None,
-                   graph: bool = False, check: bool = True, autotune: bool = False):
+                   graph: bool = False, check: bool = True, autotune: bool = False,
+                   persistent: bool = False):
     """Compress a list of CUDA tensors in one call (mgard_compress_batch).
 
     ``outs``: list of CUDA uint8 tensors (default: ``compress_bound`` bytes
@@ -555,7 +557,8 @@ def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, out
     stats = (ctypes.c_int * n)()
     st = lib().mgard_compress_batch(n, fptr, nds, shp, dt, float(tol), float(s), int(mode), optr,
                                     caps, sizes, stats,
-                                    (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0),
+                                    (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+                                    | (BATCH_PERSISTENT if persistent else 0),
                                     _stream())
     if check:
         _check(st)

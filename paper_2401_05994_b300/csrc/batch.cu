@@ -97,9 +97,14 @@ struct Lanes {
     // Run through a graph captured on the first call.
     template <typename F>
     mgard_status run_graph(cudaStream_t st, int n, F&& body) {
+        return run_graph_seq(st, [&](cudaStream_t s) { return run(s, n, body); });
+    }
+    // The same for any sequence of launches on one stream (whole(stream)).
+    template <typename F>
+    mgard_status run_graph_seq(cudaStream_t st, F&& whole) {
         if (!exec) {
             MGB_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
-            const mgard_status e = run(origin, n, body);
+            const mgard_status e = whole(origin);
             cudaGraph_t g = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(origin, &g);
             if (e != MGARD_OK) {
@@ -124,6 +129,8 @@ struct BatchState {
     std::vector<std::unique_ptr<CompressWork<double>>> wd;
     CompressMeta* metas = nullptr;      // device, one per field
     CompressMeta* hmetas = nullptr;     // pinned host copy
+    CodebookJob* jobs = nullptr;        // device, one per field (persistent codebook phase)
+    unsigned* job_counter = nullptr;    // device
     Lanes lanes;
 
     ~BatchState() {
@@ -132,6 +139,8 @@ struct BatchState {
         wf.clear();
         wd.clear();
         if (metas) cudaFreeAsync(metas, lanes.side[0]);
+        if (jobs) cudaFreeAsync(jobs, lanes.side[0]);
+        if (job_counter) cudaFreeAsync(job_counter, lanes.side[0]);
         if (lanes.side[0]) cudaStreamSynchronize(lanes.side[0]);
         lanes.destroy();
         if (hmetas) cudaFreeHost(hmetas);
@@ -160,6 +169,17 @@ struct BatchState {
                 MGB_TRY(wd.back()->alloc(*p, s0));
             }
         }
+        if (k.flags & MGARD_BATCH_PERSISTENT) {
+            std::vector<CodebookJob> hj;
+            for (int i = 0; i < k.n; ++i)
+                hj.push_back(k.dtype == MGARD_F32 ? codebook_job<float>(*plans[i], *wf[i])
+                                                  : codebook_job<double>(*plans[i], *wd[i]));
+            count_device_alloc();
+            MGB_CUDA(cudaMallocAsync((void**)&jobs, sizeof(CodebookJob) * k.n, s0));
+            count_device_alloc();
+            MGB_CUDA(cudaMallocAsync((void**)&job_counter, sizeof(unsigned), s0));
+            MGB_CUDA(cudaMemcpyAsync(jobs, hj.data(), sizeof(CodebookJob) * k.n, cudaMemcpyHostToDevice, s0));
+        }
         MGB_TRY(huffman_prepare());
         MGB_CUDA(cudaStreamSynchronize(s0));
         if (k.flags & MGARD_BATCH_AUTOTUNE) {   // each distinct shape once, before any capture
@@ -181,6 +201,40 @@ struct BatchState {
                                         key.s, (mgard_tolmode)key.mode, dd, cap, *wf[i], metas + i, ss);
         return compress_core<double>(*plans[i], (const double*)key.fields[i], heads[i], key.tol,
                                      key.s, (mgard_tolmode)key.mode, dd, cap, *wd[i], metas + i, ss);
+    }
+
+    // The persistent form: every field's decomposition, widths and
+    // quantization (front), one launch for all codebooks and tables, then
+    // every field's count pass, header and payload (back).
+    template <typename T>
+    mgard_status front_t(int i, cudaStream_t ss, CompressWork<T>& w) {
+        const Plan& p = *plans[i];
+        const uint64_t N = (uint64_t)p.total();
+        const Sections fx = layout(p.L, (N + CHUNK - 1) / CHUNK, 0, 0);
+        MGB_CUDA(cudaMemsetAsync(key.outs[i], 0, fx.outliers, ss));
+        MGB_TRY(compress_decompose<T>(p, (const T*)key.fields[i], key.s, (mgard_tolmode)key.mode, w,
+                                      metas + i, ss));
+        return compress_encode_front<T>(p, (const T*)key.fields[i], key.tol, key.s,
+                                        (mgard_tolmode)key.mode, w, metas + i, ss);
+    }
+    template <typename T>
+    mgard_status back_t(int i, cudaStream_t ss, CompressWork<T>& w) {
+        const Plan& p = *plans[i];
+        char* dd = (char*)key.outs[i];
+        MGB_TRY(compress_encode_back<T>(p, heads[i], dd, key.caps[i], w, metas + i, ss));
+        return compress_pack<T>(p, dd, w, metas + i, ss);
+    }
+    mgard_status front(int i, cudaStream_t ss) {
+        return key.dtype == MGARD_F32 ? front_t<float>(i, ss, *wf[i]) : front_t<double>(i, ss, *wd[i]);
+    }
+    mgard_status back(int i, cudaStream_t ss) {
+        return key.dtype == MGARD_F32 ? back_t<float>(i, ss, *wf[i]) : back_t<double>(i, ss, *wd[i]);
+    }
+    mgard_status phased(cudaStream_t st) {
+        const int n = key.n;
+        MGB_TRY(lanes.run(st, n, [this](int i, cudaStream_t ss) { return front(i, ss); }));
+        MGB_TRY(huffman_codebook_tables_batch(jobs, n, job_counter, st));
+        return lanes.run(st, n, [this](int i, cudaStream_t ss) { return back(i, ss); });
     }
 };
 
@@ -224,7 +278,8 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
     }
     if (!(tol > 0.0) || !std::isfinite(tol) || std::isnan(s) || s < 0.0 ||
         (mode != MGARD_ABS && mode != MGARD_REL) ||
-        (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_AUTOTUNE | MGARD_BATCH_REPEAT))) {
+        (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_AUTOTUNE | MGARD_BATCH_REPEAT |
+                   MGARD_BATCH_PERSISTENT))) {
         set_error("tol must be positive and finite, s >= 0 or INFINITY, mode ABS or REL");
         return MGARD_EINVAL;
     }
@@ -287,9 +342,16 @@ extern "C" mgard_status mgard_compress_batch(int n, const void* const* fields, c
         while (g_batches.size() > BATCH_CACHE) g_batches.pop_back();
         b = g_batches.front().get();
     }
-    auto body = [b](int i, cudaStream_t ss) { return b->field(i, ss); };
-    if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph(st, n, body));
-    else MGB_TRY(b->lanes.run(st, n, body));
+    if (flags & MGARD_BATCH_PERSISTENT) {
+        if (use_graph(flags, b->lanes))
+            MGB_TRY(b->lanes.run_graph_seq(st, [b](cudaStream_t s0) { return b->phased(s0); }));
+        else
+            MGB_TRY(b->phased(st));
+    } else {
+        auto body = [b](int i, cudaStream_t ss) { return b->field(i, ss); };
+        if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph(st, n, body));
+        else MGB_TRY(b->lanes.run(st, n, body));
+    }
     ++b->lanes.runs;
     MGB_CUDA(cudaMemcpyAsync(b->hmetas, b->metas, sizeof(CompressMeta) * n, cudaMemcpyDeviceToHost, st));
     MGB_CUDA(cudaStreamSynchronize(st));

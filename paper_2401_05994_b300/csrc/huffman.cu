@@ -204,10 +204,10 @@ __device__ void round_merge(CodebookSmem& S, int n) {
     }
 }
 
-__global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long long* __restrict__ hist,
-                                                         uint8_t* __restrict__ lengths, int wide) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CodebookSmem& S = *reinterpret_cast<CodebookSmem*>(smem_raw);
+// Code lengths of one histogram by one block of CB_THREADS threads (S in
+// shared memory).  Every return is taken by the whole block.
+__device__ void codebook_body(const unsigned long long* __restrict__ hist,
+                              uint8_t* __restrict__ lengths, int wide, CodebookSmem& S) {
     const int tid = threadIdx.x;
     for (int s = tid; s < DICT; s += blockDim.x) lengths[s] = 0;
     for (int shift = 0; shift < 64; ++shift) {
@@ -277,14 +277,19 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
     }
 }
 
+__global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long long* __restrict__ hist,
+                                                         uint8_t* __restrict__ lengths, int wide) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    codebook_body(hist, lengths, wide, *reinterpret_cast<CodebookSmem*>(smem_raw));
+}
+
 // Canonical codes and decoding tables from the code lengths, one block.
 // A symbol's place in (length, symbol) order is fi[len] plus the number of
 // lower symbols of the same length: counts per 32-symbol chunk (one warp
 // match each), an exclusive scan over the chunks per length (one warp per
 // length), and the rank inside the chunk give it without a sort.
-__global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict__ lengths,
-                                                       uint32_t* __restrict__ codes,
-                                                       DecodeTables* __restrict__ dt) {
+__device__ void tables_body(const uint8_t* __restrict__ lengths, uint32_t* __restrict__ codes,
+                            DecodeTables* __restrict__ dt) {
     constexpr int NCH = DICT / 32;                 // chunks of 32 symbols
     constexpr int PER = DICT / CB_THREADS;         // symbols per thread
     static_assert(NCH == 4 * 32 && PER * CB_THREADS == DICT && LMAX <= CB_THREADS / 32,
@@ -396,6 +401,36 @@ __global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict
                 ent = (uint16_t)((l << 12) | (unsigned)ssym[idx]);
         }
         dt->lut[k] = ent;
+    }
+}
+
+__global__ void __launch_bounds__(CB_THREADS) k_tables(const uint8_t* __restrict__ lengths,
+                                                       uint32_t* __restrict__ codes,
+                                                       DecodeTables* __restrict__ dt) {
+    tables_body(lengths, codes, dt);
+}
+
+// Codebooks and tables of many histograms: a persistent grid whose blocks
+// take jobs from a device counter (one atomicAdd per job, no waits between
+// blocks) until the list is exhausted.  Each job is one field's codebook
+// followed by its canonical codes and decoding tables, exactly as the
+// single-field kernels compute them.
+__global__ void __launch_bounds__(CB_THREADS) k_codebook_tables_batch(const CodebookJob* __restrict__ jobs,
+                                                                      int n, unsigned* next) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CodebookSmem& S = *reinterpret_cast<CodebookSmem*>(smem_raw);
+    __shared__ int job;
+    for (;;) {
+        if (threadIdx.x == 0) job = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int j = job;
+        __syncthreads();   // every thread holds j before the next job is taken
+        if (j >= n) return;
+        const CodebookJob J = jobs[j];
+        codebook_body(J.hist, J.lengths, J.wide, S);
+        __syncthreads();   // the lengths are in global memory, visible to the block
+        tables_body(J.lengths, J.codes, J.dt);
+        __syncthreads();
     }
 }
 
@@ -949,6 +984,9 @@ mgard_status huffman_prepare() {
     if (!done[dev]) {
         MGB_CUDA(cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(CodebookSmem)));
+        MGB_CUDA(cudaFuncSetAttribute(k_codebook_tables_batch,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(CodebookSmem)));
         // The decoder's threads read their payload words one at a time and
         // rely on L1 keeping each thread's line between reads.  Left to
         // itself the driver configures shared memory for a third block that
@@ -985,6 +1023,21 @@ mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, 
 mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
                             cudaStream_t st) {
     MGB_LAUNCH("k_tables", st, k_tables<<<1, CB_THREADS, 0, st>>>(lengths, codes, dt));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+mgard_status huffman_codebook_tables_batch(const CodebookJob* jobs, int n, unsigned* counter,
+                                           cudaStream_t st) {
+    if (n <= 0) return MGARD_OK;
+    MGB_TRY(huffman_prepare());
+    int dev = 0, sms = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    MGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MGB_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    MGB_LAUNCH("k_codebook_tables_batch", st,
+               k_codebook_tables_batch<<<std::min(n, sms), CB_THREADS, sizeof(CodebookSmem), st>>>(
+                   jobs, n, counter));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }

@@ -35,6 +35,19 @@ mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, 
 // Canonical codes and decode tables from code lengths (single CTA).
 mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
                             cudaStream_t st);
+// Codebooks and tables of n fields in one launch: a persistent grid (up to
+// one block per SM) whose blocks take jobs from *counter (device; reset
+// here, stream-ordered).  Results equal huffman_codebook + huffman_tables
+// of every job.
+struct CodebookJob {
+    const unsigned long long* hist;
+    uint8_t* lengths;
+    uint32_t* codes;
+    DecodeTables* dt;
+    int wide;
+};
+mgard_status huffman_codebook_tables_batch(const CodebookJob* jobs, int n, unsigned* counter,
+                                           cudaStream_t st);
 // Pass 1 of encoding: per-chunk word and escape counts and their exclusive
 // prefixes; totals (device, 2 x uint64) receive total words / escapes.
 // `scratch` (device, count_scratch_bytes(n)) may be null: then it is

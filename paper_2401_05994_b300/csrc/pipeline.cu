@@ -206,12 +206,10 @@ mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tol
 }
 
 template <typename T>
-mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0, double tol,
-                             double s, mgard_tolmode mode, char* dd, uint64_t cap,
-                             CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
-    const int64_t N = p.total();
+mgard_status compress_encode_front(const Plan& p, const T* din, double tol, double s,
+                                   mgard_tolmode mode, CompressWork<T>& w, CompressMeta* meta,
+                                   cudaStream_t st) {
     const int L = p.L;
-    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
     MGB_LAUNCH("k_meta_reset", st, k_meta_reset<<<1, 32, 0, st>>>(meta));
     MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
     unsigned* status = &meta->status;
@@ -245,19 +243,45 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
                                       w.hist.template as<unsigned long long>(), status, st));
         }
     }
-    MGB_TRY(huffman_codebook(w.hist.template as<unsigned long long>(), w.lengths.template as<uint8_t>(),
-                             nullptr, st, (uint64_t)N >= (uint64_t(1) << 32)));
-    MGB_TRY(huffman_tables(w.lengths.template as<uint8_t>(), w.codes.template as<uint32_t>(),
-                           w.dt.template as<DecodeTables>(), st));
+    return MGARD_OK;
+}
+
+template <typename T>
+CodebookJob codebook_job(const Plan& p, CompressWork<T>& w) {
+    CodebookJob j;
+    j.hist = w.hist.template as<unsigned long long>();
+    j.lengths = w.lengths.template as<uint8_t>();
+    j.codes = w.codes.template as<uint32_t>();
+    j.dt = w.dt.template as<DecodeTables>();
+    j.wide = (uint64_t)p.total() >= (uint64_t(1) << 32) ? 1 : 0;
+    return j;
+}
+
+template <typename T>
+mgard_status compress_encode_back(const Plan& p, const mgard_header& h0, char* dd, uint64_t cap,
+                                  CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+    const int64_t N = p.total();
+    const uint64_t nchunks = ((uint64_t)N + CHUNK - 1) / CHUNK;
     uint64_t* word_off = w.offs.template as<uint64_t>();
     uint64_t* esc_off = word_off + nchunks;
-    MGB_TRY(huffman_count(sym, N, w.lengths.template as<uint8_t>(), word_off, esc_off,
-                          w.totals.template as<unsigned long long>(), status, st,
+    MGB_TRY(huffman_count(w.sym.template as<uint16_t>(), N, w.lengths.template as<uint8_t>(), word_off,
+                          esc_off, w.totals.template as<unsigned long long>(), &meta->status, st,
                           w.scan.template as<unsigned long long>()));
     MGB_LAUNCH("k_finalize", st, k_finalize<<<1, 32, 0, st>>>(
         h0, w.totals.template as<unsigned long long>(), meta, reinterpret_cast<unsigned char*>(dd), cap));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
+}
+
+template <typename T>
+mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0, double tol,
+                             double s, mgard_tolmode mode, char* dd, uint64_t cap,
+                             CompressWork<T>& w, CompressMeta* meta, cudaStream_t st) {
+    MGB_TRY(compress_encode_front<T>(p, din, tol, s, mode, w, meta, st));
+    const CodebookJob j = codebook_job<T>(p, w);
+    MGB_TRY(huffman_codebook(j.hist, j.lengths, nullptr, st, j.wide != 0));
+    MGB_TRY(huffman_tables(j.lengths, j.codes, j.dt, st));
+    return compress_encode_back<T>(p, h0, dd, cap, w, meta, st);
 }
 
 template <typename T>
@@ -422,7 +446,14 @@ template struct CompressWork<double>;
                                              double, mgard_tolmode, char*, uint64_t,              \
                                              CompressWork<T>&, CompressMeta*, cudaStream_t);      \
     template mgard_status compress_pack<T>(const Plan&, char*, CompressWork<T>&, CompressMeta*,   \
-                                           cudaStream_t);
+                                           cudaStream_t);                                         \
+    template mgard_status compress_encode_front<T>(const Plan&, const T*, double, double,         \
+                                                   mgard_tolmode, CompressWork<T>&, CompressMeta*, \
+                                                   cudaStream_t);                                 \
+    template CodebookJob codebook_job<T>(const Plan&, CompressWork<T>&);                          \
+    template mgard_status compress_encode_back<T>(const Plan&, const mgard_header&, char*,        \
+                                                  uint64_t, CompressWork<T>&, CompressMeta*,      \
+                                                  cudaStream_t);
 INST_PHASES(float)
 INST_PHASES(double)
 #undef INST_PHASES

@@ -10,6 +10,7 @@
 
 #include "../../include/mgard_format.h"
 #include "multilevel.cuh"
+#include "huffman.cuh"
 #include "quantize.cuh"
 
 namespace mgb {
@@ -106,6 +107,19 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
 template <typename T>
 mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, CompressMeta* meta,
                            cudaStream_t st);
+// compress_encode in three parts, for batches that build the codebooks of
+// all fields in one launch (huffman_codebook_tables_batch on the jobs of
+// codebook_job): front = widths and quantization, back = count pass and
+// header.  front, the codebook and tables, then back equal compress_encode.
+template <typename T>
+mgard_status compress_encode_front(const Plan& p, const T* din, double tol, double s,
+                                   mgard_tolmode mode, CompressWork<T>& w, CompressMeta* meta,
+                                   cudaStream_t st);
+template <typename T>
+CodebookJob codebook_job(const Plan& p, CompressWork<T>& w);
+template <typename T>
+mgard_status compress_encode_back(const Plan& p, const mgard_header& h0, char* dd, uint64_t cap,
+                                  CompressWork<T>& w, CompressMeta* meta, cudaStream_t st);
 
 // Out-of-core buffers (ooc.cu), read by mgard_decompress and mgard_info on
 // host memory.

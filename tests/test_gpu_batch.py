@@ -38,7 +38,8 @@ def _single(f, tol, s, mode):
 
 @pytest.mark.parametrize("s", [math.inf, 0.0, 1.0])
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_bytes_equal_single(s, graph):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_bytes_equal_single(s, graph, persistent):
     fields = _fields()
     ref = [_single(f, 1e-3, s, binding.REL) for f in fields]
     outs = [torch.empty(binding.compress_bound(f.shape), dtype=torch.uint8, device=DEV) for f in fields]
@@ -46,21 +47,24 @@ def test_batch_bytes_equal_single(s, graph):
         for o in outs:
             o.fill_(0xAB)
         views, sizes, stats = binding.compress_batch(fields, 1e-3, s, binding.REL, outs=outs,
-                                                     graph=graph)
+                                                     graph=graph, persistent=persistent)
         assert stats == [0] * len(fields)
         for v, z, r in zip(views, sizes, ref):
             assert z == len(r)
             assert np.array_equal(v.cpu().numpy(), r)
 
 
-def test_batch_graph_replay_sees_new_data():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_graph_replay_sees_new_data(persistent):
     fields = _fields(shapes=[(33, 33, 33), (17, 65, 9)])
     outs = [torch.empty(binding.compress_bound(f.shape), dtype=torch.uint8, device=DEV) for f in fields]
-    binding.compress_batch(fields, 1e-3, math.inf, binding.REL, outs=outs, graph=True)
+    binding.compress_batch(fields, 1e-3, math.inf, binding.REL, outs=outs, graph=True,
+                           persistent=persistent)
     # same buffers, new contents: the replayed graph must read them
     for k, f in enumerate(fields):
         f.copy_(synth.gaussian_random_field(tuple(f.shape), seed=900 + k).to(DEV))
-    views, sizes, _ = binding.compress_batch(fields, 1e-3, math.inf, binding.REL, outs=outs, graph=True)
+    views, sizes, _ = binding.compress_batch(fields, 1e-3, math.inf, binding.REL, outs=outs, graph=True,
+                                             persistent=persistent)
     for f, v in zip(fields, views):
         assert np.array_equal(v.cpu().numpy(), _single(f, 1e-3, math.inf, binding.REL))
 
@@ -75,14 +79,15 @@ def test_batch_error_bound(s):
         assert err <= binding.info(v)["tol_abs"]
 
 
-def test_batch_capacity_and_nonfinite_per_field():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_capacity_and_nonfinite_per_field(persistent):
     fields = _fields(shapes=[(33, 33, 33), (20, 20, 20), (40, 9, 9)])
     fields[2][1, 2, 3] = float("nan")
     outs = [torch.empty(binding.compress_bound(f.shape), dtype=torch.uint8, device=DEV) for f in fields]
     need = len(_single(fields[1], 1e-3, math.inf, binding.REL))
     outs[1] = torch.empty(need - 64, dtype=torch.uint8, device=DEV)
     _, sizes, stats = binding.compress_batch(fields, 1e-3, math.inf, binding.REL, outs=outs,
-                                             check=False)
+                                             check=False, persistent=persistent)
     assert stats[0] == 0
     assert stats[1] == 10   # MGARD_ECAPACITY
     assert sizes[1] == need
