@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(RT) k3_restrict_rows(const Tin* __restrict__ i
 }
 
 // -- mass norm u^T M_l u (level energies of the s-norm) ----------------------------
-// Per row (z, y): M u = sum over the 3 x 3 neighbouring rows of
-// Mz[z][z'] My[y][y'] (Mx row'), each term a 3-tap product along x.  The
-// stencil runs in T; each lane sums its products over a row in T and adds
-// that to a double accumulator, and blocks reduce in a fixed order, so the
-// partial sums do not depend on timing.
+// Per row (z, y): M u = Mx applied to the sum over the 3 x 3 neighbouring
+// rows of Mz[z][z'] My[y][y'] row'.  The stencil runs in T; each lane sums
+// its products over a row in T and adds that to a double accumulator, and
+// blocks reduce in a fixed order, so the partial sums do not depend on
+// timing.
 template <typename T>
 __device__ inline void mass_taps(const AxisT<T>& ax, int i, int m, T f[3], int p[3]) {
     if (!ax.mdiag) {   // inactive axis: identity
@@ -583,15 +583,35 @@ __global__ void __launch_bounds__(RT) k3_mass_norm(const T* __restrict__ u, Leve
                 w[3 * a + b] = fz[a] * fy[b];
             }
         const T* urow = u + r * nx;
-        T racc = T(0);
-        for (int x = lane; x < nx; x += 32) {
-            const T wl = x > 0 ? mox[x - 1] : T(0), wc = mdx[x], wr = x + 1 < nx ? mox[x] : T(0);
-            const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
-            T mu = T(0);
+        // s(x) = sum_k w_k row_k(x) (the y and z taps), then (M u)(x) =
+        // wl s(x-1) + wc s(x) + wr s(x+1): each source element is loaded
+        // once, the x neighbours come from the adjacent lanes, and the next
+        // 32 columns' sums are loaded before the current ones are used
+        auto colsum = [&](int x) {
+            T a = T(0);
+            if (x < nx) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                mu += w[k] * (wl * rows[k][xl] + wc * rows[k][x] + wr * rows[k][xr]);
-            racc += urow[x] * mu;
+                for (int k = 0; k < 9; ++k) a += w[k] * rows[k][x];
+            }
+            return a;
+        };
+        T racc = T(0);
+        T s_cur = colsum(lane);
+        T s_left = T(0);   // s(x0 - 1): the previous block's last column
+        for (int x0 = 0; x0 < nx; x0 += 32) {
+            const int x = x0 + lane;
+            const T s_next = colsum(x + 32);
+            T sl = __shfl_up_sync(0xffffffffu, s_cur, 1);
+            T sr = __shfl_down_sync(0xffffffffu, s_cur, 1);
+            const T nfirst = __shfl_sync(0xffffffffu, s_next, 0);
+            if (lane == 0) sl = s_left;
+            if (lane == 31) sr = nfirst;
+            if (x < nx) {
+                const T wl = x > 0 ? mox[x - 1] : T(0), wc = mdx[x], wr = x + 1 < nx ? mox[x] : T(0);
+                racc += urow[x] * (wl * sl + wc * s_cur + wr * sr);
+            }
+            s_left = __shfl_sync(0xffffffffu, s_cur, 31);
+            s_cur = s_next;
         }
         acc += (double)racc;
     }
