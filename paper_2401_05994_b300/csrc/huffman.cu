@@ -766,6 +766,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
 // -- decoding ------------------------------------------------------------------
 constexpr int DEC_THREADS = 640;
 constexpr int DEC_BLOCKS_PER_SM = 2;   // 33 KB of tables per block; registers capped to fit 2
+
 // Two blocks of 640 threads (40 warps per SM, as five blocks of 256 would
 // give) hold two copies of the decode tables instead of five, so more of
 // the SM's shared L1 stays cache for the threads' payload words.
@@ -805,10 +806,10 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
         const uint4* src = reinterpret_cast<const uint4*>(gdt->lut);
         uint4* dst = reinterpret_cast<uint4*>(lut);
         for (int k = threadIdx.x; k < (int)(sizeof(lut) / 16); k += blockDim.x) dst[k] = src[k];
-        if (threadIdx.x < LMAX + 2) {
-            lim[threadIdx.x] = gdt->lim[threadIdx.x];
-            fcode[threadIdx.x] = gdt->first_code[threadIdx.x];
-            findex[threadIdx.x] = gdt->first_index[threadIdx.x];
+        for (int k = threadIdx.x; k < LMAX + 2; k += blockDim.x) {   // blocks may be one warp
+            lim[k] = gdt->lim[k];
+            fcode[k] = gdt->first_code[k];
+            findex[k] = gdt->first_index[k];
         }
     }
     __syncthreads();
