@@ -559,6 +559,14 @@ __device__ inline void mass_taps(const AxisT<T>& ax, int i, int m, T f[3], int p
     p[2] = i + 1 < m ? i + 1 : i;
 }
 
+// Work items: (z, a strip of MN_Y rows of y, a block of MN_X columns).
+// A warp slides down its strip keeping t_y(x) = sum_a Mz[z][z_a] u[z_a][y][x]
+// for rows y-1, y, y+1 in registers (three loads per row), combines them
+// with the y taps, and takes the x taps from the adjacent lanes; lanes 0
+// and 31 carry the columns either side of the block.
+constexpr int MN_Y = 16;
+constexpr int MN_X = 30;
+
 template <typename T>
 __global__ void __launch_bounds__(RT) k3_mass_norm(const T* __restrict__ u, Level<T> lv,
                                                    double* __restrict__ partial) {
@@ -566,53 +574,50 @@ __global__ void __launch_bounds__(RT) k3_mass_norm(const T* __restrict__ u, Leve
     const T* __restrict__ mdx = lv.ax[3].mdt;
     const T* __restrict__ mox = lv.ax[3].mot;
     const int lane = threadIdx.x & 31;
+    const int nys = (ny + MN_Y - 1) / MN_Y, nxb = (nx + MN_X - 1) / MN_X;
+    const int64_t items = (int64_t)nz * nys * nxb;
     double acc = 0.0;
-    WARP_ROWS((int64_t)nz * ny, r) {
-        const int z = (int)((uint32_t)r / (uint32_t)ny), y = (int)(r - (int64_t)z * ny);
-        T fz[3], fy[3];
-        int pz[3], py[3];
+    for (int64_t it = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); it < items;
+         it += (int64_t)gridDim.x * WPB) {
+        const int xb = (int)(it % nxb);
+        const int64_t rest = it / nxb;
+        const int ys = (int)(rest % nys), z = (int)(rest / nys);
+        const int x = xb * MN_X + lane - 1;
+        const int xc = min(max(x, 0), nx - 1);   // halo columns outside the axis get weight 0
+        T fz[3];
+        int pz[3];
         mass_taps(lv.ax[1], z, nz, fz, pz);
-        mass_taps(lv.ax[2], y, ny, fy, py);
-        const T* rows[9];
-        T w[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                rows[3 * a + b] = u + ((int64_t)pz[a] * ny + py[b]) * nx;
-                w[3 * a + b] = fz[a] * fy[b];
-            }
-        const T* urow = u + r * nx;
-        // s(x) = sum_k w_k row_k(x) (the y and z taps), then (M u)(x) =
-        // wl s(x-1) + wc s(x) + wr s(x+1): each source element is loaded
-        // once, the x neighbours come from the adjacent lanes, and the next
-        // 32 columns' sums are loaded before the current ones are used
-        auto colsum = [&](int x) {
-            T a = T(0);
-            if (x < nx) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) a += w[k] * rows[k][x];
-            }
-            return a;
+        const T* z0 = u + (int64_t)pz[0] * ny * nx + xc;
+        const T* z1 = u + (int64_t)pz[1] * ny * nx + xc;
+        const T* z2 = u + (int64_t)pz[2] * ny * nx + xc;
+        auto trow = [&](int y, T& centre) {
+            const int64_t o = (int64_t)y * nx;
+            const T a0 = z0[o], a1 = z1[o], a2 = z2[o];
+            centre = a1;   // pz[1] = z: the row's own values
+            return fz[0] * a0 + fz[1] * a1 + fz[2] * a2;
         };
+        const int y0 = ys * MN_Y, y1 = min(ny, y0 + MN_Y);
+        T cprev, ccur, cnext;
+        T tprev = trow(y0 > 0 ? y0 - 1 : y0, cprev);
+        T tcur = trow(y0, ccur);
         T racc = T(0);
-        T s_cur = colsum(lane);
-        T s_left = T(0);   // s(x0 - 1): the previous block's last column
-        for (int x0 = 0; x0 < nx; x0 += 32) {
-            const int x = x0 + lane;
-            const T s_next = colsum(x + 32);
-            T sl = __shfl_up_sync(0xffffffffu, s_cur, 1);
-            T sr = __shfl_down_sync(0xffffffffu, s_cur, 1);
-            const T nfirst = __shfl_sync(0xffffffffu, s_next, 0);
-            if (lane == 0) sl = s_left;
-            if (lane == 31) sr = nfirst;
-            if (x < nx) {
+        for (int y = y0; y < y1; ++y) {
+            const T tnext = trow(y + 1 < ny ? y + 1 : y, cnext);
+            T fy[3];
+            int py[3];
+            mass_taps(lv.ax[2], y, ny, fy, py);
+            const T sv = fy[0] * tprev + fy[1] * tcur + fy[2] * tnext;   // zero weights at the ends
+            const T sl = __shfl_up_sync(0xffffffffu, sv, 1);
+            const T sr = __shfl_down_sync(0xffffffffu, sv, 1);
+            if (lane >= 1 && lane <= MN_X && x < nx) {
                 const T wl = x > 0 ? mox[x - 1] : T(0), wc = mdx[x], wr = x + 1 < nx ? mox[x] : T(0);
-                racc += urow[x] * (wl * sl + wc * s_cur + wr * sr);
+                racc += ccur * (wl * sl + wc * sv + wr * sr);
             }
-            s_left = __shfl_sync(0xffffffffu, s_cur, 31);
-            s_cur = s_next;
+            tprev = tcur;
+            tcur = tnext;
+            ccur = cnext;
         }
+        (void)cprev;
         acc += (double)racc;
     }
     __shared__ double sh[RT];
