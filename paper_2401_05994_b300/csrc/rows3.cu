@@ -564,7 +564,7 @@ __device__ inline void mass_taps(const AxisT<T>& ax, int i, int m, T f[3], int p
 // for rows y-1, y, y+1 in registers (three loads per row), combines them
 // with the y taps, and takes the x taps from the adjacent lanes; lanes 0
 // and 31 carry the columns either side of the block.
-constexpr int MN_Y = 16;
+constexpr int MN_Y = 32;
 constexpr int MN_X = 30;
 
 template <typename T>
