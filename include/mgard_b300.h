@@ -104,8 +104,14 @@ mgard_status mgard_recompose(void* data, int ndim, const int64_t* shape, mgard_d
 /* ---- Low-level API: error estimators ("Software design", second paragraph)
  * Bin widths w_0..w_L (host array of L+1 doubles) for an absolute
  * tolerance.  s = INFINITY selects the L-infinity bound
- *   w = 2 tau / (1 + sum_{l=1..L} (1 + K_l)),
- *   K_l = prod_d ||(M^d_{l-1})^{-1} (P^d)^T M^d_l||_inf,
+ *   w = 2 tau / (1 + sum_{l=1..L} c_l),
+ * c_l an upper bound of the largest row sum of level l's error operator
+ * I_new - P C_l (C_l = M_{l-1}^{-1} P^T M_l, P interpolation, I_new the
+ * identity on the new nodes): with, per axis, the row sums T of
+ * B_d = P_d C_d, their parts Tc over coarse columns and the diagonals b, a
+ * row sums to prod T - prod Tc + [row new](|1 - prod b| - prod |b|), and
+ * c_l takes per-axis extremes over each class of rows (which axes are
+ * coarse); finer levels only interpolate, so |e| <= (w/2)(1 + sum c_l);
  * finite s >= 0 the s-norm bound
  *   w_l = 2 tau / sqrt((L+1) 4^{s l} mu_l n_l),
  *   mu_l = prod_d max_i (h_{i-1}+h_i)/2, n_l = nodes new on level l;

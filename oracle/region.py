@@ -26,15 +26,17 @@ see the small widths of the region, and a far-field tail weighted by the
 background width:
 
 * ``S_{l,d}``: the row-sum norm of the axis operator (their product is
-  ``K_l``, the constant of the uniform L-infinity width);
+  ``K_l``);
 * ``t_{l,d}(rho)``: the largest row sum of the entries more than ``rho``
   level-l nodes from the row's coarse node;
 * ``T_l(rho) = sum_d t_{l,d}(rho) prod_{e != d} S_{l,e}`` bounds the tail of
   the tensor operator (the difference of two products, telescoped).
 
 Rule
-    ``den = 1 + sum_l (1 + K_l)`` and ``w_bg`` the uniform L-infinity width
-    of ``tau`` (with the compressor's margin).
+    ``den = 1 + sum_l c_l``, the constant of the uniform L-infinity width
+    (``c_l`` bounds the row sums of level l's whole error operator, so also
+    the part of a row inside the dilation), and ``w_bg = 2 tau / den`` that
+    width (with the compressor's margin).
     ``rho``: the smallest radius in ``0 .. RHO_MAX`` with
     ``tau sum_l T_l(rho) / den <= min_r tau_r / 8``.
     ``k_r``: the smallest ``k >= 0`` with
@@ -118,7 +120,7 @@ def plan(shape, tol: float, regions):
     h = hierarchy(shape)
     if h.L < 1:
         raise ValueError("regions need at least one level")
-    den = 1.0 + sum(1.0 + bounds.K(h, l) for l in range(1, h.L + 1))
+    den = bounds.linf_denominator(h)
     T = [tail_bounds(h, l) for l in range(1, h.L + 1)]
     tmin = min([r[2] for r in regions] + [tol])
     rho = None

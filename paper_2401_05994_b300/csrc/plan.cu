@@ -9,6 +9,7 @@
 // R = P^T M, and the Thomas factorization of the coarse mass matrix.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -147,6 +148,103 @@ double correction_norm(const std::vector<double>& xc, const std::vector<int64_t>
     return best;
 }
 
+// Row classes of B = P C on one axis of a level transition (C the axis
+// correction operator M_c^{-1} P^T M, rows of the level-l grid): for the
+// rows at coarse nodes (k = 0) and at new nodes (k = 1) the largest row sum
+// T = sum_i |B(q, i)|, the smallest sum Tc over the coarse columns, and the
+// range of the diagonal b = B(q, q) and of |b|.  Rows of C come from unit
+// solves as in correction_norm (whole axis up to 2048 coarse nodes, a +-300
+// window beyond); a new row combines its two coarse neighbours' rows with
+// the interpolation weights.
+void axis_row_classes(const std::vector<double>& xc, const std::vector<int64_t>& rf,
+                      const std::vector<double>& rw, int64_t m, const std::vector<int>& fcls,
+                      const std::vector<double>& wl, const std::vector<double>& wr,
+                      Plan::RowClass cls[2]) {
+    const int64_t mc = (int64_t)xc.size();
+    const int64_t W = 300;
+    const bool full = mc <= 2048;
+    for (int k = 0; k < 2; ++k) {
+        cls[k].tmax = 0.0;
+        cls[k].tcmin = std::numeric_limits<double>::infinity();
+        cls[k].bmin = std::numeric_limits<double>::infinity();
+        cls[k].bmax = -std::numeric_limits<double>::infinity();
+        cls[k].absbmin = std::numeric_limits<double>::infinity();
+    }
+    // row J of C over the fine index range [lo, hi]
+    struct Row {
+        int64_t lo = 0, hi = -1;
+        std::vector<double> v;
+        double at(int64_t i) const { return i >= lo && i <= hi ? v[i - lo] : 0.0; }
+    };
+    auto make_row = [&](int64_t J, Row& r) {
+        const int64_t lo = full ? 0 : std::max<int64_t>(0, J - W);
+        const int64_t hi = full ? mc - 1 : std::min<int64_t>(mc - 1, J + W);
+        std::vector<double> g;
+        unit_solve(xc, J, lo, hi, g);
+        r.lo = std::max<int64_t>(0, rf[lo] - 2);
+        r.hi = std::min<int64_t>(m - 1, rf[hi] + 2);
+        r.v.assign(r.hi - r.lo + 1, 0.0);
+        for (int64_t K = lo; K <= hi; ++K)
+            for (int t = 0; t < 5; ++t) {
+                const int64_t i = rf[K] - 2 + t;
+                if (i < r.lo || i > r.hi) continue;
+                r.v[i - r.lo] += g[K - lo] * rw[K * 5 + t];
+            }
+    };
+    auto account = [&](int k, int64_t q, double a, double b_, const Row& r0, const Row* r1) {
+        // B(q, :) = a r0 + b_ r1
+        const int64_t lo = r1 ? std::min(r0.lo, r1->lo) : r0.lo;
+        const int64_t hi = r1 ? std::max(r0.hi, r1->hi) : r0.hi;
+        double T = 0.0, Tc = 0.0;
+        for (int64_t i = lo; i <= hi; ++i) {
+            const double v = std::fabs(a * r0.at(i) + (r1 ? b_ * r1->at(i) : 0.0));
+            T += v;
+            if (fcls[i] >= 0) Tc += v;
+        }
+        const double d = a * r0.at(q) + (r1 ? b_ * r1->at(q) : 0.0);
+        Plan::RowClass& c = cls[k];
+        c.tmax = std::max(c.tmax, T);
+        c.tcmin = std::min(c.tcmin, Tc);
+        c.bmin = std::min(c.bmin, d);
+        c.bmax = std::max(c.bmax, d);
+        c.absbmin = std::min(c.absbmin, std::fabs(d));
+    };
+    Row prev, cur;
+    for (int64_t J = 0; J < mc; ++J) {
+        make_row(J, cur);
+        account(0, rf[J], 1.0, 0.0, cur, nullptr);
+        if (J > 0)   // the new nodes between coarse J-1 and J
+            for (int64_t q = rf[J - 1] + 1; q < rf[J]; ++q) account(1, q, wl[q], wr[q], prev, &cur);
+        std::swap(prev, cur);
+    }
+}
+
+// c_l of the L-infinity width: an upper bound of the largest row sum
+// max_q sum_{i new} |A(q, i)| of A = I_new - P C on the level-l grid.  For a
+// row q with per-axis values T, Tc, b the sum is
+// prod T - prod Tc + [q new] (|1 - prod b| - prod |b|); over each of the
+// 2^D classes of rows (which axes are coarse) the axis extremes bound it.
+double linf_level_constant(const Plan& p, int l) {
+    const int D = p.D;
+    double best = 0.0;
+    for (int mask = 0; mask < (1 << D); ++mask) {   // bit set: new on that axis
+        double tmax = 1.0, tcmin = 1.0, lo = 1.0, hi = 1.0, absb = 1.0;
+        for (int k = 0; k < D; ++k) {
+            const Plan::RowClass& c = p.rows[l][4 - D + k][(mask >> k) & 1];
+            tmax *= c.tmax;
+            tcmin *= c.tcmin;
+            const double cand[4] = {lo * c.bmin, lo * c.bmax, hi * c.bmin, hi * c.bmax};
+            lo = std::min(std::min(cand[0], cand[1]), std::min(cand[2], cand[3]));
+            hi = std::max(std::max(cand[0], cand[1]), std::max(cand[2], cand[3]));
+            absb *= c.absbmin;
+        }
+        double v = tmax - tcmin;
+        if (mask) v += std::max(std::fabs(1.0 - lo), std::fabs(1.0 - hi)) - absb;
+        best = std::max(best, v);
+    }
+    return best;
+}
+
 template <typename T>
 std::vector<T> cast(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
@@ -227,6 +325,8 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
     p.Kax.assign(L + 1, {1.0, 1.0, 1.0, 1.0});
     p.tails.assign(L + 1, std::vector<double>(4 * (Plan::RHO_MAX + 1), 0.0));
     p.hmax.assign(L + 1, {0, 0, 0, 0});
+    p.rows.assign(L + 1, {});
+    p.linf_c.assign(L + 1, 0.0);
     for (int l = 0; l <= L; ++l)
         for (int a = 0; a < 4; ++a)
             for (size_t i = 1; i < idx[l][a].size(); ++i)
@@ -317,6 +417,7 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             thomas(xc, sub, inv, tcp);
             p.Kax[l][a] = correction_norm(xc, rf, rw, m, p.tails[l].data() + a * (Plan::RHO_MAX + 1));
             p.K[l] *= p.Kax[l][a];
+            axis_row_classes(xc, rf, rw, m, fcls, wl, wr, p.rows[l][a].data());
             std::vector<int> rfi(rf.begin(), rf.end());
             o.fcls = blob.add(fcls);
             o.cbefore = blob.add(cbefore);
@@ -352,6 +453,7 @@ static mgard_status build_plan(const int64_t n4[4], int D, int L, Plan& p, bool 
             o.cpd = blob.add(tcp);
         }
     }
+    for (int l = 1; l <= L; ++l) p.linf_c[l] = linf_level_constant(p, l);
     if (!device) return MGARD_OK;
     count_device_alloc();
     cudaError_t e = cudaMalloc(&p.dbuf, blob.bytes.size());
@@ -451,9 +553,8 @@ void release_plans() {
 void width_denominators(const Plan& p, double s, double* den) {
     const int L = p.L;
     if (std::isinf(s)) {
-        double acc = 0.0;
-        for (int l = 1; l <= L; ++l) acc += 1.0 + p.K[l];
-        const double denom = 1.0 + acc;
+        double denom = 1.0;   // 1 + sum_l c_l, in level order
+        for (int l = 1; l <= L; ++l) denom += p.linf_c[l];
         for (int l = 0; l <= L; ++l) den[l] = denom;
     } else {
         for (int l = 0; l <= L; ++l) {

@@ -36,6 +36,15 @@ struct Plan {
     // (entries more than rho level-l nodes from the row's coarse node), and
     // the largest spacing of the level-l nodes in input-grid units
     static constexpr int RHO_MAX = 48;
+    // the L-infinity width: per level and axis, the row classes of B = P C
+    // (rows[l][a][0] at coarse nodes, [1] at new nodes), and c_l, the bound
+    // of the largest row sum of I_new - P C_l they give (l >= 1); the width
+    // is 2 tau / (1 + sum_l c_l)
+    struct RowClass {
+        double tmax, tcmin, bmin, bmax, absbmin;
+    };
+    std::vector<std::array<std::array<RowClass, 2>, 4>> rows;
+    std::vector<double> linf_c;
     std::vector<std::array<double, 4>> Kax;
     std::vector<std::vector<double>> tails;
     std::vector<std::array<int64_t, 4>> hmax;

@@ -15,7 +15,9 @@
 // largest node spacing of a level), with
 //   rho: the smallest radius with tau sum_l T_l(rho) / den <= min tau_r / 8,
 //   k_r: the smallest k with 2^-k tau <= tau_r - tau sum_l T_l(rho) / den,
-// den = 1 + sum_l (1 + K_l) as for the uniform L-infinity width.
+// den = 1 + sum_l c_l as for the uniform L-infinity width (c_l bounds the
+// row sums of a level's whole error operator, so it also bounds the part
+// of a row inside the dilation).
 #include <algorithm>
 #include <cmath>
 
@@ -67,8 +69,8 @@ mgard_status region_params(const Plan& p, int ndim, const int64_t* shape, double
         }
         tmin = std::min(tmin, rg[r].tol);
     }
-    double den = 1.0;
-    for (int l = 1; l <= p.L; ++l) den += 1.0 + p.K[l];
+    double den = 1.0;   // the uniform L-infinity constant 1 + sum_l c_l
+    for (int l = 1; l <= p.L; ++l) den += p.linf_c[l];
     constexpr int R1 = Plan::RHO_MAX + 1;
     auto tail_sum = [&](int c) {
         double total = 0.0;

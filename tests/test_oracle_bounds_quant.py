@@ -37,6 +37,41 @@ def test_K_below_classical_bound(shape):
         assert 0 < bounds.K(h, l) <= 3.0 ** h.D
 
 
+def _level_error_maps(shape):
+    """Per level l >= 1, the largest row sum of |R| over the columns of the
+    level-l coefficients, R the exact map from coefficient errors to the
+    reconstruction (every column a recomposition of a unit vector)."""
+    h = grid.hierarchy(shape)
+    lev = grid.node_level(h).reshape(-1)
+    n = int(np.prod(shape))
+    R = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        R[:, j] = multilevel.recompose(e.reshape(shape)).reshape(-1)
+    A = np.abs(R)
+    return h, [float(np.max(A[:, lev == l].sum(axis=1))) for l in range(1, h.L + 1)]
+
+
+@pytest.mark.parametrize("shape,exact", [((65,), False), ((40,), False), ((33, 33), True),
+                                         ((33, 20), False), ((9, 9, 9), True),
+                                         ((9, 10, 11), True), ((5, 6, 7, 5), False)])
+def test_linf_level_constant_against_brute_force(shape, exact):
+    """c_l bounds every level's worst row of the exact error map; on these
+    2D and 3D grids the class extremes meet at one row and c_l is that
+    worst row itself."""
+    h, brute = _level_error_maps(shape)
+    for l, b in zip(range(1, h.L + 1), brute):
+        c = bounds.linf_level_constant(h, l)
+        assert b <= c * (1 + 1e-12), (l, b, c)
+        if exact:
+            assert abs(c - b) <= 1e-12 * c, (l, b, c)
+        else:
+            assert c <= 1.25 * b
+        # never looser than the per-level bound 1 + K_l
+        assert c <= 1.0 + bounds.K(h, l)
+
+
 def _levels_and_masks(shape):
     h = grid.hierarchy(shape)
     lev = grid.node_level(h)
