@@ -135,11 +135,11 @@ def test_features_of_a_single_spike():
 def test_ratio_ceiling_of_the_advected_series():
     """What a rigorous bound allows on the advected k^-5/3 series that the
     ratio-targeted workload uses (a step of it at 64 x 96 x 96, seed 1): even
-    at a relative L-infinity tolerance of 1 (errors up to max|u|) only about
-    a third of the coefficients quantize to zero, and the compressed size,
+    at a relative L-infinity tolerance of 1 (errors up to max|u|) fewer than
+    half of the coefficients quantize to zero, and the compressed size,
     counted with the format's rules (payload words per chunk, chunks of the
     zero symbol free, 28 bytes of offsets per chunk, 4 bytes per escape, the
-    code-length table), stays near 12x.  Under the L2 norm (s = 0) a 30%
+    code-length table), stays near 14x.  Under the L2 norm (s = 0) a 30%
     relative error gives about the same.  Ratios of 50 or 100 would need a
     tolerance above the field's own magnitude; the ratio targets of the
     predictor's benchmark are therefore taken below this ceiling."""
