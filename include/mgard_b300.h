@@ -391,8 +391,8 @@ mgard_status mgard_info(const void* in, size_t in_bytes, int* ndim, int64_t shap
  * reconstructs every coefficient within 2^(exponent - P) (0 when q's first P
  * bits are 0, else the middle of the truncation interval).  The L-infinity
  * error of the recomposed field is then at most sum_l weight_l
- * 2^(exponent_l - P_l) in exact arithmetic (weight_0 = 1, weight_l = 1 + K_l
- * as in the compressor's bound; all-zero levels count 0); the float
+ * 2^(exponent_l - P_l) in exact arithmetic (weight_0 = 1, weight_l = c_l of
+ * the compressor's L-infinity bound; all-zero levels count 0); the float
  * arithmetic of decomposition and recomposition adds its own rounding.
  * Grids of up to three active axes (MGARD_ESHAPE otherwise). */
 #define MGARD_MDR_MAX_LEVELS 64

@@ -25,7 +25,8 @@ Reconstruct with P planes of level l
 Error estimate (L-infinity)
     The recomposition bound of the compressor (see bounds.py): an error of
     at most d_l in the level-l coefficients gives at most
-    ``sum_l w_l d_l`` with w_0 = 1 and w_l = 1 + K_l.  With d_l = 2^(e_l-P_l)
+    ``sum_l w_l d_l`` with w_0 = 1 and w_l = c_l (the per-level constant of
+    the L-infinity width).  With d_l = 2^(e_l-P_l)
     (0 for an all-zero level) that is the estimate of a plane selection.
 
 Request (greedy)
@@ -99,9 +100,9 @@ def decode_level(n: int, e: int, signs, planes, P: int, B: int) -> np.ndarray:
 
 
 def weights(shape, max_levels=None) -> np.ndarray:
-    """w_0 = 1, w_l = 1 + K_l (the L-infinity recomposition weights)."""
+    """w_0 = 1, w_l = c_l (the L-infinity recomposition weights)."""
     h = hierarchy(shape, max_levels)
-    return np.array([1.0] + [1.0 + bounds.K(h, l) for l in range(1, h.L + 1)])
+    return np.array([1.0] + [bounds.linf_level_constant(h, l) for l in range(1, h.L + 1)])
 
 
 def refactor(u: np.ndarray, B: int = 32, max_levels=None):

@@ -121,7 +121,7 @@ void level_layout(const Plan& p, int B, mgard_mdr_header* h) {
         lv.words = (uint32_t)((lv.count + 31) / 32);
         lv.offset = off;
         off += ((uint64_t)(B + 1) * lv.words * 4 + 15) & ~uint64_t(15);
-        lv.weight = l == 0 ? 1.0 : 1.0 + p.K[l];
+        lv.weight = l == 0 ? 1.0 : p.linf_c[l];
     }
     h->total_bytes = off;
 }

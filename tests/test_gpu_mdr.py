@@ -72,7 +72,7 @@ def test_planes_bit_exact_with_oracle_encoding(shape, dtype):
         assert np.array_equal(signs, rs)
         for b in range(B):
             assert np.array_equal(planes[b], rp[b]), (l, b)
-        w = 1.0 if l == 0 else 1.0 + bounds.K(hh, l)
+        w = 1.0 if l == 0 else bounds.linf_level_constant(hh, l)
         assert abs(lv["weight"] - w) <= 1e-12 * w
 
 
