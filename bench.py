@@ -46,11 +46,11 @@ SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
 # capture of the same command (profiles/dram_traffic_513cube.md; one pass per
 # launch).  Valid for the kernel versions captured.
 NCU_TRAFFIC_513 = {
-    "k_restrict_solve": (943.0e6, 251.9e6, 20), "k_decode": (332.2e6, 497.2e6, 1),
-    "k3_coeff": (671.6e6, 812.0e6, 5), "k_pack": (353.1e6, 189.1e6, 1),
-    "k3_fill": (618.0e6, 515.0e6, 5), "k3_restrict_x": (560.0e6, 242.5e6, 8),
-    "k_quantize_stream": (553.4e6, 282.5e6, 1), "k_solve_warp": (313.3e6, 33.9e6, 10),
-    "k_maxabs": (540.1e6, 3.3e6, 1), "k_chunk_count": (270.1e6, 1.4e6, 1),
+    "k_restrict_solve": (943.0e6, 252.1e6, 20), "k_decode": (298.3e6, 496.2e6, 1),
+    "k3_coeff": (671.3e6, 811.7e6, 5), "k_pack": (319.9e6, 165.4e6, 1),
+    "k3_fill": (618.6e6, 516.2e6, 5), "k3_restrict_x": (556.6e6, 241.9e6, 7),
+    "k_quantize_stream": (550.0e6, 258.3e6, 1), "k_solve_warp": (313.3e6, 33.9e6, 10),
+    "k_maxabs": (540.1e6, 3.0e6, 1), "k_chunk_count": (270.2e6, 1.3e6, 1),
 }
 
 
