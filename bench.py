@@ -312,7 +312,7 @@ def run_batch(args, rank, world, dev, barrier):
     def compress_eager():
         return binding.compress_batch(fields, tol, s_norm, binding.REL, outs=outs, graph=False)[0]
 
-    def compress_persistent():   # all codebooks in one persistent launch between two phases
+    def compress_persistent():   # every field's tail, then every codebook, in one persistent launch each
         return binding.compress_batch(fields, tol, s_norm, binding.REL, outs=outs, graph=True,
                                       persistent=True)[0]
 
@@ -381,9 +381,9 @@ def run_batch(args, rank, world, dev, barrier):
                                    f"{nbytes / 1e9:.3f} GB, s=0 rel 1e-3",
                        "l2": "batch larger than L2, no flush", "parallelism": f"replicas x{world}"},
             "compress_ms": {"graph": ms_graph, "graph_s1": ms_graph_s1,
-                            "graph_persistent_codebooks": ms_persistent,
+                            "graph_persistent": ms_persistent,
                             "streams_no_graph": ms_eager, "separate_calls": ms_each},
-            "compress_gbs": {"graph": gbs(ms_graph), "graph_persistent_codebooks": gbs(ms_persistent),
+            "compress_gbs": {"graph": gbs(ms_graph), "graph_persistent": gbs(ms_persistent),
                              "streams_no_graph": gbs(ms_eager), "separate_calls": gbs(ms_each)},
             "decompress_ms": {"graph": ms_dec_graph, "separate_calls": ms_dec_each},
             "clocks": clocks,

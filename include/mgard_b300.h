@@ -265,10 +265,13 @@ mgard_status mgard_decompress(const void* in, size_t in_bytes, void** field,
 #define MGARD_BATCH_GRAPH 1
 #define MGARD_BATCH_AUTOTUNE 2   /* run mgard_autotune on every new shape of the batch first */
 #define MGARD_BATCH_REPEAT 4     /* capture and replay a graph once an identical call repeats */
-/* Build the codebooks and decoding tables of all fields in one launch: a
- * persistent grid (up to one block per SM) takes one job per field from a
- * device counter, between a phase that decomposes and quantizes every field
- * and a phase that encodes them (same bytes as without the flag). */
+/* Run the batch in phases with persistent multi-field launches: every
+ * field's decomposition down to its small levels; one launch for all those
+ * one-block tails (levels of at most a few thousand nodes); every field's
+ * widths and quantization; one launch for all codebooks and decoding
+ * tables; every field's encoding.  Each persistent launch is a grid of up
+ * to one block per SM whose blocks take one field at a time from a device
+ * counter.  Same bytes as without the flag. */
 #define MGARD_BATCH_PERSISTENT 8
 mgard_status mgard_compress_batch(int n, const void* const* fields, const int* ndims,
                                   const int64_t* const* shapes, mgard_dtype dtype, double tol,

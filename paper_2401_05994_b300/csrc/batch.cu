@@ -20,6 +20,7 @@
 
 #include "huffman.cuh"
 #include "pipeline.cuh"
+#include "rows3.cuh"
 
 namespace mgb {
 
@@ -131,6 +132,13 @@ struct BatchState {
     CompressMeta* hmetas = nullptr;     // pinned host copy
     CodebookJob* jobs = nullptr;        // device, one per field (persistent codebook phase)
     unsigned* job_counter = nullptr;    // device
+    // persistent tail phase: the fields whose small levels wait for one
+    // batched launch, and that launch's job list (device) and shared memory
+    std::vector<char> tail_deferred;
+    void* tail_jobs = nullptr;
+    int ntail = 0;
+    size_t tail_smem = 0;
+    unsigned* tail_counter = nullptr;
     Lanes lanes;
 
     ~BatchState() {
@@ -141,11 +149,16 @@ struct BatchState {
         if (metas) cudaFreeAsync(metas, lanes.side[0]);
         if (jobs) cudaFreeAsync(jobs, lanes.side[0]);
         if (job_counter) cudaFreeAsync(job_counter, lanes.side[0]);
+        if (tail_jobs) cudaFreeAsync(tail_jobs, lanes.side[0]);
+        if (tail_counter) cudaFreeAsync(tail_counter, lanes.side[0]);
         if (lanes.side[0]) cudaStreamSynchronize(lanes.side[0]);
         lanes.destroy();
         if (hmetas) cudaFreeHost(hmetas);
         cudaGetLastError();
     }
+
+    template <typename T>
+    CompressWork<T>& work(int i);
 
     mgard_status init(const BatchKey& k, const int* ndims, const int64_t* const* shapes) {
         key = k;
@@ -179,6 +192,7 @@ struct BatchState {
             count_device_alloc();
             MGB_CUDA(cudaMallocAsync((void**)&job_counter, sizeof(unsigned), s0));
             MGB_CUDA(cudaMemcpyAsync(jobs, hj.data(), sizeof(CodebookJob) * k.n, cudaMemcpyHostToDevice, s0));
+            MGB_TRY(k.dtype == MGARD_F32 ? tail_jobs_t<float>(k, s0) : tail_jobs_t<double>(k, s0));
         }
         MGB_TRY(huffman_prepare());
         MGB_CUDA(cudaStreamSynchronize(s0));
@@ -203,17 +217,60 @@ struct BatchState {
                                      key.s, (mgard_tolmode)key.mode, dd, cap, *wd[i], metas + i, ss);
     }
 
-    // The persistent form: every field's decomposition, widths and
-    // quantization (front), one launch for all codebooks and tables, then
-    // every field's count pass, header and payload (back).
+    // The persistent form: every field's decomposition down to its
+    // one-block tail (front_a); one launch for all those tails; every field's
+    // level 0, widths and quantization (front_b); one launch for all
+    // codebooks and tables; then every field's count pass, header and
+    // payload (back).  Fields whose decomposition needs level energies
+    // (finite s > 0, relative) run their tail in front_a.
     template <typename T>
-    mgard_status front_t(int i, cudaStream_t ss, CompressWork<T>& w) {
+    mgard_status tail_jobs_t(const BatchKey& k, cudaStream_t s0) {
+        const size_t bytes = tail_args_bytes<T>();
+        std::vector<char> host;
+        tail_deferred.assign(k.n, 0);
+        const bool energies = k.mode == MGARD_REL && !std::isinf(k.s) && k.s != 0.0;
+        for (int i = 0; i < k.n; ++i) {
+            const Plan& p = *plans[i];
+            const int Lt = rows3_ok(p) ? tail_levels(p) : 0;
+            if (!Lt || energies) continue;
+            CompressWork<T>& w = work<T>(i);
+            const T* level_Lt = Lt == p.L ? (const T*)k.fields[i] : w.py.lv[Lt];
+            host.resize(host.size() + bytes);
+            size_t smem = 0;
+            MGB_TRY(tail_job<T>(p, Lt, w.py, level_Lt, w.top.template as<T>(), w.top.template as<T>(),
+                                host.data() + host.size() - bytes, &smem));
+            tail_smem = std::max(tail_smem, smem);
+            tail_deferred[i] = 1;
+            ++ntail;
+        }
+        if (!ntail) return MGARD_OK;
+        count_device_alloc();
+        MGB_CUDA(cudaMallocAsync(&tail_jobs, host.size(), s0));
+        count_device_alloc();
+        MGB_CUDA(cudaMallocAsync((void**)&tail_counter, sizeof(unsigned), s0));
+        MGB_CUDA(cudaMemcpyAsync(tail_jobs, host.data(), host.size(), cudaMemcpyHostToDevice, s0));
+        return MGARD_OK;
+    }
+    template <typename T>
+    mgard_status front_a_t(int i, cudaStream_t ss, CompressWork<T>& w) {
         const Plan& p = *plans[i];
         const uint64_t N = (uint64_t)p.total();
         const Sections fx = layout(p.L, (N + CHUNK - 1) / CHUNK, 0, 0);
         MGB_CUDA(cudaMemsetAsync(key.outs[i], 0, fx.outliers, ss));
-        MGB_TRY(compress_decompose<T>(p, (const T*)key.fields[i], key.s, (mgard_tolmode)key.mode, w,
-                                      metas + i, ss));
+        w.py.defer_tail = tail_deferred[i] != 0;
+        const mgard_status r = compress_decompose<T>(p, (const T*)key.fields[i], key.s,
+                                                     (mgard_tolmode)key.mode, w, metas + i, ss);
+        w.py.defer_tail = false;
+        if (r == MGARD_OK && (w.py.tail_pending != (tail_deferred[i] != 0))) {
+            set_error("batched tail: the decomposition did not stop where planned");
+            return MGARD_EINVAL;
+        }
+        return r;
+    }
+    template <typename T>
+    mgard_status front_b_t(int i, cudaStream_t ss, CompressWork<T>& w) {
+        const Plan& p = *plans[i];
+        if (tail_deferred[i]) MGB_TRY(decompose_finish<T>(p, w.py, w.top.template as<T>(), ss));
         return compress_encode_front<T>(p, (const T*)key.fields[i], key.tol, key.s,
                                         (mgard_tolmode)key.mode, w, metas + i, ss);
     }
@@ -224,19 +281,36 @@ struct BatchState {
         MGB_TRY(compress_encode_back<T>(p, heads[i], dd, key.caps[i], w, metas + i, ss));
         return compress_pack<T>(p, dd, w, metas + i, ss);
     }
-    mgard_status front(int i, cudaStream_t ss) {
-        return key.dtype == MGARD_F32 ? front_t<float>(i, ss, *wf[i]) : front_t<double>(i, ss, *wd[i]);
+    mgard_status front_a(int i, cudaStream_t ss) {
+        return key.dtype == MGARD_F32 ? front_a_t<float>(i, ss, *wf[i]) : front_a_t<double>(i, ss, *wd[i]);
+    }
+    mgard_status front_b(int i, cudaStream_t ss) {
+        return key.dtype == MGARD_F32 ? front_b_t<float>(i, ss, *wf[i]) : front_b_t<double>(i, ss, *wd[i]);
     }
     mgard_status back(int i, cudaStream_t ss) {
         return key.dtype == MGARD_F32 ? back_t<float>(i, ss, *wf[i]) : back_t<double>(i, ss, *wd[i]);
     }
     mgard_status phased(cudaStream_t st) {
         const int n = key.n;
-        MGB_TRY(lanes.run(st, n, [this](int i, cudaStream_t ss) { return front(i, ss); }));
+        MGB_TRY(lanes.run(st, n, [this](int i, cudaStream_t ss) { return front_a(i, ss); }));
+        if (ntail)
+            MGB_TRY(key.dtype == MGARD_F32
+                        ? tail_decompose_batch<float>(tail_jobs, ntail, tail_smem, tail_counter, st)
+                        : tail_decompose_batch<double>(tail_jobs, ntail, tail_smem, tail_counter, st));
+        MGB_TRY(lanes.run(st, n, [this](int i, cudaStream_t ss) { return front_b(i, ss); }));
         MGB_TRY(huffman_codebook_tables_batch(jobs, n, job_counter, st));
         return lanes.run(st, n, [this](int i, cudaStream_t ss) { return back(i, ss); });
     }
 };
+
+template <>
+CompressWork<float>& BatchState::work<float>(int i) {
+    return *wf[i];
+}
+template <>
+CompressWork<double>& BatchState::work<double>(int i) {
+    return *wd[i];
+}
 
 // Graphs are used when asked for, or (MGARD_BATCH_REPEAT) from the second
 // identical call on; never while kernel tracing is on (graph launches are not

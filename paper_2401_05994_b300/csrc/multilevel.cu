@@ -1461,8 +1461,13 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
     // energies are taken afterwards; in place it overwrites them, so levels
     // with energies requested run level by level.
     const int Lt = (rows3_ok(p) && (zs || (!E && !Epart))) ? tail_levels(p) : 0;
+    py.tail_pending = false;
     for (int l = p.L; l >= 1; --l) {
         const T* src = l == p.L ? in : py.lv[l];
+        if (l == Lt && py.defer_tail && zs && !E && !Epart) {   // the caller runs the tail
+            py.tail_pending = true;
+            return MGARD_OK;
+        }
         if (l == Lt) {
             MGB_TRY(tail_decompose<T>(p, Lt, py, src, zs, top, st));
             for (int k = Lt; k >= 1; --k) {   // level 0 follows below
@@ -1494,6 +1499,14 @@ mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& p
     if (Epart) MGB_TRY(mass_norm2_partials<T>(p, 0, u0, Epart, st));
     if (zs)   // level 0 leads the symbol order
         MGB_CUDA(cudaMemcpyAsync(zs, u0, p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    return MGARD_OK;
+}
+
+template <typename T>
+mgard_status decompose_finish(const Plan& p, Pyramid<T>& py, T* zs, cudaStream_t st) {
+    if (zs && p.L)   // level 0 leads the symbol order
+        MGB_CUDA(cudaMemcpyAsync(zs, py.lv[0], p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    py.tail_pending = false;
     return MGARD_OK;
 }
 
@@ -1559,6 +1572,7 @@ mgard_status gather_levels(const Plan& p, const T* data, Pyramid<T>& py, cudaStr
     template struct Pyramid<T>;                                                               \
     template mgard_status decompose_pyramid<T>(const Plan&, const T*, T*, Pyramid<T>&,         \
                                                cudaStream_t, double*, double*, T*);            \
+    template mgard_status decompose_finish<T>(const Plan&, Pyramid<T>&, T*, cudaStream_t);     \
     template mgard_status max_abs_partials<T>(const T*, int64_t, double*, unsigned*,           \
                                               cudaStream_t);                                   \
     template mgard_status mass_norm2_partials<T>(const Plan&, int, const T*, double*,          \

@@ -47,6 +47,12 @@ struct Pyramid {
     // device status word for kernels' bounded waits (ST_TIMEOUT); null: the
     // library's per-device fallback word
     unsigned* status = nullptr;
+    // with defer_tail, decompose_pyramid leaves the one-block tail (and the
+    // copy of level 0 into the symbol-order array) to the caller, which runs
+    // it (a batched tail launch) and then decompose_finish; tail_pending
+    // tells whether it did
+    bool defer_tail = false;
+    bool tail_pending = false;
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 
@@ -82,6 +88,19 @@ int tail_levels(const Plan& p);
 template <typename T>
 mgard_status tail_decompose(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs,
                             T* top, cudaStream_t st);
+// The same for many fields in one launch: tail_job fills one field's
+// arguments (host memory of tail_args_bytes<T>() bytes; *smem receives the
+// shared memory they need); tail_decompose_batch runs n of them (device
+// array `jobs`) on a persistent grid whose blocks take jobs from *counter
+// (device; reset here, stream-ordered), with smem the largest need.
+template <typename T>
+size_t tail_args_bytes();
+template <typename T>
+mgard_status tail_job(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs, T* top,
+                      void* args, size_t* smem);
+template <typename T>
+mgard_status tail_decompose_batch(const void* jobs, int n, size_t smem, unsigned* counter,
+                                  cudaStream_t st);
 // The inverse for levels 1..Lt: from py.lv[0] and the coefficients (zs, or
 // the level arrays), writes level Lt's nodal values to level_Lt (and
 // levels 1..Lt-1 into the pyramid).
@@ -104,6 +123,11 @@ template <typename T>
 mgard_status decompose_pyramid(const Plan& p, const T* in, T* top, Pyramid<T>& py,
                                cudaStream_t st, double* E, double* Epart = nullptr,
                                T* zs = nullptr);
+
+// What decompose_pyramid left when it deferred the tail, after the tail
+// has run: level 0 into the symbol-order array zs.
+template <typename T>
+mgard_status decompose_finish(const Plan& p, Pyramid<T>& py, T* zs, cudaStream_t st);
 
 // Recompose: `top` holds level-L coefficients (coarse positions ignored),
 // py.lv[l] the coefficients of level l >= 1 (coarse positions ignored) and

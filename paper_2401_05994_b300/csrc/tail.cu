@@ -188,7 +188,7 @@ __device__ inline TailMem<T> tail_mem(const TailArgs<T>& a) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) {
+__device__ void tail_decompose_body(const TailArgs<T>& a) {
     const TailMem<T> m = tail_mem(a);
     for (int k = threadIdx.x; k < a.size[a.Lt]; k += TAIL_THREADS) m.u[a.Lt][k] = a.g[a.Lt][k];
     __syncthreads();
@@ -231,7 +231,30 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) {
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose(TailArgs<T> a) {
+    tail_decompose_body(a);
+}
+
+// The tails of many fields: a persistent grid whose blocks take one field
+// at a time from a device counter (one atomicAdd per job, no waits between
+// blocks), each job the same steps as k_tail_decompose on that field.
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_decompose_batch(const TailArgs<T>* jobs,
+                                                                       int n, unsigned* next) {
+    __shared__ int job;
+    for (;;) {
+        if (threadIdx.x == 0) job = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int j = job;
+        __syncthreads();   // every thread holds j before the next job is taken
+        if (j >= n) return;
+        tail_decompose_body(jobs[j]);
+        __syncthreads();   // the shared arrays are reused by the next job
+    }
+}
+
+template <typename T>
+__device__ void tail_recompose_body(const TailArgs<T>& a) {
     const TailMem<T> m = tail_mem(a);
     for (int k = threadIdx.x; k < a.size[0]; k += TAIL_THREADS) m.u[0][k] = a.g[0][k];
     __syncthreads();
@@ -265,6 +288,11 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) 
         __syncthreads();
     }
     for (int k = threadIdx.x; k < a.size[a.Lt]; k += TAIL_THREADS) a.g[a.Lt][k] = m.u[a.Lt][k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) {
+    tail_recompose_body(a);
 }
 
 template <typename T>
@@ -335,6 +363,44 @@ mgard_status tail_recompose(const Plan& p, int Lt, Pyramid<T>& py, const T* zs, 
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
+
+template <typename T>
+size_t tail_args_bytes() {
+    return sizeof(TailArgs<T>);
+}
+
+template <typename T>
+mgard_status tail_job(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, T* zs, T* top,
+                      void* args, size_t* smem) {
+    return make_args<T>(p, Lt, py, const_cast<T*>(level_Lt), zs, top,
+                        reinterpret_cast<TailArgs<T>*>(args), smem);
+}
+
+template <typename T>
+mgard_status tail_decompose_batch(const void* jobs, int n, size_t smem, unsigned* counter,
+                                  cudaStream_t st) {
+    if (n <= 0) return MGARD_OK;
+    int dev = 0, sms = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    MGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MGB_TRY(allow_dynamic_smem((const void*)k_tail_decompose_batch<T>, smem));
+    MGB_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    MGB_LAUNCH("k_tail_decompose_batch", st,
+               k_tail_decompose_batch<T><<<std::min(n, sms), TAIL_THREADS, smem, st>>>(
+                   reinterpret_cast<const TailArgs<T>*>(jobs), n, counter));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
+#define INST_TAIL_BATCH(T)                                                                       \
+    template size_t tail_args_bytes<T>();                                                        \
+    template mgard_status tail_job<T>(const Plan&, int, Pyramid<T>&, const T*, T*, T*, void*,    \
+                                      size_t*);                                                  \
+    template mgard_status tail_decompose_batch<T>(const void*, int, size_t, unsigned*,           \
+                                                  cudaStream_t);
+INST_TAIL_BATCH(float)
+INST_TAIL_BATCH(double)
+#undef INST_TAIL_BATCH
 
 template mgard_status tail_decompose<float>(const Plan&, int, Pyramid<float>&, const float*, float*,
                                             float*, cudaStream_t);
