@@ -69,6 +69,19 @@ def test_bin_widths_match_oracle(shape, s):
     assert np.max(np.abs(got - exp) / exp) < 1e-12
 
 
+def test_linf_width_of_the_benchmark_grid():
+    """The L-infinity width of the 513^3 benchmark grid: the plan's per-level
+    constants from unit solves against the oracle's dense evaluation, and
+    the 1.39x gain over the earlier 1 + K_l bound."""
+    shape = (513, 513, 513)
+    got = binding.bin_widths(shape, 1.0, math.inf)
+    exp = bounds.bin_widths(shape, 1.0, math.inf)
+    assert np.max(np.abs(got - exp) / exp) < 1e-12
+    h = grid.hierarchy(shape)
+    old = 1.0 + sum(1.0 + bounds.K(h, l) for l in range(1, h.L + 1))
+    assert 1.35 < got[0] / (2.0 * bounds.WIDTH_MARGIN / old) < 1.45
+
+
 def test_bin_widths_large_axis_window():
     """Axes of more than 2048 coarse nodes evaluate the correction norm on
     windows near the ends and one interior row; the result must equal the
