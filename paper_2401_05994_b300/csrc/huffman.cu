@@ -802,10 +802,14 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
     __shared__ __align__(16) uint16_t lut[1 << LUT_BITS];
     __shared__ unsigned long long lim[LMAX + 2];
     __shared__ uint32_t fcode[LMAX + 2], findex[LMAX + 2];
+    __shared__ __align__(16) uint16_t ssorted[DICT];   // symbols of codes longer than LUT_BITS
     {
         const uint4* src = reinterpret_cast<const uint4*>(gdt->lut);
         uint4* dst = reinterpret_cast<uint4*>(lut);
         for (int k = threadIdx.x; k < (int)(sizeof(lut) / 16); k += blockDim.x) dst[k] = src[k];
+        const uint4* ssrc = reinterpret_cast<const uint4*>(gdt->sorted);
+        uint4* sdst = reinterpret_cast<uint4*>(ssorted);
+        for (int k = threadIdx.x; k < (int)(sizeof(ssorted) / 16); k += blockDim.x) sdst[k] = ssrc[k];
         for (int k = threadIdx.x; k < LMAX + 2; k += blockDim.x) {   // blocks may be one warp
             lim[k] = gdt->lim[k];
             fcode[k] = gdt->first_code[k];
@@ -818,7 +822,7 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(status, ST_CORRUPT);
         return;
     }
-    const uint16_t* __restrict__ sorted = gdt->sorted;
+    const uint16_t* sorted = ssorted;
     bool ok = true;
     const uint64_t nsub = nchunks * NSUB;
     for (uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gid < nsub;

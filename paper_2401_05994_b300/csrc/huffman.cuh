@@ -1,6 +1,8 @@
 // Huffman codebook, encoder and decoder (declarations).
 #pragma once
 
+#include <cstddef>
+
 #include "common.cuh"
 
 namespace mgb {
@@ -24,6 +26,8 @@ struct DecodeTables {
     uint32_t maxlen;
     uint32_t valid;                     // 0 if the lengths violate the Kraft inequality
 };
+// the decoder copies lut and sorted in 16-byte units
+static_assert(offsetof(DecodeTables, sorted) % 16 == 0, "sorted must stay 16-byte aligned");
 
 // One-time per-device setup of the kernels (launch attributes); called by
 // huffman_codebook and, before any stream capture, by batched compression.
