@@ -362,6 +362,8 @@ def run_batch(args, rank, world, dev, barrier):
     ms_each = timed(compress_each, max(3, args.steps // 2))
     views = step()
     ms_dec_graph = timed(lambda: binding.decompress_batch(views, outs=recs, graph=True), args.steps)
+    ms_dec_persistent = timed(lambda: binding.decompress_batch(views, outs=recs, graph=True,
+                                                               persistent=True), args.steps)
     ms_dec_each = timed(lambda: decompress_each(views), max(3, args.steps // 2))
     views = step()
     worst = 0.0
@@ -385,7 +387,8 @@ def run_batch(args, rank, world, dev, barrier):
                             "streams_no_graph": ms_eager, "separate_calls": ms_each},
             "compress_gbs": {"graph": gbs(ms_graph), "graph_persistent": gbs(ms_persistent),
                              "streams_no_graph": gbs(ms_eager), "separate_calls": gbs(ms_each)},
-            "decompress_ms": {"graph": ms_dec_graph, "separate_calls": ms_dec_each},
+            "decompress_ms": {"graph": ms_dec_graph, "graph_persistent": ms_dec_persistent,
+                              "separate_calls": ms_dec_each},
             "clocks": clocks,
             "verify": {"worst_error_over_tol": worst, "ok": worst <= 1.0,
                        "ratio": nbytes / comp},

@@ -284,7 +284,10 @@ mgard_status mgard_compress_batch(int n, const void* const* fields, const int* n
  * (device, field_caps[i] bytes, at least the field's size).  The headers
  * come to the host in one round trip; the buffers then decompress on
  * internal streams (MGARD_BATCH_GRAPH: from a captured graph, replayed for
- * identical arguments and headers).  statuses[i] (host, may be NULL):
+ * identical arguments and headers; MGARD_BATCH_PERSISTENT, for buffers of
+ * one dtype: every buffer decoded to level 0, one persistent launch for all
+ * their small levels, then every buffer's larger levels; same results).
+ * statuses[i] (host, may be NULL):
  * MGARD_ECORRUPT for a buffer that fails validation, MGARD_ECAPACITY for a
  * field buffer that is too small; the other buffers still decompress.
  * Synchronizes `stream`.  Returns MGARD_OK or the first failing status. */

@@ -566,7 +566,8 @@ def compress_batch(fields, tol: float, s: float = math.inf, mode: int = REL, out
     return [o[:min(z, o.numel())] for o, z in zip(outs, sizes)], sizes, [int(x) for x in stats]
 
 
-def decompress_batch(bufs, outs=None, graph: bool = False, check: bool = True):
+def decompress_batch(bufs, outs=None, graph: bool = False, check: bool = True,
+                     persistent: bool = False):
     """Decompress a list of CUDA uint8 tensors (mgard_decompress_batch).
     ``outs``: list of CUDA tensors of the fields' shapes and dtypes (default:
     allocated from the headers).  Returns ``(outs, statuses)``."""
@@ -586,7 +587,8 @@ def decompress_batch(bufs, outs=None, graph: bool = False, check: bool = True):
     ocap = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
     stats = (ctypes.c_int * n)()
     st = lib().mgard_decompress_batch(n, iptr, isz, optr, ocap, stats,
-                                      BATCH_GRAPH if graph else 0, _stream())
+                                      (BATCH_GRAPH if graph else 0)
+                                      | (BATCH_PERSISTENT if persistent else 0), _stream())
     if check:
         _check(st)
     return outs, [int(x) for x in stats]

@@ -490,11 +490,20 @@ struct DecompressBatch {
     std::vector<mgard_status> pre;        // result of the host checks, per buffer
     unsigned* stat = nullptr;             // device, one per buffer
     unsigned* hstat = nullptr;            // pinned
+    // persistent tail phase (MGARD_BATCH_PERSISTENT): the buffers whose small
+    // levels wait for one batched launch, its job list and shared memory
+    std::vector<char> tail_deferred;
+    void* tail_jobs = nullptr;
+    int ntail = 0;
+    size_t tail_smem = 0;
+    unsigned* tail_counter = nullptr;
     Lanes lanes;
 
     ~DecompressBatch() {
         wf.clear();
         wd.clear();
+        if (tail_jobs) cudaFreeAsync(tail_jobs, lanes.side[0]);
+        if (tail_counter) cudaFreeAsync(tail_counter, lanes.side[0]);
         if (stat) cudaFreeAsync(stat, lanes.side[0]);
         if (lanes.side[0]) cudaStreamSynchronize(lanes.side[0]);
         lanes.destroy();
@@ -507,12 +516,77 @@ struct DecompressBatch {
         const mgard_header& h = heads[i];
         MGB_CUDA(cudaMemsetAsync(stat + i, 0, sizeof(unsigned), ss));
         if (h.dtype == MGARD_F32)
-            return decompress_core<float>(*plans[i], h, widths[i].data(), (const char*)key.ins[i],
-                                          (float*)key.outs[i], *wf[i], stat + i, ss);
-        return decompress_core<double>(*plans[i], h, widths[i].data(), (const char*)key.ins[i],
-                                       (double*)key.outs[i], *wd[i], stat + i, ss);
+            return item_t<float>(i, ss, *wf[i]);
+        return item_t<double>(i, ss, *wd[i]);
     }
+    template <typename T>
+    mgard_status item_t(int i, cudaStream_t ss, DecompressWork<T>& w) {
+        w.py.defer_tail = !tail_deferred.empty() && tail_deferred[i];
+        const mgard_status r = decompress_core<T>(*plans[i], heads[i], widths[i].data(),
+                                                  (const char*)key.ins[i], (T*)key.outs[i], w,
+                                                  stat + i, ss);
+        w.py.defer_tail = false;
+        const bool deferred = !tail_deferred.empty() && tail_deferred[i];
+        if (r == MGARD_OK && deferred != w.py.tail_pending) {
+            set_error("batched tail: the recomposition did not stop where planned");
+            return MGARD_EINVAL;
+        }
+        return r;
+    }
+    // after the batched tails: the levels above them
+    template <typename T>
+    mgard_status rest_t(int i, cudaStream_t ss, DecompressWork<T>& w) {
+        if (tail_deferred.empty() || !tail_deferred[i]) return MGARD_OK;
+        w.py.tail_done = true;
+        const mgard_status r = recompose_pyramid<T>(*plans[i], nullptr, (T*)key.outs[i], w.py, ss,
+                                                    w.zs.template as<T>());
+        w.py.tail_done = false;
+        return r;
+    }
+    mgard_status rest(int k, cudaStream_t ss) {
+        const int i = items[k];
+        return heads[i].dtype == MGARD_F32 ? rest_t<float>(i, ss, *wf[i]) : rest_t<double>(i, ss, *wd[i]);
+    }
+    template <typename T>
+    mgard_status tail_jobs_t(cudaStream_t s0) {
+        const size_t bytes = tail_args_bytes<T>();
+        std::vector<char> host;
+        tail_deferred.assign(plans.size(), 0);
+        for (int i : items) {
+            if (heads[i].dtype != (sizeof(T) == 4 ? (uint32_t)MGARD_F32 : (uint32_t)MGARD_F64)) continue;
+            const Plan& p = *plans[i];
+            const int Lt = rows3_ok(p) ? tail_levels(p) : 0;
+            if (!Lt) continue;
+            DecompressWork<T>& w = dwork<T>(i);
+            T* level_Lt = Lt == p.L ? (T*)key.outs[i] : w.py.lv[Lt];
+            host.resize(host.size() + bytes);
+            size_t smem = 0;
+            MGB_TRY(tail_job<T>(p, Lt, w.py, level_Lt, w.zs.template as<T>(), nullptr,
+                                host.data() + host.size() - bytes, &smem));
+            tail_smem = std::max(tail_smem, smem);
+            tail_deferred[i] = 1;
+            ++ntail;
+        }
+        if (!ntail) return MGARD_OK;
+        count_device_alloc();
+        MGB_CUDA(cudaMallocAsync(&tail_jobs, host.size(), s0));
+        count_device_alloc();
+        MGB_CUDA(cudaMallocAsync((void**)&tail_counter, sizeof(unsigned), s0));
+        MGB_CUDA(cudaMemcpyAsync(tail_jobs, host.data(), host.size(), cudaMemcpyHostToDevice, s0));
+        return MGARD_OK;
+    }
+    template <typename T>
+    DecompressWork<T>& dwork(int i);
 };
+
+template <>
+DecompressWork<float>& DecompressBatch::dwork<float>(int i) {
+    return *wf[i];
+}
+template <>
+DecompressWork<double>& DecompressBatch::dwork<double>(int i) {
+    return *wd[i];
+}
 
 std::list<std::unique_ptr<DecompressBatch>> g_dbatches;
 
@@ -533,7 +607,7 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
         set_error("null argument");
         return MGARD_EINVAL;
     }
-    if (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_REPEAT)) {
+    if (flags & ~(MGARD_BATCH_GRAPH | MGARD_BATCH_REPEAT | MGARD_BATCH_PERSISTENT)) {
         set_error("unknown flags");
         return MGARD_EINVAL;
     }
@@ -629,6 +703,12 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
             }
             nb->items.push_back(i);
         }
+        if ((flags & MGARD_BATCH_PERSISTENT) && !nb->items.empty()) {   // one dtype per batch
+            const uint32_t dt = nb->heads[nb->items[0]].dtype;
+            bool same = true;
+            for (int i : nb->items) same = same && nb->heads[i].dtype == dt;
+            if (same) MGB_TRY(dt == MGARD_F32 ? nb->tail_jobs_t<float>(s0) : nb->tail_jobs_t<double>(s0));
+        }
         MGB_CUDA(cudaStreamSynchronize(s0));
         nb->pre = pre;
         g_dbatches.push_front(std::move(nb));
@@ -638,7 +718,22 @@ extern "C" mgard_status mgard_decompress_batch(int n, const void* const* ins,
     const std::vector<mgard_status>& pre = b->pre;
     const int m = (int)b->items.size();
     auto body = [b](int k, cudaStream_t ss) { return b->item(k, ss); };
-    if (m) {
+    // persistent form: every buffer decoded down to level 0, one launch for
+    // all their small levels, then every buffer's larger levels
+    auto phased = [b, m, body](cudaStream_t s0) -> mgard_status {
+        MGB_TRY(b->lanes.run(s0, m, body));
+        const uint32_t dt = b->heads[b->items[0]].dtype;
+        MGB_TRY(dt == MGARD_F32
+                    ? tail_recompose_batch<float>(b->tail_jobs, b->ntail, b->tail_smem, b->tail_counter, s0)
+                    : tail_recompose_batch<double>(b->tail_jobs, b->ntail, b->tail_smem, b->tail_counter, s0));
+        return b->lanes.run(s0, m, [b](int k, cudaStream_t ss) { return b->rest(k, ss); });
+    };
+    if (m && b->ntail) {
+        if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph_seq(st, phased));
+        else MGB_TRY(phased(st));
+        ++b->lanes.runs;
+        MGB_CUDA(cudaMemcpyAsync(b->hstat, b->stat, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, st));
+    } else if (m) {
         if (use_graph(flags, b->lanes)) MGB_TRY(b->lanes.run_graph(st, m, body));
         else MGB_TRY(b->lanes.run(st, m, body));
         ++b->lanes.runs;

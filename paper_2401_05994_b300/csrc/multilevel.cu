@@ -1526,7 +1526,12 @@ mgard_status recompose_pyramid(const Plan& p, const T* top, T* out, Pyramid<T>& 
     if (zs) MGB_CUDA(cudaMemcpyAsync(py.lv[0], zs, p.count[0] * sizeof(T), cudaMemcpyDeviceToDevice, st));
     // small levels in one launch (row-kernel shapes)
     const int Lt = rows3_ok(p) ? tail_levels(p) : 0;
-    if (Lt) MGB_TRY(tail_recompose<T>(p, Lt, py, zs, top, Lt == p.L ? out : py.lv[Lt], st));
+    if (Lt && py.defer_tail && zs) {   // the caller runs the tail, then calls again with tail_done
+        py.tail_pending = true;
+        return MGARD_OK;
+    }
+    if (Lt && !py.tail_done) MGB_TRY(tail_recompose<T>(p, Lt, py, zs, top, Lt == p.L ? out : py.lv[Lt], st));
+    py.tail_pending = false;
     for (int l = Lt + 1; l <= p.L; ++l) {
         const T* z = zs ? zs : (l == p.L ? top : py.lv[l]);
         const int64_t zoff = zs ? p.offset[l] : -1;

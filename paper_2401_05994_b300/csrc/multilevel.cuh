@@ -53,6 +53,9 @@ struct Pyramid {
     // tells whether it did
     bool defer_tail = false;
     bool tail_pending = false;
+    // recompose_pyramid with defer_tail stops after level 0 in the same way
+    // (tail_pending); called again with tail_done it skips the tail
+    bool tail_done = false;
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 
@@ -100,6 +103,9 @@ mgard_status tail_job(const Plan& p, int Lt, Pyramid<T>& py, const T* level_Lt, 
                       void* args, size_t* smem);
 template <typename T>
 mgard_status tail_decompose_batch(const void* jobs, int n, size_t smem, unsigned* counter,
+                                  cudaStream_t st);
+template <typename T>
+mgard_status tail_recompose_batch(const void* jobs, int n, size_t smem, unsigned* counter,
                                   cudaStream_t st);
 // The inverse for levels 1..Lt: from py.lv[0] and the coefficients (zs, or
 // the level arrays), writes level Lt's nodal values to level_Lt (and

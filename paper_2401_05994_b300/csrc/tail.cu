@@ -295,6 +295,22 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose(TailArgs<T> a) 
     tail_recompose_body(a);
 }
 
+// The inverse for many fields, scheduled like k_tail_decompose_batch.
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_recompose_batch(const TailArgs<T>* jobs,
+                                                                       int n, unsigned* next) {
+    __shared__ int job;
+    for (;;) {
+        if (threadIdx.x == 0) job = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int j = job;
+        __syncthreads();
+        if (j >= n) return;
+        tail_recompose_body(jobs[j]);
+        __syncthreads();
+    }
+}
+
 template <typename T>
 mgard_status make_args(const Plan& p, int Lt, Pyramid<T>& py, T* top_level, T* zs, T* ztop,
                        TailArgs<T>* a, size_t* smem) {
@@ -392,11 +408,29 @@ mgard_status tail_decompose_batch(const void* jobs, int n, size_t smem, unsigned
     return MGARD_OK;
 }
 
+template <typename T>
+mgard_status tail_recompose_batch(const void* jobs, int n, size_t smem, unsigned* counter,
+                                  cudaStream_t st) {
+    if (n <= 0) return MGARD_OK;
+    int dev = 0, sms = 0;
+    MGB_CUDA(cudaGetDevice(&dev));
+    MGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MGB_TRY(allow_dynamic_smem((const void*)k_tail_recompose_batch<T>, smem));
+    MGB_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    MGB_LAUNCH("k_tail_recompose_batch", st,
+               k_tail_recompose_batch<T><<<std::min(n, sms), TAIL_THREADS, smem, st>>>(
+                   reinterpret_cast<const TailArgs<T>*>(jobs), n, counter));
+    MGB_CUDA(cudaGetLastError());
+    return MGARD_OK;
+}
+
 #define INST_TAIL_BATCH(T)                                                                       \
     template size_t tail_args_bytes<T>();                                                        \
     template mgard_status tail_job<T>(const Plan&, int, Pyramid<T>&, const T*, T*, T*, void*,    \
                                       size_t*);                                                  \
     template mgard_status tail_decompose_batch<T>(const void*, int, size_t, unsigned*,           \
+                                                  cudaStream_t);                                 \
+    template mgard_status tail_recompose_batch<T>(const void*, int, size_t, unsigned*,           \
                                                   cudaStream_t);
 INST_TAIL_BATCH(float)
 INST_TAIL_BATCH(double)

@@ -103,14 +103,15 @@ def test_batch_rejects_host_buffers():
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_decompress_batch_equals_single(graph):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_decompress_batch_equals_single(graph, persistent):
     fields = _fields()
     views, _, _ = binding.compress_batch(fields, 1e-3, math.inf, binding.REL)
     bufs = [v.clone() for v in views]
     ref = [binding.decompress(b).cpu().numpy() for b in bufs]
     outs = [torch.full(f.shape, 7.0, dtype=f.dtype, device=DEV) for f in fields]
     for _ in range(2):   # graph replay on the second call
-        got, stats = binding.decompress_batch(bufs, outs=outs, graph=graph)
+        got, stats = binding.decompress_batch(bufs, outs=outs, graph=graph, persistent=persistent)
         assert stats == [0] * len(bufs)
         for g, r in zip(got, ref):
             assert np.array_equal(g.cpu().numpy(), r)
