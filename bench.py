@@ -405,8 +405,8 @@ def run_ratio(args, rank, world, dev):
     shape = (256, 384, 384)
     ntrain, ntest = 60, 40
     step_stride = max(1, int(os.environ.get("RATIO_STRIDE", "1")))
-    # ratios a rigorous L-infinity bound reaches on this field: about 12 at a
-    # relative tolerance of 1 (a third of the coefficients quantize to zero
+    # ratios a rigorous L-infinity bound reaches on this field: about 14 at a
+    # relative tolerance of 1 (under half of the coefficients quantize to zero
     # there); 50 and 100 would need tolerances above the field's magnitude
     targets = [float(v) for v in os.environ.get("RATIO_TARGETS", "3,6,10").split(",")]
     field = lambda t: synth.advected_field(shape, t, seed=1 + 100 * rank, device=dev).contiguous()
