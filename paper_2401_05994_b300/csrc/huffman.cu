@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(CB_THREADS) k_codebook(const unsigned long lon
     codebook_body(hist, lengths, wide, *reinterpret_cast<CodebookSmem*>(smem_raw));
 }
 
-// Canonical codes and decoding tables from the code lengths, one block.
+// Canonical codes and decoding tables from the code lengths, one block
+// (dt null: the codes alone).
 // A symbol's place in (length, symbol) order is fi[len] plus the number of
 // lower symbols of the same length: counts per 32-symbol chunk (one warp
 // match each), an exclusive scan over the chunks per length (one warp per
@@ -354,14 +355,16 @@ __device__ void tables_body(const uint8_t* __restrict__ lengths, uint32_t* __res
             if (cnt[l]) maxlen = l;
         }
         const bool valid = !bad && kraft <= (1ull << LMAX);
-        for (int l = 0; l < LMAX + 2; ++l) {
+        for (int l = 0; dt && l < LMAX + 2; ++l) {
             const bool in = l >= 1 && l <= LMAX;
             dt->first_code[l] = in ? (uint32_t)fc[l] : 0;
             dt->first_index[l] = in ? fi[l] : 0;
             dt->lim[l] = in ? ((fc[l] + cnt[l]) << (LMAX - l)) : 0;
         }
-        dt->maxlen = maxlen;
-        dt->valid = valid ? 1 : 0;
+        if (dt) {
+            dt->maxlen = maxlen;
+            dt->valid = valid ? 1 : 0;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -375,9 +378,10 @@ __device__ void tables_body(const uint8_t* __restrict__ lengths, uint32_t* __res
         const unsigned rank = cc[s >> 5][len] + myrank[it];
         const unsigned p = fi[len] + rank;
         ssym[p] = (uint16_t)s;
-        dt->sorted[p] = (uint16_t)s;
+        if (dt) dt->sorted[p] = (uint16_t)s;
         codes[s] = (uint32_t)(fc[len] + rank);
     }
+    if (!dt) return;   // codes only (the encoder needs no decoding tables)
     __syncthreads();
     // prefix table: the code under each 14-bit prefix, found from the
     // canonical limits (every entry costs the same, whatever the lengths).

@@ -36,7 +36,8 @@ mgard_status huffman_prepare();
 // weights (needed when the histogram totals 2^32 symbols or more).
 mgard_status huffman_codebook(const unsigned long long* hist, uint8_t* lengths, uint32_t* codes,
                               cudaStream_t st, bool wide = true);
-// Canonical codes and decode tables from code lengths (single CTA).
+// Canonical codes and decode tables from code lengths (single CTA); with
+// dt null only the codes.
 mgard_status huffman_tables(const uint8_t* lengths, uint32_t* codes, DecodeTables* dt,
                             cudaStream_t st);
 // Codebooks and tables of n fields in one launch: a persistent grid (up to

@@ -280,7 +280,7 @@ mgard_status compress_encode(const Plan& p, const T* din, const mgard_header& h0
     MGB_TRY(compress_encode_front<T>(p, din, tol, s, mode, w, meta, st));
     const CodebookJob j = codebook_job<T>(p, w);
     MGB_TRY(huffman_codebook(j.hist, j.lengths, nullptr, st, j.wide != 0));
-    MGB_TRY(huffman_tables(j.lengths, j.codes, j.dt, st));
+    MGB_TRY(huffman_tables(j.lengths, j.codes, nullptr, st));   // the encoder needs the codes only
     return compress_encode_back<T>(p, h0, dd, cap, w, meta, st);
 }
 
