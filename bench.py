@@ -1059,8 +1059,8 @@ def main():
            "h2d_bytes_per_step": field_bytes + hb.nbytes,
            "d2h_bytes_per_step": hb.nbytes + field_bytes}
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    cpu = None   # the oracle baseline: rank 0 of a one-GPU run only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b, t, cores = cpu_oracle_sample(u.cpu().numpy(), TOL)
         cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"{SAMPLE}^3 sub-cube of the field, compress+decompress incl. decode"}
