@@ -679,6 +679,210 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve_tma(
     }
 }
 
+// The same pass with each warp owning one segment of the coarse rows from
+// the copy to the write.  Warp w's segment is coarse rows [r0, r0 + cnt),
+// r0 = w seg; its fine rows f(r0) - 2 .. f(r0) + 2 seg arrive by TMA in one
+// box of br = 2 seg + 3 rows into the warp's own buffer, the warp restricts
+// them straight into registers (lane l: column l), hands the buffer to the
+// next tile's copy, solves its segment with the maps of the other segments
+// folded through shared memory, and writes its rows from registers.  No
+// restricted tile passes through shared memory.  Tiles are 32 columns of
+// one outer index (`tin`, boxes of 32 x br x 1); when the last columns of an
+// outer index are at most four (the padded row of a 2^k + 1 axis), they are
+// taken from eight outer indices at once (`ttail`, boxes of 4 x br x 8, in
+// shared memory as [8][br][4]: lane l reads outer l / 4, column l % 4), so
+// no tile runs with 4 of its 32 lanes live.  Products of the segments' map
+// slopes do not depend on the data and are taken once per block.  Same
+// arithmetic, in the same order, as k_restrict_solve and
+// k_restrict_solve_tma.
+// Coarse row J's restriction from the rows of a box whose first row is fine
+// row f0 (RP: the box's row pitch), by the tables: valid for any J.
+template <typename Tw, int RP>
+__device__ inline Tw restrict_row(const Tw* __restrict__ b, int J, int mc, int m, int f0,
+                                  const Tw* __restrict__ rw) {
+    const int f = J == mc - 1 ? m - 1 : 2 * J;
+    Tw acc = Tw(0);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int ip = f - 2 + t;   // rows outside the axis arrived as zeros
+        const Tw w = (ip >= 0 && ip < m) ? rw[J * 5 + t] : Tw(0);
+        acc += w * b[(ip - f0) * RP];
+    }
+    return acc;
+}
+
+// A segment's restriction into registers: every row with the uniform window
+// (rows 2j .. 2j+4 of the box), then the axis' first and last rows again by
+// the tables.  The caller guarantees that rows 1 .. mc-2 are uniform.
+template <typename Tw, int K, int RP>
+__device__ inline void restrict_segment(const Tw* __restrict__ b, Tw (&v)[K], int cnt,
+                                        const Tw (&wi)[5], int r0, int mc, int m, int f0,
+                                        const Tw* __restrict__ rw) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        Tw acc = Tw(0);
+        if (j < cnt) {
+            const Tw* r = b + 2 * j * RP;
+            acc = wi[0] * r[0];
+            acc += wi[1] * r[RP];
+            acc += wi[2] * r[2 * RP];
+            acc += wi[3] * r[3 * RP];
+            acc += wi[4] * r[4 * RP];
+        }
+        v[j] = acc;
+    }
+    if (r0 == 0 && cnt > 0) v[0] = restrict_row<Tw, RP>(b, 0, mc, m, f0, rw);
+    if (cnt > 0 && r0 + cnt == mc) {
+        const Tw g = restrict_row<Tw, RP>(b, mc - 1, mc, m, f0, rw);
+        // a mask the compiler cannot see through, so the select stays one
+        // select per register instead of an indexed store to local memory
+        uint64_t hit;
+        asm("mov.b64 %0, %1;" : "=l"(hit) : "l"(1ull << (cnt - 1)));
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if ((hit >> j) & 1ull) v[j] = g;
+    }
+}
+
+template <typename Tw, int K, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg(
+    const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap ttail,
+    Tw* __restrict__ out, int64_t outer_n, int m, int mc, int64_t inner, AxisT<Tw> ax, int seg,
+    int br, int64_t tpo, int64_t ntail, unsigned* status) {
+    extern __shared__ __align__(128) unsigned char seg_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)seg_raw + 127) & ~(uintptr_t)127);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Tw* box = reinterpret_cast<Tw*>(base) + (size_t)wid * br * 32;   // this warp's fine rows
+    Tw* sal = reinterpret_cast<Tw*>(base) + (size_t)NW * br * 32;    // [mc] -a_k inv_k
+    Tw* sinv = sal + mc;                                             // [mc] inv_k
+    Tw* sga = sinv + mc;                                             // [mc] -c'_k
+    uint64_t* bar = reinterpret_cast<uint64_t*>(((uintptr_t)(sga + mc) + 7) & ~(uintptr_t)7);
+    __shared__ Tw sB[NW][32], sAf[NW], sAb[NW];
+    for (int k = threadIdx.x; k < mc; k += blockDim.x) {
+        sal[k] = -ax.tsub[k] * ax.tinv[k];
+        sinv[k] = ax.tinv[k];
+        sga[k] = -ax.tcp[k];
+    }
+    const int r0 = wid * seg;
+    const int cnt = max(0, min(seg, mc - r0));
+    const int f0 = (r0 == mc - 1 ? m - 1 : 2 * r0) - 2;   // fine row of the box's first row
+    Tw wi[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) wi[t] = ax.rwi[t];
+    const int64_t nmain = outer_n * tpo;
+    const int64_t ntiles = nmain + ntail;
+    const int64_t x0 = tpo * 32;   // first column of the tail boxes
+    const uint32_t box_bytes = (uint32_t)br * 32u * (uint32_t)sizeof(Tw);
+    const bool owner = lane == 0 && cnt > 0;   // issues and waits for this warp's copies
+    auto issue = [&](int64_t tile) {
+        mbar_expect_tx(&bar[wid], box_bytes);
+        if (tile < nmain) {
+            const int64_t o = tile / tpo;
+            tma_load_3d(box, &tin, (int)((tile - o * tpo) * 32), f0, (int)o, &bar[wid]);
+        } else {
+            tma_load_3d(box, &ttail, (int)x0, f0, (int)((tile - nmain) * 8), &bar[wid]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NW; ++w) mbar_init(&bar[w]);
+        mbar_fence_init();
+    }
+    __syncthreads();   // the barriers and the factor tables are ready
+    if (lane == 0) {
+        Tw A = Tw(1);
+        for (int j = 0; j < cnt; ++j) A = sal[r0 + j] * A;
+        sAf[wid] = A;
+        A = Tw(1);
+        for (int j = cnt - 1; j >= 0; --j) A = sga[r0 + j] * A;
+        sAb[wid] = A;
+    }
+    if (owner && blockIdx.x < ntiles) issue(blockIdx.x);
+    uint32_t phase = 0;
+    bool failed = false, pending = owner && blockIdx.x < ntiles;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        bool ok = true;
+        if (owner) ok = mbar_wait(&bar[wid], phase, TMA_MAX_POLLS);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        pending = false;
+        Tw v[K];
+        const bool tail = tile >= nmain;
+        if (!tail)
+            restrict_segment<Tw, K, 32>(box + lane, v, cnt, wi, r0, mc, m, f0, ax.rw);
+        else
+            restrict_segment<Tw, K, 4>(box + (lane >> 2) * br * 4 + (lane & 3), v, cnt, wi, r0,
+                                       mc, m, f0, ax.rw);
+        __syncwarp();   // every lane has read the box: the next tile's rows may land in it
+        const int64_t next = tile + gridDim.x;
+        if (owner && next < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(next);
+            pending = true;
+        }
+        // forward sweep: y_k = al_k y_{k-1} + v_k inv_k
+        Tw B = Tw(0);
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (j < cnt) {
+                const Tw al = sal[r0 + j], w = v[j] * sinv[r0 + j];
+                v[j] = w;
+                B = al * B + w;
+            }
+        sB[wid][lane] = B;
+        __syncthreads();
+        Tw y = Tw(0);
+        for (int s2 = 0; s2 < wid; ++s2) y = sAf[s2] * y + sB[s2][lane];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (j < cnt) {
+                y = sal[r0 + j] * y + v[j];
+                v[j] = y;
+            }
+        // backward sweep: x_k = -c'_k x_{k+1} + y_k
+        B = Tw(0);
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j)
+            if (j < cnt) B = sga[r0 + j] * B + v[j];
+        __syncthreads();   // every thread has read the forward maps
+        sB[wid][lane] = B;
+        __syncthreads();
+        Tw x = Tw(0);
+        for (int s2 = NW - 1; s2 > wid; --s2) x = sAb[s2] * x + sB[s2][lane];
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j)
+            if (j < cnt) {
+                x = sga[r0 + j] * x + v[j];
+                v[j] = x;
+            }
+        // write the segment's rows
+        int64_t o, col;
+        bool live;
+        if (!tail) {
+            o = tile / tpo;
+            col = (tile - o * tpo) * 32 + lane;
+            live = col < inner;
+        } else {
+            o = (tile - nmain) * 8 + (lane >> 2);
+            col = x0 + (lane & 3);
+            live = o < outer_n && col < inner;
+        }
+        if (live && cnt > 0) {
+            Tw* dst = out + (o * mc + r0) * inner + col;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) dst[(int64_t)j * inner] = v[j];
+        }
+    }
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(status, (unsigned)ST_TIMEOUT);
+        // the copy this warp asked for last may still be in flight
+        if (owner && pending) mbar_wait(&bar[wid], phase, TMA_MAX_POLLS);
+    }
+}
+
 // Lines along the contiguous axis, one warp per line held in registers: lane
 // j owns elements [jE, jE+E).  Both Thomas sweeps are first-order affine
 // recurrences (y_k = alpha_k y_{k-1} + beta_k forward, x_k = gamma_k
@@ -1202,6 +1406,61 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
     return MGARD_OK;
 }
 
+// The per-warp segment pass (k_restrict_solve_seg): eight warps of at most
+// 33 coarse rows each up to 264 coarse rows, sixteen up to 528 (float; in
+// double, segments of at most 17 rows); chosen when its boxes fit in 200 KB
+// of shared memory and the axis' interior rows are uniform.  *done stays
+// false otherwise.
+template <typename Tw>
+mgard_status restrict_solve_seg(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
+                                int64_t inner, const AxisT<Tw>& ax, cudaStream_t st, bool* done,
+                                unsigned* status) {
+    const int nw = mc <= 264 ? 8 : 16;
+    // rows 1 .. mc-2 must take the uniform window (the first and last rows
+    // are taken from the tables)
+    if (mc > 528 || (mc > 2 && (ax.rlo > 1 || ax.rhi < mc - 1))) return MGARD_OK;
+    const int seg = (int)((mc + nw - 1) / nw);
+    const int br = 2 * seg + 3;
+    const size_t bytes = ((size_t)nw * br * 32 + 3 * (size_t)mc) * sizeof(Tw) + 8 +
+                         (size_t)nw * 8 + 128;   // barriers, their alignment, 128-byte slack
+    if (bytes > (size_t)200 * 1024) return MGARD_OK;
+    // the last columns of each outer index go to 4-wide tail boxes when there are at most four
+    const int64_t rem = inner % 32;
+    const bool tails = rem >= 1 && rem <= 4;
+    const int64_t tpo = tails ? inner / 32 : (inner + 31) / 32;
+    const int64_t ntail = tails ? (outer + 7) / 8 : 0;
+    const int64_t ntiles = outer * tpo + ntail;
+    CUtensorMap tin, ttail;
+    const uint64_t dims[3] = {(uint64_t)inner, (uint64_t)m, (uint64_t)outer};
+    const uint64_t strides[2] = {(uint64_t)inner * sizeof(Tw), (uint64_t)(m * inner) * sizeof(Tw)};
+    const uint32_t box[3] = {32u, (uint32_t)br, 1u};
+    const uint32_t tbox[3] = {4u, (uint32_t)br, 8u};
+    if (encode_tensor_map_3d(&tin, in, (int)sizeof(Tw), dims, strides, box) != MGARD_OK ||
+        encode_tensor_map_3d(&ttail, in, (int)sizeof(Tw), dims, strides, tbox) != MGARD_OK) {
+        cudaGetLastError();
+        return MGARD_OK;   // another form runs instead
+    }
+    auto go = [&](auto kern, int threads) -> mgard_status {
+        MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
+        int grid = 0;
+        MGB_TRY(resident_grid((const void*)kern, threads, bytes, ntiles, &grid));
+        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, threads, bytes, st>>>(tin, ttail, out, outer, (int)m, (int)mc, inner, ax, seg, br, tpo, ntail, status));
+        MGB_CUDA(cudaGetLastError());
+        *done = true;
+        return MGARD_OK;
+    };
+    if (seg <= 2) return go(k_restrict_solve_seg<Tw, 2, 8>, 256);
+    if (seg <= 4) return go(k_restrict_solve_seg<Tw, 4, 8>, 256);
+    if (seg <= 8) return go(k_restrict_solve_seg<Tw, 8, 8>, 256);
+    if (seg <= 17 && nw == 8) return go(k_restrict_solve_seg<Tw, 17, 8>, 256);
+    // segments of 33 rows: float only (33 doubles per thread would spill)
+    if constexpr (sizeof(Tw) == 4) {
+        if (nw == 16) return go(k_restrict_solve_seg<Tw, 33, 16>, 512);
+        return go(k_restrict_solve_seg<Tw, 33, 8>, 256);
+    }
+    return MGARD_OK;
+}
+
 // The TMA-staged pass: the fewest parts whose box (2 jp + 5 rows, at most
 // 256) and shared memory fit three blocks per SM (72 KB), else two (110 KB),
 // else one (200 KB).  *done stays false when the rows are not 16-byte aligned
@@ -1213,6 +1472,8 @@ mgard_status restrict_solve_tma(const Tw* in, Tw* out, int64_t outer, int64_t m,
     if (!status || (inner * (int64_t)sizeof(Tw)) % 16 != 0 || ((uintptr_t)in & 15) != 0 ||
         inner > (int64_t(1) << 31) || outer > (int64_t(1) << 31))
         return MGARD_OK;
+    MGB_TRY(restrict_solve_seg<Tw>(in, out, outer, m, mc, inner, ax, st, done, status));
+    if (*done) return MGARD_OK;
     auto smem_for = [&](int parts, int* jp, int* br) {
         *jp = (int)((mc + parts - 1) / parts);
         *br = 2 * *jp + 5;
