@@ -679,22 +679,26 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_restrict_solve_tma(
     }
 }
 
-// The same pass with each warp owning one segment of the coarse rows from
-// the copy to the write.  Warp w's segment is coarse rows [r0, r0 + cnt),
-// r0 = w seg; its fine rows f(r0) - 2 .. f(r0) + 2 seg arrive by TMA in one
-// box of br = 2 seg + 3 rows into the warp's own buffer, the warp restricts
-// them straight into registers (lane l: column l), hands the buffer to the
-// next tile's copy, solves its segment with the maps of the other segments
-// folded through shared memory, and writes its rows from registers.  No
-// restricted tile passes through shared memory.  Tiles are 32 columns of
-// one outer index (`tin`, boxes of 32 x br x 1); when the last columns of an
-// outer index are at most four (the padded row of a 2^k + 1 axis), they are
-// taken from eight outer indices at once (`ttail`, boxes of 4 x br x 8, in
-// shared memory as [8][br][4]: lane l reads outer l / 4, column l % 4), so
-// no tile runs with 4 of its 32 lanes live.  Products of the segments' map
-// slopes do not depend on the data and are taken once per block.  Same
-// arithmetic, in the same order, as k_restrict_solve and
+// The same pass with each warp owning one segment of K coarse rows from the
+// copy to the write.  Warp w's segment is coarse rows [r0, r0 + K), r0 = w K;
+// its fine rows f(r0) - 2 .. f(r0) + 2 K arrive by TMA in one box of
+// br = 2 K + 3 rows into the warp's own buffer, the warp restricts them
+// straight into registers (lane l: column l), hands the buffer to the next
+// tile's copy, solves its segment with the maps of the other segments folded
+// through shared memory, and writes its rows from registers.  No restricted
+// tile passes through shared memory.  Rows past the axis (the end of the last
+// segment, and whole segments when K NW > mc) run through the same
+// arithmetic with factors 0 (al = inv = -c' = 0), which leaves the real rows'
+// results unchanged bit for bit, so no loop tests a row count.  Tiles are 32
+// columns of one outer index (`tin`, boxes of 32 x br x 1); when the last
+// columns of an outer index are at most four (the padded row of a 2^k + 1
+// axis), they are taken from eight outer indices at once (`ttail`, boxes of
+// 4 x br x 8, in shared memory as [8][br][4]: lane l reads outer l / 4,
+// column l % 4), so no tile runs with 4 of its 32 lanes live.  Products of
+// the segments' map slopes do not depend on the data and are taken once per
+// block.  Same arithmetic, in the same order, as k_restrict_solve and
 // k_restrict_solve_tma.
+
 // Coarse row J's restriction from the rows of a box whose first row is fine
 // row f0 (RP: the box's row pitch), by the tables: valid for any J.
 template <typename Tw, int RP>
@@ -715,56 +719,68 @@ __device__ inline Tw restrict_row(const Tw* __restrict__ b, int J, int mc, int m
 // (rows 2j .. 2j+4 of the box), then the axis' first and last rows again by
 // the tables.  The caller guarantees that rows 1 .. mc-2 are uniform.
 template <typename Tw, int K, int RP>
-__device__ inline void restrict_segment(const Tw* __restrict__ b, Tw (&v)[K], int cnt,
-                                        const Tw (&wi)[5], int r0, int mc, int m, int f0,
+__device__ inline void restrict_segment(const Tw* __restrict__ b, Tw (&v)[K], const Tw (&wi)[5],
+                                        int r0, int mc, int m, int f0,
                                         const Tw* __restrict__ rw) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        Tw acc = Tw(0);
-        if (j < cnt) {
-            const Tw* r = b + 2 * j * RP;
-            acc = wi[0] * r[0];
-            acc += wi[1] * r[RP];
-            acc += wi[2] * r[2 * RP];
-            acc += wi[3] * r[3 * RP];
-            acc += wi[4] * r[4 * RP];
-        }
+        const Tw* r = b + 2 * j * RP;
+        Tw acc = wi[0] * r[0];
+        acc += wi[1] * r[RP];
+        acc += wi[2] * r[2 * RP];
+        acc += wi[3] * r[3 * RP];
+        acc += wi[4] * r[4 * RP];
         v[j] = acc;
     }
-    if (r0 == 0 && cnt > 0) v[0] = restrict_row<Tw, RP>(b, 0, mc, m, f0, rw);
-    if (cnt > 0 && r0 + cnt == mc) {
+    if (r0 == 0) v[0] = restrict_row<Tw, RP>(b, 0, mc, m, f0, rw);
+    if (mc - 1 - r0 < K) {   // the axis' last row is this segment's row mc-1-r0
         const Tw g = restrict_row<Tw, RP>(b, mc - 1, mc, m, f0, rw);
         // a mask the compiler cannot see through, so the select stays one
         // select per register instead of an indexed store to local memory
         uint64_t hit;
-        asm("mov.b64 %0, %1;" : "=l"(hit) : "l"(1ull << (cnt - 1)));
+        asm("mov.b64 %0, %1;" : "=l"(hit) : "l"(1ull << (mc - 1 - r0)));
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if ((hit >> j) & 1ull) v[j] = g;
     }
 }
 
+// Four consecutive factors of a segment's table (16-byte aligned).
+__device__ inline void load4(const float* p, float (&o)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ inline void load4(const double* p, double (&o)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
 template <typename Tw, int K, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg(
     const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap ttail,
-    Tw* __restrict__ out, int64_t outer_n, int m, int mc, int64_t inner, AxisT<Tw> ax, int seg,
-    int br, int64_t tpo, int64_t ntail, unsigned* status) {
+    Tw* __restrict__ out, int64_t outer_n, int m, int mc, int64_t inner, AxisT<Tw> ax, int br,
+    int64_t tpo, int64_t ntail, unsigned* status) {
+    constexpr int KP = (K + 3) / 4 * 4;   // a segment's table entries, padded to 16 bytes
     extern __shared__ __align__(128) unsigned char seg_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)seg_raw + 127) & ~(uintptr_t)127);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Tw* box = reinterpret_cast<Tw*>(base) + (size_t)wid * br * 32;   // this warp's fine rows
-    Tw* sal = reinterpret_cast<Tw*>(base) + (size_t)NW * br * 32;    // [mc] -a_k inv_k
-    Tw* sinv = sal + mc;                                             // [mc] inv_k
-    Tw* sga = sinv + mc;                                             // [mc] -c'_k
-    uint64_t* bar = reinterpret_cast<uint64_t*>(((uintptr_t)(sga + mc) + 7) & ~(uintptr_t)7);
+    Tw* tab = reinterpret_cast<Tw*>(base) + (size_t)NW * br * 32;    // [3][NW][KP] factors
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tab + 3 * NW * KP);
     __shared__ Tw sB[NW][32], sAf[NW], sAb[NW];
-    for (int k = threadIdx.x; k < mc; k += blockDim.x) {
-        sal[k] = -ax.tsub[k] * ax.tinv[k];
-        sinv[k] = ax.tinv[k];
-        sga[k] = -ax.tcp[k];
+    // factors per segment row: -a_J inv_J, inv_J, -c'_J; 0 past the axis
+    for (int k = threadIdx.x; k < NW * KP; k += blockDim.x) {
+        const int J = (k / KP) * K + k % KP;
+        const bool in_seg = k % KP < K && J < mc;
+        tab[k] = in_seg ? -ax.tsub[J] * ax.tinv[J] : Tw(0);
+        tab[NW * KP + k] = in_seg ? ax.tinv[J] : Tw(0);
+        tab[2 * NW * KP + k] = in_seg ? -ax.tcp[J] : Tw(0);
     }
-    const int r0 = wid * seg;
-    const int cnt = max(0, min(seg, mc - r0));
+    const Tw* tal = tab + wid * KP;
+    const Tw* tinv = tab + NW * KP + wid * KP;
+    const Tw* tga = tab + 2 * NW * KP + wid * KP;
+    const int r0 = wid * K;
+    const bool active = r0 < mc;   // the segment holds rows of the axis
     const int f0 = (r0 == mc - 1 ? m - 1 : 2 * r0) - 2;   // fine row of the box's first row
     Tw wi[5];
 #pragma unroll
@@ -773,7 +789,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
     const int64_t ntiles = nmain + ntail;
     const int64_t x0 = tpo * 32;   // first column of the tail boxes
     const uint32_t box_bytes = (uint32_t)br * 32u * (uint32_t)sizeof(Tw);
-    const bool owner = lane == 0 && cnt > 0;   // issues and waits for this warp's copies
+    const bool owner = lane == 0 && active;   // issues and waits for this warp's copies
     auto issue = [&](int64_t tile) {
         mbar_expect_tx(&bar[wid], box_bytes);
         if (tile < nmain) {
@@ -790,10 +806,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
     __syncthreads();   // the barriers and the factor tables are ready
     if (lane == 0) {
         Tw A = Tw(1);
-        for (int j = 0; j < cnt; ++j) A = sal[r0 + j] * A;
+        for (int j = 0; j < K; ++j) A = tal[j] * A;
         sAf[wid] = A;
         A = Tw(1);
-        for (int j = cnt - 1; j >= 0; --j) A = sga[r0 + j] * A;
+        for (int j = K - 1; j >= 0; --j) A = tga[j] * A;
         sAb[wid] = A;
     }
     if (owner && blockIdx.x < ntiles) issue(blockIdx.x);
@@ -810,11 +826,15 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
         pending = false;
         Tw v[K];
         const bool tail = tile >= nmain;
-        if (!tail)
-            restrict_segment<Tw, K, 32>(box + lane, v, cnt, wi, r0, mc, m, f0, ax.rw);
-        else
-            restrict_segment<Tw, K, 4>(box + (lane >> 2) * br * 4 + (lane & 3), v, cnt, wi, r0,
-                                       mc, m, f0, ax.rw);
+        if (!active) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = Tw(0);
+        } else if (!tail) {
+            restrict_segment<Tw, K, 32>(box + lane, v, wi, r0, mc, m, f0, ax.rw);
+        } else {
+            restrict_segment<Tw, K, 4>(box + (lane >> 2) * br * 4 + (lane & 3), v, wi, r0, mc, m,
+                                       f0, ax.rw);
+        }
         __syncwarp();   // every lane has read the box: the next tile's rows may land in it
         const int64_t next = tile + gridDim.x;
         if (owner && next < ntiles) {
@@ -823,41 +843,47 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
             pending = true;
         }
         // forward sweep: y_k = al_k y_{k-1} + v_k inv_k
+        Tw f4a[4], f4b[4];
         Tw B = Tw(0);
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (j < cnt) {
-                const Tw al = sal[r0 + j], w = v[j] * sinv[r0 + j];
-                v[j] = w;
-                B = al * B + w;
+        for (int j = 0; j < K; ++j) {
+            if (j % 4 == 0) {
+                load4(tal + j, f4a);
+                load4(tinv + j, f4b);
             }
+            const Tw w = v[j] * f4b[j % 4];
+            v[j] = w;
+            B = f4a[j % 4] * B + w;
+        }
         sB[wid][lane] = B;
         __syncthreads();
         Tw y = Tw(0);
         for (int s2 = 0; s2 < wid; ++s2) y = sAf[s2] * y + sB[s2][lane];
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (j < cnt) {
-                y = sal[r0 + j] * y + v[j];
-                v[j] = y;
-            }
+        for (int j = 0; j < K; ++j) {
+            if (j % 4 == 0) load4(tal + j, f4a);
+            y = f4a[j % 4] * y + v[j];
+            v[j] = y;
+        }
         // backward sweep: x_k = -c'_k x_{k+1} + y_k
         B = Tw(0);
 #pragma unroll
-        for (int j = K - 1; j >= 0; --j)
-            if (j < cnt) B = sga[r0 + j] * B + v[j];
+        for (int j = K - 1; j >= 0; --j) {
+            if (j % 4 == 3 || j == K - 1) load4(tga + (j & ~3), f4a);
+            B = f4a[j % 4] * B + v[j];
+        }
         __syncthreads();   // every thread has read the forward maps
         sB[wid][lane] = B;
         __syncthreads();
         Tw x = Tw(0);
         for (int s2 = NW - 1; s2 > wid; --s2) x = sAb[s2] * x + sB[s2][lane];
 #pragma unroll
-        for (int j = K - 1; j >= 0; --j)
-            if (j < cnt) {
-                x = sga[r0 + j] * x + v[j];
-                v[j] = x;
-            }
-        // write the segment's rows
+        for (int j = K - 1; j >= 0; --j) {
+            if (j % 4 == 3 || j == K - 1) load4(tga + (j & ~3), f4a);
+            x = f4a[j % 4] * x + v[j];
+            v[j] = x;
+        }
+        // write the segment's rows that lie on the axis
         int64_t o, col;
         bool live;
         if (!tail) {
@@ -869,11 +895,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
             col = x0 + (lane & 3);
             live = o < outer_n && col < inner;
         }
-        if (live && cnt > 0) {
+        if (live && active) {
             Tw* dst = out + (o * mc + r0) * inner + col;
+            if (r0 + K <= mc) {
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (j < cnt) dst[(int64_t)j * inner] = v[j];
+                for (int j = 0; j < K; ++j) dst[(int64_t)j * inner] = v[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (r0 + j < mc) dst[(int64_t)j * inner] = v[j];
+            }
         }
     }
     if (failed) {
@@ -1406,23 +1437,32 @@ mgard_status solve_strided(Tw* x, int64_t outer, int64_t m, int64_t stride, cons
     return MGARD_OK;
 }
 
-// The per-warp segment pass (k_restrict_solve_seg): eight warps of at most
-// 33 coarse rows each up to 264 coarse rows, sixteen up to 528 (float; in
-// double, segments of at most 17 rows); chosen when its boxes fit in 200 KB
-// of shared memory and the axis' interior rows are uniform.  *done stays
-// false otherwise.
+// The per-warp segment pass (k_restrict_solve_seg): eight warps of K coarse
+// rows, K in {2, 3, 5, 9, 17, 33} the smallest with 8 K >= mc (2^k + 1 coarse
+// rows fill the segments exactly), sixteen warps of 33 up to 528 rows (float;
+// in double, segments of at most 17 rows); chosen when its boxes fit in
+// 200 KB of shared memory and the axis' interior rows are uniform.  *done
+// stays false otherwise.
 template <typename Tw>
 mgard_status restrict_solve_seg(const Tw* in, Tw* out, int64_t outer, int64_t m, int64_t mc,
                                 int64_t inner, const AxisT<Tw>& ax, cudaStream_t st, bool* done,
                                 unsigned* status) {
-    const int nw = mc <= 264 ? 8 : 16;
     // rows 1 .. mc-2 must take the uniform window (the first and last rows
     // are taken from the tables)
     if (mc > 528 || (mc > 2 && (ax.rlo > 1 || ax.rhi < mc - 1))) return MGARD_OK;
-    const int seg = (int)((mc + nw - 1) / nw);
-    const int br = 2 * seg + 3;
-    const size_t bytes = ((size_t)nw * br * 32 + 3 * (size_t)mc) * sizeof(Tw) + 8 +
-                         (size_t)nw * 8 + 128;   // barriers, their alignment, 128-byte slack
+    const int nw = mc <= 264 ? 8 : 16;
+    int K = 33;
+    if (nw == 8)
+        for (int k : {2, 3, 5, 9, 17, 33})
+            if ((int64_t)k * nw >= mc) {
+                K = k;
+                break;
+            }
+    if (sizeof(Tw) == 8 && K > 17) return MGARD_OK;   // 33 doubles per thread would spill
+    const int KP = (K + 3) / 4 * 4;
+    const int br = 2 * K + 3;
+    const size_t bytes = ((size_t)nw * br * 32 + 3 * (size_t)nw * KP) * sizeof(Tw) +
+                         (size_t)nw * 8 + 128;   // barriers, 128-byte alignment slack
     if (bytes > (size_t)200 * 1024) return MGARD_OK;
     // the last columns of each outer index go to 4-wide tail boxes when there are at most four
     const int64_t rem = inner % 32;
@@ -1444,16 +1484,19 @@ mgard_status restrict_solve_seg(const Tw* in, Tw* out, int64_t outer, int64_t m,
         MGB_TRY(allow_dynamic_smem((const void*)kern, bytes));
         int grid = 0;
         MGB_TRY(resident_grid((const void*)kern, threads, bytes, ntiles, &grid));
-        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, threads, bytes, st>>>(tin, ttail, out, outer, (int)m, (int)mc, inner, ax, seg, br, tpo, ntail, status));
+        MGB_LAUNCH("k_restrict_solve", st, kern<<<grid, threads, bytes, st>>>(tin, ttail, out, outer, (int)m, (int)mc, inner, ax, br, tpo, ntail, status));
         MGB_CUDA(cudaGetLastError());
         *done = true;
         return MGARD_OK;
     };
-    if (seg <= 2) return go(k_restrict_solve_seg<Tw, 2, 8>, 256);
-    if (seg <= 4) return go(k_restrict_solve_seg<Tw, 4, 8>, 256);
-    if (seg <= 8) return go(k_restrict_solve_seg<Tw, 8, 8>, 256);
-    if (seg <= 17 && nw == 8) return go(k_restrict_solve_seg<Tw, 17, 8>, 256);
-    // segments of 33 rows: float only (33 doubles per thread would spill)
+    switch (K) {
+        case 2: return go(k_restrict_solve_seg<Tw, 2, 8>, 256);
+        case 3: return go(k_restrict_solve_seg<Tw, 3, 8>, 256);
+        case 5: return go(k_restrict_solve_seg<Tw, 5, 8>, 256);
+        case 9: return go(k_restrict_solve_seg<Tw, 9, 8>, 256);
+        case 17: return go(k_restrict_solve_seg<Tw, 17, 8>, 256);
+        default: break;
+    }
     if constexpr (sizeof(Tw) == 4) {
         if (nw == 16) return go(k_restrict_solve_seg<Tw, 33, 16>, 512);
         return go(k_restrict_solve_seg<Tw, 33, 8>, 256);
