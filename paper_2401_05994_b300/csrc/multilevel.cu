@@ -756,7 +756,7 @@ __device__ inline void load4(const double* p, double (&o)[4]) {
 }
 
 template <typename Tw, int K, int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg(
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (K <= 17 ? 2 : 1)) k_restrict_solve_seg(
     const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap ttail,
     Tw* __restrict__ out, int64_t outer_n, int m, int mc, int64_t inner, AxisT<Tw> ax, int br,
     int64_t tpo, int64_t ntail, unsigned* status) {
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
     Tw* box = reinterpret_cast<Tw*>(base) + (size_t)wid * br * 32;   // this warp's fine rows
     Tw* tab = reinterpret_cast<Tw*>(base) + (size_t)NW * br * 32;    // [3][NW][KP] factors
     uint64_t* bar = reinterpret_cast<uint64_t*>(tab + 3 * NW * KP);
-    __shared__ Tw sB[NW][32], sAf[NW], sAb[NW];
+    __shared__ Tw sBf[NW][32], sBb[NW][32], sAf[NW], sAb[NW];
     // factors per segment row: -a_J inv_J, inv_J, -c'_J; 0 past the axis
     for (int k = threadIdx.x; k < NW * KP; k += blockDim.x) {
         const int J = (k / KP) * K + k % KP;
@@ -855,10 +855,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
             v[j] = w;
             B = f4a[j % 4] * B + w;
         }
-        sB[wid][lane] = B;
+        sBf[wid][lane] = B;
         __syncthreads();
         Tw y = Tw(0);
-        for (int s2 = 0; s2 < wid; ++s2) y = sAf[s2] * y + sB[s2][lane];
+        for (int s2 = 0; s2 < wid; ++s2) y = sAf[s2] * y + sBf[s2][lane];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             if (j % 4 == 0) load4(tal + j, f4a);
@@ -872,11 +872,12 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 1) k_restrict_solve_seg
             if (j % 4 == 3 || j == K - 1) load4(tga + (j & ~3), f4a);
             B = f4a[j % 4] * B + v[j];
         }
-        __syncthreads();   // every thread has read the forward maps
-        sB[wid][lane] = B;
+        // (the forward maps have their own buffer: the next tile writes them
+        // only after its first barrier, when every thread has read them)
+        sBb[wid][lane] = B;
         __syncthreads();
         Tw x = Tw(0);
-        for (int s2 = NW - 1; s2 > wid; --s2) x = sAb[s2] * x + sB[s2][lane];
+        for (int s2 = NW - 1; s2 > wid; --s2) x = sAb[s2] * x + sBb[s2][lane];
 #pragma unroll
         for (int j = K - 1; j >= 0; --j) {
             if (j % 4 == 3 || j == K - 1) load4(tga + (j & ~3), f4a);
