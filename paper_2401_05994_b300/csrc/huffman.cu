@@ -19,6 +19,8 @@
 #include <map>
 #include <mutex>
 
+#include <type_traits>
+
 #include "huffman.cuh"
 #include "multilevel.cuh"
 
@@ -403,6 +405,20 @@ __device__ void tables_body(const uint8_t* __restrict__ lengths, uint32_t* __res
             const unsigned long long idx = fi[l] + ((top >> (32 - l)) - fc[l]);
             if ((top >> (32 - l)) >= fc[l] && idx < DICT)
                 ent = (uint16_t)((l << 12) | (unsigned)ssym[idx]);
+        } else {
+            // longer codes: when every code under the prefix has the same
+            // length L (the first and last value under it reach the same
+            // number of limits), the entry is 15 << 12 | L and the decoder
+            // skips the search over the limits
+            const unsigned long long last = top + ((1ull << (32 - LUT_BITS)) - 1);
+            unsigned la = 1, lb = 1;
+            for (int j = 1; j <= LMAX; ++j) {
+                const unsigned long long lj = (fc[j] + cnt[j]) << (LMAX - j);
+                la += top >= lj;
+                lb += last >= lj;
+            }
+            if (la == lb && la > LUT_BITS && la <= LMAX && cnt[la])
+                ent = (uint16_t)((15u << 12) | la);
         }
         dt->lut[k] = ent;
     }
@@ -778,7 +794,12 @@ constexpr int DEC_BLOCKS_PER_SM = 2;   // 33 KB of tables per block; registers c
 // Decoding: one thread per sub-chunk of SUB symbols, in a grid that stays
 // resident (each block copies the prefix table once).  The bit window is a
 // left-justified 64-bit register refilled one word at a time; a symbol costs
-// one shared-memory lookup unless its code is longer than LUT_BITS.  Word
+// one shared-memory lookup unless its code is longer than LUT_BITS (then the
+// prefix entry gives its length when all codes under the prefix share one,
+// else the canonical limits are searched).  Word and escape indices are
+// relative to the chunk and the sub-chunk (32-bit arithmetic), and whole
+// groups of eight symbols inside one level run without tests for the
+// sub-chunk's end or a level boundary.  Word
 // loads never leave the chunk, escape reads never leave the chunk's escape
 // range, and a sub-chunk whose code stream does not end where its recorded
 // offsets say (or that meets a prefix with no code) marks the stream corrupt.
@@ -868,17 +889,25 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
         // window: `nb` valid bits, left-justified in `win`; the next two
         // words wait in f[] (loaded two refills ahead of their use; a longer
         // queue covered more latency but cost more moves than it saved)
-        uint64_t wi = bstart >> 5;
-        const uint32_t w0 = wi < cw1 ? words[wi] : 0u;
+        // word indices relative to the chunk (a chunk holds at most
+        // CHUNK * LMAX / 32 words), so the refill does 32-bit arithmetic
+        const uint32_t* __restrict__ cwp = words + cw0;
+        const uint32_t nwc = (uint32_t)min(cw1 - cw0, (uint64_t)0x7fffffff);
+        uint32_t wi = (uint32_t)min((bstart >> 5) - cw0, (uint64_t)0x7fffffff);
+        const uint32_t w0 = wi < nwc ? cwp[wi] : 0u;
         ++wi;
         uint32_t f[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) f[q] = wi + q < cw1 ? words[wi + q] : 0u;
+        for (int q = 0; q < 2; ++q) f[q] = wi + q < nwc ? cwp[wi + q] : 0u;
         const unsigned skip = (unsigned)(bstart & 31);
         const uint64_t wi_start = wi;   // words entered into the window so far: wi - wi_start + 1
         uint64_t win = ((uint64_t)w0 << 32) << skip;
         int nb = 32 - (int)skip;
-        int32_t next_out = e < e_end ? outliers[e] : 0;   // the next escape value, loaded ahead
+        // escapes relative to the sub-chunk's first (at most SUB of them)
+        const int32_t* __restrict__ ep = outliers + e;
+        const uint32_t ne = (uint32_t)min(e_end - e, (uint64_t)0x7fffffff);
+        uint32_t ei = 0;
+        int32_t next_out = ei < ne ? ep[ei] : 0;   // the next escape value, loaded ahead
         uint32_t pk[4] = {0, 0, 0, 0};
         OutT vk[8];
         // level of the current symbol (dequantizing output)
@@ -901,56 +930,70 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
         // (pk, vk) stay in registers.  A malformed stream only raises `bad`
         // (every access stays bounded); the sub-chunk is then rejected.
         bool bad = false;
-        for (int k0 = 0; k0 < cnt; k0 += 8) {
-            const bool whole = k0 + 8 <= cnt;
-#pragma unroll
-            for (int slot = 0; slot < 8; ++slot) {
-                const int k = k0 + slot;
-                if (!whole && k >= cnt) continue;
-                if (nb <= 32) {
-                    win |= (uint64_t)f[0] << (32 - nb);
-                    nb += 32;
-                    f[0] = f[1];
-                    f[1] = wi + 2 < cw1 ? words[wi + 2] : 0u;
-                    ++wi;
-                }
-                const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
-                unsigned len, s;
-                if (ent) {
-                    len = ent >> 12;
-                    s = ent & 0xFFF;
-                } else {
-                    const uint32_t top = (uint32_t)(win >> 32);
-                    unsigned l = LUT_BITS + 1;
+        // one symbol; FAST: the group is whole and stays in one level, so
+        // neither the sub-chunk's end nor a level boundary is tested
+        auto decode_one = [&](auto fast_tag, int k0, int slot) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+            const int k = k0 + slot;
+            if (!FAST && k >= cnt) return;
+            if (nb <= 32) {
+                win |= (uint64_t)f[0] << (32 - nb);
+                nb += 32;
+                f[0] = f[1];
+                // past the chunk's last word the load repeats it: those bits
+                // never reach a code (the used-bit check below holds)
+                f[1] = cwp[min(wi + 2, nwc - 1)];
+                ++wi;
+            }
+            const unsigned ent = lut[(unsigned)(win >> (64 - LUT_BITS))];
+            unsigned len, s;
+            if ((ent >> 12) - 1u < (unsigned)LUT_BITS) {   // a code of at most LUT_BITS
+                len = ent >> 12;
+                s = ent & 0xFFF;
+            } else {
+                const uint32_t top = (uint32_t)(win >> 32);
+                unsigned l = ent & 0xFFF;   // the prefix's one length, or 0: search
+                if (!l) {
+                    l = LUT_BITS + 1;
                     while (l <= maxlen && (unsigned long long)top >= lim[l]) ++l;
                     if (l > maxlen) {   // no code has this prefix
                         bad = true;
                         l = LUT_BITS + 1;
                     }
-                    len = l;
-                    s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
                 }
-                win <<= len;
-                nb -= (int)len;
-                int32_t qesc = 0;
-                if (s == MGARD_ESC) {
-                    bad = bad || e >= e_end;   // more escapes than the sub-chunk holds
-                    qesc = next_out;
-                    if (SYM) escapes[first + k] = next_out;
-                    ++e;
-                    next_out = e < e_end ? outliers[e] : 0;
-                }
-                if (SYM) {
-                    if (slot & 1) pk[slot >> 1] |= s << 16;
-                    else pk[slot >> 1] = s;
-                } else {
-                    if (k >= next_lvl) enter_level((long long)(first + k));
-                    OutT v;
-                    if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)cwf, cws, cw);
-                    else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), cwf);
-                    else v = (OutT)((double)((int)s - RADIUS) * cw);
-                    vk[slot] = v;
-                }
+                len = l;
+                s = sorted[min(findex[l] + ((top >> (32 - l)) - fcode[l]), (unsigned)DICT - 1)];
+            }
+            win <<= len;
+            nb -= (int)len;
+            int32_t qesc = 0;
+            if (s == MGARD_ESC) {
+                bad = bad || ei >= ne;   // more escapes than the sub-chunk holds
+                qesc = next_out;
+                if (SYM) escapes[first + k] = next_out;
+                ++ei;
+                next_out = ei < ne ? ep[ei] : 0;
+            }
+            if (SYM) {
+                if (slot & 1) pk[slot >> 1] |= s << 16;
+                else pk[slot >> 1] = s;
+            } else {
+                if (!FAST && k >= next_lvl) enter_level((long long)(first + k));
+                OutT v;
+                if (s == MGARD_ESC) v = dequant_escape<OutT>(qesc, (OutT)cwf, cws, cw);
+                else if (sizeof(OutT) == 4) v = (OutT)__fmul_rn((float)((int)s - RADIUS), cwf);
+                else v = (OutT)((double)((int)s - RADIUS) * cw);
+                vk[slot] = v;
+            }
+        };
+        for (int k0 = 0; k0 < cnt; k0 += 8) {
+            const bool whole = k0 + 8 <= cnt;
+            if (whole && (SYM || k0 + 8 <= next_lvl)) {
+#pragma unroll
+                for (int slot = 0; slot < 8; ++slot) decode_one(std::true_type{}, k0, slot);
+            } else {
+#pragma unroll
+                for (int slot = 0; slot < 8; ++slot) decode_one(std::false_type{}, k0, slot);
             }
             if (!whole) continue;
             if (SYM) *reinterpret_cast<uint4*>(sym + first + k0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -977,7 +1020,7 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
         // the codes must end inside the sub-chunk's bit range (exactly at its
         // end unless padding follows) and use exactly its escapes
         const uint64_t span = endbit - bstart;
-        if (used > span || (sc + 1 < NSUB && used != span) || e != e_end) ok = false;
+        if (used > span || (sc + 1 < NSUB && used != span) || ei != ne) ok = false;
     }
     if (!ok) atomicOr(status, ST_CORRUPT);
 }

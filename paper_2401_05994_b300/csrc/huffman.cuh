@@ -17,7 +17,9 @@ constexpr int SUBREC = 2 * (NSUB - 1);   // uint16 offsets recorded per chunk
 
 struct DecodeTables {
     // 14-bit prefix -> (length << 12) | symbol for codes of at most 14 bits;
-    // 0 when the code under the prefix is longer (or no code has the prefix)
+    // (15 << 12) | L when every code under the prefix is longer and all have
+    // the same length L; 0 otherwise (longer codes of several lengths, or no
+    // code has the prefix)
     uint16_t lut[1 << LUT_BITS];
     unsigned long long lim[LMAX + 2];   // lim[l]: first code of length l+1, left-justified in 32 bits
     uint32_t first_code[LMAX + 2];
