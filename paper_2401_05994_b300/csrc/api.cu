@@ -8,6 +8,7 @@
 //   compress:   [norm] -> decompose -> widths -> quantize+histogram ->
 //               codebook -> count/scan -> pack -> header
 //   decompress: header checks -> tables -> decode -> dequantize -> recompose
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -180,19 +181,29 @@ mgard_status read_header(const void* in, size_t in_bytes, bool in_dev, mgard_hea
         set_error("compressed buffer too small");
         return MGARD_ECORRUPT;
     }
+    // a device buffer's header and widths (which follow it) come over in
+    // one copy and one synchronization
+    constexpr size_t HEAD = 768;   // header + widths of up to 64 levels
+    static_assert(sizeof(mgard_header) <= HEAD, "the header fits the first copy");
+    alignas(16) char head[HEAD];
+    const size_t got = std::min(in_bytes, HEAD);
     if (in_dev) {
-        MGB_CUDA(cudaMemcpyAsync(h, in, sizeof(*h), cudaMemcpyDeviceToHost, st));
+        MGB_CUDA(cudaMemcpyAsync(head, in, got, cudaMemcpyDeviceToHost, st));
         MGB_CUDA(cudaStreamSynchronize(st));
     } else {
-        std::memcpy(h, in, sizeof(*h));
+        std::memcpy(head, in, got);
     }
+    std::memcpy(h, head, sizeof(*h));
     MGB_TRY(check_header(*h, in_bytes));
     widths->resize(h->nlevels + 1);
-    if (in_dev)
-        MGB_CUDA(cudaMemcpy(widths->data(), (const char*)in + h->off_widths, 8 * (h->nlevels + 1),
+    const size_t wbytes = 8 * (size_t)(h->nlevels + 1);
+    if (h->off_widths + wbytes <= got)
+        std::memcpy(widths->data(), head + h->off_widths, wbytes);
+    else if (in_dev)
+        MGB_CUDA(cudaMemcpy(widths->data(), (const char*)in + h->off_widths, wbytes,
                             cudaMemcpyDeviceToHost));
     else
-        std::memcpy(widths->data(), (const char*)in + h->off_widths, 8 * (h->nlevels + 1));
+        std::memcpy(widths->data(), (const char*)in + h->off_widths, wbytes);
     if (!widths_valid(widths->data(), (int)h->nlevels)) {
         set_error("corrupt header: bin width");
         return MGARD_ECORRUPT;

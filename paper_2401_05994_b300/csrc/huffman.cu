@@ -702,81 +702,88 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) k_pack(
         uint32_t carry = 0;            // the partial word the round starts in
         int64_t pend_at = -1;          // escape values are stored one escape late
         int32_t pend_v = 0;
+        // a full chunk (every lane has 8 symbols in every round) runs
+        // without the per-symbol count tests
+        auto rounds = [&](auto full_tag) {
+            constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-        for (int rd = 0; rd < NSUB; ++rd) {
-            for (int k = lane; k < PACK_WB; k += 32) wb[k] = k == 0 ? carry : 0u;
-            __syncwarp();
-            if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
-                sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
-                sub_off[c * SUBREC + (NSUB - 1) + rd - 1] = (uint16_t)esc0;
-            }
-            const int first = rd * SUB + lane * 8;
-            const int cnt = max(0, min(8, ccnt - first));
-            unsigned sv[8];
-            {
-                const uint4 v = raw[rd];
-                sv[0] = v.x & 0xFFFF; sv[1] = v.x >> 16; sv[2] = v.y & 0xFFFF; sv[3] = v.y >> 16;
-                sv[4] = v.z & 0xFFFF; sv[5] = v.z >> 16; sv[6] = v.w & 0xFFFF; sv[7] = v.w >> 16;
-            }
-            unsigned bits = 0, esc = 0, ln[8];   // code lengths, looked up once
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                ln[k] = k < cnt ? len_s[sv[k]] : 0u;
-                bits += ln[k];
-                if (k < cnt) esc += sv[k] == MGARD_ESC;
-            }
-            unsigned ib = bits, ie = esc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned vb = __shfl_up_sync(0xffffffffu, ib, o);
-                const unsigned ve = __shfl_up_sync(0xffffffffu, ie, o);
-                if (lane >= o) {
-                    ib += vb;
-                    ie += ve;
+            for (int rd = 0; rd < NSUB; ++rd) {
+                for (int k = lane; k < PACK_WB; k += 32) wb[k] = k == 0 ? carry : 0u;
+                __syncwarp();
+                if (rd > 0 && lane == 0) {   // where sub-chunk rd starts inside the chunk
+                    sub_off[c * SUBREC + rd - 1] = (uint16_t)bit0;
+                    sub_off[c * SUBREC + (NSUB - 1) + rd - 1] = (uint16_t)esc0;
                 }
-            }
-            const unsigned base = bit0 >> 5;   // the round's first word in the chunk
-            const unsigned bpos = bit0 + ib - bits;
-            unsigned epos = esc0 + ie - esc;
-            const unsigned rtot = __shfl_sync(0xffffffffu, ie, 31);   // escapes of the round
-            if (COMPACT)
-                for (unsigned k = lane; k < rtot; k += 32)
-                    outliers[eo + esc0 + k] = escapes[cbase + rd * SUB + k];
-            bit0 += __shfl_sync(0xffffffffu, ib, 31);
-            esc0 += rtot;
-            unsigned w = (bpos >> 5) - base;
-            int nb = (int)(bpos & 31);
-            unsigned long long acc = 0;
-            bool firstw = true;
+                const int first = rd * SUB + lane * 8;
+                const int cnt = FULL ? 8 : max(0, min(8, ccnt - first));
+                unsigned sv[8];
+                {
+                    const uint4 v = raw[rd];
+                    sv[0] = v.x & 0xFFFF; sv[1] = v.x >> 16; sv[2] = v.y & 0xFFFF; sv[3] = v.y >> 16;
+                    sv[4] = v.z & 0xFFFF; sv[5] = v.z >> 16; sv[6] = v.w & 0xFFFF; sv[7] = v.w >> 16;
+                }
+                unsigned bits = 0, esc = 0, ln[8];   // code lengths, looked up once
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (k < cnt) {
-                    const unsigned s = sv[k], len = ln[k];
-                    acc = (acc << len) | code_s[s];
-                    nb += (int)len;
-                    if (nb >= 32) {
-                        const uint32_t word = (uint32_t)(acc >> (nb - 32));
-                        if (firstw) atomicOr(&wb[w], word);
-                        else wb[w] = word;
-                        firstw = false;
-                        ++w;
-                        nb -= 32;
-                        acc &= (nb ? ((1ull << nb) - 1) : 0ull);
-                    }
-                    if (!COMPACT && s == MGARD_ESC) {
-                        if (pend_at >= 0) outliers[pend_at] = pend_v;
-                        pend_at = (int64_t)(eo + epos++);
-                        pend_v = escapes[cbase + first + k];
+                for (int k = 0; k < 8; ++k) {
+                    ln[k] = k < cnt ? len_s[sv[k]] : 0u;
+                    bits += ln[k];
+                    if (k < cnt) esc += sv[k] == MGARD_ESC;
+                }
+                unsigned ib = bits, ie = esc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned vb = __shfl_up_sync(0xffffffffu, ib, o);
+                    const unsigned ve = __shfl_up_sync(0xffffffffu, ie, o);
+                    if (lane >= o) {
+                        ib += vb;
+                        ie += ve;
                     }
                 }
-            if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
-            __syncwarp();
-            // the round's complete words; the word holding its end carries over
-            const unsigned nfull = (bit0 >> 5) - base;
-            for (unsigned k = lane; k < nfull; k += 32) words[wo + base + k] = wb[k];
-            carry = wb[nfull];
-            __syncwarp();
-        }
+                const unsigned base = bit0 >> 5;   // the round's first word in the chunk
+                const unsigned bpos = bit0 + ib - bits;
+                unsigned epos = esc0 + ie - esc;
+                const unsigned rtot = __shfl_sync(0xffffffffu, ie, 31);   // escapes of the round
+                if (COMPACT)
+                    for (unsigned k = lane; k < rtot; k += 32)
+                        outliers[eo + esc0 + k] = escapes[cbase + rd * SUB + k];
+                bit0 += __shfl_sync(0xffffffffu, ib, 31);
+                esc0 += rtot;
+                unsigned w = (bpos >> 5) - base;
+                int nb = (int)(bpos & 31);
+                unsigned long long acc = 0;
+                bool firstw = true;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k < cnt) {
+                        const unsigned s = sv[k], len = ln[k];
+                        acc = (acc << len) | code_s[s];
+                        nb += (int)len;
+                        if (nb >= 32) {
+                            const uint32_t word = (uint32_t)(acc >> (nb - 32));
+                            if (firstw) atomicOr(&wb[w], word);
+                            else wb[w] = word;
+                            firstw = false;
+                            ++w;
+                            nb -= 32;
+                            acc &= (nb ? ((1ull << nb) - 1) : 0ull);
+                        }
+                        if (!COMPACT && s == MGARD_ESC) {
+                            if (pend_at >= 0) outliers[pend_at] = pend_v;
+                            pend_at = (int64_t)(eo + epos++);
+                            pend_v = escapes[cbase + first + k];
+                        }
+                    }
+                if (nb > 0) atomicOr(&wb[w], (uint32_t)(acc << (32 - nb)));
+                __syncwarp();
+                // the round's complete words; the word holding its end carries over
+                const unsigned nfull = (bit0 >> 5) - base;
+                for (unsigned k = lane; k < nfull; k += 32) words[wo + base + k] = wb[k];
+                carry = wb[nfull];
+                __syncwarp();
+            }
+        };
+        if (ccnt == CHUNK) rounds(std::true_type{});
+        else rounds(std::false_type{});
         if ((bit0 & 31) && lane == 0) words[wo + (bit0 >> 5)] = carry;
         if (!COMPACT && pend_at >= 0) outliers[pend_at] = pend_v;
         __syncwarp();

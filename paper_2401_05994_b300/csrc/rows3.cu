@@ -6,6 +6,8 @@
 // decomposition differs.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "rows3.cuh"
 
 namespace mgb {
@@ -271,35 +273,43 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         if (PAIR) {
             for (int p0 = lane; p0 < ncx; p0 += 32 * U) {
                 const bool tail = absorbs_tail(p0 - lane, ncx, U);
-                T u0[U + 1], u1[U + 1];
+                // FULL: U pairs per lane, every one with its new node inside
+                // the row and no tail, so no element is tested
+                auto pass = [&](auto full_tag) {
+                    constexpr bool FULL = decltype(full_tag)::value;
+                    constexpr int NJ = FULL ? U : U + 1;
+                    T u0[U + 1], u1[U + 1];
 #pragma unroll
-                for (int j = 0; j < U + 1; ++j) {   // loads first
-                    const int p = p0 + 32 * j;
-                    if (p >= ncx || (j == U && !tail)) continue;
-                    u0[j] = urow[2 * p];
-                    if (p + 1 < ncx) u1[j] = urow[2 * p + 1];
-                }
+                    for (int j = 0; j < NJ; ++j) {   // loads first
+                        const int p = p0 + 32 * j;
+                        if (!FULL && (p >= ncx || (j == U && !tail))) continue;
+                        u0[j] = urow[2 * p];
+                        if (FULL || p + 1 < ncx) u1[j] = urow[2 * p + 1];
+                    }
 #pragma unroll
-                for (int j = 0; j < U + 1; ++j) {
-                    const int p = p0 + 32 * j;
-                    if (p >= ncx || (j == U && !tail)) continue;
-                    const T r0 = R[p];
-                    // coarse x = 2p: the interpolant is R[p] itself
-                    const T a0 = lerp_x(T(1), r0, T(0), r0);
-                    if (rowc) {
-                        crow[p] = u0[j];
-                        if (RX) Z[2 * p] = T(0);
-                    } else {
-                        const T c = u0[j] - a0;
-                        orow[2 * p] = c;
-                        if (RX) Z[2 * p] = c;
+                    for (int j = 0; j < NJ; ++j) {
+                        const int p = p0 + 32 * j;
+                        if (!FULL && (p >= ncx || (j == U && !tail))) continue;
+                        const T r0 = R[p];
+                        // coarse x = 2p: the interpolant is R[p] itself
+                        const T a0 = lerp_x(T(1), r0, T(0), r0);
+                        if (rowc) {
+                            crow[p] = u0[j];
+                            if (RX) Z[2 * p] = T(0);
+                        } else {
+                            const T c = u0[j] - a0;
+                            orow[2 * p] = c;
+                            if (RX) Z[2 * p] = c;
+                        }
+                        if (FULL || p + 1 < ncx) {   // new x = 2p + 1 between coarse p and p + 1
+                            const T c = u1[j] - lerp_x(T(0.5), r0, T(0.5), R[p + 1]);
+                            orow[(ZS && rowc) ? p : 2 * p + 1] = c;
+                            if (RX) Z[2 * p + 1] = c;
+                        }
                     }
-                    if (p + 1 < ncx) {   // new x = 2p + 1 between coarse p and p + 1
-                        const T c = u1[j] - lerp_x(T(0.5), r0, T(0.5), R[p + 1]);
-                        orow[(ZS && rowc) ? p : 2 * p + 1] = c;
-                        if (RX) Z[2 * p + 1] = c;
-                    }
-                }
+                };
+                if (!tail && p0 - lane + 32 * U < ncx) pass(std::true_type{});
+                else pass(std::false_type{});
                 if (tail) break;
             }
         } else
@@ -398,24 +408,31 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         if (PAIR) {   // lane p: coarse x = 2p and new x = 2p + 1 (see k3_coeff)
             for (int p0 = lane; p0 < ncx; p0 += 32 * U) {
                 const bool tail = absorbs_tail(p0 - lane, ncx, U);
-                T z0[U + 1], z1[U + 1];
+                // FULL: as in k3_coeff, no element is tested
+                auto pass = [&](auto full_tag) {
+                    constexpr bool FULL = decltype(full_tag)::value;
+                    constexpr int NJ = FULL ? U : U + 1;
+                    T z0[U + 1], z1[U + 1];
 #pragma unroll
-                for (int j = 0; j < U + 1; ++j) {   // loads first
-                    const int p = p0 + 32 * j;
-                    if (p >= ncx || (j == U && !tail)) continue;
-                    if (!rowc) z0[j] = zrow[2 * p];
-                    if (p + 1 < ncx) z1[j] = zrow[(ZS && rowc) ? p : 2 * p + 1];
-                }
+                    for (int j = 0; j < NJ; ++j) {   // loads first
+                        const int p = p0 + 32 * j;
+                        if (!FULL && (p >= ncx || (j == U && !tail))) continue;
+                        if (!rowc) z0[j] = zrow[2 * p];
+                        if (FULL || p + 1 < ncx) z1[j] = zrow[(ZS && rowc) ? p : 2 * p + 1];
+                    }
 #pragma unroll
-                for (int j = 0; j < U + 1; ++j) {
-                    const int p = p0 + 32 * j;
-                    if (p >= ncx || (j == U && !tail)) continue;
-                    const T r0 = R[p];
-                    T v0 = lerp_x(T(1), r0, T(0), r0);
-                    if (!rowc) v0 += z0[j];   // z vanishes on coarse nodes of the coarse grid's rows
-                    orow[2 * p] = v0;
-                    if (p + 1 < ncx) orow[2 * p + 1] = lerp_x(T(0.5), r0, T(0.5), R[p + 1]) + z1[j];
-                }
+                    for (int j = 0; j < NJ; ++j) {
+                        const int p = p0 + 32 * j;
+                        if (!FULL && (p >= ncx || (j == U && !tail))) continue;
+                        const T r0 = R[p];
+                        T v0 = lerp_x(T(1), r0, T(0), r0);
+                        if (!rowc) v0 += z0[j];   // z vanishes on coarse nodes of the coarse grid's rows
+                        orow[2 * p] = v0;
+                        if (FULL || p + 1 < ncx) orow[2 * p + 1] = lerp_x(T(0.5), r0, T(0.5), R[p + 1]) + z1[j];
+                    }
+                };
+                if (!tail && p0 - lane + 32 * U < ncx) pass(std::true_type{});
+                else pass(std::false_type{});
                 if (tail) break;
             }
         } else
@@ -475,6 +492,38 @@ __global__ void __launch_bounds__(RT) k3_restrict_x(const Tin* __restrict__ in,
         const int sh = (ZS && rowc) ? 1 : 0;
         for (int J0 = lane; J0 < ncx; J0 += 32 * U) {
             const bool tail = absorbs_tail(J0 - lane, ncx, U);
+            const int base = J0 - lane;
+            if (!tail && base >= rlo && base + 32 * U <= rhi) {
+                // every J of the pass takes the uniform window: no tests
+                Tout acc[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int J = J0 + 32 * j;
+                    if (sh) {   // coarse row in symbol order: only the odd taps
+                        Tout a = wi[0] * Tout(0);
+                        a += wi[1] * (Tout)irow[J - 1];
+                        a += wi[2] * Tout(0);
+                        a += wi[3] * (Tout)irow[J];
+                        a += wi[4] * Tout(0);
+                        acc[j] = a;
+                    } else {
+                        const Tout e0 = rowc ? Tout(0) : (Tout)irow[2 * J - 2];
+                        const Tout e1 = (Tout)irow[2 * J - 1];
+                        const Tout e2 = rowc ? Tout(0) : (Tout)irow[2 * J];
+                        const Tout e3 = (Tout)irow[2 * J + 1];
+                        const Tout e4 = rowc ? Tout(0) : (Tout)irow[2 * J + 2];
+                        Tout a = wi[0] * e0;
+                        a += wi[1] * e1;
+                        a += wi[2] * e2;
+                        a += wi[3] * e3;
+                        a += wi[4] * e4;
+                        acc[j] = a;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) orow[J0 + 32 * j] = acc[j];
+                continue;
+            }
             Tout acc[U + 1];
 #pragma unroll
             for (int j = 0; j < U + 1; ++j) {
