@@ -54,6 +54,7 @@ struct Lanes {
     cudaStream_t side[BATCH_STREAMS] = {};
     cudaStream_t origin = nullptr;
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    cudaEvent_t aux_ev[3] = {};   // fork, mid, join of a field's second stream (AuxLane)
     cudaGraphExec_t exec = nullptr;
     int runs = 0;   // calls served so far
 
@@ -63,8 +64,18 @@ struct Lanes {
             MGB_CUDA(cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming));
         }
         MGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (int k = 0; k < 3; ++k) MGB_CUDA(cudaEventCreateWithFlags(&aux_ev[k], cudaEventDisableTiming));
         MGB_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
         return MGARD_OK;
+    }
+    // A one-field run uses side[0] only: side[1] is the field's second stream.
+    AuxLane aux() const {
+        AuxLane a;
+        a.stream = side[1];
+        a.fork = aux_ev[0];
+        a.mid = aux_ev[1];
+        a.join = aux_ev[2];
+        return a;
     }
     void destroy() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -76,6 +87,10 @@ struct Lanes {
             side[k] = nullptr;
         }
         if (fork) cudaEventDestroy(fork);
+        for (int k = 0; k < 3; ++k) {
+            if (aux_ev[k]) cudaEventDestroy(aux_ev[k]);
+            aux_ev[k] = nullptr;
+        }
         if (origin) cudaStreamDestroy(origin);
         fork = nullptr;
         origin = nullptr;
@@ -210,11 +225,16 @@ struct BatchState {
     mgard_status field(int i, cudaStream_t ss) {
         char* dd = (char*)key.outs[i];
         const uint64_t cap = key.caps[i];
+        // a single field runs its small levels beside its quantization
+        const AuxLane a = lanes.aux();
+        const AuxLane* ap = key.n == 1 ? &a : nullptr;
         if (key.dtype == MGARD_F32)
             return compress_core<float>(*plans[i], (const float*)key.fields[i], heads[i], key.tol,
-                                        key.s, (mgard_tolmode)key.mode, dd, cap, *wf[i], metas + i, ss);
+                                        key.s, (mgard_tolmode)key.mode, dd, cap, *wf[i], metas + i, ss,
+                                        nullptr, ap);
         return compress_core<double>(*plans[i], (const double*)key.fields[i], heads[i], key.tol,
-                                     key.s, (mgard_tolmode)key.mode, dd, cap, *wd[i], metas + i, ss);
+                                     key.s, (mgard_tolmode)key.mode, dd, cap, *wd[i], metas + i, ss,
+                                     nullptr, ap);
     }
 
     // The persistent form: every field's decomposition down to its

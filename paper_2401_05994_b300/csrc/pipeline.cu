@@ -208,7 +208,7 @@ mgard_status compress_decompose(const Plan& p, const T* din, double s, mgard_tol
 template <typename T>
 mgard_status compress_encode_front(const Plan& p, const T* din, double tol, double s,
                                    mgard_tolmode mode, CompressWork<T>& w, CompressMeta* meta,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool quantize) {
     const int L = p.L;
     MGB_LAUNCH("k_meta_reset", st, k_meta_reset<<<1, 32, 0, st>>>(meta));
     MGB_CUDA(cudaMemsetAsync(w.hist.p, 0, DICT * sizeof(unsigned long long), st));
@@ -231,6 +231,7 @@ mgard_status compress_encode_front(const Plan& p, const T* din, double tol, doub
     double* widths = w.wdev.template as<double>();
     MGB_LAUNCH("k_widths", st, k_widths<<<1, 32, 0, st>>>(a, parts, parts + RED_PARTS, meta, widths));
     MGB_CUDA(cudaGetLastError());
+    if (!quantize) return MGARD_OK;
     uint16_t* sym = w.sym.template as<uint16_t>();
     int32_t* esc = w.esc.template as<int32_t>();
     if (rows3_ok(p)) {
@@ -313,7 +314,7 @@ template <typename T>
 mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
                            double s, mgard_tolmode mode, char* dd, uint64_t cap,
                            CompressWork<T>& w, CompressMeta* meta, cudaStream_t st,
-                           const RegionScale* rs) {
+                           const RegionScale* rs, const AuxLane* aux) {
     const uint64_t N = (uint64_t)p.total();
     const Sections fx = layout(p.L, (N + CHUNK - 1) / CHUNK, 0, 0);
     if (cap < fx.outliers || ((uintptr_t)dd & 15) != 0) {
@@ -321,7 +322,41 @@ mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, 
         return MGARD_EINVAL;
     }
     MGB_CUDA(cudaMemsetAsync(dd, 0, fx.outliers, st));   // fixed sections, gaps included
-    MGB_TRY(compress_decompose<T>(p, din, s, mode, w, meta, st));
+    // the tail beside the larger levels' quantization: the decomposition
+    // stops before the tail (it does so only where no level energies are
+    // needed: tail_pending says whether it did)
+    const int Lt = rows3_ok(p) ? tail_levels(p) : 0;
+    const bool beside = aux && aux->stream && !rs && Lt >= 1 && Lt < p.L;
+    w.py.defer_tail = beside;
+    const mgard_status dr = compress_decompose<T>(p, din, s, mode, w, meta, st);
+    w.py.defer_tail = false;
+    MGB_TRY(dr);
+    if (w.py.tail_pending) {
+        T* top = w.top.template as<T>();
+        uint16_t* sym = w.sym.template as<uint16_t>();
+        int32_t* esc = w.esc.template as<int32_t>();
+        unsigned long long* hist = w.hist.template as<unsigned long long>();
+        const double* widths = w.wdev.template as<double>();
+        // symbols [0, S) hold the tail's levels (and the start of the next
+        // level, already final); S on a sub-chunk boundary
+        const int64_t S = std::min<int64_t>((int64_t)N, (p.offset[Lt + 1] + SUB - 1) / SUB * SUB);
+        MGB_CUDA(cudaEventRecord(aux->fork, st));
+        MGB_CUDA(cudaStreamWaitEvent(aux->stream, aux->fork, 0));
+        MGB_TRY(tail_decompose<T>(p, Lt, w.py, w.py.lv[Lt], top, top, aux->stream));
+        MGB_TRY(decompose_finish<T>(p, w.py, top, aux->stream));
+        MGB_TRY(compress_encode_front<T>(p, din, tol, s, mode, w, meta, st, false));   // widths
+        MGB_CUDA(cudaEventRecord(aux->mid, st));
+        MGB_TRY(quantize_stream<T>(p, top, widths, sym, esc, hist, &meta->status, st, S, -1, true));
+        MGB_CUDA(cudaStreamWaitEvent(aux->stream, aux->mid, 0));
+        MGB_TRY(quantize_stream<T>(p, top, widths, sym, esc, hist, &meta->status, aux->stream, 0, S));
+        MGB_CUDA(cudaEventRecord(aux->join, aux->stream));
+        MGB_CUDA(cudaStreamWaitEvent(st, aux->join, 0));
+        const CodebookJob j = codebook_job<T>(p, w);
+        MGB_TRY(huffman_codebook(j.hist, j.lengths, nullptr, st, j.wide != 0));
+        MGB_TRY(huffman_tables(j.lengths, j.codes, nullptr, st));
+        MGB_TRY(compress_encode_back<T>(p, h0, dd, cap, w, meta, st));
+        return compress_pack<T>(p, dd, w, meta, st);
+    }
     if (rs) {   // region-adaptive widths: coefficients scaled by 2^k of their node
         if (p.L < 1) {
             set_error("regions need at least one level");
@@ -449,7 +484,7 @@ template struct CompressWork<double>;
                                            cudaStream_t);                                         \
     template mgard_status compress_encode_front<T>(const Plan&, const T*, double, double,         \
                                                    mgard_tolmode, CompressWork<T>&, CompressMeta*, \
-                                                   cudaStream_t);                                 \
+                                                   cudaStream_t, bool);                           \
     template CodebookJob codebook_job<T>(const Plan&, CompressWork<T>&);                          \
     template mgard_status compress_encode_back<T>(const Plan&, const mgard_header&, char*,        \
                                                   uint64_t, CompressWork<T>&, CompressMeta*,      \
@@ -460,7 +495,7 @@ INST_PHASES(double)
 template mgard_status compress_core<float>(const Plan&, const float*, const mgard_header&, double,
                                            double, mgard_tolmode, char*, uint64_t,
                                            CompressWork<float>&, CompressMeta*, cudaStream_t,
-                                           const RegionScale*);
+                                           const RegionScale*, const AuxLane*);
 template struct DecompressWork<float>;
 template struct DecompressWork<double>;
 template mgard_status decompress_core<float>(const Plan&, const mgard_header&, const double*,
@@ -472,6 +507,6 @@ template mgard_status decompress_core<double>(const Plan&, const mgard_header&, 
 template mgard_status compress_core<double>(const Plan&, const double*, const mgard_header&, double,
                                             double, mgard_tolmode, char*, uint64_t,
                                             CompressWork<double>&, CompressMeta*, cudaStream_t,
-                                            const RegionScale*);
+                                            const RegionScale*, const AuxLane*);
 
 }  // namespace mgb

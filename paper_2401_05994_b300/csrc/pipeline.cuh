@@ -52,11 +52,21 @@ mgard_header header_template(const Plan& p, mgard_dtype dtype, int ndim, const i
 // the payload is not written.
 // With `rs`, region-adaptive widths (quantize.cuh): the coefficients are
 // scaled by 2^k of their node between decomposition and quantization.
+// A second stream beside the caller's and the events that fork work onto
+// it and join it back.  With one, compression runs the small levels'
+// one-block tail beside the larger levels' quantization instead of before
+// it; graph capture records the fork and the join as edges.  Null:
+// everything on the caller's stream.
+struct AuxLane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, mid = nullptr, join = nullptr;
+};
+
 template <typename T>
 mgard_status compress_core(const Plan& p, const T* din, const mgard_header& h0, double tol,
                            double s, mgard_tolmode mode, char* dd, uint64_t cap,
                            CompressWork<T>& w, CompressMeta* meta, cudaStream_t st,
-                           const RegionScale* rs = nullptr);
+                           const RegionScale* rs = nullptr, const AuxLane* aux = nullptr);
 
 // Map device status bits (ST_*) to an mgard_status with its message.
 mgard_status status_to_error(unsigned st);
@@ -111,10 +121,11 @@ mgard_status compress_pack(const Plan& p, char* dd, CompressWork<T>& w, Compress
 // all fields in one launch (huffman_codebook_tables_batch on the jobs of
 // codebook_job): front = widths and quantization, back = count pass and
 // header.  front, the codebook and tables, then back equal compress_encode.
+// With quantize false, front stops after the widths.
 template <typename T>
 mgard_status compress_encode_front(const Plan& p, const T* din, double tol, double s,
                                    mgard_tolmode mode, CompressWork<T>& w, CompressMeta* meta,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool quantize = true);
 template <typename T>
 CodebookJob codebook_job(const Plan& p, CompressWork<T>& w);
 template <typename T>

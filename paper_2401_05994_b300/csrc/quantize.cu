@@ -232,7 +232,7 @@ template <typename T>
 __global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize_stream(
     const T* __restrict__ zs, int64_t n, LevelOffsets lo, const double* __restrict__ wdev,
     uint16_t* __restrict__ sym, int32_t* __restrict__ esc, unsigned long long* __restrict__ hist,
-    unsigned* status) {
+    unsigned* status, int64_t g_begin) {
     __shared__ unsigned sh[2][DICT];
     __shared__ double ws[MAX_LEVELS + 1];
     __shared__ T iws[MAX_LEVELS + 1];
@@ -280,9 +280,9 @@ __global__ void __launch_bounds__(QS_THREADS, sizeof(T) == 4 ? 4 : 3) k_quantize
     int lcur = 0;
     // the next group's values are loaded while this group is quantized
     T nxt[8];
-    load8((blockIdx.x * (int64_t)QS_THREADS + threadIdx.x) * 8, nxt);
+    load8((g_begin + blockIdx.x * (int64_t)QS_THREADS + threadIdx.x) * 8, nxt);
     // block-uniform trip count (the escape scan needs whole warps)
-    for (int64_t gb = blockIdx.x * (int64_t)QS_THREADS; gb * 8 < n; gb += stride) {
+    for (int64_t gb = g_begin + blockIdx.x * (int64_t)QS_THREADS; gb * 8 < n; gb += stride) {
         const int64_t g = gb + threadIdx.x;
         const int64_t i0 = g * 8;
         T v[8];
@@ -464,23 +464,39 @@ LevelOffsets level_offsets(const Plan& p) {
 template <typename T>
 mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16_t* sym,
                              int32_t* esc, unsigned long long* hist, unsigned* status,
-                             cudaStream_t st) {
-    const int64_t n = p.total();
+                             cudaStream_t st, int64_t i_begin, int64_t i_end, bool spare_sm) {
+    const int64_t n = i_end < 0 ? p.total() : std::min<int64_t>(i_end, p.total());
     if (p.L > MAX_LEVELS) {
         set_error("too many levels");
         return MGARD_ESHAPE;
     }
+    if (i_begin % QS_SUB != 0 || i_begin < 0) {
+        set_error("quantize_stream: range must start on a sub-chunk");
+        return MGARD_EINVAL;
+    }
+    if (i_begin >= n) return MGARD_OK;
+    const int64_t groups = (n - i_begin + 8 * QS_THREADS - 1) / (8 * QS_THREADS);
     int grid = 0;
-    MGB_TRY(resident_grid((const void*)k_quantize_stream<T>, QS_THREADS, 0, (n + 8 * QS_THREADS - 1) / (8 * QS_THREADS), &grid));
+    MGB_TRY(resident_grid((const void*)k_quantize_stream<T>, QS_THREADS, 0, groups, &grid));
+    if (spare_sm) {
+        int per_sm = 0, sms = 0, dev = 0;
+        MGB_CUDA(cudaGetDevice(&dev));
+        MGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quantize_stream<T>, QS_THREADS, 0));
+        grid = std::max(1, std::min(grid, (sms - 1) * std::max(per_sm, 1)));
+    }
     MGB_LAUNCH("k_quantize_stream", st, k_quantize_stream<T><<<grid, QS_THREADS, 0, st>>>(
-                                            zs, n, level_offsets(p), w, sym, esc, hist, status));
+                                            zs, n, level_offsets(p), w, sym, esc, hist, status,
+                                            i_begin / 8));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
 template mgard_status quantize_stream<float>(const Plan&, const float*, const double*, uint16_t*,
-                                             int32_t*, unsigned long long*, unsigned*, cudaStream_t);
+                                             int32_t*, unsigned long long*, unsigned*, cudaStream_t,
+                                             int64_t, int64_t, bool);
 template mgard_status quantize_stream<double>(const Plan&, const double*, const double*, uint16_t*,
-                                              int32_t*, unsigned long long*, unsigned*, cudaStream_t);
+                                              int32_t*, unsigned long long*, unsigned*, cudaStream_t,
+                                              int64_t, int64_t, bool);
 
 int64_t feature_blocks(const Plan& p, int l) {
     if (rows3_ok(p)) return range_feature_blocks(p.count[l]);

@@ -28,10 +28,15 @@ mgard_status dequantize_level(const Plan& p, int l, const uint16_t* sym, const i
 // compacted per Huffman sub-chunk: the r-th escape of sub-chunk s at
 // esc[s * (MGARD_CHUNK / MGARD_NSUB) + r] (huffman_pack's `compact` layout).
 LevelOffsets level_offsets(const Plan& p);
+// With i_begin / i_end (i_begin a multiple of the sub-chunk size, 256), only
+// symbols [i_begin, i_end) are quantized (the histogram accumulates); with
+// spare_sm the grid leaves one SM's worth of blocks free for a kernel
+// running beside it.
 template <typename T>
 mgard_status quantize_stream(const Plan& p, const T* zs, const double* w, uint16_t* sym,
                              int32_t* esc, unsigned long long* hist, unsigned* status,
-                             cudaStream_t st);
+                             cudaStream_t st, int64_t i_begin = 0, int64_t i_end = -1,
+                             bool spare_sm = false);
 
 // Statistics of the level-l coefficients (the features of the tolerance
 // predictor): feature_blocks(p, l) FeatPart records, reduced in a fixed
