@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
     const uint16_t* __restrict__ sub_off, const DecodeTables* __restrict__ gdt, uint64_t n,
     const int32_t* __restrict__ outliers, uint64_t noutliers, const uint64_t* __restrict__ esc_off,
     uint16_t* __restrict__ sym, int32_t* __restrict__ escapes, OutT* __restrict__ vals,
-    DeqArgs dq, unsigned* status, uint64_t nchunks) {
+    DeqArgs dq, unsigned* status, uint64_t nchunks, unsigned long long* grab) {
     constexpr bool SYM = sizeof(OutT) == 2;
     __shared__ __align__(16) uint16_t lut[1 << LUT_BITS];
     __shared__ unsigned long long lim[LMAX + 2];
@@ -857,8 +857,21 @@ __global__ void __launch_bounds__(DEC_THREADS, 2) k_decode(
     const uint16_t* sorted = ssorted;
     bool ok = true;
     const uint64_t nsub = nchunks * NSUB;
-    for (uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gid < nsub;
-         gid += (uint64_t)gridDim.x * blockDim.x) {
+    // sub-chunks in runs of 32, one per warp: taken from a device counter
+    // when one is given (a warp that finishes early takes the next run, so
+    // no block waits on a slow one), else in grid order
+    const int wl = threadIdx.x & 31;
+    const uint64_t wstep = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t wbase = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u);
+    auto next_run = [&](uint64_t b) -> uint64_t {
+        if (!grab) return b;
+        unsigned long long r = 0;
+        if (wl == 0) r = atomicAdd(grab, 32ull);
+        return __shfl_sync(0xffffffffu, r, 0);
+    };
+    for (wbase = next_run(wbase); wbase < nsub; wbase = next_run(wbase + wstep)) {
+        const uint64_t gid = wbase + wl;
+        if (gid >= nsub) continue;
         const uint64_t c = gid / NSUB;
         const int sc = (int)(gid % NSUB);
         const uint64_t first = c * CHUNK + (uint64_t)sc * SUB;
@@ -1163,7 +1176,7 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
     DeqArgs dq;
     std::memset(&dq, 0, sizeof(dq));
     MGB_LAUNCH("k_decode", st, k_decode<uint16_t><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
-                                          esc_off, sym, escapes, nullptr, dq, status, nchunks));
+                                          esc_off, sym, escapes, nullptr, dq, status, nchunks, nullptr));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
@@ -1173,24 +1186,27 @@ mgard_status huffman_decode_values(const uint32_t* words, uint64_t nwords, const
                                    const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
                                    const int32_t* outliers, uint64_t noutliers,
                                    const uint64_t* esc_off, const DeqArgs& dq, T* vals,
-                                   unsigned* status, cudaStream_t st) {
+                                   unsigned* status, cudaStream_t st, unsigned long long* grab) {
     const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
     if (!nchunks) return MGARD_OK;
     const int grid = grid_for((int64_t)(nchunks * NSUB), DEC_THREADS, 148LL * DEC_BLOCKS_PER_SM);
     MGB_TRY(huffman_prepare());
+    if (grab) MGB_CUDA(cudaMemsetAsync(grab, 0, sizeof(*grab), st));
     MGB_LAUNCH("k_decode", st, k_decode<T><<<grid, DEC_THREADS, 0, st>>>(words, nwords, word_off, sub_off, dt, n, outliers, noutliers,
-                                          esc_off, nullptr, nullptr, vals, dq, status, nchunks));
+                                          esc_off, nullptr, nullptr, vals, dq, status, nchunks, grab));
     MGB_CUDA(cudaGetLastError());
     return MGARD_OK;
 }
 template mgard_status huffman_decode_values<float>(const uint32_t*, uint64_t, const uint64_t*,
                                                    const uint16_t*, const DecodeTables*, uint64_t,
                                                    const int32_t*, uint64_t, const uint64_t*,
-                                                   const DeqArgs&, float*, unsigned*, cudaStream_t);
+                                                   const DeqArgs&, float*, unsigned*, cudaStream_t,
+                                                   unsigned long long*);
 template mgard_status huffman_decode_values<double>(const uint32_t*, uint64_t, const uint64_t*,
                                                     const uint16_t*, const DecodeTables*, uint64_t,
                                                     const int32_t*, uint64_t, const uint64_t*,
-                                                    const DeqArgs&, double*, unsigned*, cudaStream_t);
+                                                    const DeqArgs&, double*, unsigned*, cudaStream_t,
+                                                    unsigned long long*);
 
 
 // ---------------------------------------------------------------------------

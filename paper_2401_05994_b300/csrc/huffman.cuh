@@ -96,11 +96,15 @@ mgard_status huffman_decode(const uint32_t* words, uint64_t nwords, const uint64
 
 // Decoding straight to dequantized coefficients in symbol order (vals, n
 // values), as the dequantization of the decoded symbols would give them.
+// grab (device, 8 bytes; reset here): warps take runs of sub-chunks from
+// it, so the launch ends when the work does rather than when its slowest
+// block does; null: a fixed assignment in grid order.
 template <typename T>
 mgard_status huffman_decode_values(const uint32_t* words, uint64_t nwords, const uint64_t* word_off,
                                    const uint16_t* sub_off, const DecodeTables* dt, uint64_t n,
                                    const int32_t* outliers, uint64_t noutliers,
                                    const uint64_t* esc_off, const DeqArgs& dq, T* vals,
-                                   unsigned* status, cudaStream_t st);
+                                   unsigned* status, cudaStream_t st,
+                                   unsigned long long* grab = nullptr);
 
 }  // namespace mgb

@@ -414,6 +414,7 @@ mgard_status DecompressWork<T>::alloc(const Plan& p, cudaStream_t st) {
     MGB_TRY(py.alloc(p, st));
     MGB_TRY(codes.alloc(DICT * sizeof(uint32_t), st));
     MGB_TRY(dt.alloc(sizeof(DecodeTables), st));
+    MGB_TRY(grab.alloc(sizeof(unsigned long long), st));
     if (rows3_ok(p)) {   // decoded straight to coefficients in symbol order
         MGB_TRY(zs.alloc(N * sizeof(T), st));
     } else {
@@ -454,7 +455,8 @@ mgard_status decompress_core(const Plan& p, const mgard_header& h, const double*
         }
         T* zs = work.zs.template as<T>();
         MGB_TRY(huffman_decode_values<T>(words, h.nwords, woff, soff, dt, N, outl, h.noutliers, eoff,
-                                         dq, zs, status, st));
+                                         dq, zs, status, st,
+                                         work.grab.template as<unsigned long long>()));
         if (rs) MGB_TRY(region_scale<T>(p, *rs, zs, nullptr, -1, st));
         return recompose_pyramid<T>(p, nullptr, dout, work.py, st, zs);
     }

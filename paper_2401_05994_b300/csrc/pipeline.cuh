@@ -81,6 +81,7 @@ template <typename T>
 struct DecompressWork {
     Pyramid<T> py;
     DevBuf codes, dt, sym, esc, zs;   // zs (row-kernel shapes) or sym + esc
+    DevBuf grab;                      // the decoder's work counter
     mgard_status alloc(const Plan& p, cudaStream_t st);
 };
 
