@@ -46,11 +46,11 @@ SAMPLE = 129       # edge of the sub-cube the CPU oracle compresses per sample
 # capture of the same command (profiles/dram_traffic_513cube.md; one pass per
 # launch).  Valid for the kernel versions captured.
 NCU_TRAFFIC_513 = {
-    "k3_coeff": (672.2e6, 812.6e6, 5), "k_decode": (294.2e6, 494.1e6, 1),
-    "k_restrict_solve": (1013.9e6, 262.9e6, 20), "k3_fill": (618.3e6, 515.5e6, 5),
-    "k_pack": (319.9e6, 165.4e6, 1), "k3_restrict_x": (582.2e6, 243.5e6, 6),
-    "k_quantize_stream": (549.9e6, 258.3e6, 1), "k_solve_warp": (313.3e6, 34.1e6, 10),
-    "k_maxabs": (540.1e6, 3.3e6, 1), "k_chunk_count": (270.2e6, 1.4e6, 1),
+    "k3_coeff": (657.2e6, 807.9e6, 5), "k_decode": (294.2e6, 493.4e6, 1),
+    "k_restrict_solve": (1012.5e6, 262.2e6, 20), "k3_fill": (618.3e6, 515.6e6, 5),
+    "k_pack": (319.9e6, 165.5e6, 1), "k3_restrict_x": (583.4e6, 244.7e6, 7),
+    "k_quantize_stream": (550.7e6, 258.4e6, 2), "k_solve_warp": (313.3e6, 33.9e6, 10),
+    "k_maxabs": (540.1e6, 3.0e6, 1), "k_chunk_count": (270.2e6, 1.3e6, 1),
 }
 
 
