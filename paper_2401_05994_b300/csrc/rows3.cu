@@ -43,6 +43,10 @@ __device__ inline bool absorbs_tail(int base, int n, int U) {
     return base + 32 * U < n && base + 32 * (U + 1) >= n;
 }
 
+// Elements of T that fill a multiple of 8 bytes (per-warp shared-memory rows).
+template <typename T>
+__host__ __device__ inline int pad8(int n) { return sizeof(T) >= 8 ? n : (n + 1) & ~1; }
+
 // Rounding spelled out, so the staged and per-element forms of the
 // interpolation (below) give the same bits whatever the compiler contracts.
 __device__ inline float rmul(float a, float b) { return __fmul_rn(a, b); }
@@ -263,8 +267,11 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
         const T* urow = in + r * nx;
         T* orow = ZS ? out + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : out + r * nx;
         T* crow = rowc ? coarse + ((int64_t)sz.J * ncy + sy.J) * ncx : nullptr;
-        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ((STAGE ? ncx : 0) + (RX ? nx : 0));
-        T* Z = R + (STAGE ? ncx : 0);
+        // per-warp rows padded to 8 bytes, so the coefficient pairs go to
+        // shared memory as one access each
+        const int ncxp = pad8<T>(ncx), nxp = pad8<T>(nx);
+        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ((STAGE ? ncxp : 0) + (RX ? nxp : 0));
+        T* Z = R + (STAGE ? ncxp : 0);
         if (STAGE) {
             // coarse node J sits at fine x = 2J, the last one at nx - 1
             for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, min(2 * j, nx - 1));
@@ -293,18 +300,26 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
                         const T r0 = R[p];
                         // coarse x = 2p: the interpolant is R[p] itself
                         const T a0 = lerp_x(T(1), r0, T(0), r0);
+                        T c0 = T(0);
                         if (rowc) {
                             crow[p] = u0[j];
-                            if (RX) Z[2 * p] = T(0);
                         } else {
-                            const T c = u0[j] - a0;
-                            orow[2 * p] = c;
-                            if (RX) Z[2 * p] = c;
+                            c0 = u0[j] - a0;
+                            orow[2 * p] = c0;
                         }
                         if (FULL || p + 1 < ncx) {   // new x = 2p + 1 between coarse p and p + 1
                             const T c = u1[j] - lerp_x(T(0.5), r0, T(0.5), R[p + 1]);
                             orow[(ZS && rowc) ? p : 2 * p + 1] = c;
-                            if (RX) Z[2 * p + 1] = c;
+                            if (RX) {
+                                if (sizeof(T) == 4)
+                                    *reinterpret_cast<float2*>(Z + 2 * p) = make_float2((float)c0, (float)c);
+                                else {
+                                    Z[2 * p] = c0;
+                                    Z[2 * p + 1] = c;
+                                }
+                            }
+                        } else if (RX) {
+                            Z[2 * p] = c0;
                         }
                     }
                 };
@@ -359,9 +374,23 @@ __global__ void __launch_bounds__(RT) k3_coeff(const T* in, T* out, T* __restric
 #pragma unroll
             for (int t = 0; t < 5; ++t) wi[t] = axw.rwi[t];
             Tw* xrow = rx + r * xpitch;
-            for (int J = lane; J < ncx; J += 32)
-                xrow[J] = restrict_row_at<Tw>(J, nx, ncx, rowc, wi, axw.rlo, axw.rhi, axw.rw,
-                                              [&](int ip) { return (Tw)Z[ip]; });
+            for (int J = lane; J < ncx; J += 32) {
+                if (sizeof(T) == 4 && sizeof(Tw) == 4 && J >= axw.rlo && J < axw.rhi) {
+                    // the uniform window from two pair loads and one element (Z
+                    // holds 0 at the coarse nodes of a coarse row)
+                    const float2 a = *reinterpret_cast<const float2*>(Z + 2 * J - 2);
+                    const float2 b = *reinterpret_cast<const float2*>(Z + 2 * J);
+                    Tw acc = wi[0] * (Tw)a.x;
+                    acc += wi[1] * (Tw)a.y;
+                    acc += wi[2] * (Tw)b.x;
+                    acc += wi[3] * (Tw)b.y;
+                    acc += wi[4] * (Tw)Z[2 * J + 2];
+                    xrow[J] = acc;
+                } else {
+                    xrow[J] = restrict_row_at<Tw>(J, nx, ncx, rowc, wi, axw.rlo, axw.rhi, axw.rw,
+                                                  [&](int ip) { return (Tw)Z[ip]; });
+                }
+            }
         }
         if (STAGE || RX) __syncwarp();   // R and Z are rewritten by the warp's next row
     }
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(RT) k3_fill(const T* zin, const T* __restrict_
         else PREFETCH_NEXT_ROW(zin, r, (int64_t)nz * ny, nx, sizeof(T));
         const T* zrow = ZS ? zin + zs_row_base(zoff, r, nx, z, y, nz, ny, ncy, ncx) : zin + r * nx;
         T* orow = out + r * nx;
-        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * ncx;
+        T* R = reinterpret_cast<T*>(stage_raw) + (threadIdx.x >> 5) * pad8<T>(ncx);
         if (STAGE) {
             for (int j = lane; j < ncx; j += 32) R[j] = combine_rows(rows, rw, use, j);
             __syncwarp();
@@ -877,7 +906,7 @@ QRow make_qrow(const Plan& p, int l) {
 // or the rows do not fit the default 48 KB.
 template <typename T>
 size_t stage_bytes(const Level<T>& lv, const RowCfg& c) {
-    const size_t b = (size_t)WPB * (size_t)lv.nc[3] * sizeof(T);
+    const size_t b = (size_t)WPB * (size_t)pad8<T>((int)lv.nc[3]) * sizeof(T);
     return c.stage != 0 && b <= 48 * 1024 ? b : 0;
 }
 
@@ -899,7 +928,7 @@ mgard_status rows3_coeff(const Plan& p, int l, const T* in, T* out, T* coarse, c
     const int g = row_grid(lv.n[1] * lv.n[2], c.bpsm);
     const size_t sm = stage_bytes<T>(lv, c);
     // the fused x restriction keeps the row's coefficients beside the staged row
-    const size_t smx = sm + (size_t)WPB * (size_t)lv.n[3] * sizeof(T);
+    const size_t smx = sm + (size_t)WPB * (size_t)pad8<T>((int)lv.n[3]) * sizeof(T);
     const bool fuse = rx && sm && smx <= 48 * 1024;
     const bool pair = sm && pair_ok(lv);
     if (fused) *fused = fuse;
