@@ -191,6 +191,41 @@ def test_encode_decode_bit_exact(n):
     assert np.array_equal(de.cpu().numpy()[d == 0], esc[s == 0])
 
 
+@pytest.mark.parametrize("case", [5, 6, 11, 13])
+def test_decode_long_codes_bit_exact(case):
+    """Streams dominated by codes longer than the decoder's 14-bit prefix
+    table, whose entries give the length when every code under a prefix has
+    the same one and leave a search otherwise.  The codebooks: geometric
+    weights (75 one-length prefixes, 4 mixed), the length-limited Fibonacci
+    codes (up to 32 bits, one mixed prefix), the spread of 2^k weights (140
+    and 7) and the quantized-field shape with its tail of ones, escape
+    symbol included (6 and 2).  Symbols are drawn from the used ones, long
+    codes favoured; the library's encoder must give the oracle's stream and
+    its decoder must give back every symbol and escape value."""
+    h = _hist_cases()[case]
+    L = huffman.code_lengths(h)
+    used = np.flatnonzero(L > 0)
+    assert L.max() > 14
+    rng = np.random.default_rng(case)
+    w = 2.0 ** (L[used] - L[used].min())   # longer codes drawn more often
+    n = 50001
+    s = rng.choice(used, n, p=w / w.sum()).astype(np.uint16)
+    esc = np.zeros(n, dtype=np.int32)
+    if L[0] > 0:
+        esc[s == 0] = rng.integers(-10 ** 6, 10 ** 6, int((s == 0).sum()))
+    st = torch.from_numpy(s.astype(np.int32)).to(torch.uint16).to(DEV)
+    Ld = torch.from_numpy(L).to(DEV)
+    words, woff, eoff, sub, outl = binding.huffman_encode(st, Ld, torch.from_numpy(esc).to(DEV))
+    rw, rwo, reo, rsub = huffman.encode(s, L, fill_symbol=2048)
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), rw)
+    assert np.array_equal(woff.cpu().numpy().astype(np.uint64), rwo)
+    ds, de = binding.huffman_decode(words, woff, eoff, sub, Ld, n, outl)
+    assert np.array_equal(ds.cpu().numpy(), s)
+    if L[0] > 0:
+        d = ds.cpu().numpy()
+        assert np.array_equal(de.cpu().numpy()[d == 0], esc[s == 0])
+
+
 @pytest.mark.parametrize("s", [math.inf, 0.0, 1.0])
 @pytest.mark.parametrize("case", ["c1_2d_f64", "grf_3d_f32", "uneven_3d_f32"])
 def test_compress_round_trip_meets_bound(case, s):
